@@ -1,0 +1,129 @@
+/*
+ * cz.h -- C ABI of the GB300 wavelet codec for block-structured 3D fields.
+ *
+ * The codec is the first compression substage of CubismZ (Hadjidoukas and
+ * Wermelinger, arXiv 1903.07761): every cubic block of a 3D float field
+ * (Sec. 2.1: constant-size cubic blocks, power-of-two edge) goes through a
+ * full dyadic 3D interpolating-wavelet transform on the interval (Sec. 2.3
+ * "Wavelet-based compression" and "Wavelet types": W4, W4li, W3ai), its
+ * detail coefficients are thresholded against eps, and the block is stored
+ * as a bit-set mask plus the significant coefficients (Sec. 2.3).  An
+ * optional second substage byte-shuffles each block's output with the
+ * element size of the data (Sec. 2.3 "Lossless compression") and applies
+ * zero run-length coding.  Offsets of the per-block chunks come from an
+ * exclusive prefix sum (Sec. 2.2, the paper's MPI scan of file offsets),
+ * here a single-pass scan on the device.  Decompression reverses the steps
+ * block by block (Sec. 2.3 "Data decompression").
+ *
+ * Conventions
+ *  - Pointers named d_* are CUDA device pointers, h_* are host pointers.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy stream.
+ *  - All work is enqueued asynchronously on `stream`; the calls themselves
+ *    never allocate device memory and never synchronise unless stated.
+ *  - The caller owns every buffer.  Fields are dense C-order arrays
+ *    field[z][y][x] (x fastest) of float (CZ_F32) or double (CZ_F64).
+ *  - Return values: CZ_OK or a negative CZ_ERR_* code for errors found on
+ *    the host.  Errors found on the device (capacity, corrupt stream,
+ *    look-back timeout) are written to a status word in the workspace and
+ *    read with cz_status().  Kernels never trap.
+ *
+ * Stream layout (little-endian), produced and consumed only by this library:
+ *   header (128 B) | (nblocks+1) u64 chunk offsets | pad to 16 | chunks
+ *   chunk  = [u32 nnz][u32 ntok][ntok u32 tokens][literal words]  (stage 2)
+ *          = [u32 nnz][u32 0][payload]                            (no stage 2)
+ *   payload = 64 coarse values | B^3/32 u32 mask words | nnz values
+ * Blocks are numbered x fastest over the block grid.
+ */
+#ifndef CZ_H
+#define CZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* wavelet kinds (Sec. 2.3 "Wavelet types") */
+enum { CZ_W4 = 0, CZ_W4LI = 1, CZ_W3AI = 2 };
+/* element types: the paper's precision option (float, double) */
+enum { CZ_F32 = 0, CZ_F64 = 1 };
+/* threshold: t = eps * (max - min) of the whole field, or t = eps */
+enum { CZ_EPS_REL = 0, CZ_EPS_ABS = 1 };
+
+enum {
+  CZ_OK = 0,
+  CZ_ERR_ARG = -1,      /* invalid parameter or unsupported combination   */
+  CZ_ERR_CAPACITY = -2, /* output or workspace buffer too small           */
+  CZ_ERR_CORRUPT = -3,  /* stream header, offsets or chunk inconsistent   */
+  CZ_ERR_TIMEOUT = -4,  /* a bounded device-side wait gave up             */
+  CZ_ERR_CUDA = -5,     /* a CUDA runtime call failed                     */
+  CZ_ERR_BUDGET = -6    /* request refused by a memory budget             */
+};
+
+#define CZ_HEADER_BYTES 128
+
+typedef struct cz_params {
+  int32_t nx, ny, nz; /* field dims in elements; each a multiple of block   */
+  int32_t block;      /* cubic block edge B: 8, 16 or 32 (32 only for F32)  */
+  int32_t dtype;      /* CZ_F32 or CZ_F64                                   */
+  int32_t kind;       /* CZ_W4, CZ_W4LI or CZ_W3AI                          */
+  int32_t eps_mode;   /* CZ_EPS_REL (default) or CZ_EPS_ABS                 */
+  int32_t stage2;     /* 1: byte shuffle + zero-RLE each chunk; 0: raw      */
+  double eps;         /* tolerance, >= 0                                    */
+  double range;       /* >= 0: max - min supplied by the caller (skips the
+                         min/max pass); < 0: computed on the device        */
+} cz_params;
+
+/* Worst-case stream size for p.  Returns CZ_OK or CZ_ERR_ARG. */
+int cz_compress_bound(const cz_params *p, size_t *bytes);
+
+/* Device workspace needed by cz_compress / cz_decompress for p:
+ * a status word, the min/max keys and one u64 look-back word per block. */
+int cz_workspace_size(const cz_params *p, size_t *bytes);
+
+/* Compress d_field into d_out (capacity out_cap bytes).
+ * Steps: optional min/max pass (range < 0 and eps_mode REL), then one fused
+ * kernel per block: load, forward transform, threshold, mask + compaction,
+ * optional stage 2, decoupled look-back for the chunk offset, write.
+ * *d_out_bytes (device u64, may be NULL) receives the stream length; if it
+ * exceeds out_cap the status word is CZ_ERR_CAPACITY and the stream is
+ * incomplete.  d_ws must hold cz_workspace_size() bytes; it is overwritten.
+ * Host-side errors: CZ_ERR_ARG, CZ_ERR_CAPACITY (out_cap below the fixed
+ * header+table size, ws too small), CZ_ERR_CUDA. */
+int cz_compress(const cz_params *p, const void *d_field, void *d_out,
+                size_t out_cap, uint64_t *d_out_bytes, void *d_ws,
+                size_t ws_bytes, void *stream);
+
+/* Decompress the stream d_in (in_bytes long) into d_field (field_cap bytes).
+ * The parameters come from the stream header: pass a host copy of its first
+ * CZ_HEADER_BYTES bytes in h_header, or NULL to have the call copy it from
+ * the device (one synchronous 128-byte copy on `stream`).  Chunk offsets and
+ * chunk contents are validated on the device; a bad chunk sets the status
+ * word to CZ_ERR_CORRUPT and its block is written as zeros. */
+int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header,
+                  void *d_field, size_t field_cap, void *d_ws, size_t ws_bytes,
+                  void *stream);
+
+/* Parse a host copy of a stream header into *p (and the threshold used). */
+int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used);
+
+/* Synchronise `stream` and return the device status word of d_ws
+ * (CZ_OK or a CZ_ERR_* code set by a kernel). */
+int cz_status(const void *d_ws, void *stream);
+
+/* Human-readable text of a CZ_* code (static storage). */
+const char *cz_strerror(int code);
+
+/* Dense coefficients, for testing the transform alone: the forward
+ * transform of every block of d_field written in place of the field layout
+ * to d_coef (same shape and type), or the inverse of d_coef into d_field. */
+int cz_forward_dense(const cz_params *p, const void *d_field, void *d_coef,
+                     void *stream);
+int cz_inverse_dense(const cz_params *p, const void *d_coef, void *d_field,
+                     void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -292,11 +292,11 @@ def unshuffle(b: bytes, s: int) -> bytes:
 
 
 def rle_encode(b: bytes):
-    """-> (tokens as list of (lit, zrun), literal bytes)."""
+    """-> (tokens as list of (literal words, zero words), literal bytes)."""
     a = np.frombuffer(b, np.uint8).copy()
     tcap = a.size // 4 + 16
     tok = np.zeros(tcap, np.uint32)
-    lit = np.zeros(max(a.size, 1), np.uint8)
+    lit = np.zeros(max(a.size, 4), np.uint8)
     nt, nl = C.c_size_t(), C.c_size_t()
     r = lib().czo_rle_encode(_ptr(a), a.size, _ptr(tok), tcap, C.byref(nt),
                              _ptr(lit), lit.size, C.byref(nl))

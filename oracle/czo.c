@@ -135,14 +135,16 @@ void czo_unshuffle(const uint8_t *in, size_t nbytes, int s, uint8_t *out)
 }
 
 /* --------------------------------------------------------------------------
- * Zero run-length coding.  The input is cut into pairs
+ * Zero run-length coding of the shuffled payload, in 32-bit words (the
+ * payload is a whole number of words).  The word sequence is cut into pairs
  *   (literal run, zero run)
- * where every zero run is a maximal run of at least CZO_ZMIN zero bytes and
- * the literal run is everything between it and the previous such run; a
- * final pair with zero run 0 carries trailing literals.  Each pair is one
- * token (u32: literal length in the low 16 bits, zero-run length in the high
- * 16 bits); a literal run longer than 65535 first emits (65535, 0) tokens, a
- * zero run longer than 65535 emits (lit, 65535) and then (0, rest).
+ * where every zero run is a maximal run of at least CZO_ZMIN_WORDS zero
+ * words and the literal run is everything between it and the previous such
+ * run; a final pair with zero run 0 carries trailing literals.  Each pair is
+ * one token (u32: literal words in the low 16 bits, zero words in the high
+ * 16 bits); a literal run longer than 65535 words first emits (65535, 0)
+ * tokens, a zero run longer than 65535 emits (lit, 65535) and then
+ * (0, rest).  The literal words follow the tokens.
  * -------------------------------------------------------------------------- */
 static int emit_pair(size_t lit, size_t zr, uint32_t *tok, size_t cap, size_t *nt)
 {
@@ -162,22 +164,31 @@ static int emit_pair(size_t lit, size_t zr, uint32_t *tok, size_t cap, size_t *n
   return CZO_OK;
 }
 
+static uint32_t word_at(const uint8_t *in, size_t w)
+{
+  uint32_t v;
+  memcpy(&v, in + 4 * w, 4);
+  return v;
+}
+
 int64_t czo_rle_encode(const uint8_t *in, size_t n, uint32_t *tokens,
                        size_t tok_cap, size_t *ntok, uint8_t *lits,
                        size_t lit_cap, size_t *nlit)
 {
+  if (n % 4 != 0) return CZO_ERR_ARG;
+  const size_t W = n / 4;
   size_t nt = 0, nl = 0, lit_start = 0, i = 0;
-  while (i < n) {
-    if (in[i] != 0) {
+  while (i < W) {
+    if (word_at(in, i) != 0) {
       ++i;
       continue;
     }
     size_t j = i;
-    while (j < n && in[j] == 0) ++j;
-    if (j - i >= CZO_ZMIN) {
+    while (j < W && word_at(in, j) == 0) ++j;
+    if (j - i >= CZO_ZMIN_WORDS) {
       size_t lit = i - lit_start;
-      if (nl + lit > lit_cap) return CZO_ERR_CAPACITY;
-      memcpy(lits + nl, in + lit_start, lit);
+      if (4 * (nl + lit) > lit_cap) return CZO_ERR_CAPACITY;
+      memcpy(lits + 4 * nl, in + 4 * lit_start, 4 * lit);
       nl += lit;
       int r = emit_pair(lit, j - i, tokens, tok_cap, &nt);
       if (r) return r;
@@ -185,33 +196,36 @@ int64_t czo_rle_encode(const uint8_t *in, size_t n, uint32_t *tokens,
     }
     i = j;
   }
-  if (lit_start < n) {
-    size_t lit = n - lit_start;
-    if (nl + lit > lit_cap) return CZO_ERR_CAPACITY;
-    memcpy(lits + nl, in + lit_start, lit);
+  if (lit_start < W) {
+    size_t lit = W - lit_start;
+    if (4 * (nl + lit) > lit_cap) return CZO_ERR_CAPACITY;
+    memcpy(lits + 4 * nl, in + 4 * lit_start, 4 * lit);
     nl += lit;
     int r = emit_pair(lit, 0, tokens, tok_cap, &nt);
     if (r) return r;
   }
   *ntok = nt;
-  *nlit = nl;
-  return (int64_t)(4 * nt + nl);
+  *nlit = 4 * nl;
+  return (int64_t)(4 * nt + 4 * nl);
 }
 
+/* nlit and n in bytes (multiples of 4); token counts in words */
 int czo_rle_decode(const uint32_t *tokens, size_t ntok, const uint8_t *lits,
                    size_t nlit, uint8_t *out, size_t n)
 {
+  if (n % 4 != 0) return CZO_ERR_CORRUPT;
+  const size_t W = n / 4, NL = nlit / 4;
   size_t o = 0, l = 0;
   for (size_t q = 0; q < ntok; ++q) {
     size_t lit = tokens[q] & 0xFFFFu, zr = tokens[q] >> 16;
-    if (l + lit > nlit || o + lit + zr > n) return CZO_ERR_CORRUPT;
-    memcpy(out + o, lits + l, lit);
+    if (l + lit > NL || o + lit + zr > W) return CZO_ERR_CORRUPT;
+    memcpy(out + 4 * o, lits + 4 * l, 4 * lit);
     o += lit;
     l += lit;
-    memset(out + o, 0, zr);
+    memset(out + 4 * o, 0, 4 * zr);
     o += zr;
   }
-  return o == n ? CZO_OK : CZO_ERR_CORRUPT;
+  return o == W ? CZO_OK : CZO_ERR_CORRUPT;
 }
 
 /* --------------------------------------------------------------------------
@@ -315,7 +329,7 @@ int czo_compress_bound(const czo_params *p, size_t *bytes)
   size_t B = (size_t)p->block, s = p->dtype == CZO_F64 ? 8 : 4;
   size_t nb = (size_t)(p->nx / p->block) * (p->ny / p->block) * (p->nz / p->block);
   size_t pmax = 64 * s + B * B * B / 8 + (B * B * B - 64) * s;
-  size_t chunk = 16 + pmax + 8 * ((pmax + 65534) / 65535);
+  size_t chunk = 16 + pmax + 8 * ((pmax / 4 + 65534) / 65535);
   chunk = (chunk + 3) / 4 * 4;
   *bytes = (CZO_HEADER_BYTES + 8 * (nb + 1) + 15) / 16 * 16 + nb * chunk;
   return CZO_OK;

@@ -52,7 +52,7 @@ enum {
 
 #define CZO_HEADER_BYTES 128
 #define CZO_MAGIC 0x315A4343u /* bytes "CCZ1" */
-#define CZO_ZMIN 8            /* shortest zero run coded as a run (bytes) */
+#define CZO_ZMIN_WORDS 2      /* shortest zero run coded as a run (32-bit words) */
 
 typedef struct czo_params {
   int32_t nx, ny, nz; /* field dims in elements, C order [nz][ny][nx]        */
@@ -107,8 +107,9 @@ double czo_threshold(double eps, int eps_mode, double range);
 /* ---- stage 2 primitives ---------------------------------------------------- */
 void czo_shuffle(const uint8_t *in, size_t nbytes, int s, uint8_t *out);
 void czo_unshuffle(const uint8_t *in, size_t nbytes, int s, uint8_t *out);
-/* zero-RLE: tokens (u32 = literal_len | zero_run << 16) then the literals.
- * Returns bytes written (8-byte count header not included) or < 0.           */
+/* zero-RLE over 32-bit words (n a multiple of 4): tokens (u32 = literal words
+ * | zero words << 16) then the literal words.  *nlit is in bytes.  Returns
+ * bytes of tokens + literals, or < 0.                                         */
 int64_t czo_rle_encode(const uint8_t *in, size_t n, uint32_t *tokens,
                        size_t tok_cap, size_t *ntok, uint8_t *lits,
                        size_t lit_cap, size_t *nlit);

@@ -1,0 +1,305 @@
+// cz_api.cu -- host side of the C ABI declared in include/cz.h.
+//
+// Validates parameters, lays out the workspace, enqueues the min/max pass
+// (a0) and the per-block codec kernels on the caller's stream, and parses
+// stream headers.  No device memory is allocated here.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "../../include/cz.h"
+#include "cz_kernels.cuh"
+#include "cz_launch.h"
+
+using namespace czk;
+
+namespace {
+
+struct Shape {
+  int nbx, nby, nbz, nblocks, L, es;
+  unsigned long long data0;
+};
+
+int check(const cz_params *p, Shape *sh)
+{
+  if (!p) return CZ_ERR_ARG;
+  const int B = p->block;
+  if (B != 8 && B != 16 && B != 32) return CZ_ERR_ARG;
+  if (p->dtype != CZ_F32 && p->dtype != CZ_F64) return CZ_ERR_ARG;
+  if (p->dtype == CZ_F64 && B == 32) return CZ_ERR_ARG;  // 256 KiB tile: not provided
+  if (p->kind < CZ_W4 || p->kind > CZ_W3AI) return CZ_ERR_ARG;
+  if (p->eps_mode != CZ_EPS_REL && p->eps_mode != CZ_EPS_ABS) return CZ_ERR_ARG;
+  if (p->stage2 != 0 && p->stage2 != 1) return CZ_ERR_ARG;
+  if (!(p->eps >= 0) || std::isinf(p->eps)) return CZ_ERR_ARG;
+  if (std::isnan(p->range)) return CZ_ERR_ARG;
+  if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0) return CZ_ERR_ARG;
+  if (p->nx % B || p->ny % B || p->nz % B) return CZ_ERR_ARG;
+  const long long nb = (long long)(p->nx / B) * (p->ny / B) * (p->nz / B);
+  if (nb > (1ll << 30)) return CZ_ERR_ARG;
+  if (sh) {
+    sh->nbx = p->nx / B;
+    sh->nby = p->ny / B;
+    sh->nbz = p->nz / B;
+    sh->nblocks = (int)nb;
+    sh->L = B == 8 ? 1 : (B == 16 ? 2 : 3);
+    sh->es = p->dtype == CZ_F64 ? 8 : 4;
+    sh->data0 = (HEADER_BYTES + 8ull * (nb + 1) + 15) / 16 * 16;
+  }
+  return CZ_OK;
+}
+
+size_t ws_need(const Shape &sh) { return WS_HDR + 8ull * sh.nblocks; }
+
+cudaError_t run_compress(int dtype, int B, int kind, const FwdArgs *a, cudaStream_t s)
+{
+  if (dtype == CZ_F32) {
+    if (B == 8) return czl_compress_f32_b8(kind, a, s);
+    if (B == 16) return czl_compress_f32_b16(kind, a, s);
+    return czl_compress_f32_b32(kind, a, s);
+  }
+  if (B == 8) return czl_compress_f64_b8(kind, a, s);
+  return czl_compress_f64_b16(kind, a, s);
+}
+
+cudaError_t run_decompress(int dtype, int B, int kind, const InvArgs *a, cudaStream_t s)
+{
+  if (dtype == CZ_F32) {
+    if (B == 8) return czl_decompress_f32_b8(kind, a, s);
+    if (B == 16) return czl_decompress_f32_b16(kind, a, s);
+    return czl_decompress_f32_b32(kind, a, s);
+  }
+  if (B == 8) return czl_decompress_f64_b8(kind, a, s);
+  return czl_decompress_f64_b16(kind, a, s);
+}
+
+cudaError_t run_dense(int dtype, int B, int kind, int fwd, const DenseArgs *a, int nb, cudaStream_t s)
+{
+  if (dtype == CZ_F32) {
+    if (B == 8) return czl_dense_f32_b8(kind, fwd, a, nb, s);
+    if (B == 16) return czl_dense_f32_b16(kind, fwd, a, nb, s);
+    return czl_dense_f32_b32(kind, fwd, a, nb, s);
+  }
+  if (B == 8) return czl_dense_f64_b8(kind, fwd, a, nb, s);
+  return czl_dense_f64_b16(kind, fwd, a, nb, s);
+}
+
+template <typename T>
+cudaError_t run_minmax(const void *field, size_t n, WsHdr *ws, cudaStream_t s)
+{
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  size_t blocks = (n / (sizeof(T) == 4 ? 4 : 2) + 511) / 512;
+  const size_t cap = (size_t)sms * 4;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  k_minmax<T><<<(unsigned)blocks, 512, 0, s>>>(reinterpret_cast<const T *>(field), n, ws);
+  return cudaGetLastError();
+}
+
+unsigned long long rd64(const unsigned char *p)
+{
+  unsigned long long v;
+  std::memcpy(&v, p, 8);
+  return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cz_compress_bound(const cz_params *p, size_t *bytes)
+{
+  Shape sh;
+  const int r = check(p, &sh);
+  if (r != CZ_OK || !bytes) return r ? r : CZ_ERR_ARG;
+  const size_t B = (size_t)p->block, s = (size_t)sh.es;
+  const size_t pmax = 64 * s + B * B * B / 8 + (B * B * B - 64) * s;
+  // raw chunk: 8 + pmax; stage-2 chunk: 8 + 4 * tokens + literals, where
+  // every token but the last and the splits removes >= 2 zero words
+  size_t chunk = 16 + pmax + 8 * ((pmax / 4 + 65534) / 65535);
+  chunk = (chunk + 3) / 4 * 4;
+  *bytes = (size_t)sh.data0 + (size_t)sh.nblocks * chunk;
+  return CZ_OK;
+}
+
+int cz_workspace_size(const cz_params *p, size_t *bytes)
+{
+  Shape sh;
+  const int r = check(p, &sh);
+  if (r != CZ_OK || !bytes) return r ? r : CZ_ERR_ARG;
+  *bytes = ws_need(sh);
+  return CZ_OK;
+}
+
+int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out_cap,
+                uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes, void *stream)
+{
+  Shape sh;
+  int r = check(p, &sh);
+  if (r != CZ_OK) return r;
+  if (!d_field || !d_out || !d_ws) return CZ_ERR_ARG;
+  if (((uintptr_t)d_field % 16) || ((uintptr_t)d_out % 16) || ((uintptr_t)d_ws % 16)) return CZ_ERR_ARG;
+  if (out_cap < sh.data0 || ws_bytes < ws_need(sh)) return CZ_ERR_CAPACITY;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  WsHdr *ws = reinterpret_cast<WsHdr *>(d_ws);
+  if (cudaMemsetAsync(d_ws, 0, ws_need(sh), s) != cudaSuccess) return CZ_ERR_CUDA;
+  if (p->range < 0) {
+    if (cudaMemsetAsync(&ws->minkey, 0xFF, 8, s) != cudaSuccess) return CZ_ERR_CUDA;
+    const size_t n = (size_t)p->nx * p->ny * p->nz;
+    const cudaError_t e = p->dtype == CZ_F32 ? run_minmax<float>(d_field, n, ws, s)
+                                             : run_minmax<double>(d_field, n, ws, s);
+    if (e != cudaSuccess) return CZ_ERR_CUDA;
+  }
+  FwdArgs a{};
+  a.field = d_field;
+  a.out = reinterpret_cast<unsigned char *>(d_out);
+  a.out_bytes = reinterpret_cast<unsigned long long *>(d_out_bytes);
+  a.ws = d_ws;
+  a.out_cap = out_cap;
+  a.data0 = sh.data0;
+  a.eps = p->eps;
+  a.range = p->range;
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  a.nbx = sh.nbx;
+  a.nby = sh.nby;
+  a.nbz = sh.nbz;
+  a.nblocks = sh.nblocks;
+  a.eps_mode = p->eps_mode;
+  a.stage2 = p->stage2;
+  a.kind = p->kind;
+  a.dtype = p->dtype;
+  return run_compress(p->dtype, p->block, p->kind, &a, s) == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
+}
+
+int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used)
+{
+  if (!h_in || !p || n < (size_t)HEADER_BYTES) return CZ_ERR_ARG;
+  const unsigned char *h = reinterpret_cast<const unsigned char *>(h_in);
+  unsigned magic;
+  unsigned short ver, hb;
+  std::memcpy(&magic, h, 4);
+  std::memcpy(&ver, h + 4, 2);
+  std::memcpy(&hb, h + 6, 2);
+  if (magic != MAGIC || ver != 1 || hb != HEADER_BYTES) return CZ_ERR_CORRUPT;
+  cz_params q{};
+  std::memcpy(&q.nx, h + 8, 4);
+  std::memcpy(&q.ny, h + 12, 4);
+  std::memcpy(&q.nz, h + 16, 4);
+  q.block = h[20];
+  q.dtype = h[21];
+  q.kind = h[22];
+  q.stage2 = h[23];
+  q.eps_mode = h[24];
+  std::memcpy(&q.eps, h + 32, 8);
+  std::memcpy(&q.range, h + 64, 8);
+  if (std::isnan(q.range)) return CZ_ERR_CORRUPT;
+  if (check(&q, nullptr) != CZ_OK) return CZ_ERR_CORRUPT;
+  unsigned nb;
+  std::memcpy(&nb, h + 28, 4);
+  if ((long long)nb != (long long)(q.nx / q.block) * (q.ny / q.block) * (q.nz / q.block)) return CZ_ERR_CORRUPT;
+  *p = q;
+  if (t_used) std::memcpy(t_used, h + 40, 8);
+  return CZ_OK;
+}
+
+int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header, void *d_field,
+                  size_t field_cap, void *d_ws, size_t ws_bytes, void *stream)
+{
+  if (!d_in || !d_field || !d_ws) return CZ_ERR_ARG;
+  if (((uintptr_t)d_in % 16) || ((uintptr_t)d_field % 16) || ((uintptr_t)d_ws % 16)) return CZ_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned char hb[HEADER_BYTES];
+  if (in_bytes < (size_t)HEADER_BYTES) return CZ_ERR_CORRUPT;
+  if (h_header) {
+    std::memcpy(hb, h_header, HEADER_BYTES);
+  } else {
+    if (cudaMemcpyAsync(hb, d_in, HEADER_BYTES, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CZ_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CZ_ERR_CUDA;
+  }
+  cz_params p;
+  int r = cz_read_header(hb, HEADER_BYTES, &p, nullptr);
+  if (r != CZ_OK) return r;
+  Shape sh;
+  check(&p, &sh);
+  const unsigned long long total = rd64(hb + 80), data_bytes = rd64(hb + 72);
+  if (total > in_bytes || sh.data0 + data_bytes != total) return CZ_ERR_CORRUPT;
+  if ((size_t)p.nx * p.ny * p.nz * sh.es > field_cap) return CZ_ERR_CAPACITY;
+  if (ws_bytes < (size_t)WS_HDR) return CZ_ERR_CAPACITY;
+  if (cudaMemsetAsync(d_ws, 0, WS_HDR, s) != cudaSuccess) return CZ_ERR_CUDA;
+  InvArgs a{};
+  a.in = reinterpret_cast<const unsigned char *>(d_in);
+  a.field = d_field;
+  a.ws = d_ws;
+  a.in_bytes = total;
+  a.data0 = sh.data0;
+  a.nx = p.nx;
+  a.ny = p.ny;
+  a.nz = p.nz;
+  a.nbx = sh.nbx;
+  a.nby = sh.nby;
+  a.nbz = sh.nbz;
+  a.nblocks = sh.nblocks;
+  a.stage2 = p.stage2;
+  return run_decompress(p.dtype, p.block, p.kind, &a, s) == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
+}
+
+int cz_status(const void *d_ws, void *stream)
+{
+  if (!d_ws) return CZ_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned st = 0;
+  if (cudaMemcpyAsync(&st, d_ws, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CZ_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CZ_ERR_CUDA;
+  return (int)st;
+}
+
+const char *cz_strerror(int code)
+{
+  switch (code) {
+    case CZ_OK: return "ok";
+    case CZ_ERR_ARG: return "invalid argument or unsupported combination";
+    case CZ_ERR_CAPACITY: return "buffer too small";
+    case CZ_ERR_CORRUPT: return "corrupt or inconsistent stream";
+    case CZ_ERR_TIMEOUT: return "device-side wait timed out";
+    case CZ_ERR_CUDA: return "CUDA runtime error";
+    case CZ_ERR_BUDGET: return "request exceeds the memory budget";
+    default: return "unknown error";
+  }
+}
+
+static int dense(const cz_params *p, const void *src, void *dst, int fwd, void *stream)
+{
+  Shape sh;
+  const int r = check(p, &sh);
+  if (r != CZ_OK) return r;
+  if (!src || !dst) return CZ_ERR_ARG;
+  DenseArgs a{};
+  a.src = src;
+  a.dst = dst;
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  a.nbx = sh.nbx;
+  a.nby = sh.nby;
+  a.nbz = sh.nbz;
+  return run_dense(p->dtype, p->block, p->kind, fwd, &a, sh.nblocks, reinterpret_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? CZ_OK
+             : CZ_ERR_CUDA;
+}
+
+int cz_forward_dense(const cz_params *p, const void *d_field, void *d_coef, void *stream)
+{
+  return dense(p, d_field, d_coef, 1, stream);
+}
+
+int cz_inverse_dense(const cz_params *p, const void *d_coef, void *d_field, void *stream)
+{
+  return dense(p, d_coef, d_field, 0, stream);
+}
+
+}  // extern "C"

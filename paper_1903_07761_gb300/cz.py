@@ -1,0 +1,213 @@
+"""Python binding of the C ABI in include/cz.h (argument marshalling only).
+
+Every compute step runs in the CUDA kernels of ``libcz.so``; this module
+loads the library (building it first if it is missing or stale), fills the
+``cz_params`` struct, and passes device pointers and the current torch CUDA
+stream through ctypes.  There is no CPU fallback: if the library cannot be
+loaded, importing the functions raises.
+
+The functions named ``cz_*`` mirror the ABI one to one.  ``compress`` /
+``decompress`` are thin conveniences over them for torch CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+from . import _build
+
+W4, W4LI, W3AI = 0, 1, 2
+F32, F64 = 0, 1
+EPS_REL, EPS_ABS = 0, 1
+OK, ERR_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_TIMEOUT, ERR_CUDA, ERR_BUDGET = 0, -1, -2, -3, -4, -5, -6
+HEADER_BYTES = 128
+KINDS = {"w4": W4, "w4li": W4LI, "w3ai": W3AI}
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+        ("block", C.c_int32), ("dtype", C.c_int32), ("kind", C.c_int32),
+        ("eps_mode", C.c_int32), ("stage2", C.c_int32),
+        ("eps", C.c_double), ("range", C.c_double),
+    ]
+
+
+class CzError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {cz_strerror(code)} ({code})" if what else cz_strerror(code))
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded libcz.so (built in-tree on first use)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            P = C.c_void_p
+            PP = C.POINTER(Params)
+            L.cz_compress_bound.argtypes = [PP, C.POINTER(C.c_size_t)]
+            L.cz_workspace_size.argtypes = [PP, C.POINTER(C.c_size_t)]
+            L.cz_compress.argtypes = [PP, P, P, C.c_size_t, P, P, C.c_size_t, P]
+            L.cz_decompress.argtypes = [P, C.c_size_t, P, P, C.c_size_t, P, C.c_size_t, P]
+            L.cz_read_header.argtypes = [P, C.c_size_t, PP, C.POINTER(C.c_double)]
+            L.cz_status.argtypes = [P, P]
+            L.cz_strerror.argtypes = [C.c_int]
+            L.cz_strerror.restype = C.c_char_p
+            L.cz_forward_dense.argtypes = [PP, P, P, P]
+            L.cz_inverse_dense.argtypes = [PP, P, P, P]
+            for f in (L.cz_compress_bound, L.cz_workspace_size, L.cz_compress, L.cz_decompress,
+                      L.cz_read_header, L.cz_status, L.cz_forward_dense, L.cz_inverse_dense):
+                f.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------ raw ABI
+def cz_compress_bound(p: Params) -> int:
+    n = C.c_size_t()
+    r = lib().cz_compress_bound(C.byref(p), C.byref(n))
+    if r != OK:
+        raise CzError(r, "cz_compress_bound")
+    return n.value
+
+
+def cz_workspace_size(p: Params) -> int:
+    n = C.c_size_t()
+    r = lib().cz_workspace_size(C.byref(p), C.byref(n))
+    if r != OK:
+        raise CzError(r, "cz_workspace_size")
+    return n.value
+
+
+def cz_compress(p: Params, d_field: int, d_out: int, out_cap: int, d_out_bytes: int,
+                d_ws: int, ws_bytes: int, stream: int) -> int:
+    return lib().cz_compress(C.byref(p), d_field, d_out, out_cap, d_out_bytes or None,
+                             d_ws, ws_bytes, stream or None)
+
+
+def cz_decompress(d_in: int, in_bytes: int, h_header, d_field: int, field_cap: int,
+                  d_ws: int, ws_bytes: int, stream: int) -> int:
+    hdr = None
+    if h_header is not None:
+        hdr = C.create_string_buffer(bytes(h_header[:HEADER_BYTES]), HEADER_BYTES)
+    return lib().cz_decompress(d_in, in_bytes, hdr, d_field, field_cap, d_ws, ws_bytes,
+                               stream or None)
+
+
+def cz_read_header(h_in: bytes):
+    buf = C.create_string_buffer(bytes(h_in[:HEADER_BYTES]), HEADER_BYTES)
+    p = Params()
+    t = C.c_double()
+    r = lib().cz_read_header(buf, HEADER_BYTES, C.byref(p), C.byref(t))
+    if r != OK:
+        raise CzError(r, "cz_read_header")
+    return p, t.value
+
+
+def cz_status(d_ws: int, stream: int) -> int:
+    return lib().cz_status(d_ws, stream or None)
+
+
+def cz_strerror(code: int) -> str:
+    return lib().cz_strerror(code).decode()
+
+
+def cz_forward_dense(p: Params, d_field: int, d_coef: int, stream: int) -> int:
+    return lib().cz_forward_dense(C.byref(p), d_field, d_coef, stream or None)
+
+
+def cz_inverse_dense(p: Params, d_coef: int, d_field: int, stream: int) -> int:
+    return lib().cz_inverse_dense(C.byref(p), d_coef, d_field, stream or None)
+
+
+# ------------------------------------------------------------------ torch conveniences
+def params_for(shape, dtype_is_f64: bool, block: int, kind, eps: float, eps_mode: int = EPS_REL,
+               stage2: bool = True, range_: float = -1.0) -> Params:
+    nz, ny, nx = shape
+    if isinstance(kind, str):
+        kind = KINDS[kind]
+    return Params(nx, ny, nz, block, F64 if dtype_is_f64 else F32, kind, eps_mode,
+                  int(stage2), float(eps), float(range_))
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Workspace:
+    """Device workspace sized for the largest parameter set seen so far."""
+
+    def __init__(self, device=None):
+        self.buf = None
+        self.device = device
+
+    def get(self, nbytes: int):
+        import torch
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device or "cuda")
+        return self.buf
+
+
+def compress(field, block: int = 32, kind="w4", eps: float = 1e-3, eps_mode: int = EPS_REL,
+             stage2: bool = True, range_: float = -1.0, out=None, ws: Workspace | None = None,
+             stream=None, check: bool = True):
+    """Compress a contiguous CUDA tensor [nz, ny, nx] (float32/float64).
+
+    Returns (stream_tensor, nbytes_tensor); the stream is stream_tensor[:nbytes].
+    With check=True the call synchronises and raises on a device-side error.
+    """
+    import torch
+    assert field.is_cuda and field.is_contiguous() and field.dim() == 3
+    p = params_for(tuple(field.shape), field.dtype == torch.float64, block, kind, eps, eps_mode,
+                   stage2, range_)
+    cap = cz_compress_bound(p)
+    if out is None or out.numel() < cap:
+        out = torch.empty(cap, dtype=torch.uint8, device=field.device)
+    ws = ws or Workspace(field.device)
+    wsb = ws.get(cz_workspace_size(p))
+    nbytes = torch.zeros(1, dtype=torch.int64, device=field.device)
+    s = _stream(stream)
+    r = cz_compress(p, field.data_ptr(), out.data_ptr(), out.numel(), nbytes.data_ptr(),
+                    wsb.data_ptr(), wsb.numel(), s)
+    if r != OK:
+        raise CzError(r, "cz_compress")
+    if check:
+        st = cz_status(wsb.data_ptr(), s)
+        if st != OK:
+            raise CzError(st, "cz_compress (device)")
+    return out, nbytes
+
+
+def decompress(stream_t, nbytes: int | None = None, header: bytes | None = None, out=None,
+               ws: Workspace | None = None, stream=None, check: bool = True):
+    """Decompress a CUDA uint8 stream tensor into a new (or given) field tensor."""
+    import torch
+    if header is None:
+        header = stream_t[:HEADER_BYTES].cpu().numpy().tobytes()
+    p, _ = cz_read_header(header)
+    n = int(nbytes) if nbytes is not None else stream_t.numel()
+    dt = torch.float64 if p.dtype == F64 else torch.float32
+    if out is None:
+        out = torch.empty((p.nz, p.ny, p.nx), dtype=dt, device=stream_t.device)
+    ws = ws or Workspace(stream_t.device)
+    wsb = ws.get(256)
+    s = _stream(stream)
+    r = cz_decompress(stream_t.data_ptr(), n, header, out.data_ptr(),
+                      out.numel() * out.element_size(), wsb.data_ptr(), wsb.numel(), s)
+    if r != OK:
+        raise CzError(r, "cz_decompress")
+    if check:
+        st = cz_status(wsb.data_ptr(), s)
+        if st != OK:
+            raise CzError(st, "cz_decompress (device)")
+    return out

@@ -363,15 +363,15 @@ def test_shuffle_is_byte_matrix_transpose(s):
 
 
 def _segments_to_bytes(segs):
-    out = bytearray()
+    words = []
     for kind, *rest in segs:
         if kind == "lit":
-            out += bytes(rest[0])
+            words += list(rest[0])
         elif kind == "zero":
-            out += bytes(rest[0])
+            words += [0] * rest[0]
         elif kind == "litfill":
-            out += bytes([rest[1]]) * rest[0]
-    return bytes(out)
+            words += [rest[1]] * rest[0]
+    return np.array(words, np.uint32).tobytes()
 
 
 def test_rle_tokens_match_hand_derived_fixtures():
@@ -381,32 +381,46 @@ def test_rle_tokens_match_hand_derived_fixtures():
         b = _segments_to_bytes(case["segments"])
         toks, lits = O.rle_encode(b)
         assert [list(t) for t in toks] == case["tokens"], case["name"]
-        assert lits == bytes(x for x in b if True)[: len(lits)] or True
-        assert sum(t[0] for t in toks) == len(lits)
+        assert 4 * sum(t[0] for t in toks) == len(lits)
         assert O.rle_decode(toks, lits, len(b)) == b, case["name"]
 
 
 @pytest.mark.parametrize("pattern", ["random", "zeros", "nozero", "sparse", "long"])
 def test_rle_roundtrip_adversarial(pattern):
-    rng = np.random.default_rng(hash(pattern) % 2 ** 32)
-    n = 200_000
+    rng = np.random.default_rng(sum(map(ord, pattern)))
+    n = 300_000  # words
     if pattern == "random":
-        a = rng.integers(0, 256, n, dtype=np.uint8)
+        a = rng.integers(0, 2 ** 32, n, dtype=np.uint32)
     elif pattern == "zeros":
-        a = np.zeros(n, np.uint8)
+        a = np.zeros(n, np.uint32)
     elif pattern == "nozero":
-        a = rng.integers(1, 256, n, dtype=np.uint8)
+        a = rng.integers(1, 2 ** 32, n, dtype=np.uint32)
     elif pattern == "sparse":
-        a = (rng.random(n) < 0.05).astype(np.uint8) * rng.integers(1, 256, n, dtype=np.uint8)
+        a = (rng.random(n) < 0.2).astype(np.uint32) * rng.integers(1, 2 ** 32, n, dtype=np.uint32)
     else:
-        a = np.zeros(n, np.uint8)
-        a[70_000:140_000] = rng.integers(1, 256, 70_000, dtype=np.uint8)
+        a = np.zeros(n, np.uint32)
+        a[70_000:140_000] = rng.integers(1, 2 ** 32, 70_000, dtype=np.uint32)
     b = a.tobytes()
     toks, lits = O.rle_encode(b)
     assert all(0 <= l <= 65535 and 0 <= z <= 65535 for l, z in toks)
     assert O.rle_decode(toks, lits, len(b)) == b
-    # every coded run is at least 8 zeros unless it is a split remainder
-    assert sum(z for _, z in toks) + len(lits) == len(b)
+    assert 4 * sum(z for _, z in toks) + len(lits) == len(b)
+    # the literal words are exactly the words outside coded runs, in order
+    coded = np.zeros(n, bool)
+    pos = 0
+    for l, z in toks:
+        pos += l
+        coded[pos:pos + z] = True
+        pos += z
+    np.testing.assert_array_equal(np.frombuffer(lits, np.uint32), a[~coded])
+    assert np.all(a[coded] == 0)
+    # every maximal zero run of >= 2 words is coded, single zero words are not
+    iz = np.concatenate([[False], a == 0, [False]])
+    starts = np.flatnonzero(~iz[:-1] & iz[1:])
+    ends = np.flatnonzero(iz[:-1] & ~iz[1:])
+    for s_, e_ in zip(starts, ends):
+        assert coded[s_:e_].all() == (e_ - s_ >= 2)
+        assert coded[s_:e_].any() == (e_ - s_ >= 2)
 
 
 @pytest.mark.parametrize("kind", KINDS)
