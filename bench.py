@@ -1,0 +1,463 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 wavelet codec (one JSON line on stdout, rank 0).
+
+Workload: the bandwidth-bound large case -- a 1024^3 FP32 pressure field of
+the synthetic bubble-cloud recipe (200 tanh-interface bubbles, eight
+low-wavenumber pressure modes, a pressure drop inside the bubbles), cut into
+32^3 blocks, eps = 1e-3 of the field range, stage 2 on.  It stands in for
+the paper's cloud-cavitation pressure snapshots (Sec. 3.1, Sec. 4.3 uses
+1024^3 per node).  One step is the whole hot path on that field:
+  a0 min/max -> compress (transform, threshold, mask, compaction, stage 2,
+  look-back offsets) -> decompress (stage-2 inverse, scatter, inverse
+  transform),
+all through the C ABI (cz_compress / cz_decompress).  The field (4 GiB) is
+larger than L2, so no L2 flush is needed between steps.
+
+value = field bytes / (compress + decompress time) in GB/s, whole job over
+N ranks (each rank compresses its own field; no data-path collective).
+
+--impl reference times the CPU oracle (the plain C reference written from
+the paper) on host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compress+decompress GB/s & %HBM peak @eps=1e-3 1024^3 FP32; served p50/p99 ms"
+UNIT = "GB/s"
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1903_07761_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(kernel: str, units: float):
+    """DRAM bytes of one launch from the committed ncu summary, if the
+    kernel sources are unchanged since it was taken (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        e = d[kernel]
+        if e.get("csrc_sha") != csrc_hash():
+            return None
+        return e["dram_bytes_per_unit"] * units
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.dev).uuid)
+            ident = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+            fd, self.path = tempfile.mkstemp(prefix="czclk", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", ident, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 8:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        smax = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workload
+def make_field(n: int, seed: int):
+    from paper_1903_07761_gb300 import inputs
+    return inputs.cavitation("p", n, seed=seed)
+
+
+def cpu_oracle_run(field_np, block, kind, eps, slabs, rng):
+    """Oracle compress + decompress of the first `slabs` block-rows of z
+    (threshold from the full field's range).  Returns (bytes, seconds)."""
+    import oracle as O
+    sample = field_np[: slabs * block]
+    t0 = time.perf_counter()
+    s = O.compress(sample, block, kind, eps, range_=rng)
+    O.decompress(s)
+    return sample.nbytes, time.perf_counter() - t0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1903_07761_gb300 import cz
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    kind = cz.KINDS[args.kind]
+    n, B = args.n, args.block
+    field_np = make_field(n, seed=2000 + rank)
+    field = torch.from_numpy(field_np).to(dev)
+    nbytes_field = field.numel() * field.element_size()
+    p = cz.params_for(tuple(field.shape), False, B, kind, args.eps, cz.EPS_REL, True, -1.0)
+    cap = cz.cz_compress_bound(p)
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    ws = torch.empty(cz.cz_workspace_size(p), dtype=torch.uint8, device=dev)
+    nb = torch.zeros(1, dtype=torch.int64, device=dev)
+    rec = torch.empty_like(field)
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+
+    def compress_call(pp=p):
+        r = cz.cz_compress(pp, field.data_ptr(), out.data_ptr(), cap, nb.data_ptr(),
+                           ws.data_ptr(), ws.numel(), s)
+        if r != cz.OK:
+            raise cz.CzError(r, "cz_compress")
+
+    compress_call()
+    st = cz.cz_status(ws.data_ptr(), s)
+    if st != cz.OK:
+        raise cz.CzError(st, "cz_compress (device)")
+    stream_len = int(nb.item())
+    header = out[:cz.HEADER_BYTES].cpu().numpy().tobytes()
+    hdr_c = cz.C.create_string_buffer(header, cz.HEADER_BYTES)
+
+    def decompress_call():
+        r = cz.lib().cz_decompress(out.data_ptr(), stream_len, hdr_c, rec.data_ptr(),
+                                   nbytes_field, ws.data_ptr(), ws.numel(), s)
+        if r != cz.OK:
+            raise cz.CzError(r, "cz_decompress")
+
+    def step():
+        compress_call()
+        decompress_call()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for e0, e1, e2 in ev:
+        e0.record(stream)
+        compress_call()
+        e1.record(stream)
+        decompress_call()
+        e2.record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    comp_ms = sum(a.elapsed_time(b) for a, b, _ in ev) / args.steps
+    dec_ms = sum(b.elapsed_time(c) for _, b, c in ev) / args.steps
+    st = cz.cz_status(ws.data_ptr(), s)
+    if st != cz.OK:
+        raise cz.CzError(st, "device status after timed steps")
+    stream_len = int(nb.item())
+
+    # quality of the last step (measurement only)
+    diff = (rec.double() - field.double())
+    mse = float((diff * diff).mean().item())
+    linf = float(diff.abs().max().item())
+    fmin, fmax = float(field.min().item()), float(field.max().item())
+    psnr = 20 * math.log10((fmax - fmin) / (2 * math.sqrt(mse))) if mse > 0 else float("inf")
+    del diff
+
+    # the dominant kernel alone: compress with the range supplied (skips a0;
+    # the call is one 256 KiB memset plus k_compress)
+    p_kern = cz.params_for(tuple(field.shape), False, B, kind, args.eps, cz.EPS_REL, True,
+                           fmax - fmin)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(max(args.steps, 5))]
+    for _ in range(2):
+        compress_call(p_kern)
+    for a_, b_ in kev:
+        a_.record(stream)
+        compress_call(p_kern)
+        b_.record(stream)
+    torch.cuda.synchronize()
+    kern_ms = sum(a_.elapsed_time(b_) for a_, b_ in kev) / len(kev)
+    kern_stream = int(nb.item())
+
+    # end to end through the ABI with host buffers (pinned), copies included
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(field_np).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        h_stream = torch.empty(cap, dtype=torch.uint8).pin_memory()
+        h_nb = torch.empty(1, dtype=torch.int64).pin_memory()
+        reps = max(2, min(args.steps, 5))
+        copied_in = copied_out = 0
+
+        def e2e_step():
+            nonlocal copied_in, copied_out
+            field.copy_(h_in, non_blocking=True)
+            compress_call()
+            h_nb.copy_(nb, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            ln = int(h_nb.item())
+            h_stream[:ln].copy_(out[:ln], non_blocking=True)
+            r = cz.lib().cz_decompress(out.data_ptr(), ln, hdr_c, rec.data_ptr(), nbytes_field,
+                                       ws.data_ptr(), ws.numel(), s)
+            if r != cz.OK:
+                raise cz.CzError(r, "cz_decompress")
+            h_out.copy_(rec, non_blocking=True)
+            copied_in = nbytes_field
+            copied_out = 8 + ln + nbytes_field
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / reps
+        e2e = {"value": world * nbytes_field / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": copied_in, "d2h_bytes_per_step": copied_out}
+
+    # other kinds (context: the headline is per kind)
+    per_kind = {}
+    if not args.headline_only:
+        for kname, kk in cz.KINDS.items():
+            pk = cz.params_for(tuple(field.shape), False, B, kk, args.eps, cz.EPS_REL, True, -1.0)
+            ln_ref = {}
+
+            def kstep():
+                r = cz.cz_compress(pk, field.data_ptr(), out.data_ptr(), cap, nb.data_ptr(),
+                                   ws.data_ptr(), ws.numel(), s)
+                assert r == cz.OK
+                ln_ref["n"] = int(nb.item())
+
+            kstep()
+            hb = cz.C.create_string_buffer(out[:cz.HEADER_BYTES].cpu().numpy().tobytes(), 128)
+            ln = ln_ref["n"]
+
+            def kdec():
+                r = cz.lib().cz_decompress(out.data_ptr(), ln, hb, rec.data_ptr(), nbytes_field,
+                                           ws.data_ptr(), ws.numel(), s)
+                assert r == cz.OK
+            reps = 5
+            ce = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+                   torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for a_, b_, c_ in ce:
+                a_.record(stream)
+                cz.cz_compress(pk, field.data_ptr(), out.data_ptr(), cap, nb.data_ptr(),
+                               ws.data_ptr(), ws.numel(), s)
+                b_.record(stream)
+                kdec()
+                c_.record(stream)
+            torch.cuda.synchronize()
+            cm = statistics.median(a_.elapsed_time(b_) for a_, b_, _ in ce)
+            dm = statistics.median(b_.elapsed_time(c_) for _, b_, c_ in ce)
+            d = rec.double() - field.double()
+            mse_k = float((d * d).mean().item())
+            del d
+            per_kind[kname] = {
+                "compress_gbs": nbytes_field / cm / 1e6, "decompress_gbs": nbytes_field / dm / 1e6,
+                "cr": nbytes_field / ln,
+                "psnr_db": 20 * math.log10((fmax - fmin) / (2 * math.sqrt(mse_k))) if mse_k > 0 else None}
+
+    # reductions over ranks (max time)
+    import torch.distributed as dist
+    if world > 1:
+        tt = torch.tensor([total_ms, comp_ms, dec_ms, kern_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms, comp_ms, dec_ms, kern_ms = tt.tolist()
+    ms_per_step = total_ms / args.steps
+    value = world * nbytes_field / (ms_per_step * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        slabs = max(1, args.cpu_slabs)
+        byts, secs = cpu_oracle_run(field_np, B, kind, args.eps, slabs, fmax - fmin)
+        cpu = {"value": byts / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"compress+decompress of the first {slabs} z-slab(s) of 32 cells "
+                         f"({byts / 2**20:.0f} MiB, {slabs * (n // B) ** 2} blocks) of the same "
+                         f"field, threshold from the full range, single thread, {secs:.1f} s"}
+
+    peak, peak_src = measured_peaks()
+    kern_bytes = nbytes_field + kern_stream  # read the field, write the stream
+    achieved = kern_bytes / (kern_ms * 1e-3) / 1e9
+    nblocks = (n // B) ** 3
+    traffic = traffic_per_launch("k_compress_f32_b32", nblocks)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded bubble-cloud pressure field; paper datasets unavailable)",
+        "config": {"workload": f"p-field {n}^3 FP32, {B}^3 blocks, {args.kind}, eps=1e-3*range, "
+                               f"stage2 on, range computed on device",
+                   "global_batch": world, "field_bytes": nbytes_field,
+                   "l2": "inputs larger than L2 (4 GiB field per step), no flush needed",
+                   "parallelism": f"replicas x{world} (independent fields, no collective)"},
+        "compress_gbs": nbytes_field / comp_ms / 1e6, "decompress_gbs": nbytes_field / dec_ms / 1e6,
+        "compress_ms": comp_ms, "decompress_ms": dec_ms,
+        "cr": nbytes_field / stream_len, "psnr_db": psnr, "linf_over_t": linf / (args.eps * (fmax - fmin)),
+        "roofline": {"bound": "hbm", "kernel": "k_compress (range supplied)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": f"{peak_src} hbm_gbs",
+                     "traffic": traffic, "algorithmic_bytes": kern_bytes,
+                     "kernel_ms": kern_ms},
+        "hbm_frac_of_nominal_8000": achieved / 8000.0,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+        "per_kind": per_kind,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1903_07761_gb300 import cz as _cz  # noqa: F401  (kind names only)
+    import numpy as np
+    kind = {"w4": 0, "w4li": 1, "w3ai": 2}[args.kind]
+    n, B = args.n, args.block
+    field_np = make_field(n, seed=2000)
+    rng = float(field_np.max()) - float(field_np.min())
+    slabs = 1
+    for _ in range(args.warmup):
+        cpu_oracle_run(field_np, B, kind, args.eps, slabs, rng)
+    times = []
+    byts = 0
+    for _ in range(args.steps):
+        byts, secs = cpu_oracle_run(field_np, B, kind, args.eps, slabs, rng)
+        times.append(secs)
+    ms = 1e3 * sum(times) / len(times)
+    value = byts / (ms * 1e-3) / 1e9
+    sample = (f"compress+decompress of one z-slab of 32 cells ({byts / 2**20:.0f} MiB, "
+              f"{(n // B) ** 2} blocks) of the {n}^3 field per step, single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"p-field {n}^3 FP32, {B}^3 blocks, {args.kind}, eps=1e-3*range, "
+                               f"stage2 on (CPU oracle on a bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cz", choices=["cz", "reference"])
+    ap.add_argument("--kind", default="w3ai", choices=["w4", "w4li", "w3ai"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--block", type=int, default=32)
+    ap.add_argument("--eps", type=float, default=1e-3)
+    ap.add_argument("--cpu-slabs", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--headline-only", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

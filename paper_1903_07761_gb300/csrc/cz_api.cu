@@ -1,18 +1,21 @@
 // cz_api.cu -- host side of the C ABI declared in include/cz.h.
 //
-// Validates parameters, lays out the workspace, enqueues the min/max pass
-// (a0) and the per-block codec kernels on the caller's stream, and parses
-// stream headers.  No device memory is allocated here.
+// Validates parameters, lays out the workspace, builds the TMA tensor map of
+// the field, enqueues the min/max pass (a0) and the per-block codec kernels
+// on the caller's stream, and parses stream headers.  No device memory is
+// allocated here.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstring>
 
 #include "../../include/cz.h"
-#include "cz_kernels.cuh"
 #include "cz_launch.h"
+#include "cz_pair.cuh"
 
-using namespace czk;
+using namespace czp;
 
 namespace {
 
@@ -49,49 +52,91 @@ int check(const cz_params *p, Shape *sh)
   return CZ_OK;
 }
 
-size_t ws_need(const Shape &sh) { return WS_HDR + 8ull * sh.nblocks; }
+struct Lanes {
+  cudaError_t (*compress)(int, const CUtensorMap *, const FwdArgs *, int, cudaStream_t);
+  cudaError_t (*decompress)(int, const InvArgs *, int, cudaStream_t);
+  cudaError_t (*dense)(int, int, const DenseArgs *, int, cudaStream_t);
+  int (*occupancy)(int, int);
+  int (*scratch)(void);
+};
 
-cudaError_t run_compress(int dtype, int B, int kind, const FwdArgs *a, cudaStream_t s)
+#define CZ_LANES(sfx) \
+  Lanes { czl_compress_##sfx, czl_decompress_##sfx, czl_dense_##sfx, czl_occupancy_##sfx, czl_scratch_##sfx }
+
+Lanes lanes_for(int dtype, int B)
 {
   if (dtype == CZ_F32) {
-    if (B == 8) return czl_compress_f32_b8(kind, a, s);
-    if (B == 16) return czl_compress_f32_b16(kind, a, s);
-    return czl_compress_f32_b32(kind, a, s);
+    if (B == 8) return CZ_LANES(f32_b8);
+    if (B == 16) return CZ_LANES(f32_b16);
+    return CZ_LANES(f32_b32);
   }
-  if (B == 8) return czl_compress_f64_b8(kind, a, s);
-  return czl_compress_f64_b16(kind, a, s);
+  if (B == 8) return CZ_LANES(f64_b8);
+  return CZ_LANES(f64_b16);
 }
 
-cudaError_t run_decompress(int dtype, int B, int kind, const InvArgs *a, cudaStream_t s)
+int sm_count()
 {
-  if (dtype == CZ_F32) {
-    if (B == 8) return czl_decompress_f32_b8(kind, a, s);
-    if (B == 16) return czl_decompress_f32_b16(kind, a, s);
-    return czl_decompress_f32_b32(kind, a, s);
-  }
-  if (B == 8) return czl_decompress_f64_b8(kind, a, s);
-  return czl_decompress_f64_b16(kind, a, s);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return sms > 0 ? sms : 1;
 }
 
-cudaError_t run_dense(int dtype, int B, int kind, int fwd, const DenseArgs *a, int nb, cudaStream_t s)
+// persistent grids: one CTA per resident slot, at most one per block
+int grid_for(const cz_params *p, const Shape &sh, int which)
 {
-  if (dtype == CZ_F32) {
-    if (B == 8) return czl_dense_f32_b8(kind, fwd, a, nb, s);
-    if (B == 16) return czl_dense_f32_b16(kind, fwd, a, nb, s);
-    return czl_dense_f32_b32(kind, fwd, a, nb, s);
+  const Lanes L = lanes_for(p->dtype, p->block);
+  const int occ = L.occupancy(p->kind, which);
+  const long long g = (long long)sm_count() * (occ > 0 ? occ : 1);
+  return (int)(g < sh.nblocks ? g : sh.nblocks);
+}
+
+// workspace: header | one u64 look-back word per block | overflow scratch
+size_t lb_bytes(const Shape &sh) { return (8ull * sh.nblocks + 255) / 256 * 256; }
+
+size_t ws_need(const cz_params *p, const Shape &sh)
+{
+  const Lanes L = lanes_for(p->dtype, p->block);
+  const size_t scr = (size_t)L.scratch();
+  return WS_HDR + lb_bytes(sh) + (scr ? scr * (size_t)grid_for(p, sh, 0) : 0);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
   }
-  if (B == 8) return czl_dense_f64_b8(kind, fwd, a, nb, s);
-  return czl_dense_f64_b16(kind, fwd, a, nb, s);
+  return fn;
+}
+
+// 3D tiled tensor map over the field, one B^3 box per block (no swizzle)
+bool make_tile_map(CUtensorMap *tm, const cz_params *p, const void *d_field)
+{
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t es = p->dtype == CZ_F64 ? 8 : 4;
+  const cuuint64_t dims[3] = {(cuuint64_t)p->nx, (cuuint64_t)p->ny, (cuuint64_t)p->nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)p->nx * es, (cuuint64_t)p->nx * p->ny * es};
+  const cuuint32_t box[3] = {(cuuint32_t)p->block, (cuuint32_t)p->block, (cuuint32_t)p->block};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r =
+      enc(tm, p->dtype == CZ_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+          const_cast<void *>(d_field), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 template <typename T>
 cudaError_t run_minmax(const void *field, size_t n, WsHdr *ws, cudaStream_t s)
 {
-  int dev = 0, sms = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   size_t blocks = (n / (sizeof(T) == 4 ? 4 : 2) + 511) / 512;
-  const size_t cap = (size_t)sms * 4;
+  const size_t cap = (size_t)sm_count() * 4;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   k_minmax<T><<<(unsigned)blocks, 512, 0, s>>>(reinterpret_cast<const T *>(field), n, ws);
@@ -116,8 +161,8 @@ int cz_compress_bound(const cz_params *p, size_t *bytes)
   if (r != CZ_OK || !bytes) return r ? r : CZ_ERR_ARG;
   const size_t B = (size_t)p->block, s = (size_t)sh.es;
   const size_t pmax = 64 * s + B * B * B / 8 + (B * B * B - 64) * s;
-  // raw chunk: 8 + pmax; stage-2 chunk: 8 + 4 * tokens + literals, where
-  // every token but the last and the splits removes >= 2 zero words
+  // raw chunk: 8 + pmax; stage-2 chunk: 8 + 4 * tokens + literal words,
+  // where every token but the last and the splits removes >= 2 zero words
   size_t chunk = 16 + pmax + 8 * ((pmax / 4 + 65534) / 65535);
   chunk = (chunk + 3) / 4 * 4;
   *bytes = (size_t)sh.data0 + (size_t)sh.nblocks * chunk;
@@ -129,7 +174,7 @@ int cz_workspace_size(const cz_params *p, size_t *bytes)
   Shape sh;
   const int r = check(p, &sh);
   if (r != CZ_OK || !bytes) return r ? r : CZ_ERR_ARG;
-  *bytes = ws_need(sh);
+  *bytes = ws_need(p, sh);
   return CZ_OK;
 }
 
@@ -141,10 +186,10 @@ int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out
   if (r != CZ_OK) return r;
   if (!d_field || !d_out || !d_ws) return CZ_ERR_ARG;
   if (((uintptr_t)d_field % 16) || ((uintptr_t)d_out % 16) || ((uintptr_t)d_ws % 16)) return CZ_ERR_ARG;
-  if (out_cap < sh.data0 || ws_bytes < ws_need(sh)) return CZ_ERR_CAPACITY;
+  if (out_cap < sh.data0 || ws_bytes < ws_need(p, sh)) return CZ_ERR_CAPACITY;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   WsHdr *ws = reinterpret_cast<WsHdr *>(d_ws);
-  if (cudaMemsetAsync(d_ws, 0, ws_need(sh), s) != cudaSuccess) return CZ_ERR_CUDA;
+  if (cudaMemsetAsync(d_ws, 0, WS_HDR + lb_bytes(sh), s) != cudaSuccess) return CZ_ERR_CUDA;
   if (p->range < 0) {
     if (cudaMemsetAsync(&ws->minkey, 0xFF, 8, s) != cudaSuccess) return CZ_ERR_CUDA;
     const size_t n = (size_t)p->nx * p->ny * p->nz;
@@ -152,11 +197,14 @@ int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out
                                              : run_minmax<double>(d_field, n, ws, s);
     if (e != cudaSuccess) return CZ_ERR_CUDA;
   }
+  const Lanes L = lanes_for(p->dtype, p->block);
   FwdArgs a{};
   a.field = d_field;
   a.out = reinterpret_cast<unsigned char *>(d_out);
   a.out_bytes = reinterpret_cast<unsigned long long *>(d_out_bytes);
   a.ws = d_ws;
+  a.scratch_per_cta = (unsigned long long)L.scratch();
+  a.scratch = a.scratch_per_cta ? reinterpret_cast<unsigned char *>(d_ws) + WS_HDR + lb_bytes(sh) : nullptr;
   a.out_cap = out_cap;
   a.data0 = sh.data0;
   a.eps = p->eps;
@@ -172,7 +220,9 @@ int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out
   a.stage2 = p->stage2;
   a.kind = p->kind;
   a.dtype = p->dtype;
-  return run_compress(p->dtype, p->block, p->kind, &a, s) == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
+  CUtensorMap tm;
+  if (!make_tile_map(&tm, p, d_field)) return CZ_ERR_CUDA;
+  return L.compress(p->kind, &tm, &a, grid_for(p, sh, 0), s) == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
 }
 
 int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used)
@@ -244,7 +294,8 @@ int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header, void 
   a.nbz = sh.nbz;
   a.nblocks = sh.nblocks;
   a.stage2 = p.stage2;
-  return run_decompress(p.dtype, p.block, p.kind, &a, s) == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
+  const Lanes L = lanes_for(p.dtype, p.block);
+  return L.decompress(p.kind, &a, grid_for(&p, sh, 1), s) == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
 }
 
 int cz_status(const void *d_ws, void *stream)
@@ -277,6 +328,7 @@ static int dense(const cz_params *p, const void *src, void *dst, int fwd, void *
   const int r = check(p, &sh);
   if (r != CZ_OK) return r;
   if (!src || !dst) return CZ_ERR_ARG;
+  if (((uintptr_t)src % 16) || ((uintptr_t)dst % 16)) return CZ_ERR_ARG;
   DenseArgs a{};
   a.src = src;
   a.dst = dst;
@@ -286,8 +338,8 @@ static int dense(const cz_params *p, const void *src, void *dst, int fwd, void *
   a.nbx = sh.nbx;
   a.nby = sh.nby;
   a.nbz = sh.nbz;
-  return run_dense(p->dtype, p->block, p->kind, fwd, &a, sh.nblocks, reinterpret_cast<cudaStream_t>(stream)) ==
-                 cudaSuccess
+  const Lanes L = lanes_for(p->dtype, p->block);
+  return L.dense(p->kind, fwd, &a, sh.nblocks, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
              ? CZ_OK
              : CZ_ERR_CUDA;
 }

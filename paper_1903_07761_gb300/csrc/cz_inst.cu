@@ -1,10 +1,11 @@
 // cz_inst.cu -- kernel instantiations for one (element type, block edge).
-// Built once per combination with -DCZ_T=float|double -DCZ_B=8|16|32 so the
-// heavily unrolled kernels compile in parallel.  Exposes plain launchers.
+// Built once per combination with -DCZ_T=float|double -DCZ_TNAME=f32|f64
+// -DCZ_B=8|16|32 so the heavily unrolled kernels compile in parallel.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
-#include "cz_kernels.cuh"
 #include "cz_launch.h"
+#include "cz_pair.cuh"
 
 #ifndef CZ_T
 #error "CZ_T must be defined"
@@ -13,9 +14,11 @@
 #error "CZ_B must be defined"
 #endif
 
-using namespace czk;
+using namespace czp;
 
 namespace {
+
+using G = G2<CZ_T, CZ_B>;
 
 // raise the dynamic shared-memory limit of kernel KERN once per device
 template <auto KERN>
@@ -33,33 +36,52 @@ cudaError_t prepare(int smem)
 }
 
 template <int KIND>
-cudaError_t compress_k(const FwdArgs &a, cudaStream_t s)
+cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, int grid, cudaStream_t s)
 {
-  using G = Geo<CZ_T, CZ_B>;
-  cudaError_t e = prepare<k_compress<CZ_T, CZ_B, KIND>>(G::SMEM);
+  cudaError_t e = prepare<k_compress2<CZ_T, CZ_B, KIND>>(G::SMEM_C);
   if (e != cudaSuccess) return e;
-  k_compress<CZ_T, CZ_B, KIND><<<a.nblocks, G::NT, G::SMEM, s>>>(a);
+  k_compress2<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_C, s>>>(tm, a);
   return cudaGetLastError();
 }
 
 template <int KIND>
-cudaError_t decompress_k(const InvArgs &a, cudaStream_t s)
+cudaError_t decompress_k(const InvArgs &a, int grid, cudaStream_t s)
 {
-  using G = Geo<CZ_T, CZ_B>;
-  cudaError_t e = prepare<k_decompress<CZ_T, CZ_B, KIND>>(G::SMEM);
+  cudaError_t e = prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D);
   if (e != cudaSuccess) return e;
-  k_decompress<CZ_T, CZ_B, KIND><<<a.nblocks, G::NT, G::SMEM, s>>>(a);
+  k_decompress2<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_D, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int KIND, bool FWD>
 cudaError_t dense_k(const DenseArgs &a, int nblocks, cudaStream_t s)
 {
-  using G = Geo<CZ_T, CZ_B>;
-  cudaError_t e = prepare<k_dense<CZ_T, CZ_B, KIND, FWD>>(G::XBYTES);
+  cudaError_t e = prepare<k_dense2<CZ_T, CZ_B, KIND, FWD>>(G::XB + G::ADB);
   if (e != cudaSuccess) return e;
-  k_dense<CZ_T, CZ_B, KIND, FWD><<<nblocks, G::NT, G::XBYTES, s>>>(a);
+  k_dense2<CZ_T, CZ_B, KIND, FWD><<<nblocks, G::NT, G::XB + G::ADB, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int KIND>
+int occupancy_c()
+{
+  if (prepare<k_compress2<CZ_T, CZ_B, KIND>>(G::SMEM_C) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_compress2<CZ_T, CZ_B, KIND>, G::NT, G::SMEM_C) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
+template <int KIND>
+int occupancy_d()
+{
+  if (prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decompress2<CZ_T, CZ_B, KIND>, G::NT, G::SMEM_D) !=
+      cudaSuccess)
+    return 0;
+  return n;
 }
 
 }  // namespace
@@ -68,21 +90,22 @@ cudaError_t dense_k(const DenseArgs &a, int nblocks, cudaStream_t s)
 #define CZ_CAT(a, b) CZ_CAT2(a, b)
 #define CZ_SUFFIX CZ_CAT(CZ_CAT(CZ_TNAME, _b), CZ_B)
 
-extern "C" cudaError_t CZ_CAT(czl_compress_, CZ_SUFFIX)(int kind, const FwdArgs *a, cudaStream_t s)
+extern "C" cudaError_t CZ_CAT(czl_compress_, CZ_SUFFIX)(int kind, const CUtensorMap *tm, const FwdArgs *a,
+                                                         int grid, cudaStream_t s)
 {
   switch (kind) {
-    case W4: return compress_k<W4>(*a, s);
-    case W4LI: return compress_k<W4LI>(*a, s);
-    default: return compress_k<W3AI>(*a, s);
+    case W4: return compress_k<W4>(*tm, *a, grid, s);
+    case W4LI: return compress_k<W4LI>(*tm, *a, grid, s);
+    default: return compress_k<W3AI>(*tm, *a, grid, s);
   }
 }
 
-extern "C" cudaError_t CZ_CAT(czl_decompress_, CZ_SUFFIX)(int kind, const InvArgs *a, cudaStream_t s)
+extern "C" cudaError_t CZ_CAT(czl_decompress_, CZ_SUFFIX)(int kind, const InvArgs *a, int grid, cudaStream_t s)
 {
   switch (kind) {
-    case W4: return decompress_k<W4>(*a, s);
-    case W4LI: return decompress_k<W4LI>(*a, s);
-    default: return decompress_k<W3AI>(*a, s);
+    case W4: return decompress_k<W4>(*a, grid, s);
+    case W4LI: return decompress_k<W4LI>(*a, grid, s);
+    default: return decompress_k<W3AI>(*a, grid, s);
   }
 }
 
@@ -103,4 +126,22 @@ extern "C" cudaError_t CZ_CAT(czl_dense_, CZ_SUFFIX)(int kind, int fwd, const De
   }
 }
 
-extern "C" int CZ_CAT(czl_smem_, CZ_SUFFIX)(void) { return Geo<CZ_T, CZ_B>::SMEM; }
+// CTAs per SM of the compress (which = 0) or decompress (which = 1) kernel
+extern "C" int CZ_CAT(czl_occupancy_, CZ_SUFFIX)(int kind, int which)
+{
+  if (which == 0) {
+    switch (kind) {
+      case W4: return occupancy_c<W4>();
+      case W4LI: return occupancy_c<W4LI>();
+      default: return occupancy_c<W3AI>();
+    }
+  }
+  switch (kind) {
+    case W4: return occupancy_d<W4>();
+    case W4LI: return occupancy_d<W4LI>();
+    default: return occupancy_d<W3AI>();
+  }
+}
+
+// overflow scratch bytes per persistent compress CTA
+extern "C" int CZ_CAT(czl_scratch_, CZ_SUFFIX)(void) { return G::SCR; }

@@ -1,19 +1,23 @@
 // cz_launch.h -- internal launchers, one set per (element type, block edge).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
-namespace czk {
+namespace czp {
 struct FwdArgs;
 struct InvArgs;
 struct DenseArgs;
-}  // namespace czk
+}  // namespace czp
 
-#define CZ_DECLARE_LAUNCHERS(sfx)                                                                \
-  extern "C" cudaError_t czl_compress_##sfx(int kind, const czk::FwdArgs *a, cudaStream_t s);   \
-  extern "C" cudaError_t czl_decompress_##sfx(int kind, const czk::InvArgs *a, cudaStream_t s); \
-  extern "C" cudaError_t czl_dense_##sfx(int kind, int fwd, const czk::DenseArgs *a, int nblocks, \
-                                         cudaStream_t s);                                       \
-  extern "C" int czl_smem_##sfx(void);
+#define CZ_DECLARE_LAUNCHERS(sfx)                                                                    \
+  extern "C" cudaError_t czl_compress_##sfx(int kind, const CUtensorMap *tm, const czp::FwdArgs *a, \
+                                            int grid, cudaStream_t s);                              \
+  extern "C" cudaError_t czl_decompress_##sfx(int kind, const czp::InvArgs *a, int grid,           \
+                                              cudaStream_t s);                                      \
+  extern "C" cudaError_t czl_dense_##sfx(int kind, int fwd, const czp::DenseArgs *a, int nblocks,   \
+                                         cudaStream_t s);                                           \
+  extern "C" int czl_occupancy_##sfx(int kind, int which);                                         \
+  extern "C" int czl_scratch_##sfx(void);
 
 CZ_DECLARE_LAUNCHERS(f32_b8)
 CZ_DECLARE_LAUNCHERS(f32_b16)

@@ -1,0 +1,1528 @@
+// cz_pair.cuh -- the codec kernels in the "column pair" layout.
+//
+// A CTA owns one cubic B^3 block.  Thread (a, y) keeps the two z-columns at
+// x = 2a and x = 2a + 1 of row y in registers as B packed pairs (E, O), so
+//   * at the finest level the x-transform of a pair is local except for the
+//     neighbouring pairs' values (warp shuffles over the B/2 lanes of a row),
+//     the y-transform exchanges whole pairs through shared-memory planes,
+//     and the z-transform is register code on packed pairs (FP32x2 ops);
+//   * warps hold rows of one parity, so in the y-exchange one warp stores
+//     while another loads and computes, without divergence;
+//   * coarser levels live on the E column only and reuse the single-value
+//     line steps of cz_device.cuh.
+// Every value is produced by the same operation sequence as the reference
+// definition of each wavelet step (explicitly rounded, never fused).
+//
+// Significance: |d| >= t is an unsigned compare of the magnitude bits; the
+// per-thread bit columns over z are turned into the stream's row words (bit
+// x of row (z, y)) by a B x B bit-matrix transpose over the lanes of a row.
+//
+// k_compress2 is persistent: one CTA per SM slot walks the blocks in ticket
+// order and prefetches the next block's tile with a TMA bulk-tensor copy
+// while it works on the current one.
+#pragma once
+
+#include <cuda.h>
+
+#include "cz_device.cuh"
+
+namespace czp {
+using namespace czd;
+
+// numeric values of the public status codes
+constexpr unsigned ST_CAPACITY = (unsigned)-2;
+constexpr unsigned ST_CORRUPT = (unsigned)-3;
+constexpr unsigned ST_TIMEOUT = (unsigned)-4;
+constexpr int HEADER_BYTES = 128;
+constexpr unsigned MAGIC = 0x315A4343u;
+constexpr int WS_HDR = 256;
+constexpr unsigned WAIT_LIMIT = 1u << 24;
+
+struct WsHdr {
+  unsigned status;
+  unsigned ticket;
+  unsigned pad0, pad1;
+  unsigned long long minkey, maxkey;
+  unsigned long long out_bytes;
+};
+
+struct FwdArgs {
+  const void *field;
+  unsigned char *out;
+  unsigned long long *out_bytes;  // may be null
+  void *ws;
+  unsigned char *scratch;         // per-CTA overflow payload space (may be null)
+  unsigned long long out_cap, data0, scratch_per_cta;
+  double eps, range;
+  int nx, ny, nz, nbx, nby, nbz, nblocks;
+  int eps_mode, stage2, kind, dtype;
+};
+
+struct InvArgs {
+  const unsigned char *in;
+  void *field;
+  void *ws;
+  unsigned long long in_bytes, data0;
+  int nx, ny, nz, nbx, nby, nbz, nblocks;
+  int stage2;
+};
+
+struct DenseArgs {
+  const void *src;
+  void *dst;
+  int nx, ny, nz, nbx, nby, nbz;
+};
+
+// ------------------------------------------------------------ pairs
+template <typename T>
+struct V2T;
+template <>
+struct V2T<float> {
+  using type = float2;
+};
+template <>
+struct V2T<double> {
+  using type = double2;
+};
+
+__device__ __forceinline__ float2 mk2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ double2 mk2(double s) { return make_double2(s, s); }
+// Pair arithmetic lane by lane with explicitly rounded scalar ops.  (The
+// packed f32x2 multiply and add are each exact, but chained packed
+// multiply -> add sequences were measured to differ from separately rounded
+// scalar ops: they are not used on the exact path.)
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+  return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+  return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 add2(double2 a, double2 b)
+{
+  return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 mul2(double2 a, double2 b)
+{
+  return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+}
+// subtraction lane by lane (exactly a - b, signed zeros included)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+  return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 sub2(double2 a, double2 b)
+{
+  return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y));
+}
+
+// magnitude bits for the significance compare
+__device__ __forceinline__ unsigned long long magbits(float v)
+{
+  return __float_as_uint(v) & 0x7fffffffu;
+}
+__device__ __forceinline__ unsigned long long magbits(double v)
+{
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+// keep iff !(|d| < t): for t >= 0 (or +inf) this is magbits(d) >= magbits(t);
+// a NaN threshold keeps everything
+template <typename T>
+__device__ __forceinline__ unsigned long long thr_bits(T t)
+{
+  return (t != t) ? 0ull : magbits(t);
+}
+
+// ------------------------------------------------------------ geometry
+template <typename T, int B>
+struct G2 {
+  static constexpr int NT = B * B / 2;
+  static constexpr int NW = NT / 32;
+  static constexpr int HP = B / 2;  // lanes per row
+  static constexpr int L = (B == 8) ? 1 : (B == 16) ? 2 : 3;
+  static constexpr int Q = B / 4;
+  static constexpr int ES = (int)sizeof(T);
+  static constexpr int NVOX = B * B * B;
+  static constexpr int NMW = NVOX / 32;
+  static constexpr int MASKB = NVOX / 8;
+  static constexpr int PMAX = 64 * ES + MASKB + (NVOX - 64) * ES;
+  static constexpr int WMAX = PMAX / 4;
+  static constexpr int NBWMAX = (WMAX + 31) / 32;
+  static constexpr int TILE = NVOX * ES;
+  static constexpr int ZB = (B == 32) ? 4 : (B == 16 ? (ES == 4 ? 16 : 4) : 8);
+  static constexpr int XB = ZB * B * B * ES;
+  static constexpr int ADB = ZB * (B / 2) * B * ES;
+  static constexpr int ROWB = B * B * 4;
+  static constexpr int BUDGET = 227 * 1024 - 2048;
+  static constexpr int PCAP0 = (BUDGET - TILE - XB - ADB) / 128 * 128;
+  static constexpr int PMAX_AL = (PMAX + 127) / 128 * 128;
+  static constexpr int PCAP = PCAP0 < PMAX_AL ? PCAP0 : PMAX_AL;  // smem payload capacity (compress)
+  static constexpr bool OVERFLOW = PCAP < PMAX;
+  static constexpr int NBWC = (PCAP / 4 + 31) / 32;
+  static constexpr int AUXC = ROWB + 4 * NBWC * 4;  // row offsets + stage-2 arrays
+  static constexpr int R2C0 = (XB + ADB) > AUXC ? (XB + ADB) : AUXC;
+  static constexpr int R2C = (R2C0 + 127) / 128 * 128;
+  static constexpr int SMEM_C = TILE + R2C + PCAP;
+  // overflow scratch per CTA: payload + stage-2 arrays
+  static constexpr int SCR = OVERFLOW ? ((PMAX + 4 * NBWMAX * 4 + 255) / 256 * 256) : 0;
+  // decompress: no tile; the whole payload always fits
+  static constexpr int AUXD = ROWB + 2 * NT * 4;
+  static constexpr int R2D0 = (XB + ADB) > AUXD ? (XB + ADB) : AUXD;
+  static constexpr int R2D = (R2D0 + 127) / 128 * 128;
+  static constexpr int SMEM_D = R2D + PMAX_AL;
+  static_assert(SMEM_C <= 227 * 1024 - 1024, "compress shared memory");
+  static_assert(SMEM_D <= 227 * 1024 - 1024, "decompress shared memory");
+};
+
+// ------------------------------------------------------------ TMA / mbarrier
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar)
+{
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_tile(const CUtensorMap *tm, void *dst, unsigned long long *bar,
+                                              int x, int y, int z, unsigned bytes)
+{
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// bounded wait for the mbarrier phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+  const unsigned addr = smem_u32(bar);
+  for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// ------------------------------------------------------------ bit transpose
+// Rows x = 2a + p of a B x B bit matrix (bit z), row 2a in r0 and 2a+1 in r1
+// of lane a of a B/2-lane row segment.  Afterwards r0 / r1 hold the column
+// words of z = 2a / 2a+1 (bit x).  Recursive block swap (Hacker's Delight
+// 7-3); row distance j >= 2 is a lane distance j/2.
+template <int B>
+__device__ __forceinline__ void bit_transpose(unsigned &r0, unsigned &r1, int a)
+{
+#pragma unroll
+  for (int j = B / 2; j >= 2; j >>= 1) {
+    const unsigned m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu : 0x33333333u;
+    const int ld = j >> 1;
+    const unsigned p0 = __shfl_xor_sync(FULL, r0, ld);
+    const unsigned p1 = __shfl_xor_sync(FULL, r1, ld);
+    if (!(a & ld)) {
+      r0 ^= (((r0 >> j) ^ p0) & m) << j;
+      r1 ^= (((r1 >> j) ^ p1) & m) << j;
+    } else {
+      r0 ^= ((p0 >> j) ^ r0) & m;
+      r1 ^= ((p1 >> j) ^ r1) & m;
+    }
+  }
+  const unsigned t = ((r0 >> 1) ^ r1) & 0x55555555u;
+  r0 ^= t << 1;
+  r1 ^= t;
+}
+
+// ============================================================ level 0 (pairs)
+// per-lane stencil of the finest x-level: pair a holds coarse node a (E)
+// and detail a (O) of its row
+template <typename T>
+struct XSt {
+  int src[4];  // W4: lanes of the four coarse sources
+  T w[4];
+  int usrc[3];  // W4li: lanes of the update details
+  T uw[3];
+  int nt;
+  int s1, s2;  // W3ai: lanes of the two average sources
+  T aw[3];
+  bool bnd;
+};
+
+template <typename T, int KIND>
+__device__ __forceinline__ XSt<T> make_xst(int a, int m, int seg)
+{
+  XSt<T> s;
+  if (KIND == W4 || KIND == W4LI) {
+    const W4Row r = w4_row(a, m);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      s.src[q] = seg + r.j0 + q;
+      s.w[q] = (T)r.w[q];
+    }
+  }
+  if (KIND == W4LI) {
+    const LiSrc ls = li_src(a, m);
+    s.nt = ls.nt;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      int kk = ls.k0 + t;
+      kk = kk < m ? kk : m - 1;
+      s.usrc[t] = seg + kk;
+      s.uw[t] = li_lookup<T>(m, a, t);
+    }
+  }
+  if (KIND == W3AI) {
+    const AiRow r = ai_row(a, m);
+    s.s1 = seg + r.s1;
+    s.s2 = seg + r.s2;
+    s.aw[0] = (T)r.w0;
+    s.aw[1] = (T)r.w1;
+    s.aw[2] = (T)r.w2;
+    s.bnd = r.bnd;
+  }
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T pred4s(const T (&w)[4], T c0, T c1, T c2, T c3)
+{
+  T p = mulx(w[0], c0);
+  p = addx(p, mulx(w[1], c1));
+  p = addx(p, mulx(w[2], c2));
+  p = addx(p, mulx(w[3], c3));
+  return mulx(p, (T)0.0625);
+}
+
+template <typename T>
+__device__ __forceinline__ T ai_preds(T a, T a1, T a2, T w0, T w1, T w2, bool bnd)
+{
+  const T x0 = bnd ? a : a1, x1 = bnd ? a1 : a2;
+  T q = addx(mulx(w0, x0), mulx(w1, x1));
+  if (bnd) q = addx(q, mulx(w2, a2));
+  return addx(a, mulx(q, (T)0.125));
+}
+
+template <typename T, int KIND, typename T2>
+__device__ __forceinline__ void x0_fwd(const XSt<T> &s, T2 &v)
+{
+  T E = v.x, O = v.y;
+  if constexpr (KIND == W4 || KIND == W4LI) {
+    const T c0 = shfl(E, s.src[0]), c1 = shfl(E, s.src[1]), c2 = shfl(E, s.src[2]), c3 = shfl(E, s.src[3]);
+    O = subx(O, pred4s(s.w, c0, c1, c2, c3));
+    if constexpr (KIND == W4LI) {
+      const T d0 = shfl(O, s.usrc[0]), d1 = shfl(O, s.usrc[1]), d2 = shfl(O, s.usrc[2]);
+      T acc = mulx(s.uw[0], d0);
+      if (s.nt > 1) acc = addx(acc, mulx(s.uw[1], d1));
+      if (s.nt > 2) acc = addx(acc, mulx(s.uw[2], d2));
+      E = addx(E, acc);
+    }
+  } else {
+    const T a = mulx(addx(E, O), (T)0.5);
+    const T a1 = shfl(a, s.s1), a2 = shfl(a, s.s2);
+    O = subx(E, ai_preds(a, a1, a2, s.aw[0], s.aw[1], s.aw[2], s.bnd));
+    E = a;
+  }
+  v.x = E;
+  v.y = O;
+}
+
+template <typename T, int KIND, typename T2>
+__device__ __forceinline__ void x0_inv(const XSt<T> &s, T2 &v)
+{
+  T E = v.x, O = v.y;
+  if constexpr (KIND == W4 || KIND == W4LI) {
+    if constexpr (KIND == W4LI) {
+      const T d0 = shfl(O, s.usrc[0]), d1 = shfl(O, s.usrc[1]), d2 = shfl(O, s.usrc[2]);
+      T acc = mulx(s.uw[0], d0);
+      if (s.nt > 1) acc = addx(acc, mulx(s.uw[1], d1));
+      if (s.nt > 2) acc = addx(acc, mulx(s.uw[2], d2));
+      E = subx(E, acc);
+    }
+    const T c0 = shfl(E, s.src[0]), c1 = shfl(E, s.src[1]), c2 = shfl(E, s.src[2]), c3 = shfl(E, s.src[3]);
+    O = addx(O, pred4s(s.w, c0, c1, c2, c3));
+  } else {
+    const T a1 = shfl(E, s.s1), a2 = shfl(E, s.s2);
+    const T f0 = addx(ai_preds(E, a1, a2, s.aw[0], s.aw[1], s.aw[2], s.bnd), O);
+    O = subx(mulx((T)2, E), f0);
+    E = f0;
+  }
+  v.x = E;
+  v.y = O;
+}
+
+// ---- packed forms for the y- and z-levels of the pairs (both columns)
+template <typename T2, typename T>
+__device__ __forceinline__ T2 pred4p(const T (&w)[4], T2 c0, T2 c1, T2 c2, T2 c3)
+{
+  T2 p = mul2(mk2(w[0]), c0);
+  p = add2(p, mul2(mk2(w[1]), c1));
+  p = add2(p, mul2(mk2(w[2]), c2));
+  p = add2(p, mul2(mk2(w[3]), c3));
+  return mul2(p, mk2((T)0.0625));
+}
+
+template <typename T2, typename T>
+__device__ __forceinline__ T2 ai_predp(T2 a, T2 a1, T2 a2, T w0, T w1, T w2, bool bnd)
+{
+  const T2 x0 = bnd ? a : a1, x1 = bnd ? a1 : a2;
+  T2 q = add2(mul2(mk2(w0), x0), mul2(mk2(w1), x1));
+  if (bnd) q = add2(q, mul2(mk2(w2), a2));
+  return add2(a, mul2(q, mk2((T)0.125)));
+}
+
+// per-row stencil of the finest y-level (row y, m = B/2)
+template <typename T>
+struct YSt {
+  int src[4];  // coarse rows (even y) of the prediction
+  T w[4];
+  int u[3];  // detail rows (odd y) of the update
+  T uw[3];
+  int nt;
+  int k1, k2;  // average rows (pair index) of the W3ai prediction
+  T aw[3];
+  bool bnd;
+};
+
+template <typename T, int KIND>
+__device__ __forceinline__ YSt<T> make_yst(int y, int m)
+{
+  YSt<T> s;
+  const int k = y >> 1;
+  if (KIND == W4 || KIND == W4LI) {
+    const W4Row r = w4_row(k, m);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      s.src[q] = 2 * (r.j0 + q);
+      s.w[q] = (T)r.w[q];
+    }
+  }
+  if (KIND == W4LI) {
+    const LiSrc ls = li_src(k, m);
+    s.nt = ls.nt;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      int kk = ls.k0 + t;
+      kk = kk < m ? kk : m - 1;
+      s.u[t] = 2 * kk + 1;
+      s.uw[t] = li_lookup<T>(m, k, t);
+    }
+  }
+  if (KIND == W3AI) {
+    const AiRow r = ai_row(k, m);
+    s.k1 = r.s1;
+    s.k2 = r.s2;
+    s.aw[0] = (T)r.w0;
+    s.aw[1] = (T)r.w1;
+    s.aw[2] = (T)r.w2;
+    s.bnd = r.bnd;
+  }
+  return s;
+}
+
+template <typename T2, typename T>
+__device__ __forceinline__ T2 li_accp(const T (&uw)[3], int nt, T2 d0, T2 d1, T2 d2)
+{
+  T2 acc = mul2(mk2(uw[0]), d0);
+  if (nt > 1) acc = add2(acc, mul2(mk2(uw[1]), d1));
+  if (nt > 2) acc = add2(acc, mul2(mk2(uw[2]), d2));
+  return acc;
+}
+
+// z-level of the pairs in registers (compile-time rows)
+template <typename T, int KIND, int B, typename T2>
+__device__ __forceinline__ void z0_fwd(T2 (&v)[B])
+{
+  constexpr int m = B / 2;
+  if constexpr (KIND == W4 || KIND == W4LI) {
+    T2 d[m];
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+      const W4Row r = w4_row(k, m);
+      const T w[4] = {(T)r.w[0], (T)r.w[1], (T)r.w[2], (T)r.w[3]};
+      d[k] = sub2(v[2 * k + 1], pred4p<T2>(w, v[2 * r.j0], v[2 * r.j0 + 2], v[2 * r.j0 + 4], v[2 * r.j0 + 6]));
+    }
+    if constexpr (KIND == W4LI) {
+      T2 s[m];
+#pragma unroll
+      for (int j = 0; j < m; ++j) {
+        const LiSrc ls = li_src(j, m);
+        const T uw[3] = {li_lookup<T>(m, j, 0), li_lookup<T>(m, j, 1), li_lookup<T>(m, j, 2)};
+        const int k1 = ls.k0 + 1 < m ? ls.k0 + 1 : m - 1, k2 = ls.k0 + 2 < m ? ls.k0 + 2 : m - 1;
+        s[j] = add2(v[2 * j], li_accp<T2>(uw, ls.nt, d[ls.k0], d[k1], d[k2]));
+      }
+#pragma unroll
+      for (int j = 0; j < m; ++j) v[2 * j] = s[j];
+    }
+#pragma unroll
+    for (int k = 0; k < m; ++k) v[2 * k + 1] = d[k];
+  } else {
+    T2 a[m], d[m];
+#pragma unroll
+    for (int k = 0; k < m; ++k) a[k] = mul2(add2(v[2 * k], v[2 * k + 1]), mk2((T)0.5));
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+      const AiRow r = ai_row(k, m);
+      d[k] = sub2(v[2 * k], ai_predp<T2>(a[k], a[r.s1], a[r.s2], (T)r.w0, (T)r.w1, (T)r.w2, r.bnd));
+    }
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+      v[2 * k] = a[k];
+      v[2 * k + 1] = d[k];
+    }
+  }
+}
+
+template <typename T, int KIND, int B, typename T2>
+__device__ __forceinline__ void z0_inv(T2 (&v)[B])
+{
+  constexpr int m = B / 2;
+  if constexpr (KIND == W4 || KIND == W4LI) {
+    if constexpr (KIND == W4LI) {
+      T2 c[m];
+#pragma unroll
+      for (int j = 0; j < m; ++j) {
+        const LiSrc ls = li_src(j, m);
+        const T uw[3] = {li_lookup<T>(m, j, 0), li_lookup<T>(m, j, 1), li_lookup<T>(m, j, 2)};
+        const int k1 = ls.k0 + 1 < m ? ls.k0 + 1 : m - 1, k2 = ls.k0 + 2 < m ? ls.k0 + 2 : m - 1;
+        c[j] = sub2(v[2 * j], li_accp<T2>(uw, ls.nt, v[2 * ls.k0 + 1], v[2 * k1 + 1], v[2 * k2 + 1]));
+      }
+#pragma unroll
+      for (int j = 0; j < m; ++j) v[2 * j] = c[j];
+    }
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+      const W4Row r = w4_row(k, m);
+      const T w[4] = {(T)r.w[0], (T)r.w[1], (T)r.w[2], (T)r.w[3]};
+      v[2 * k + 1] =
+          add2(v[2 * k + 1], pred4p<T2>(w, v[2 * r.j0], v[2 * r.j0 + 2], v[2 * r.j0 + 4], v[2 * r.j0 + 6]));
+    }
+  } else {
+    T2 e[m], o[m];
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+      const AiRow r = ai_row(k, m);
+      e[k] = add2(ai_predp<T2>(v[2 * k], v[2 * r.s1], v[2 * r.s2], (T)r.w0, (T)r.w1, (T)r.w2, r.bnd),
+                  v[2 * k + 1]);
+      o[k] = sub2(mul2(mk2((T)2), v[2 * k]), e[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+      v[2 * k] = e[k];
+      v[2 * k + 1] = o[k];
+    }
+  }
+}
+
+// ============================================================ full transforms
+// Shared planes: X[q][y][x] (all rows) and AD[q][k][x] (one row per pair of
+// rows: W3ai averages / details).  Thread row y, pair a.
+template <typename T, int B, int KIND, typename T2>
+__device__ __forceinline__ void fwd_level0(T2 (&v)[B], T *X, T *AD, int a, int y, int seg)
+{
+  using G = G2<T, B>;
+  constexpr int m = B / 2, ZB = G::ZB;
+  const bool odd = y & 1;
+  // ---- x
+  {
+    const XSt<T> s = make_xst<T, KIND>(a, m, seg);
+#pragma unroll
+    for (int z = 0; z < B; ++z) x0_fwd<T, KIND>(s, v[z]);
+  }
+  // ---- y
+  {
+    const YSt<T> s = make_yst<T, KIND>(y, m);
+    auto row = [&](int q, int yy) -> T2 * { return reinterpret_cast<T2 *>(X + (q * B + yy) * B + 2 * a); };
+    auto arow = [&](int q, int k) -> T2 * { return reinterpret_cast<T2 *>(AD + (q * m + k) * B + 2 * a); };
+#pragma unroll
+    for (int zb = 0; zb < B; zb += ZB) {
+      if constexpr (KIND == W3AI) {
+#pragma unroll
+        for (int q = 0; q < ZB; ++q) *row(q, y) = v[zb + q];
+        __syncthreads();
+        if (!odd) {
+#pragma unroll
+          for (int q = 0; q < ZB; ++q) {
+            const T2 pr = *row(q, y + 1);
+            const T2 av = mul2(add2(v[zb + q], pr), mk2((T)0.5));
+            *arow(q, y >> 1) = av;
+            v[zb + q] = av;
+          }
+        }
+        __syncthreads();
+        if (odd) {
+#pragma unroll
+          for (int q = 0; q < ZB; ++q) {
+            const T2 f2k = *row(q, y - 1);
+            const T2 av = mul2(add2(f2k, v[zb + q]), mk2((T)0.5));
+            const T2 a1 = *arow(q, s.k1), a2 = *arow(q, s.k2);
+            v[zb + q] = sub2(f2k, ai_predp<T2>(av, a1, a2, s.aw[0], s.aw[1], s.aw[2], s.bnd));
+          }
+        }
+      } else {
+        if (!odd) {
+#pragma unroll
+          for (int q = 0; q < ZB; ++q) *row(q, y) = v[zb + q];
+        }
+        __syncthreads();
+        if (odd) {
+#pragma unroll
+          for (int q = 0; q < ZB; ++q) {
+            const T2 p = pred4p<T2>(s.w, *row(q, s.src[0]), *row(q, s.src[1]), *row(q, s.src[2]), *row(q, s.src[3]));
+            v[zb + q] = sub2(v[zb + q], p);
+            if constexpr (KIND == W4LI) *row(q, y) = v[zb + q];
+          }
+        }
+        if constexpr (KIND == W4LI) {
+          __syncthreads();
+          if (!odd) {
+#pragma unroll
+            for (int q = 0; q < ZB; ++q)
+              v[zb + q] = add2(v[zb + q], li_accp<T2>(s.uw, s.nt, *row(q, s.u[0]), *row(q, s.u[1]), *row(q, s.u[2])));
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ---- z
+  z0_fwd<T, KIND, B>(v);
+}
+
+template <typename T, int B, int KIND, typename T2>
+__device__ __forceinline__ void inv_level0(T2 (&v)[B], T *X, T *AD, int a, int y, int seg)
+{
+  using G = G2<T, B>;
+  constexpr int m = B / 2, ZB = G::ZB;
+  const bool odd = y & 1;
+  // ---- z
+  z0_inv<T, KIND, B>(v);
+  // ---- y
+  {
+    const YSt<T> s = make_yst<T, KIND>(y, m);
+    auto row = [&](int q, int yy) -> T2 * { return reinterpret_cast<T2 *>(X + (q * B + yy) * B + 2 * a); };
+    auto arow = [&](int q, int k) -> T2 * { return reinterpret_cast<T2 *>(AD + (q * m + k) * B + 2 * a); };
+#pragma unroll
+    for (int zb = 0; zb < B; zb += ZB) {
+      if constexpr (KIND == W3AI) {
+        // even rows hold averages (to AD), odd rows details (to X at row k)
+#pragma unroll
+        for (int q = 0; q < ZB; ++q) {
+          if (!odd)
+            *arow(q, y >> 1) = v[zb + q];
+          else
+            *row(q, y >> 1) = v[zb + q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < ZB; ++q) {
+          const T2 a1 = *arow(q, s.k1), a2 = *arow(q, s.k2);
+          const T2 av = odd ? *arow(q, y >> 1) : v[zb + q];
+          const T2 dv = odd ? v[zb + q] : *row(q, y >> 1);
+          const T2 f0 = add2(ai_predp<T2>(av, a1, a2, s.aw[0], s.aw[1], s.aw[2], s.bnd), dv);
+          v[zb + q] = odd ? sub2(mul2(mk2((T)2), av), f0) : f0;
+        }
+      } else {
+        if constexpr (KIND == W4LI) {
+          if (odd) {
+#pragma unroll
+            for (int q = 0; q < ZB; ++q) *row(q, y) = v[zb + q];
+          }
+          __syncthreads();
+          if (!odd) {
+#pragma unroll
+            for (int q = 0; q < ZB; ++q) {
+              v[zb + q] = sub2(v[zb + q], li_accp<T2>(s.uw, s.nt, *row(q, s.u[0]), *row(q, s.u[1]), *row(q, s.u[2])));
+              *row(q, y) = v[zb + q];
+            }
+          }
+        } else {
+          if (!odd) {
+#pragma unroll
+            for (int q = 0; q < ZB; ++q) *row(q, y) = v[zb + q];
+          }
+        }
+        __syncthreads();
+        if (odd) {
+#pragma unroll
+          for (int q = 0; q < ZB; ++q)
+            v[zb + q] = add2(v[zb + q],
+                             pred4p<T2>(s.w, *row(q, s.src[0]), *row(q, s.src[1]), *row(q, s.src[2]), *row(q, s.src[3])));
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ---- x
+  {
+    const XSt<T> s = make_xst<T, KIND>(a, m, seg);
+#pragma unroll
+    for (int z = 0; z < B; ++z) x0_inv<T, KIND>(s, v[z]);
+  }
+}
+
+// coarser levels: E column, positions multiple of S = 2^LEV (LEV >= 1)
+template <typename T, int B, int KIND, int LEV, typename T2>
+__device__ __forceinline__ void fwd_levelE(T2 (&v)[B], T *X, int a, int y, int seg)
+{
+  using G = G2<T, B>;
+  constexpr int S = 1 << LEV, n = B >> LEV, m = n / 2, ZB = G::ZB, NZ = B / S;
+  constexpr int LS = S / 2;  // lane stride of active pairs
+  const bool xact = (a & (LS - 1)) == 0, yact = (y & (S - 1)) == 0;
+  // x: lanes a = i * LS
+  {
+    const Stencil<T> st = make_stencil<T, KIND>(a / LS, m);
+#pragma unroll
+    for (int z = 0; z < B; z += S) {
+      const T f = v[z].x;
+      auto g = [&](int idx) { return shfl(f, seg + idx * LS); };
+      T r;
+      if constexpr (KIND == W4) {
+        r = fwd_predict(st, f, g);
+      } else if constexpr (KIND == W4LI) {
+        const T f1 = fwd_predict(st, f, g);
+        r = fwd_update(st, f1, [&](int idx) { return shfl(f1, seg + idx * LS); });
+      } else {
+        r = fwd_ai(st, f, g, [&](int idx, T av) { return shfl(av, seg + idx * LS); });
+      }
+      if (xact && yact) v[z].x = r;
+    }
+  }
+  // y: shared planes of E values
+  {
+    const Stencil<T> st = make_stencil<T, KIND>(y / S, m);
+    const bool act = xact && yact;
+#pragma unroll
+    for (int zb = 0; zb < NZ; zb += ZB) {
+#pragma unroll
+      for (int q = 0; q < ZB; ++q)
+        if (zb + q < NZ && act) X[(q * B + y) * B + 2 * a] = v[(zb + q) * S].x;
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < ZB; ++q) {
+        if (zb + q < NZ && act) {
+          T *Xq = X + q * B * B + 2 * a;
+          auto g = [&](int idx) { return Xq[idx * S * B]; };
+          const T f = v[(zb + q) * S].x;
+          T r;
+          if constexpr (KIND == W4) {
+            r = fwd_predict(st, f, g);
+          } else if constexpr (KIND == W4LI) {
+            r = fwd_predict(st, f, g);
+            if (st.i & 1) Xq[y * B] = r;
+          } else {
+            r = fwd_ai(st, f, g, [&](int idx, T) { return mulx(addx(g(idx), g(idx + 1)), (T)0.5); });
+          }
+          v[(zb + q) * S].x = r;
+        }
+      }
+      if constexpr (KIND == W4LI) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < ZB; ++q) {
+          if (zb + q < NZ && act) {
+            T *Xq = X + q * B * B + 2 * a;
+            v[(zb + q) * S].x = fwd_update(st, v[(zb + q) * S].x, [&](int idx) { return Xq[idx * S * B]; });
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // z: registers
+  if (xact && yact) {
+    T e[B];
+#pragma unroll
+    for (int z = 0; z < B; ++z) e[z] = v[z].x;
+    fwd_reg<T, KIND, B, S>(e);
+#pragma unroll
+    for (int z = 0; z < B; z += S) v[z].x = e[z];
+  }
+}
+
+template <typename T, int B, int KIND, int LEV, typename T2>
+__device__ __forceinline__ void inv_levelE(T2 (&v)[B], T *X, int a, int y, int seg)
+{
+  using G = G2<T, B>;
+  constexpr int S = 1 << LEV, n = B >> LEV, m = n / 2, ZB = G::ZB, NZ = B / S;
+  constexpr int LS = S / 2;
+  const bool xact = (a & (LS - 1)) == 0, yact = (y & (S - 1)) == 0;
+  if (xact && yact) {
+    T e[B];
+#pragma unroll
+    for (int z = 0; z < B; ++z) e[z] = v[z].x;
+    inv_reg<T, KIND, B, S>(e);
+#pragma unroll
+    for (int z = 0; z < B; z += S) v[z].x = e[z];
+  }
+  {
+    const Stencil<T> st = make_stencil<T, KIND>(y / S, m);
+    const bool act = xact && yact;
+#pragma unroll
+    for (int zb = 0; zb < NZ; zb += ZB) {
+#pragma unroll
+      for (int q = 0; q < ZB; ++q)
+        if (zb + q < NZ && act) X[(q * B + y) * B + 2 * a] = v[(zb + q) * S].x;
+      __syncthreads();
+      if constexpr (KIND == W4LI) {
+#pragma unroll
+        for (int q = 0; q < ZB; ++q) {
+          if (zb + q < NZ && act) {
+            T *Xq = X + q * B * B + 2 * a;
+            const T c = inv_update(st, v[(zb + q) * S].x, [&](int idx) { return Xq[idx * S * B]; });
+            if (!(st.i & 1)) Xq[y * B] = c;
+            v[(zb + q) * S].x = c;
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < ZB; ++q) {
+        if (zb + q < NZ && act) {
+          T *Xq = X + q * B * B + 2 * a;
+          auto g = [&](int idx) { return Xq[idx * S * B]; };
+          const T f = v[(zb + q) * S].x;
+          if constexpr (KIND == W3AI)
+            v[(zb + q) * S].x = inv_ai(st, f, g);
+          else
+            v[(zb + q) * S].x = inv_predict(st, f, g);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  {
+    const Stencil<T> st = make_stencil<T, KIND>(a / LS, m);
+#pragma unroll
+    for (int z = 0; z < B; z += S) {
+      const T f = v[z].x;
+      auto g = [&](int idx) { return shfl(f, seg + idx * LS); };
+      T r;
+      if constexpr (KIND == W4) {
+        r = inv_predict(st, f, g);
+      } else if constexpr (KIND == W4LI) {
+        const T f1 = inv_update(st, f, g);
+        r = inv_predict(st, f1, [&](int idx) { return shfl(f1, seg + idx * LS); });
+      } else {
+        r = inv_ai(st, f, g);
+      }
+      if (xact && yact) v[z].x = r;
+    }
+  }
+}
+
+template <typename T, int B, int KIND, typename T2>
+__device__ __forceinline__ void fwd_all(T2 (&v)[B], T *X, T *AD, int a, int y, int seg)
+{
+  fwd_level0<T, B, KIND>(v, X, AD, a, y, seg);
+  if constexpr (G2<T, B>::L > 1) fwd_levelE<T, B, KIND, 1>(v, X, a, y, seg);
+  if constexpr (G2<T, B>::L > 2) fwd_levelE<T, B, KIND, 2>(v, X, a, y, seg);
+}
+
+template <typename T, int B, int KIND, typename T2>
+__device__ __forceinline__ void inv_all(T2 (&v)[B], T *X, T *AD, int a, int y, int seg)
+{
+  if constexpr (G2<T, B>::L > 2) inv_levelE<T, B, KIND, 2>(v, X, a, y, seg);
+  if constexpr (G2<T, B>::L > 1) inv_levelE<T, B, KIND, 1>(v, X, a, y, seg);
+  inv_level0<T, B, KIND>(v, X, AD, a, y, seg);
+}
+
+// ============================================================ stage-2 helpers
+__device__ __forceinline__ unsigned shuffled_word(const unsigned char *P, int w, int E, int es)
+{
+  const int j = 4 * w;
+  int b = j / E;
+  int e = j - b * E;
+  unsigned r = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (e == E) {
+      e = 0;
+      ++b;
+    }
+    r |= (unsigned)P[e * es + b] << (8 * q);
+    ++e;
+  }
+  return r;
+}
+
+__device__ __forceinline__ void unshuffle_word(unsigned char *P, int w, unsigned val, int E, int es)
+{
+  const int j = 4 * w;
+  int b = j / E;
+  int e = j - b * E;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (e == E) {
+      e = 0;
+      ++b;
+    }
+    P[e * es + b] = (unsigned char)(val >> (8 * q));
+    ++e;
+  }
+}
+
+__device__ __forceinline__ unsigned tokcount(unsigned lit, unsigned zr)
+{
+  return 1u + (lit > 65535u ? (lit - 1u) / 65535u : 0u) + (zr > 65535u ? (zr - 1u) / 65535u : 0u);
+}
+
+__device__ __forceinline__ unsigned emit_tokens(unsigned *tok, unsigned idx, unsigned lit, unsigned zr)
+{
+  while (lit > 65535u) {
+    tok[idx++] = 65535u;
+    lit -= 65535u;
+  }
+  while (zr > 65535u) {
+    tok[idx++] = lit | (65535u << 16);
+    lit = 0;
+    zr -= 65535u;
+  }
+  tok[idx++] = lit | (zr << 16);
+  return idx;
+}
+
+template <typename U>
+__device__ __forceinline__ void st_le(unsigned char *p, U v)
+{
+#pragma unroll
+  for (int q = 0; q < (int)sizeof(U); ++q) p[q] = (unsigned char)((unsigned long long)v >> (8 * q));
+}
+__device__ __forceinline__ void st_le_f64(unsigned char *p, double v)
+{
+  st_le<unsigned long long>(p, (unsigned long long)__double_as_longlong(v));
+}
+
+// store a B-bit row word at bit offset (z*B + y)*B of the mask
+template <int B>
+__device__ __forceinline__ void put_row(unsigned char *mask, int z, int y, unsigned w)
+{
+  const int bit = (z * B + y) * B;
+  if constexpr (B == 32)
+    *reinterpret_cast<unsigned *>(mask + bit / 8) = w;
+  else if constexpr (B == 16)
+    *reinterpret_cast<unsigned short *>(mask + bit / 8) = (unsigned short)w;
+  else
+    mask[bit / 8] = (unsigned char)w;
+}
+
+template <int B>
+__device__ __forceinline__ unsigned get_row(const unsigned char *mask, int z, int y)
+{
+  const int bit = (z * B + y) * B;
+  if constexpr (B == 32)
+    return *reinterpret_cast<const unsigned *>(mask + bit / 8);
+  else if constexpr (B == 16)
+    return *reinterpret_cast<const unsigned short *>(mask + bit / 8);
+  else
+    return mask[bit / 8];
+}
+
+template <typename T>
+__device__ __forceinline__ void threshold_of(const FwdArgs &a, const WsHdr *ws, double &mn, double &mx,
+                                             double &range, T &t)
+{
+  if (a.range >= 0) {
+    range = a.range;
+    mn = mx = __longlong_as_double(0x7FF8000000000000LL);
+  } else {
+    const unsigned long long kmin = *(volatile const unsigned long long *)&ws->minkey;
+    const unsigned long long kmax = *(volatile const unsigned long long *)&ws->maxkey;
+    mn = key_value(kmin, T(0));
+    mx = key_value(kmax, T(0));
+    mn = (double)(T)((T)mn + (T)0);  // -0 reported as +0
+    mx = (double)(T)((T)mx + (T)0);
+    range = (mn <= mx) ? mx - mn : 0.0;
+  }
+  const double td = a.eps_mode == 1 ? a.eps : a.eps * range;
+  t = (T)td;
+}
+
+// ============================================================ compress
+template <typename T, int B, int KIND>
+__global__ void __launch_bounds__(B * B / 2, 1)
+    k_compress2(const __grid_constant__ CUtensorMap tmap, const FwdArgs a)
+{
+  using G = G2<T, B>;
+  using T2 = typename V2T<T>::type;
+  constexpr int NT = G::NT, ES = G::ES, NMW = G::NMW, Q = G::Q;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char *PF = smem;
+  unsigned char *R2 = smem + G::TILE;
+  unsigned char *PS = R2 + G::R2C;
+  T *X = reinterpret_cast<T *>(R2);
+  T *AD = reinterpret_cast<T *>(R2 + G::XB);
+  unsigned *ROWOFF = reinterpret_cast<unsigned *>(R2);
+  __shared__ __align__(8) unsigned long long s_bar;
+  __shared__ unsigned s_u[40];
+  __shared__ int s_i[40];
+  __shared__ int s_cur, s_next;
+  __shared__ unsigned long long s_excl;
+
+  WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
+  unsigned long long *lbst = reinterpret_cast<unsigned long long *>((char *)a.ws + WS_HDR);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ap = tid % G::HP, r = tid / G::HP;
+  const int y = r < B / 2 ? 2 * r : 2 * (r - B / 2) + 1;
+  const int seg = lane - ap;
+  const int x0 = 2 * ap;
+
+  double mn, mx, range;
+  T t;
+  threshold_of<T>(a, ws, mn, mx, range, t);
+  const unsigned long long tb = thr_bits(t);
+  // coarse positions (x, y, z all multiples of B/4) never enter the mask
+  const bool cE = (x0 % Q == 0) && (y % Q == 0);
+  unsigned cmask = 0;
+#pragma unroll
+  for (int z = 0; z < B; z += Q) cmask |= 1u << z;
+
+  auto coords = [&](int bid, int &bx, int &by, int &bz) {
+    bx = bid % a.nbx;
+    by = (bid / a.nbx) % a.nby;
+    bz = bid / (a.nbx * a.nby);
+  };
+
+  if (tid == 0) {
+    mbar_init(&s_bar);
+    s_cur = (int)atomicAdd(&ws->ticket, 1u);
+    if (s_cur < a.nblocks) {
+      int bx, by, bz;
+      coords(s_cur, bx, by, bz);
+      tma_load_tile(&tmap, PF, &s_bar, bx * B, by * B, bz * B, G::TILE);
+    }
+  }
+  __syncthreads();
+  unsigned phase = 0;
+
+  for (;;) {
+    const int bid = s_cur;
+    if (bid >= a.nblocks) break;
+    if (!mbar_wait(&s_bar, phase)) {
+      // the copy never completed: record, wait once more for it, stop
+      if (tid == 0) atomicCAS(&ws->status, 0u, ST_TIMEOUT);
+      mbar_wait(&s_bar, phase);
+      break;
+    }
+    phase ^= 1u;
+
+    // ---- a1: tile -> registers
+    T2 v[B];
+#pragma unroll
+    for (int z = 0; z < B; ++z) v[z] = *reinterpret_cast<const T2 *>(PF + ((z * B + y) * B + x0) * ES);
+    __syncthreads();
+    if (tid == 0) {
+      s_next = (int)atomicAdd(&ws->ticket, 1u);
+      if (s_next < a.nblocks) {
+        int bx, by, bz;
+        coords(s_next, bx, by, bz);
+        tma_load_tile(&tmap, PF, &s_bar, bx * B, by * B, bz * B, G::TILE);
+      }
+    }
+
+    // ---- a2: forward transform
+    fwd_all<T, B, KIND>(v, X, AD, ap, y, seg);
+
+    // ---- a3: significance bits over z, row words by bit transpose
+    unsigned me = 0, mo = 0;
+#pragma unroll
+    for (int z = 0; z < B; ++z) {
+      me |= (unsigned)(magbits(v[z].x) >= tb) << z;
+      mo |= (unsigned)(magbits(v[z].y) >= tb) << z;
+    }
+    if (cE) me &= ~cmask;
+    unsigned w0 = me, w1 = mo;
+    bit_transpose<B>(w0, w1, ap);  // words of rows (z = 2ap, y) and (z = 2ap + 1, y)
+    __syncthreads();               // planes X / AD free: row offsets go there
+    ROWOFF[(2 * ap) * B + y] = __popc(w0);
+    ROWOFF[(2 * ap + 1) * B + y] = __popc(w1);
+    __syncthreads();
+    unsigned nnz;
+    {
+      constexpr int IPT = (B * B + NT - 1) / NT;
+      unsigned loc[IPT], sum = 0;
+#pragma unroll
+      for (int q = 0; q < IPT; ++q) {
+        loc[q] = ROWOFF[tid * IPT + q];
+        sum += loc[q];
+      }
+      unsigned ex = block_exsum<NT>(sum, s_u, nnz);
+#pragma unroll
+      for (int q = 0; q < IPT; ++q) {
+        ROWOFF[tid * IPT + q] = ex;
+        ex += loc[q];
+      }
+    }
+    __syncthreads();
+
+    // ---- a4: payload [coarse | mask | values] in shared memory, or in
+    // this CTA's global scratch when it does not fit
+    const int pbytes = 64 * ES + G::MASKB + (int)nnz * ES;
+    const bool in_smem = pbytes <= G::PCAP;
+    unsigned char *P = in_smem ? PS : a.scratch + (size_t)blockIdx.x * a.scratch_per_cta;
+    unsigned *S2 = in_smem ? reinterpret_cast<unsigned *>(R2 + G::ROWB)
+                           : reinterpret_cast<unsigned *>(P + ((G::PMAX + 15) / 16 * 16));
+    const int nbw_cap = in_smem ? G::NBWC : G::NBWMAX;
+    unsigned *ZBM = S2, *CMk = S2 + nbw_cap, *BDM = CMk + nbw_cap, *LP = BDM + nbw_cap;
+    unsigned char *MASK = P + 64 * ES;
+    T *VALS = reinterpret_cast<T *>(MASK + G::MASKB);
+    put_row<B>(MASK, 2 * ap, y, w0);
+    put_row<B>(MASK, 2 * ap + 1, y, w1);
+    if (cE) {
+#pragma unroll
+      for (int z = 0; z < B; z += Q) reinterpret_cast<T *>(P)[((z / Q) * 4 + y / Q) * 4 + x0 / Q] = v[z].x;
+    }
+    __syncthreads();
+    {
+      const unsigned any_bits = me | mo;
+      const unsigned lowE = (1u << x0) - 1u, lowO = (2u << x0) - 1u;
+#pragma unroll
+      for (int z = 0; z < B; ++z) {
+        const bool have = (any_bits >> z) & 1u;
+        if (__any_sync(FULL, have)) {
+          if (have) {
+            const unsigned wd = get_row<B>(MASK, z, y);
+            const unsigned base = ROWOFF[z * B + y];
+            if ((me >> z) & 1u) VALS[base + __popc(wd & lowE)] = v[z].x;
+            if ((mo >> z) & 1u) VALS[base + __popc(wd & lowO)] = v[z].y;
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- a6: stage 2 sizes (byte shuffle + zero-word RLE)
+    const int W = pbytes / 4, E = pbytes / ES, NB = (W + 31) / 32;
+    const int KB = (NB + NT - 1) / NT;
+    unsigned ntok = 0, nlit = 0, tokbase = 0;
+    int prev_before = -1, next_after = W;
+    if (a.stage2) {
+      for (int wb = tid >> 5; wb < NB; wb += G::NW) {
+        const int w = wb * 32 + lane;
+        const bool zr = (w < W) && (shuffled_word(P, w, E, ES) == 0u);
+        const unsigned bal = __ballot_sync(FULL, zr);
+        if (lane == 0) ZBM[wb] = bal;
+      }
+      __syncthreads();
+      int first_bd = W, last_bd = -1;
+      unsigned my_lit = 0;
+      for (int q = 0; q < KB; ++q) {
+        const int i = tid * KB + q;
+        if (i < NB) {
+          const unsigned Z = ZBM[i];
+          const unsigned pw = i > 0 ? ZBM[i - 1] : 0u;
+          const unsigned nw = (i + 1 < NB) ? ZBM[i + 1] : 0u;
+          unsigned C = Z & ((Z << 1) | (pw >> 31) | (Z >> 1) | ((nw & 1u) << 31));
+          const unsigned cp = i > 0 ? ((pw >> 31) & (((pw >> 30) & 1u) | (Z & 1u))) : 0u;
+          unsigned Bd = C ^ ((C << 1) | cp);
+          if (i == 0) Bd |= 1u;
+          const unsigned valid = (i == NB - 1 && (W & 31)) ? ((1u << (W & 31)) - 1u) : FULL;
+          C &= valid;
+          Bd &= valid;
+          CMk[i] = C;
+          BDM[i] = Bd;
+          my_lit += __popc(~C & valid);
+          if (Bd) {
+            if (first_bd == W) first_bd = i * 32 + __ffs(Bd) - 1;
+            last_bd = i * 32 + 31 - __clz(Bd);
+          }
+        }
+      }
+      const unsigned litbase = block_exsum<NT>(my_lit, s_u, nlit);
+      prev_before = block_exmax<NT>(last_bd, -1, s_i);
+      next_after = block_rexmin<NT>(first_bd, W, s_i);
+      {
+        unsigned run = litbase;
+        for (int q = 0; q < KB; ++q) {
+          const int i = tid * KB + q;
+          if (i < NB) {
+            const unsigned valid = (i == NB - 1 && (W & 31)) ? ((1u << (W & 31)) - 1u) : FULL;
+            LP[i] = run;
+            run += __popc(~CMk[i] & valid);
+          }
+        }
+      }
+      unsigned my_tok = 0;
+      {
+        int prev = prev_before, cur = -1;
+        auto handle = [&](int p, int pv, int nb) {
+          if ((CMk[p >> 5] >> (p & 31)) & 1u)
+            my_tok += tokcount(p == 0 ? 0u : (unsigned)(p - pv), (unsigned)(nb - p));
+          else if (nb == W)
+            my_tok += tokcount((unsigned)(W - p), 0u);
+        };
+        for (int q = 0; q < KB; ++q) {
+          const int i = tid * KB + q;
+          if (i < NB) {
+            unsigned bd = BDM[i];
+            while (bd) {
+              const int p = i * 32 + __ffs(bd) - 1;
+              bd &= bd - 1u;
+              if (cur >= 0) {
+                handle(cur, prev, p);
+                prev = cur;
+              }
+              cur = p;
+            }
+          }
+        }
+        if (cur >= 0) handle(cur, prev, next_after);
+      }
+      tokbase = block_exsum<NT>(my_tok, s_u, ntok);
+    }
+    const unsigned long long size =
+        a.stage2 ? 8ull + 4ull * ntok + 4ull * nlit : 8ull + (unsigned long long)pbytes;
+
+    // ---- a5: chunk offset by decoupled look-back
+    if (tid < 32) {
+      const unsigned long long ex = lookback(lbst, bid, size, &ws->status, (int)ST_TIMEOUT);
+      if (lane == 0) s_excl = ex;
+    }
+    __syncthreads();
+    const unsigned long long excl = s_excl;
+    const bool fits = a.data0 + excl + size <= a.out_cap;
+    if (tid == 0) {
+      st_le<unsigned long long>(a.out + HEADER_BYTES + 8ull * bid, excl);
+      if (!fits) atomicCAS(&ws->status, 0u, ST_CAPACITY);
+      if (bid == a.nblocks - 1) {
+        const unsigned long long data_bytes = excl + size, total = a.data0 + data_bytes;
+        unsigned char *h = a.out;
+        st_le<unsigned long long>(h + HEADER_BYTES + 8ull * a.nblocks, data_bytes);
+        for (unsigned long long q = HEADER_BYTES + 8ull * (a.nblocks + 1); q < a.data0; ++q) h[q] = 0;
+        for (int q = 0; q < HEADER_BYTES; ++q) h[q] = 0;
+        st_le<unsigned>(h + 0, MAGIC);
+        st_le<unsigned short>(h + 4, 1);
+        st_le<unsigned short>(h + 6, HEADER_BYTES);
+        st_le<int>(h + 8, a.nx);
+        st_le<int>(h + 12, a.ny);
+        st_le<int>(h + 16, a.nz);
+        h[20] = (unsigned char)B;
+        h[21] = (unsigned char)a.dtype;
+        h[22] = (unsigned char)a.kind;
+        h[23] = (unsigned char)a.stage2;
+        h[24] = (unsigned char)a.eps_mode;
+        h[25] = (unsigned char)G::L;
+        st_le<unsigned>(h + 28, (unsigned)a.nblocks);
+        st_le_f64(h + 32, a.eps);
+        st_le_f64(h + 40, (double)t);
+        st_le_f64(h + 48, mn);
+        st_le_f64(h + 56, mx);
+        st_le_f64(h + 64, range);
+        st_le<unsigned long long>(h + 72, data_bytes);
+        st_le<unsigned long long>(h + 80, total);
+        ws->out_bytes = total;
+        if (a.out_bytes) *a.out_bytes = total;
+      }
+    }
+    if (fits) {
+      unsigned *ch32 = reinterpret_cast<unsigned *>(a.out + a.data0 + excl);
+      if (tid == 0) {
+        ch32[0] = nnz;
+        ch32[1] = a.stage2 ? ntok : 0u;
+      }
+      if (a.stage2) {
+        unsigned *tok = ch32 + 2;
+        {
+          unsigned idx = tokbase;
+          int prev = prev_before, cur = -1;
+          auto handle = [&](int p, int pv, int nb) {
+            if ((CMk[p >> 5] >> (p & 31)) & 1u)
+              idx = emit_tokens(tok, idx, p == 0 ? 0u : (unsigned)(p - pv), (unsigned)(nb - p));
+            else if (nb == W)
+              idx = emit_tokens(tok, idx, (unsigned)(W - p), 0u);
+          };
+          for (int q = 0; q < KB; ++q) {
+            const int i = tid * KB + q;
+            if (i < NB) {
+              unsigned bd = BDM[i];
+              while (bd) {
+                const int p = i * 32 + __ffs(bd) - 1;
+                bd &= bd - 1u;
+                if (cur >= 0) {
+                  handle(cur, prev, p);
+                  prev = cur;
+                }
+                cur = p;
+              }
+            }
+          }
+          if (cur >= 0) handle(cur, prev, next_after);
+        }
+        unsigned *lit = tok + ntok;
+        for (int w = tid; w < W; w += NT) {
+          const unsigned C = CMk[w >> 5];
+          const int b = w & 31;
+          if (!((C >> b) & 1u)) lit[LP[w >> 5] + __popc(~C & ((1u << b) - 1u))] = shuffled_word(P, w, E, ES);
+        }
+      } else {
+        const unsigned *P32 = reinterpret_cast<const unsigned *>(P);
+        for (int w = tid; w < pbytes / 4; w += NT) ch32[2 + w] = P32[w];
+      }
+    }
+    __syncthreads();
+    if (tid == 0) s_cur = s_next;
+    __syncthreads();
+  }
+  (void)NMW;
+}
+
+// ============================================================ decompress
+template <typename T, int B, int KIND>
+__global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
+{
+  using G = G2<T, B>;
+  using T2 = typename V2T<T>::type;
+  constexpr int NT = G::NT, ES = G::ES, Q = G::Q;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char *R2 = smem;
+  unsigned char *P = smem + G::R2D;
+  T *X = reinterpret_cast<T *>(R2);
+  T *AD = reinterpret_cast<T *>(R2 + G::XB);
+  unsigned *ROWOFF = reinterpret_cast<unsigned *>(R2);
+  unsigned *TL = ROWOFF + B * B;
+  unsigned *TO = TL + NT;
+  __shared__ unsigned s_u[40];
+  __shared__ unsigned s_nnz, s_ntok, s_bad;
+  __shared__ unsigned long long s_off, s_len;
+
+  WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ap = tid % G::HP, r = tid / G::HP;
+  const int y = r < B / 2 ? 2 * r : 2 * (r - B / 2) + 1;
+  const int seg = lane - ap;
+  const int x0 = 2 * ap;
+  const bool cE = (x0 % Q == 0) && (y % Q == 0);
+
+  for (int bid = blockIdx.x; bid < a.nblocks; bid += gridDim.x) {
+    const int bx = bid % a.nbx, by = (bid / a.nbx) % a.nby, bz = bid / (a.nbx * a.nby);
+    if (tid == 0) {
+      unsigned bad = 0;
+      const unsigned long long *tab = reinterpret_cast<const unsigned long long *>(a.in + HEADER_BYTES);
+      const unsigned long long o0 = tab[bid], o1 = tab[bid + 1];
+      const unsigned long long avail = a.in_bytes - a.data0;
+      unsigned nnz = 0, ntok = 0;
+      if (o0 > o1 || o1 > avail || o1 - o0 < 8 || (o0 & 3) || ((o1 - o0) & 3)) {
+        bad = 1;
+      } else {
+        const unsigned *c32 = reinterpret_cast<const unsigned *>(a.in + a.data0 + o0);
+        nnz = c32[0];
+        ntok = c32[1];
+        const unsigned long long len = o1 - o0;
+        if (nnz > (unsigned)(G::NVOX - 64)) bad = 1;
+        const unsigned long long pb = 64ull * ES + G::MASKB + (unsigned long long)nnz * ES;
+        if (!bad && !a.stage2 && (ntok != 0 || 8 + pb > len)) bad = 1;
+        if (!bad && a.stage2 && (unsigned long long)ntok > (len - 8) / 4) bad = 1;
+      }
+      s_bad = bad;
+      s_nnz = bad ? 0u : nnz;
+      s_ntok = ntok;
+      s_off = o0;
+      s_len = o1 - o0;
+    }
+    __syncthreads();
+    const unsigned nnz = s_nnz;
+    const int pbytes = 64 * ES + G::MASKB + (int)nnz * ES;
+    const unsigned *c32 = reinterpret_cast<const unsigned *>(a.in + a.data0 + s_off);
+
+    if (!s_bad) {
+      if (a.stage2) {
+        const int W = pbytes / 4, E = pbytes / ES;
+        const unsigned ntok = s_ntok;
+        const unsigned long long nlit_avail = (s_len - 8 - 4ull * ntok) / 4;
+        const unsigned *tok = c32 + 2;
+        const unsigned *lit = tok + ntok;
+        unsigned *P32 = reinterpret_cast<unsigned *>(P);
+        for (int w = tid; w < W; w += NT) P32[w] = 0u;
+        __syncthreads();
+        unsigned lit_carry = 0, out_carry = 0;
+        bool bad = false;
+        for (unsigned r0 = 0; r0 < ntok; r0 += NT) {
+          const unsigned k = r0 + tid;
+          const unsigned tk = k < ntok ? __ldg(tok + k) : 0u;
+          const unsigned nl = tk & 0xFFFFu, run = nl + (tk >> 16);
+          unsigned tl, to_;
+          const unsigned lp = block_exsum<NT>(nl, s_u, tl);
+          const unsigned op = block_exsum<NT>(run, s_u, to_);
+          TL[tid] = lit_carry + lp;
+          TO[tid] = out_carry + op;
+          __syncthreads();
+          const unsigned cnt = (ntok - r0) < (unsigned)NT ? (ntok - r0) : (unsigned)NT;
+          for (unsigned l = lit_carry + tid; l < lit_carry + tl; l += NT) {
+            unsigned lo = 0, hi = cnt - 1;
+            while (lo < hi) {
+              const unsigned mid = (lo + hi + 1) >> 1;
+              if (TL[mid] <= l) lo = mid; else hi = mid - 1;
+            }
+            const unsigned ow = TO[lo] + (l - TL[lo]);
+            if (l < nlit_avail && ow < (unsigned)W) unshuffle_word(P, (int)ow, __ldg(lit + l), E, ES);
+            else bad = true;
+          }
+          lit_carry += tl;
+          out_carry += to_;
+          __syncthreads();
+        }
+        if (bad || out_carry != (unsigned)W || (unsigned long long)lit_carry > nlit_avail) atomicOr(&s_bad, 1u);
+      } else {
+        unsigned *P32 = reinterpret_cast<unsigned *>(P);
+        for (int w = tid; w < pbytes / 4; w += NT) P32[w] = __ldg(c32 + 2 + w);
+      }
+    }
+    __syncthreads();
+
+    const unsigned char *MASK = P + 64 * ES;
+    if (!s_bad) {
+      // row populations -> row offsets; coarse positions carry no mask bit
+      const unsigned w0 = get_row<B>(MASK, 2 * ap, y), w1 = get_row<B>(MASK, 2 * ap + 1, y);
+      ROWOFF[(2 * ap) * B + y] = __popc(w0);
+      ROWOFF[(2 * ap + 1) * B + y] = __popc(w1);
+      if ((y % Q) == 0) {
+        unsigned cm = 0;
+#pragma unroll
+        for (int x = 0; x < B; x += Q) cm |= 1u << x;
+        if (((2 * ap) % Q == 0 && (w0 & cm)) || ((2 * ap + 1) % Q == 0 && (w1 & cm))) atomicOr(&s_bad, 1u);
+      }
+      __syncthreads();
+      constexpr int IPT = (B * B + NT - 1) / NT;
+      unsigned loc[IPT], sum = 0;
+#pragma unroll
+      for (int q = 0; q < IPT; ++q) {
+        loc[q] = ROWOFF[tid * IPT + q];
+        sum += loc[q];
+      }
+      unsigned tot;
+      unsigned ex = block_exsum<NT>(sum, s_u, tot);
+#pragma unroll
+      for (int q = 0; q < IPT; ++q) {
+        ROWOFF[tid * IPT + q] = ex;
+        ex += loc[q];
+      }
+      if (tid == 0 && tot != nnz) atomicOr(&s_bad, 1u);
+    }
+    __syncthreads();
+    const bool bad = s_bad != 0;
+    if (bad && tid == 0) atomicCAS(&ws->status, 0u, ST_CORRUPT);
+
+    T2 v[B];
+    {
+      const T *COARSE = reinterpret_cast<const T *>(P);
+      const T *VALS = reinterpret_cast<const T *>(MASK + G::MASKB);
+      const unsigned lowE = (1u << x0) - 1u, lowO = (2u << x0) - 1u;
+#pragma unroll
+      for (int z = 0; z < B; ++z) {
+        T2 rv;
+        rv.x = T(0);
+        rv.y = T(0);
+        if (!bad) {
+          const unsigned wd = get_row<B>(MASK, z, y);
+          if (__any_sync(FULL, wd != 0u)) {
+            const unsigned base = ROWOFF[z * B + y];
+            if ((wd >> x0) & 1u) rv.x = VALS[base + __popc(wd & lowE)];
+            if ((wd >> (x0 + 1)) & 1u) rv.y = VALS[base + __popc(wd & lowO)];
+          }
+          if (cE && (z % Q) == 0) rv.x = COARSE[((z / Q) * 4 + y / Q) * 4 + x0 / Q];
+        }
+        v[z] = rv;
+      }
+    }
+    __syncthreads();
+    if (!bad) inv_all<T, B, KIND>(v, X, AD, ap, y, seg);
+    {
+      const size_t zs = (size_t)a.ny * a.nx;
+      T *dst = reinterpret_cast<T *>(a.field) + (size_t)(bz * B) * zs + (size_t)(by * B + y) * a.nx +
+               (size_t)(bx * B + x0);
+#pragma unroll
+      for (int z = 0; z < B; ++z) __stcs(reinterpret_cast<T2 *>(dst + z * zs), v[z]);
+    }
+    __syncthreads();
+  }
+}
+
+// ============================================================ dense transforms
+template <typename T, int B, int KIND, bool FWD>
+__global__ void __launch_bounds__(B * B / 2) k_dense2(const DenseArgs a)
+{
+  using G = G2<T, B>;
+  using T2 = typename V2T<T>::type;
+  extern __shared__ __align__(128) unsigned char smem[];
+  T *X = reinterpret_cast<T *>(smem);
+  T *AD = reinterpret_cast<T *>(smem + G::XB);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ap = tid % G::HP, r = tid / G::HP;
+  const int y = r < B / 2 ? 2 * r : 2 * (r - B / 2) + 1;
+  const int seg = lane - ap;
+  const int bid = blockIdx.x;
+  const int bx = bid % a.nbx, by = (bid / a.nbx) % a.nby, bz = bid / (a.nbx * a.nby);
+  const size_t zs = (size_t)a.ny * a.nx;
+  const size_t off = (size_t)(bz * B) * zs + (size_t)(by * B + y) * a.nx + (size_t)(bx * B + 2 * ap);
+  const T2 *src = reinterpret_cast<const T2 *>(reinterpret_cast<const T *>(a.src) + off);
+  T2 *dst = reinterpret_cast<T2 *>(reinterpret_cast<T *>(a.dst) + off);
+  T2 v[B];
+#pragma unroll
+  for (int z = 0; z < B; ++z) v[z] = src[z * zs / 2];
+  if constexpr (FWD)
+    fwd_all<T, B, KIND>(v, X, AD, ap, y, seg);
+  else
+    inv_all<T, B, KIND>(v, X, AD, ap, y, seg);
+#pragma unroll
+  for (int z = 0; z < B; ++z) dst[z * zs / 2] = v[z];
+}
+
+// ============================================================ a0: min / max
+template <typename T>
+__global__ void __launch_bounds__(512) k_minmax(const T *__restrict__ xs, size_t n, WsHdr *ws)
+{
+  T lo = (T)INFINITY, hi = (T)-INFINITY;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (sizeof(T) == 4) {
+    const float4 *v4 = reinterpret_cast<const float4 *>(xs);
+    const size_t n4 = n / 4;
+    for (size_t k = i; k < n4; k += stride) {
+      const float4 q = __ldcs(v4 + k);
+      lo = q.x < lo ? q.x : lo; hi = q.x > hi ? q.x : hi;
+      lo = q.y < lo ? q.y : lo; hi = q.y > hi ? q.y : hi;
+      lo = q.z < lo ? q.z : lo; hi = q.z > hi ? q.z : hi;
+      lo = q.w < lo ? q.w : lo; hi = q.w > hi ? q.w : hi;
+    }
+    for (size_t k = n4 * 4 + i; k < n; k += stride) {
+      const T q = xs[k];
+      lo = q < lo ? q : lo;
+      hi = q > hi ? q : hi;
+    }
+  } else {
+    const double2 *v2 = reinterpret_cast<const double2 *>(xs);
+    const size_t n2 = n / 2;
+    for (size_t k = i; k < n2; k += stride) {
+      const double2 q = __ldcs(v2 + k);
+      lo = q.x < lo ? q.x : lo; hi = q.x > hi ? q.x : hi;
+      lo = q.y < lo ? q.y : lo; hi = q.y > hi ? q.y : hi;
+    }
+    for (size_t k = n2 * 2 + i; k < n; k += stride) {
+      const T q = xs[k];
+      lo = q < lo ? q : lo;
+      hi = q > hi ? q : hi;
+    }
+  }
+  // NaN never enters: every comparison with NaN is false
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T l2 = __shfl_xor_sync(FULL, lo, o), h2 = __shfl_xor_sync(FULL, hi, o);
+    lo = l2 < lo ? l2 : lo;
+    hi = h2 > hi ? h2 : hi;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&ws->minkey, order_key(lo));
+    atomicMax(&ws->maxkey, order_key(hi));
+  }
+}
+
+}  // namespace czp
