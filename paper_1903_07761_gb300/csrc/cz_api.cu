@@ -12,6 +12,7 @@
 #include <cstring>
 
 #include "../../include/cz.h"
+#include "cz_compress.cuh"
 #include "cz_launch.h"
 #include "cz_pair.cuh"
 
@@ -53,11 +54,11 @@ int check(const cz_params *p, Shape *sh)
 }
 
 struct Lanes {
-  cudaError_t (*compress)(int, const CUtensorMap *, const FwdArgs *, int, cudaStream_t);
+  cudaError_t (*compress)(int, const CUtensorMap *, const FwdArgs *, const PlaceArgs *, int, cudaStream_t);
   cudaError_t (*decompress)(int, const InvArgs *, int, cudaStream_t);
   cudaError_t (*dense)(int, int, const DenseArgs *, int, cudaStream_t);
   int (*occupancy)(int, int);
-  int (*scratch)(void);
+  int (*scratch)(int);
 };
 
 #define CZ_LANES(sfx) \
@@ -91,15 +92,31 @@ int grid_for(const cz_params *p, const Shape &sh, int which)
   return (int)(g < sh.nblocks ? g : sh.nblocks);
 }
 
-// workspace: header | one u64 look-back word per block | overflow scratch
+// workspace: header | one u64 look-back word per block | block table
+// (staging offset, chunk bytes) | overflow scratch per compress CTA |
+// chunk staging (room for the largest chunk of every block)
 size_t lb_bytes(const Shape &sh) { return (8ull * sh.nblocks + 255) / 256 * 256; }
+size_t table_bytes(const Shape &sh) { return (16ull * sh.nblocks + 255) / 256 * 256; }
 
-size_t ws_need(const cz_params *p, const Shape &sh)
+struct WsLayout {
+  size_t lb, table, scratch, staging, total;
+  size_t scratch_per_cta;
+};
+
+WsLayout ws_layout(const cz_params *p, const Shape &sh)
 {
   const Lanes L = lanes_for(p->dtype, p->block);
-  const size_t scr = (size_t)L.scratch();
-  return WS_HDR + lb_bytes(sh) + (scr ? scr * (size_t)grid_for(p, sh, 0) : 0);
+  WsLayout w;
+  w.scratch_per_cta = (size_t)L.scratch(0);
+  w.lb = WS_HDR;
+  w.table = w.lb + lb_bytes(sh);
+  w.scratch = w.table + table_bytes(sh);
+  w.staging = w.scratch + (w.scratch_per_cta ? w.scratch_per_cta * (size_t)grid_for(p, sh, 0) : 0);
+  w.total = w.staging + (size_t)L.scratch(1) * (size_t)sh.nblocks;
+  return w;
 }
+
+size_t ws_need(const cz_params *p, const Shape &sh) { return ws_layout(p, sh).total; }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
@@ -186,10 +203,12 @@ int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out
   if (r != CZ_OK) return r;
   if (!d_field || !d_out || !d_ws) return CZ_ERR_ARG;
   if (((uintptr_t)d_field % 16) || ((uintptr_t)d_out % 16) || ((uintptr_t)d_ws % 16)) return CZ_ERR_ARG;
-  if (out_cap < sh.data0 || ws_bytes < ws_need(p, sh)) return CZ_ERR_CAPACITY;
+  const WsLayout wl = ws_layout(p, sh);
+  if (out_cap < sh.data0 || ws_bytes < wl.total) return CZ_ERR_CAPACITY;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   WsHdr *ws = reinterpret_cast<WsHdr *>(d_ws);
-  if (cudaMemsetAsync(d_ws, 0, WS_HDR + lb_bytes(sh), s) != cudaSuccess) return CZ_ERR_CUDA;
+  unsigned char *wsb = reinterpret_cast<unsigned char *>(d_ws);
+  if (cudaMemsetAsync(d_ws, 0, wl.table, s) != cudaSuccess) return CZ_ERR_CUDA;
   if (p->range < 0) {
     if (cudaMemsetAsync(&ws->minkey, 0xFF, 8, s) != cudaSuccess) return CZ_ERR_CUDA;
     const size_t n = (size_t)p->nx * p->ny * p->nz;
@@ -203,8 +222,11 @@ int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out
   a.out = reinterpret_cast<unsigned char *>(d_out);
   a.out_bytes = reinterpret_cast<unsigned long long *>(d_out_bytes);
   a.ws = d_ws;
-  a.scratch_per_cta = (unsigned long long)L.scratch();
-  a.scratch = a.scratch_per_cta ? reinterpret_cast<unsigned char *>(d_ws) + WS_HDR + lb_bytes(sh) : nullptr;
+  a.scratch_per_cta = wl.scratch_per_cta;
+  a.scratch = wl.scratch_per_cta ? wsb + wl.scratch : nullptr;
+  a.staging = wsb + wl.staging;
+  a.staging_cap = wl.total - wl.staging;
+  a.table = reinterpret_cast<unsigned long long *>(wsb + wl.table);
   a.out_cap = out_cap;
   a.data0 = sh.data0;
   a.eps = p->eps;
@@ -220,9 +242,29 @@ int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out
   a.stage2 = p->stage2;
   a.kind = p->kind;
   a.dtype = p->dtype;
+  PlaceArgs pa{};
+  pa.staging = a.staging;
+  pa.table = a.table;
+  pa.out = a.out;
+  pa.out_bytes = a.out_bytes;
+  pa.ws = d_ws;
+  pa.out_cap = out_cap;
+  pa.data0 = sh.data0;
+  pa.eps = p->eps;
+  pa.range = p->range;
+  pa.nx = p->nx;
+  pa.ny = p->ny;
+  pa.nz = p->nz;
+  pa.nblocks = sh.nblocks;
+  pa.block = p->block;
+  pa.levels = sh.L;
+  pa.eps_mode = p->eps_mode;
+  pa.stage2 = p->stage2;
+  pa.kind = p->kind;
+  pa.dtype = p->dtype;
   CUtensorMap tm;
   if (!make_tile_map(&tm, p, d_field)) return CZ_ERR_CUDA;
-  return L.compress(p->kind, &tm, &a, grid_for(p, sh, 0), s) == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
+  return L.compress(p->kind, &tm, &a, &pa, grid_for(p, sh, 0), s) == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
 }
 
 int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used)

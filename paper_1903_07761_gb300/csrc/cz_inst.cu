@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "cz_compress.cuh"
 #include "cz_launch.h"
 #include "cz_pair.cuh"
 
@@ -36,11 +37,14 @@ cudaError_t prepare(int smem)
 }
 
 template <int KIND>
-cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, int grid, cudaStream_t s)
+cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const PlaceArgs &pa, int grid, cudaStream_t s)
 {
-  cudaError_t e = prepare<k_compress2<CZ_T, CZ_B, KIND>>(G::SMEM_C);
+  cudaError_t e = prepare<k_stage1<CZ_T, CZ_B, KIND>>(G::SMEM_C);
   if (e != cudaSuccess) return e;
-  k_compress2<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_C, s>>>(tm, a);
+  k_stage1<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_C, s>>>(tm, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_place<CZ_T><<<a.nblocks, 128, 0, s>>>(pa);
   return cudaGetLastError();
 }
 
@@ -65,9 +69,9 @@ cudaError_t dense_k(const DenseArgs &a, int nblocks, cudaStream_t s)
 template <int KIND>
 int occupancy_c()
 {
-  if (prepare<k_compress2<CZ_T, CZ_B, KIND>>(G::SMEM_C) != cudaSuccess) return 0;
+  if (prepare<k_stage1<CZ_T, CZ_B, KIND>>(G::SMEM_C) != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_compress2<CZ_T, CZ_B, KIND>, G::NT, G::SMEM_C) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage1<CZ_T, CZ_B, KIND>, G::NT, G::SMEM_C) !=
       cudaSuccess)
     return 0;
   return n;
@@ -91,12 +95,12 @@ int occupancy_d()
 #define CZ_SUFFIX CZ_CAT(CZ_CAT(CZ_TNAME, _b), CZ_B)
 
 extern "C" cudaError_t CZ_CAT(czl_compress_, CZ_SUFFIX)(int kind, const CUtensorMap *tm, const FwdArgs *a,
-                                                         int grid, cudaStream_t s)
+                                                         const PlaceArgs *pa, int grid, cudaStream_t s)
 {
   switch (kind) {
-    case W4: return compress_k<W4>(*tm, *a, grid, s);
-    case W4LI: return compress_k<W4LI>(*tm, *a, grid, s);
-    default: return compress_k<W3AI>(*tm, *a, grid, s);
+    case W4: return compress_k<W4>(*tm, *a, *pa, grid, s);
+    case W4LI: return compress_k<W4LI>(*tm, *a, *pa, grid, s);
+    default: return compress_k<W3AI>(*tm, *a, *pa, grid, s);
   }
 }
 
@@ -143,5 +147,6 @@ extern "C" int CZ_CAT(czl_occupancy_, CZ_SUFFIX)(int kind, int which)
   }
 }
 
-// overflow scratch bytes per persistent compress CTA
-extern "C" int CZ_CAT(czl_scratch_, CZ_SUFFIX)(void) { return G::SCR; }
+// overflow scratch bytes per persistent compress CTA (which = 0) and the
+// largest chunk (which = 1)
+extern "C" int CZ_CAT(czl_scratch_, CZ_SUFFIX)(int which) { return which == 0 ? G::SCR : G::CHMAX; }

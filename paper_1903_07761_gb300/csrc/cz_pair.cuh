@@ -17,9 +17,10 @@
 // per-thread bit columns over z are turned into the stream's row words (bit
 // x of row (z, y)) by a B x B bit-matrix transpose over the lanes of a row.
 //
-// k_compress2 is persistent: one CTA per SM slot walks the blocks in ticket
-// order and prefetches the next block's tile with a TMA bulk-tensor copy
-// while it works on the current one.
+// Compression runs as two kernels (cz_compress.cuh): a persistent stage
+// kernel that turns blocks into finished chunks in workspace staging while
+// the next tile arrives by TMA, and a placement kernel that computes chunk
+// offsets with a decoupled look-back and copies the chunks into the stream.
 #pragma once
 
 #include <cuda.h>
@@ -38,12 +39,15 @@ constexpr unsigned MAGIC = 0x315A4343u;
 constexpr int WS_HDR = 256;
 constexpr unsigned WAIT_LIMIT = 1u << 24;
 
+// workspace header (the look-back words, the block table, the overflow
+// scratch and the chunk staging area follow it)
 struct WsHdr {
   unsigned status;
   unsigned ticket;
   unsigned pad0, pad1;
   unsigned long long minkey, maxkey;
   unsigned long long out_bytes;
+  unsigned long long bump;  // staging bytes handed out so far
 };
 
 struct FwdArgs {
@@ -51,8 +55,10 @@ struct FwdArgs {
   unsigned char *out;
   unsigned long long *out_bytes;  // may be null
   void *ws;
-  unsigned char *scratch;         // per-CTA overflow payload space (may be null)
-  unsigned long long out_cap, data0, scratch_per_cta;
+  unsigned char *scratch;  // per-CTA overflow payload space (may be null)
+  unsigned char *staging;  // finished chunks, in completion order
+  unsigned long long *table;  // per block: staging offset, chunk bytes
+  unsigned long long out_cap, data0, scratch_per_cta, staging_cap;
   double eps, range;
   int nx, ny, nz, nbx, nby, nbz, nblocks;
   int eps_mode, stage2, kind, dtype;
@@ -143,6 +149,7 @@ struct G2 {
   static constexpr int L = (B == 8) ? 1 : (B == 16) ? 2 : 3;
   static constexpr int Q = B / 4;
   static constexpr int ES = (int)sizeof(T);
+  static constexpr int LGES = ES == 8 ? 3 : 2;
   static constexpr int NVOX = B * B * B;
   static constexpr int NMW = NVOX / 32;
   static constexpr int MASKB = NVOX / 8;
@@ -154,18 +161,21 @@ struct G2 {
   static constexpr int XB = ZB * B * B * ES;
   static constexpr int ADB = ZB * (B / 2) * B * ES;
   static constexpr int ROWB = B * B * 4;
+  static constexpr int NAUX = 6;  // stage-2 arrays per zero-bitmap word
   static constexpr int BUDGET = 227 * 1024 - 2048;
-  static constexpr int PCAP0 = (BUDGET - TILE - XB - ADB) / 128 * 128;
   static constexpr int PMAX_AL = (PMAX + 127) / 128 * 128;
-  static constexpr int PCAP = PCAP0 < PMAX_AL ? PCAP0 : PMAX_AL;  // smem payload capacity (compress)
-  static constexpr bool OVERFLOW = PCAP < PMAX;
+  // compress: tile | planes / aux | payload (capacity PCAP)
+  static constexpr int PCAP0 = (BUDGET - TILE - XB - ADB) / 128 * 128;
+  static constexpr int PCAP = PCAP0 < PMAX_AL ? PCAP0 : PMAX_AL;
   static constexpr int NBWC = (PCAP / 4 + 31) / 32;
-  static constexpr int AUXC = ROWB + 4 * NBWC * 4;  // row offsets + stage-2 arrays
+  static constexpr int AUXC = ROWB + MASKB + NAUX * NBWC * 4;
   static constexpr int R2C0 = (XB + ADB) > AUXC ? (XB + ADB) : AUXC;
   static constexpr int R2C = (R2C0 + 127) / 128 * 128;
   static constexpr int SMEM_C = TILE + R2C + PCAP;
-  // overflow scratch per CTA: payload + stage-2 arrays
-  static constexpr int SCR = OVERFLOW ? ((PMAX + 4 * NBWMAX * 4 + 255) / 256 * 256) : 0;
+  // overflow scratch per compress CTA: payload + stage-2 arrays
+  static constexpr int SCR = PCAP < PMAX ? ((PMAX_AL + NAUX * NBWMAX * 4 + 255) / 256 * 256) : 0;
+  // largest chunk: raw 8 + PMAX, or 8 + 4 (tokens + literals) <= 12 + PMAX
+  static constexpr int CHMAX = (16 + PMAX + 15) / 16 * 16;
   // decompress: no tile; the whole payload always fits
   static constexpr int AUXD = ROWB + 2 * NT * 4;
   static constexpr int R2D0 = (XB + ADB) > AUXD ? (XB + ADB) : AUXD;
@@ -173,6 +183,7 @@ struct G2 {
   static constexpr int SMEM_D = R2D + PMAX_AL;
   static_assert(SMEM_C <= 227 * 1024 - 1024, "compress shared memory");
   static_assert(SMEM_D <= 227 * 1024 - 1024, "decompress shared memory");
+  static_assert(WMAX < 65536, "zero-RLE tokens hold run lengths below 65536 words");
 };
 
 // ------------------------------------------------------------ TMA / mbarrier
@@ -928,11 +939,11 @@ __device__ __forceinline__ unsigned get_row(const unsigned char *mask, int z, in
 }
 
 template <typename T>
-__device__ __forceinline__ void threshold_of(const FwdArgs &a, const WsHdr *ws, double &mn, double &mx,
-                                             double &range, T &t)
+__device__ __forceinline__ void threshold_of(double eps, int eps_mode, double range_in, const WsHdr *ws,
+                                             double &mn, double &mx, double &range, T &t)
 {
-  if (a.range >= 0) {
-    range = a.range;
+  if (range_in >= 0) {
+    range = range_in;
     mn = mx = __longlong_as_double(0x7FF8000000000000LL);
   } else {
     const unsigned long long kmin = *(volatile const unsigned long long *)&ws->minkey;
@@ -943,336 +954,8 @@ __device__ __forceinline__ void threshold_of(const FwdArgs &a, const WsHdr *ws, 
     mx = (double)(T)((T)mx + (T)0);
     range = (mn <= mx) ? mx - mn : 0.0;
   }
-  const double td = a.eps_mode == 1 ? a.eps : a.eps * range;
+  const double td = eps_mode == 1 ? eps : eps * range;
   t = (T)td;
-}
-
-// ============================================================ compress
-template <typename T, int B, int KIND>
-__global__ void __launch_bounds__(B * B / 2, 1)
-    k_compress2(const __grid_constant__ CUtensorMap tmap, const FwdArgs a)
-{
-  using G = G2<T, B>;
-  using T2 = typename V2T<T>::type;
-  constexpr int NT = G::NT, ES = G::ES, NMW = G::NMW, Q = G::Q;
-  extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char *PF = smem;
-  unsigned char *R2 = smem + G::TILE;
-  unsigned char *PS = R2 + G::R2C;
-  T *X = reinterpret_cast<T *>(R2);
-  T *AD = reinterpret_cast<T *>(R2 + G::XB);
-  unsigned *ROWOFF = reinterpret_cast<unsigned *>(R2);
-  __shared__ __align__(8) unsigned long long s_bar;
-  __shared__ unsigned s_u[40];
-  __shared__ int s_i[40];
-  __shared__ int s_cur, s_next;
-  __shared__ unsigned long long s_excl;
-
-  WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
-  unsigned long long *lbst = reinterpret_cast<unsigned long long *>((char *)a.ws + WS_HDR);
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int ap = tid % G::HP, r = tid / G::HP;
-  const int y = r < B / 2 ? 2 * r : 2 * (r - B / 2) + 1;
-  const int seg = lane - ap;
-  const int x0 = 2 * ap;
-
-  double mn, mx, range;
-  T t;
-  threshold_of<T>(a, ws, mn, mx, range, t);
-  const unsigned long long tb = thr_bits(t);
-  // coarse positions (x, y, z all multiples of B/4) never enter the mask
-  const bool cE = (x0 % Q == 0) && (y % Q == 0);
-  unsigned cmask = 0;
-#pragma unroll
-  for (int z = 0; z < B; z += Q) cmask |= 1u << z;
-
-  auto coords = [&](int bid, int &bx, int &by, int &bz) {
-    bx = bid % a.nbx;
-    by = (bid / a.nbx) % a.nby;
-    bz = bid / (a.nbx * a.nby);
-  };
-
-  if (tid == 0) {
-    mbar_init(&s_bar);
-    s_cur = (int)atomicAdd(&ws->ticket, 1u);
-    if (s_cur < a.nblocks) {
-      int bx, by, bz;
-      coords(s_cur, bx, by, bz);
-      tma_load_tile(&tmap, PF, &s_bar, bx * B, by * B, bz * B, G::TILE);
-    }
-  }
-  __syncthreads();
-  unsigned phase = 0;
-
-  for (;;) {
-    const int bid = s_cur;
-    if (bid >= a.nblocks) break;
-    if (!mbar_wait(&s_bar, phase)) {
-      // the copy never completed: record, wait once more for it, stop
-      if (tid == 0) atomicCAS(&ws->status, 0u, ST_TIMEOUT);
-      mbar_wait(&s_bar, phase);
-      break;
-    }
-    phase ^= 1u;
-
-    // ---- a1: tile -> registers
-    T2 v[B];
-#pragma unroll
-    for (int z = 0; z < B; ++z) v[z] = *reinterpret_cast<const T2 *>(PF + ((z * B + y) * B + x0) * ES);
-    __syncthreads();
-    if (tid == 0) {
-      s_next = (int)atomicAdd(&ws->ticket, 1u);
-      if (s_next < a.nblocks) {
-        int bx, by, bz;
-        coords(s_next, bx, by, bz);
-        tma_load_tile(&tmap, PF, &s_bar, bx * B, by * B, bz * B, G::TILE);
-      }
-    }
-
-    // ---- a2: forward transform
-    fwd_all<T, B, KIND>(v, X, AD, ap, y, seg);
-
-    // ---- a3: significance bits over z, row words by bit transpose
-    unsigned me = 0, mo = 0;
-#pragma unroll
-    for (int z = 0; z < B; ++z) {
-      me |= (unsigned)(magbits(v[z].x) >= tb) << z;
-      mo |= (unsigned)(magbits(v[z].y) >= tb) << z;
-    }
-    if (cE) me &= ~cmask;
-    unsigned w0 = me, w1 = mo;
-    bit_transpose<B>(w0, w1, ap);  // words of rows (z = 2ap, y) and (z = 2ap + 1, y)
-    __syncthreads();               // planes X / AD free: row offsets go there
-    ROWOFF[(2 * ap) * B + y] = __popc(w0);
-    ROWOFF[(2 * ap + 1) * B + y] = __popc(w1);
-    __syncthreads();
-    unsigned nnz;
-    {
-      constexpr int IPT = (B * B + NT - 1) / NT;
-      unsigned loc[IPT], sum = 0;
-#pragma unroll
-      for (int q = 0; q < IPT; ++q) {
-        loc[q] = ROWOFF[tid * IPT + q];
-        sum += loc[q];
-      }
-      unsigned ex = block_exsum<NT>(sum, s_u, nnz);
-#pragma unroll
-      for (int q = 0; q < IPT; ++q) {
-        ROWOFF[tid * IPT + q] = ex;
-        ex += loc[q];
-      }
-    }
-    __syncthreads();
-
-    // ---- a4: payload [coarse | mask | values] in shared memory, or in
-    // this CTA's global scratch when it does not fit
-    const int pbytes = 64 * ES + G::MASKB + (int)nnz * ES;
-    const bool in_smem = pbytes <= G::PCAP;
-    unsigned char *P = in_smem ? PS : a.scratch + (size_t)blockIdx.x * a.scratch_per_cta;
-    unsigned *S2 = in_smem ? reinterpret_cast<unsigned *>(R2 + G::ROWB)
-                           : reinterpret_cast<unsigned *>(P + ((G::PMAX + 15) / 16 * 16));
-    const int nbw_cap = in_smem ? G::NBWC : G::NBWMAX;
-    unsigned *ZBM = S2, *CMk = S2 + nbw_cap, *BDM = CMk + nbw_cap, *LP = BDM + nbw_cap;
-    unsigned char *MASK = P + 64 * ES;
-    T *VALS = reinterpret_cast<T *>(MASK + G::MASKB);
-    put_row<B>(MASK, 2 * ap, y, w0);
-    put_row<B>(MASK, 2 * ap + 1, y, w1);
-    if (cE) {
-#pragma unroll
-      for (int z = 0; z < B; z += Q) reinterpret_cast<T *>(P)[((z / Q) * 4 + y / Q) * 4 + x0 / Q] = v[z].x;
-    }
-    __syncthreads();
-    {
-      const unsigned any_bits = me | mo;
-      const unsigned lowE = (1u << x0) - 1u, lowO = (2u << x0) - 1u;
-#pragma unroll
-      for (int z = 0; z < B; ++z) {
-        const bool have = (any_bits >> z) & 1u;
-        if (__any_sync(FULL, have)) {
-          if (have) {
-            const unsigned wd = get_row<B>(MASK, z, y);
-            const unsigned base = ROWOFF[z * B + y];
-            if ((me >> z) & 1u) VALS[base + __popc(wd & lowE)] = v[z].x;
-            if ((mo >> z) & 1u) VALS[base + __popc(wd & lowO)] = v[z].y;
-          }
-        }
-      }
-    }
-    __syncthreads();
-
-    // ---- a6: stage 2 sizes (byte shuffle + zero-word RLE)
-    const int W = pbytes / 4, E = pbytes / ES, NB = (W + 31) / 32;
-    const int KB = (NB + NT - 1) / NT;
-    unsigned ntok = 0, nlit = 0, tokbase = 0;
-    int prev_before = -1, next_after = W;
-    if (a.stage2) {
-      for (int wb = tid >> 5; wb < NB; wb += G::NW) {
-        const int w = wb * 32 + lane;
-        const bool zr = (w < W) && (shuffled_word(P, w, E, ES) == 0u);
-        const unsigned bal = __ballot_sync(FULL, zr);
-        if (lane == 0) ZBM[wb] = bal;
-      }
-      __syncthreads();
-      int first_bd = W, last_bd = -1;
-      unsigned my_lit = 0;
-      for (int q = 0; q < KB; ++q) {
-        const int i = tid * KB + q;
-        if (i < NB) {
-          const unsigned Z = ZBM[i];
-          const unsigned pw = i > 0 ? ZBM[i - 1] : 0u;
-          const unsigned nw = (i + 1 < NB) ? ZBM[i + 1] : 0u;
-          unsigned C = Z & ((Z << 1) | (pw >> 31) | (Z >> 1) | ((nw & 1u) << 31));
-          const unsigned cp = i > 0 ? ((pw >> 31) & (((pw >> 30) & 1u) | (Z & 1u))) : 0u;
-          unsigned Bd = C ^ ((C << 1) | cp);
-          if (i == 0) Bd |= 1u;
-          const unsigned valid = (i == NB - 1 && (W & 31)) ? ((1u << (W & 31)) - 1u) : FULL;
-          C &= valid;
-          Bd &= valid;
-          CMk[i] = C;
-          BDM[i] = Bd;
-          my_lit += __popc(~C & valid);
-          if (Bd) {
-            if (first_bd == W) first_bd = i * 32 + __ffs(Bd) - 1;
-            last_bd = i * 32 + 31 - __clz(Bd);
-          }
-        }
-      }
-      const unsigned litbase = block_exsum<NT>(my_lit, s_u, nlit);
-      prev_before = block_exmax<NT>(last_bd, -1, s_i);
-      next_after = block_rexmin<NT>(first_bd, W, s_i);
-      {
-        unsigned run = litbase;
-        for (int q = 0; q < KB; ++q) {
-          const int i = tid * KB + q;
-          if (i < NB) {
-            const unsigned valid = (i == NB - 1 && (W & 31)) ? ((1u << (W & 31)) - 1u) : FULL;
-            LP[i] = run;
-            run += __popc(~CMk[i] & valid);
-          }
-        }
-      }
-      unsigned my_tok = 0;
-      {
-        int prev = prev_before, cur = -1;
-        auto handle = [&](int p, int pv, int nb) {
-          if ((CMk[p >> 5] >> (p & 31)) & 1u)
-            my_tok += tokcount(p == 0 ? 0u : (unsigned)(p - pv), (unsigned)(nb - p));
-          else if (nb == W)
-            my_tok += tokcount((unsigned)(W - p), 0u);
-        };
-        for (int q = 0; q < KB; ++q) {
-          const int i = tid * KB + q;
-          if (i < NB) {
-            unsigned bd = BDM[i];
-            while (bd) {
-              const int p = i * 32 + __ffs(bd) - 1;
-              bd &= bd - 1u;
-              if (cur >= 0) {
-                handle(cur, prev, p);
-                prev = cur;
-              }
-              cur = p;
-            }
-          }
-        }
-        if (cur >= 0) handle(cur, prev, next_after);
-      }
-      tokbase = block_exsum<NT>(my_tok, s_u, ntok);
-    }
-    const unsigned long long size =
-        a.stage2 ? 8ull + 4ull * ntok + 4ull * nlit : 8ull + (unsigned long long)pbytes;
-
-    // ---- a5: chunk offset by decoupled look-back
-    if (tid < 32) {
-      const unsigned long long ex = lookback(lbst, bid, size, &ws->status, (int)ST_TIMEOUT);
-      if (lane == 0) s_excl = ex;
-    }
-    __syncthreads();
-    const unsigned long long excl = s_excl;
-    const bool fits = a.data0 + excl + size <= a.out_cap;
-    if (tid == 0) {
-      st_le<unsigned long long>(a.out + HEADER_BYTES + 8ull * bid, excl);
-      if (!fits) atomicCAS(&ws->status, 0u, ST_CAPACITY);
-      if (bid == a.nblocks - 1) {
-        const unsigned long long data_bytes = excl + size, total = a.data0 + data_bytes;
-        unsigned char *h = a.out;
-        st_le<unsigned long long>(h + HEADER_BYTES + 8ull * a.nblocks, data_bytes);
-        for (unsigned long long q = HEADER_BYTES + 8ull * (a.nblocks + 1); q < a.data0; ++q) h[q] = 0;
-        for (int q = 0; q < HEADER_BYTES; ++q) h[q] = 0;
-        st_le<unsigned>(h + 0, MAGIC);
-        st_le<unsigned short>(h + 4, 1);
-        st_le<unsigned short>(h + 6, HEADER_BYTES);
-        st_le<int>(h + 8, a.nx);
-        st_le<int>(h + 12, a.ny);
-        st_le<int>(h + 16, a.nz);
-        h[20] = (unsigned char)B;
-        h[21] = (unsigned char)a.dtype;
-        h[22] = (unsigned char)a.kind;
-        h[23] = (unsigned char)a.stage2;
-        h[24] = (unsigned char)a.eps_mode;
-        h[25] = (unsigned char)G::L;
-        st_le<unsigned>(h + 28, (unsigned)a.nblocks);
-        st_le_f64(h + 32, a.eps);
-        st_le_f64(h + 40, (double)t);
-        st_le_f64(h + 48, mn);
-        st_le_f64(h + 56, mx);
-        st_le_f64(h + 64, range);
-        st_le<unsigned long long>(h + 72, data_bytes);
-        st_le<unsigned long long>(h + 80, total);
-        ws->out_bytes = total;
-        if (a.out_bytes) *a.out_bytes = total;
-      }
-    }
-    if (fits) {
-      unsigned *ch32 = reinterpret_cast<unsigned *>(a.out + a.data0 + excl);
-      if (tid == 0) {
-        ch32[0] = nnz;
-        ch32[1] = a.stage2 ? ntok : 0u;
-      }
-      if (a.stage2) {
-        unsigned *tok = ch32 + 2;
-        {
-          unsigned idx = tokbase;
-          int prev = prev_before, cur = -1;
-          auto handle = [&](int p, int pv, int nb) {
-            if ((CMk[p >> 5] >> (p & 31)) & 1u)
-              idx = emit_tokens(tok, idx, p == 0 ? 0u : (unsigned)(p - pv), (unsigned)(nb - p));
-            else if (nb == W)
-              idx = emit_tokens(tok, idx, (unsigned)(W - p), 0u);
-          };
-          for (int q = 0; q < KB; ++q) {
-            const int i = tid * KB + q;
-            if (i < NB) {
-              unsigned bd = BDM[i];
-              while (bd) {
-                const int p = i * 32 + __ffs(bd) - 1;
-                bd &= bd - 1u;
-                if (cur >= 0) {
-                  handle(cur, prev, p);
-                  prev = cur;
-                }
-                cur = p;
-              }
-            }
-          }
-          if (cur >= 0) handle(cur, prev, next_after);
-        }
-        unsigned *lit = tok + ntok;
-        for (int w = tid; w < W; w += NT) {
-          const unsigned C = CMk[w >> 5];
-          const int b = w & 31;
-          if (!((C >> b) & 1u)) lit[LP[w >> 5] + __popc(~C & ((1u << b) - 1u))] = shuffled_word(P, w, E, ES);
-        }
-      } else {
-        const unsigned *P32 = reinterpret_cast<const unsigned *>(P);
-        for (int w = tid; w < pbytes / 4; w += NT) ch32[2 + w] = P32[w];
-      }
-    }
-    __syncthreads();
-    if (tid == 0) s_cur = s_next;
-    __syncthreads();
-  }
-  (void)NMW;
 }
 
 // ============================================================ decompress
