@@ -100,7 +100,7 @@ size_t table_bytes(const Shape &sh) { return (16ull * sh.nblocks + 255) / 256 * 
 
 struct WsLayout {
   size_t lb, table, scratch, staging, total;
-  size_t scratch_per_cta;
+  size_t scratch_per_cta, arena;
 };
 
 WsLayout ws_layout(const cz_params *p, const Shape &sh)
@@ -112,7 +112,11 @@ WsLayout ws_layout(const cz_params *p, const Shape &sh)
   w.table = w.lb + lb_bytes(sh);
   w.scratch = w.table + table_bytes(sh);
   w.staging = w.scratch + (w.scratch_per_cta ? w.scratch_per_cta * (size_t)grid_for(p, sh, 0) : 0);
-  w.total = w.staging + (size_t)L.scratch(1) * (size_t)sh.nblocks;
+  // one staging arena per compress CTA, room for the largest chunk of each
+  // of its blocks (blocks are dealt round robin)
+  const size_t grid = (size_t)grid_for(p, sh, 0);
+  w.arena = (((size_t)sh.nblocks + grid - 1) / grid) * (size_t)L.scratch(1);
+  w.total = w.staging + w.arena * grid;
   return w;
 }
 
@@ -225,7 +229,7 @@ int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out
   a.scratch_per_cta = wl.scratch_per_cta;
   a.scratch = wl.scratch_per_cta ? wsb + wl.scratch : nullptr;
   a.staging = wsb + wl.staging;
-  a.staging_cap = wl.total - wl.staging;
+  a.arena_bytes = wl.arena;
   a.table = reinterpret_cast<unsigned long long *>(wsb + wl.table);
   a.out_cap = out_cap;
   a.data0 = sh.data0;

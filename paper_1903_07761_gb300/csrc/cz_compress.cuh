@@ -6,11 +6,11 @@
 //   [64 coarse values | mask row words | kept details in position order]
 // either raw or, with stage 2, directly in byte-shuffled order (byte b of
 // payload element e at b * E + e; the element size is a power of two, so
-// no division is needed).  One warp then finds the zero-word runs of the
-// shuffled payload with warp scans over a ballot bitmap, the CTA writes the
-// finished chunk [nnz | ntok | tokens | literal words] to workspace staging
-// at an offset taken from an atomic bump counter, and records (offset,
-// bytes) in the block table.  No CTA ever waits for another one.
+// no division is needed).  The CTA then finds the zero-word runs of the
+// shuffled payload from a ballot bitmap with one block scan, and the CTA
+// writes the finished chunk [nnz | ntok | tokens | literal words] to its own
+// staging arena and records (offset, bytes) in the block table.  No CTA
+// ever waits for another one.
 //
 // k_place (one CTA per chunk, ticket order): exclusive prefix of the chunk
 // sizes by decoupled look-back, copy of the chunk to its place in the
@@ -49,9 +49,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
   unsigned char *MASKU = R2 + G::ROWB;  // unshuffled mask rows (for placing values)
   __shared__ __align__(8) unsigned long long s_bar;
   __shared__ unsigned s_u[40];
-  __shared__ unsigned s_ntok, s_nlit, s_ns, s_lastc;
-  __shared__ int s_laste;
-  __shared__ unsigned long long s_soff;
+  __shared__ unsigned long long s_aoff;  // bytes used in this CTA's staging arena
 
   WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -63,17 +61,19 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
   double mn, mx, range;
   T t;
   threshold_of<T>(a.eps, a.eps_mode, a.range, ws, mn, mx, range, t);
-  const unsigned long long tb = thr_bits(t);
+  const auto tb = thr_bits(t);
   const bool cE = (x0 % Q == 0) && (y % Q == 0);  // this column pair holds coarse values (E)
   unsigned cmask = 0;
 #pragma unroll
   for (int z = 0; z < B; z += Q) cmask |= 1u << z;
+  unsigned char *arena = a.staging + (size_t)blockIdx.x * a.arena_bytes;
 
   auto tile_of = [&](int bid) {
     const int bx = bid % a.nbx, by = (bid / a.nbx) % a.nby, bz = bid / (a.nbx * a.nby);
     tma_load_tile(&tmap, PF, &s_bar, bx * B, by * B, bz * B, G::TILE);
   };
   if (tid == 0) {
+    s_aoff = 0;
     mbar_init(&s_bar);
     if ((int)blockIdx.x < a.nblocks) tile_of(blockIdx.x);
   }
@@ -144,8 +144,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     unsigned *AUX = in_smem ? reinterpret_cast<unsigned *>(MASKU + G::MASKB)
                             : reinterpret_cast<unsigned *>(scr + G::PMAX_AL);
     const int cap = in_smem ? G::NBWC : G::NBWMAX;
-    unsigned *ZBM = AUX, *CM = AUX + cap, *CPRE = AUX + 2 * cap, *TPRE = AUX + 3 * cap,
-             *PREVE = AUX + 4 * cap, *NEXTE = AUX + 5 * cap;
+    unsigned *ZBM = AUX, *CM = AUX + cap, *EB = AUX + 2 * cap, *PRE = AUX + 3 * cap;
     const bool shuf = a.stage2 != 0;
     // payload byte p -> position (byte p % ES of element p / ES goes to
     // plane p % ES at index p / ES)
@@ -181,28 +180,30 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
 #pragma unroll
       for (int z = 0; z < B; z += Q) put_val(((z / Q) * 4 + y / Q) * 4 + x0 / Q, v[z].x);
     }
-    __syncthreads();
     {
+      // kept details of this column pair, z by z (work grows with the count)
       const int VOFF = (64 * ES + G::MASKB) >> LGES;
-      const unsigned any_bits = me | mo;
       const unsigned lowE = (1u << x0) - 1u, lowO = (2u << x0) - 1u;
-#pragma unroll
-      for (int z = 0; z < B; ++z) {
-        const bool have = (any_bits >> z) & 1u;
-        if (__any_sync(FULL, have)) {
-          if (have) {
-            const unsigned wd = get_row<B>(MASKU, z, y);
-            const unsigned base = ROWOFF[z * B + y];
-            if ((me >> z) & 1u) put_val(VOFF + base + __popc(wd & lowE), v[z].x);
-            if ((mo >> z) & 1u) put_val(VOFF + base + __popc(wd & lowO), v[z].y);
-          }
-        }
+      unsigned bits = me | mo;
+      while (bits) {
+        const int z = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const T2 val = pick<B>(v, z);
+        const unsigned wd = get_row<B>(MASKU, z, y);
+        const unsigned base = ROWOFF[z * B + y];
+        if ((me >> z) & 1u) put_val(VOFF + base + __popc(wd & lowE), val.x);
+        if ((mo >> z) & 1u) put_val(VOFF + base + __popc(wd & lowO), val.y);
       }
     }
     __syncthreads();
 
-    // ---- a6: zero-word runs of the shuffled payload
+    // ---- a6: zero-word runs of the shuffled payload.  Coded words C are
+    // zero words with a zero neighbour; a run starts at S bits and ends
+    // before an Eb bit (or at W).  One token per run: (literal words since
+    // the previous run, run length); a final (literals, 0) token when the
+    // payload does not end in a run.
     const unsigned *P32 = reinterpret_cast<const unsigned *>(P);
+    unsigned ns_tot = 0, nc_tot = 0, lastc = 1;
     if (shuf) {
       for (int g = wid; g < NB; g += G::NW) {
         const int w = g * 32 + lane;
@@ -210,109 +211,58 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
         if (lane == 0) ZBM[g] = bal;
       }
       __syncthreads();
-      if (wid == 0) {
-        // forward sweep: coded words C (zero words with a zero neighbour),
-        // run starts S, run ends Ebits; prefix counts of tokens and coded
-        // words, and the last run end before each bitmap word
-        unsigned carry_s = 0, carry_c = 0, prevC = 0, prevZ = 0;
-        int carry_e = 0;
-        for (int g0 = 0; g0 < NB; g0 += 32) {
-          const int g = g0 + lane;
-          const unsigned Z = g < NB ? ZBM[g] : 0u;
-          unsigned Zp = __shfl_up_sync(FULL, Z, 1);
-          if (lane == 0) Zp = prevZ;
-          unsigned Zn = __shfl_down_sync(FULL, Z, 1);
-          if (lane == 31) Zn = g + 1 < NB ? ZBM[g + 1] : 0u;
-          const unsigned valid = g < NB ? ((g == NB - 1 && (W & 31)) ? ((1u << (W & 31)) - 1u) : FULL) : 0u;
+      const int KB = (NB + NT - 1) / NT;  // bitmap words per thread (contiguous)
+      unsigned mine = 0;
+      for (int q = 0; q < KB; ++q) {
+        const int g = tid * KB + q;
+        if (g < NB) {
+          const unsigned Z = ZBM[g];
+          const unsigned Zp = g > 0 ? ZBM[g - 1] : 0u, Zn = g + 1 < NB ? ZBM[g + 1] : 0u;
+          const unsigned valid = (g == NB - 1 && (W & 31)) ? ((1u << (W & 31)) - 1u) : FULL;
           const unsigned C = Z & ((Z << 1) | (Zp >> 31) | (Z >> 1) | ((Zn & 1u) << 31)) & valid;
-          unsigned Cp = __shfl_up_sync(FULL, C, 1);
-          if (lane == 0) Cp = prevC;
-          const unsigned cin = Cp >> 31;
+          // coded bit of the word before: zero with a zero neighbour
+          const unsigned cin = g > 0 ? ((Zp >> 31) & (((Zp >> 30) & 1u) | (Z & 1u))) : 0u;
           const unsigned S = C & ~((C << 1) | cin);
-          const unsigned Eb = ~C & ((C << 1) | cin) & valid;
-          const unsigned ns = __popc(S), nc = __popc(C);
-          const int le = Eb ? g * 32 + 31 - __clz(Eb) : 0;
-          unsigned is = ns, ic = nc;
-          int ie = le;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const unsigned us = __shfl_up_sync(FULL, is, o), uc = __shfl_up_sync(FULL, ic, o);
-            const int ue = __shfl_up_sync(FULL, ie, o);
-            if (lane >= o) {
-              is += us;
-              ic += uc;
-              ie = max(ie, ue);
-            }
-          }
-          int ee = __shfl_up_sync(FULL, ie, 1);
-          if (lane == 0) ee = 0;
-          if (g < NB) {
-            CM[g] = C;
-            TPRE[g] = carry_s + is - ns;
-            CPRE[g] = carry_c + ic - nc;
-            PREVE[g] = (unsigned)max(carry_e, ee);
-          }
-          carry_s += __shfl_sync(FULL, is, 31);
-          carry_c += __shfl_sync(FULL, ic, 31);
-          carry_e = max(carry_e, __shfl_sync(FULL, ie, 31));
-          prevC = __shfl_sync(FULL, C, 31);
-          prevZ = __shfl_sync(FULL, Z, 31);
-        }
-        __syncwarp();
-        // backward sweep: first run end after each bitmap word (W if none)
-        int carry_n = W;
-        for (int g0 = ((NB - 1) >> 5) << 5; g0 >= 0; g0 -= 32) {
-          const int g = g0 + lane;
-          int fe = 0x7fffffff;
-          if (g < NB) {
-            const unsigned C = CM[g];
-            const unsigned cin = g > 0 ? (CM[g - 1] >> 31) : 0u;
-            const unsigned valid = (g == NB - 1 && (W & 31)) ? ((1u << (W & 31)) - 1u) : FULL;
-            const unsigned Eb = ~C & ((C << 1) | cin) & valid;
-            if (Eb) fe = g * 32 + __ffs(Eb) - 1;
-          }
-          int m = fe;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int d = __shfl_down_sync(FULL, m, o);
-            if (lane + o < 32) m = min(m, d);
-          }
-          int after = __shfl_down_sync(FULL, m, 1);
-          if (lane == 31) after = 0x7fffffff;
-          if (g < NB) NEXTE[g] = (unsigned)min(carry_n, after);
-          carry_n = min(carry_n, __shfl_sync(FULL, m, 0));
-        }
-        __syncwarp();
-        if (lane == 0) {
-          const unsigned lastc = (CM[NB - 1] >> ((W - 1) & 31)) & 1u;
-          s_ns = carry_s;
-          s_lastc = lastc;
-          s_laste = carry_e;
-          s_ntok = carry_s + (lastc ? 0u : 1u);
-          s_nlit = (unsigned)W - carry_c;
+          CM[g] = C;
+          EB[g] = ~C & ((C << 1) | cin) & valid;
+          mine += (unsigned)__popc(S) | ((unsigned)__popc(C) << 16);
         }
       }
-    } else if (tid == 0) {
-      s_ntok = 0;
-      s_nlit = 0;
+      unsigned tot;
+      unsigned run = block_exsum<NT>(mine, s_u, tot);  // packed: runs | coded words << 16
+      for (int q = 0; q < KB; ++q) {
+        const int g = tid * KB + q;
+        if (g < NB) {
+          PRE[g] = run;
+          const unsigned C = CM[g];
+          const unsigned cin = g > 0 ? (CM[g - 1] >> 31) : 0u;
+          run += (unsigned)__popc(C & ~((C << 1) | cin)) | ((unsigned)__popc(C) << 16);
+        }
+      }
+      ns_tot = tot & 0xFFFFu;
+      nc_tot = tot >> 16;
+      lastc = (ZBM[NB - 1] >> ((W - 1) & 31)) & 1u;  // last word zero ...
+      if (lastc) {                                     // ... and coded?
+        const int l = W - 1;
+        const bool prevz = l > 0 && ((ZBM[(l - 1) >> 5] >> ((l - 1) & 31)) & 1u);
+        lastc = prevz ? 1u : 0u;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    const unsigned ntok = s_ntok, nlit = s_nlit;
+    const unsigned ntok = shuf ? ns_tot + (lastc ? 0u : 1u) : 0u;
+    const unsigned nlit = shuf ? (unsigned)W - nc_tot : 0u;
     const unsigned long long size = shuf ? 8ull + 4ull * ntok + 4ull * nlit : 8ull + (unsigned long long)pbytes;
 
-    // ---- chunk -> staging (offset from the bump counter)
+    // ---- finished chunk -> this CTA's staging arena
+    const unsigned long long so = s_aoff;
+    const bool ok = so + size <= a.arena_bytes;
     if (tid == 0) {
-      const unsigned long long so = atomicAdd(&ws->bump, (size + 15) & ~15ull);
-      s_soff = so;
-      const bool ok = so + size <= a.staging_cap;
       if (!ok) atomicCAS(&ws->status, 0u, ST_CAPACITY);
-      a.table[2 * bid] = so;
+      a.table[2 * bid] = (unsigned long long)(arena - a.staging) + so;
       a.table[2 * bid + 1] = ok ? size : 0xFFFFFFFFFFFFFFFFull;
     }
-    __syncthreads();
-    const unsigned long long so = s_soff;
-    if (so + size <= a.staging_cap) {
-      unsigned *ch = reinterpret_cast<unsigned *>(a.staging + so);
+    if (ok) {
+      unsigned *ch = reinterpret_cast<unsigned *>(arena + so);
       if (tid == 0) {
         ch[0] = nnz;
         ch[1] = ntok;
@@ -320,35 +270,56 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
       if (shuf) {
         unsigned *tok = ch + 2;
         unsigned *lit = tok + ntok;
-        // one token per coded run: (literal words before it, run length)
-        for (int g = tid; g < NB; g += NT) {
-          const unsigned C = CM[g];
+        const int KB = (NB + NT - 1) / NT;
+        for (int q = 0; q < KB; ++q) {
+          const int g = tid * KB + q;
+          if (g >= NB) break;
+          const unsigned C = CM[g], Eb = EB[g];
           const unsigned cin = g > 0 ? (CM[g - 1] >> 31) : 0u;
-          const unsigned valid = (g == NB - 1 && (W & 31)) ? ((1u << (W & 31)) - 1u) : FULL;
           unsigned S = C & ~((C << 1) | cin);
-          const unsigned Eb = ~C & ((C << 1) | cin) & valid;
-          unsigned k = TPRE[g];
+          unsigned k = PRE[g] & 0xFFFFu;
           while (S) {
             const int b = __ffs(S) - 1;
             S &= S - 1u;
             const int p = g * 32 + b;
+            // previous run end (or 0) and this run's end (or W)
+            int pe = 0, ne = W;
             const unsigned below = Eb & ((1u << b) - 1u), above = Eb & ~((2u << b) - 1u);
-            const int pe = below ? g * 32 + 31 - __clz(below) : (int)PREVE[g];
-            const int ne = above ? g * 32 + __ffs(above) - 1 : (int)NEXTE[g];
-            tok[k++] = (unsigned)(p - pe) | ((unsigned)(ne - p) << 16);
+            if (below) {
+              pe = g * 32 + 31 - __clz(below);
+            } else {
+              for (int h = g - 1; h >= 0; --h)
+                if (EB[h]) {
+                  pe = h * 32 + 31 - __clz(EB[h]);
+                  break;
+                }
+            }
+            if (above) {
+              ne = g * 32 + __ffs(above) - 1;
+            } else {
+              for (int h = g + 1; h < NB; ++h)
+                if (EB[h]) {
+                  ne = h * 32 + __ffs(EB[h]) - 1;
+                  break;
+                }
+            }
+            tok[k] = (unsigned)(p - pe) | ((unsigned)(ne - p) << 16);
+            if (k + 1 == ns_tot && !lastc) tok[k + 1] = (unsigned)(W - ne);  // trailing literals
+            ++k;
           }
         }
-        if (tid == 0 && !s_lastc) tok[s_ns] = (unsigned)(W - s_laste);
+        if (tid == 0 && ns_tot == 0) tok[0] = (unsigned)W;  // no run at all
         for (int w = tid; w < W; w += NT) {
           const int g = w >> 5, b = w & 31;
           const unsigned C = CM[g];
-          if (!((C >> b) & 1u)) lit[(unsigned)w - (CPRE[g] + __popc(C & ((1u << b) - 1u)))] = P32[w];
+          if (!((C >> b) & 1u)) lit[(unsigned)w - ((PRE[g] >> 16) + __popc(C & ((1u << b) - 1u)))] = P32[w];
         }
       } else {
         for (int w = tid; w < W; w += NT) ch[2 + w] = P32[w];
       }
     }
     __syncthreads();
+    if (tid == 0 && ok) s_aoff = so + ((size + 15) & ~15ull);
   }
 }
 

@@ -56,9 +56,9 @@ struct FwdArgs {
   unsigned long long *out_bytes;  // may be null
   void *ws;
   unsigned char *scratch;  // per-CTA overflow payload space (may be null)
-  unsigned char *staging;  // finished chunks, in completion order
+  unsigned char *staging;     // finished chunks, one arena per CTA
   unsigned long long *table;  // per block: staging offset, chunk bytes
-  unsigned long long out_cap, data0, scratch_per_cta, staging_cap;
+  unsigned long long out_cap, data0, scratch_per_cta, arena_bytes;
   double eps, range;
   int nx, ny, nz, nbx, nby, nbz, nblocks;
   int eps_mode, stage2, kind, dtype;
@@ -123,11 +123,8 @@ __device__ __forceinline__ double2 sub2(double2 a, double2 b)
   return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y));
 }
 
-// magnitude bits for the significance compare
-__device__ __forceinline__ unsigned long long magbits(float v)
-{
-  return __float_as_uint(v) & 0x7fffffffu;
-}
+// magnitude bits for the significance compare (32-bit for float)
+__device__ __forceinline__ unsigned magbits(float v) { return __float_as_uint(v) & 0x7fffffffu; }
 __device__ __forceinline__ unsigned long long magbits(double v)
 {
   return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
@@ -135,10 +132,31 @@ __device__ __forceinline__ unsigned long long magbits(double v)
 // keep iff !(|d| < t): for t >= 0 (or +inf) this is magbits(d) >= magbits(t);
 // a NaN threshold keeps everything
 template <typename T>
-__device__ __forceinline__ unsigned long long thr_bits(T t)
+__device__ __forceinline__ auto thr_bits(T t) -> decltype(magbits(t))
 {
-  return (t != t) ? 0ull : magbits(t);
+  return (t != t) ? decltype(magbits(t))(0) : magbits(t);
 }
+
+// v[z] for a run-time z without indexing the register array dynamically
+#define CZ_PICK_CASE(q) \
+  case q:               \
+    if constexpr (q < B) return v[q]; \
+    break;
+template <int B, typename T2>
+__device__ __forceinline__ T2 pick(const T2 (&v)[B], int z)
+{
+  switch (z) {
+    CZ_PICK_CASE(0) CZ_PICK_CASE(1) CZ_PICK_CASE(2) CZ_PICK_CASE(3) CZ_PICK_CASE(4) CZ_PICK_CASE(5)
+    CZ_PICK_CASE(6) CZ_PICK_CASE(7) CZ_PICK_CASE(8) CZ_PICK_CASE(9) CZ_PICK_CASE(10) CZ_PICK_CASE(11)
+    CZ_PICK_CASE(12) CZ_PICK_CASE(13) CZ_PICK_CASE(14) CZ_PICK_CASE(15) CZ_PICK_CASE(16) CZ_PICK_CASE(17)
+    CZ_PICK_CASE(18) CZ_PICK_CASE(19) CZ_PICK_CASE(20) CZ_PICK_CASE(21) CZ_PICK_CASE(22) CZ_PICK_CASE(23)
+    CZ_PICK_CASE(24) CZ_PICK_CASE(25) CZ_PICK_CASE(26) CZ_PICK_CASE(27) CZ_PICK_CASE(28) CZ_PICK_CASE(29)
+    CZ_PICK_CASE(30) CZ_PICK_CASE(31)
+    default: break;
+  }
+  return v[0];
+}
+#undef CZ_PICK_CASE
 
 // ------------------------------------------------------------ geometry
 template <typename T, int B>
