@@ -54,15 +54,16 @@ int check(const cz_params *p, Shape *sh)
 }
 
 struct Lanes {
-  cudaError_t (*compress)(int, const CUtensorMap *, const FwdArgs *, const PlaceArgs *, int, cudaStream_t);
+  cudaError_t (*compress)(int, const CUtensorMap *, const FwdArgs *, const S2Args *, const PlaceArgs *, int, int,
+                          int, cudaStream_t);
   cudaError_t (*decompress)(int, const InvArgs *, int, cudaStream_t);
   cudaError_t (*dense)(int, int, const DenseArgs *, int, cudaStream_t);
   int (*occupancy)(int, int);
-  int (*scratch)(int);
+  int (*slot_bytes)();
 };
 
 #define CZ_LANES(sfx) \
-  Lanes { czl_compress_##sfx, czl_decompress_##sfx, czl_dense_##sfx, czl_occupancy_##sfx, czl_scratch_##sfx }
+  Lanes { czl_compress_##sfx, czl_decompress_##sfx, czl_dense_##sfx, czl_occupancy_##sfx, czl_slot_bytes_##sfx }
 
 Lanes lanes_for(int dtype, int B)
 {
@@ -93,30 +94,29 @@ int grid_for(const cz_params *p, const Shape &sh, int which)
 }
 
 // workspace: header | one u64 look-back word per block | block table
-// (staging offset, chunk bytes) | overflow scratch per compress CTA |
-// chunk staging (room for the largest chunk of every block)
+// (slot offset, chunk bytes) | staging (one arena per stage CTA, room for
+// the largest slot of each of its blocks)
 size_t lb_bytes(const Shape &sh) { return (8ull * sh.nblocks + 255) / 256 * 256; }
 size_t table_bytes(const Shape &sh) { return (16ull * sh.nblocks + 255) / 256 * 256; }
 
 struct WsLayout {
-  size_t lb, table, scratch, staging, total;
-  size_t scratch_per_cta, arena;
+  size_t lb, table, staging, total, arena;
+  int grid, grid2, grid3;
 };
 
 WsLayout ws_layout(const cz_params *p, const Shape &sh)
 {
   const Lanes L = lanes_for(p->dtype, p->block);
   WsLayout w;
-  w.scratch_per_cta = (size_t)L.scratch(0);
+  w.grid = grid_for(p, sh, 0);
+  w.grid2 = grid_for(p, sh, 2);
+  w.grid3 = grid_for(p, sh, 3);
   w.lb = WS_HDR;
   w.table = w.lb + lb_bytes(sh);
-  w.scratch = w.table + table_bytes(sh);
-  w.staging = w.scratch + (w.scratch_per_cta ? w.scratch_per_cta * (size_t)grid_for(p, sh, 0) : 0);
-  // one staging arena per compress CTA, room for the largest chunk of each
-  // of its blocks (blocks are dealt round robin)
-  const size_t grid = (size_t)grid_for(p, sh, 0);
-  w.arena = (((size_t)sh.nblocks + grid - 1) / grid) * (size_t)L.scratch(1);
-  w.total = w.staging + w.arena * grid;
+  w.staging = w.table + table_bytes(sh);
+  // blocks are dealt round robin to the stage CTAs
+  w.arena = (((size_t)sh.nblocks + w.grid - 1) / w.grid) * (size_t)L.slot_bytes();
+  w.total = w.staging + w.arena * (size_t)w.grid;
   return w;
 }
 
@@ -223,16 +223,10 @@ int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out
   const Lanes L = lanes_for(p->dtype, p->block);
   FwdArgs a{};
   a.field = d_field;
-  a.out = reinterpret_cast<unsigned char *>(d_out);
-  a.out_bytes = reinterpret_cast<unsigned long long *>(d_out_bytes);
   a.ws = d_ws;
-  a.scratch_per_cta = wl.scratch_per_cta;
-  a.scratch = wl.scratch_per_cta ? wsb + wl.scratch : nullptr;
   a.staging = wsb + wl.staging;
   a.arena_bytes = wl.arena;
   a.table = reinterpret_cast<unsigned long long *>(wsb + wl.table);
-  a.out_cap = out_cap;
-  a.data0 = sh.data0;
   a.eps = p->eps;
   a.range = p->range;
   a.nx = p->nx;
@@ -246,11 +240,15 @@ int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out
   a.stage2 = p->stage2;
   a.kind = p->kind;
   a.dtype = p->dtype;
+  S2Args sa{};
+  sa.staging = a.staging;
+  sa.table = a.table;
+  sa.nblocks = sh.nblocks;
   PlaceArgs pa{};
   pa.staging = a.staging;
   pa.table = a.table;
-  pa.out = a.out;
-  pa.out_bytes = a.out_bytes;
+  pa.out = reinterpret_cast<unsigned char *>(d_out);
+  pa.out_bytes = reinterpret_cast<unsigned long long *>(d_out_bytes);
   pa.ws = d_ws;
   pa.out_cap = out_cap;
   pa.data0 = sh.data0;
@@ -268,7 +266,7 @@ int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out
   pa.dtype = p->dtype;
   CUtensorMap tm;
   if (!make_tile_map(&tm, p, d_field)) return CZ_ERR_CUDA;
-  return L.compress(p->kind, &tm, &a, &pa, grid_for(p, sh, 0), s) == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
+  return L.compress(p->kind, &tm, &a, &sa, &pa, wl.grid, wl.grid2, wl.grid3, s) == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
 }
 
 int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used)

@@ -37,14 +37,33 @@ cudaError_t prepare(int smem)
 }
 
 template <int KIND>
-cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const PlaceArgs &pa, int grid, cudaStream_t s)
+cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const S2Args &sa, const PlaceArgs &pa, int grid,
+                       int grid2, int grid3, cudaStream_t s)
 {
   cudaError_t e = prepare<k_stage1<CZ_T, CZ_B, KIND>>(G::SMEM_C);
   if (e != cudaSuccess) return e;
   k_stage1<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_C, s>>>(tm, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_place<CZ_T><<<a.nblocks, 128, 0, s>>>(pa);
+  if (pa.stage2) {
+    e = prepare<k_stage2<CZ_T, CZ_B, false>>(G::SMEM_S2);
+    if (e != cudaSuccess) return e;
+    k_stage2<CZ_T, CZ_B, false><<<grid2, 128, G::SMEM_S2, s>>>(sa);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if constexpr (G::HAS_BIG) {
+      e = prepare<k_stage2<CZ_T, CZ_B, true>>(G::SMEM_S2B);
+      if (e != cudaSuccess) return e;
+      k_stage2<CZ_T, CZ_B, true><<<grid3, 512, G::SMEM_S2B, s>>>(sa);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  const int tiles = (pa.nblocks + PLACE_TILE - 1) / PLACE_TILE;
+  k_place<CZ_T><<<tiles, PLACE_TILE, 0, s>>>(pa);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_copy<CZ_T><<<(pa.nblocks + 7) / 8, 256, 0, s>>>(pa);
   return cudaGetLastError();
 }
 
@@ -60,9 +79,9 @@ cudaError_t decompress_k(const InvArgs &a, int grid, cudaStream_t s)
 template <int KIND, bool FWD>
 cudaError_t dense_k(const DenseArgs &a, int nblocks, cudaStream_t s)
 {
-  cudaError_t e = prepare<k_dense2<CZ_T, CZ_B, KIND, FWD>>(G::XB + G::ADB);
+  cudaError_t e = prepare<k_dense2<CZ_T, CZ_B, KIND, FWD>>(G::SMEM_DN0);
   if (e != cudaSuccess) return e;
-  k_dense2<CZ_T, CZ_B, KIND, FWD><<<nblocks, G::NT, G::XB + G::ADB, s>>>(a);
+  k_dense2<CZ_T, CZ_B, KIND, FWD><<<nblocks, G::NT, G::SMEM_DN0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -72,6 +91,18 @@ int occupancy_c()
   if (prepare<k_stage1<CZ_T, CZ_B, KIND>>(G::SMEM_C) != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage1<CZ_T, CZ_B, KIND>, G::NT, G::SMEM_C) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
+template <bool BIG>
+int occupancy_s2()
+{
+  constexpr int sm = BIG ? G::SMEM_S2B : G::SMEM_S2;
+  if (prepare<k_stage2<CZ_T, CZ_B, BIG>>(sm) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage2<CZ_T, CZ_B, BIG>, BIG ? 512 : 128, sm) !=
       cudaSuccess)
     return 0;
   return n;
@@ -95,12 +126,13 @@ int occupancy_d()
 #define CZ_SUFFIX CZ_CAT(CZ_CAT(CZ_TNAME, _b), CZ_B)
 
 extern "C" cudaError_t CZ_CAT(czl_compress_, CZ_SUFFIX)(int kind, const CUtensorMap *tm, const FwdArgs *a,
-                                                         const PlaceArgs *pa, int grid, cudaStream_t s)
+                                                         const S2Args *sa, const PlaceArgs *pa, int grid,
+                                                         int grid2, int grid3, cudaStream_t s)
 {
   switch (kind) {
-    case W4: return compress_k<W4>(*tm, *a, *pa, grid, s);
-    case W4LI: return compress_k<W4LI>(*tm, *a, *pa, grid, s);
-    default: return compress_k<W3AI>(*tm, *a, *pa, grid, s);
+    case W4: return compress_k<W4>(*tm, *a, *sa, *pa, grid, grid2, grid3, s);
+    case W4LI: return compress_k<W4LI>(*tm, *a, *sa, *pa, grid, grid2, grid3, s);
+    default: return compress_k<W3AI>(*tm, *a, *sa, *pa, grid, grid2, grid3, s);
   }
 }
 
@@ -130,9 +162,12 @@ extern "C" cudaError_t CZ_CAT(czl_dense_, CZ_SUFFIX)(int kind, int fwd, const De
   }
 }
 
-// CTAs per SM of the compress (which = 0) or decompress (which = 1) kernel
+// CTAs per SM of the stage kernel (which = 0), the decompress kernel
+// (which = 1), the small (which = 2) or the large (which = 3) stage-2 kernel
 extern "C" int CZ_CAT(czl_occupancy_, CZ_SUFFIX)(int kind, int which)
 {
+  if (which == 2) return occupancy_s2<false>();
+  if (which == 3) return G::HAS_BIG ? occupancy_s2<true>() : 1;
   if (which == 0) {
     switch (kind) {
       case W4: return occupancy_c<W4>();
@@ -147,6 +182,5 @@ extern "C" int CZ_CAT(czl_occupancy_, CZ_SUFFIX)(int kind, int which)
   }
 }
 
-// overflow scratch bytes per persistent compress CTA (which = 0) and the
-// largest chunk (which = 1)
-extern "C" int CZ_CAT(czl_scratch_, CZ_SUFFIX)(int which) { return which == 0 ? G::SCR : G::CHMAX; }
+// bytes of the staging slot of the largest payload
+extern "C" int CZ_CAT(czl_slot_bytes_, CZ_SUFFIX)() { return G::PSLOT; }

@@ -7,18 +7,20 @@ namespace czp {
 struct FwdArgs;
 struct InvArgs;
 struct DenseArgs;
+struct S2Args;
 struct PlaceArgs;
 }  // namespace czp
 
 #define CZ_DECLARE_LAUNCHERS(sfx)                                                                    \
   extern "C" cudaError_t czl_compress_##sfx(int kind, const CUtensorMap *tm, const czp::FwdArgs *a, \
-                                            const czp::PlaceArgs *pa, int grid, cudaStream_t s);    \
+                                            const czp::S2Args *sa, const czp::PlaceArgs *pa,        \
+                                            int grid, int grid2, int grid3, cudaStream_t s);        \
   extern "C" cudaError_t czl_decompress_##sfx(int kind, const czp::InvArgs *a, int grid,           \
                                               cudaStream_t s);                                      \
   extern "C" cudaError_t czl_dense_##sfx(int kind, int fwd, const czp::DenseArgs *a, int nblocks,   \
                                          cudaStream_t s);                                           \
   extern "C" int czl_occupancy_##sfx(int kind, int which);                                         \
-  extern "C" int czl_scratch_##sfx(int which);
+  extern "C" int czl_slot_bytes_##sfx();
 
 CZ_DECLARE_LAUNCHERS(f32_b8)
 CZ_DECLARE_LAUNCHERS(f32_b16)

@@ -52,13 +52,10 @@ struct WsHdr {
 
 struct FwdArgs {
   const void *field;
-  unsigned char *out;
-  unsigned long long *out_bytes;  // may be null
   void *ws;
-  unsigned char *scratch;  // per-CTA overflow payload space (may be null)
-  unsigned char *staging;     // finished chunks, one arena per CTA
-  unsigned long long *table;  // per block: staging offset, chunk bytes
-  unsigned long long out_cap, data0, scratch_per_cta, arena_bytes;
+  unsigned char *staging;     // raw payloads, one arena per CTA
+  unsigned long long *table;  // per block: staging offset, nnz
+  unsigned long long arena_bytes;
   double eps, range;
   int nx, ny, nz, nbx, nby, nbz, nblocks;
   int eps_mode, stage2, kind, dtype;
@@ -175,32 +172,40 @@ struct G2 {
   static constexpr int WMAX = PMAX / 4;
   static constexpr int NBWMAX = (WMAX + 31) / 32;
   static constexpr int TILE = NVOX * ES;
-  static constexpr int ZB = (B == 32) ? 4 : (B == 16 ? (ES == 4 ? 16 : 4) : 8);
-  static constexpr int XB = ZB * B * B * ES;
-  static constexpr int ADB = ZB * (B / 2) * B * ES;
+  // y-exchange planes per batch: forward kernels use the shared memory the
+  // payload no longer needs, the inverse kernel keeps room for the payload
+  static constexpr int ZBF = B == 32 ? (ES == 4 ? 16 : 4) : B;
+  static constexpr int ZBI = B == 32 ? 4 : (B == 16 ? (ES == 4 ? 16 : 4) : 8);
+  static constexpr int XBF = ZBF * B * B * ES, ADBF = ZBF * (B / 2) * B * ES;
+  static constexpr int XBI = ZBI * B * B * ES, ADBI = ZBI * (B / 2) * B * ES;
   static constexpr int ROWB = B * B * 4;
-  static constexpr int NAUX = 6;  // stage-2 arrays per zero-bitmap word
-  static constexpr int BUDGET = 227 * 1024 - 2048;
   static constexpr int PMAX_AL = (PMAX + 127) / 128 * 128;
-  // compress: tile | planes / aux | payload (capacity PCAP)
-  static constexpr int PCAP0 = (BUDGET - TILE - XB - ADB) / 128 * 128;
-  static constexpr int PCAP = PCAP0 < PMAX_AL ? PCAP0 : PMAX_AL;
-  static constexpr int NBWC = (PCAP / 4 + 31) / 32;
-  static constexpr int AUXC = ROWB + MASKB + NAUX * NBWC * 4;
-  static constexpr int R2C0 = (XB + ADB) > AUXC ? (XB + ADB) : AUXC;
+  // stage kernel: tile | planes, later row offsets and mask rows
+  static constexpr int R2C0 = (XBF + ADBF) > (ROWB + MASKB) ? (XBF + ADBF) : (ROWB + MASKB);
   static constexpr int R2C = (R2C0 + 127) / 128 * 128;
-  static constexpr int SMEM_C = TILE + R2C + PCAP;
-  // overflow scratch per compress CTA: payload + stage-2 arrays
-  static constexpr int SCR = PCAP < PMAX ? ((PMAX_AL + NAUX * NBWMAX * 4 + 255) / 256 * 256) : 0;
-  // largest chunk: raw 8 + PMAX, or 8 + 4 (tokens + literals) <= 12 + PMAX
-  static constexpr int CHMAX = (16 + PMAX + 15) / 16 * 16;
+  static constexpr int SMEM_C = TILE + R2C;
+  // staging slot of one block: [nnz | 0 | raw payload]; the finished
+  // stage-2 chunk replaces it in place and is at most 12 bytes longer than
+  // the payload (every coded run of >= 2 zero words saves at least one
+  // word; one trailing token), so a slot holds payload + 12 bytes
+  static constexpr int PSLOT = (PMAX + 12 + 15) / 16 * 16;
+  // stage-2 kernels: the shuffled payload lives in shared memory; payloads
+  // of up to SHCAP bytes go to small CTAs, larger ones to large CTAs
+  static constexpr int SHCAP = PMAX_AL < 16384 ? PMAX_AL : 16384;
+  static constexpr int NBS = (SHCAP / 4 + 31) / 32;
+  static constexpr int SMEM_S2 = SHCAP + 4 * NBS * 4;
+  static constexpr bool HAS_BIG = SHCAP < PMAX;
+  static constexpr int SMEM_S2B = PMAX_AL + 4 * NBWMAX * 4;
+  // dense kernels
+  static constexpr int SMEM_DN0 = (XBF + ADBF) > (XBI + ADBI) ? (XBF + ADBF) : (XBI + ADBI);
   // decompress: no tile; the whole payload always fits
   static constexpr int AUXD = ROWB + 2 * NT * 4;
-  static constexpr int R2D0 = (XB + ADB) > AUXD ? (XB + ADB) : AUXD;
+  static constexpr int R2D0 = (XBI + ADBI) > AUXD ? (XBI + ADBI) : AUXD;
   static constexpr int R2D = (R2D0 + 127) / 128 * 128;
   static constexpr int SMEM_D = R2D + PMAX_AL;
-  static_assert(SMEM_C <= 227 * 1024 - 1024, "compress shared memory");
+  static_assert(SMEM_C <= 227 * 1024 - 1024, "stage kernel shared memory");
   static_assert(SMEM_D <= 227 * 1024 - 1024, "decompress shared memory");
+  static_assert(SMEM_S2B <= 227 * 1024 - 1024, "stage-2 shared memory");
   static_assert(WMAX < 65536, "zero-RLE tokens hold run lengths below 65536 words");
 };
 
@@ -559,7 +564,7 @@ template <typename T, int B, int KIND, typename T2>
 __device__ __forceinline__ void fwd_level0(T2 (&v)[B], T *X, T *AD, int a, int y, int seg)
 {
   using G = G2<T, B>;
-  constexpr int m = B / 2, ZB = G::ZB;
+  constexpr int m = B / 2, ZB = G::ZBF;
   const bool odd = y & 1;
   // ---- x
   {
@@ -631,7 +636,7 @@ template <typename T, int B, int KIND, typename T2>
 __device__ __forceinline__ void inv_level0(T2 (&v)[B], T *X, T *AD, int a, int y, int seg)
 {
   using G = G2<T, B>;
-  constexpr int m = B / 2, ZB = G::ZB;
+  constexpr int m = B / 2, ZB = G::ZBI;
   const bool odd = y & 1;
   // ---- z
   z0_inv<T, KIND, B>(v);
@@ -704,7 +709,7 @@ template <typename T, int B, int KIND, int LEV, typename T2>
 __device__ __forceinline__ void fwd_levelE(T2 (&v)[B], T *X, int a, int y, int seg)
 {
   using G = G2<T, B>;
-  constexpr int S = 1 << LEV, n = B >> LEV, m = n / 2, ZB = G::ZB, NZ = B / S;
+  constexpr int S = 1 << LEV, n = B >> LEV, m = n / 2, ZB = G::ZBF, NZ = B / S;
   constexpr int LS = S / 2;  // lane stride of active pairs
   const bool xact = (a & (LS - 1)) == 0, yact = (y & (S - 1)) == 0;
   // x: lanes a = i * LS
@@ -782,7 +787,7 @@ template <typename T, int B, int KIND, int LEV, typename T2>
 __device__ __forceinline__ void inv_levelE(T2 (&v)[B], T *X, int a, int y, int seg)
 {
   using G = G2<T, B>;
-  constexpr int S = 1 << LEV, n = B >> LEV, m = n / 2, ZB = G::ZB, NZ = B / S;
+  constexpr int S = 1 << LEV, n = B >> LEV, m = n / 2, ZB = G::ZBI, NZ = B / S;
   constexpr int LS = S / 2;
   const bool xact = (a & (LS - 1)) == 0, yact = (y & (S - 1)) == 0;
   if (xact && yact) {
@@ -987,7 +992,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
   unsigned char *R2 = smem;
   unsigned char *P = smem + G::R2D;
   T *X = reinterpret_cast<T *>(R2);
-  T *AD = reinterpret_cast<T *>(R2 + G::XB);
+  T *AD = reinterpret_cast<T *>(R2 + G::XBI);
   unsigned *ROWOFF = reinterpret_cast<unsigned *>(R2);
   unsigned *TL = ROWOFF + B * B;
   unsigned *TO = TL + NT;
@@ -1155,7 +1160,7 @@ __global__ void __launch_bounds__(B * B / 2) k_dense2(const DenseArgs a)
   using T2 = typename V2T<T>::type;
   extern __shared__ __align__(128) unsigned char smem[];
   T *X = reinterpret_cast<T *>(smem);
-  T *AD = reinterpret_cast<T *>(smem + G::XB);
+  T *AD = reinterpret_cast<T *>(smem + (FWD ? G::XBF : G::XBI));
   const int tid = threadIdx.x, lane = tid & 31;
   const int ap = tid % G::HP, r = tid / G::HP;
   const int y = r < B / 2 ? 2 * r : 2 * (r - B / 2) + 1;
