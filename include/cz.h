@@ -105,6 +105,33 @@ int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header,
                   void *d_field, size_t field_cap, void *d_ws, size_t ws_bytes,
                   void *stream);
 
+/* Size of the workspace that cz_compress_noalloc uses: 64 MiB. */
+#define CZ_NOALLOC_WS_BYTES (64u << 20)
+
+/* cz_compress for callers that cannot allocate device memory.  The paper
+ * has no counterpart; this entry point exists for the in-situ use the paper
+ * describes, where a solver that has committed the device's memory
+ * compresses its fields between time steps.  Such callers cannot make
+ * cudaMalloc/cudaFree calls there: the memory may not be free, the calls
+ * can synchronise the device, and caching allocators (PyTorch's included)
+ * may hold what is free.  Instead of a caller-supplied d_ws this call uses
+ * a CZ_NOALLOC_WS_BYTES array that the library owns in device memory, so
+ * it works only for fields whose cz_workspace_size() is at most
+ * CZ_NOALLOC_WS_BYTES (e.g. 64 blocks of 32^3 FP32, a 128^3 field); larger
+ * fields return CZ_ERR_CAPACITY before anything is enqueued.
+ *  - The first call on a device looks up the array's address with that
+ *    device current (the CUDA runtime loads the library's module then).
+ *    Make that first call before any stream capture begins.
+ *  - There is one array per device: calls whose work may overlap on the
+ *    device (different streams, or different host threads) race on it and
+ *    corrupt each other's output.  Calls enqueued on one stream run one
+ *    after the other and are safe.
+ *  - Device-side status is not reported; a stream length in *d_out_bytes
+ *    above out_cap means the output did not fit.
+ * Other arguments and host-side errors are those of cz_compress. */
+int cz_compress_noalloc(const cz_params *p, const void *d_field, void *d_out,
+                        size_t out_cap, uint64_t *d_out_bytes, void *stream);
+
 /* Parse a host copy of a stream header into *p (and the threshold used). */
 int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used);
 

@@ -57,9 +57,10 @@ def _jobs(verbose_ptxas: bool):
         cmd = [nvcc(), *ARCH, *NVFLAGS, *extra, f"-DCZ_T={ctype}", f"-DCZ_TNAME={tname}",
                f"-DCZ_B={b}", "-c", os.path.join(CSRC, "cz_inst.cu"), "-o", obj]
         jobs.append((obj, cmd))
-    obj = os.path.join(BUILD_DIR, "cz_api.o")
-    jobs.append((obj, [nvcc(), *ARCH, *NVFLAGS, *extra, "-c", os.path.join(CSRC, "cz_api.cu"),
-                       "-o", obj]))
+    for name in ("cz_api", "cz_noalloc"):
+        obj = os.path.join(BUILD_DIR, f"{name}.o")
+        jobs.append((obj, [nvcc(), *ARCH, *NVFLAGS, *extra, "-c", os.path.join(CSRC, f"{name}.cu"),
+                           "-o", obj]))
     return jobs
 
 

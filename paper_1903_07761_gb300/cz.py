@@ -21,6 +21,7 @@ F32, F64 = 0, 1
 EPS_REL, EPS_ABS = 0, 1
 OK, ERR_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_TIMEOUT, ERR_CUDA, ERR_BUDGET = 0, -1, -2, -3, -4, -5, -6
 HEADER_BYTES = 128
+NOALLOC_WS_BYTES = 64 << 20  # CZ_NOALLOC_WS_BYTES
 KINDS = {"w4": W4, "w4li": W4LI, "w3ai": W3AI}
 
 
@@ -56,6 +57,7 @@ def lib():
             L.cz_workspace_size.argtypes = [PP, C.POINTER(C.c_size_t)]
             L.cz_compress.argtypes = [PP, P, P, C.c_size_t, P, P, C.c_size_t, P]
             L.cz_decompress.argtypes = [P, C.c_size_t, P, P, C.c_size_t, P, C.c_size_t, P]
+            L.cz_compress_noalloc.argtypes = [PP, P, P, C.c_size_t, P, P]
             L.cz_read_header.argtypes = [P, C.c_size_t, PP, C.POINTER(C.c_double)]
             L.cz_status.argtypes = [P, P]
             L.cz_strerror.argtypes = [C.c_int]
@@ -63,7 +65,7 @@ def lib():
             L.cz_forward_dense.argtypes = [PP, P, P, P]
             L.cz_inverse_dense.argtypes = [PP, P, P, P]
             for f in (L.cz_compress_bound, L.cz_workspace_size, L.cz_compress, L.cz_decompress,
-                      L.cz_read_header, L.cz_status, L.cz_forward_dense, L.cz_inverse_dense):
+                      L.cz_compress_noalloc, L.cz_read_header, L.cz_status, L.cz_forward_dense, L.cz_inverse_dense):
                 f.restype = C.c_int
             _lib = L
     return _lib
@@ -90,6 +92,13 @@ def cz_compress(p: Params, d_field: int, d_out: int, out_cap: int, d_out_bytes: 
                 d_ws: int, ws_bytes: int, stream: int) -> int:
     return lib().cz_compress(C.byref(p), d_field, d_out, out_cap, d_out_bytes or None,
                              d_ws, ws_bytes, stream or None)
+
+
+def cz_compress_noalloc(p: Params, d_field: int, d_out: int, out_cap: int, d_out_bytes: int,
+                        stream: int) -> int:
+    """cz_compress with the library's own fixed workspace (no allocation)."""
+    return lib().cz_compress_noalloc(C.byref(p), d_field, d_out, out_cap, d_out_bytes or None,
+                                     stream or None)
 
 
 def cz_decompress(d_in: int, in_bytes: int, h_header, d_field: int, field_cap: int,
