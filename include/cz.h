@@ -78,14 +78,19 @@ typedef struct cz_params {
 /* Worst-case stream size for p.  Returns CZ_OK or CZ_ERR_ARG. */
 int cz_compress_bound(const cz_params *p, size_t *bytes);
 
-/* Device workspace needed by cz_compress / cz_decompress for p:
- * a status word, the min/max keys and one u64 look-back word per block. */
+/* Device workspace needed by cz_compress / cz_decompress for p: a status
+ * word, the min/max keys, one u64 look-back word per block, a block table
+ * (16 bytes per block) and the staging slots the chunks are built in (room
+ * for the largest chunk of every block, about the size of the field).
+ * Needs the current device (it sizes the persistent grids by its SM count). */
 int cz_workspace_size(const cz_params *p, size_t *bytes);
 
 /* Compress d_field into d_out (capacity out_cap bytes).
- * Steps: optional min/max pass (range < 0 and eps_mode REL), then one fused
- * kernel per block: load, forward transform, threshold, mask + compaction,
- * optional stage 2, decoupled look-back for the chunk offset, write.
+ * Steps: optional min/max pass (range < 0 and eps_mode REL); a persistent
+ * kernel that loads each block with TMA, transforms it, thresholds it and
+ * writes mask + compacted values to a staging slot; optional stage 2 on
+ * every slot; chunk offsets by a decoupled look-back over tiles of chunks;
+ * a copy of the chunks into the stream.
  * *d_out_bytes (device u64, may be NULL) receives the stream length; if it
  * exceeds out_cap the status word is CZ_ERR_CAPACITY and the stream is
  * incomplete.  d_ws must hold cz_workspace_size() bytes; it is overwritten.

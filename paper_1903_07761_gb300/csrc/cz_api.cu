@@ -55,7 +55,7 @@ int check(const cz_params *p, Shape *sh)
 
 struct Lanes {
   cudaError_t (*compress)(int, const CUtensorMap *, const FwdArgs *, const S2Args *, const PlaceArgs *, int, int,
-                          int, cudaStream_t);
+                          int, const cudaEvent_t *, cudaStream_t);
   cudaError_t (*decompress)(int, const InvArgs *, int, cudaStream_t);
   cudaError_t (*dense)(int, int, const DenseArgs *, int, cudaStream_t);
   int (*occupancy)(int, int);
@@ -199,8 +199,11 @@ int cz_workspace_size(const cz_params *p, size_t *bytes)
   return CZ_OK;
 }
 
-int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out_cap,
-                uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes, void *stream)
+namespace {
+
+int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t out_cap,
+                  uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes, void *stream,
+                  const cudaEvent_t *marks)
 {
   Shape sh;
   int r = check(p, &sh);
@@ -266,7 +269,33 @@ int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out
   pa.dtype = p->dtype;
   CUtensorMap tm;
   if (!make_tile_map(&tm, p, d_field)) return CZ_ERR_CUDA;
-  return L.compress(p->kind, &tm, &a, &sa, &pa, wl.grid, wl.grid2, wl.grid3, s) == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
+  return L.compress(p->kind, &tm, &a, &sa, &pa, wl.grid, wl.grid2, wl.grid3, marks, s) == cudaSuccess
+             ? CZ_OK
+             : CZ_ERR_CUDA;
+}
+
+}  // namespace
+
+int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out_cap,
+                uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes, void *stream)
+{
+  return compress_impl(p, d_field, d_out, out_cap, d_out_bytes, d_ws, ws_bytes, stream, nullptr);
+}
+
+// Not part of the ABI: cz_compress with four CUDA events recorded on
+// `stream` around its kernels (before the stage kernel, after it, after
+// stage 2, after the chunk copy), for timing the kernels one by one.
+int czi_compress_marked(const cz_params *p, const void *d_field, void *d_out, size_t out_cap,
+                        uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes, void *stream,
+                        void *const *events)
+{
+  if (!events) return CZ_ERR_ARG;
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) {
+    if (!events[i]) return CZ_ERR_ARG;
+    ev[i] = reinterpret_cast<cudaEvent_t>(events[i]);
+  }
+  return compress_impl(p, d_field, d_out, out_cap, d_out_bytes, d_ws, ws_bytes, stream, ev);
 }
 
 int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used)

@@ -73,7 +73,6 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
   double mn, mx, range;
   T t;
   threshold_of<T>(a.eps, a.eps_mode, a.range, ws, mn, mx, range, t);
-  const auto tb = thr_bits(t);
   const bool cE = (x0 % Q == 0) && (y % Q == 0);  // this column pair holds coarse values (E)
   unsigned cmask = 0;
 #pragma unroll
@@ -115,8 +114,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     unsigned me = 0, mo = 0;
 #pragma unroll
     for (int z = 0; z < B; ++z) {
-      me |= (unsigned)(magbits(v[z].x) >= tb) << z;
-      mo |= (unsigned)(magbits(v[z].y) >= tb) << z;
+      me |= (unsigned)keep(v[z].x, t) << z;
+      mo |= (unsigned)keep(v[z].y, t) << z;
     }
     if (cE) me &= ~cmask;
     unsigned w0 = me, w1 = mo;
@@ -158,18 +157,19 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
 #pragma unroll
         for (int z = 0; z < B; z += Q) reinterpret_cast<T *>(P)[((z / Q) * 4 + y / Q) * 4 + x0 / Q] = v[z].x;
       }
-      // kept details of this column pair, z by z (work grows with the count)
+      // kept details of this column pair (z unrolled: v[z] stays a register)
       T *VALS = reinterpret_cast<T *>(P + 64 * ES + G::MASKB);
       const unsigned lowE = (1u << x0) - 1u, lowO = (2u << x0) - 1u;
-      unsigned bits = me | mo;
-      while (bits) {
-        const int z = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        const T2 val = pick<B>(v, z);
-        const unsigned wd = get_row<B>(MASKU, z, y);
-        const unsigned base = ROWOFF[z * B + y];
-        if ((me >> z) & 1u) VALS[base + __popc(wd & lowE)] = val.x;
-        if ((mo >> z) & 1u) VALS[base + __popc(wd & lowO)] = val.y;
+      if (me | mo) {
+#pragma unroll
+        for (int z = 0; z < B; ++z) {
+          if (((me | mo) >> z) & 1u) {
+            const unsigned wd = get_row<B>(MASKU, z, y);
+            const unsigned base = ROWOFF[z * B + y];
+            if ((me >> z) & 1u) VALS[base + __popc(wd & lowE)] = v[z].x;
+            if ((mo >> z) & 1u) VALS[base + __popc(wd & lowO)] = v[z].y;
+          }
+        }
       }
     }
     if (tid == 0) {

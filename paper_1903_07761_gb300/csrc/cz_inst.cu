@@ -38,13 +38,15 @@ cudaError_t prepare(int smem)
 
 template <int KIND>
 cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const S2Args &sa, const PlaceArgs &pa, int grid,
-                       int grid2, int grid3, cudaStream_t s)
+                       int grid2, int grid3, const cudaEvent_t *marks, cudaStream_t s)
 {
   cudaError_t e = prepare<k_stage1<CZ_T, CZ_B, KIND>>(G::SMEM_C);
   if (e != cudaSuccess) return e;
+  if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
   k_stage1<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_C, s>>>(tm, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (marks && (e = cudaEventRecord(marks[1], s)) != cudaSuccess) return e;
   if (pa.stage2) {
     e = prepare<k_stage2<CZ_T, CZ_B, false>>(G::SMEM_S2);
     if (e != cudaSuccess) return e;
@@ -59,11 +61,15 @@ cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const S2Args &sa
       if (e != cudaSuccess) return e;
     }
   }
+  if (marks && (e = cudaEventRecord(marks[2], s)) != cudaSuccess) return e;
   const int tiles = (pa.nblocks + PLACE_TILE - 1) / PLACE_TILE;
   k_place<CZ_T><<<tiles, PLACE_TILE, 0, s>>>(pa);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_copy<CZ_T><<<(pa.nblocks + 7) / 8, 256, 0, s>>>(pa);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (marks && (e = cudaEventRecord(marks[3], s)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -127,12 +133,13 @@ int occupancy_d()
 
 extern "C" cudaError_t CZ_CAT(czl_compress_, CZ_SUFFIX)(int kind, const CUtensorMap *tm, const FwdArgs *a,
                                                          const S2Args *sa, const PlaceArgs *pa, int grid,
-                                                         int grid2, int grid3, cudaStream_t s)
+                                                         int grid2, int grid3, const cudaEvent_t *marks,
+                                                         cudaStream_t s)
 {
   switch (kind) {
-    case W4: return compress_k<W4>(*tm, *a, *sa, *pa, grid, grid2, grid3, s);
-    case W4LI: return compress_k<W4LI>(*tm, *a, *sa, *pa, grid, grid2, grid3, s);
-    default: return compress_k<W3AI>(*tm, *a, *sa, *pa, grid, grid2, grid3, s);
+    case W4: return compress_k<W4>(*tm, *a, *sa, *pa, grid, grid2, grid3, marks, s);
+    case W4LI: return compress_k<W4LI>(*tm, *a, *sa, *pa, grid, grid2, grid3, marks, s);
+    default: return compress_k<W3AI>(*tm, *a, *sa, *pa, grid, grid2, grid3, marks, s);
   }
 }
 

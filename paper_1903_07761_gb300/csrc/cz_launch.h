@@ -14,7 +14,8 @@ struct PlaceArgs;
 #define CZ_DECLARE_LAUNCHERS(sfx)                                                                    \
   extern "C" cudaError_t czl_compress_##sfx(int kind, const CUtensorMap *tm, const czp::FwdArgs *a, \
                                             const czp::S2Args *sa, const czp::PlaceArgs *pa,        \
-                                            int grid, int grid2, int grid3, cudaStream_t s);        \
+                                            int grid, int grid2, int grid3,                         \
+                                            const cudaEvent_t *marks, cudaStream_t s);              \
   extern "C" cudaError_t czl_decompress_##sfx(int kind, const czp::InvArgs *a, int grid,           \
                                               cudaStream_t s);                                      \
   extern "C" cudaError_t czl_dense_##sfx(int kind, int fwd, const czp::DenseArgs *a, int nblocks,   \

@@ -120,40 +120,10 @@ __device__ __forceinline__ double2 sub2(double2 a, double2 b)
   return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y));
 }
 
-// magnitude bits for the significance compare (32-bit for float)
-__device__ __forceinline__ unsigned magbits(float v) { return __float_as_uint(v) & 0x7fffffffu; }
-__device__ __forceinline__ unsigned long long magbits(double v)
-{
-  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
-}
-// keep iff !(|d| < t): for t >= 0 (or +inf) this is magbits(d) >= magbits(t);
-// a NaN threshold keeps everything
-template <typename T>
-__device__ __forceinline__ auto thr_bits(T t) -> decltype(magbits(t))
-{
-  return (t != t) ? decltype(magbits(t))(0) : magbits(t);
-}
-
-// v[z] for a run-time z without indexing the register array dynamically
-#define CZ_PICK_CASE(q) \
-  case q:               \
-    if constexpr (q < B) return v[q]; \
-    break;
-template <int B, typename T2>
-__device__ __forceinline__ T2 pick(const T2 (&v)[B], int z)
-{
-  switch (z) {
-    CZ_PICK_CASE(0) CZ_PICK_CASE(1) CZ_PICK_CASE(2) CZ_PICK_CASE(3) CZ_PICK_CASE(4) CZ_PICK_CASE(5)
-    CZ_PICK_CASE(6) CZ_PICK_CASE(7) CZ_PICK_CASE(8) CZ_PICK_CASE(9) CZ_PICK_CASE(10) CZ_PICK_CASE(11)
-    CZ_PICK_CASE(12) CZ_PICK_CASE(13) CZ_PICK_CASE(14) CZ_PICK_CASE(15) CZ_PICK_CASE(16) CZ_PICK_CASE(17)
-    CZ_PICK_CASE(18) CZ_PICK_CASE(19) CZ_PICK_CASE(20) CZ_PICK_CASE(21) CZ_PICK_CASE(22) CZ_PICK_CASE(23)
-    CZ_PICK_CASE(24) CZ_PICK_CASE(25) CZ_PICK_CASE(26) CZ_PICK_CASE(27) CZ_PICK_CASE(28) CZ_PICK_CASE(29)
-    CZ_PICK_CASE(30) CZ_PICK_CASE(31)
-    default: break;
-  }
-  return v[0];
-}
-#undef CZ_PICK_CASE
+// significance: keep iff !(|d| < t) (ties kept; a NaN detail or a NaN
+// threshold keeps the value)
+__device__ __forceinline__ bool keep(float d, float t) { return !(fabsf(d) < t); }
+__device__ __forceinline__ bool keep(double d, double t) { return !(fabs(d) < t); }
 
 // ------------------------------------------------------------ geometry
 template <typename T, int B>
@@ -704,153 +674,103 @@ __device__ __forceinline__ void inv_level0(T2 (&v)[B], T *X, T *AD, int a, int y
   }
 }
 
-// coarser levels: E column, positions multiple of S = 2^LEV (LEV >= 1)
-template <typename T, int B, int KIND, int LEV, typename T2>
-__device__ __forceinline__ void fwd_levelE(T2 (&v)[B], T *X, int a, int y, int seg)
+// ============================================================ coarser levels
+// After level 0 the coarse values (all coordinates even) form an N^3 cube,
+// N = B/2, held by the threads of even rows in v[2j].x.  Levels 1.. are the
+// same transform on that cube, run in shared memory by all NT threads:
+// C(x, y, z) = C[(z N + y)(N + 1) + x] (rows padded by one element, so that
+// lines along x, taken y-fastest across threads, hit distinct banks).
+template <int N>
+__device__ __forceinline__ int cidx(int x, int y, int z)
 {
-  using G = G2<T, B>;
-  constexpr int S = 1 << LEV, n = B >> LEV, m = n / 2, ZB = G::ZBF, NZ = B / S;
-  constexpr int LS = S / 2;  // lane stride of active pairs
-  const bool xact = (a & (LS - 1)) == 0, yact = (y & (S - 1)) == 0;
-  // x: lanes a = i * LS
-  {
-    const Stencil<T> st = make_stencil<T, KIND>(a / LS, m);
-#pragma unroll
-    for (int z = 0; z < B; z += S) {
-      const T f = v[z].x;
-      auto g = [&](int idx) { return shfl(f, seg + idx * LS); };
-      T r;
-      if constexpr (KIND == W4) {
-        r = fwd_predict(st, f, g);
-      } else if constexpr (KIND == W4LI) {
-        const T f1 = fwd_predict(st, f, g);
-        r = fwd_update(st, f1, [&](int idx) { return shfl(f1, seg + idx * LS); });
-      } else {
-        r = fwd_ai(st, f, g, [&](int idx, T av) { return shfl(av, seg + idx * LS); });
-      }
-      if (xact && yact) v[z].x = r;
-    }
-  }
-  // y: shared planes of E values
-  {
-    const Stencil<T> st = make_stencil<T, KIND>(y / S, m);
-    const bool act = xact && yact;
-#pragma unroll
-    for (int zb = 0; zb < NZ; zb += ZB) {
-#pragma unroll
-      for (int q = 0; q < ZB; ++q)
-        if (zb + q < NZ && act) X[(q * B + y) * B + 2 * a] = v[(zb + q) * S].x;
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < ZB; ++q) {
-        if (zb + q < NZ && act) {
-          T *Xq = X + q * B * B + 2 * a;
-          auto g = [&](int idx) { return Xq[idx * S * B]; };
-          const T f = v[(zb + q) * S].x;
-          T r;
-          if constexpr (KIND == W4) {
-            r = fwd_predict(st, f, g);
-          } else if constexpr (KIND == W4LI) {
-            r = fwd_predict(st, f, g);
-            if (st.i & 1) Xq[y * B] = r;
-          } else {
-            r = fwd_ai(st, f, g, [&](int idx, T) { return mulx(addx(g(idx), g(idx + 1)), (T)0.5); });
-          }
-          v[(zb + q) * S].x = r;
-        }
-      }
-      if constexpr (KIND == W4LI) {
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < ZB; ++q) {
-          if (zb + q < NZ && act) {
-            T *Xq = X + q * B * B + 2 * a;
-            v[(zb + q) * S].x = fwd_update(st, v[(zb + q) * S].x, [&](int idx) { return Xq[idx * S * B]; });
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-  // z: registers
-  if (xact && yact) {
-    T e[B];
-#pragma unroll
-    for (int z = 0; z < B; ++z) e[z] = v[z].x;
-    fwd_reg<T, KIND, B, S>(e);
-#pragma unroll
-    for (int z = 0; z < B; z += S) v[z].x = e[z];
+  return (z * N + y) * (N + 1) + x;
+}
+
+// line `li` of pass AXIS at level stride S: base index and step along it
+// (consecutive lines start in distinct banks)
+template <int N, int S, int AXIS>
+__device__ __forceinline__ void cube_line(int li, int &base, int &step)
+{
+  constexpr int n = N / S;
+  const int f = li % n, g = li / n;  // fast, slow line coordinates (units of S)
+  if (AXIS == 0) {  // lines along x, y fastest
+    base = cidx<N>(0, f * S, g * S);
+    step = S;
+  } else if (AXIS == 1) {  // along y, x fastest
+    base = cidx<N>(f * S, 0, g * S);
+    step = S * (N + 1);
+  } else {  // along z, x fastest
+    base = cidx<N>(f * S, g * S, 0);
+    step = S * N * (N + 1);
   }
 }
 
-template <typename T, int B, int KIND, int LEV, typename T2>
-__device__ __forceinline__ void inv_levelE(T2 (&v)[B], T *X, int a, int y, int seg)
+// one axis of one level: a thread per line, the line in registers
+// (compile-time stencils), written back in place
+template <typename T, int N, int KIND, int NT, int S, int AXIS, bool FWD>
+__device__ __forceinline__ void cube_pass(T *C)
 {
-  using G = G2<T, B>;
-  constexpr int S = 1 << LEV, n = B >> LEV, m = n / 2, ZB = G::ZBI, NZ = B / S;
-  constexpr int LS = S / 2;
-  const bool xact = (a & (LS - 1)) == 0, yact = (y & (S - 1)) == 0;
-  if (xact && yact) {
-    T e[B];
+  constexpr int n = N / S, LINES = n * n;
+  static_assert(LINES <= NT, "one line per thread");
+  const int tid = threadIdx.x;
+  if (tid < LINES) {
+    int base, step;
+    cube_line<N, S, AXIS>(tid, base, step);
+    T e[n];
 #pragma unroll
-    for (int z = 0; z < B; ++z) e[z] = v[z].x;
-    inv_reg<T, KIND, B, S>(e);
+    for (int i = 0; i < n; ++i) e[i] = C[base + i * step];
+    if constexpr (FWD)
+      fwd_reg<T, KIND, n, 1>(e);
+    else
+      inv_reg<T, KIND, n, 1>(e);
 #pragma unroll
-    for (int z = 0; z < B; z += S) v[z].x = e[z];
+    for (int i = 0; i < n; ++i)
+      if (KIND != W4 || (i & 1)) C[base + i * step] = e[i];  // W4 changes only the odd points
   }
-  {
-    const Stencil<T> st = make_stencil<T, KIND>(y / S, m);
-    const bool act = xact && yact;
-#pragma unroll
-    for (int zb = 0; zb < NZ; zb += ZB) {
-#pragma unroll
-      for (int q = 0; q < ZB; ++q)
-        if (zb + q < NZ && act) X[(q * B + y) * B + 2 * a] = v[(zb + q) * S].x;
-      __syncthreads();
-      if constexpr (KIND == W4LI) {
-#pragma unroll
-        for (int q = 0; q < ZB; ++q) {
-          if (zb + q < NZ && act) {
-            T *Xq = X + q * B * B + 2 * a;
-            const T c = inv_update(st, v[(zb + q) * S].x, [&](int idx) { return Xq[idx * S * B]; });
-            if (!(st.i & 1)) Xq[y * B] = c;
-            v[(zb + q) * S].x = c;
-          }
-        }
-        __syncthreads();
-      }
-#pragma unroll
-      for (int q = 0; q < ZB; ++q) {
-        if (zb + q < NZ && act) {
-          T *Xq = X + q * B * B + 2 * a;
-          auto g = [&](int idx) { return Xq[idx * S * B]; };
-          const T f = v[(zb + q) * S].x;
-          if constexpr (KIND == W3AI)
-            v[(zb + q) * S].x = inv_ai(st, f, g);
-          else
-            v[(zb + q) * S].x = inv_predict(st, f, g);
-        }
-      }
-      __syncthreads();
-    }
+  __syncthreads();
+}
+
+// all levels of the N^3 cube down to 4^3 (x, y, z per level)
+template <typename T, int N, int KIND, int NT, int S = 1>
+__device__ __forceinline__ void cube_fwd(T *C)
+{
+  if constexpr (N / S >= 8) {
+    cube_pass<T, N, KIND, NT, S, 0, true>(C);
+    cube_pass<T, N, KIND, NT, S, 1, true>(C);
+    cube_pass<T, N, KIND, NT, S, 2, true>(C);
+    cube_fwd<T, N, KIND, NT, 2 * S>(C);
   }
-  {
-    const Stencil<T> st = make_stencil<T, KIND>(a / LS, m);
+}
+
+template <typename T, int N, int KIND, int NT, int S = 1>
+__device__ __forceinline__ void cube_inv(T *C)
+{
+  if constexpr (N / S >= 8) {
+    cube_inv<T, N, KIND, NT, 2 * S>(C);
+    cube_pass<T, N, KIND, NT, S, 2, false>(C);
+    cube_pass<T, N, KIND, NT, S, 1, false>(C);
+    cube_pass<T, N, KIND, NT, S, 0, false>(C);
+  }
+}
+
+// coarse values of level 0 <-> the cube (threads of even rows)
+template <typename T, int B, typename T2>
+__device__ __forceinline__ void to_cube(const T2 (&v)[B], T *C, int a, int y)
+{
+  constexpr int N = B / 2;
+  if (!(y & 1)) {
 #pragma unroll
-    for (int z = 0; z < B; z += S) {
-      const T f = v[z].x;
-      auto g = [&](int idx) { return shfl(f, seg + idx * LS); };
-      T r;
-      if constexpr (KIND == W4) {
-        r = inv_predict(st, f, g);
-      } else if constexpr (KIND == W4LI) {
-        const T f1 = inv_update(st, f, g);
-        r = inv_predict(st, f1, [&](int idx) { return shfl(f1, seg + idx * LS); });
-      } else {
-        r = inv_ai(st, f, g);
-      }
-      if (xact && yact) v[z].x = r;
-    }
+    for (int j = 0; j < N; ++j) C[cidx<N>(a, y >> 1, j)] = v[2 * j].x;
+  }
+}
+
+template <typename T, int B, typename T2>
+__device__ __forceinline__ void from_cube(T2 (&v)[B], const T *C, int a, int y)
+{
+  constexpr int N = B / 2;
+  if (!(y & 1)) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[2 * j].x = C[cidx<N>(a, y >> 1, j)];
   }
 }
 
@@ -858,15 +778,25 @@ template <typename T, int B, int KIND, typename T2>
 __device__ __forceinline__ void fwd_all(T2 (&v)[B], T *X, T *AD, int a, int y, int seg)
 {
   fwd_level0<T, B, KIND>(v, X, AD, a, y, seg);
-  if constexpr (G2<T, B>::L > 1) fwd_levelE<T, B, KIND, 1>(v, X, a, y, seg);
-  if constexpr (G2<T, B>::L > 2) fwd_levelE<T, B, KIND, 2>(v, X, a, y, seg);
+  if constexpr (G2<T, B>::L > 1) {
+    to_cube<T, B>(v, X, a, y);
+    __syncthreads();
+    cube_fwd<T, B / 2, KIND, G2<T, B>::NT>(X);
+    from_cube<T, B>(v, X, a, y);
+    __syncthreads();
+  }
 }
 
 template <typename T, int B, int KIND, typename T2>
 __device__ __forceinline__ void inv_all(T2 (&v)[B], T *X, T *AD, int a, int y, int seg)
 {
-  if constexpr (G2<T, B>::L > 2) inv_levelE<T, B, KIND, 2>(v, X, a, y, seg);
-  if constexpr (G2<T, B>::L > 1) inv_levelE<T, B, KIND, 1>(v, X, a, y, seg);
+  if constexpr (G2<T, B>::L > 1) {
+    to_cube<T, B>(v, X, a, y);
+    __syncthreads();
+    cube_inv<T, B / 2, KIND, G2<T, B>::NT>(X);
+    from_cube<T, B>(v, X, a, y);
+    __syncthreads();
+  }
   inv_level0<T, B, KIND>(v, X, AD, a, y, seg);
 }
 

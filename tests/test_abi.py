@@ -1,0 +1,111 @@
+"""The C ABI without a GPU: the library builds and loads, exports every
+function that include/cz.h declares, and its host-side logic (parameter
+checks, stream bound, header parsing, error texts) behaves as declared.
+No call here launches a kernel.
+"""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "cz.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const\s+char\s*\*)\s*(cz_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def cz():
+    from paper_1903_07761_gb300 import cz as mod
+    mod.lib()
+    return mod
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("cz_compress", "cz_decompress", "cz_compress_bound", "cz_workspace_size",
+              "cz_read_header", "cz_status", "cz_strerror", "cz_forward_dense",
+              "cz_inverse_dense", "cz_compress_noalloc"):
+        assert n in names
+
+
+def test_library_exports_every_declared_function(cz):
+    from paper_1903_07761_gb300 import _build
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    for n in _declared():
+        assert hasattr(cz.lib(), n)
+
+
+def test_strerror_covers_every_code(cz):
+    texts = {code: cz.cz_strerror(code) for code in
+             (cz.OK, cz.ERR_ARG, cz.ERR_CAPACITY, cz.ERR_CORRUPT, cz.ERR_TIMEOUT, cz.ERR_CUDA, cz.ERR_BUDGET)}
+    assert all(texts.values())
+    assert len(set(texts.values())) == len(texts)
+
+
+@pytest.mark.parametrize("dims,block,f64", [((32, 32, 32), 32, False), ((16, 48, 32), 16, True),
+                                            ((8, 8, 24), 8, False)])
+def test_compress_bound_covers_the_worst_stream(cz, dims, block, f64):
+    p = cz.params_for(dims, f64, block, "w4", 0.0, cz.EPS_REL, True, 1.0)
+    bound = cz.cz_compress_bound(p)
+    assert bound >= O.compress_bound(dims, block, np.float64 if f64 else np.float32)
+    # white noise at eps = 0 keeps every coefficient: the stream must fit
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal(dims).astype(np.float64 if f64 else np.float32)
+    for st2 in (True, False):
+        s = O.compress(f, block, O.W4, 0.0, O.EPS_REL, st2)
+        assert len(s) <= bound
+
+
+def test_invalid_parameters_are_refused_on_the_host(cz):
+    bad = [((32, 32, 48), 32, False), ((16, 16, 16), 12, False), ((32, 32, 32), 32, True),
+           ((0, 32, 32), 32, False)]
+    for dims, block, f64 in bad:
+        p = cz.params_for(dims, f64, block, "w4", 1e-3, cz.EPS_REL, True, 1.0)
+        with pytest.raises(cz.CzError) as e:
+            cz.cz_compress_bound(p)
+        assert e.value.code == cz.ERR_ARG
+    p = cz.params_for((32, 32, 32), False, 32, "w4", -1.0, cz.EPS_REL, True, 1.0)
+    with pytest.raises(cz.CzError):
+        cz.cz_compress_bound(p)
+    p = cz.params_for((32, 32, 32), False, 32, "w4", float("nan"), cz.EPS_REL, True, 1.0)
+    with pytest.raises(cz.CzError):
+        cz.cz_compress_bound(p)
+    # null buffers are refused before any CUDA call
+    p = cz.params_for((32, 32, 32), False, 32, "w4", 1e-3, cz.EPS_REL, True, 1.0)
+    assert cz.cz_compress(p, 0, 0, 1 << 20, 0, 0, 1 << 20, 0) == cz.ERR_ARG
+    assert cz.lib().cz_compress_noalloc(C.byref(cz.params_for((32, 32, 48), False, 32, "w4", 1e-3)),
+                                        None, None, 0, None, None) == cz.ERR_ARG
+
+
+def test_read_header_of_an_oracle_stream(cz):
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((16, 32, 48)).astype(np.float32)
+    s = O.compress(f, 16, O.W3AI, 1e-2, O.EPS_REL, True)
+    p, t = cz.cz_read_header(s[:cz.HEADER_BYTES])
+    assert (p.nx, p.ny, p.nz, p.block, p.dtype, p.kind, p.stage2) == (48, 32, 16, 16, cz.F32, cz.W3AI, 1)
+    assert p.eps == 1e-2 and p.eps_mode == cz.EPS_REL
+    h = O.read_header(s)
+    assert t == h["t"]
+    assert p.range == h["range"]
+    bad = bytearray(s[:cz.HEADER_BYTES])
+    bad[0] ^= 1  # magic
+    with pytest.raises(cz.CzError) as e:
+        cz.cz_read_header(bytes(bad))
+    assert e.value.code == cz.ERR_CORRUPT
+    bad = bytearray(s[:cz.HEADER_BYTES])
+    bad[28] ^= 1  # block count disagrees with the dims
+    with pytest.raises(cz.CzError):
+        cz.cz_read_header(bytes(bad))
