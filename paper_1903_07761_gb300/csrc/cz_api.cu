@@ -56,7 +56,7 @@ int check(const cz_params *p, Shape *sh)
 struct Lanes {
   cudaError_t (*compress)(int, const CUtensorMap *, const FwdArgs *, const S2Args *, const PlaceArgs *, int, int,
                           int, const cudaEvent_t *, cudaStream_t);
-  cudaError_t (*decompress)(int, const InvArgs *, int, cudaStream_t);
+  cudaError_t (*decompress)(int, const InvArgs *, const UnArgs *, int, int, int, cudaStream_t);
   cudaError_t (*dense)(int, int, const DenseArgs *, int, cudaStream_t);
   int (*occupancy)(int, int);
   int (*slot_bytes)();
@@ -351,8 +351,14 @@ int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header, void 
   const unsigned long long total = rd64(hb + 80), data_bytes = rd64(hb + 72);
   if (total > in_bytes || sh.data0 + data_bytes != total) return CZ_ERR_CORRUPT;
   if ((size_t)p.nx * p.ny * p.nz * sh.es > field_cap) return CZ_ERR_CAPACITY;
-  if (ws_bytes < (size_t)WS_HDR) return CZ_ERR_CAPACITY;
+  const Lanes L = lanes_for(p.dtype, p.block);
+  // workspace: header | block table (nnz, bad flag) | one staging slot per
+  // block for the decoded stage-2 payloads (within cz_workspace_size)
+  const size_t slot = (size_t)L.slot_bytes();
+  const size_t need = p.stage2 ? WS_HDR + table_bytes(sh) + (size_t)sh.nblocks * slot : (size_t)WS_HDR;
+  if (ws_bytes < need) return CZ_ERR_CAPACITY;
   if (cudaMemsetAsync(d_ws, 0, WS_HDR, s) != cudaSuccess) return CZ_ERR_CUDA;
+  unsigned char *wsb = reinterpret_cast<unsigned char *>(d_ws);
   InvArgs a{};
   a.in = reinterpret_cast<const unsigned char *>(d_in);
   a.field = d_field;
@@ -367,8 +373,21 @@ int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header, void 
   a.nbz = sh.nbz;
   a.nblocks = sh.nblocks;
   a.stage2 = p.stage2;
-  const Lanes L = lanes_for(p.dtype, p.block);
-  return L.decompress(p.kind, &a, grid_for(&p, sh, 1), s) == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
+  a.table = reinterpret_cast<const unsigned long long *>(wsb + WS_HDR);
+  a.staging = wsb + WS_HDR + table_bytes(sh);
+  a.slot = slot;
+  UnArgs ua{};
+  ua.in = a.in;
+  ua.staging = wsb + WS_HDR + table_bytes(sh);
+  ua.table = reinterpret_cast<unsigned long long *>(wsb + WS_HDR);
+  ua.in_bytes = total;
+  ua.data0 = sh.data0;
+  ua.slot = slot;
+  ua.nblocks = sh.nblocks;
+  return L.decompress(p.kind, &a, &ua, grid_for(&p, sh, 1), grid_for(&p, sh, 4), grid_for(&p, sh, 5), s) ==
+                 cudaSuccess
+             ? CZ_OK
+             : CZ_ERR_CUDA;
 }
 
 int cz_status(const void *d_ws, void *stream)

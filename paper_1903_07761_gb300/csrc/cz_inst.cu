@@ -74,9 +74,24 @@ cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const S2Args &sa
 }
 
 template <int KIND>
-cudaError_t decompress_k(const InvArgs &a, int grid, cudaStream_t s)
+cudaError_t decompress_k(const InvArgs &a, const UnArgs &ua, int grid, int gridu, int gridub, cudaStream_t s)
 {
-  cudaError_t e = prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D);
+  cudaError_t e;
+  if (a.stage2) {
+    e = prepare<k_unstage<CZ_T, CZ_B, false>>(G::SMEM_U);
+    if (e != cudaSuccess) return e;
+    k_unstage<CZ_T, CZ_B, false><<<gridu, 128, G::SMEM_U, s>>>(ua);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if constexpr (G::HAS_BIG) {
+      e = prepare<k_unstage<CZ_T, CZ_B, true>>(G::SMEM_UB);
+      if (e != cudaSuccess) return e;
+      k_unstage<CZ_T, CZ_B, true><<<gridub, 512, G::SMEM_UB, s>>>(ua);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  e = prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D);
   if (e != cudaSuccess) return e;
   k_decompress2<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_D, s>>>(a);
   return cudaGetLastError();
@@ -114,6 +129,18 @@ int occupancy_s2()
   return n;
 }
 
+template <bool BIG>
+int occupancy_u()
+{
+  constexpr int sm = BIG ? G::SMEM_UB : G::SMEM_U;
+  if (prepare<k_unstage<CZ_T, CZ_B, BIG>>(sm) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_unstage<CZ_T, CZ_B, BIG>, BIG ? 512 : 128, sm) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
 template <int KIND>
 int occupancy_d()
 {
@@ -143,12 +170,13 @@ extern "C" cudaError_t CZ_CAT(czl_compress_, CZ_SUFFIX)(int kind, const CUtensor
   }
 }
 
-extern "C" cudaError_t CZ_CAT(czl_decompress_, CZ_SUFFIX)(int kind, const InvArgs *a, int grid, cudaStream_t s)
+extern "C" cudaError_t CZ_CAT(czl_decompress_, CZ_SUFFIX)(int kind, const InvArgs *a, const UnArgs *ua, int grid,
+                                                           int gridu, int gridub, cudaStream_t s)
 {
   switch (kind) {
-    case W4: return decompress_k<W4>(*a, grid, s);
-    case W4LI: return decompress_k<W4LI>(*a, grid, s);
-    default: return decompress_k<W3AI>(*a, grid, s);
+    case W4: return decompress_k<W4>(*a, *ua, grid, gridu, gridub, s);
+    case W4LI: return decompress_k<W4LI>(*a, *ua, grid, gridu, gridub, s);
+    default: return decompress_k<W3AI>(*a, *ua, grid, gridu, gridub, s);
   }
 }
 
@@ -170,11 +198,14 @@ extern "C" cudaError_t CZ_CAT(czl_dense_, CZ_SUFFIX)(int kind, int fwd, const De
 }
 
 // CTAs per SM of the stage kernel (which = 0), the decompress kernel
-// (which = 1), the small (which = 2) or the large (which = 3) stage-2 kernel
+// (which = 1), the small (2) or large (3) stage-2 kernel, the small (4) or
+// large (5) stage-2 inverse kernel
 extern "C" int CZ_CAT(czl_occupancy_, CZ_SUFFIX)(int kind, int which)
 {
   if (which == 2) return occupancy_s2<false>();
   if (which == 3) return G::HAS_BIG ? occupancy_s2<true>() : 1;
+  if (which == 4) return occupancy_u<false>();
+  if (which == 5) return G::HAS_BIG ? occupancy_u<true>() : 1;
   if (which == 0) {
     switch (kind) {
       case W4: return occupancy_c<W4>();

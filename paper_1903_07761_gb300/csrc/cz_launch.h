@@ -6,6 +6,7 @@
 namespace czp {
 struct FwdArgs;
 struct InvArgs;
+struct UnArgs;
 struct DenseArgs;
 struct S2Args;
 struct PlaceArgs;
@@ -16,8 +17,8 @@ struct PlaceArgs;
                                             const czp::S2Args *sa, const czp::PlaceArgs *pa,        \
                                             int grid, int grid2, int grid3,                         \
                                             const cudaEvent_t *marks, cudaStream_t s);              \
-  extern "C" cudaError_t czl_decompress_##sfx(int kind, const czp::InvArgs *a, int grid,           \
-                                              cudaStream_t s);                                      \
+  extern "C" cudaError_t czl_decompress_##sfx(int kind, const czp::InvArgs *a, const czp::UnArgs *ua, \
+                                              int grid, int gridu, int gridub, cudaStream_t s);       \
   extern "C" cudaError_t czl_dense_##sfx(int kind, int fwd, const czp::DenseArgs *a, int nblocks,   \
                                          cudaStream_t s);                                           \
   extern "C" int czl_occupancy_##sfx(int kind, int which);                                         \

@@ -65,9 +65,20 @@ struct InvArgs {
   const unsigned char *in;
   void *field;
   void *ws;
-  unsigned long long in_bytes, data0;
+  const unsigned char *staging;       // stage 2: decoded payloads, one slot per block
+  const unsigned long long *table;    // stage 2: per block nnz, bad flag
+  unsigned long long in_bytes, data0, slot;
   int nx, ny, nz, nbx, nby, nbz, nblocks;
   int stage2;
+};
+
+// stage-2 decoding: chunk -> raw payload in a staging slot
+struct UnArgs {
+  const unsigned char *in;
+  unsigned char *staging;
+  unsigned long long *table;  // per block: nnz, bad flag
+  unsigned long long in_bytes, data0, slot;
+  int nblocks;
 };
 
 struct DenseArgs {
@@ -142,10 +153,10 @@ struct G2 {
   static constexpr int WMAX = PMAX / 4;
   static constexpr int NBWMAX = (WMAX + 31) / 32;
   static constexpr int TILE = NVOX * ES;
-  // y-exchange planes per batch: forward kernels use the shared memory the
-  // payload no longer needs, the inverse kernel keeps room for the payload
+  // y-exchange planes per batch (the inverse kernel keeps room for the
+  // payload beside them)
   static constexpr int ZBF = B == 32 ? (ES == 4 ? 16 : 4) : B;
-  static constexpr int ZBI = B == 32 ? 4 : (B == 16 ? (ES == 4 ? 16 : 4) : 8);
+  static constexpr int ZBI = B == 32 ? 8 : (B == 16 && ES == 8 ? 4 : B);
   static constexpr int XBF = ZBF * B * B * ES, ADBF = ZBF * (B / 2) * B * ES;
   static constexpr int XBI = ZBI * B * B * ES, ADBI = ZBI * (B / 2) * B * ES;
   static constexpr int ROWB = B * B * 4;
@@ -166,13 +177,16 @@ struct G2 {
   static constexpr int SMEM_S2 = SHCAP + 4 * NBS * 4;
   static constexpr bool HAS_BIG = SHCAP < PMAX;
   static constexpr int SMEM_S2B = PMAX_AL + 4 * NBWMAX * 4;
+  // stage-2 inverse kernels: payload + two token prefix arrays
+  static constexpr int SMEM_U = SHCAP + 2 * 128 * 4;
+  static constexpr int SMEM_UB = PMAX_AL + 2 * 512 * 4;
   // dense kernels
   static constexpr int SMEM_DN0 = (XBF + ADBF) > (XBI + ADBI) ? (XBF + ADBF) : (XBI + ADBI);
   // decompress: no tile; the whole payload always fits
-  static constexpr int AUXD = ROWB + 2 * NT * 4;
-  static constexpr int R2D0 = (XBI + ADBI) > AUXD ? (XBI + ADBI) : AUXD;
+  static constexpr int R2D0 = (XBI + ADBI) > ROWB ? (XBI + ADBI) : ROWB;
   static constexpr int R2D = (R2D0 + 127) / 128 * 128;
-  static constexpr int SMEM_D = R2D + PMAX_AL;
+  static constexpr int PBCAP = PMAX_AL < 65536 ? PMAX_AL : 65536;  // decompress payload buffer
+  static constexpr int SMEM_D = R2D + 2 * PBCAP;
   static_assert(SMEM_C <= 227 * 1024 - 1024, "stage kernel shared memory");
   static_assert(SMEM_D <= 227 * 1024 - 1024, "decompress shared memory");
   static_assert(SMEM_S2B <= 227 * 1024 - 1024, "stage-2 shared memory");
@@ -202,6 +216,19 @@ __device__ __forceinline__ void tma_load_tile(const CUtensorMap *tm, void *dst, 
       "[%5];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
+}
+
+// 1D bulk copy global -> shared (addresses 16-byte aligned, bytes a
+// multiple of 16) completing on the mbarrier
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 // bounded wait for the mbarrier phase with the given parity; false on timeout
@@ -800,61 +827,7 @@ __device__ __forceinline__ void inv_all(T2 (&v)[B], T *X, T *AD, int a, int y, i
   inv_level0<T, B, KIND>(v, X, AD, a, y, seg);
 }
 
-// ============================================================ stage-2 helpers
-__device__ __forceinline__ unsigned shuffled_word(const unsigned char *P, int w, int E, int es)
-{
-  const int j = 4 * w;
-  int b = j / E;
-  int e = j - b * E;
-  unsigned r = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if (e == E) {
-      e = 0;
-      ++b;
-    }
-    r |= (unsigned)P[e * es + b] << (8 * q);
-    ++e;
-  }
-  return r;
-}
-
-__device__ __forceinline__ void unshuffle_word(unsigned char *P, int w, unsigned val, int E, int es)
-{
-  const int j = 4 * w;
-  int b = j / E;
-  int e = j - b * E;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if (e == E) {
-      e = 0;
-      ++b;
-    }
-    P[e * es + b] = (unsigned char)(val >> (8 * q));
-    ++e;
-  }
-}
-
-__device__ __forceinline__ unsigned tokcount(unsigned lit, unsigned zr)
-{
-  return 1u + (lit > 65535u ? (lit - 1u) / 65535u : 0u) + (zr > 65535u ? (zr - 1u) / 65535u : 0u);
-}
-
-__device__ __forceinline__ unsigned emit_tokens(unsigned *tok, unsigned idx, unsigned lit, unsigned zr)
-{
-  while (lit > 65535u) {
-    tok[idx++] = 65535u;
-    lit -= 65535u;
-  }
-  while (zr > 65535u) {
-    tok[idx++] = lit | (65535u << 16);
-    lit = 0;
-    zr -= 65535u;
-  }
-  tok[idx++] = lit | (zr << 16);
-  return idx;
-}
-
+// ============================================================ stream helpers
 template <typename U>
 __device__ __forceinline__ void st_le(unsigned char *p, U v)
 {
@@ -912,34 +885,28 @@ __device__ __forceinline__ void threshold_of(double eps, int eps_mode, double ra
 }
 
 // ============================================================ decompress
-template <typename T, int B, int KIND>
-__global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
+// ---- stage-2 inverse, one chunk at a time: the tokens are expanded by
+// block scans of (literal words, output words) per token, each literal
+// word is unshuffled into the payload in shared memory, and the payload is
+// written to the block's staging slot.  Small CTAs take the payloads of up
+// to G2::SHCAP bytes (and the malformed chunks), a second launch with large
+// CTAs the rest.
+template <typename T, int B, bool BIG>
+__global__ void __launch_bounds__(BIG ? 512 : 128) k_unstage(const UnArgs a)
 {
   using G = G2<T, B>;
-  using T2 = typename V2T<T>::type;
-  constexpr int NT = G::NT, ES = G::ES, Q = G::Q;
+  constexpr int NT = BIG ? 512 : 128, ES = G::ES;
+  constexpr int CAPB = BIG ? G::PMAX_AL : G::SHCAP;
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char *R2 = smem;
-  unsigned char *P = smem + G::R2D;
-  T *X = reinterpret_cast<T *>(R2);
-  T *AD = reinterpret_cast<T *>(R2 + G::XBI);
-  unsigned *ROWOFF = reinterpret_cast<unsigned *>(R2);
-  unsigned *TL = ROWOFF + B * B;
+  unsigned char *P = smem;
+  unsigned *TL = reinterpret_cast<unsigned *>(smem + CAPB);
   unsigned *TO = TL + NT;
   __shared__ unsigned s_u[40];
   __shared__ unsigned s_nnz, s_ntok, s_bad;
   __shared__ unsigned long long s_off, s_len;
-
-  WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int ap = tid % G::HP, r = tid / G::HP;
-  const int y = r < B / 2 ? 2 * r : 2 * (r - B / 2) + 1;
-  const int seg = lane - ap;
-  const int x0 = 2 * ap;
-  const bool cE = (x0 % Q == 0) && (y % Q == 0);
+  const int tid = threadIdx.x;
 
   for (int bid = blockIdx.x; bid < a.nblocks; bid += gridDim.x) {
-    const int bx = bid % a.nbx, by = (bid / a.nbx) % a.nby, bz = bid / (a.nbx * a.nby);
     if (tid == 0) {
       unsigned bad = 0;
       const unsigned long long *tab = reinterpret_cast<const unsigned long long *>(a.in + HEADER_BYTES);
@@ -952,11 +919,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
         const unsigned *c32 = reinterpret_cast<const unsigned *>(a.in + a.data0 + o0);
         nnz = c32[0];
         ntok = c32[1];
-        const unsigned long long len = o1 - o0;
         if (nnz > (unsigned)(G::NVOX - 64)) bad = 1;
-        const unsigned long long pb = 64ull * ES + G::MASKB + (unsigned long long)nnz * ES;
-        if (!bad && !a.stage2 && (ntok != 0 || 8 + pb > len)) bad = 1;
-        if (!bad && a.stage2 && (unsigned long long)ntok > (len - 8) / 4) bad = 1;
+        if (!bad && (unsigned long long)ntok > (o1 - o0 - 8) / 4) bad = 1;
       }
       s_bad = bad;
       s_nnz = bad ? 0u : nnz;
@@ -967,55 +931,177 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
     __syncthreads();
     const unsigned nnz = s_nnz;
     const int pbytes = 64 * ES + G::MASKB + (int)nnz * ES;
-    const unsigned *c32 = reinterpret_cast<const unsigned *>(a.in + a.data0 + s_off);
-
+    if (s_bad ? BIG : ((pbytes > G::SHCAP) != BIG)) {  // the other launch's chunk
+      __syncthreads();
+      continue;
+    }
     if (!s_bad) {
-      if (a.stage2) {
-        const int W = pbytes / 4, E = pbytes / ES;
-        const unsigned ntok = s_ntok;
-        const unsigned long long nlit_avail = (s_len - 8 - 4ull * ntok) / 4;
-        const unsigned *tok = c32 + 2;
-        const unsigned *lit = tok + ntok;
-        unsigned *P32 = reinterpret_cast<unsigned *>(P);
-        for (int w = tid; w < W; w += NT) P32[w] = 0u;
+      const int W = pbytes / 4, E = pbytes >> G::LGES;
+      const unsigned ntok = s_ntok;
+      const unsigned long long nlit_avail = (s_len - 8 - 4ull * ntok) / 4;
+      const unsigned *c32 = reinterpret_cast<const unsigned *>(a.in + a.data0 + s_off);
+      const unsigned *tok = c32 + 2;
+      const unsigned *lit = tok + ntok;
+      unsigned *SH32 = reinterpret_cast<unsigned *>(P);  // the shuffled payload
+      for (int w = tid; w < W; w += NT) SH32[w] = 0u;
+      __syncthreads();
+      unsigned lit_carry = 0, out_carry = 0;
+      bool bad = false;
+      for (unsigned r0 = 0; r0 < ntok; r0 += NT) {
+        const unsigned k = r0 + tid;
+        const unsigned tk = k < ntok ? __ldg(tok + k) : 0u;
+        const unsigned nl = tk & 0xFFFFu, run = nl + (tk >> 16);
+        unsigned tl, to_;
+        const unsigned lp = block_exsum<NT>(nl, s_u, tl);
+        const unsigned op = block_exsum<NT>(run, s_u, to_);
+        TL[tid] = lit_carry + lp;
+        TO[tid] = out_carry + op;
         __syncthreads();
-        unsigned lit_carry = 0, out_carry = 0;
-        bool bad = false;
-        for (unsigned r0 = 0; r0 < ntok; r0 += NT) {
-          const unsigned k = r0 + tid;
-          const unsigned tk = k < ntok ? __ldg(tok + k) : 0u;
-          const unsigned nl = tk & 0xFFFFu, run = nl + (tk >> 16);
-          unsigned tl, to_;
-          const unsigned lp = block_exsum<NT>(nl, s_u, tl);
-          const unsigned op = block_exsum<NT>(run, s_u, to_);
-          TL[tid] = lit_carry + lp;
-          TO[tid] = out_carry + op;
-          __syncthreads();
-          const unsigned cnt = (ntok - r0) < (unsigned)NT ? (ntok - r0) : (unsigned)NT;
-          for (unsigned l = lit_carry + tid; l < lit_carry + tl; l += NT) {
-            unsigned lo = 0, hi = cnt - 1;
-            while (lo < hi) {
-              const unsigned mid = (lo + hi + 1) >> 1;
-              if (TL[mid] <= l) lo = mid; else hi = mid - 1;
-            }
-            const unsigned ow = TO[lo] + (l - TL[lo]);
-            if (l < nlit_avail && ow < (unsigned)W) unshuffle_word(P, (int)ow, __ldg(lit + l), E, ES);
-            else bad = true;
+        const unsigned cnt = (ntok - r0) < (unsigned)NT ? (ntok - r0) : (unsigned)NT;
+        for (unsigned l = lit_carry + tid; l < lit_carry + tl; l += NT) {
+          unsigned lo = 0, hi = cnt - 1;
+          while (lo < hi) {
+            const unsigned mid = (lo + hi + 1) >> 1;
+            if (TL[mid] <= l)
+              lo = mid;
+            else
+              hi = mid - 1;
           }
-          lit_carry += tl;
-          out_carry += to_;
-          __syncthreads();
+          const unsigned ow = TO[lo] + (l - TL[lo]);
+          if (l < nlit_avail && ow < (unsigned)W)
+            SH32[ow] = __ldg(lit + l);
+          else
+            bad = true;
         }
-        if (bad || out_carry != (unsigned)W || (unsigned long long)lit_carry > nlit_avail) atomicOr(&s_bad, 1u);
-      } else {
-        unsigned *P32 = reinterpret_cast<unsigned *>(P);
-        for (int w = tid; w < pbytes / 4; w += NT) P32[w] = __ldg(c32 + 2 + w);
+        lit_carry += tl;
+        out_carry += to_;
+        __syncthreads();
+      }
+      if (bad || out_carry != (unsigned)W || (unsigned long long)lit_carry > nlit_avail) atomicOr(&s_bad, 1u);
+      __syncthreads();
+      if (!s_bad) {
+        // unshuffle straight into the slot: byte q of raw word k is byte
+        // (4k + q) % ES of element (4k + q) / ES, found at plane offset
+        unsigned *dst = reinterpret_cast<unsigned *>(a.staging + (size_t)bid * a.slot);
+        for (int k = tid; k < W; k += NT) {
+          const int e = (4 * k) >> G::LGES, b0 = (4 * k) & (ES - 1);
+          unsigned wv = 0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) wv |= (unsigned)P[(b0 + q) * E + e] << (8 * q);
+          dst[k] = wv;
+        }
       }
     }
+    if (tid == 0) {
+      a.table[2 * bid] = s_bad ? 0ull : (unsigned long long)nnz;
+      a.table[2 * bid + 1] = s_bad ? 1ull : 0ull;
+    }
     __syncthreads();
+  }
+}
 
+template <typename T, int B, int KIND>
+__global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
+{
+  using G = G2<T, B>;
+  using T2 = typename V2T<T>::type;
+  constexpr int NT = G::NT, ES = G::ES, Q = G::Q;
+  constexpr int HEAD = 64 * ES + G::MASKB;  // coarse values + mask
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char *R2 = smem;
+  T *X = reinterpret_cast<T *>(R2);
+  T *AD = reinterpret_cast<T *>(R2 + G::XBI);
+  unsigned *ROWOFF = reinterpret_cast<unsigned *>(R2);
+  unsigned char *BUF0 = smem + G::R2D;  // two payload buffers of G::PBCAP bytes
+  __shared__ __align__(8) unsigned long long s_bar[2];
+  __shared__ unsigned s_u[40];
+  __shared__ unsigned s_nnz[2], s_bad[2];
+  __shared__ unsigned s_badx;
+
+  WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ap = tid % G::HP, r = tid / G::HP;
+  const int y = r < B / 2 ? 2 * r : 2 * (r - B / 2) + 1;
+  const int seg = lane - ap;
+  const int x0 = 2 * ap;
+  const bool cE = (x0 % Q == 0) && (y % Q == 0);
+  const bool pre = a.stage2 != 0;  // decoded payloads sit in 16-byte aligned slots
+
+  // metadata of block b into buffer slot j, and (with stage 2) the start
+  // of its payload copy; called by thread 0
+  auto fetch = [&](int b, int j) {
+    unsigned bad = 0, nnz = 0;
+    unsigned long long o0 = 0;
+    if (pre) {  // decoded (and checked) by k_unstage
+      bad = a.table[2 * b + 1] != 0;
+      nnz = bad ? 0u : (unsigned)a.table[2 * b];
+    } else {
+      const unsigned long long *tab = reinterpret_cast<const unsigned long long *>(a.in + HEADER_BYTES);
+      o0 = tab[b];
+      const unsigned long long o1 = tab[b + 1];
+      const unsigned long long avail = a.in_bytes - a.data0;
+      if (o0 > o1 || o1 > avail || o1 - o0 < 8 || (o0 & 3) || ((o1 - o0) & 3)) {
+        bad = 1;
+      } else {
+        const unsigned *c32 = reinterpret_cast<const unsigned *>(a.in + a.data0 + o0);
+        nnz = c32[0];
+        if (nnz > (unsigned)(G::NVOX - 64)) bad = 1;
+        const unsigned long long pb = 64ull * ES + G::MASKB + (unsigned long long)nnz * ES;
+        if (!bad && (c32[1] != 0 || 8 + pb > o1 - o0)) bad = 1;
+      }
+    }
+    s_bad[j] = bad;
+    s_nnz[j] = bad ? 0u : nnz;
+    if (pre && !bad) {
+      const int pbytes = HEAD + (int)nnz * ES;
+      const int cp = pbytes <= G::PBCAP ? pbytes : HEAD;
+      bulk_load(BUF0 + j * G::PBCAP, a.staging + (size_t)b * a.slot, (unsigned)((cp + 15) & ~15), &s_bar[j]);
+    }
+    return o0;
+  };
+
+  if (tid == 0) {
+    mbar_init(&s_bar[0]);
+    mbar_init(&s_bar[1]);
+  }
+  __syncthreads();
+  __shared__ unsigned long long s_off;
+  if (tid == 0 && (int)blockIdx.x < a.nblocks) s_off = fetch(blockIdx.x, 0);
+  __syncthreads();
+  unsigned phase[2] = {0u, 0u};
+  int j = 0;
+
+  for (int bid = blockIdx.x; bid < a.nblocks; bid += gridDim.x, j ^= 1) {
+    const int bx = bid % a.nbx, by = (bid / a.nbx) % a.nby, bz = bid / (a.nbx * a.nby);
+    unsigned char *P = BUF0 + j * G::PBCAP;
+    const unsigned nnz = s_nnz[j];
+    const int pbytes = HEAD + (int)nnz * ES;
+    bool bad0 = s_bad[j] != 0;
+    if (pre) {
+      if (!bad0) {
+        if (!mbar_wait(&s_bar[j], phase[j])) {
+          // the copy never completed: record, wait once more for it, stop
+          if (tid == 0) atomicCAS(&ws->status, 0u, ST_TIMEOUT);
+          mbar_wait(&s_bar[j], phase[j]);
+          break;
+        }
+        phase[j] ^= 1u;
+      }
+    } else if (!bad0) {
+      const unsigned *c32 = reinterpret_cast<const unsigned *>(a.in + a.data0 + s_off);
+      const int cp = pbytes <= G::PBCAP ? pbytes : HEAD;
+      for (int w = tid; w < cp / 4; w += NT) reinterpret_cast<unsigned *>(P)[w] = __ldg(c32 + 2 + w);
+      __syncthreads();
+    }
+    // values beyond the buffer are read from global memory
+    const T *VALS = pbytes <= G::PBCAP
+                        ? reinterpret_cast<const T *>(P + HEAD)
+                        : (pre ? reinterpret_cast<const T *>(a.staging + (size_t)bid * a.slot + HEAD)
+                               : reinterpret_cast<const T *>(a.in + a.data0 + s_off + 8 + HEAD));
     const unsigned char *MASK = P + 64 * ES;
-    if (!s_bad) {
+    if (tid == 0) s_badx = 0;
+    __syncthreads();
+    if (!bad0) {
       // row populations -> row offsets; coarse positions carry no mask bit
       const unsigned w0 = get_row<B>(MASK, 2 * ap, y), w1 = get_row<B>(MASK, 2 * ap + 1, y);
       ROWOFF[(2 * ap) * B + y] = __popc(w0);
@@ -1024,7 +1110,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
         unsigned cm = 0;
 #pragma unroll
         for (int x = 0; x < B; x += Q) cm |= 1u << x;
-        if (((2 * ap) % Q == 0 && (w0 & cm)) || ((2 * ap + 1) % Q == 0 && (w1 & cm))) atomicOr(&s_bad, 1u);
+        if (((2 * ap) % Q == 0 && (w0 & cm)) || ((2 * ap + 1) % Q == 0 && (w1 & cm))) atomicOr(&s_badx, 1u);
       }
       __syncthreads();
       constexpr int IPT = (B * B + NT - 1) / NT;
@@ -1041,16 +1127,15 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
         ROWOFF[tid * IPT + q] = ex;
         ex += loc[q];
       }
-      if (tid == 0 && tot != nnz) atomicOr(&s_bad, 1u);
+      if (tid == 0 && tot != nnz) atomicOr(&s_badx, 1u);
     }
     __syncthreads();
-    const bool bad = s_bad != 0;
+    const bool bad = bad0 || s_badx != 0;
     if (bad && tid == 0) atomicCAS(&ws->status, 0u, ST_CORRUPT);
 
     T2 v[B];
     {
       const T *COARSE = reinterpret_cast<const T *>(P);
-      const T *VALS = reinterpret_cast<const T *>(MASK + G::MASKB);
       const unsigned lowE = (1u << x0) - 1u, lowO = (2u << x0) - 1u;
 #pragma unroll
       for (int z = 0; z < B; ++z) {
@@ -1059,7 +1144,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
         rv.y = T(0);
         if (!bad) {
           const unsigned wd = get_row<B>(MASK, z, y);
-          if (__any_sync(FULL, wd != 0u)) {
+          if (wd) {
             const unsigned base = ROWOFF[z * B + y];
             if ((wd >> x0) & 1u) rv.x = VALS[base + __popc(wd & lowE)];
             if ((wd >> (x0 + 1)) & 1u) rv.y = VALS[base + __popc(wd & lowO)];
@@ -1069,7 +1154,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
         v[z] = rv;
       }
     }
-    __syncthreads();
+    __syncthreads();  // buffer j and the row offsets are free
+    if (tid == 0 && bid + (int)gridDim.x < a.nblocks) s_off = fetch(bid + gridDim.x, j ^ 1);
     if (!bad) inv_all<T, B, KIND>(v, X, AD, ap, y, seg);
     {
       const size_t zs = (size_t)a.ny * a.nx;

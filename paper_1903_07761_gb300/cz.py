@@ -209,7 +209,7 @@ def decompress(stream_t, nbytes: int | None = None, header: bytes | None = None,
     if out is None:
         out = torch.empty((p.nz, p.ny, p.nx), dtype=dt, device=stream_t.device)
     ws = ws or Workspace(stream_t.device)
-    wsb = ws.get(256)
+    wsb = ws.get(cz_workspace_size(p))
     s = _stream(stream)
     r = cz_decompress(stream_t.data_ptr(), n, header, out.data_ptr(),
                       out.numel() * out.element_size(), wsb.data_ptr(), wsb.numel(), s)
