@@ -453,7 +453,7 @@ def main():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--block", type=int, default=32)
     ap.add_argument("--eps", type=float, default=1e-3)
-    ap.add_argument("--cpu-slabs", type=int, default=8)
+    ap.add_argument("--cpu-slabs", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--headline-only", action="store_true")
