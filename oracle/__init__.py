@@ -31,6 +31,7 @@ _lib = None
 W4, W4LI, W3AI = 0, 1, 2
 F32, F64 = 0, 1
 EPS_REL, EPS_ABS = 0, 1
+BOUND_PAPER, BOUND_STRICT = 0, 1
 OK, ERR_ARG, ERR_CAPACITY, ERR_CORRUPT = 0, -1, -2, -3
 HEADER_BYTES = 128
 
@@ -40,6 +41,7 @@ class Params(C.Structure):
         ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
         ("block", C.c_int32), ("dtype", C.c_int32), ("kind", C.c_int32),
         ("eps_mode", C.c_int32), ("stage2", C.c_int32),
+        ("bound_mode", C.c_int32), ("flags", C.c_int32),
         ("eps", C.c_double), ("range", C.c_double),
     ]
 
@@ -96,6 +98,8 @@ def lib():
                                           C.POINTER(C.c_double), C.POINTER(C.c_uint64)]
             L.czo_threshold.argtypes = [C.c_double, C.c_int, C.c_double]
             L.czo_threshold.restype = C.c_double
+            L.czo_synthesis_norm.argtypes = [C.c_int, C.c_int]
+            L.czo_synthesis_norm.restype = C.c_double
             L.czo_shuffle.argtypes = [P, C.c_size_t, C.c_int, P]
             L.czo_unshuffle.argtypes = [P, C.c_size_t, C.c_int, P]
             L.czo_rle_encode.argtypes = [P, C.c_size_t, P, C.c_size_t, C.POINTER(C.c_size_t),
@@ -186,16 +190,18 @@ def decode_block(kind: int, B: int, dtype, chunk: bytes, stage2: bool) -> np.nda
 
 
 # ---------------------------------------------------------------- whole field
-def params(shape, block, dtype, kind, eps, eps_mode=EPS_REL, stage2=True, range_=-1.0):
+def params(shape, block, dtype, kind, eps, eps_mode=EPS_REL, stage2=True, range_=-1.0,
+           bound_mode=0):
     nz, ny, nx = shape
     return Params(nx, ny, nz, block, F64 if np.dtype(dtype) == np.float64 else F32,
-                  kind, eps_mode, int(stage2), float(eps), float(range_))
+                  kind, eps_mode, int(stage2), int(bound_mode), 0, float(eps), float(range_))
 
 
 def compress(field: np.ndarray, block: int, kind: int, eps: float,
-             eps_mode: int = EPS_REL, stage2: bool = True, range_: float = -1.0) -> bytes:
+             eps_mode: int = EPS_REL, stage2: bool = True, range_: float = -1.0,
+             bound_mode: int = 0) -> bytes:
     field = np.ascontiguousarray(field)
-    p = params(field.shape, block, field.dtype, kind, eps, eps_mode, stage2, range_)
+    p = params(field.shape, block, field.dtype, kind, eps, eps_mode, stage2, range_, bound_mode)
     cap = C.c_size_t()
     r = lib().czo_compress_bound(C.byref(p), C.byref(cap))
     if r != OK:
@@ -227,7 +233,7 @@ def read_header(stream: bytes) -> dict:
     if r != OK:
         raise ValueError(f"bad header: {r}")
     return dict(nx=p.nx, ny=p.ny, nz=p.nz, block=p.block, dtype=p.dtype, kind=p.kind,
-                eps_mode=p.eps_mode, stage2=p.stage2, eps=p.eps, range=p.range,
+                eps_mode=p.eps_mode, stage2=p.stage2, bound_mode=p.bound_mode, eps=p.eps, range=p.range,
                 t=t.value, min=mn.value, max=mx.value, total=tot.value)
 
 
@@ -313,3 +319,12 @@ def rle_decode(tokens, lits: bytes, n: int) -> bytes:
     if r != OK:
         raise ValueError(f"rle_decode failed: {r}")
     return out[:n].tobytes()
+
+
+def synthesis_norm(kind: int, block: int) -> float:
+    """C of the strict bound mode: the largest row sum of |synthesis| over
+    the detail columns of one block (see czo_synthesis_norm)."""
+    c = lib().czo_synthesis_norm(kind, block)
+    if not c > 0:
+        raise ValueError("unsupported kind / block")
+    return c

@@ -113,6 +113,50 @@ double czo_threshold(double eps, int eps_mode, double range)
   return eps_mode == CZO_EPS_ABS ? eps : eps * range;
 }
 
+/* see czo.h; every sum runs in increasing index order, in double */
+double czo_synthesis_norm(int kind, int B)
+{
+  enum { MAXB = 64, MAXL = 4 };
+  if (B < 8 || B > MAXB || (B & (B - 1))) return -1.0;
+  int L = 0;
+  while ((B >> L) > 4) ++L;
+  if (L > MAXL) return -1.0;
+  double R[MAXL][MAXB], E[MAXL][MAXB];
+  for (int l = 0; l < L; ++l) {
+    const int nl = B >> l;
+    for (int x = 0; x < B; ++x) R[l][x] = E[l][x] = 0.0;
+    for (int j = 0; j < nl; ++j) {
+      /* column j of m_l: unit coefficient at local index j of level l,
+         synthesised level by level down to the B fine samples */
+      double w[MAXB] = {0};
+      w[j] = 1.0;
+      for (int k = l; k >= 0; --k) {
+        const int nk = B >> k;
+        if (czo_inv1d_f64(kind, w, nk, 1) != CZO_OK) return -1.0;
+        if (k > 0) {
+          double u[MAXB] = {0};
+          for (int i = 0; i < nk; ++i) u[2 * i] = w[i];
+          for (int i = 0; i < 2 * nk; ++i) w[i] = u[i];
+        }
+      }
+      for (int x = 0; x < B; ++x) {
+        const double a = fabs(w[x]);
+        R[l][x] += a;
+        if (!(j & 1)) E[l][x] += a;
+      }
+    }
+  }
+  double C = 0.0;
+  for (int iz = 0; iz < B; ++iz)
+    for (int iy = 0; iy < B; ++iy)
+      for (int ix = 0; ix < B; ++ix) {
+        double s = 0.0;
+        for (int l = 0; l < L; ++l) s += (R[l][ix] * R[l][iy]) * R[l][iz] - (E[l][ix] * E[l][iy]) * E[l][iz];
+        if (s > C) C = s;
+      }
+  return C;
+}
+
 /* --------------------------------------------------------------------------
  * Stage 2 (Sec. 2.3 "Lossless compression": shuffling of the whole output,
  * coefficients and masks together, with the element size of the data).
@@ -233,7 +277,7 @@ int czo_rle_decode(const uint32_t *tokens, size_t ntok, const uint8_t *lits,
  *   0 u32 magic "CCZ1"   4 u16 version=1   6 u16 header bytes=128
  *   8 i32 nx  12 i32 ny  16 i32 nz
  *  20 u8 B  21 u8 dtype  22 u8 kind  23 u8 stage2  24 u8 eps_mode  25 u8 L
- *  28 u32 nblocks
+ *  26 u8 bound_mode  28 u32 nblocks
  *  32 f64 eps  40 f64 t (threshold as used, widened)  48 f64 min  56 f64 max
  *  64 f64 range  72 u64 chunk-section bytes  80 u64 total stream bytes
  * Then (nblocks+1) u64 chunk offsets relative to the chunk section, which
@@ -261,6 +305,7 @@ static void czo_write_header(uint8_t *out, const czo_params *p, double t,
   out[23] = (uint8_t)p->stage2;
   out[24] = (uint8_t)p->eps_mode;
   out[25] = (uint8_t)L;
+  out[26] = (uint8_t)p->bound_mode;
   memcpy(out + 28, &nb, 4);
   memcpy(out + 32, &p->eps, 8);
   memcpy(out + 40, &t, 8);
@@ -290,6 +335,7 @@ int czo_read_header(const uint8_t *in, size_t n, czo_params *p, double *t,
   p->kind = in[22];
   p->stage2 = in[23];
   p->eps_mode = in[24];
+  p->bound_mode = in[26];
   memcpy(&p->eps, in + 32, 8);
   memcpy(t, in + 40, 8);
   memcpy(mn, in + 48, 8);
@@ -320,6 +366,7 @@ static int check_params(const czo_params *p)
   if (p->dtype != CZO_F32 && p->dtype != CZO_F64) return CZO_ERR_ARG;
   if (p->kind < CZO_W4 || p->kind > CZO_W3AI) return CZO_ERR_ARG;
   if (!(p->eps >= 0)) return CZO_ERR_ARG;
+  if (p->bound_mode != CZO_BOUND_PAPER && p->bound_mode != CZO_BOUND_STRICT) return CZO_ERR_ARG;
   return CZO_OK;
 }
 

@@ -41,6 +41,7 @@ extern "C" {
 enum { CZO_W4 = 0, CZO_W4LI = 1, CZO_W3AI = 2 };
 enum { CZO_F32 = 0, CZO_F64 = 1 };
 enum { CZO_EPS_REL = 0, CZO_EPS_ABS = 1 };
+enum { CZO_BOUND_PAPER = 0, CZO_BOUND_STRICT = 1 };
 
 /* return codes (mirrors the numeric meaning of the library's codes) */
 enum {
@@ -61,6 +62,9 @@ typedef struct czo_params {
   int32_t kind;       /* CZO_W4 / CZO_W4LI / CZO_W3AI                          */
   int32_t eps_mode;   /* CZO_EPS_REL: t = eps*range ; CZO_EPS_ABS: t = eps     */
   int32_t stage2;     /* 1: byte shuffle + zero-RLE per chunk                  */
+  int32_t bound_mode; /* CZO_BOUND_PAPER: threshold t ; CZO_BOUND_STRICT:
+                         threshold t / C (see czo_synthesis_norm)             */
+  int32_t flags;      /* unused by the oracle (library build options)          */
   double eps;
   double range;       /* >= 0: use this range ; < 0: compute max - min         */
 } czo_params;
@@ -103,6 +107,19 @@ void czo_minmax_f32(const float *x, size_t n, double *mn, double *mx);
 void czo_minmax_f64(const double *x, size_t n, double *mn, double *mx);
 /* threshold t = eps*range (REL) or eps (ABS), formed in double */
 double czo_threshold(double eps, int eps_mode, double range);
+
+/* C = max over the positions i of a B^3 block of sum_j |S_ij| over the
+ * detail columns j of the block synthesis operator S (decoder = S applied to
+ * the kept coefficients).  Dropping details smaller than t / C therefore
+ * changes no value by more than t (the bound Sec. 2.3 states for the
+ * threshold).  Computed from the 1D level syntheses: a level-l detail is
+ * rebuilt by the syntheses of levels l..0 only, whose composition is the
+ * Kronecker cube of a B x (B >> l) matrix m_l, so its columns' row sums
+ * are products of the 1D row sums R_l (all columns) and E_l (even columns,
+ * which are coarse values, not details):
+ *   C = max_i sum_l ( R_l(ix) R_l(iy) R_l(iz) - E_l(ix) E_l(iy) E_l(iz) ).
+ * Returns a negative value for an unsupported (kind, B). */
+double czo_synthesis_norm(int kind, int B);
 
 /* ---- stage 2 primitives ---------------------------------------------------- */
 void czo_shuffle(const uint8_t *in, size_t nbytes, int s, uint8_t *out);

@@ -352,6 +352,49 @@ def test_decoder_is_linear_synthesis_and_error_is_bounded(kind):
     assert np.abs(r - f).max() <= t * C + 1e-12
 
 
+# ---------------------------------------------------------------- strict bound
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("B", [8, 16])
+def test_strict_norm_equals_dense_synthesis_row_sums(kind, B):
+    """C from the Kronecker formula = brute force over the 3D synthesis
+    columns of every detail position (Sec. 2.3's error bound, made exact)."""
+    D = detail_mask(B).ravel()
+    rows = np.zeros(B ** 3)
+    e = np.zeros(B ** 3)
+    for j in np.flatnonzero(D):
+        e[j] = 1.0
+        rows += np.abs(O.inv3d(kind, e.reshape(B, B, B)).ravel())
+        e[j] = 0.0
+    assert O.synthesis_norm(kind, B) == pytest.approx(rows.max(), rel=1e-12)
+
+
+def test_strict_norm_closed_form_w3ai_b8():
+    """W3ai at B = 8 has one level (m = 4).  The first sample of a line is
+    f0 = A0 + d0 = (11 a0 - 4 a1 + a2)/8 + d0, so its row sum over all
+    coefficients is R = 11/8 + 4/8 + 1/8 + 1 = 3 and over the coarse ones
+    E = 2; every other row is smaller.  The corner sample then collects
+    R^3 - E^3 = 27 - 8 = 19 from the detail columns."""
+    assert O.synthesis_norm(O.W3AI, 8) == 19.0
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("B", [8, 16, 32])
+def test_strict_mode_keeps_error_below_nominal_threshold(kind, B):
+    rng = np.random.default_rng(100 * B + kind)
+    f = np.cumsum(np.cumsum(rng.standard_normal((B, 2 * B, B)), axis=2), axis=1)
+    eps = 1e-2
+    s = O.compress(f, B, kind, eps, O.EPS_REL, True, bound_mode=O.BOUND_STRICT)
+    h = O.read_header(s)
+    rng_ = float(f.max() - f.min())
+    assert h["bound_mode"] == O.BOUND_STRICT
+    assert h["t"] == pytest.approx(eps * rng_ / O.synthesis_norm(kind, B), rel=1e-15)
+    r = O.decompress(s)
+    assert np.abs(r - f).max() <= eps * rng_
+    # the paper mode keeps fewer values and may exceed the nominal bound
+    sp = O.compress(f, B, kind, eps, O.EPS_REL, True)
+    assert len(sp) <= len(s)
+
+
 # ---------------------------------------------------------------- stage 2
 @pytest.mark.parametrize("s", [4, 8])
 def test_shuffle_is_byte_matrix_transpose(s):
