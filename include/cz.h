@@ -50,6 +50,13 @@ enum { CZ_W4 = 0, CZ_W4LI = 1, CZ_W3AI = 2 };
 enum { CZ_F32 = 0, CZ_F64 = 1 };
 /* threshold: t = eps * (max - min) of the whole field, or t = eps */
 enum { CZ_EPS_REL = 0, CZ_EPS_ABS = 1 };
+/* error bound: CZ_BOUND_PAPER drops details below t (Sec. 2.3: decimation
+ * error "not larger than" the threshold, which holds per level and axis);
+ * CZ_BOUND_STRICT drops details below t / C, C the largest row sum of
+ * |synthesis| over the detail columns of a block, so that the decoded error
+ * never exceeds t (C: 127 / 1572 / 5331 for W4 at B = 8 / 16 / 32, 19 / 100 /
+ * 249 for W3ai, 51 / 1229 / 4637 for W4li) */
+enum { CZ_BOUND_PAPER = 0, CZ_BOUND_STRICT = 1 };
 
 enum {
   CZ_OK = 0,
@@ -70,6 +77,8 @@ typedef struct cz_params {
   int32_t kind;       /* CZ_W4, CZ_W4LI or CZ_W3AI                          */
   int32_t eps_mode;   /* CZ_EPS_REL (default) or CZ_EPS_ABS                 */
   int32_t stage2;     /* 1: byte shuffle + zero-RLE each chunk; 0: raw      */
+  int32_t bound_mode; /* CZ_BOUND_PAPER (default) or CZ_BOUND_STRICT        */
+  int32_t flags;      /* reserved, must be 0                                */
   double eps;         /* tolerance, >= 0                                    */
   double range;       /* >= 0: max - min supplied by the caller (skips the
                          min/max pass); < 0: computed on the device        */

@@ -23,6 +23,7 @@ LIB = os.path.join(OUT_DIR, "libcz.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-fast-math",
+           "-Xcompiler", "-ffp-contract=off",
            "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 # (type, block) instantiations of the kernels

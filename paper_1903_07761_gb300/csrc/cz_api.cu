@@ -10,6 +10,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/cz.h"
 #include "cz_compress.cuh"
@@ -35,6 +36,8 @@ int check(const cz_params *p, Shape *sh)
   if (p->kind < CZ_W4 || p->kind > CZ_W3AI) return CZ_ERR_ARG;
   if (p->eps_mode != CZ_EPS_REL && p->eps_mode != CZ_EPS_ABS) return CZ_ERR_ARG;
   if (p->stage2 != 0 && p->stage2 != 1) return CZ_ERR_ARG;
+  if (p->bound_mode != CZ_BOUND_PAPER && p->bound_mode != CZ_BOUND_STRICT) return CZ_ERR_ARG;
+  if (p->flags != 0) return CZ_ERR_ARG;
   if (!(p->eps >= 0) || std::isinf(p->eps)) return CZ_ERR_ARG;
   if (std::isnan(p->range)) return CZ_ERR_ARG;
   if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0) return CZ_ERR_ARG;
@@ -51,6 +54,120 @@ int check(const cz_params *p, Shape *sh)
     sh->data0 = (HEADER_BYTES + 8ull * (nb + 1) + 15) / 16 * 16;
   }
   return CZ_OK;
+}
+
+// ---- strict error bound (host, fp64, every sum in increasing index order)
+// One level of the 1D inverse transform on f[0..n): the same steps as the
+// kernels (undo the W4li update, add back the W4 prediction; W3ai: even
+// sample A_k + d_k, odd sample 2 a_k minus it).
+void inv1d_host(int kind, double *f, int n)
+{
+  const int m = n / 2;
+  double c[32], d[32], o[32];
+  for (int k = 0; k < m; ++k) {
+    c[k] = f[2 * k];
+    d[k] = f[2 * k + 1];
+  }
+  if (kind == CZ_W4 || kind == CZ_W4LI) {
+    if (kind == CZ_W4LI) {
+      double e[32];
+      for (int j = 0; j < m; ++j) {
+        const czd::LiSrc ls = czd::li_src(j, m);
+        double acc = czd::li_weight<double>(m, j, 0) * d[ls.k0];
+        for (int t = 1; t < ls.nt; ++t) acc = acc + czd::li_weight<double>(m, j, t) * d[ls.k0 + t];
+        e[j] = c[j] - acc;
+      }
+      for (int j = 0; j < m; ++j) c[j] = e[j];
+    }
+    for (int k = 0; k < m; ++k) {
+      const czd::W4Row r = czd::w4_row(k, m);
+      double pr = (double)r.w[0] * c[r.j0];
+      pr = pr + (double)r.w[1] * c[r.j0 + 1];
+      pr = pr + (double)r.w[2] * c[r.j0 + 2];
+      pr = pr + (double)r.w[3] * c[r.j0 + 3];
+      o[k] = d[k] + pr * 0.0625;
+    }
+  } else {
+    double e[32];
+    for (int k = 0; k < m; ++k) {
+      double q;
+      if (k == 0) {
+        q = 3.0 * c[0];
+        q = q - 4.0 * c[1];
+        q = q + c[2];
+      } else if (k == m - 1) {
+        q = -3.0 * c[m - 1];
+        q = q + 4.0 * c[m - 2];
+        q = q - c[m - 3];
+      } else {
+        q = c[k - 1] - c[k + 1];
+      }
+      e[k] = (c[k] + q * 0.125) + d[k];
+    }
+    for (int k = 0; k < m; ++k) o[k] = 2.0 * c[k] - e[k];
+    for (int k = 0; k < m; ++k) c[k] = e[k];
+  }
+  for (int k = 0; k < m; ++k) {
+    f[2 * k] = c[k];
+    f[2 * k + 1] = o[k];
+  }
+}
+
+// C = max over the positions i of a block of sum_j |S_ij| over the detail
+// columns j of the block synthesis S.  A level-l detail is rebuilt by the
+// syntheses of levels l..0 only, whose composition is the Kronecker cube of
+// a B x (B >> l) matrix; its columns' row sums are products of the 1D row
+// sums over all columns (R) and over the even (coarse) columns (E).
+double synthesis_norm_uncached(int kind, int B)
+{
+  int L = 0;
+  while ((B >> L) > 4) ++L;
+  double R[3][32], E[3][32];
+  for (int l = 0; l < L; ++l) {
+    const int nl = B >> l;
+    for (int x = 0; x < B; ++x) R[l][x] = E[l][x] = 0.0;
+    for (int j = 0; j < nl; ++j) {
+      double w[32] = {0};
+      w[j] = 1.0;
+      for (int k = l; k >= 0; --k) {
+        const int nk = B >> k;
+        inv1d_host(kind, w, nk);
+        if (k > 0) {
+          double u[32] = {0};
+          for (int i = 0; i < nk; ++i) u[2 * i] = w[i];
+          for (int i = 0; i < 2 * nk; ++i) w[i] = u[i];
+        }
+      }
+      for (int x = 0; x < B; ++x) {
+        const double a = std::fabs(w[x]);
+        R[l][x] += a;
+        if (!(j & 1)) E[l][x] += a;
+      }
+    }
+  }
+  double C = 0.0;
+  for (int iz = 0; iz < B; ++iz)
+    for (int iy = 0; iy < B; ++iy)
+      for (int ix = 0; ix < B; ++ix) {
+        double sum = 0.0;
+        for (int l = 0; l < L; ++l) sum += (R[l][ix] * R[l][iy]) * R[l][iz] - (E[l][ix] * E[l][iy]) * E[l][iz];
+        if (sum > C) C = sum;
+      }
+  return C;
+}
+
+// divisor of the threshold for p: 1 (paper bound) or C (strict bound),
+// computed once per (kind, B)
+double threshold_divisor(const cz_params *p)
+{
+  if (p->bound_mode != CZ_BOUND_STRICT) return 1.0;
+  static std::mutex mu;
+  static double cache[3][3] = {{0}};
+  const int bi = p->block == 8 ? 0 : (p->block == 16 ? 1 : 2);
+  std::lock_guard<std::mutex> lock(mu);
+  double &c = cache[p->kind][bi];
+  if (c == 0.0) c = synthesis_norm_uncached(p->kind, p->block);
+  return c;
 }
 
 struct Lanes {
@@ -232,6 +349,7 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
   a.table = reinterpret_cast<unsigned long long *>(wsb + wl.table);
   a.eps = p->eps;
   a.range = p->range;
+  a.cnorm = threshold_divisor(p);
   a.nx = p->nx;
   a.ny = p->ny;
   a.nz = p->nz;
@@ -257,6 +375,8 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
   pa.data0 = sh.data0;
   pa.eps = p->eps;
   pa.range = p->range;
+  pa.cnorm = a.cnorm;
+  pa.bound_mode = p->bound_mode;
   pa.nx = p->nx;
   pa.ny = p->ny;
   pa.nz = p->nz;
@@ -280,6 +400,17 @@ int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out
                 uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes, void *stream)
 {
   return compress_impl(p, d_field, d_out, out_cap, d_out_bytes, d_ws, ws_bytes, stream, nullptr);
+}
+
+// Not part of the ABI: the strict-bound divisor C of (kind, B), for tests.
+double czi_synthesis_norm(int kind, int block)
+{
+  if (kind < CZ_W4 || kind > CZ_W3AI || (block != 8 && block != 16 && block != 32)) return -1.0;
+  cz_params p{};
+  p.kind = kind;
+  p.block = block;
+  p.bound_mode = CZ_BOUND_STRICT;
+  return threshold_divisor(&p);
 }
 
 // Not part of the ABI: cz_compress with four CUDA events recorded on
@@ -317,6 +448,7 @@ int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used)
   q.kind = h[22];
   q.stage2 = h[23];
   q.eps_mode = h[24];
+  q.bound_mode = h[26];
   std::memcpy(&q.eps, h + 32, 8);
   std::memcpy(&q.range, h + 64, 8);
   if (std::isnan(q.range)) return CZ_ERR_CORRUPT;

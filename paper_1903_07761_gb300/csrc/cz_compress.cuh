@@ -39,9 +39,9 @@ struct PlaceArgs {
   unsigned long long *out_bytes;  // may be null
   void *ws;
   unsigned long long out_cap, data0;
-  double eps, range;
+  double eps, range, cnorm;
   int nx, ny, nz, nblocks;
-  int block, levels, eps_mode, stage2, kind, dtype;
+  int block, levels, eps_mode, stage2, kind, dtype, bound_mode;
 };
 
 constexpr int PLACE_TILE = 128;  // chunks (and threads) per k_place CTA
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
 
   double mn, mx, range;
   T t;
-  threshold_of<T>(a.eps, a.eps_mode, a.range, ws, mn, mx, range, t);
+  threshold_of<T>(a.eps, a.eps_mode, a.cnorm, a.range, ws, mn, mx, range, t);
   const bool cE = (x0 % Q == 0) && (y % Q == 0);  // this column pair holds coarse values (E)
   unsigned cmask = 0;
 #pragma unroll
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(PLACE_TILE) k_place(const PlaceArgs a)
   if (tid == 0 && c0 + n == a.nblocks) {
     double mn, mx, range;
     T t;
-    threshold_of<T>(a.eps, a.eps_mode, a.range, ws, mn, mx, range, t);
+    threshold_of<T>(a.eps, a.eps_mode, a.cnorm, a.range, ws, mn, mx, range, t);
     const unsigned long long data_bytes = excl + ttot, total = a.data0 + data_bytes;
     unsigned char *h = a.out;
     st_le<unsigned long long>(h + HEADER_BYTES + 8ull * a.nblocks, data_bytes);
@@ -383,6 +383,7 @@ __global__ void __launch_bounds__(PLACE_TILE) k_place(const PlaceArgs a)
     h[23] = (unsigned char)a.stage2;
     h[24] = (unsigned char)a.eps_mode;
     h[25] = (unsigned char)a.levels;
+    h[26] = (unsigned char)a.bound_mode;
     st_le<unsigned>(h + 28, (unsigned)a.nblocks);
     st_le_f64(h + 32, a.eps);
     st_le_f64(h + 40, (double)t);

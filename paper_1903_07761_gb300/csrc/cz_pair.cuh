@@ -56,7 +56,7 @@ struct FwdArgs {
   unsigned char *staging;     // raw payloads, one arena per CTA
   unsigned long long *table;  // per block: staging offset, nnz
   unsigned long long arena_bytes;
-  double eps, range;
+  double eps, range, cnorm;
   int nx, ny, nz, nbx, nby, nbz, nblocks;
   int eps_mode, stage2, kind, dtype;
 };
@@ -865,8 +865,8 @@ __device__ __forceinline__ unsigned get_row(const unsigned char *mask, int z, in
 }
 
 template <typename T>
-__device__ __forceinline__ void threshold_of(double eps, int eps_mode, double range_in, const WsHdr *ws,
-                                             double &mn, double &mx, double &range, T &t)
+__device__ __forceinline__ void threshold_of(double eps, int eps_mode, double cnorm, double range_in,
+                                             const WsHdr *ws, double &mn, double &mx, double &range, T &t)
 {
   if (range_in >= 0) {
     range = range_in;
@@ -880,7 +880,8 @@ __device__ __forceinline__ void threshold_of(double eps, int eps_mode, double ra
     mx = (double)(T)((T)mx + (T)0);
     range = (mn <= mx) ? mx - mn : 0.0;
   }
-  const double td = eps_mode == 1 ? eps : eps * range;
+  // cnorm = 1 (paper bound) or the synthesis norm C (strict bound)
+  const double td = (eps_mode == 1 ? eps : eps * range) / cnorm;
   t = (T)td;
 }
 

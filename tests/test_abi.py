@@ -109,3 +109,24 @@ def test_read_header_of_an_oracle_stream(cz):
     bad[28] ^= 1  # block count disagrees with the dims
     with pytest.raises(cz.CzError):
         cz.cz_read_header(bytes(bad))
+
+
+def test_strict_divisor_equals_the_oracles(cz):
+    """The library computes the strict-bound divisor C on the host in the
+    same operation order as the oracle; equal C gives equal thresholds."""
+    L = cz.lib()
+    L.czi_synthesis_norm.argtypes = [C.c_int, C.c_int]
+    L.czi_synthesis_norm.restype = C.c_double
+    for kind in (O.W4, O.W4LI, O.W3AI):
+        for B in (8, 16, 32):
+            assert L.czi_synthesis_norm(kind, B) == O.synthesis_norm(kind, B)
+
+
+def test_bound_mode_and_flags_are_checked(cz):
+    p = cz.params_for((32, 32, 32), False, 32, "w4", 1e-3, cz.EPS_REL, True, 1.0, bound_mode=2)
+    with pytest.raises(cz.CzError):
+        cz.cz_compress_bound(p)
+    p = cz.params_for((32, 32, 32), False, 32, "w4", 1e-3, cz.EPS_REL, True, 1.0)
+    p.flags = 1
+    with pytest.raises(cz.CzError):
+        cz.cz_compress_bound(p)

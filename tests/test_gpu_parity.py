@@ -64,6 +64,23 @@ def test_stream_and_decode_bit_identical(dtype, block, shape, kind, stage2):
 
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("dtype,block,shape", CASES)
+def test_strict_bound_mode(dtype, block, shape, kind):
+    """Strict bound: threshold eps * range / C; the stream equals the oracle's
+    and the decoded error stays below eps * range."""
+    f = smooth_field(shape, dtype, seed=11 + kind)
+    eps = 1e-2
+    ref = O.compress(f, block, kind, eps, bound_mode=O.BOUND_STRICT)
+    got = gpu_compress(f, block, kind, eps, bound_mode=O.BOUND_STRICT)
+    assert got == ref, describe_diff(got, ref)
+    rec = gpu_decompress(got)
+    np.testing.assert_array_equal(rec.view(np.uint8), O.decompress(ref).view(np.uint8))
+    rng_ = float(f.max()) - float(f.min())
+    ulp = np.finfo(dtype).eps * float(np.abs(f).max()) * 8  # rounding of the reconstruction itself
+    assert np.abs(rec.astype(np.float64) - f.astype(np.float64)).max() <= eps * rng_ + ulp
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("dtype,block,shape", CASES)
 def test_eps_zero_and_huge(dtype, block, shape, kind):
     f = smooth_field(shape, dtype, seed=7)
     for eps, mode in ((0.0, O.EPS_REL), (1e300, O.EPS_ABS)):
