@@ -146,6 +146,37 @@ int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header,
 int cz_compress_noalloc(const cz_params *p, const void *d_field, void *d_out,
                         size_t out_cap, uint64_t *d_out_bytes, void *stream);
 
+/* ---- many fields in one call (the paper compresses many blocks of many
+ * quantities per node, Sec. 2.2; here whole fields are batched) ----------
+ * Fields with the same dtype, block, kind, stage2 and bound_mode (at most
+ * 32 at a time, in the order given) share one persistent launch of each
+ * kernel: their blocks form one index space, each block finds its field,
+ * and every field still gets its own stream, identical byte for byte to the
+ * one cz_compress would write.  Field i is d_fields[i] (parameters p[i]),
+ * its stream goes to d_outs[i] (capacity out_caps[i], length to
+ * d_out_bytes[i], a device array of n u64, may be NULL).  The call makes no
+ * allocation and no synchronisation; with its parameters fixed it can be
+ * captured in a CUDA graph once a call outside the capture has set up the
+ * kernels.  Errors as for cz_compress; the status word is shared.
+ * Host-side: d_ws must hold cz_batch_workspace_size() bytes (the largest
+ * group's workspace; groups run one after another and reuse it). */
+int cz_batch_workspace_size(int n, const cz_params *p, size_t *bytes);
+int cz_compress_batch(int n, const cz_params *p, const void *const *d_fields,
+                      void *const *d_outs, const size_t *out_caps,
+                      uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes,
+                      void *stream);
+
+/* Autotuner of the batched launch: times cz_compress_batch on these very
+ * arguments under each candidate block-to-CTA mapping (a stage grid of one
+ * CTA per SM, or the fewest CTAs that keep the same number of rounds) and
+ * stage-2 grid size (all resident CTAs, or half), `reps` timed calls each
+ * after one warm-up, and keeps the fastest for later calls with the same
+ * field parameters.  Synchronises `stream`.  The outputs are overwritten. */
+int cz_batch_tune(int n, const cz_params *p, const void *const *d_fields,
+                  void *const *d_outs, const size_t *out_caps,
+                  uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes,
+                  void *stream, int reps);
+
 /* Parse a host copy of a stream header into *p (and the threshold used). */
 int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used);
 

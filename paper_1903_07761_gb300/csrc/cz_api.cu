@@ -11,6 +11,8 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "../../include/cz.h"
 #include "cz_compress.cuh"
@@ -173,14 +175,20 @@ double threshold_divisor(const cz_params *p)
 struct Lanes {
   cudaError_t (*compress)(int, const CUtensorMap *, const FwdArgs *, const S2Args *, const PlaceArgs *, int, int,
                           int, const cudaEvent_t *, cudaStream_t);
+  cudaError_t (*compress_batch)(int, const StageMaps<MAXF> *, const FwdArgs *, const S2Args *, const BatchOut *,
+                                const PlaceArgs *, int, int, int, int, cudaStream_t);
   cudaError_t (*decompress)(int, const InvArgs *, const UnArgs *, int, int, int, cudaStream_t);
   cudaError_t (*dense)(int, int, const DenseArgs *, int, cudaStream_t);
   int (*occupancy)(int, int);
   int (*slot_bytes)();
 };
 
-#define CZ_LANES(sfx) \
-  Lanes { czl_compress_##sfx, czl_decompress_##sfx, czl_dense_##sfx, czl_occupancy_##sfx, czl_slot_bytes_##sfx }
+#define CZ_LANES(sfx)                                                                                      \
+  Lanes                                                                                                    \
+  {                                                                                                        \
+    czl_compress_##sfx, czl_compress_batch_##sfx, czl_decompress_##sfx, czl_dense_##sfx, czl_occupancy_##sfx, \
+        czl_slot_bytes_##sfx                                                                               \
+  }
 
 Lanes lanes_for(int dtype, int B)
 {
@@ -279,6 +287,230 @@ cudaError_t run_minmax(const void *field, size_t n, WsHdr *ws, cudaStream_t s)
   if (blocks == 0) blocks = 1;
   k_minmax<T><<<(unsigned)blocks, 512, 0, s>>>(reinterpret_cast<const T *>(field), n, ws);
   return cudaGetLastError();
+}
+
+// ---- batched compression
+// fields of one launch: same element type, block, kind, stage 2 and bound
+// mode, at most MAXF, in the order the caller gave them
+struct Group {
+  std::vector<int> idx;
+};
+
+std::vector<Group> plan_batch(int n, const cz_params *p)
+{
+  std::vector<Group> out;
+  std::vector<int> open;  // index in `out` of the last group of each signature
+  auto same = [&](const cz_params &a, const cz_params &b) {
+    return a.dtype == b.dtype && a.block == b.block && a.kind == b.kind && a.stage2 == b.stage2 &&
+           a.bound_mode == b.bound_mode;
+  };
+  for (int i = 0; i < n; ++i) {
+    int g = -1;
+    for (int q : open)
+      if (same(p[out[q].idx[0]], p[i]) && (int)out[q].idx.size() < MAXF) g = q;
+    if (g < 0) {
+      out.push_back(Group{});
+      g = (int)out.size() - 1;
+      open.push_back(g);
+    }
+    out[g].idx.push_back(i);
+  }
+  return out;
+}
+
+// knobs chosen by cz_batch_tune for a batch signature
+struct BatchKnobs {
+  int s1_balanced;  // stage grid: fewest CTAs with the same number of rounds
+  int s2_div;       // stage-2 CTAs: resident slots / s2_div
+};
+
+struct BatchLayout {
+  size_t keys, lb, table, staging, total, arena;
+  int grid, grid2, grid3, tiles, nblocks;
+};
+
+BatchLayout batch_layout(const Group &g, const cz_params *p, const BatchKnobs &kn)
+{
+  const cz_params &p0 = p[g.idx[0]];
+  BatchLayout w{};
+  w.nblocks = 0;
+  w.tiles = 0;
+  for (int i : g.idx) {
+    Shape sh;
+    check(&p[i], &sh);
+    w.nblocks += sh.nblocks;
+    w.tiles += (sh.nblocks + PLACE_TILE - 1) / PLACE_TILE;
+  }
+  Shape all{};
+  all.nblocks = w.nblocks;
+  w.grid = grid_for(&p0, all, 0);
+  if (kn.s1_balanced) {
+    const int rounds = (w.nblocks + w.grid - 1) / w.grid;
+    w.grid = (w.nblocks + rounds - 1) / rounds;
+  }
+  w.grid2 = grid_for(&p0, all, 2) / (kn.s2_div > 0 ? kn.s2_div : 1);
+  w.grid3 = grid_for(&p0, all, 3) / (kn.s2_div > 0 ? kn.s2_div : 1);
+  if (w.grid2 < 1) w.grid2 = 1;
+  if (w.grid3 < 1) w.grid3 = 1;
+  const Lanes L = lanes_for(p0.dtype, p0.block);
+  w.keys = WS_HDR;
+  w.lb = w.keys + 16 * MAXF;
+  w.table = w.lb + (8ull * w.tiles + 255) / 256 * 256;
+  w.staging = w.table + (16ull * w.nblocks + 255) / 256 * 256;
+  w.arena = (((size_t)w.nblocks + w.grid - 1) / w.grid) * (size_t)L.slot_bytes();
+  w.total = w.staging + w.arena * (size_t)w.grid;
+  return w;
+}
+
+std::mutex g_knob_mu;
+std::vector<std::pair<unsigned long long, BatchKnobs>> g_knobs;
+
+// signature of a batch: the parameters of every field (not the pointers)
+unsigned long long batch_signature(int n, const cz_params *p)
+{
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](unsigned long long v) { h = (h ^ v) * 1099511628211ull; };
+  mix((unsigned long long)n);
+  for (int i = 0; i < n; ++i) {
+    mix((unsigned long long)p[i].nx);
+    mix((unsigned long long)p[i].ny);
+    mix((unsigned long long)p[i].nz);
+    mix((unsigned long long)(p[i].block | p[i].dtype << 8 | p[i].kind << 12 | p[i].stage2 << 16 |
+                             p[i].bound_mode << 20));
+  }
+  return h;
+}
+
+BatchKnobs knobs_for(int n, const cz_params *p)
+{
+  const unsigned long long sig = batch_signature(n, p);
+  std::lock_guard<std::mutex> lock(g_knob_mu);
+  for (auto &e : g_knobs)
+    if (e.first == sig) return e.second;
+  return BatchKnobs{0, 1};
+}
+
+void set_knobs(int n, const cz_params *p, const BatchKnobs &k)
+{
+  const unsigned long long sig = batch_signature(n, p);
+  std::lock_guard<std::mutex> lock(g_knob_mu);
+  for (auto &e : g_knobs)
+    if (e.first == sig) {
+      e.second = k;
+      return;
+    }
+  g_knobs.push_back({sig, k});
+}
+
+size_t batch_ws_need(int n, const cz_params *p, const BatchKnobs &kn)
+{
+  size_t need = WS_HDR;
+  for (const Group &g : plan_batch(n, p)) {
+    const BatchLayout w = batch_layout(g, p, kn);
+    need = w.total > need ? w.total : need;
+  }
+  return need;
+}
+
+int compress_batch_impl(int n, const cz_params *p, const void *const *d_fields, void *const *d_outs,
+                        const size_t *out_caps, uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes,
+                        cudaStream_t s, const BatchKnobs &kn)
+{
+  if (n < 0 || (n > 0 && (!p || !d_fields || !d_outs || !out_caps)) || !d_ws) return CZ_ERR_ARG;
+  if ((uintptr_t)d_ws % 16) return CZ_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    Shape sh;
+    const int r = check(&p[i], &sh);
+    if (r != CZ_OK) return r;
+    if (!d_fields[i] || !d_outs[i] || ((uintptr_t)d_fields[i] % 16) || ((uintptr_t)d_outs[i] % 16))
+      return CZ_ERR_ARG;
+    if (out_caps[i] < sh.data0) return CZ_ERR_CAPACITY;
+  }
+  if (ws_bytes < batch_ws_need(n, p, kn)) return CZ_ERR_CAPACITY;
+  unsigned char *wsb = reinterpret_cast<unsigned char *>(d_ws);
+  if (cudaMemsetAsync(d_ws, 0, 4, s) != cudaSuccess) return CZ_ERR_CUDA;  // status, once for the batch
+  for (const Group &g : plan_batch(n, p)) {
+    const cz_params &p0 = p[g.idx[0]];
+    const BatchLayout w = batch_layout(g, p, kn);
+    const int nf = (int)g.idx.size();
+    // ticket, min/max keys (min keys all ones) and look-back words
+    if (cudaMemsetAsync(wsb + 4, 0, w.table - 4, s) != cudaSuccess) return CZ_ERR_CUDA;
+    if (cudaMemset2DAsync(wsb + w.keys, 16, 0xFF, 8, nf, s) != cudaSuccess) return CZ_ERR_CUDA;
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(wsb + w.keys);
+    MinmaxArgs mm{};
+    mm.keys = keys;
+    unsigned long long maxn = 0;
+    StageMaps<MAXF> maps{};
+    BatchOut bo{};
+    bo.nf = nf;
+    int first = 0, tfirst = 0;
+    for (int f = 0; f < nf; ++f) {
+      const int i = g.idx[f];
+      Shape sh;
+      check(&p[i], &sh);
+      const bool need_range = p[i].range < 0 && p[i].eps_mode == CZ_EPS_REL;
+      mm.field[f] = d_fields[i];
+      mm.n[f] = need_range ? (unsigned long long)p[i].nx * p[i].ny * p[i].nz : 0ull;
+      maxn = mm.n[f] > maxn ? mm.n[f] : maxn;
+      if (!make_tile_map(&maps.tm[f], &p[i], d_fields[i])) return CZ_ERR_CUDA;
+      maps.g[f] = FieldGeo{sh.nbx, sh.nby, first, p[i].eps_mode, p[i].eps, p[i].range};
+      FieldOut &fo = bo.f[f];
+      fo.out = reinterpret_cast<unsigned char *>(d_outs[i]);
+      fo.out_bytes = d_out_bytes ? reinterpret_cast<unsigned long long *>(d_out_bytes + i) : nullptr;
+      fo.out_cap = out_caps[i];
+      fo.data0 = sh.data0;
+      fo.eps = p[i].eps;
+      fo.range_in = p[i].range;
+      fo.nx = p[i].nx;
+      fo.ny = p[i].ny;
+      fo.nz = p[i].nz;
+      fo.nblocks = sh.nblocks;
+      fo.first = first;
+      fo.tfirst = tfirst;
+      fo.eps_mode = p[i].eps_mode;
+      first += sh.nblocks;
+      tfirst += (sh.nblocks + PLACE_TILE - 1) / PLACE_TILE;
+    }
+    if (maxn > 0) {
+      const dim3 grid((unsigned)((maxn + MM_CHUNK - 1) / MM_CHUNK), (unsigned)nf);
+      if (p0.dtype == CZ_F32)
+        k_minmax_multi<float><<<grid, 512, 0, s>>>(mm);
+      else
+        k_minmax_multi<double><<<grid, 512, 0, s>>>(mm);
+      if (cudaGetLastError() != cudaSuccess) return CZ_ERR_CUDA;
+    }
+    FwdArgs a{};
+    a.ws = d_ws;
+    a.keys = keys;
+    a.staging = wsb + w.staging;
+    a.arena_bytes = w.arena;
+    a.table = reinterpret_cast<unsigned long long *>(wsb + w.table);
+    a.cnorm = threshold_divisor(&p0);
+    a.nblocks = w.nblocks;
+    a.nf = nf;
+    S2Args sa{};
+    sa.staging = a.staging;
+    sa.table = a.table;
+    sa.nblocks = w.nblocks;
+    PlaceArgs pa{};
+    pa.staging = a.staging;
+    pa.table = a.table;
+    pa.keys = keys;
+    pa.lbst = reinterpret_cast<unsigned long long *>(wsb + w.lb);
+    pa.ws = d_ws;
+    pa.cnorm = a.cnorm;
+    pa.nblocks = w.nblocks;
+    pa.block = p0.block;
+    pa.levels = p0.block == 8 ? 1 : (p0.block == 16 ? 2 : 3);
+    pa.stage2 = p0.stage2;
+    pa.kind = p0.kind;
+    pa.dtype = p0.dtype;
+    pa.bound_mode = p0.bound_mode;
+    const Lanes L = lanes_for(p0.dtype, p0.block);
+    if (L.compress_batch(p0.kind, &maps, &a, &sa, &bo, &pa, w.grid, w.grid2, w.grid3, w.tiles, s) != cudaSuccess)
+      return CZ_ERR_CUDA;
+  }
+  return CZ_OK;
 }
 
 unsigned long long rd64(const unsigned char *p)
@@ -400,6 +632,63 @@ int cz_compress(const cz_params *p, const void *d_field, void *d_out, size_t out
                 uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes, void *stream)
 {
   return compress_impl(p, d_field, d_out, out_cap, d_out_bytes, d_ws, ws_bytes, stream, nullptr);
+}
+
+int cz_batch_workspace_size(int n, const cz_params *p, size_t *bytes)
+{
+  if (n < 0 || !bytes || (n > 0 && !p)) return CZ_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (check(&p[i], nullptr) != CZ_OK) return CZ_ERR_ARG;
+  // room for every knob setting the tuner may pick
+  const size_t a = batch_ws_need(n, p, BatchKnobs{0, 1}), b = batch_ws_need(n, p, BatchKnobs{1, 1});
+  *bytes = a > b ? a : b;
+  return CZ_OK;
+}
+
+int cz_compress_batch(int n, const cz_params *p, const void *const *d_fields, void *const *d_outs,
+                      const size_t *out_caps, uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes, void *stream)
+{
+  return compress_batch_impl(n, p, d_fields, d_outs, out_caps, d_out_bytes, d_ws, ws_bytes,
+                             reinterpret_cast<cudaStream_t>(stream), knobs_for(n, p));
+}
+
+int cz_batch_tune(int n, const cz_params *p, const void *const *d_fields, void *const *d_outs,
+                  const size_t *out_caps, uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes, void *stream,
+                  int reps)
+{
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const BatchKnobs cand[4] = {{0, 1}, {1, 1}, {0, 2}, {1, 2}};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return CZ_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return CZ_ERR_CUDA;
+  }
+  int best = -1;
+  float best_ms = 0;
+  int r = CZ_OK;
+  for (int c = 0; c < 4 && r == CZ_OK; ++c) {
+    r = compress_batch_impl(n, p, d_fields, d_outs, out_caps, d_out_bytes, d_ws, ws_bytes, s, cand[c]);  // warm
+    if (r != CZ_OK) break;
+    if (cudaEventRecord(e0, s) != cudaSuccess) r = CZ_ERR_CUDA;
+    for (int q = 0; q < (reps > 0 ? reps : 3) && r == CZ_OK; ++q)
+      r = compress_batch_impl(n, p, d_fields, d_outs, out_caps, d_out_bytes, d_ws, ws_bytes, s, cand[c]);
+    if (r != CZ_OK) break;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      r = CZ_ERR_CUDA;
+      break;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best < 0 || ms < best_ms) {
+      best = c;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (r == CZ_OK && best >= 0) set_knobs(n, p, cand[best]);
+  return r;
 }
 
 // Not part of the ABI: the strict-bound divisor C of (kind, B), for tests.

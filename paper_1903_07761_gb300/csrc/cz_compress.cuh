@@ -35,6 +35,8 @@ struct S2Args {
 struct PlaceArgs {
   const unsigned char *staging;
   const unsigned long long *table;
+  const unsigned long long *keys;  // batched: min/max keys, two per field
+  unsigned long long *lbst;        // batched: look-back words, one per tile
   unsigned char *out;
   unsigned long long *out_bytes;  // may be null
   void *ws;
@@ -46,8 +48,20 @@ struct PlaceArgs {
 
 constexpr int PLACE_TILE = 128;  // chunks (and threads) per k_place CTA
 
-template <typename T, int B, int KIND>
-__global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__ CUtensorMap tmap, const FwdArgs a)
+// field of global block bid among the nf fields of a batched launch
+template <int NF>
+__device__ __forceinline__ int field_of(const StageMaps<NF> &maps, int nf, int bid)
+{
+  int f = 0;
+  for (int q = 1; q < nf; ++q)
+    if (maps.g[q].first <= bid) f = q;
+  return f;
+}
+
+// NF = 1: one field described by a; NF > 1: up to NF fields of one group,
+// their blocks numbered consecutively (field by field) in one index space
+template <typename T, int B, int KIND, int NF>
+__global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__ StageMaps<NF> maps, const FwdArgs a)
 {
   using G = G2<T, B>;
   using T2 = typename V2T<T>::type;
@@ -72,7 +86,15 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
 
   double mn, mx, range;
   T t;
-  threshold_of<T>(a.eps, a.eps_mode, a.cnorm, a.range, ws, mn, mx, range, t);
+  __shared__ T s_t[NF];
+  if constexpr (NF == 1) {
+    threshold_of<T>(a.eps, a.eps_mode, a.cnorm, a.range, ws, mn, mx, range, t);
+  } else if (tid < a.nf) {
+    T tf;
+    threshold_keys<T>(maps.g[tid].eps, maps.g[tid].eps_mode, a.cnorm, maps.g[tid].range_in, a.keys + 2 * tid, mn,
+                      mx, range, tf);
+    s_t[tid] = tf;
+  }
   const bool cE = (x0 % Q == 0) && (y % Q == 0);  // this column pair holds coarse values (E)
   unsigned cmask = 0;
 #pragma unroll
@@ -80,8 +102,15 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
   unsigned char *arena = a.staging + (size_t)blockIdx.x * a.arena_bytes;
 
   auto tile_of = [&](int bid) {
-    const int bx = bid % a.nbx, by = (bid / a.nbx) % a.nby, bz = bid / (a.nbx * a.nby);
-    tma_load_tile(&tmap, PF, &s_bar, bx * B, by * B, bz * B, G::TILE);
+    int f = 0, lb = bid, nbx = a.nbx, nby = a.nby;
+    if constexpr (NF > 1) {
+      f = field_of<NF>(maps, a.nf, bid);
+      lb = bid - maps.g[f].first;
+      nbx = maps.g[f].nbx;
+      nby = maps.g[f].nby;
+    }
+    const int bx = lb % nbx, by = (lb / nbx) % nby, bz = lb / (nbx * nby);
+    tma_load_tile(&maps.tm[f], PF, &s_bar, bx * B, by * B, bz * B, G::TILE);
   };
   if (tid == 0) {
     s_aoff = 0;
@@ -111,6 +140,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     fwd_all<T, B, KIND>(v, X, AD, ap, y, seg);
 
     // ---- significance bits over z, mask row words by bit transpose
+    if constexpr (NF > 1) t = s_t[field_of<NF>(maps, a.nf, bid)];
     unsigned me = 0, mo = 0;
 #pragma unroll
     for (int z = 0; z < B; ++z) {
@@ -409,6 +439,120 @@ __global__ void __launch_bounds__(256) k_copy(const PlaceArgs a)
   if (a.data0 + off + cb > a.out_cap) return;
   const unsigned *__restrict__ src = reinterpret_cast<const unsigned *>(a.staging + so);
   unsigned *__restrict__ dst = reinterpret_cast<unsigned *>(a.out + a.data0 + off);
+  const unsigned nw = (unsigned)(cb >> 2);
+  constexpr int U = 8;
+  for (unsigned q0 = lane; q0 < nw; q0 += 32 * U) {
+    unsigned w[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) w[j] = q0 + 32 * j < nw ? src[q0 + 32 * j] : 0u;
+#pragma unroll
+    for (int j = 0; j < U; ++j)
+      if (q0 + 32 * j < nw) dst[q0 + 32 * j] = w[j];
+  }
+}
+
+// ---- batched placement: tiles of 128 chunks of one field; each field's
+// look-back segment starts at its first tile, each field gets its own
+// offset table and header
+template <int NF>
+__device__ __forceinline__ int field_of_tile(const BatchOut &bo, int tile)
+{
+  int f = 0;
+  for (int q = 1; q < bo.nf; ++q)
+    if (bo.f[q].tfirst <= tile) f = q;
+  return f;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PLACE_TILE) k_place_multi(const __grid_constant__ BatchOut bo, const PlaceArgs a)
+{
+  constexpr int PT = PLACE_TILE, NT = PLACE_TILE;
+  __shared__ unsigned s_u[40];
+  __shared__ int s_tile;
+  __shared__ unsigned long long s_excl;
+  WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
+  unsigned long long *lbst = a.lbst;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = (int)atomicAdd(&ws->ticket, 1u);  // earlier tiles are resident or done
+  __syncthreads();
+  const int tile = s_tile;
+  const int f = field_of_tile<MAXF>(bo, tile);
+  const FieldOut &fo = bo.f[f];
+  const int c0 = fo.first + (tile - fo.tfirst) * PT;  // first global chunk of the tile
+  const int cend = fo.first + fo.nblocks;
+  const int n = cend - c0 < PT ? cend - c0 : PT;
+  unsigned long long cb = 0;
+  if (tid < n) {
+    cb = a.table[2 * (c0 + tid) + 1];
+    if (cb == 0xFFFFFFFFFFFFFFFFull) {  // lost: leave an empty chunk
+      atomicCAS(&ws->status, 0u, ST_CAPACITY);
+      cb = 0;
+    }
+  }
+  unsigned ttot;
+  const unsigned loc = block_exsum<NT>((unsigned)cb, s_u, ttot);
+  if (tid < 32) {
+    const unsigned long long ex = lookback(lbst, tile, ttot, &ws->status, (int)ST_TIMEOUT, fo.tfirst);
+    if (tid == 0) s_excl = ex;
+  }
+  __syncthreads();
+  const unsigned long long excl = s_excl;
+  if (tid < n) {
+    const unsigned long long off = excl + loc;
+    st_le<unsigned long long>(fo.out + HEADER_BYTES + 8ull * (c0 - fo.first + tid), off);
+    if (fo.data0 + off + cb > fo.out_cap) atomicCAS(&ws->status, 0u, ST_CAPACITY);
+  }
+  if (tid == 0 && c0 + n == cend) {
+    double mn, mx, range;
+    T t;
+    threshold_keys<T>(fo.eps, fo.eps_mode, a.cnorm, fo.range_in, a.keys + 2 * f, mn, mx, range, t);
+    const unsigned long long data_bytes = excl + ttot, total = fo.data0 + data_bytes;
+    unsigned char *h = fo.out;
+    st_le<unsigned long long>(h + HEADER_BYTES + 8ull * fo.nblocks, data_bytes);
+    for (unsigned long long q = HEADER_BYTES + 8ull * (fo.nblocks + 1); q < fo.data0; ++q) h[q] = 0;
+    for (int q = 0; q < HEADER_BYTES; ++q) h[q] = 0;
+    st_le<unsigned>(h + 0, MAGIC);
+    st_le<unsigned short>(h + 4, 1);
+    st_le<unsigned short>(h + 6, HEADER_BYTES);
+    st_le<int>(h + 8, fo.nx);
+    st_le<int>(h + 12, fo.ny);
+    st_le<int>(h + 16, fo.nz);
+    h[20] = (unsigned char)a.block;
+    h[21] = (unsigned char)a.dtype;
+    h[22] = (unsigned char)a.kind;
+    h[23] = (unsigned char)a.stage2;
+    h[24] = (unsigned char)fo.eps_mode;
+    h[25] = (unsigned char)a.levels;
+    h[26] = (unsigned char)a.bound_mode;
+    st_le<unsigned>(h + 28, (unsigned)fo.nblocks);
+    st_le_f64(h + 32, fo.eps);
+    st_le_f64(h + 40, (double)t);
+    st_le_f64(h + 48, mn);
+    st_le_f64(h + 56, mx);
+    st_le_f64(h + 64, range);
+    st_le<unsigned long long>(h + 72, data_bytes);
+    st_le<unsigned long long>(h + 80, total);
+    if (fo.out_bytes) *fo.out_bytes = total;
+  }
+}
+
+// one warp per chunk of the batch: staging slot -> its field's stream
+template <typename T>
+__global__ void __launch_bounds__(256) k_copy_multi(const __grid_constant__ BatchOut bo, const PlaceArgs a)
+{
+  const int bid = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (bid >= a.nblocks) return;
+  int f = 0;
+  for (int q = 1; q < bo.nf; ++q)
+    if (bo.f[q].first <= bid) f = q;
+  const FieldOut &fo = bo.f[f];
+  const unsigned long long so = a.table[2 * bid], cb = a.table[2 * bid + 1];
+  if (cb == 0xFFFFFFFFFFFFFFFFull) return;
+  const unsigned long long off =
+      *reinterpret_cast<const unsigned long long *>(fo.out + HEADER_BYTES + 8ull * (bid - fo.first));
+  if (fo.data0 + off + cb > fo.out_cap) return;
+  const unsigned *__restrict__ src = reinterpret_cast<const unsigned *>(a.staging + so);
+  unsigned *__restrict__ dst = reinterpret_cast<unsigned *>(fo.out + fo.data0 + off);
   const unsigned nw = (unsigned)(cb >> 2);
   constexpr int U = 8;
   for (unsigned q0 = lane; q0 < nw; q0 += 32 * U) {

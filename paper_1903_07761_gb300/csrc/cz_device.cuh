@@ -563,20 +563,22 @@ constexpr unsigned LB_SPIN_LIMIT = 1u << 22;
 // On a wait that exceeds the spin limit, sets *status (if still 0) to
 // `timeout_code` and returns what it has: the caller's output is then
 // wrong but the kernel ends.
+// Indices below `first` count as an inclusive prefix of 0 (a segment of
+// the state array starts there).
 __device__ __forceinline__ unsigned long long lookback(unsigned long long *state, int bid,
                                                        unsigned long long agg,
-                                                       unsigned int *status, int timeout_code)
+                                                       unsigned int *status, int timeout_code, int first = 0)
 {
   const int lane = threadIdx.x & 31;
   using aref = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
-  if (lane == 0) aref(state[bid]).store((bid == 0 ? LB_PRE : LB_AGG) | agg, cuda::memory_order_relaxed);
+  if (lane == 0) aref(state[bid]).store((bid == first ? LB_PRE : LB_AGG) | agg, cuda::memory_order_relaxed);
   unsigned long long excl = 0;
   int base = bid;
   unsigned spins = 0;
-  while (base > 0) {
+  while (base > first) {
     const int j = base - 1 - lane;
-    unsigned long long s = LB_PRE;  // before block 0: prefix 0
-    if (j >= 0) s = aref(state[j]).load(cuda::memory_order_relaxed);
+    unsigned long long s = LB_PRE;  // before the segment: prefix 0
+    if (j >= first) s = aref(state[j]).load(cuda::memory_order_relaxed);
     const unsigned long long flag = s & ~LB_VAL;
     const unsigned pm = __ballot_sync(FULL, flag == LB_PRE);
     const unsigned im = __ballot_sync(FULL, flag == 0);
@@ -597,7 +599,7 @@ __device__ __forceinline__ unsigned long long lookback(unsigned long long *state
     if (pm) break;
     base -= 32;
   }
-  if (lane == 0 && bid != 0)
+  if (lane == 0 && bid != first)
     aref(state[bid]).store(LB_PRE | ((excl + agg) & LB_VAL), cuda::memory_order_relaxed);
   return excl;
 }

@@ -36,18 +36,11 @@ cudaError_t prepare(int smem)
   return e;
 }
 
-template <int KIND>
-cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const S2Args &sa, const PlaceArgs &pa, int grid,
-                       int grid2, int grid3, const cudaEvent_t *marks, cudaStream_t s)
+// stage 2 on every slot (small and large payloads), when enabled
+cudaError_t stage2_k(const S2Args &sa, int stage2, int grid2, int grid3, cudaStream_t s)
 {
-  cudaError_t e = prepare<k_stage1<CZ_T, CZ_B, KIND>>(G::SMEM_C);
-  if (e != cudaSuccess) return e;
-  if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
-  k_stage1<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_C, s>>>(tm, a);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (marks && (e = cudaEventRecord(marks[1], s)) != cudaSuccess) return e;
-  if (pa.stage2) {
+  cudaError_t e = cudaSuccess;
+  if (stage2) {
     e = prepare<k_stage2<CZ_T, CZ_B, false>>(G::SMEM_S2);
     if (e != cudaSuccess) return e;
     k_stage2<CZ_T, CZ_B, false><<<grid2, 128, G::SMEM_S2, s>>>(sa);
@@ -61,6 +54,23 @@ cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const S2Args &sa
       if (e != cudaSuccess) return e;
     }
   }
+  return e;
+}
+
+template <int KIND>
+cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const S2Args &sa, const PlaceArgs &pa, int grid,
+                       int grid2, int grid3, const cudaEvent_t *marks, cudaStream_t s)
+{
+  cudaError_t e = prepare<k_stage1<CZ_T, CZ_B, KIND, 1>>(G::SMEM_C);
+  if (e != cudaSuccess) return e;
+  StageMaps<1> maps{};
+  maps.tm[0] = tm;
+  if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
+  k_stage1<CZ_T, CZ_B, KIND, 1><<<grid, G::NT, G::SMEM_C, s>>>(maps, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (marks && (e = cudaEventRecord(marks[1], s)) != cudaSuccess) return e;
+  if ((e = stage2_k(sa, pa.stage2, grid2, grid3, s)) != cudaSuccess) return e;
   if (marks && (e = cudaEventRecord(marks[2], s)) != cudaSuccess) return e;
   const int tiles = (pa.nblocks + PLACE_TILE - 1) / PLACE_TILE;
   k_place<CZ_T><<<tiles, PLACE_TILE, 0, s>>>(pa);
@@ -70,6 +80,23 @@ cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const S2Args &sa
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (marks && (e = cudaEventRecord(marks[3], s)) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t compress_batch_k(const StageMaps<MAXF> &maps, const FwdArgs &a, const S2Args &sa, const BatchOut &bo,
+                             const PlaceArgs &pa, int grid, int grid2, int grid3, int tiles, cudaStream_t s)
+{
+  cudaError_t e = prepare<k_stage1<CZ_T, CZ_B, KIND, MAXF>>(G::SMEM_C);
+  if (e != cudaSuccess) return e;
+  k_stage1<CZ_T, CZ_B, KIND, MAXF><<<grid, G::NT, G::SMEM_C, s>>>(maps, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = stage2_k(sa, pa.stage2, grid2, grid3, s)) != cudaSuccess) return e;
+  k_place_multi<CZ_T><<<tiles, PLACE_TILE, 0, s>>>(bo, pa);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_copy_multi<CZ_T><<<(pa.nblocks + 7) / 8, 256, 0, s>>>(bo, pa);
   return cudaGetLastError();
 }
 
@@ -109,9 +136,9 @@ cudaError_t dense_k(const DenseArgs &a, int nblocks, cudaStream_t s)
 template <int KIND>
 int occupancy_c()
 {
-  if (prepare<k_stage1<CZ_T, CZ_B, KIND>>(G::SMEM_C) != cudaSuccess) return 0;
+  if (prepare<k_stage1<CZ_T, CZ_B, KIND, 1>>(G::SMEM_C) != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage1<CZ_T, CZ_B, KIND>, G::NT, G::SMEM_C) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage1<CZ_T, CZ_B, KIND, 1>, G::NT, G::SMEM_C) !=
       cudaSuccess)
     return 0;
   return n;
@@ -170,6 +197,18 @@ extern "C" cudaError_t CZ_CAT(czl_compress_, CZ_SUFFIX)(int kind, const CUtensor
   }
 }
 
+extern "C" cudaError_t CZ_CAT(czl_compress_batch_, CZ_SUFFIX)(int kind, const StageMaps<MAXF> *maps,
+                                                               const FwdArgs *a, const S2Args *sa,
+                                                               const BatchOut *bo, const PlaceArgs *pa, int grid,
+                                                               int grid2, int grid3, int tiles, cudaStream_t s)
+{
+  switch (kind) {
+    case W4: return compress_batch_k<W4>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, s);
+    case W4LI: return compress_batch_k<W4LI>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, s);
+    default: return compress_batch_k<W3AI>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, s);
+  }
+}
+
 extern "C" cudaError_t CZ_CAT(czl_decompress_, CZ_SUFFIX)(int kind, const InvArgs *a, const UnArgs *ua, int grid,
                                                            int gridu, int gridub, cudaStream_t s)
 {
@@ -200,7 +239,25 @@ extern "C" cudaError_t CZ_CAT(czl_dense_, CZ_SUFFIX)(int kind, int fwd, const De
 // CTAs per SM of the stage kernel (which = 0), the decompress kernel
 // (which = 1), the small (2) or large (3) stage-2 kernel, the small (4) or
 // large (5) stage-2 inverse kernel
+static int occupancy_query(int kind, int which);
+
+// cached per device: later calls (e.g. inside a stream capture) make no
+// CUDA call but cudaGetDevice
 extern "C" int CZ_CAT(czl_occupancy_, CZ_SUFFIX)(int kind, int which)
+{
+  static int cache[64][3][6];  // device, kind, which; 0 = not yet known
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || kind < 0 || kind > 2 || which < 0 ||
+      which > 5)
+    return occupancy_query(kind, which);
+  int v = __atomic_load_n(&cache[dev][kind][which], __ATOMIC_ACQUIRE);
+  if (v > 0) return v;
+  v = occupancy_query(kind, which);
+  if (v > 0) __atomic_store_n(&cache[dev][kind][which], v, __ATOMIC_RELEASE);
+  return v;
+}
+
+static int occupancy_query(int kind, int which)
 {
   if (which == 2) return occupancy_s2<false>();
   if (which == 3) return G::HAS_BIG ? occupancy_s2<true>() : 1;

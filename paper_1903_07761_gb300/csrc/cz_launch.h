@@ -10,6 +10,9 @@ struct UnArgs;
 struct DenseArgs;
 struct S2Args;
 struct PlaceArgs;
+struct BatchOut;
+template <int NF>
+struct StageMaps;
 }  // namespace czp
 
 #define CZ_DECLARE_LAUNCHERS(sfx)                                                                    \
@@ -17,6 +20,10 @@ struct PlaceArgs;
                                             const czp::S2Args *sa, const czp::PlaceArgs *pa,        \
                                             int grid, int grid2, int grid3,                         \
                                             const cudaEvent_t *marks, cudaStream_t s);              \
+  extern "C" cudaError_t czl_compress_batch_##sfx(                                                   \
+      int kind, const czp::StageMaps<32> *maps, const czp::FwdArgs *a, const czp::S2Args *sa,          \
+      const czp::BatchOut *bo, const czp::PlaceArgs *pa, int grid, int grid2, int grid3, int tiles,    \
+      cudaStream_t s);                                                                                  \
   extern "C" cudaError_t czl_decompress_##sfx(int kind, const czp::InvArgs *a, const czp::UnArgs *ua, \
                                               int grid, int gridu, int gridub, cudaStream_t s);       \
   extern "C" cudaError_t czl_dense_##sfx(int kind, int fwd, const czp::DenseArgs *a, int nblocks,   \

@@ -50,14 +50,47 @@ struct WsHdr {
   unsigned long long bump;  // staging bytes handed out so far
 };
 
+// ---- several fields in one launch (one group: same type, block, kind)
+constexpr int MAXF = 32;  // fields per batched launch
+
+// per-field geometry and threshold inputs of the stage kernel
+struct FieldGeo {
+  int nbx, nby, first;  // block grid (x, y) and the field's first global block
+  int eps_mode;
+  double eps, range_in;  // range_in < 0: range from this field's min/max keys
+};
+
+// tensor maps (and geometry) of the fields of one launch, passed by value
+template <int NF>
+struct StageMaps {
+  CUtensorMap tm[NF];
+  FieldGeo g[NF];
+};
+
+// per-field output description of the placement and copy kernels
+struct FieldOut {
+  unsigned char *out;
+  unsigned long long *out_bytes;  // device u64 or null
+  unsigned long long out_cap, data0;
+  double eps, range_in;
+  int nx, ny, nz, nblocks, first, tfirst;  // blocks, first global block, first global tile
+  int eps_mode;
+};
+
+struct BatchOut {
+  FieldOut f[MAXF];
+  int nf;
+};
+
 struct FwdArgs {
   const void *field;
   void *ws;
+  unsigned long long *keys;  // batched: min/max keys, two per field
   unsigned char *staging;     // raw payloads, one arena per CTA
   unsigned long long *table;  // per block: staging offset, nnz
   unsigned long long arena_bytes;
   double eps, range, cnorm;
-  int nx, ny, nz, nbx, nby, nbz, nblocks;
+  int nx, ny, nz, nbx, nby, nbz, nblocks, nf;
   int eps_mode, stage2, kind, dtype;
 };
 
@@ -865,15 +898,16 @@ __device__ __forceinline__ unsigned get_row(const unsigned char *mask, int z, in
 }
 
 template <typename T>
-__device__ __forceinline__ void threshold_of(double eps, int eps_mode, double cnorm, double range_in,
-                                             const WsHdr *ws, double &mn, double &mx, double &range, T &t)
+__device__ __forceinline__ void threshold_keys(double eps, int eps_mode, double cnorm, double range_in,
+                                               const unsigned long long *keys, double &mn, double &mx,
+                                               double &range, T &t)
 {
   if (range_in >= 0) {
     range = range_in;
     mn = mx = __longlong_as_double(0x7FF8000000000000LL);
   } else {
-    const unsigned long long kmin = *(volatile const unsigned long long *)&ws->minkey;
-    const unsigned long long kmax = *(volatile const unsigned long long *)&ws->maxkey;
+    const unsigned long long kmin = *(volatile const unsigned long long *)&keys[0];
+    const unsigned long long kmax = *(volatile const unsigned long long *)&keys[1];
     mn = key_value(kmin, T(0));
     mx = key_value(kmax, T(0));
     mn = (double)(T)((T)mn + (T)0);  // -0 reported as +0
@@ -883,6 +917,13 @@ __device__ __forceinline__ void threshold_of(double eps, int eps_mode, double cn
   // cnorm = 1 (paper bound) or the synthesis norm C (strict bound)
   const double td = (eps_mode == 1 ? eps : eps * range) / cnorm;
   t = (T)td;
+}
+
+template <typename T>
+__device__ __forceinline__ void threshold_of(double eps, int eps_mode, double cnorm, double range_in,
+                                             const WsHdr *ws, double &mn, double &mx, double &range, T &t)
+{
+  threshold_keys<T>(eps, eps_mode, cnorm, range_in, &ws->minkey, mn, mx, range, t);
 }
 
 // ============================================================ decompress
@@ -1200,12 +1241,13 @@ __global__ void __launch_bounds__(B * B / 2) k_dense2(const DenseArgs a)
 }
 
 // ============================================================ a0: min / max
+// min / max of xs[i], xs[i + stride], ... (< n), NaN never enters (every
+// comparison with NaN is false); lanes then combine and commit with atomics
 template <typename T>
-__global__ void __launch_bounds__(512) k_minmax(const T *__restrict__ xs, size_t n, WsHdr *ws)
+__device__ __forceinline__ void minmax_part(const T *__restrict__ xs, size_t n, size_t i, size_t stride,
+                                            unsigned long long *kmin, unsigned long long *kmax)
 {
   T lo = (T)INFINITY, hi = (T)-INFINITY;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if constexpr (sizeof(T) == 4) {
     const float4 *v4 = reinterpret_cast<const float4 *>(xs);
     const size_t n4 = n / 4;
@@ -1235,7 +1277,6 @@ __global__ void __launch_bounds__(512) k_minmax(const T *__restrict__ xs, size_t
       hi = q > hi ? q : hi;
     }
   }
-  // NaN never enters: every comparison with NaN is false
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const T l2 = __shfl_xor_sync(FULL, lo, o), h2 = __shfl_xor_sync(FULL, hi, o);
@@ -1243,9 +1284,36 @@ __global__ void __launch_bounds__(512) k_minmax(const T *__restrict__ xs, size_t
     hi = h2 > hi ? h2 : hi;
   }
   if ((threadIdx.x & 31) == 0) {
-    atomicMin(&ws->minkey, order_key(lo));
-    atomicMax(&ws->maxkey, order_key(hi));
+    atomicMin(kmin, order_key(lo));
+    atomicMax(kmax, order_key(hi));
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_minmax(const T *__restrict__ xs, size_t n, WsHdr *ws)
+{
+  minmax_part<T>(xs, n, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x,
+                 &ws->minkey, &ws->maxkey);
+}
+
+// batched: field blockIdx.y, chunk blockIdx.x of MM_CHUNK elements (an
+// even count, so vector loads stay aligned); keys[2f], keys[2f+1]
+constexpr size_t MM_CHUNK = 1u << 20;
+struct MinmaxArgs {
+  const void *field[MAXF];
+  unsigned long long n[MAXF];
+  unsigned long long *keys;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_minmax_multi(const __grid_constant__ MinmaxArgs a)
+{
+  const int f = blockIdx.y;
+  const size_t b0 = (size_t)blockIdx.x * MM_CHUNK;
+  if (b0 >= a.n[f]) return;
+  const size_t len = a.n[f] - b0 < MM_CHUNK ? a.n[f] - b0 : MM_CHUNK;
+  minmax_part<T>(reinterpret_cast<const T *>(a.field[f]) + b0, len, threadIdx.x, blockDim.x, &a.keys[2 * f],
+                 &a.keys[2 * f + 1]);
 }
 
 }  // namespace czp

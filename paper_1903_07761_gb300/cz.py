@@ -60,6 +60,11 @@ def lib():
             L.cz_compress.argtypes = [PP, P, P, C.c_size_t, P, P, C.c_size_t, P]
             L.cz_decompress.argtypes = [P, C.c_size_t, P, P, C.c_size_t, P, C.c_size_t, P]
             L.cz_compress_noalloc.argtypes = [PP, P, P, C.c_size_t, P, P]
+            L.cz_batch_workspace_size.argtypes = [C.c_int, PP, C.POINTER(C.c_size_t)]
+            L.cz_compress_batch.argtypes = [C.c_int, PP, C.POINTER(P), C.POINTER(P),
+                                            C.POINTER(C.c_size_t), P, P, C.c_size_t, P]
+            L.cz_batch_tune.argtypes = [C.c_int, PP, C.POINTER(P), C.POINTER(P),
+                                        C.POINTER(C.c_size_t), P, P, C.c_size_t, P, C.c_int]
             L.cz_read_header.argtypes = [P, C.c_size_t, PP, C.POINTER(C.c_double)]
             L.cz_status.argtypes = [P, P]
             L.cz_strerror.argtypes = [C.c_int]
@@ -67,7 +72,8 @@ def lib():
             L.cz_forward_dense.argtypes = [PP, P, P, P]
             L.cz_inverse_dense.argtypes = [PP, P, P, P]
             for f in (L.cz_compress_bound, L.cz_workspace_size, L.cz_compress, L.cz_decompress,
-                      L.cz_compress_noalloc, L.cz_read_header, L.cz_status, L.cz_forward_dense, L.cz_inverse_dense):
+                      L.cz_compress_noalloc, L.cz_batch_workspace_size, L.cz_compress_batch,
+                      L.cz_batch_tune, L.cz_read_header, L.cz_status, L.cz_forward_dense, L.cz_inverse_dense):
                 f.restype = C.c_int
             _lib = L
     return _lib
@@ -101,6 +107,39 @@ def cz_compress_noalloc(p: Params, d_field: int, d_out: int, out_cap: int, d_out
     """cz_compress with the library's own fixed workspace (no allocation)."""
     return lib().cz_compress_noalloc(C.byref(p), d_field, d_out, out_cap, d_out_bytes or None,
                                      stream or None)
+
+
+class BatchArgs:
+    """ctypes arrays of one batched call (kept alive by the caller)."""
+
+    def __init__(self, params, d_fields, d_outs, out_caps):
+        n = len(params)
+        self.n = n
+        self.params = (Params * n)(*params)
+        self.fields = (C.c_void_p * n)(*d_fields)
+        self.outs = (C.c_void_p * n)(*d_outs)
+        self.caps = (C.c_size_t * n)(*out_caps)
+
+
+def cz_batch_workspace_size(params) -> int:
+    n = len(params)
+    arr = (Params * n)(*params)
+    out = C.c_size_t()
+    r = lib().cz_batch_workspace_size(n, arr, C.byref(out))
+    if r != OK:
+        raise CzError(r, "cz_batch_workspace_size")
+    return out.value
+
+
+def cz_compress_batch(b: BatchArgs, d_out_bytes: int, d_ws: int, ws_bytes: int, stream: int) -> int:
+    return lib().cz_compress_batch(b.n, b.params, b.fields, b.outs, b.caps, d_out_bytes or None,
+                                   d_ws, ws_bytes, stream or None)
+
+
+def cz_batch_tune(b: BatchArgs, d_out_bytes: int, d_ws: int, ws_bytes: int, stream: int,
+                  reps: int = 3) -> int:
+    return lib().cz_batch_tune(b.n, b.params, b.fields, b.outs, b.caps, d_out_bytes or None,
+                               d_ws, ws_bytes, stream or None, reps)
 
 
 def cz_decompress(d_in: int, in_bytes: int, h_header, d_field: int, field_cap: int,
@@ -222,3 +261,45 @@ def decompress(stream_t, nbytes: int | None = None, header: bytes | None = None,
         if st != OK:
             raise CzError(st, "cz_decompress (device)")
     return out
+
+
+def compress_batch(fields, block=None, kind="w3ai", eps=1e-3, eps_mode: int = EPS_REL,
+                   stage2: bool = True, bound_mode: int = BOUND_PAPER, stream=None, check: bool = True,
+                   tune: bool = False):
+    """Compress a list of contiguous CUDA tensors in one batched call.
+
+    block, kind and eps may be scalars or per-field lists (block defaults to
+    32 for float32 and 16 for float64).  Returns a list of (stream_tensor,
+    nbytes) pairs; stream i is out[i][:nbytes[i]].
+    """
+    import torch
+    n = len(fields)
+    per = lambda v: list(v) if isinstance(v, (list, tuple)) else [v] * n
+    blocks = per(block) if block is not None else [16 if f.dtype == torch.float64 else 32 for f in fields]
+    kinds, epss = per(kind), per(eps)
+    params, caps, outs = [], [], []
+    for f, b, k, e in zip(fields, blocks, kinds, epss):
+        assert f.is_cuda and f.is_contiguous() and f.dim() == 3
+        p = params_for(tuple(f.shape), f.dtype == torch.float64, b, k, e, eps_mode, stage2, -1.0,
+                       bound_mode)
+        params.append(p)
+        cap = cz_compress_bound(p)
+        caps.append(cap)
+        outs.append(torch.empty(cap, dtype=torch.uint8, device=f.device))
+    dev = fields[0].device
+    nbytes = torch.zeros(n, dtype=torch.int64, device=dev)
+    ws = torch.empty(cz_batch_workspace_size(params), dtype=torch.uint8, device=dev)
+    b = BatchArgs(params, [f.data_ptr() for f in fields], [o.data_ptr() for o in outs], caps)
+    s = _stream(stream)
+    if tune:
+        r = cz_batch_tune(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(), s)
+        if r != OK:
+            raise CzError(r, "cz_batch_tune")
+    r = cz_compress_batch(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(), s)
+    if r != OK:
+        raise CzError(r, "cz_compress_batch")
+    if check:
+        st = cz_status(ws.data_ptr(), s)
+        if st != OK:
+            raise CzError(st, "cz_compress_batch (device)")
+    return [(outs[i], nbytes[i]) for i in range(n)]

@@ -1,0 +1,100 @@
+"""Batched compression: many fields of uneven block counts, mixed FP32 /
+FP64, per-field eps, in one call.  Every field's stream must equal, byte for
+byte, the one cz_compress writes for it alone (and hence the oracle's), also
+after the autotuner has picked its launch shape and when the call is
+replayed from a captured CUDA graph.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _fields(seed, n=12):
+    from paper_1903_07761_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        f64 = bool(i % 3 == 2)
+        B = 16 if f64 else 32
+        dims = tuple(int(B * rng.integers(1, 4)) for _ in range(3))
+        f = inputs.field(inputs.P, dims, np.float64 if f64 else np.float32, seed=3000 + i, nbubbles=6)
+        out.append((f, B, float(rng.choice([1e-2, 1e-3, 1e-4]))))
+    return out
+
+
+def test_batch_streams_equal_single_field_streams():
+    import torch
+    from paper_1903_07761_gb300 import cz
+    items = _fields(1)
+    tens = [torch.from_numpy(f).cuda() for f, _, _ in items]
+    res = cz.compress_batch(tens, block=[B for _, B, _ in items], kind="w3ai",
+                            eps=[e for _, _, e in items])
+    torch.cuda.synchronize()
+    for (f, B, e), t, (out, nb) in zip(items, tens, res):
+        single, snb = cz.compress(t, block=B, kind="w3ai", eps=e)
+        torch.cuda.synchronize()
+        got = out[:int(nb.item())].cpu().numpy().tobytes()
+        want = single[:int(snb.item())].cpu().numpy().tobytes()
+        assert got == want
+    # and the oracle agrees on a few of them
+    for (f, B, e), (out, nb) in list(zip(items, res))[:4]:
+        got = out[:int(nb.item())].cpu().numpy().tobytes()
+        assert got == O.compress(f, B, O.W3AI, e)
+
+
+@pytest.mark.parametrize("kind", ["w4", "w4li"])
+def test_batch_other_kinds_and_strict(kind):
+    import torch
+    from paper_1903_07761_gb300 import cz
+    items = _fields(2, n=6)
+    tens = [torch.from_numpy(f).cuda() for f, _, _ in items]
+    for bm in (cz.BOUND_PAPER, cz.BOUND_STRICT):
+        res = cz.compress_batch(tens, kind=kind, eps=[e for _, _, e in items], bound_mode=bm)
+        torch.cuda.synchronize()
+        for (f, B, e), (out, nb) in zip(items, res):
+            got = out[:int(nb.item())].cpu().numpy().tobytes()
+            assert got == O.compress(f, B, cz.KINDS[kind], e, bound_mode=bm)
+
+
+def test_batch_tuned_and_graph_replay_give_the_same_streams():
+    import torch
+    from paper_1903_07761_gb300 import cz
+    items = _fields(3, n=10)
+    tens = [torch.from_numpy(f).cuda() for f, _, _ in items]
+    ref = [bytes(o[:int(n.item())].cpu().numpy()) for o, n in
+           cz.compress_batch(tens, kind="w3ai", eps=[e for _, _, e in items])]
+    # tuned launch shape
+    res = cz.compress_batch(tens, kind="w3ai", eps=[e for _, _, e in items], tune=True)
+    torch.cuda.synchronize()
+    assert [bytes(o[:int(n.item())].cpu().numpy()) for o, n in res] == ref
+    # captured in a CUDA graph (set up by one call outside the capture)
+    params, caps, outs = [], [], []
+    for (f, B, e), t in zip(items, tens):
+        p = cz.params_for(tuple(t.shape), t.dtype == torch.float64, B, "w3ai", e)
+        params.append(p)
+        caps.append(cz.cz_compress_bound(p))
+        outs.append(torch.zeros(caps[-1], dtype=torch.uint8, device="cuda"))
+    nbytes = torch.zeros(len(items), dtype=torch.int64, device="cuda")
+    ws = torch.empty(cz.cz_batch_workspace_size(params), dtype=torch.uint8, device="cuda")
+    b = cz.BatchArgs(params, [t.data_ptr() for t in tens], [o.data_ptr() for o in outs], caps)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        assert cz.cz_compress_batch(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(), side.cuda_stream) == cz.OK
+    torch.cuda.synchronize()
+    for o in outs:
+        o.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        assert cz.cz_compress_batch(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(),
+                                    torch.cuda.current_stream().cuda_stream) == cz.OK
+    for _ in range(2):
+        for o in outs:
+            o.zero_()
+        nbytes.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        got = [bytes(o[:int(n)].cpu().numpy()) for o, n in zip(outs, nbytes.cpu().tolist())]
+        assert got == ref
