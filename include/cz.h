@@ -177,6 +177,52 @@ int cz_batch_tune(int n, const cz_params *p, const void *const *d_fields,
                   uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes,
                   void *stream, int reps);
 
+/* ---- request server (the paper compresses in situ, while the simulation
+ * runs, Sec. 2.2; here requests of mixed sizes and precisions arrive at any
+ * time and share the device) ----------------------------------------------
+ * The server allocates one device pool of budget_bytes when it is created
+ * (the HBM budget; every admitted request takes its workspace from it) and
+ * `streams` CUDA streams, and runs a worker thread that admits waiting
+ * requests in arrival order as streams and pool memory free up.  Compress
+ * requests that wait together and share dtype, block, kind, stage2 and
+ * bound_mode are launched as one cz_compress_batch call.  Requests keep
+ * their buffers (caller-owned, on the device) until they are done; results
+ * are identical to cz_compress / cz_decompress on the same inputs.  Latency
+ * is measured from submission to the worker seeing the request's work
+ * finished. */
+enum { CZ_OP_COMPRESS = 0, CZ_OP_DECOMPRESS = 1 };
+enum { CZ_REQ_QUEUED = 0, CZ_REQ_RUNNING = 1, CZ_REQ_DONE = 2 };
+
+typedef struct cz_request {
+  int32_t op;          /* CZ_OP_COMPRESS or CZ_OP_DECOMPRESS                  */
+  int32_t reserved;
+  cz_params params;    /* compress: the field's parameters                    */
+  const void *d_in;    /* compress: field; decompress: stream                 */
+  size_t in_bytes;     /* decompress: stream bytes                            */
+  unsigned char h_header[CZ_HEADER_BYTES]; /* decompress: host copy of the
+                                              stream's header                 */
+  void *d_out;         /* compress: stream buffer; decompress: field buffer   */
+  size_t out_cap;      /* bytes of d_out                                      */
+  uint64_t *d_out_bytes; /* compress: device u64 for the stream length, or NULL */
+} cz_request;
+
+/* Create a server on the current device.  CZ_ERR_CUDA if the pool cannot be
+ * allocated. */
+int cz_server_create(size_t budget_bytes, int streams, void **server);
+/* Queue a request (copied); returns its ticket.  CZ_ERR_BUDGET if its
+ * workspace can never fit the budget, else the host-side errors of the
+ * corresponding call. */
+int cz_server_submit(void *server, const cz_request *req, uint64_t *ticket);
+/* State (CZ_REQ_*), result (CZ_OK or a CZ_ERR_* code from the host call or
+ * the device status word) and latency in ms (-1 until done).  A done ticket
+ * is reported once, then forgotten. */
+int cz_server_poll(void *server, uint64_t ticket, int *state, int *result,
+                   double *latency_ms);
+/* Block until the ticket is done; then as cz_server_poll. */
+int cz_server_wait(void *server, uint64_t ticket, int *result, double *latency_ms);
+/* Finish all queued and running work, then free the server. */
+int cz_server_destroy(void *server);
+
 /* Parse a host copy of a stream header into *p (and the threshold used). */
 int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used);
 

@@ -58,7 +58,7 @@ def _jobs(verbose_ptxas: bool):
         cmd = [nvcc(), *ARCH, *NVFLAGS, *extra, f"-DCZ_T={ctype}", f"-DCZ_TNAME={tname}",
                f"-DCZ_B={b}", "-c", os.path.join(CSRC, "cz_inst.cu"), "-o", obj]
         jobs.append((obj, cmd))
-    for name in ("cz_api", "cz_noalloc"):
+    for name in ("cz_api", "cz_noalloc", "cz_serve"):
         obj = os.path.join(BUILD_DIR, f"{name}.o")
         jobs.append((obj, [nvcc(), *ARCH, *NVFLAGS, *extra, "-c", os.path.join(CSRC, f"{name}.cu"),
                            "-o", obj]))

@@ -36,6 +36,18 @@ class Params(C.Structure):
     ]
 
 
+OP_COMPRESS, OP_DECOMPRESS = 0, 1
+REQ_QUEUED, REQ_RUNNING, REQ_DONE = 0, 1, 2
+
+
+class Request(C.Structure):
+    _fields_ = [
+        ("op", C.c_int32), ("reserved", C.c_int32), ("params", Params),
+        ("d_in", C.c_void_p), ("in_bytes", C.c_size_t), ("h_header", C.c_ubyte * HEADER_BYTES),
+        ("d_out", C.c_void_p), ("out_cap", C.c_size_t), ("d_out_bytes", C.c_void_p),
+    ]
+
+
 class CzError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         self.code = code
@@ -60,6 +72,12 @@ def lib():
             L.cz_compress.argtypes = [PP, P, P, C.c_size_t, P, P, C.c_size_t, P]
             L.cz_decompress.argtypes = [P, C.c_size_t, P, P, C.c_size_t, P, C.c_size_t, P]
             L.cz_compress_noalloc.argtypes = [PP, P, P, C.c_size_t, P, P]
+            L.cz_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(P)]
+            L.cz_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(C.c_uint64)]
+            L.cz_server_poll.argtypes = [P, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.POINTER(C.c_double)]
+            L.cz_server_wait.argtypes = [P, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+            L.cz_server_destroy.argtypes = [P]
             L.cz_batch_workspace_size.argtypes = [C.c_int, PP, C.POINTER(C.c_size_t)]
             L.cz_compress_batch.argtypes = [C.c_int, PP, C.POINTER(P), C.POINTER(P),
                                             C.POINTER(C.c_size_t), P, P, C.c_size_t, P]
@@ -73,7 +91,8 @@ def lib():
             L.cz_inverse_dense.argtypes = [PP, P, P, P]
             for f in (L.cz_compress_bound, L.cz_workspace_size, L.cz_compress, L.cz_decompress,
                       L.cz_compress_noalloc, L.cz_batch_workspace_size, L.cz_compress_batch,
-                      L.cz_batch_tune, L.cz_read_header, L.cz_status, L.cz_forward_dense, L.cz_inverse_dense):
+                      L.cz_batch_tune, L.cz_server_create, L.cz_server_submit, L.cz_server_poll,
+                      L.cz_server_wait, L.cz_server_destroy, L.cz_read_header, L.cz_status, L.cz_forward_dense, L.cz_inverse_dense):
                 f.restype = C.c_int
             _lib = L
     return _lib
@@ -303,3 +322,66 @@ def compress_batch(fields, block=None, kind="w3ai", eps=1e-3, eps_mode: int = EP
         if st != OK:
             raise CzError(st, "cz_compress_batch (device)")
     return [(outs[i], nbytes[i]) for i in range(n)]
+
+
+class Server:
+    """The request server of the C ABI (cz_server_*): device pool of
+    `budget_bytes`, `streams` CUDA streams, continuous admission."""
+
+    def __init__(self, budget_bytes: int, streams: int = 4):
+        self.h = C.c_void_p()
+        r = lib().cz_server_create(int(budget_bytes), int(streams), C.byref(self.h))
+        if r != OK:
+            raise CzError(r, "cz_server_create")
+
+    def submit_compress(self, p: Params, d_field: int, d_out: int, out_cap: int, d_out_bytes: int) -> int:
+        q = Request()
+        q.op = OP_COMPRESS
+        q.params = p
+        q.d_in = d_field
+        q.d_out = d_out
+        q.out_cap = out_cap
+        q.d_out_bytes = d_out_bytes or None
+        return self._submit(q)
+
+    def submit_decompress(self, d_stream: int, nbytes: int, header: bytes, d_field: int, field_cap: int) -> int:
+        q = Request()
+        q.op = OP_DECOMPRESS
+        q.d_in = d_stream
+        q.in_bytes = nbytes
+        C.memmove(q.h_header, bytes(header[:HEADER_BYTES]), HEADER_BYTES)
+        q.d_out = d_field
+        q.out_cap = field_cap
+        return self._submit(q)
+
+    def _submit(self, q) -> int:
+        t = C.c_uint64()
+        r = lib().cz_server_submit(self.h, C.byref(q), C.byref(t))
+        if r != OK:
+            raise CzError(r, "cz_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        st, res, lat = C.c_int(), C.c_int(), C.c_double()
+        r = lib().cz_server_poll(self.h, ticket, C.byref(st), C.byref(res), C.byref(lat))
+        if r != OK:
+            raise CzError(r, "cz_server_poll")
+        return st.value, res.value, lat.value
+
+    def wait(self, ticket: int):
+        res, lat = C.c_int(), C.c_double()
+        r = lib().cz_server_wait(self.h, ticket, C.byref(res), C.byref(lat))
+        if r != OK:
+            raise CzError(r, "cz_server_wait")
+        return res.value, lat.value
+
+    def close(self):
+        if self.h:
+            lib().cz_server_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

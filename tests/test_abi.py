@@ -130,3 +130,22 @@ def test_bound_mode_and_flags_are_checked(cz):
     p.flags = 1
     with pytest.raises(cz.CzError):
         cz.cz_compress_bound(p)
+
+
+def test_struct_layouts_match_the_header(cz, tmp_path):
+    """ctypes mirrors of cz_params / cz_request have the C layout."""
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "cz.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(cz_params), sizeof(cz_request),'
+                   ' offsetof(cz_params, eps), offsetof(cz_request, h_header), offsetof(cz_request, d_out));'
+                   'return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [C.sizeof(cz.Params), C.sizeof(cz.Request), cz.Params.eps.offset, cz.Request.h_header.offset,
+            cz.Request.d_out.offset]
+    assert got == want
