@@ -355,6 +355,19 @@ def run_gpu(args, rank, world, local_rank):
                 "cr": nbytes_field / ln,
                 "psnr_db": 20 * math.log10((fmax - fmin) / (2 * math.sqrt(mse_k))) if mse_k > 0 else None}
 
+    # batched fields and the served request stream (rank 0, one GPU)
+    batched_res = served_res = None
+    if rank == 0 and world == 1:
+        from paper_1903_07761_gb300 import workloads
+        del rec
+        torch.cuda.empty_cache()
+        if not args.no_batch:
+            batched_res = workloads.batched()
+            torch.cuda.empty_cache()
+        if not args.no_serve:
+            served_res = workloads.served()
+            torch.cuda.empty_cache()
+
     # reductions over ranks (max time)
     import torch.distributed as dist
     if world > 1:
@@ -405,6 +418,8 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "per_kind": per_kind,
+        "batched": batched_res,
+        "served": served_res,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -457,6 +472,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--headline-only", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-fields comparison")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-requests comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -236,9 +236,11 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_stage2(const S2Args a)
   for (int bid = blockIdx.x; bid < a.nblocks; bid += gridDim.x) {
     const unsigned long long so = a.table[2 * bid], cb = a.table[2 * bid + 1];
     if (cb == 0xFFFFFFFFFFFFFFFFull) continue;  // the staging arena overflowed for this block
-    const int pbytes = (int)cb - 8;
-    if ((pbytes > G::SHCAP) != BIG) continue;  // the other launch's payload
     unsigned *ch = reinterpret_cast<unsigned *>(a.staging + so);
+    // payload size from the slot's nnz word, which the rewrite keeps (the
+    // table's size becomes the finished chunk's, which may be larger)
+    const int pbytes = 64 * ES + G::MASKB + (int)ch[0] * ES;
+    if ((pbytes > G::SHCAP) != BIG) continue;  // the other launch's payload
     const int E = pbytes >> LGES, W = pbytes >> 2, NB = (W + 31) >> 5;
     unsigned *ZBM = AUX, *CM = AUX + cap, *EB = AUX + 2 * cap, *PRE = AUX + 3 * cap;
     // payload word k holds bytes 0..3 of element 4k / ES at byte offset 4k % ES

@@ -1,0 +1,251 @@
+"""Batched and served workloads on the GPU, measured against plain launches.
+
+* batched(): 64 fields with edge lengths log-uniform on [64, 384] (each axis
+  drawn on its own, rounded to a multiple of 32), half FP32 (32^3 blocks) and
+  half FP64 (16^3 blocks), eps drawn from {1e-2, 1e-3, 1e-4} per field,
+  W3ai, content from the bubble-cloud pressure recipe; compressed by one
+  tuned cz_compress_batch call replayed from a CUDA graph, against the 64
+  cz_compress calls one after another.  The streams are identical, so the
+  PSNRs are equal.
+* served(): a Poisson stream of compress and decompress requests (1:1) of
+  cubic fields with edges log-uniform on [32, 512] (rounded to 32), 70 % FP32
+  and 30 % FP64, eps in {1e-3, 1e-4}, through the request server under an
+  HBM budget, against one-at-a-time plain launches on the same trace.
+
+Both return plain dicts for the benchmark line.  Inputs are synthetic
+(seeded); see inputs/czgen.c.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import cz, inputs
+
+
+def _loguniform_edge(rng, lo, hi):
+    e = math.exp(rng.uniform(math.log(lo), math.log(hi)))
+    return int(max(lo, min(hi, round(e / 32) * 32)))
+
+
+# ------------------------------------------------------------------ batched
+def batched(nfields: int = 64, reps: int = 10, seed: int = 3000, nbubbles: int = 200):
+    import torch
+    rng = np.random.default_rng(seed)
+    fields, params, bytes_total = [], [], 0
+    for i in range(nfields):
+        f64 = i % 2 == 1
+        dims = tuple(_loguniform_edge(rng, 64, 384) for _ in range(3))
+        eps = float(rng.choice([1e-2, 1e-3, 1e-4]))
+        f = inputs.field(inputs.P, dims, np.float64 if f64 else np.float32, seed=seed + i,
+                         nbubbles=nbubbles)
+        t = torch.from_numpy(f).cuda()
+        fields.append(t)
+        B = 16 if f64 else 32
+        params.append(cz.params_for(tuple(t.shape), f64, B, "w3ai", eps))
+        bytes_total += t.numel() * t.element_size()
+    caps = [cz.cz_compress_bound(p) for p in params]
+    outs = [torch.zeros(c, dtype=torch.uint8, device="cuda") for c in caps]
+    nbytes = torch.zeros(nfields, dtype=torch.int64, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+
+    # plain: one cz_compress per field, one after another (own workspace sized
+    # for the largest field)
+    ws_plain = torch.empty(max(cz.cz_workspace_size(p) for p in params), dtype=torch.uint8, device="cuda")
+    one = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def plain():
+        for p, t, o, c in zip(params, fields, outs, caps):
+            r = cz.cz_compress(p, t.data_ptr(), o.data_ptr(), c, one.data_ptr(), ws_plain.data_ptr(),
+                               ws_plain.numel(), s)
+            assert r == cz.OK
+
+    plain()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plain()
+    e1.record()
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / reps
+    # streams of the plain path, to compare with the batched ones
+    plain_streams = []
+    for p, t, o, c in zip(params, fields, outs, caps):
+        r = cz.cz_compress(p, t.data_ptr(), o.data_ptr(), c, one.data_ptr(), ws_plain.data_ptr(),
+                           ws_plain.numel(), s)
+        assert r == cz.OK
+        torch.cuda.synchronize()
+        plain_streams.append(bytes(o[:int(one.item())].cpu().numpy()))
+    del ws_plain
+
+    # batched: tune once, capture one call in a CUDA graph, replay
+    ws = torch.empty(cz.cz_batch_workspace_size(params), dtype=torch.uint8, device="cuda")
+    b = cz.BatchArgs(params, [t.data_ptr() for t in fields], [o.data_ptr() for o in outs], caps)
+    assert cz.cz_batch_tune(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(), s, 3) == cz.OK
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        assert cz.cz_compress_batch(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(), side.cuda_stream) == cz.OK
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        assert cz.cz_compress_batch(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(),
+                                    torch.cuda.current_stream().cuda_stream) == cz.OK
+    g.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / reps
+    lens = nbytes.cpu().tolist()
+    same = all(bytes(o[:n].cpu().numpy()) == ps for o, n, ps in zip(outs, lens, plain_streams))
+    stream_bytes = sum(lens)
+    # PSNR of a few fields (identical streams give identical PSNR on both paths)
+    ps = []
+    for i in range(0, nfields, 16):
+        rec = cz.decompress(outs[i], nbytes=lens[i])
+        d = rec.double() - fields[i].double()
+        mse = float((d * d).mean().item())
+        rg = float(fields[i].max().item() - fields[i].min().item())
+        ps.append(20 * math.log10(rg / (2 * math.sqrt(mse))) if mse > 0 else float("inf"))
+    return {
+        "workload": f"{nfields} fields, edges log-uniform [64,384] step 32, FP32 32^3 / FP64 16^3 blocks, "
+                    f"eps in {{1e-2,1e-3,1e-4}}, W3ai, range computed",
+        "field_bytes": bytes_total, "stream_bytes": stream_bytes,
+        "plain_ms": plain_ms, "plain_gbs": bytes_total / plain_ms / 1e6,
+        "batched_ms": batch_ms, "batched_gbs": bytes_total / batch_ms / 1e6,
+        "speedup": plain_ms / batch_ms, "streams_identical": same,
+        "psnr_db_sample": ps, "graph": True,
+    }
+
+
+# ------------------------------------------------------------------ served
+class _Pool:
+    """Device fields and streams of every size class of the served trace."""
+
+    def __init__(self, seed: int, nbubbles: int, max_edge: int):
+        import torch
+        self.fields, self.streams = {}, {}
+        base = {}
+        for f64 in (False, True):
+            dt = np.float64 if f64 else np.float32
+            base[f64] = torch.from_numpy(inputs.field(inputs.P, (max_edge,) * 3, dt, seed=seed + int(f64),
+                                                      nbubbles=nbubbles)).cuda()
+        for e in range(32, max_edge + 1, 32):
+            for f64 in (False, True):
+                self.fields[(e, f64)] = base[f64][:e, :e, :e].contiguous()
+        self.base = base
+
+    def stream_of(self, e, f64, eps, kind):
+        key = (e, f64, eps, kind)
+        if key not in self.streams:
+            out, nb = cz.compress(self.fields[(e, f64)], block=16 if f64 else 32, kind=kind, eps=eps)
+            n = int(nb.item())
+            self.streams[key] = (out[:n].clone(), n, out[:cz.HEADER_BYTES].cpu().numpy().tobytes())
+        return self.streams[key]
+
+
+def _trace(rate: float, n: int, seed: int, max_edge: int):
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    reqs = []
+    for i in range(n):
+        e = _loguniform_edge(rng, 32, max_edge)
+        f64 = rng.random() < 0.3
+        eps = float(rng.choice([1e-3, 1e-4]))
+        op = cz.OP_COMPRESS if i % 2 == 0 else cz.OP_DECOMPRESS
+        reqs.append((float(t[i]), op, e, f64, eps))
+    return reqs
+
+
+def served(rates=(1000.0, 5000.0), n: int = 400, budget_gb: float = 40.0, streams: int = 4,
+           seed: int = 4000, nbubbles: int = 200, max_edge: int = 512, kind: str = "w3ai"):
+    import torch
+    pool = _Pool(seed, nbubbles, max_edge)
+    # output buffers: a small ring per size class and op (requests of one
+    # class that overlap may share a buffer: their outputs are not read)
+    ring = 2
+    outs = {}
+
+    def out_for(op, e, f64, i):
+        key = (op, e, f64, i % ring)
+        if key not in outs:
+            p = cz.params_for((e, e, e), f64, 16 if f64 else 32, kind, 1e-3)
+            nbytes = cz.cz_compress_bound(p) if op == cz.OP_COMPRESS else e ** 3 * (8 if f64 else 4)
+            outs[key] = (torch.empty(nbytes, dtype=torch.uint8, device="cuda"),
+                         torch.zeros(1, dtype=torch.int64, device="cuda"))
+        return outs[key]
+
+    results = []
+    for rate in rates:
+        reqs = _trace(rate, n, seed + int(rate), max_edge)
+        for _, op, e, f64, eps in reqs:  # decompress inputs, made before the clock starts
+            if op == cz.OP_DECOMPRESS:
+                pool.stream_of(e, f64, eps, kind)
+        torch.cuda.synchronize()
+        nbytes_total = sum(e ** 3 * (8 if f64 else 4) for _, _, e, f64, _ in reqs)
+
+        # ---- through the server
+        lat = []
+        with cz.Server(int(budget_gb * (1 << 30)), streams) as srv:
+            tickets = []
+            t0 = time.perf_counter()
+            for i, (ta, op, e, f64, eps) in enumerate(reqs):
+                while time.perf_counter() - t0 < ta:
+                    pass
+                o, nb = out_for(op, e, f64, i)
+                if op == cz.OP_COMPRESS:
+                    p = cz.params_for((e, e, e), f64, 16 if f64 else 32, kind, eps)
+                    tk = srv.submit_compress(p, pool.fields[(e, f64)].data_ptr(), o.data_ptr(), o.numel(),
+                                             nb.data_ptr())
+                else:
+                    sd, sn, hdr = pool.stream_of(e, f64, eps, kind)
+                    tk = srv.submit_decompress(sd.data_ptr(), sn, hdr, o.data_ptr(), o.numel())
+                tickets.append(tk)
+            for tk in tickets:
+                res, ms = srv.wait(tk)
+                assert res == cz.OK, res
+                lat.append(ms)
+            wall = time.perf_counter() - t0
+        srv_gbs = nbytes_total / wall / 1e9
+
+        # ---- one at a time, plain launches, same trace
+        s = torch.cuda.current_stream().cuda_stream
+        ws = torch.empty(max(cz.cz_workspace_size(cz.params_for((e, e, e), f64, 16 if f64 else 32, kind, eps))
+                             for _, _, e, f64, eps in reqs), dtype=torch.uint8, device="cuda")
+        plat = []
+        t0 = time.perf_counter()
+        for i, (ta, op, e, f64, eps) in enumerate(reqs):
+            while time.perf_counter() - t0 < ta:
+                pass
+            o, nb = out_for(op, e, f64, i)
+            if op == cz.OP_COMPRESS:
+                p = cz.params_for((e, e, e), f64, 16 if f64 else 32, kind, eps)
+                r = cz.cz_compress(p, pool.fields[(e, f64)].data_ptr(), o.data_ptr(), o.numel(), nb.data_ptr(),
+                                   ws.data_ptr(), ws.numel(), s)
+            else:
+                sd, sn, hdr = pool.stream_of(e, f64, eps, kind)
+                r = cz.cz_decompress(sd.data_ptr(), sn, hdr, o.data_ptr(), o.numel(), ws.data_ptr(), ws.numel(), s)
+            assert r == cz.OK
+            torch.cuda.current_stream().synchronize()
+            plat.append((time.perf_counter() - t0 - ta) * 1e3)
+        pwall = time.perf_counter() - t0
+        del ws
+        results.append({
+            "rate_per_s": rate, "requests": n,
+            "server": {"gbs": srv_gbs, "p50_ms": float(np.percentile(lat, 50)),
+                       "p99_ms": float(np.percentile(lat, 99)), "wall_s": wall},
+            "plain": {"gbs": nbytes_total / pwall / 1e9, "p50_ms": float(np.percentile(plat, 50)),
+                      "p99_ms": float(np.percentile(plat, 99)), "wall_s": pwall},
+        })
+    return {
+        "workload": f"Poisson compress/decompress 1:1, cubic edges log-uniform [32,{max_edge}] step 32, "
+                    f"70% FP32 (32^3 blocks) / 30% FP64 (16^3 blocks), eps in {{1e-3,1e-4}}, {kind}, "
+                    f"budget {budget_gb:g} GB, {streams} streams",
+        "runs": results,
+    }

@@ -62,6 +62,37 @@ def test_stream_and_decode_bit_identical(dtype, block, shape, kind, stage2):
         np.testing.assert_array_equal(rec.view(np.uint8), want.view(np.uint8))
 
 
+@pytest.mark.parametrize("dtype,block", [(np.float64, 16), (np.float32, 16)])
+def test_payload_exactly_at_the_stage2_shared_capacity(dtype, block):
+    """One block whose payload is exactly 16 KiB (the stage-2 kernels'
+    shared-memory capacity) and has no zero-word runs, so its finished chunk
+    is 12 bytes longer than the payload: it must be encoded once, by the
+    small-payload launch.  The block is built from chosen coefficients: the
+    synthesis of exactly nnz details of magnitude in [1, 2] (all kept) plus
+    random coarse values, every other coefficient zero (rounding noise far
+    below the threshold)."""
+    es = np.dtype(dtype).itemsize
+    nnz = (16384 - 64 * es - block ** 3 // 8) // es
+    rng = np.random.default_rng(99)
+    Q = block // 4
+    coarse = np.zeros((block,) * 3, bool)
+    coarse[::Q, ::Q, ::Q] = True
+    det = np.flatnonzero(~coarse.ravel())
+    c = np.zeros(block ** 3)
+    pick = rng.choice(det, nnz, replace=False)
+    c[pick] = rng.uniform(1, 2, nnz) * rng.choice([-1.0, 1.0], nnz)
+    c[coarse.ravel()] = rng.uniform(-4, 4, 64)
+    blk = O.inv3d(O.W3AI, c.reshape((block,) * 3))
+    f = np.concatenate([blk, blk[::-1].copy()], axis=2).astype(dtype)  # two blocks along x
+    for stage2 in (True, False):
+        ref = O.compress(f, block, O.W3AI, 1e-3, eps_mode=O.EPS_ABS, stage2=stage2)
+        got = gpu_compress(f, block, O.W3AI, 1e-3, eps_mode=O.EPS_ABS, stage2=stage2)
+        assert got == ref, describe_diff(got, ref)
+        np.testing.assert_array_equal(gpu_decompress(got).view(np.uint8), O.decompress(ref).view(np.uint8))
+    d0, offs = O.chunk_table(ref)
+    assert int(np.frombuffer(ref[d0:d0 + 4], np.uint32)[0]) == nnz  # the first block is at the capacity
+
+
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("dtype,block,shape", CASES)
 def test_strict_bound_mode(dtype, block, shape, kind):
