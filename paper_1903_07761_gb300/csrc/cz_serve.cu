@@ -18,7 +18,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
-#include <deque>
+#include <list>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -50,8 +50,6 @@ struct Slot {
   bool busy = false;
   std::vector<uint64_t> tickets;
   size_t ws_off = 0, ws_len = 0;
-  uint64_t *d_lens = nullptr;  // batched launch: stream lengths (in the pool)
-  std::vector<uint64_t *> dst_lens;
 };
 
 // first-fit allocator of [offset, length) ranges of the pool, 256-byte units
@@ -382,7 +380,7 @@ class Server {
   bool stop_ = false;
   uint64_t next_ = 0;
   std::unordered_map<uint64_t, Req> reqs_;
-  std::deque<uint64_t> queue_;
+  std::list<uint64_t> queue_;  // arrival order; erasing one entry keeps the others' iterators
 };
 
 }  // namespace
