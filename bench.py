@@ -75,6 +75,21 @@ def traffic_per_launch(kernel: str, units: float):
         return None
 
 
+def rank_max(values, device):
+    """Element-wise maximum of a list of floats over all ranks (the job's
+    time is the slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def replica_throughput(world, bytes_per_rank, ms_per_step):
+    """Whole-job GB/s: every rank processes its own field in each step."""
+    return world * bytes_per_rank / (ms_per_step * 1e-3) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -369,13 +384,10 @@ def run_gpu(args, rank, world, local_rank):
             torch.cuda.empty_cache()
 
     # reductions over ranks (max time)
-    import torch.distributed as dist
     if world > 1:
-        tt = torch.tensor([total_ms, comp_ms, dec_ms, stage1_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms, comp_ms, dec_ms, stage1_ms = tt.tolist()
+        total_ms, comp_ms, dec_ms, stage1_ms = rank_max([total_ms, comp_ms, dec_ms, stage1_ms], dev)
     ms_per_step = total_ms / args.steps
-    value = world * nbytes_field / (ms_per_step * 1e-3) / 1e9
+    value = replica_throughput(world, nbytes_field, ms_per_step)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -223,6 +223,21 @@ int cz_server_wait(void *server, uint64_t ticket, int *result, double *latency_m
 /* Finish all queued and running work, then free the server. */
 int cz_server_destroy(void *server);
 
+/* ---- several GPUs: slabs of one field -----------------------------------
+ * Blocks are independent (Sec. 2.2), so a field cut into z-slabs of whole
+ * block planes can be compressed slab by slab (one GPU or rank each) with
+ * the same parameters and the same supplied range (so that the threshold is
+ * the same everywhere).  This host-side call joins the slab streams, given
+ * in z order as host buffers, into the stream of the whole field: header
+ * with the summed nz, offsets rebased by the exclusive prefix sum of the
+ * slabs' data bytes (the paper's scan of per-rank sizes), chunks appended.
+ * The result equals, byte for byte, the stream cz_compress writes for the
+ * whole field with that range.  With h_out == NULL only *out_bytes is set.
+ * CZ_ERR_ARG if the slabs disagree on anything but nz, CZ_ERR_CORRUPT for
+ * a malformed stream, CZ_ERR_CAPACITY if out_cap is too small. */
+int cz_stream_concat(int n, const void *const *h_streams, const size_t *sizes,
+                     void *h_out, size_t out_cap, size_t *out_bytes);
+
 /* Parse a host copy of a stream header into *p (and the threshold used). */
 int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used);
 

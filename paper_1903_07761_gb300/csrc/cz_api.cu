@@ -691,6 +691,87 @@ int cz_batch_tune(int n, const cz_params *p, const void *const *d_fields, void *
   return r;
 }
 
+int cz_stream_concat(int n, const void *const *h_streams, const size_t *sizes, void *h_out, size_t out_cap,
+                     size_t *out_bytes)
+{
+  if (n < 1 || !h_streams || !sizes || !out_bytes) return CZ_ERR_ARG;
+  cz_params p0{}, pr{};
+  double t0 = 0, tr = 0;
+  unsigned long long nz = 0, nblocks = 0, data = 0;
+  double mn = 0, mx = 0;
+  for (int r = 0; r < n; ++r) {
+    if (!h_streams[r]) return CZ_ERR_ARG;
+    const unsigned char *h = reinterpret_cast<const unsigned char *>(h_streams[r]);
+    const int e = cz_read_header(h, sizes[r], r ? &pr : &p0, r ? &tr : &t0);
+    if (e != CZ_OK) return e;
+    const cz_params &q = r ? pr : p0;
+    Shape sh;
+    check(&q, &sh);
+    const unsigned long long total = rd64(h + 80), db = rd64(h + 72);
+    if (total > sizes[r] || sh.data0 + db != total) return CZ_ERR_CORRUPT;
+    const unsigned char *h0 = reinterpret_cast<const unsigned char *>(h_streams[0]);
+    if (r) {  // slabs of one field: everything but nz must agree, eps and the threshold included
+      if (pr.nx != p0.nx || pr.ny != p0.ny || pr.block != p0.block || pr.dtype != p0.dtype || pr.kind != p0.kind ||
+          pr.stage2 != p0.stage2 || pr.eps_mode != p0.eps_mode || pr.bound_mode != p0.bound_mode ||
+          std::memcmp(&tr, &t0, 8) != 0 || std::memcmp(h + 32, h0 + 32, 8) != 0 ||
+          std::memcmp(h + 64, h0 + 64, 8) != 0)
+        return CZ_ERR_ARG;
+    }
+    // min / max over the slabs (NaN, when the range was supplied, only if
+    // no slab has a value)
+    double a, b;
+    std::memcpy(&a, h + 48, 8);
+    std::memcpy(&b, h + 56, 8);
+    if (r == 0) {
+      mn = a;
+      mx = b;
+    } else {
+      if (std::isnan(mn) || (!std::isnan(a) && a < mn)) mn = a;
+      if (std::isnan(mx) || (!std::isnan(b) && b > mx)) mx = b;
+    }
+    nz += (unsigned long long)q.nz;
+    nblocks += (unsigned long long)sh.nblocks;
+    data += db;
+  }
+  if (nz > 0x7FFFFFFFull || nblocks > (1ull << 30)) return CZ_ERR_ARG;
+  const unsigned long long data0 = (HEADER_BYTES + 8ull * (nblocks + 1) + 15) / 16 * 16, total = data0 + data;
+  *out_bytes = (size_t)total;
+  if (!h_out) return CZ_OK;  // size query
+  if (out_cap < total) return CZ_ERR_CAPACITY;
+  unsigned char *o = reinterpret_cast<unsigned char *>(h_out);
+  std::memset(o, 0, (size_t)data0);
+  std::memcpy(o, h_streams[0], HEADER_BYTES);
+  const int nz32 = (int)nz;
+  const unsigned nb32 = (unsigned)nblocks;
+  std::memcpy(o + 16, &nz32, 4);
+  std::memcpy(o + 28, &nb32, 4);
+  std::memcpy(o + 48, &mn, 8);
+  std::memcpy(o + 56, &mx, 8);
+  std::memcpy(o + 72, &data, 8);
+  std::memcpy(o + 80, &total, 8);
+  // offsets rebased by the data bytes of the slabs before (the exclusive
+  // scan of per-rank sizes), chunks appended in rank order
+  unsigned long long base = 0, blk = 0;
+  for (int r = 0; r < n; ++r) {
+    const unsigned char *h = reinterpret_cast<const unsigned char *>(h_streams[r]);
+    cz_params q;
+    double tq;
+    cz_read_header(h, sizes[r], &q, &tq);
+    Shape sh;
+    check(&q, &sh);
+    const unsigned long long db = rd64(h + 72);
+    for (int b = 0; b < sh.nblocks; ++b) {
+      const unsigned long long off = rd64(h + HEADER_BYTES + 8ull * b) + base;
+      std::memcpy(o + HEADER_BYTES + 8ull * (blk + b), &off, 8);
+    }
+    std::memcpy(o + data0 + base, h + sh.data0, (size_t)db);
+    base += db;
+    blk += (unsigned long long)sh.nblocks;
+  }
+  std::memcpy(o + HEADER_BYTES + 8ull * nblocks, &base, 8);
+  return CZ_OK;
+}
+
 // Not part of the ABI: the strict-bound divisor C of (kind, B), for tests.
 double czi_synthesis_norm(int kind, int block)
 {

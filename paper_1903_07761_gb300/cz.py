@@ -72,6 +72,8 @@ def lib():
             L.cz_compress.argtypes = [PP, P, P, C.c_size_t, P, P, C.c_size_t, P]
             L.cz_decompress.argtypes = [P, C.c_size_t, P, P, C.c_size_t, P, C.c_size_t, P]
             L.cz_compress_noalloc.argtypes = [PP, P, P, C.c_size_t, P, P]
+            L.cz_stream_concat.argtypes = [C.c_int, C.POINTER(P), C.POINTER(C.c_size_t), P, C.c_size_t,
+                                           C.POINTER(C.c_size_t)]
             L.cz_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(P)]
             L.cz_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(C.c_uint64)]
             L.cz_server_poll.argtypes = [P, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -91,7 +93,7 @@ def lib():
             L.cz_inverse_dense.argtypes = [PP, P, P, P]
             for f in (L.cz_compress_bound, L.cz_workspace_size, L.cz_compress, L.cz_decompress,
                       L.cz_compress_noalloc, L.cz_batch_workspace_size, L.cz_compress_batch,
-                      L.cz_batch_tune, L.cz_server_create, L.cz_server_submit, L.cz_server_poll,
+                      L.cz_batch_tune, L.cz_stream_concat, L.cz_server_create, L.cz_server_submit, L.cz_server_poll,
                       L.cz_server_wait, L.cz_server_destroy, L.cz_read_header, L.cz_status, L.cz_forward_dense, L.cz_inverse_dense):
                 f.restype = C.c_int
             _lib = L
@@ -385,3 +387,21 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def stream_concat(streams) -> bytes:
+    """Join slab streams (bytes, in z order) into the whole field's stream
+    (cz_stream_concat); host-side, no GPU needed."""
+    n = len(streams)
+    bufs = [C.create_string_buffer(bytes(s), len(s)) for s in streams]
+    ptrs = (C.c_void_p * n)(*[C.cast(b, C.c_void_p) for b in bufs])
+    sizes = (C.c_size_t * n)(*[len(s) for s in streams])
+    total = C.c_size_t()
+    r = lib().cz_stream_concat(n, ptrs, sizes, None, 0, C.byref(total))
+    if r != OK:
+        raise CzError(r, "cz_stream_concat")
+    out = C.create_string_buffer(total.value)
+    r = lib().cz_stream_concat(n, ptrs, sizes, out, total.value, C.byref(total))
+    if r != OK:
+        raise CzError(r, "cz_stream_concat")
+    return out.raw[:total.value]
