@@ -177,7 +177,7 @@ struct Lanes {
                           int, const cudaEvent_t *, cudaStream_t);
   cudaError_t (*compress_batch)(int, const StageMaps<MAXF> *, const FwdArgs *, const S2Args *, const BatchOut *,
                                 const PlaceArgs *, int, int, int, int, cudaStream_t);
-  cudaError_t (*decompress)(int, const InvArgs *, const UnArgs *, int, int, int, cudaStream_t);
+  cudaError_t (*decompress)(int, const CUtensorMap *, const InvArgs *, const UnArgs *, int, int, int, cudaStream_t);
   cudaError_t (*dense)(int, int, const DenseArgs *, int, cudaStream_t);
   int (*occupancy)(int, int);
   int (*slot_bytes)();
@@ -886,7 +886,9 @@ int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header, void 
   ua.data0 = sh.data0;
   ua.slot = slot;
   ua.nblocks = sh.nblocks;
-  return L.decompress(p.kind, &a, &ua, grid_for(&p, sh, 1), grid_for(&p, sh, 4), grid_for(&p, sh, 5), s) ==
+  CUtensorMap om;
+  if (!make_tile_map(&om, &p, d_field)) return CZ_ERR_CUDA;
+  return L.decompress(p.kind, &om, &a, &ua, grid_for(&p, sh, 1), grid_for(&p, sh, 4), grid_for(&p, sh, 5), s) ==
                  cudaSuccess
              ? CZ_OK
              : CZ_ERR_CUDA;

@@ -48,6 +48,13 @@ struct PlaceArgs {
 
 constexpr int PLACE_TILE = 128;  // chunks (and threads) per k_place CTA
 
+// block table size words: ~0 = lost (staging overflow); bit 62 set = the
+// size of a chunk that stage 2 has finished (so that the other stage-2
+// launch, which classifies by size, leaves it alone)
+constexpr unsigned long long TB_LOST = 0xFFFFFFFFFFFFFFFFull;
+constexpr unsigned long long TB_FIN = 1ull << 62;
+__device__ __forceinline__ unsigned long long tb_size(unsigned long long cb) { return cb & ~TB_FIN; }
+
 // field of global block bid among the nf fields of a batched launch
 template <int NF>
 __device__ __forceinline__ int field_of(const StageMaps<NF> &maps, int nf, int bid)
@@ -211,7 +218,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
         atomicCAS(&ws->status, 0u, ST_CAPACITY);
       }
       a.table[2 * bid] = (unsigned long long)(arena - a.staging) + so;
-      a.table[2 * bid + 1] = ok ? 8ull + (unsigned long long)pbytes : 0xFFFFFFFFFFFFFFFFull;
+      a.table[2 * bid + 1] = ok ? 8ull + (unsigned long long)pbytes : TB_LOST;
     }
     __syncthreads();
     if (tid == 0 && ok) s_aoff = so + slot;
@@ -235,12 +242,10 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_stage2(const S2Args a)
 
   for (int bid = blockIdx.x; bid < a.nblocks; bid += gridDim.x) {
     const unsigned long long so = a.table[2 * bid], cb = a.table[2 * bid + 1];
-    if (cb == 0xFFFFFFFFFFFFFFFFull) continue;  // the staging arena overflowed for this block
-    unsigned *ch = reinterpret_cast<unsigned *>(a.staging + so);
-    // payload size from the slot's nnz word, which the rewrite keeps (the
-    // table's size becomes the finished chunk's, which may be larger)
-    const int pbytes = 64 * ES + G::MASKB + (int)ch[0] * ES;
+    if (cb == TB_LOST || (cb & TB_FIN)) continue;  // staging overflow, or finished by the other launch
+    const int pbytes = (int)cb - 8;
     if ((pbytes > G::SHCAP) != BIG) continue;  // the other launch's payload
+    unsigned *ch = reinterpret_cast<unsigned *>(a.staging + so);
     const int E = pbytes >> LGES, W = pbytes >> 2, NB = (W + 31) >> 5;
     unsigned *ZBM = AUX, *CM = AUX + cap, *EB = AUX + 2 * cap, *PRE = AUX + 3 * cap;
     // payload word k holds bytes 0..3 of element 4k / ES at byte offset 4k % ES
@@ -346,7 +351,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_stage2(const S2Args a)
     if (tid == 0) {
       if (ns_tot == 0) tok[0] = (unsigned)W;  // no run at all
       ch[1] = ntok;
-      a.table[2 * bid + 1] = 8ull + 4ull * ntok + 4ull * nlit;
+      a.table[2 * bid + 1] = TB_FIN | (8ull + 4ull * ntok + 4ull * nlit);
     }
     for (int w = tid; w < W; w += NT) {
       const int g = w >> 5, b = w & 31;
@@ -375,10 +380,11 @@ __global__ void __launch_bounds__(PLACE_TILE) k_place(const PlaceArgs a)
   unsigned long long cb = 0;
   if (tid < n) {
     cb = a.table[2 * (c0 + tid) + 1];
-    if (cb == 0xFFFFFFFFFFFFFFFFull) {  // lost: leave an empty chunk
+    if (cb == TB_LOST) {  // lost: leave an empty chunk
       atomicCAS(&ws->status, 0u, ST_CAPACITY);
       cb = 0;
     }
+    cb = tb_size(cb);
   }
   unsigned ttot;
   const unsigned loc = block_exsum<NT>((unsigned)cb, s_u, ttot);  // < 2^32: 128 chunks of at most PMAX + 12 bytes
@@ -435,8 +441,9 @@ __global__ void __launch_bounds__(256) k_copy(const PlaceArgs a)
 {
   const int bid = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (bid >= a.nblocks) return;
-  const unsigned long long so = a.table[2 * bid], cb = a.table[2 * bid + 1];
-  if (cb == 0xFFFFFFFFFFFFFFFFull) return;
+  const unsigned long long so = a.table[2 * bid], cb0 = a.table[2 * bid + 1];
+  if (cb0 == TB_LOST) return;
+  const unsigned long long cb = tb_size(cb0);
   const unsigned long long off = *reinterpret_cast<const unsigned long long *>(a.out + HEADER_BYTES + 8ull * bid);
   if (a.data0 + off + cb > a.out_cap) return;
   const unsigned *__restrict__ src = reinterpret_cast<const unsigned *>(a.staging + so);
@@ -486,10 +493,11 @@ __global__ void __launch_bounds__(PLACE_TILE) k_place_multi(const __grid_constan
   unsigned long long cb = 0;
   if (tid < n) {
     cb = a.table[2 * (c0 + tid) + 1];
-    if (cb == 0xFFFFFFFFFFFFFFFFull) {  // lost: leave an empty chunk
+    if (cb == TB_LOST) {  // lost: leave an empty chunk
       atomicCAS(&ws->status, 0u, ST_CAPACITY);
       cb = 0;
     }
+    cb = tb_size(cb);
   }
   unsigned ttot;
   const unsigned loc = block_exsum<NT>((unsigned)cb, s_u, ttot);
@@ -548,8 +556,9 @@ __global__ void __launch_bounds__(256) k_copy_multi(const __grid_constant__ Batc
   for (int q = 1; q < bo.nf; ++q)
     if (bo.f[q].first <= bid) f = q;
   const FieldOut &fo = bo.f[f];
-  const unsigned long long so = a.table[2 * bid], cb = a.table[2 * bid + 1];
-  if (cb == 0xFFFFFFFFFFFFFFFFull) return;
+  const unsigned long long so = a.table[2 * bid], cb0 = a.table[2 * bid + 1];
+  if (cb0 == TB_LOST) return;
+  const unsigned long long cb = tb_size(cb0);
   const unsigned long long off =
       *reinterpret_cast<const unsigned long long *>(fo.out + HEADER_BYTES + 8ull * (bid - fo.first));
   if (fo.data0 + off + cb > fo.out_cap) return;

@@ -101,7 +101,8 @@ cudaError_t compress_batch_k(const StageMaps<MAXF> &maps, const FwdArgs &a, cons
 }
 
 template <int KIND>
-cudaError_t decompress_k(const InvArgs &a, const UnArgs &ua, int grid, int gridu, int gridub, cudaStream_t s)
+cudaError_t decompress_k(const CUtensorMap &om, const InvArgs &a, const UnArgs &ua, int grid, int gridu, int gridub,
+                         cudaStream_t s)
 {
   cudaError_t e;
   if (a.stage2) {
@@ -120,7 +121,7 @@ cudaError_t decompress_k(const InvArgs &a, const UnArgs &ua, int grid, int gridu
   }
   e = prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D);
   if (e != cudaSuccess) return e;
-  k_decompress2<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_D, s>>>(a);
+  k_decompress2<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_D, s>>>(om, a);
   return cudaGetLastError();
 }
 
@@ -209,13 +210,14 @@ extern "C" cudaError_t CZ_CAT(czl_compress_batch_, CZ_SUFFIX)(int kind, const St
   }
 }
 
-extern "C" cudaError_t CZ_CAT(czl_decompress_, CZ_SUFFIX)(int kind, const InvArgs *a, const UnArgs *ua, int grid,
-                                                           int gridu, int gridub, cudaStream_t s)
+extern "C" cudaError_t CZ_CAT(czl_decompress_, CZ_SUFFIX)(int kind, const CUtensorMap *om, const InvArgs *a,
+                                                           const UnArgs *ua, int grid, int gridu, int gridub,
+                                                           cudaStream_t s)
 {
   switch (kind) {
-    case W4: return decompress_k<W4>(*a, *ua, grid, gridu, gridub, s);
-    case W4LI: return decompress_k<W4LI>(*a, *ua, grid, gridu, gridub, s);
-    default: return decompress_k<W3AI>(*a, *ua, grid, gridu, gridub, s);
+    case W4: return decompress_k<W4>(*om, *a, *ua, grid, gridu, gridub, s);
+    case W4LI: return decompress_k<W4LI>(*om, *a, *ua, grid, gridu, gridub, s);
+    default: return decompress_k<W3AI>(*om, *a, *ua, grid, gridu, gridub, s);
   }
 }
 

@@ -24,7 +24,8 @@ struct StageMaps;
       int kind, const czp::StageMaps<32> *maps, const czp::FwdArgs *a, const czp::S2Args *sa,          \
       const czp::BatchOut *bo, const czp::PlaceArgs *pa, int grid, int grid2, int grid3, int tiles,    \
       cudaStream_t s);                                                                                  \
-  extern "C" cudaError_t czl_decompress_##sfx(int kind, const czp::InvArgs *a, const czp::UnArgs *ua, \
+  extern "C" cudaError_t czl_decompress_##sfx(int kind, const CUtensorMap *om, const czp::InvArgs *a,  \
+                                              const czp::UnArgs *ua,                                  \
                                               int grid, int gridu, int gridub, cudaStream_t s);       \
   extern "C" cudaError_t czl_dense_##sfx(int kind, int fwd, const czp::DenseArgs *a, int nblocks,   \
                                          cudaStream_t s);                                           \

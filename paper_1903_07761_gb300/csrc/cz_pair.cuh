@@ -218,8 +218,11 @@ struct G2 {
   // decompress: no tile; the whole payload always fits
   static constexpr int R2D0 = (XBI + ADBI) > ROWB ? (XBI + ADBI) : ROWB;
   static constexpr int R2D = (R2D0 + 127) / 128 * 128;
-  static constexpr int PBCAP = PMAX_AL < 65536 ? PMAX_AL : 65536;  // decompress payload buffer
-  static constexpr int SMEM_D = R2D + 2 * PBCAP;
+  // decompress payload buffer: whole payloads of up to PBCAP bytes (with
+  // 32^3 blocks most payloads, the rest read their values from global memory)
+  static constexpr int PBCAP = B == 32 ? (PMAX_AL < 16384 ? PMAX_AL : 16384) : PMAX_AL;
+  // planes | two payload buffers | output tile (stored by TMA)
+  static constexpr int SMEM_D = R2D + 2 * PBCAP + TILE;
   static_assert(SMEM_C <= 227 * 1024 - 1024, "stage kernel shared memory");
   static_assert(SMEM_D <= 227 * 1024 - 1024, "decompress shared memory");
   static_assert(SMEM_S2B <= 227 * 1024 - 1024, "stage-2 shared memory");
@@ -263,6 +266,26 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
                "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+
+// tiled 3D store shared -> global of one box, in the CTA's bulk group
+// (callers fence the generic writes to the tile and synchronise first)
+__device__ __forceinline__ void tma_store_tile(const CUtensorMap *tm, const void *src, int x, int y, int z)
+{
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<unsigned long long>(tm)),
+               "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// the CTA's bulk stores have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// the CTA's bulk stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// generic-proxy writes to shared memory, made visible to the async proxy
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // bounded wait for the mbarrier phase with the given parity; false on timeout
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
@@ -1043,7 +1066,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_unstage(const UnArgs a)
 }
 
 template <typename T, int B, int KIND>
-__global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
+__global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_constant__ CUtensorMap omap,
+                                                              const InvArgs a)
 {
   using G = G2<T, B>;
   using T2 = typename V2T<T>::type;
@@ -1055,6 +1079,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
   T *AD = reinterpret_cast<T *>(R2 + G::XBI);
   unsigned *ROWOFF = reinterpret_cast<unsigned *>(R2);
   unsigned char *BUF0 = smem + G::R2D;  // two payload buffers of G::PBCAP bytes
+  unsigned char *OT = BUF0 + 2 * G::PBCAP;  // output tile [z][y][x]
   __shared__ __align__(8) unsigned long long s_bar[2];
   __shared__ unsigned s_u[40];
   __shared__ unsigned s_nnz[2], s_bad[2];
@@ -1070,13 +1095,14 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
   const bool pre = a.stage2 != 0;  // decoded payloads sit in 16-byte aligned slots
 
   // metadata of block b into buffer slot j, and (with stage 2) the start
-  // of its payload copy; called by thread 0
-  auto fetch = [&](int b, int j) {
+  // of its payload copy; called by thread 0 with b's table entry (t0, t1)
+  // loaded ahead
+  auto fetch = [&](int b, int j, unsigned long long t0, unsigned long long t1) {
     unsigned bad = 0, nnz = 0;
     unsigned long long o0 = 0;
     if (pre) {  // decoded (and checked) by k_unstage
-      bad = a.table[2 * b + 1] != 0;
-      nnz = bad ? 0u : (unsigned)a.table[2 * b];
+      bad = t1 != 0;
+      nnz = bad ? 0u : (unsigned)t0;
     } else {
       const unsigned long long *tab = reinterpret_cast<const unsigned long long *>(a.in + HEADER_BYTES);
       o0 = tab[b];
@@ -1108,7 +1134,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
   }
   __syncthreads();
   __shared__ unsigned long long s_off;
-  if (tid == 0 && (int)blockIdx.x < a.nblocks) s_off = fetch(blockIdx.x, 0);
+  if (tid == 0 && (int)blockIdx.x < a.nblocks)
+    s_off = fetch(blockIdx.x, 0, pre ? a.table[2 * blockIdx.x] : 0ull, pre ? a.table[2 * blockIdx.x + 1] : 0ull);
   __syncthreads();
   unsigned phase[2] = {0u, 0u};
   int j = 0;
@@ -1116,6 +1143,13 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
   for (int bid = blockIdx.x; bid < a.nblocks; bid += gridDim.x, j ^= 1) {
     const int bx = bid % a.nbx, by = (bid / a.nbx) % a.nby, bz = bid / (a.nbx * a.nby);
     unsigned char *P = BUF0 + j * G::PBCAP;
+    // next block's table entry, loaded now and used after the scatter
+    const int nbid = bid + (int)gridDim.x;
+    unsigned long long nt0 = 0, nt1 = 0;
+    if (tid == 0 && pre && nbid < a.nblocks) {
+      nt0 = a.table[2 * nbid];
+      nt1 = a.table[2 * nbid + 1];
+    }
     const unsigned nnz = s_nnz[j];
     const int pbytes = HEAD + (int)nnz * ES;
     bool bad0 = s_bad[j] != 0;
@@ -1143,9 +1177,13 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
     const unsigned char *MASK = P + 64 * ES;
     if (tid == 0) s_badx = 0;
     __syncthreads();
+    // this thread's mask rows (z = 2ap, 2ap + 1 at row y) and, transposed
+    // over the row's lanes, its own z-columns (x0 and x0 + 1)
+    const unsigned w0 = bad0 ? 0u : get_row<B>(MASK, 2 * ap, y), w1 = bad0 ? 0u : get_row<B>(MASK, 2 * ap + 1, y);
+    unsigned me = w0, mo = w1;
+    bit_transpose<B>(me, mo, ap);
     if (!bad0) {
       // row populations -> row offsets; coarse positions carry no mask bit
-      const unsigned w0 = get_row<B>(MASK, 2 * ap, y), w1 = get_row<B>(MASK, 2 * ap + 1, y);
       ROWOFF[(2 * ap) * B + y] = __popc(w0);
       ROWOFF[(2 * ap + 1) * B + y] = __popc(w1);
       if ((y % Q) == 0) {
@@ -1176,38 +1214,46 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const InvArgs a)
     if (bad && tid == 0) atomicCAS(&ws->status, 0u, ST_CORRUPT);
 
     T2 v[B];
-    {
-      const T *COARSE = reinterpret_cast<const T *>(P);
-      const unsigned lowE = (1u << x0) - 1u, lowO = (2u << x0) - 1u;
 #pragma unroll
-      for (int z = 0; z < B; ++z) {
-        T2 rv;
-        rv.x = T(0);
-        rv.y = T(0);
-        if (!bad) {
-          const unsigned wd = get_row<B>(MASK, z, y);
-          if (wd) {
+    for (int z = 0; z < B; ++z) {
+      v[z].x = T(0);
+      v[z].y = T(0);
+    }
+    if (!bad) {
+      // kept values of this column pair (z unrolled: v[z] stays a register;
+      // threads whose columns keep nothing skip the rows entirely)
+      const unsigned lowE = (1u << x0) - 1u, lowO = (2u << x0) - 1u;
+      if (me | mo) {
+#pragma unroll
+        for (int z = 0; z < B; ++z) {
+          if (((me | mo) >> z) & 1u) {
+            const unsigned wd = get_row<B>(MASK, z, y);
             const unsigned base = ROWOFF[z * B + y];
-            if ((wd >> x0) & 1u) rv.x = VALS[base + __popc(wd & lowE)];
-            if ((wd >> (x0 + 1)) & 1u) rv.y = VALS[base + __popc(wd & lowO)];
+            if ((me >> z) & 1u) v[z].x = VALS[base + __popc(wd & lowE)];
+            if ((mo >> z) & 1u) v[z].y = VALS[base + __popc(wd & lowO)];
           }
-          if (cE && (z % Q) == 0) rv.x = COARSE[((z / Q) * 4 + y / Q) * 4 + x0 / Q];
         }
-        v[z] = rv;
+      }
+      if (cE) {
+        const T *COARSE = reinterpret_cast<const T *>(P);
+#pragma unroll
+        for (int z = 0; z < B; z += Q) v[z].x = COARSE[((z / Q) * 4 + y / Q) * 4 + x0 / Q];
       }
     }
     __syncthreads();  // buffer j and the row offsets are free
-    if (tid == 0 && bid + (int)gridDim.x < a.nblocks) s_off = fetch(bid + gridDim.x, j ^ 1);
+    if (tid == 0 && nbid < a.nblocks) s_off = fetch(nbid, j ^ 1, nt0, nt1);
     if (!bad) inv_all<T, B, KIND>(v, X, AD, ap, y, seg);
-    {
-      const size_t zs = (size_t)a.ny * a.nx;
-      T *dst = reinterpret_cast<T *>(a.field) + (size_t)(bz * B) * zs + (size_t)(by * B + y) * a.nx +
-               (size_t)(bx * B + x0);
-#pragma unroll
-      for (int z = 0; z < B; ++z) __stcs(reinterpret_cast<T2 *>(dst + z * zs), v[z]);
-    }
+    // block -> output tile -> TMA store, which drains while the next block
+    // is decoded; the tile is reused once the previous store has read it
+    if (tid == 0) bulk_wait_read();
     __syncthreads();
+#pragma unroll
+    for (int z = 0; z < B; ++z) *reinterpret_cast<T2 *>(OT + ((z * B + y) * B + x0) * ES) = v[z];
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) tma_store_tile(&omap, OT, bx * B, by * B, bz * B);
   }
+  if (tid == 0) bulk_wait_all();
 }
 
 // ============================================================ dense transforms
