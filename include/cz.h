@@ -57,6 +57,14 @@ enum { CZ_EPS_REL = 0, CZ_EPS_ABS = 1 };
  * never exceeds t (C: 127 / 1572 / 5331 for W4 at B = 8 / 16 / 32, 19 / 100 /
  * 249 for W3ai, 51 / 1229 / 4637 for W4li) */
 enum { CZ_BOUND_PAPER = 0, CZ_BOUND_STRICT = 1 };
+/* flags: CZ_FLAG_FAST selects the fast build of the kernels, which lets the
+ * compiler fuse multiply-adds (one rounding instead of two): coefficients
+ * move by a few ulps, so a detail next to the threshold may be kept or
+ * dropped differently and streams are no longer bit-identical to the exact
+ * build's, within the tolerances tests/test_gpu_fast.py states.  The flag
+ * is recorded in the stream header; decompression uses the build the
+ * stream was made with. */
+enum { CZ_FLAG_FAST = 1 };
 
 enum {
   CZ_OK = 0,
@@ -78,7 +86,7 @@ typedef struct cz_params {
   int32_t eps_mode;   /* CZ_EPS_REL (default) or CZ_EPS_ABS                 */
   int32_t stage2;     /* 1: byte shuffle + zero-RLE each chunk; 0: raw      */
   int32_t bound_mode; /* CZ_BOUND_PAPER (default) or CZ_BOUND_STRICT        */
-  int32_t flags;      /* reserved, must be 0                                */
+  int32_t flags;      /* 0 or CZ_FLAG_FAST                                  */
   double eps;         /* tolerance, >= 0                                    */
   double range;       /* >= 0: max - min supplied by the caller (skips the
                          min/max pass); < 0: computed on the device        */

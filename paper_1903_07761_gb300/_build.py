@@ -53,11 +53,13 @@ def needs_build() -> bool:
 def _jobs(verbose_ptxas: bool):
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
     jobs = []
-    for ctype, tname, b in INST:
-        obj = os.path.join(BUILD_DIR, f"cz_inst_{tname}_b{b}.o")
-        cmd = [nvcc(), *ARCH, *NVFLAGS, *extra, f"-DCZ_T={ctype}", f"-DCZ_TNAME={tname}",
-               f"-DCZ_B={b}", "-c", os.path.join(CSRC, "cz_inst.cu"), "-o", obj]
-        jobs.append((obj, cmd))
+    for fast in (False, True):
+        for ctype, tname, b in INST:
+            obj = os.path.join(BUILD_DIR, f"cz_inst_{tname}_b{b}{'_fast' if fast else ''}.o")
+            cmd = [nvcc(), *ARCH, *NVFLAGS, *extra, f"-DCZ_T={ctype}", f"-DCZ_TNAME={tname}",
+                   f"-DCZ_B={b}", *(["-DCZ_FAST"] if fast else []), "-c", os.path.join(CSRC, "cz_inst.cu"),
+                   "-o", obj]
+            jobs.append((obj, cmd))
     for name in ("cz_api", "cz_noalloc", "cz_serve"):
         obj = os.path.join(BUILD_DIR, f"{name}.o")
         jobs.append((obj, [nvcc(), *ARCH, *NVFLAGS, *extra, "-c", os.path.join(CSRC, f"{name}.cu"),

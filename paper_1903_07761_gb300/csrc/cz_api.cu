@@ -39,7 +39,7 @@ int check(const cz_params *p, Shape *sh)
   if (p->eps_mode != CZ_EPS_REL && p->eps_mode != CZ_EPS_ABS) return CZ_ERR_ARG;
   if (p->stage2 != 0 && p->stage2 != 1) return CZ_ERR_ARG;
   if (p->bound_mode != CZ_BOUND_PAPER && p->bound_mode != CZ_BOUND_STRICT) return CZ_ERR_ARG;
-  if (p->flags != 0) return CZ_ERR_ARG;
+  if (p->flags & ~CZ_FLAG_FAST) return CZ_ERR_ARG;
   if (!(p->eps >= 0) || std::isinf(p->eps)) return CZ_ERR_ARG;
   if (std::isnan(p->range)) return CZ_ERR_ARG;
   if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0) return CZ_ERR_ARG;
@@ -190,15 +190,16 @@ struct Lanes {
         czl_slot_bytes_##sfx                                                                               \
   }
 
-Lanes lanes_for(int dtype, int B)
+Lanes lanes_for(const cz_params &p)
 {
-  if (dtype == CZ_F32) {
-    if (B == 8) return CZ_LANES(f32_b8);
-    if (B == 16) return CZ_LANES(f32_b16);
-    return CZ_LANES(f32_b32);
+  const bool fast = (p.flags & CZ_FLAG_FAST) != 0;
+  if (p.dtype == CZ_F32) {
+    if (p.block == 8) return fast ? CZ_LANES(f32_b8_fast) : CZ_LANES(f32_b8);
+    if (p.block == 16) return fast ? CZ_LANES(f32_b16_fast) : CZ_LANES(f32_b16);
+    return fast ? CZ_LANES(f32_b32_fast) : CZ_LANES(f32_b32);
   }
-  if (B == 8) return CZ_LANES(f64_b8);
-  return CZ_LANES(f64_b16);
+  if (p.block == 8) return fast ? CZ_LANES(f64_b8_fast) : CZ_LANES(f64_b8);
+  return fast ? CZ_LANES(f64_b16_fast) : CZ_LANES(f64_b16);
 }
 
 int sm_count()
@@ -212,7 +213,7 @@ int sm_count()
 // persistent grids: one CTA per resident slot, at most one per block
 int grid_for(const cz_params *p, const Shape &sh, int which)
 {
-  const Lanes L = lanes_for(p->dtype, p->block);
+  const Lanes L = lanes_for(*p);
   const int occ = L.occupancy(p->kind, which);
   const long long g = (long long)sm_count() * (occ > 0 ? occ : 1);
   return (int)(g < sh.nblocks ? g : sh.nblocks);
@@ -231,7 +232,7 @@ struct WsLayout {
 
 WsLayout ws_layout(const cz_params *p, const Shape &sh)
 {
-  const Lanes L = lanes_for(p->dtype, p->block);
+  const Lanes L = lanes_for(*p);
   WsLayout w;
   w.grid = grid_for(p, sh, 0);
   w.grid2 = grid_for(p, sh, 2);
@@ -302,7 +303,7 @@ std::vector<Group> plan_batch(int n, const cz_params *p)
   std::vector<int> open;  // index in `out` of the last group of each signature
   auto same = [&](const cz_params &a, const cz_params &b) {
     return a.dtype == b.dtype && a.block == b.block && a.kind == b.kind && a.stage2 == b.stage2 &&
-           a.bound_mode == b.bound_mode;
+           a.bound_mode == b.bound_mode && a.flags == b.flags;
   };
   for (int i = 0; i < n; ++i) {
     int g = -1;
@@ -352,7 +353,7 @@ BatchLayout batch_layout(const Group &g, const cz_params *p, const BatchKnobs &k
   w.grid3 = grid_for(&p0, all, 3) / (kn.s2_div > 0 ? kn.s2_div : 1);
   if (w.grid2 < 1) w.grid2 = 1;
   if (w.grid3 < 1) w.grid3 = 1;
-  const Lanes L = lanes_for(p0.dtype, p0.block);
+  const Lanes L = lanes_for(p0);
   w.keys = WS_HDR;
   w.lb = w.keys + 16 * MAXF;
   w.table = w.lb + (8ull * w.tiles + 255) / 256 * 256;
@@ -376,7 +377,7 @@ unsigned long long batch_signature(int n, const cz_params *p)
     mix((unsigned long long)p[i].ny);
     mix((unsigned long long)p[i].nz);
     mix((unsigned long long)(p[i].block | p[i].dtype << 8 | p[i].kind << 12 | p[i].stage2 << 16 |
-                             p[i].bound_mode << 20));
+                             p[i].bound_mode << 20 | p[i].flags << 24));
   }
   return h;
 }
@@ -506,7 +507,8 @@ int compress_batch_impl(int n, const cz_params *p, const void *const *d_fields, 
     pa.kind = p0.kind;
     pa.dtype = p0.dtype;
     pa.bound_mode = p0.bound_mode;
-    const Lanes L = lanes_for(p0.dtype, p0.block);
+    pa.flags = p0.flags;
+    const Lanes L = lanes_for(p0);
     if (L.compress_batch(p0.kind, &maps, &a, &sa, &bo, &pa, w.grid, w.grid2, w.grid3, w.tiles, s) != cudaSuccess)
       return CZ_ERR_CUDA;
   }
@@ -572,7 +574,7 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
                                              : run_minmax<double>(d_field, n, ws, s);
     if (e != cudaSuccess) return CZ_ERR_CUDA;
   }
-  const Lanes L = lanes_for(p->dtype, p->block);
+  const Lanes L = lanes_for(*p);
   FwdArgs a{};
   a.field = d_field;
   a.ws = d_ws;
@@ -609,6 +611,7 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
   pa.range = p->range;
   pa.cnorm = a.cnorm;
   pa.bound_mode = p->bound_mode;
+  pa.flags = p->flags;
   pa.nx = p->nx;
   pa.ny = p->ny;
   pa.nz = p->nz;
@@ -713,6 +716,7 @@ int cz_stream_concat(int n, const void *const *h_streams, const size_t *sizes, v
     if (r) {  // slabs of one field: everything but nz must agree, eps and the threshold included
       if (pr.nx != p0.nx || pr.ny != p0.ny || pr.block != p0.block || pr.dtype != p0.dtype || pr.kind != p0.kind ||
           pr.stage2 != p0.stage2 || pr.eps_mode != p0.eps_mode || pr.bound_mode != p0.bound_mode ||
+          pr.flags != p0.flags ||
           std::memcmp(&tr, &t0, 8) != 0 || std::memcmp(h + 32, h0 + 32, 8) != 0 ||
           std::memcmp(h + 64, h0 + 64, 8) != 0)
         return CZ_ERR_ARG;
@@ -819,6 +823,7 @@ int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used)
   q.stage2 = h[23];
   q.eps_mode = h[24];
   q.bound_mode = h[26];
+  q.flags = h[27] & CZ_FLAG_FAST;
   std::memcpy(&q.eps, h + 32, 8);
   std::memcpy(&q.range, h + 64, 8);
   if (std::isnan(q.range)) return CZ_ERR_CORRUPT;
@@ -853,7 +858,7 @@ int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header, void 
   const unsigned long long total = rd64(hb + 80), data_bytes = rd64(hb + 72);
   if (total > in_bytes || sh.data0 + data_bytes != total) return CZ_ERR_CORRUPT;
   if ((size_t)p.nx * p.ny * p.nz * sh.es > field_cap) return CZ_ERR_CAPACITY;
-  const Lanes L = lanes_for(p.dtype, p.block);
+  const Lanes L = lanes_for(p);
   // workspace: header | block table (nnz, bad flag) | one staging slot per
   // block for the decoded stage-2 payloads (within cz_workspace_size)
   const size_t slot = (size_t)L.slot_bytes();
@@ -934,7 +939,7 @@ static int dense(const cz_params *p, const void *src, void *dst, int fwd, void *
   a.nbx = sh.nbx;
   a.nby = sh.nby;
   a.nbz = sh.nbz;
-  const Lanes L = lanes_for(p->dtype, p->block);
+  const Lanes L = lanes_for(*p);
   return L.dense(p->kind, fwd, &a, sh.nblocks, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
              ? CZ_OK
              : CZ_ERR_CUDA;

@@ -43,7 +43,7 @@ struct PlaceArgs {
   unsigned long long out_cap, data0;
   double eps, range, cnorm;
   int nx, ny, nz, nblocks;
-  int block, levels, eps_mode, stage2, kind, dtype, bound_mode;
+  int block, levels, eps_mode, stage2, kind, dtype, bound_mode, flags;
 };
 
 constexpr int PLACE_TILE = 128;  // chunks (and threads) per k_place CTA
@@ -422,6 +422,7 @@ __global__ void __launch_bounds__(PLACE_TILE) k_place(const PlaceArgs a)
     h[24] = (unsigned char)a.eps_mode;
     h[25] = (unsigned char)a.levels;
     h[26] = (unsigned char)a.bound_mode;
+    h[27] = (unsigned char)a.flags;
     st_le<unsigned>(h + 28, (unsigned)a.nblocks);
     st_le_f64(h + 32, a.eps);
     st_le_f64(h + 40, (double)t);
@@ -534,6 +535,7 @@ __global__ void __launch_bounds__(PLACE_TILE) k_place_multi(const __grid_constan
     h[24] = (unsigned char)fo.eps_mode;
     h[25] = (unsigned char)a.levels;
     h[26] = (unsigned char)a.bound_mode;
+    h[27] = (unsigned char)a.flags;
     st_le<unsigned>(h + 28, (unsigned)fo.nblocks);
     st_le_f64(h + 32, fo.eps);
     st_le_f64(h + 40, (double)t);

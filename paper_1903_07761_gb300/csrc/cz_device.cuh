@@ -22,18 +22,38 @@
 #include <cstdint>
 #include <cuda/atomic>
 
+// Two builds of the kernels live in one library: the exact one (default)
+// rounds every operation on its own, in the oracle's order, so streams are
+// bit-identical to the oracle's; the fast one (translation units compiled
+// with CZ_FAST) lets the compiler contract multiply-adds into fused ones
+// (one rounding), which changes coefficients by a few ulps.  The fast build
+// gets its own namespaces so that the two sets of kernels never mix.
+#ifdef CZ_FAST
+#define czd czd_fast
+#define czp czp_fast
+#endif
+
 namespace czd {
 
 constexpr unsigned FULL = 0xffffffffu;
 enum { W4 = 0, W4LI = 1, W3AI = 2 };
 
 // ------------------------------------------------------------ arithmetic
+#ifdef CZ_FAST
+__device__ __forceinline__ float addx(float a, float b) { return a + b; }
+__device__ __forceinline__ double addx(double a, double b) { return a + b; }
+__device__ __forceinline__ float subx(float a, float b) { return a - b; }
+__device__ __forceinline__ double subx(double a, double b) { return a - b; }
+__device__ __forceinline__ float mulx(float a, float b) { return a * b; }
+__device__ __forceinline__ double mulx(double a, double b) { return a * b; }
+#else
 __device__ __forceinline__ float addx(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double addx(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float subx(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double subx(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ float mulx(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mulx(double a, double b) { return __dmul_rn(a, b); }
+#endif
 __device__ __forceinline__ float absx(float a) { return fabsf(a); }
 __device__ __forceinline__ double absx(double a) { return fabs(a); }
 

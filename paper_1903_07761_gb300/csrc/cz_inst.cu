@@ -1,6 +1,7 @@
 // cz_inst.cu -- kernel instantiations for one (element type, block edge).
 // Built once per combination with -DCZ_T=float|double -DCZ_TNAME=f32|f64
-// -DCZ_B=8|16|32 so the heavily unrolled kernels compile in parallel.
+// -DCZ_B=8|16|32 (and once more with -DCZ_FAST for the contracting build)
+// so the heavily unrolled kernels compile in parallel.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -184,7 +185,11 @@ int occupancy_d()
 
 #define CZ_CAT2(a, b) a##b
 #define CZ_CAT(a, b) CZ_CAT2(a, b)
+#ifdef CZ_FAST
+#define CZ_SUFFIX CZ_CAT(CZ_CAT(CZ_CAT(CZ_TNAME, _b), CZ_B), _fast)
+#else
 #define CZ_SUFFIX CZ_CAT(CZ_CAT(CZ_TNAME, _b), CZ_B)
+#endif
 
 extern "C" cudaError_t CZ_CAT(czl_compress_, CZ_SUFFIX)(int kind, const CUtensorMap *tm, const FwdArgs *a,
                                                          const S2Args *sa, const PlaceArgs *pa, int grid,

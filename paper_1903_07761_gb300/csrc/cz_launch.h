@@ -37,3 +37,8 @@ CZ_DECLARE_LAUNCHERS(f32_b16)
 CZ_DECLARE_LAUNCHERS(f32_b32)
 CZ_DECLARE_LAUNCHERS(f64_b8)
 CZ_DECLARE_LAUNCHERS(f64_b16)
+CZ_DECLARE_LAUNCHERS(f32_b8_fast)
+CZ_DECLARE_LAUNCHERS(f32_b16_fast)
+CZ_DECLARE_LAUNCHERS(f32_b32_fast)
+CZ_DECLARE_LAUNCHERS(f64_b8_fast)
+CZ_DECLARE_LAUNCHERS(f64_b16_fast)

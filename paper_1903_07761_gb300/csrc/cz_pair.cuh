@@ -138,6 +138,14 @@ __device__ __forceinline__ double2 mk2(double s) { return make_double2(s, s); }
 // packed f32x2 multiply and add are each exact, but chained packed
 // multiply -> add sequences were measured to differ from separately rounded
 // scalar ops: they are not used on the exact path.)
+#ifdef CZ_FAST
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 sub2(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+#else
 __device__ __forceinline__ float2 add2(float2 a, float2 b)
 {
   return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
@@ -163,6 +171,7 @@ __device__ __forceinline__ double2 sub2(double2 a, double2 b)
 {
   return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y));
 }
+#endif
 
 // significance: keep iff !(|d| < t) (ties kept; a NaN detail or a NaN
 // threshold keeps the value)

@@ -95,7 +95,7 @@ class Ranges {
 bool same_group(const cz_params &a, const cz_params &b)
 {
   return a.dtype == b.dtype && a.block == b.block && a.kind == b.kind && a.stage2 == b.stage2 &&
-         a.bound_mode == b.bound_mode;
+         a.bound_mode == b.bound_mode && a.flags == b.flags;
 }
 
 class Server {

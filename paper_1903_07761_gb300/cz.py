@@ -20,6 +20,7 @@ W4, W4LI, W3AI = 0, 1, 2
 F32, F64 = 0, 1
 EPS_REL, EPS_ABS = 0, 1
 BOUND_PAPER, BOUND_STRICT = 0, 1
+FLAG_FAST = 1
 OK, ERR_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_TIMEOUT, ERR_CUDA, ERR_BUDGET = 0, -1, -2, -3, -4, -5, -6
 HEADER_BYTES = 128
 NOALLOC_WS_BYTES = 64 << 20  # CZ_NOALLOC_WS_BYTES
@@ -200,12 +201,13 @@ def cz_inverse_dense(p: Params, d_coef: int, d_field: int, stream: int) -> int:
 
 # ------------------------------------------------------------------ torch conveniences
 def params_for(shape, dtype_is_f64: bool, block: int, kind, eps: float, eps_mode: int = EPS_REL,
-               stage2: bool = True, range_: float = -1.0, bound_mode: int = BOUND_PAPER) -> Params:
+               stage2: bool = True, range_: float = -1.0, bound_mode: int = BOUND_PAPER,
+               fast: bool = False) -> Params:
     nz, ny, nx = shape
     if isinstance(kind, str):
         kind = KINDS[kind]
     return Params(nx, ny, nz, block, F64 if dtype_is_f64 else F32, kind, eps_mode,
-                  int(stage2), int(bound_mode), 0, float(eps), float(range_))
+                  int(stage2), int(bound_mode), FLAG_FAST if fast else 0, float(eps), float(range_))
 
 
 def _stream(stream):
@@ -231,7 +233,7 @@ class Workspace:
 
 def compress(field, block: int = 32, kind="w4", eps: float = 1e-3, eps_mode: int = EPS_REL,
              stage2: bool = True, range_: float = -1.0, out=None, ws: Workspace | None = None,
-             stream=None, check: bool = True, bound_mode: int = BOUND_PAPER):
+             stream=None, check: bool = True, bound_mode: int = BOUND_PAPER, fast: bool = False):
     """Compress a contiguous CUDA tensor [nz, ny, nx] (float32/float64).
 
     Returns (stream_tensor, nbytes_tensor); the stream is stream_tensor[:nbytes].
@@ -240,7 +242,7 @@ def compress(field, block: int = 32, kind="w4", eps: float = 1e-3, eps_mode: int
     import torch
     assert field.is_cuda and field.is_contiguous() and field.dim() == 3
     p = params_for(tuple(field.shape), field.dtype == torch.float64, block, kind, eps, eps_mode,
-                   stage2, range_, bound_mode)
+                   stage2, range_, bound_mode, fast)
     cap = cz_compress_bound(p)
     if out is None or out.numel() < cap:
         out = torch.empty(cap, dtype=torch.uint8, device=field.device)

@@ -127,9 +127,11 @@ def test_bound_mode_and_flags_are_checked(cz):
     with pytest.raises(cz.CzError):
         cz.cz_compress_bound(p)
     p = cz.params_for((32, 32, 32), False, 32, "w4", 1e-3, cz.EPS_REL, True, 1.0)
-    p.flags = 1
+    p.flags = 2  # unknown flag
     with pytest.raises(cz.CzError):
         cz.cz_compress_bound(p)
+    p.flags = cz.FLAG_FAST
+    assert cz.cz_compress_bound(p) > 0
 
 
 def test_struct_layouts_match_the_header(cz, tmp_path):
