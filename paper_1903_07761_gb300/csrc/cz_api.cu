@@ -226,9 +226,11 @@ size_t lb_bytes(const Shape &sh) { return (8ull * sh.nblocks + 255) / 256 * 256;
 size_t table_bytes(const Shape &sh) { return (16ull * sh.nblocks + 255) / 256 * 256; }
 
 struct WsLayout {
-  size_t lb, table, staging, total, arena;
+  size_t lb, table, big, staging, total, arena;
   int grid, grid2, grid3;
 };
+
+size_t big_bytes(long long nblocks) { return (4ull * nblocks + 255) / 256 * 256; }
 
 WsLayout ws_layout(const cz_params *p, const Shape &sh)
 {
@@ -239,7 +241,8 @@ WsLayout ws_layout(const cz_params *p, const Shape &sh)
   w.grid3 = grid_for(p, sh, 3);
   w.lb = WS_HDR;
   w.table = w.lb + lb_bytes(sh);
-  w.staging = w.table + table_bytes(sh);
+  w.big = w.table + table_bytes(sh);
+  w.staging = w.big + big_bytes(sh.nblocks);
   // blocks are dealt round robin to the stage CTAs
   w.arena = (((size_t)sh.nblocks + w.grid - 1) / w.grid) * (size_t)L.slot_bytes();
   w.total = w.staging + w.arena * (size_t)w.grid;
@@ -326,7 +329,7 @@ struct BatchKnobs {
 };
 
 struct BatchLayout {
-  size_t keys, lb, table, staging, total, arena;
+  size_t keys, lb, table, big, staging, total, arena;
   int grid, grid2, grid3, tiles, nblocks;
 };
 
@@ -357,7 +360,8 @@ BatchLayout batch_layout(const Group &g, const cz_params *p, const BatchKnobs &k
   w.keys = WS_HDR;
   w.lb = w.keys + 16 * MAXF;
   w.table = w.lb + (8ull * w.tiles + 255) / 256 * 256;
-  w.staging = w.table + (16ull * w.nblocks + 255) / 256 * 256;
+  w.big = w.table + (16ull * w.nblocks + 255) / 256 * 256;
+  w.staging = w.big + big_bytes(w.nblocks);
   w.arena = (((size_t)w.nblocks + w.grid - 1) / w.grid) * (size_t)L.slot_bytes();
   w.total = w.staging + w.arena * (size_t)w.grid;
   return w;
@@ -483,15 +487,21 @@ int compress_batch_impl(int n, const cz_params *p, const void *const *d_fields, 
     FwdArgs a{};
     a.ws = d_ws;
     a.keys = keys;
+    a.biglist = reinterpret_cast<int *>(wsb + w.big);
     a.staging = wsb + w.staging;
     a.arena_bytes = w.arena;
     a.table = reinterpret_cast<unsigned long long *>(wsb + w.table);
     a.cnorm = threshold_divisor(&p0);
     a.nblocks = w.nblocks;
     a.nf = nf;
+    a.stage2 = p0.stage2;
+    a.kind = p0.kind;
+    a.dtype = p0.dtype;
     S2Args sa{};
     sa.staging = a.staging;
     sa.table = a.table;
+    sa.ws = d_ws;
+    sa.biglist = a.biglist;
     sa.nblocks = w.nblocks;
     PlaceArgs pa{};
     pa.staging = a.staging;
@@ -578,6 +588,7 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
   FwdArgs a{};
   a.field = d_field;
   a.ws = d_ws;
+  a.biglist = reinterpret_cast<int *>(wsb + wl.big);
   a.staging = wsb + wl.staging;
   a.arena_bytes = wl.arena;
   a.table = reinterpret_cast<unsigned long long *>(wsb + wl.table);
@@ -598,6 +609,8 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
   S2Args sa{};
   sa.staging = a.staging;
   sa.table = a.table;
+  sa.ws = d_ws;
+  sa.biglist = a.biglist;
   sa.nblocks = sh.nblocks;
   PlaceArgs pa{};
   pa.staging = a.staging;
@@ -859,10 +872,12 @@ int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header, void 
   if (total > in_bytes || sh.data0 + data_bytes != total) return CZ_ERR_CORRUPT;
   if ((size_t)p.nx * p.ny * p.nz * sh.es > field_cap) return CZ_ERR_CAPACITY;
   const Lanes L = lanes_for(p);
-  // workspace: header | block table (nnz, bad flag) | one staging slot per
-  // block for the decoded stage-2 payloads (within cz_workspace_size)
+  // workspace: header | block table (nnz, bad flag) | list of the large
+  // chunks | one staging slot per block for the decoded stage-2 payloads
+  // (within cz_workspace_size)
   const size_t slot = (size_t)L.slot_bytes();
-  const size_t need = p.stage2 ? WS_HDR + table_bytes(sh) + (size_t)sh.nblocks * slot : (size_t)WS_HDR;
+  const size_t need =
+      p.stage2 ? WS_HDR + table_bytes(sh) + big_bytes(sh.nblocks) + (size_t)sh.nblocks * slot : (size_t)WS_HDR;
   if (ws_bytes < need) return CZ_ERR_CAPACITY;
   if (cudaMemsetAsync(d_ws, 0, WS_HDR, s) != cudaSuccess) return CZ_ERR_CUDA;
   unsigned char *wsb = reinterpret_cast<unsigned char *>(d_ws);
@@ -881,11 +896,13 @@ int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header, void 
   a.nblocks = sh.nblocks;
   a.stage2 = p.stage2;
   a.table = reinterpret_cast<const unsigned long long *>(wsb + WS_HDR);
-  a.staging = wsb + WS_HDR + table_bytes(sh);
+  a.staging = wsb + WS_HDR + table_bytes(sh) + big_bytes(sh.nblocks);
   a.slot = slot;
   UnArgs ua{};
   ua.in = a.in;
-  ua.staging = wsb + WS_HDR + table_bytes(sh);
+  ua.staging = wsb + WS_HDR + table_bytes(sh) + big_bytes(sh.nblocks);
+  ua.ws = d_ws;
+  ua.biglist = reinterpret_cast<int *>(wsb + WS_HDR + table_bytes(sh));
   ua.table = reinterpret_cast<unsigned long long *>(wsb + WS_HDR);
   ua.in_bytes = total;
   ua.data0 = sh.data0;

@@ -29,6 +29,8 @@ namespace czp {
 struct S2Args {
   unsigned char *staging;
   unsigned long long *table;  // per block: slot offset, chunk bytes (~0: lost)
+  const void *ws;             // header: count of large payloads (nbig)
+  const int *biglist;         // ids of the blocks with large payloads
   int nblocks;
 };
 
@@ -214,6 +216,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
         unsigned *hw = reinterpret_cast<unsigned *>(arena + so);
         hw[0] = nnz;
         hw[1] = 0u;
+        if (a.stage2 && pbytes > G::SHCAP) a.biglist[atomicAdd(&ws->nbig, 1u)] = bid;  // for the large stage-2 launch
       } else {
         atomicCAS(&ws->status, 0u, ST_CAPACITY);
       }
@@ -235,12 +238,17 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_stage2(const S2Args a)
   constexpr int cap = BIG ? G::NBWMAX : G::NBS;     // bitmap words
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ unsigned s_u[40];
+  __shared__ int s_i[40];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   unsigned char *SH = smem;
   const unsigned *SH32 = reinterpret_cast<const unsigned *>(smem);
   unsigned *AUX = reinterpret_cast<unsigned *>(smem + CAPB);
 
-  for (int bid = blockIdx.x; bid < a.nblocks; bid += gridDim.x) {
+  // the small launch visits every block (and skips the large payloads); the
+  // large launch visits only the blocks the stage kernel listed
+  const int count = BIG ? (int)reinterpret_cast<const WsHdr *>(a.ws)->nbig : a.nblocks;
+  for (int it = blockIdx.x; it < count; it += gridDim.x) {
+    const int bid = BIG ? a.biglist[it] : it;
     const unsigned long long so = a.table[2 * bid], cb = a.table[2 * bid + 1];
     if (cb == TB_LOST || (cb & TB_FIN)) continue;  // staging overflow, or finished by the other launch
     const int pbytes = (int)cb - 8;
@@ -310,6 +318,19 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_stage2(const S2Args a)
     const unsigned nlit = (unsigned)W - nc_tot;
     unsigned *tok = ch + 2;
     unsigned *lit = tok + ntok;
+    // Run ends (Eb bits) around this thread's words: the last one before
+    // them (block max-scan, 0 if none -- no run ends at position 0) and the
+    // first one after them (block min-scan, W if none).
+    int my_last = 0, my_first = W;
+    for (int q = 0; q < KB; ++q) {
+      const int g = tid * KB + q;
+      if (g < NB && EB[g]) {
+        my_last = max(my_last, g * 32 + 31 - (int)__clz(EB[g]));
+        my_first = min(my_first, g * 32 + __ffs(EB[g]) - 1);
+      }
+    }
+    int pe_words = block_exmax<NT>(my_last, 0, s_i);
+    const int ne_after = block_rexmin<NT>(my_first, W, s_i);
     // one token per run: (literal words since the previous run, run length);
     // a final (literals, 0) token when the payload does not end in a run
     for (int q = 0; q < KB; ++q) {
@@ -323,23 +344,16 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_stage2(const S2Args a)
         const int b = __ffs(S) - 1;
         S &= S - 1u;
         const int p = g * 32 + b;
-        int pe = 0, ne = W;  // previous run's end (or 0), this run's end (or W)
+        // previous run's end (or 0), this run's end (or W)
         const unsigned below = Eb & ((1u << b) - 1u), above = Eb & ~((2u << b) - 1u);
-        if (below) {
-          pe = g * 32 + 31 - __clz(below);
-        } else {
-          for (int h = g - 1; h >= 0; --h)
-            if (EB[h]) {
-              pe = h * 32 + 31 - __clz(EB[h]);
-              break;
-            }
-        }
+        const int pe = below ? g * 32 + 31 - (int)__clz(below) : pe_words;
+        int ne = ne_after;
         if (above) {
           ne = g * 32 + __ffs(above) - 1;
         } else {
-          for (int h = g + 1; h < NB; ++h)
-            if (EB[h]) {
-              ne = h * 32 + __ffs(EB[h]) - 1;
+          for (int h = q + 1; h < KB && tid * KB + h < NB; ++h)  // this thread's later words
+            if (EB[tid * KB + h]) {
+              ne = (tid * KB + h) * 32 + __ffs(EB[tid * KB + h]) - 1;
               break;
             }
         }
@@ -347,6 +361,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_stage2(const S2Args a)
         if (k + 1 == ns_tot && !lastc) tok[k + 1] = (unsigned)(W - ne);
         ++k;
       }
+      if (Eb) pe_words = g * 32 + 31 - (int)__clz(Eb);
     }
     if (tid == 0) {
       if (ns_tot == 0) tok[0] = (unsigned)W;  // no run at all

@@ -44,7 +44,8 @@ constexpr unsigned WAIT_LIMIT = 1u << 24;
 struct WsHdr {
   unsigned status;
   unsigned ticket;
-  unsigned pad0, pad1;
+  unsigned nbig;  // blocks whose payload exceeds the small stage-2 CTAs' capacity
+  unsigned pad1;
   unsigned long long minkey, maxkey;
   unsigned long long out_bytes;
   unsigned long long bump;  // staging bytes handed out so far
@@ -85,6 +86,7 @@ struct BatchOut {
 struct FwdArgs {
   const void *field;
   void *ws;
+  int *biglist;  // ids of the blocks with large payloads (count in the header's nbig)
   unsigned long long *keys;  // batched: min/max keys, two per field
   unsigned char *staging;     // raw payloads, one arena per CTA
   unsigned long long *table;  // per block: staging offset, nnz
@@ -110,6 +112,8 @@ struct UnArgs {
   const unsigned char *in;
   unsigned char *staging;
   unsigned long long *table;  // per block: nnz, bad flag
+  void *ws;                   // header: count of large chunks (nbig)
+  int *biglist;               // ids of the chunks with large payloads
   unsigned long long in_bytes, data0, slot;
   int nblocks;
 };
@@ -219,9 +223,9 @@ struct G2 {
   static constexpr int SMEM_S2 = SHCAP + 4 * NBS * 4;
   static constexpr bool HAS_BIG = SHCAP < PMAX;
   static constexpr int SMEM_S2B = PMAX_AL + 4 * NBWMAX * 4;
-  // stage-2 inverse kernels: payload + two token prefix arrays
-  static constexpr int SMEM_U = SHCAP + 2 * 128 * 4;
-  static constexpr int SMEM_UB = PMAX_AL + 2 * 512 * 4;
+  // stage-2 inverse kernels: payload + three per-token arrays
+  static constexpr int SMEM_U = SHCAP + 3 * 128 * 4;
+  static constexpr int SMEM_UB = PMAX_AL + 3 * 512 * 4;
   // dense kernels
   static constexpr int SMEM_DN0 = (XBF + ADBF) > (XBI + ADBI) ? (XBF + ADBF) : (XBI + ADBI);
   // decompress: no tile; the whole payload always fits
@@ -959,10 +963,10 @@ __device__ __forceinline__ void threshold_of(double eps, int eps_mode, double cn
 }
 
 // ============================================================ decompress
-// ---- stage-2 inverse, one chunk at a time: the tokens are expanded by
-// block scans of (literal words, output words) per token, each literal
-// word is unshuffled into the payload in shared memory, and the payload is
-// written to the block's staging slot.  Small CTAs take the payloads of up
+// ---- stage-2 inverse, one chunk at a time: block scans of (literal
+// words, output words) per token place every token; a warp per token copies
+// its literals and writes its zero run into the shuffled payload in shared
+// memory, which is then unshuffled into the block's staging slot.  Small CTAs take the payloads of up
 // to G2::SHCAP bytes (and the malformed chunks), a second launch with large
 // CTAs the rest.
 template <typename T, int B, bool BIG>
@@ -973,14 +977,20 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_unstage(const UnArgs a)
   constexpr int CAPB = BIG ? G::PMAX_AL : G::SHCAP;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char *P = smem;
-  unsigned *TL = reinterpret_cast<unsigned *>(smem + CAPB);
-  unsigned *TO = TL + NT;
+  unsigned *TL = reinterpret_cast<unsigned *>(smem + CAPB);  // per token of a round: first literal,
+  unsigned *TO = TL + NT;                                      // first output word,
+  unsigned *TK = TO + NT;                                      // the token
   __shared__ unsigned s_u[40];
   __shared__ unsigned s_nnz, s_ntok, s_bad;
   __shared__ unsigned long long s_off, s_len;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
-  for (int bid = blockIdx.x; bid < a.nblocks; bid += gridDim.x) {
+  WsHdr *wsh = reinterpret_cast<WsHdr *>(a.ws);
+  // the small launch visits every chunk and lists the large ones, which the
+  // large launch then visits alone
+  const int count = BIG ? (int)*(volatile const unsigned *)&wsh->nbig : a.nblocks;
+  for (int it = blockIdx.x; it < count; it += gridDim.x) {
+    const int bid = BIG ? a.biglist[it] : it;
     if (tid == 0) {
       unsigned bad = 0;
       const unsigned long long *tab = reinterpret_cast<const unsigned long long *>(a.in + HEADER_BYTES);
@@ -1005,7 +1015,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_unstage(const UnArgs a)
     __syncthreads();
     const unsigned nnz = s_nnz;
     const int pbytes = 64 * ES + G::MASKB + (int)nnz * ES;
-    if (s_bad ? BIG : ((pbytes > G::SHCAP) != BIG)) {  // the other launch's chunk
+    if (!BIG && !s_bad && pbytes > G::SHCAP) {  // the large launch's chunk
+      if (tid == 0) a.biglist[atomicAdd(&wsh->nbig, 1u)] = bid;
       __syncthreads();
       continue;
     }
@@ -1017,8 +1028,6 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_unstage(const UnArgs a)
       const unsigned *tok = c32 + 2;
       const unsigned *lit = tok + ntok;
       unsigned *SH32 = reinterpret_cast<unsigned *>(P);  // the shuffled payload
-      for (int w = tid; w < W; w += NT) SH32[w] = 0u;
-      __syncthreads();
       unsigned lit_carry = 0, out_carry = 0;
       bool bad = false;
       for (unsigned r0 = 0; r0 < ntok; r0 += NT) {
@@ -1030,22 +1039,20 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_unstage(const UnArgs a)
         const unsigned op = block_exsum<NT>(run, s_u, to_);
         TL[tid] = lit_carry + lp;
         TO[tid] = out_carry + op;
+        TK[tid] = tk;
         __syncthreads();
+        // one warp per token: its literal words (coalesced), then its zero
+        // run; tokens that would read past the literals or write past the
+        // payload mark the chunk bad and write nothing
         const unsigned cnt = (ntok - r0) < (unsigned)NT ? (ntok - r0) : (unsigned)NT;
-        for (unsigned l = lit_carry + tid; l < lit_carry + tl; l += NT) {
-          unsigned lo = 0, hi = cnt - 1;
-          while (lo < hi) {
-            const unsigned mid = (lo + hi + 1) >> 1;
-            if (TL[mid] <= l)
-              lo = mid;
-            else
-              hi = mid - 1;
-          }
-          const unsigned ow = TO[lo] + (l - TL[lo]);
-          if (l < nlit_avail && ow < (unsigned)W)
-            SH32[ow] = __ldg(lit + l);
-          else
+        for (unsigned i = wid; i < cnt; i += NT / 32) {
+          const unsigned t = TK[i], l0 = TL[i], o0 = TO[i], n = t & 0xFFFFu, z = t >> 16;
+          if ((unsigned long long)l0 + n > nlit_avail || (unsigned long long)o0 + n + z > (unsigned long long)W) {
             bad = true;
+            continue;
+          }
+          for (unsigned q = lane; q < n; q += 32) SH32[o0 + q] = __ldg(lit + l0 + q);
+          for (unsigned q = lane; q < z; q += 32) SH32[o0 + n + q] = 0u;
         }
         lit_carry += tl;
         out_carry += to_;
