@@ -371,7 +371,7 @@ def run_gpu(args, rank, world, local_rank):
                 "psnr_db": 20 * math.log10((fmax - fmin) / (2 * math.sqrt(mse_k))) if mse_k > 0 else None}
 
     # batched fields and the served request stream (rank 0, one GPU)
-    batched_res = served_res = None
+    batched_res = served_res = fp64_res = None
     if rank == 0 and world == 1:
         from paper_1903_07761_gb300 import workloads
         del rec
@@ -381,6 +381,9 @@ def run_gpu(args, rank, world, local_rank):
             torch.cuda.empty_cache()
         if not args.no_serve:
             served_res = workloads.served()
+            torch.cuda.empty_cache()
+        if not args.no_fp64:
+            fp64_res = workloads.fp64()
             torch.cuda.empty_cache()
 
     # reductions over ranks (max time)
@@ -432,6 +435,7 @@ def run_gpu(args, rank, world, local_rank):
         "per_kind": per_kind,
         "batched": batched_res,
         "served": served_res,
+        "fp64": fp64_res,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -486,6 +490,7 @@ def main():
     ap.add_argument("--headline-only", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-fields comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-requests comparison")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the 768^3 FP64 case")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -293,6 +293,22 @@ cudaError_t run_minmax(const void *field, size_t n, WsHdr *ws, cudaStream_t s)
   return cudaGetLastError();
 }
 
+__global__ void k_fp64_probe(int iters, double *sink)
+{
+  double a[8];
+  const double m = 1.0 + 1e-9 * threadIdx.x, c = 1e-12;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) a[q] = 1.0 + q * 1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = fma(a[q], m, c);
+  }
+  double s = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += a[q];
+  if (s == 0.0) *sink = s;  // never true; keeps the chains live
+}
+
 // ---- batched compression
 // fields of one launch: same element type, block, kind, stage 2 and bound
 // mode, at most MAXF, in the order the caller gave them
@@ -787,6 +803,17 @@ int cz_stream_concat(int n, const void *const *h_streams, const size_t *sizes, v
   }
   std::memcpy(o + HEADER_BYTES + 8ull * nblocks, &base, 8);
   return CZ_OK;
+}
+
+// Not part of the ABI: FP64 throughput probe for the roofline of the FP64
+// path.  Every thread runs `iters` rounds of 8 independent fused multiply-
+// adds (one DFMA instruction each); the result goes to *d_sink so nothing
+// is optimised away.  DFMA instructions = grid * threads * iters * 8.
+int czi_fp64_probe(int grid, int threads, int iters, double *d_sink, void *stream)
+{
+  if (grid < 1 || threads < 32 || threads > 1024 || iters < 1 || !d_sink) return CZ_ERR_ARG;
+  k_fp64_probe<<<grid, threads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(iters, d_sink);
+  return cudaGetLastError() == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
 }
 
 // Not part of the ABI: the strict-bound divisor C of (kind, B), for tests.

@@ -249,3 +249,98 @@ def served(rates=(1000.0, 5000.0), n: int = 400, budget_gb: float = 40.0, stream
                     f"budget {budget_gb:g} GB, {streams} streams",
         "runs": results,
     }
+
+
+# ------------------------------------------------------------------ FP64
+def _w3ai_fp64_ops_per_element(B: int) -> float:
+    """FP64 instructions per element of the exact-build W3ai transform (one
+    direction) over all levels and axes, counted from the kernels' steps:
+    per pair the average (add, mul) and the detail (sub) plus the predicted
+    half-cell value, 5 operations in the interior (two weight multiplies,
+    add, multiply by 1/8, add) and 7 at the two boundary pairs of a line."""
+    total, frac = 0.0, 1.0
+    n = B
+    while n >= 8:
+        m = n // 2
+        per_line = (m - 2) * 8 + 2 * 10
+        total += 3 * frac * per_line / n
+        n //= 2
+        frac /= 8
+    return total
+
+
+def fp64(n: int = 768, kind: str = "w3ai", eps: float = 1e-3, reps: int = 10, seed: int = 2001):
+    """The FP64 case: 768^3 density field in 16^3 blocks.  GB300's FP64 rate
+    is low enough that this path is bound by the FP64 pipe, not by HBM; the
+    FP64 rate is measured here with a probe kernel (independent DFMA chains)."""
+    import ctypes as C
+    import torch
+    f = torch.from_numpy(inputs.cavitation("rho", n, np.float64, seed=seed)).cuda()
+    nbytes = f.numel() * 8
+    p = cz.params_for(tuple(f.shape), True, 16, kind, eps)
+    cap = cz.cz_compress_bound(p)
+    out = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(cz.cz_workspace_size(p), dtype=torch.uint8, device="cuda")
+    nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rec = torch.empty_like(f)
+    s = torch.cuda.current_stream().cuda_stream
+
+    def comp():
+        assert cz.cz_compress(p, f.data_ptr(), out.data_ptr(), cap, nb.data_ptr(), ws.data_ptr(), ws.numel(), s) == cz.OK
+
+    comp()
+    ln = int(nb.item())
+    hdr = C.create_string_buffer(out[:cz.HEADER_BYTES].cpu().numpy().tobytes(), cz.HEADER_BYTES)
+
+    def dec():
+        assert cz.lib().cz_decompress(out.data_ptr(), ln, hdr, rec.data_ptr(), nbytes, ws.data_ptr(), ws.numel(), s) == cz.OK
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    c_ms, d_ms = timed(comp), timed(dec)
+    # FP64 probe: DFMA instructions per second
+    L = cz.lib()
+    L.czi_fp64_probe.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+    L.czi_fp64_probe.restype = C.c_int
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    grid, thr, iters = sms * 8, 256, 4096
+
+    def probe():
+        assert L.czi_fp64_probe(grid, thr, iters, sink.data_ptr(), s) == cz.OK
+
+    p_ms = timed(probe)
+    dfma_per_s = grid * thr * iters * 8 / (p_ms * 1e-3)
+    ops = _w3ai_fp64_ops_per_element(16) + 1.0  # + the significance compare
+    comp_ops_per_s = ops * f.numel() / (c_ms * 1e-3)
+    dec_ops_per_s = _w3ai_fp64_ops_per_element(16) * f.numel() / (d_ms * 1e-3)
+    peaks = None
+    try:
+        import json, os
+        with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")) as fh:
+            peaks = float(json.load(fh)["hbm_gbs"])
+    except Exception:
+        peaks = 6800.0
+    return {
+        "workload": f"rho-field {n}^3 FP64, 16^3 blocks, {kind}, eps=1e-3*range, stage 2 on, range computed",
+        "compress_ms": c_ms, "decompress_ms": d_ms,
+        "compress_gbs": nbytes / c_ms / 1e6, "decompress_gbs": nbytes / d_ms / 1e6,
+        "cr": nbytes / ln,
+        "hbm_frac_compress": (2 * nbytes + ln) / (c_ms * 1e-3) / 1e9 / peaks,
+        "hbm_frac_decompress": (ln + nbytes) / (d_ms * 1e-3) / 1e9 / peaks,
+        "fp64_probe_dfma_per_s": dfma_per_s,
+        "fp64_ops_per_element": {"compress": ops, "decompress": _w3ai_fp64_ops_per_element(16)},
+        "fp64_pipe_frac_compress": comp_ops_per_s / dfma_per_s,
+        "fp64_pipe_frac_decompress": dec_ops_per_s / dfma_per_s,
+        "bound": "fp64 alu",
+    }
