@@ -74,24 +74,24 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
 {
   using G = G2<T, B>;
   using T2 = typename V2T<T>::type;
-  constexpr int NT = G::NT, ES = G::ES, Q = G::Q;
+  constexpr int NT = G::NT, ES = G::ES, Q = G::Q, ZH = G::ZH;
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char *PF = smem;
-  unsigned char *R2 = smem + G::TILE;
-  T *X = reinterpret_cast<T *>(R2);
-  T *AD = reinterpret_cast<T *>(R2 + G::XBF);
-  unsigned *ROWOFF = reinterpret_cast<unsigned *>(R2);
-  unsigned char *MASKU = R2 + G::ROWB;  // mask rows (for placing values)
+  unsigned char *PF = smem;                                   // tile [z][y][x], filled by TMA
+  T2 *PL = reinterpret_cast<T2 *>(smem + G::TILE);            // level-0 plane
+  T *CB = reinterpret_cast<T *>(smem + G::TILE);              // cube (start of the plane area)
+  unsigned *ROWOFF = reinterpret_cast<unsigned *>(smem + G::TILE + G::CUBE_AL);
+  unsigned char *MASKU = smem + G::TILE + G::CUBE_AL + G::ROWB;  // mask rows (for placing values)
+  T2 *HX = reinterpret_cast<T2 *>(smem + G::TILE + G::PLC);   // level-0 halo
   __shared__ __align__(8) unsigned long long s_bar;
   __shared__ unsigned s_u[40];
   __shared__ unsigned long long s_aoff;  // bytes used in this CTA's staging arena
 
   WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
   const int tid = threadIdx.x, lane = tid & 31;
-  const int ap = tid % G::HP, r = tid / G::HP;
-  const int y = r < B / 2 ? 2 * r : 2 * (r - B / 2) + 1;
+  const int ap = tid % G::HP, k = (tid / G::HP) % G::NK, h = tid / (NT / 2);
   const int seg = lane - ap;
   const int x0 = 2 * ap;
+  const int zr = h * ZH + ap;  // z of this thread's two mask rows
 
   double mn, mx, range;
   T t;
@@ -104,10 +104,10 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
                       mx, range, tf);
     s_t[tid] = tf;
   }
-  const bool cE = (x0 % Q == 0) && (y % Q == 0);  // this column pair holds coarse values (E)
-  unsigned cmask = 0;
+  const bool cE = (x0 % Q == 0) && ((2 * k) % Q == 0);  // column (x0, 2k) holds coarse values
+  unsigned ccm = 0;                                      // their bits (2 zl) in the column word
 #pragma unroll
-  for (int z = 0; z < B; z += Q) cmask |= 1u << z;
+  for (int zl = 0; zl < ZH; zl += Q) ccm |= 1u << (2 * zl);
   unsigned char *arena = a.staging + (size_t)blockIdx.x * a.arena_bytes;
 
   auto tile_of = [&](int bid) {
@@ -138,32 +138,38 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     }
     phase ^= 1u;
 
-    // ---- tile -> registers; start fetching the next tile
-    T2 v[B];
+    // ---- tile -> registers; the next tile is fetched after the
+    // transform's first barrier, when every thread has read this one
+    T2 v[2][ZH];
 #pragma unroll
-    for (int z = 0; z < B; ++z) v[z] = *reinterpret_cast<const T2 *>(PF + ((z * B + y) * B + x0) * ES);
-    __syncthreads();
-    if (tid == 0 && bid + (int)gridDim.x < a.nblocks) tile_of(bid + gridDim.x);
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int zl = 0; zl < ZH; ++zl)
+        v[r][zl] = *reinterpret_cast<const T2 *>(PF + (((h * ZH + zl) * B + 2 * k + r) * B + x0) * ES);
+    const int nb = bid + (int)gridDim.x;
 
     // ---- forward transform
-    fwd_all<T, B, KIND>(v, X, AD, ap, y, seg);
+    fwd_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg, [&] {
+      if (tid == 0 && nb < a.nblocks) tile_of(nb);
+    });
 
-    // ---- significance bits over z, mask row words by bit transpose
+    // ---- significance bits (bit 2 zl + p: column x0 + p at z = h B/2 + zl),
+    // mask rows by bit transpose over the segment
     if constexpr (NF > 1) t = s_t[field_of<NF>(maps, a.nf, bid)];
-    unsigned me = 0, mo = 0;
+    unsigned W[2];
 #pragma unroll
-    for (int z = 0; z < B; ++z) {
-      me |= (unsigned)keep(v[z].x, t) << z;
-      mo |= (unsigned)keep(v[z].y, t) << z;
+    for (int r = 0; r < 2; ++r) {
+      W[r] = 0;
+#pragma unroll
+      for (int zl = 0; zl < ZH; ++zl)
+        W[r] |= ((unsigned)keep(v[r][zl].x, t) << (2 * zl)) | ((unsigned)keep(v[r][zl].y, t) << (2 * zl + 1));
     }
-    if (cE) me &= ~cmask;
-    unsigned w0 = me, w1 = mo;
-    bit_transpose<B>(w0, w1, ap);  // row words of (z = 2ap, y) and (z = 2ap + 1, y)
-    __syncthreads();               // planes free: row offsets and mask rows go there
-    ROWOFF[(2 * ap) * B + y] = __popc(w0);
-    ROWOFF[(2 * ap + 1) * B + y] = __popc(w1);
-    put_row<B>(MASKU, 2 * ap, y, w0);
-    put_row<B>(MASKU, 2 * ap + 1, y, w1);
+    if (cE) W[0] &= ~ccm;
+    const unsigned R0 = seg_transpose<B>(W[0], ap), R1 = seg_transpose<B>(W[1], ap);  // rows (zr, 2k), (zr, 2k+1)
+    ROWOFF[zr * B + 2 * k] = __popc(R0);
+    ROWOFF[zr * B + 2 * k + 1] = __popc(R1);
+    put_row<B>(MASKU, zr, 2 * k, R0);
+    put_row<B>(MASKU, zr, 2 * k + 1, R1);
     __syncthreads();
     unsigned nnz;
     {
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
         loc[q] = ROWOFF[tid * IPT + q];
         sum += loc[q];
       }
-      unsigned ex = block_exsum<NT>(sum, s_u, nnz);
+      unsigned ex = block_exsum_nb<NT>(sum, s_u, nnz);
 #pragma unroll
       for (int q = 0; q < IPT; ++q) {
         ROWOFF[tid * IPT + q] = ex;
@@ -190,23 +196,30 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     const bool ok = so + slot <= a.arena_bytes;
     if (ok) {
       unsigned char *P = arena + so + 8;
-      put_row<B>(P + 64 * ES, 2 * ap, y, w0);
-      put_row<B>(P + 64 * ES, 2 * ap + 1, y, w1);
+      // mask rows: a coalesced copy of the shared rows (8-byte aligned)
+      for (int i = tid; i < G::MASKB / 8; i += NT)
+        reinterpret_cast<uint2 *>(P + 64 * ES)[i] = reinterpret_cast<const uint2 *>(MASKU)[i];
       if (cE) {
 #pragma unroll
-        for (int z = 0; z < B; z += Q) reinterpret_cast<T *>(P)[((z / Q) * 4 + y / Q) * 4 + x0 / Q] = v[z].x;
+        for (int zl = 0; zl < ZH; zl += Q)
+          reinterpret_cast<T *>(P)[(((h * ZH + zl) / Q) * 4 + (2 * k) / Q) * 4 + x0 / Q] = v[0][zl].x;
       }
-      // kept details of this column pair (z unrolled: v[z] stays a register)
+      // kept details of this thread's columns (z unrolled: v stays in registers)
       T *VALS = reinterpret_cast<T *>(P + 64 * ES + G::MASKB);
       const unsigned lowE = (1u << x0) - 1u, lowO = (2u << x0) - 1u;
-      if (me | mo) {
+      if (W[0] | W[1]) {
 #pragma unroll
-        for (int z = 0; z < B; ++z) {
-          if (((me | mo) >> z) & 1u) {
-            const unsigned wd = get_row<B>(MASKU, z, y);
-            const unsigned base = ROWOFF[z * B + y];
-            if ((me >> z) & 1u) VALS[base + __popc(wd & lowE)] = v[z].x;
-            if ((mo >> z) & 1u) VALS[base + __popc(wd & lowO)] = v[z].y;
+        for (int zl = 0; zl < ZH; ++zl) {
+          const int z = h * ZH + zl;
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const unsigned b2 = (W[r] >> (2 * zl)) & 3u;
+            if (b2) {
+              const unsigned wd = get_row<B>(MASKU, z, 2 * k + r);
+              const unsigned base = ROWOFF[z * B + 2 * k + r];
+              if (b2 & 1u) VALS[base + __popc(wd & lowE)] = v[r][zl].x;
+              if (b2 & 2u) VALS[base + __popc(wd & lowO)] = v[r][zl].y;
+            }
           }
         }
       }

@@ -1,10 +1,9 @@
 // cz_device.cuh -- device building blocks of the GB300 wavelet codec.
 //
-// One CTA owns one cubic B^3 block.  Thread (x, y) of the B x B thread grid
-// keeps the z-column v[0..B) of the block in registers, so
-//   * x-lines are spread over the lanes of a warp   -> warp shuffles,
-//   * y-lines are spread over warps                 -> shared-memory planes,
-//   * z-lines live in one thread's registers        -> plain register code.
+// The kernels (cz_pair.cuh) keep a block in registers spread over the
+// threads of a CTA; lines along x cross the lanes of a warp (shuffles),
+// lines along y cross warps (shared memory), lines along z stay mostly in
+// one thread's registers.
 // The 1D wavelet steps below are written once per kind and evaluated in all
 // three arrangements with the same operation order, using explicitly
 // rounded intrinsics (__fadd_rn, __fmul_rn, ...) that the compiler never
@@ -502,6 +501,24 @@ __device__ __forceinline__ U block_exsum(U v, U *tmp, U &total)
   total = tmp[32];
   __syncthreads();
   return r;
+}
+
+// Exclusive block-wide prefix with one barrier: every warp adds up the
+// totals of the warps before it itself.  tmp (>= NT/32 words) must not be
+// written again before the caller's next barrier.
+template <int NT, typename U>
+__device__ __forceinline__ U block_exsum_nb(U v, U *tmp, U &total)
+{
+  constexpr int NWP = NT / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const U inc = warp_incl_sum(v);
+  if (lane == 31) tmp[wid] = inc;
+  __syncthreads();
+  const U t = lane < NWP ? tmp[lane] : U(0);
+  const U ti = warp_incl_sum(t);
+  const U before = __shfl_sync(FULL, ti - t, wid);  // exclusive prefix of this warp's total
+  total = __shfl_sync(FULL, ti, NWP - 1);
+  return before + inc - v;
 }
 
 // Exclusive block-wide max over earlier threads (init if none).

@@ -1,21 +1,24 @@
-// cz_pair.cuh -- the codec kernels in the "column pair" layout.
+// cz_pair.cuh -- the codec kernels in the "pair quad" layout.
 //
-// A CTA owns one cubic B^3 block.  Thread (a, y) keeps the two z-columns at
-// x = 2a and x = 2a + 1 of row y in registers as B packed pairs (E, O), so
+// A CTA owns one cubic B^3 block with B^2/2 threads.  Thread (a, k, h) keeps
+// the z-columns at x = 2a, 2a + 1 of rows y = 2k, 2k + 1, over the half
+// z = h B/2 .. h B/2 + B/2 - 1, in registers as packed pairs, so
 //   * at the finest level the x-transform of a pair is local except for the
-//     neighbouring pairs' values (warp shuffles over the B/2 lanes of a row),
-//     the y-transform exchanges whole pairs through shared-memory planes,
-//     and the z-transform is register code on packed pairs (FP32x2 ops);
-//   * warps hold rows of one parity, so in the y-exchange one warp stores
-//     while another loads and computes, without divergence;
-//   * coarser levels live on the E column only and reuse the single-value
-//     line steps of cz_device.cuh.
+//     neighbouring pairs' values (warp shuffles over the B/2 lanes of a
+//     segment), the y-transform of a row pair is local except for the
+//     neighbouring row pairs' values (one shared-memory plane), and the
+//     z-transform is register code except for the two pairs next to the
+//     middle of the column (a small shared-memory halo);
+//   * the half h is the same across a warp (B >= 16), so the z-steps'
+//     compile-time stencils of the two halves never diverge within a warp;
+//   * coarser levels live on the coarse values only, gathered in a
+//     shared-memory cube and transformed one line per thread.
 // Every value is produced by the same operation sequence as the reference
 // definition of each wavelet step (explicitly rounded, never fused).
 //
-// Significance: |d| >= t is an unsigned compare of the magnitude bits; the
-// per-thread bit columns over z are turned into the stream's row words (bit
-// x of row (z, y)) by a B x B bit-matrix transpose over the lanes of a row.
+// Significance: a thread's bits over its half columns (bit 2 zl + p for column
+// 2a + p) become the stream's row words (bit x of row (z, y)) by a bit
+// transpose over the lanes of a segment.
 //
 // Compression runs as two kernels (cz_compress.cuh): a persistent stage
 // kernel that turns blocks into finished chunks in workspace staging while
@@ -187,7 +190,10 @@ template <typename T, int B>
 struct G2 {
   static constexpr int NT = B * B / 2;
   static constexpr int NW = NT / 32;
-  static constexpr int HP = B / 2;  // lanes per row
+  static constexpr int HP = B / 2;  // lanes of a segment: the x-pairs of a row
+  static constexpr int NK = B / 2;  // row pairs (y = 2k, 2k + 1)
+  static constexpr int ZH = B / 2;  // z-values of one half column
+  static constexpr int MH = B / 4;  // z-pairs of one half column
   static constexpr int L = (B == 8) ? 1 : (B == 16) ? 2 : 3;
   static constexpr int Q = B / 4;
   static constexpr int ES = (int)sizeof(T);
@@ -199,18 +205,20 @@ struct G2 {
   static constexpr int WMAX = PMAX / 4;
   static constexpr int NBWMAX = (WMAX + 31) / 32;
   static constexpr int TILE = NVOX * ES;
-  // y-exchange planes per batch (the inverse kernel keeps room for the
-  // payload beside them)
-  static constexpr int ZBF = B == 32 ? (ES == 4 ? 16 : 4) : B;
-  static constexpr int ZBI = B == 32 ? 8 : (B == 16 && ES == 8 ? 4 : B);
-  static constexpr int XBF = ZBF * B * B * ES, ADBF = ZBF * (B / 2) * B * ES;
-  static constexpr int XBI = ZBI * B * B * ES, ADBI = ZBI * (B / 2) * B * ES;
+  // level-0 exchange areas: the y plane holds one pair value per (z, k, a),
+  // the z halo two pair values per (step, half, row, k, a)
+  static constexpr int PLANE = B * NK * HP * 2 * ES;
+  static constexpr int HALO = 2 * 2 * 2 * 2 * NK * HP * 2 * ES;
+  // cube of the coarser levels: (B/2)^2 rows of B/2 + 1 elements
+  static constexpr int CUBE = L > 1 ? (B / 2) * (B / 2) * (B / 2 + 1) * ES : 0;
+  static constexpr int CUBE_AL = (CUBE + 127) / 128 * 128;
   static constexpr int ROWB = B * B * 4;
   static constexpr int PMAX_AL = (PMAX + 127) / 128 * 128;
-  // stage kernel: tile | planes, later row offsets and mask rows
-  static constexpr int R2C0 = (XBF + ADBF) > (ROWB + MASKB) ? (XBF + ADBF) : (ROWB + MASKB);
-  static constexpr int R2C = (R2C0 + 127) / 128 * 128;
-  static constexpr int SMEM_C = TILE + R2C;
+  // stage kernel: tile | plane area (the cube at its start, then the row
+  // offsets and the mask rows) | halo
+  static constexpr int PLC0 = PLANE > CUBE_AL + ROWB + MASKB ? PLANE : CUBE_AL + ROWB + MASKB;
+  static constexpr int PLC = (PLC0 + 127) / 128 * 128;
+  static constexpr int SMEM_C = TILE + PLC + HALO;
   // staging slot of one block: [nnz | 0 | raw payload]; the finished
   // stage-2 chunk replaces it in place and is at most 12 bytes longer than
   // the payload (every coded run of >= 2 zero words saves at least one
@@ -226,16 +234,19 @@ struct G2 {
   // stage-2 inverse kernels: payload + three per-token arrays
   static constexpr int SMEM_U = SHCAP + 3 * 128 * 4;
   static constexpr int SMEM_UB = PMAX_AL + 3 * 512 * 4;
-  // dense kernels
-  static constexpr int SMEM_DN0 = (XBF + ADBF) > (XBI + ADBI) ? (XBF + ADBF) : (XBI + ADBI);
-  // decompress: no tile; the whole payload always fits
-  static constexpr int R2D0 = (XBI + ADBI) > ROWB ? (XBI + ADBI) : ROWB;
+  // dense kernels: cube | plane | halo
+  static constexpr int SMEM_DN0 = CUBE_AL + PLANE + HALO;
+  // decompress: row offsets, later the cube | two payload buffers | output
+  // tile, which holds the plane and the halo while level 0 runs
+  static constexpr int R2D0 = CUBE_AL > ROWB ? CUBE_AL : ROWB;
   static constexpr int R2D = (R2D0 + 127) / 128 * 128;
   // decompress payload buffer: whole payloads of up to PBCAP bytes (with
   // 32^3 blocks most payloads, the rest read their values from global memory)
   static constexpr int PBCAP = B == 32 ? (PMAX_AL < 16384 ? PMAX_AL : 16384) : PMAX_AL;
-  // planes | two payload buffers | output tile (stored by TMA)
-  static constexpr int SMEM_D = R2D + 2 * PBCAP + TILE;
+  static constexpr int OTB0 = TILE > PLANE + HALO ? TILE : PLANE + HALO;
+  static constexpr int OTB = (OTB0 + 127) / 128 * 128;
+  static constexpr int SMEM_D = R2D + 2 * PBCAP + OTB;
+  static_assert(HP == NK && NK == ZH && NT == HP * NK * 2, "thread grid");
   static_assert(SMEM_C <= 227 * 1024 - 1024, "stage kernel shared memory");
   static_assert(SMEM_D <= 227 * 1024 - 1024, "decompress shared memory");
   static_assert(SMEM_S2B <= 227 * 1024 - 1024, "stage-2 shared memory");
@@ -317,30 +328,25 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 }
 
 // ------------------------------------------------------------ bit transpose
-// Rows x = 2a + p of a B x B bit matrix (bit z), row 2a in r0 and 2a+1 in r1
-// of lane a of a B/2-lane row segment.  Afterwards r0 / r1 hold the column
-// words of z = 2a / 2a+1 (bit x).  Recursive block swap (Hacker's Delight
-// 7-3); row distance j >= 2 is a lane distance j/2.
+// Over the B/2 lanes of a segment: lane a holds w with bit 2i + p = entry
+// (x = 2a + p, i) of a B x (B/2) bit matrix; afterwards lane a holds the word
+// of i = a, bit x.  The same steps map such words back.  Recursive block
+// swap (Hacker's Delight 7-3) in which word bit distance j pairs with lane
+// distance j/2.
 template <int B>
-__device__ __forceinline__ void bit_transpose(unsigned &r0, unsigned &r1, int a)
+__device__ __forceinline__ unsigned seg_transpose(unsigned w, int a)
 {
 #pragma unroll
   for (int j = B / 2; j >= 2; j >>= 1) {
     const unsigned m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu : 0x33333333u;
     const int ld = j >> 1;
-    const unsigned p0 = __shfl_xor_sync(FULL, r0, ld);
-    const unsigned p1 = __shfl_xor_sync(FULL, r1, ld);
-    if (!(a & ld)) {
-      r0 ^= (((r0 >> j) ^ p0) & m) << j;
-      r1 ^= (((r1 >> j) ^ p1) & m) << j;
-    } else {
-      r0 ^= ((p0 >> j) ^ r0) & m;
-      r1 ^= ((p1 >> j) ^ r1) & m;
-    }
+    const unsigned p = __shfl_xor_sync(FULL, w, ld);
+    if (!(a & ld))
+      w ^= (((w >> j) ^ p) & m) << j;
+    else
+      w ^= ((p >> j) ^ w) & m;
   }
-  const unsigned t = ((r0 >> 1) ^ r1) & 0x55555555u;
-  r0 ^= t << 1;
-  r1 ^= t;
+  return w;
 }
 
 // ============================================================ level 0 (pairs)
@@ -480,29 +486,29 @@ __device__ __forceinline__ T2 ai_predp(T2 a, T2 a1, T2 a2, T w0, T w1, T w2, boo
   return add2(a, mul2(q, mk2((T)0.125)));
 }
 
-// per-row stencil of the finest y-level (row y, m = B/2)
+// ---- finest y-level: row pairs exchange one pair value per (z, k, a)
+// through the plane P[z][k][a]
 template <typename T>
-struct YSt {
-  int src[4];  // coarse rows (even y) of the prediction
+struct YP {
+  int e[4];  // W4: row pairs whose even rows predict
   T w[4];
-  int u[3];  // detail rows (odd y) of the update
+  int d[3];  // W4li: row pairs whose details update
   T uw[3];
   int nt;
-  int k1, k2;  // average rows (pair index) of the W3ai prediction
+  int k1, k2;  // W3ai: row pairs of the two source averages
   T aw[3];
   bool bnd;
 };
 
 template <typename T, int KIND>
-__device__ __forceinline__ YSt<T> make_yst(int y, int m)
+__device__ __forceinline__ YP<T> make_yp(int k, int m)
 {
-  YSt<T> s;
-  const int k = y >> 1;
+  YP<T> s;
   if (KIND == W4 || KIND == W4LI) {
     const W4Row r = w4_row(k, m);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      s.src[q] = 2 * (r.j0 + q);
+      s.e[q] = r.j0 + q;
       s.w[q] = (T)r.w[q];
     }
   }
@@ -513,7 +519,7 @@ __device__ __forceinline__ YSt<T> make_yst(int y, int m)
     for (int t = 0; t < 3; ++t) {
       int kk = ls.k0 + t;
       kk = kk < m ? kk : m - 1;
-      s.u[t] = 2 * kk + 1;
+      s.d[t] = kk;
       s.uw[t] = li_lookup<T>(m, k, t);
     }
   }
@@ -538,236 +544,358 @@ __device__ __forceinline__ T2 li_accp(const T (&uw)[3], int nt, T2 d0, T2 d1, T2
   return acc;
 }
 
-// z-level of the pairs in registers (compile-time rows)
-template <typename T, int KIND, int B, typename T2>
-__device__ __forceinline__ void z0_fwd(T2 (&v)[B])
+// ============================================================ level 0
+// Thread (a, k, h) holds v[r][zl] = (f(2a, 2k + r, z), f(2a + 1, 2k + r, z))
+// for z = h B/2 + zl: an x-pair of both rows of a row pair over one half of
+// the z-columns.  The x-step is local to a pair except for the neighbouring
+// pairs' values (shuffles within the B/2-lane segment); the y-step is local
+// to the row pair except for the neighbouring row pairs' values (the plane);
+// the z-step is local to the half column except for two pairs next to the
+// middle (the halo).  Every step evaluates the same rounded operations in
+// the same order as the 1D definition of its wavelet.
+
+template <int B, typename T2>
+__device__ __forceinline__ T2 &plane_at(T2 *pl, int z, int k, int a)
 {
-  constexpr int m = B / 2;
-  if constexpr (KIND == W4 || KIND == W4LI) {
-    T2 d[m];
-#pragma unroll
-    for (int k = 0; k < m; ++k) {
-      const W4Row r = w4_row(k, m);
-      const T w[4] = {(T)r.w[0], (T)r.w[1], (T)r.w[2], (T)r.w[3]};
-      d[k] = sub2(v[2 * k + 1], pred4p<T2>(w, v[2 * r.j0], v[2 * r.j0 + 2], v[2 * r.j0 + 4], v[2 * r.j0 + 6]));
-    }
-    if constexpr (KIND == W4LI) {
-      T2 s[m];
-#pragma unroll
-      for (int j = 0; j < m; ++j) {
-        const LiSrc ls = li_src(j, m);
-        const T uw[3] = {li_lookup<T>(m, j, 0), li_lookup<T>(m, j, 1), li_lookup<T>(m, j, 2)};
-        const int k1 = ls.k0 + 1 < m ? ls.k0 + 1 : m - 1, k2 = ls.k0 + 2 < m ? ls.k0 + 2 : m - 1;
-        s[j] = add2(v[2 * j], li_accp<T2>(uw, ls.nt, d[ls.k0], d[k1], d[k2]));
-      }
-#pragma unroll
-      for (int j = 0; j < m; ++j) v[2 * j] = s[j];
-    }
-#pragma unroll
-    for (int k = 0; k < m; ++k) v[2 * k + 1] = d[k];
-  } else {
-    T2 a[m], d[m];
-#pragma unroll
-    for (int k = 0; k < m; ++k) a[k] = mul2(add2(v[2 * k], v[2 * k + 1]), mk2((T)0.5));
-#pragma unroll
-    for (int k = 0; k < m; ++k) {
-      const AiRow r = ai_row(k, m);
-      d[k] = sub2(v[2 * k], ai_predp<T2>(a[k], a[r.s1], a[r.s2], (T)r.w0, (T)r.w1, (T)r.w2, r.bnd));
-    }
-#pragma unroll
-    for (int k = 0; k < m; ++k) {
-      v[2 * k] = a[k];
-      v[2 * k + 1] = d[k];
-    }
-  }
+  return pl[(z * (B / 2) + k) * (B / 2) + a];
 }
 
-template <typename T, int KIND, int B, typename T2>
-__device__ __forceinline__ void z0_inv(T2 (&v)[B])
+// halo slot: step (0: predict inputs, 1: W4li update inputs), the half that
+// wrote it, slot s, row r
+template <int B, typename T2>
+__device__ __forceinline__ T2 &halo_at(T2 *hx, int step, int half, int s, int r, int k, int a)
 {
-  constexpr int m = B / 2;
-  if constexpr (KIND == W4 || KIND == W4LI) {
-    if constexpr (KIND == W4LI) {
-      T2 c[m];
-#pragma unroll
-      for (int j = 0; j < m; ++j) {
-        const LiSrc ls = li_src(j, m);
-        const T uw[3] = {li_lookup<T>(m, j, 0), li_lookup<T>(m, j, 1), li_lookup<T>(m, j, 2)};
-        const int k1 = ls.k0 + 1 < m ? ls.k0 + 1 : m - 1, k2 = ls.k0 + 2 < m ? ls.k0 + 2 : m - 1;
-        c[j] = sub2(v[2 * j], li_accp<T2>(uw, ls.nt, v[2 * ls.k0 + 1], v[2 * k1 + 1], v[2 * k2 + 1]));
-      }
-#pragma unroll
-      for (int j = 0; j < m; ++j) v[2 * j] = c[j];
-    }
-#pragma unroll
-    for (int k = 0; k < m; ++k) {
-      const W4Row r = w4_row(k, m);
-      const T w[4] = {(T)r.w[0], (T)r.w[1], (T)r.w[2], (T)r.w[3]};
-      v[2 * k + 1] =
-          add2(v[2 * k + 1], pred4p<T2>(w, v[2 * r.j0], v[2 * r.j0 + 2], v[2 * r.j0 + 4], v[2 * r.j0 + 6]));
-    }
-  } else {
-    T2 e[m], o[m];
-#pragma unroll
-    for (int k = 0; k < m; ++k) {
-      const AiRow r = ai_row(k, m);
-      e[k] = add2(ai_predp<T2>(v[2 * k], v[2 * r.s1], v[2 * r.s2], (T)r.w0, (T)r.w1, (T)r.w2, r.bnd),
-                  v[2 * k + 1]);
-      o[k] = sub2(mul2(mk2((T)2), v[2 * k]), e[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < m; ++k) {
-      v[2 * k] = e[k];
-      v[2 * k + 1] = o[k];
-    }
-  }
+  return hx[((((step * 2 + half) * 2 + s) * 2 + r) * (B / 2) + k) * (B / 2) + a];
 }
 
-// ============================================================ full transforms
-// Shared planes: X[q][y][x] (all rows) and AD[q][k][x] (one row per pair of
-// rows: W3ai averages / details).  Thread row y, pair a.
+// ---- x
 template <typename T, int B, int KIND, typename T2>
-__device__ __forceinline__ void fwd_level0(T2 (&v)[B], T *X, T *AD, int a, int y, int seg)
+__device__ __forceinline__ void x_fwd(T2 (&v)[2][B / 2], int a, int seg)
 {
-  using G = G2<T, B>;
-  constexpr int m = B / 2, ZB = G::ZBF;
-  const bool odd = y & 1;
-  // ---- x
-  {
-    const XSt<T> s = make_xst<T, KIND>(a, m, seg);
+  const XSt<T> s = make_xst<T, KIND>(a, B / 2, seg);
 #pragma unroll
-    for (int z = 0; z < B; ++z) x0_fwd<T, KIND>(s, v[z]);
-  }
-  // ---- y
-  {
-    const YSt<T> s = make_yst<T, KIND>(y, m);
-    auto row = [&](int q, int yy) -> T2 * { return reinterpret_cast<T2 *>(X + (q * B + yy) * B + 2 * a); };
-    auto arow = [&](int q, int k) -> T2 * { return reinterpret_cast<T2 *>(AD + (q * m + k) * B + 2 * a); };
+  for (int r = 0; r < 2; ++r)
 #pragma unroll
-    for (int zb = 0; zb < B; zb += ZB) {
-      if constexpr (KIND == W3AI) {
-#pragma unroll
-        for (int q = 0; q < ZB; ++q) *row(q, y) = v[zb + q];
-        __syncthreads();
-        if (!odd) {
-#pragma unroll
-          for (int q = 0; q < ZB; ++q) {
-            const T2 pr = *row(q, y + 1);
-            const T2 av = mul2(add2(v[zb + q], pr), mk2((T)0.5));
-            *arow(q, y >> 1) = av;
-            v[zb + q] = av;
-          }
-        }
-        __syncthreads();
-        if (odd) {
-#pragma unroll
-          for (int q = 0; q < ZB; ++q) {
-            const T2 f2k = *row(q, y - 1);
-            const T2 av = mul2(add2(f2k, v[zb + q]), mk2((T)0.5));
-            const T2 a1 = *arow(q, s.k1), a2 = *arow(q, s.k2);
-            v[zb + q] = sub2(f2k, ai_predp<T2>(av, a1, a2, s.aw[0], s.aw[1], s.aw[2], s.bnd));
-          }
-        }
-      } else {
-        if (!odd) {
-#pragma unroll
-          for (int q = 0; q < ZB; ++q) *row(q, y) = v[zb + q];
-        }
-        __syncthreads();
-        if (odd) {
-#pragma unroll
-          for (int q = 0; q < ZB; ++q) {
-            const T2 p = pred4p<T2>(s.w, *row(q, s.src[0]), *row(q, s.src[1]), *row(q, s.src[2]), *row(q, s.src[3]));
-            v[zb + q] = sub2(v[zb + q], p);
-            if constexpr (KIND == W4LI) *row(q, y) = v[zb + q];
-          }
-        }
-        if constexpr (KIND == W4LI) {
-          __syncthreads();
-          if (!odd) {
-#pragma unroll
-            for (int q = 0; q < ZB; ++q)
-              v[zb + q] = add2(v[zb + q], li_accp<T2>(s.uw, s.nt, *row(q, s.u[0]), *row(q, s.u[1]), *row(q, s.u[2])));
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-  // ---- z
-  z0_fwd<T, KIND, B>(v);
+    for (int zl = 0; zl < B / 2; ++zl) x0_fwd<T, KIND>(s, v[r][zl]);
 }
 
 template <typename T, int B, int KIND, typename T2>
-__device__ __forceinline__ void inv_level0(T2 (&v)[B], T *X, T *AD, int a, int y, int seg)
+__device__ __forceinline__ void x_inv(T2 (&v)[2][B / 2], int a, int seg)
 {
-  using G = G2<T, B>;
-  constexpr int m = B / 2, ZB = G::ZBI;
-  const bool odd = y & 1;
-  // ---- z
-  z0_inv<T, KIND, B>(v);
-  // ---- y
-  {
-    const YSt<T> s = make_yst<T, KIND>(y, m);
-    auto row = [&](int q, int yy) -> T2 * { return reinterpret_cast<T2 *>(X + (q * B + yy) * B + 2 * a); };
-    auto arow = [&](int q, int k) -> T2 * { return reinterpret_cast<T2 *>(AD + (q * m + k) * B + 2 * a); };
+  const XSt<T> s = make_xst<T, KIND>(a, B / 2, seg);
 #pragma unroll
-    for (int zb = 0; zb < B; zb += ZB) {
-      if constexpr (KIND == W3AI) {
-        // even rows hold averages (to AD), odd rows details (to X at row k)
+  for (int r = 0; r < 2; ++r)
 #pragma unroll
-        for (int q = 0; q < ZB; ++q) {
-          if (!odd)
-            *arow(q, y >> 1) = v[zb + q];
-          else
-            *row(q, y >> 1) = v[zb + q];
-        }
-        __syncthreads();
+    for (int zl = 0; zl < B / 2; ++zl) x0_inv<T, KIND>(s, v[r][zl]);
+}
+
+// ---- y (first_sync runs right after the first barrier)
+template <typename T, int B, int KIND, typename T2, typename F>
+__device__ __forceinline__ void y_fwd(T2 (&v)[2][B / 2], T2 *pl, int a, int k, int h, F &&first_sync)
+{
+  constexpr int ZH = B / 2, m = B / 2;
+  const YP<T> s = make_yp<T, KIND>(k, m);
+  const int z0 = h * ZH;
+  if constexpr (KIND == W3AI) {
+    // the odd row's slot takes the pair average
 #pragma unroll
-        for (int q = 0; q < ZB; ++q) {
-          const T2 a1 = *arow(q, s.k1), a2 = *arow(q, s.k2);
-          const T2 av = odd ? *arow(q, y >> 1) : v[zb + q];
-          const T2 dv = odd ? v[zb + q] : *row(q, y >> 1);
-          const T2 f0 = add2(ai_predp<T2>(av, a1, a2, s.aw[0], s.aw[1], s.aw[2], s.bnd), dv);
-          v[zb + q] = odd ? sub2(mul2(mk2((T)2), av), f0) : f0;
-        }
-      } else {
-        if constexpr (KIND == W4LI) {
-          if (odd) {
+    for (int zl = 0; zl < ZH; ++zl) {
+      v[1][zl] = mul2(add2(v[0][zl], v[1][zl]), mk2((T)0.5));
+      plane_at<B>(pl, z0 + zl, k, a) = v[1][zl];
+    }
+    __syncthreads();
+    first_sync();
 #pragma unroll
-            for (int q = 0; q < ZB; ++q) *row(q, y) = v[zb + q];
-          }
-          __syncthreads();
-          if (!odd) {
+    for (int zl = 0; zl < ZH; ++zl) {
+      const T2 av = v[1][zl];
+      const T2 a1 = plane_at<B>(pl, z0 + zl, s.k1, a), a2 = plane_at<B>(pl, z0 + zl, s.k2, a);
+      v[1][zl] = sub2(v[0][zl], ai_predp<T2>(av, a1, a2, s.aw[0], s.aw[1], s.aw[2], s.bnd));
+      v[0][zl] = av;
+    }
+  } else {
 #pragma unroll
-            for (int q = 0; q < ZB; ++q) {
-              v[zb + q] = sub2(v[zb + q], li_accp<T2>(s.uw, s.nt, *row(q, s.u[0]), *row(q, s.u[1]), *row(q, s.u[2])));
-              *row(q, y) = v[zb + q];
-            }
-          }
-        } else {
-          if (!odd) {
+    for (int zl = 0; zl < ZH; ++zl) plane_at<B>(pl, z0 + zl, k, a) = v[0][zl];
+    __syncthreads();
+    first_sync();
 #pragma unroll
-            for (int q = 0; q < ZB; ++q) *row(q, y) = v[zb + q];
-          }
-        }
-        __syncthreads();
-        if (odd) {
+    for (int zl = 0; zl < ZH; ++zl) {
+      const int z = z0 + zl;
+      v[1][zl] = sub2(v[1][zl], pred4p<T2>(s.w, plane_at<B>(pl, z, s.e[0], a), plane_at<B>(pl, z, s.e[1], a),
+                                            plane_at<B>(pl, z, s.e[2], a), plane_at<B>(pl, z, s.e[3], a)));
+    }
+    if constexpr (KIND == W4LI) {
+      __syncthreads();
 #pragma unroll
-          for (int q = 0; q < ZB; ++q)
-            v[zb + q] = add2(v[zb + q],
-                             pred4p<T2>(s.w, *row(q, s.src[0]), *row(q, s.src[1]), *row(q, s.src[2]), *row(q, s.src[3])));
-        }
+      for (int zl = 0; zl < ZH; ++zl) plane_at<B>(pl, z0 + zl, k, a) = v[1][zl];
+      __syncthreads();
+#pragma unroll
+      for (int zl = 0; zl < ZH; ++zl) {
+        const int z = z0 + zl;
+        v[0][zl] = add2(v[0][zl], li_accp<T2>(s.uw, s.nt, plane_at<B>(pl, z, s.d[0], a),
+                                               plane_at<B>(pl, z, s.d[1], a), plane_at<B>(pl, z, s.d[2], a)));
+      }
+    }
+  }
+}
+
+template <typename T, int B, int KIND, typename T2>
+__device__ __forceinline__ void y_inv(T2 (&v)[2][B / 2], T2 *pl, int a, int k, int h)
+{
+  constexpr int ZH = B / 2, m = B / 2;
+  const YP<T> s = make_yp<T, KIND>(k, m);
+  const int z0 = h * ZH;
+  if constexpr (KIND == W3AI) {
+#pragma unroll
+    for (int zl = 0; zl < ZH; ++zl) plane_at<B>(pl, z0 + zl, k, a) = v[0][zl];
+    __syncthreads();
+#pragma unroll
+    for (int zl = 0; zl < ZH; ++zl) {
+      const T2 a1 = plane_at<B>(pl, z0 + zl, s.k1, a), a2 = plane_at<B>(pl, z0 + zl, s.k2, a);
+      const T2 f0 = add2(ai_predp<T2>(v[0][zl], a1, a2, s.aw[0], s.aw[1], s.aw[2], s.bnd), v[1][zl]);
+      v[1][zl] = sub2(mul2(mk2((T)2), v[0][zl]), f0);
+      v[0][zl] = f0;
+    }
+  } else {
+    if constexpr (KIND == W4LI) {
+#pragma unroll
+      for (int zl = 0; zl < ZH; ++zl) plane_at<B>(pl, z0 + zl, k, a) = v[1][zl];
+      __syncthreads();
+#pragma unroll
+      for (int zl = 0; zl < ZH; ++zl) {
+        const int z = z0 + zl;
+        v[0][zl] = sub2(v[0][zl], li_accp<T2>(s.uw, s.nt, plane_at<B>(pl, z, s.d[0], a),
+                                               plane_at<B>(pl, z, s.d[1], a), plane_at<B>(pl, z, s.d[2], a)));
       }
       __syncthreads();
     }
-  }
-  // ---- x
-  {
-    const XSt<T> s = make_xst<T, KIND>(a, m, seg);
 #pragma unroll
-    for (int z = 0; z < B; ++z) x0_inv<T, KIND>(s, v[z]);
+    for (int zl = 0; zl < ZH; ++zl) plane_at<B>(pl, z0 + zl, k, a) = v[0][zl];
+    __syncthreads();
+#pragma unroll
+    for (int zl = 0; zl < ZH; ++zl) {
+      const int z = z0 + zl;
+      v[1][zl] = add2(v[1][zl], pred4p<T2>(s.w, plane_at<B>(pl, z, s.e[0], a), plane_at<B>(pl, z, s.e[1], a),
+                                            plane_at<B>(pl, z, s.e[2], a), plane_at<B>(pl, z, s.e[3], a)));
+    }
   }
+}
+
+// ---- z: half H of each column holds the pairs lo = H m/2 .. lo + m/2 - 1
+// (m = B/2).  Every stencil reaches at most two pairs past the middle, so a
+// half exports its two pairs next to the middle and reads the other half's.
+template <int B, int H, typename T2>
+__device__ __forceinline__ void halo_put(T2 *hx, int step, int r, int k, int a, const T2 &p0, const T2 &p1)
+{
+  halo_at<B>(hx, step, H, 0, r, k, a) = p0;
+  halo_at<B>(hx, step, H, 1, r, k, a) = p1;
+}
+
+// local z-pair of the first exported pair
+template <int B, int H>
+constexpr int halo_first()
+{
+  return H == 0 ? B / 4 - 2 : 0;
+}
+
+// the value of pair j of the column: local pairs from loc(jl), the two pairs
+// past the middle from the halo
+template <int B, int H, typename T2, typename F>
+__device__ __forceinline__ T2 zsrc(int j, const T2 (&hv)[2], F &&loc)
+{
+  constexpr int MH = B / 4, lo = H * MH;
+  if (j >= lo && j < lo + MH) return loc(j - lo);
+  const int s = H == 0 ? j - MH : j - (MH - 2);
+  return hv[s < 0 ? 0 : (s > 1 ? 1 : s)];
+}
+
+template <typename T, int B, int KIND, int H, typename T2>
+__device__ __forceinline__ void zf_a(T2 (&v)[2][B / 2], T2 *hx, int k, int a)
+{
+  constexpr int MH = B / 4, f = halo_first<B, H>();
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    if constexpr (KIND == W3AI) {
+      // the odd slot takes the pair average
+#pragma unroll
+      for (int jl = 0; jl < MH; ++jl) v[r][2 * jl + 1] = mul2(add2(v[r][2 * jl], v[r][2 * jl + 1]), mk2((T)0.5));
+      halo_put<B, H>(hx, 0, r, k, a, v[r][2 * f + 1], v[r][2 * f + 3]);
+    } else {
+      halo_put<B, H>(hx, 0, r, k, a, v[r][2 * f], v[r][2 * f + 2]);
+    }
+  }
+}
+
+template <typename T, int B, int KIND, int H, typename T2>
+__device__ __forceinline__ void zf_b(T2 (&v)[2][B / 2], T2 *hx, int k, int a)
+{
+  constexpr int MH = B / 4, m = B / 2, lo = H * MH, f = halo_first<B, H>();
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const T2 hv[2] = {halo_at<B>(hx, 0, 1 - H, 0, r, k, a), halo_at<B>(hx, 0, 1 - H, 1, r, k, a)};
+    T2 d[MH];
+    if constexpr (KIND == W3AI) {
+      auto src = [&](int j) { return zsrc<B, H>(j, hv, [&](int jl) { return v[r][2 * jl + 1]; }); };
+#pragma unroll
+      for (int jl = 0; jl < MH; ++jl) {
+        const AiRow rw = ai_row(lo + jl, m);
+        d[jl] = sub2(v[r][2 * jl], ai_predp<T2>(v[r][2 * jl + 1], src(rw.s1), src(rw.s2), (T)rw.w0, (T)rw.w1,
+                                                 (T)rw.w2, rw.bnd));
+      }
+#pragma unroll
+      for (int jl = 0; jl < MH; ++jl) {
+        v[r][2 * jl] = v[r][2 * jl + 1];
+        v[r][2 * jl + 1] = d[jl];
+      }
+    } else {
+      auto src = [&](int j) { return zsrc<B, H>(j, hv, [&](int jl) { return v[r][2 * jl]; }); };
+#pragma unroll
+      for (int jl = 0; jl < MH; ++jl) {
+        const W4Row rw = w4_row(lo + jl, m);
+        const T w[4] = {(T)rw.w[0], (T)rw.w[1], (T)rw.w[2], (T)rw.w[3]};
+        d[jl] = sub2(v[r][2 * jl + 1], pred4p<T2>(w, src(rw.j0), src(rw.j0 + 1), src(rw.j0 + 2), src(rw.j0 + 3)));
+      }
+#pragma unroll
+      for (int jl = 0; jl < MH; ++jl) v[r][2 * jl + 1] = d[jl];
+      if constexpr (KIND == W4LI) halo_put<B, H>(hx, 1, r, k, a, d[f], d[f + 1]);
+    }
+  }
+}
+
+// W4li: update of the even values from the new details
+template <typename T, int B, int H, typename T2>
+__device__ __forceinline__ void zf_c(T2 (&v)[2][B / 2], T2 *hx, int k, int a)
+{
+  constexpr int MH = B / 4, m = B / 2, lo = H * MH;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const T2 hv[2] = {halo_at<B>(hx, 1, 1 - H, 0, r, k, a), halo_at<B>(hx, 1, 1 - H, 1, r, k, a)};
+    auto src = [&](int j) { return zsrc<B, H>(j, hv, [&](int jl) { return v[r][2 * jl + 1]; }); };
+    T2 sn[MH];
+#pragma unroll
+    for (int jl = 0; jl < MH; ++jl) {
+      const int j = lo + jl;
+      const LiSrc ls = li_src(j, m);
+      const T uw[3] = {li_lookup<T>(m, j, 0), li_lookup<T>(m, j, 1), li_lookup<T>(m, j, 2)};
+      const int k1 = ls.k0 + 1 < m ? ls.k0 + 1 : m - 1, k2 = ls.k0 + 2 < m ? ls.k0 + 2 : m - 1;
+      sn[jl] = add2(v[r][2 * jl], li_accp<T2>(uw, ls.nt, src(ls.k0), src(k1), src(k2)));
+    }
+#pragma unroll
+    for (int jl = 0; jl < MH; ++jl) v[r][2 * jl] = sn[jl];
+  }
+}
+
+template <typename T, int B, int KIND, typename T2>
+__device__ __forceinline__ void z_fwd(T2 (&v)[2][B / 2], T2 *hx, int k, int a, int h)
+{
+  if (h == 0)
+    zf_a<T, B, KIND, 0>(v, hx, k, a);
+  else
+    zf_a<T, B, KIND, 1>(v, hx, k, a);
+  __syncthreads();
+  if (h == 0)
+    zf_b<T, B, KIND, 0>(v, hx, k, a);
+  else
+    zf_b<T, B, KIND, 1>(v, hx, k, a);
+  if constexpr (KIND == W4LI) {
+    __syncthreads();
+    if (h == 0)
+      zf_c<T, B, 0>(v, hx, k, a);
+    else
+      zf_c<T, B, 1>(v, hx, k, a);
+  }
+}
+
+// inverse: W4li first removes the update (halo step 1: details), then every
+// kind exports its predict inputs (step 0: coarse values) and predicts
+template <typename T, int B, int H, typename T2>
+__device__ __forceinline__ void zi_undo(T2 (&v)[2][B / 2], T2 *hx, int k, int a)
+{
+  constexpr int MH = B / 4, m = B / 2, lo = H * MH, f = halo_first<B, H>();
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const T2 hv[2] = {halo_at<B>(hx, 1, 1 - H, 0, r, k, a), halo_at<B>(hx, 1, 1 - H, 1, r, k, a)};
+    auto src = [&](int j) { return zsrc<B, H>(j, hv, [&](int jl) { return v[r][2 * jl + 1]; }); };
+    T2 c[MH];
+#pragma unroll
+    for (int jl = 0; jl < MH; ++jl) {
+      const int j = lo + jl;
+      const LiSrc ls = li_src(j, m);
+      const T uw[3] = {li_lookup<T>(m, j, 0), li_lookup<T>(m, j, 1), li_lookup<T>(m, j, 2)};
+      const int k1 = ls.k0 + 1 < m ? ls.k0 + 1 : m - 1, k2 = ls.k0 + 2 < m ? ls.k0 + 2 : m - 1;
+      c[jl] = sub2(v[r][2 * jl], li_accp<T2>(uw, ls.nt, src(ls.k0), src(k1), src(k2)));
+    }
+#pragma unroll
+    for (int jl = 0; jl < MH; ++jl) v[r][2 * jl] = c[jl];
+    halo_put<B, H>(hx, 0, r, k, a, v[r][2 * f], v[r][2 * f + 2]);
+  }
+}
+
+template <typename T, int B, int KIND, int H, typename T2>
+__device__ __forceinline__ void zi_a(T2 (&v)[2][B / 2], T2 *hx, int k, int a)
+{
+  constexpr int f = halo_first<B, H>();
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    if constexpr (KIND == W4LI)
+      halo_put<B, H>(hx, 1, r, k, a, v[r][2 * f + 1], v[r][2 * f + 3]);
+    else
+      halo_put<B, H>(hx, 0, r, k, a, v[r][2 * f], v[r][2 * f + 2]);
+  }
+}
+
+template <typename T, int B, int KIND, int H, typename T2>
+__device__ __forceinline__ void zi_b(T2 (&v)[2][B / 2], T2 *hx, int k, int a)
+{
+  constexpr int MH = B / 4, m = B / 2, lo = H * MH;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const T2 hv[2] = {halo_at<B>(hx, 0, 1 - H, 0, r, k, a), halo_at<B>(hx, 0, 1 - H, 1, r, k, a)};
+    auto src = [&](int j) { return zsrc<B, H>(j, hv, [&](int jl) { return v[r][2 * jl]; }); };
+    if constexpr (KIND == W3AI) {
+      T2 e[MH], o[MH];
+#pragma unroll
+      for (int jl = 0; jl < MH; ++jl) {
+        const AiRow rw = ai_row(lo + jl, m);
+        e[jl] = add2(ai_predp<T2>(v[r][2 * jl], src(rw.s1), src(rw.s2), (T)rw.w0, (T)rw.w1, (T)rw.w2, rw.bnd),
+                     v[r][2 * jl + 1]);
+        o[jl] = sub2(mul2(mk2((T)2), v[r][2 * jl]), e[jl]);
+      }
+#pragma unroll
+      for (int jl = 0; jl < MH; ++jl) {
+        v[r][2 * jl] = e[jl];
+        v[r][2 * jl + 1] = o[jl];
+      }
+    } else {
+#pragma unroll
+      for (int jl = 0; jl < MH; ++jl) {
+        const W4Row rw = w4_row(lo + jl, m);
+        const T w[4] = {(T)rw.w[0], (T)rw.w[1], (T)rw.w[2], (T)rw.w[3]};
+        v[r][2 * jl + 1] =
+            add2(v[r][2 * jl + 1], pred4p<T2>(w, src(rw.j0), src(rw.j0 + 1), src(rw.j0 + 2), src(rw.j0 + 3)));
+      }
+    }
+  }
+}
+
+template <typename T, int B, int KIND, typename T2>
+__device__ __forceinline__ void z_inv(T2 (&v)[2][B / 2], T2 *hx, int k, int a, int h)
+{
+  if (h == 0)
+    zi_a<T, B, KIND, 0>(v, hx, k, a);
+  else
+    zi_a<T, B, KIND, 1>(v, hx, k, a);
+  __syncthreads();
+  if constexpr (KIND == W4LI) {
+    if (h == 0)
+      zi_undo<T, B, 0>(v, hx, k, a);
+    else
+      zi_undo<T, B, 1>(v, hx, k, a);
+    __syncthreads();
+  }
+  if (h == 0)
+    zi_b<T, B, KIND, 0>(v, hx, k, a);
+  else
+    zi_b<T, B, KIND, 1>(v, hx, k, a);
 }
 
 // ============================================================ coarser levels
@@ -849,51 +977,59 @@ __device__ __forceinline__ void cube_inv(T *C)
   }
 }
 
-// coarse values of level 0 <-> the cube (threads of even rows)
+// coarse values of level 0 <-> the cube: pair jl of row 0 of thread
+// (a, k, h) holds the coarse value at cube position (a, k, h B/4 + jl)
 template <typename T, int B, typename T2>
-__device__ __forceinline__ void to_cube(const T2 (&v)[B], T *C, int a, int y)
+__device__ __forceinline__ void to_cube(const T2 (&v)[2][B / 2], T *C, int a, int k, int h)
 {
-  constexpr int N = B / 2;
-  if (!(y & 1)) {
+  constexpr int N = B / 2, MH = B / 4;
 #pragma unroll
-    for (int j = 0; j < N; ++j) C[cidx<N>(a, y >> 1, j)] = v[2 * j].x;
-  }
+  for (int jl = 0; jl < MH; ++jl) C[cidx<N>(a, k, h * MH + jl)] = v[0][2 * jl].x;
 }
 
 template <typename T, int B, typename T2>
-__device__ __forceinline__ void from_cube(T2 (&v)[B], const T *C, int a, int y)
+__device__ __forceinline__ void from_cube(T2 (&v)[2][B / 2], const T *C, int a, int k, int h)
 {
-  constexpr int N = B / 2;
-  if (!(y & 1)) {
+  constexpr int N = B / 2, MH = B / 4;
 #pragma unroll
-    for (int j = 0; j < N; ++j) v[2 * j].x = C[cidx<N>(a, y >> 1, j)];
+  for (int jl = 0; jl < MH; ++jl) v[0][2 * jl].x = C[cidx<N>(a, k, h * MH + jl)];
+}
+
+// Whole forward transform.  The plane area and the cube may overlap (the
+// cube is written after the plane's last read); the halo is separate.
+// first_sync runs right after the first barrier (every thread has read its
+// input by then).  Ends without a barrier: from_cube's reads of the cube
+// are ordered by the caller's next barrier.
+template <typename T, int B, int KIND, typename T2, typename F>
+__device__ __forceinline__ void fwd_all(T2 (&v)[2][B / 2], T2 *pl, T2 *hx, T *cube, int a, int k, int h, int seg,
+                                        F &&first_sync)
+{
+  x_fwd<T, B, KIND>(v, a, seg);
+  y_fwd<T, B, KIND>(v, pl, a, k, h, first_sync);
+  z_fwd<T, B, KIND>(v, hx, k, a, h);
+  if constexpr (G2<T, B>::L > 1) {
+    to_cube<T, B>(v, cube, a, k, h);
+    __syncthreads();
+    cube_fwd<T, B / 2, KIND, G2<T, B>::NT>(cube);
+    from_cube<T, B>(v, cube, a, k, h);
   }
 }
 
+// Whole inverse transform.  The cube must not overlap the plane or the
+// halo; the caller orders the plane's and the halo's previous uses by a
+// barrier before the call, and their last reads by one after it.
 template <typename T, int B, int KIND, typename T2>
-__device__ __forceinline__ void fwd_all(T2 (&v)[B], T *X, T *AD, int a, int y, int seg)
-{
-  fwd_level0<T, B, KIND>(v, X, AD, a, y, seg);
-  if constexpr (G2<T, B>::L > 1) {
-    to_cube<T, B>(v, X, a, y);
-    __syncthreads();
-    cube_fwd<T, B / 2, KIND, G2<T, B>::NT>(X);
-    from_cube<T, B>(v, X, a, y);
-    __syncthreads();
-  }
-}
-
-template <typename T, int B, int KIND, typename T2>
-__device__ __forceinline__ void inv_all(T2 (&v)[B], T *X, T *AD, int a, int y, int seg)
+__device__ __forceinline__ void inv_all(T2 (&v)[2][B / 2], T2 *pl, T2 *hx, T *cube, int a, int k, int h, int seg)
 {
   if constexpr (G2<T, B>::L > 1) {
-    to_cube<T, B>(v, X, a, y);
+    to_cube<T, B>(v, cube, a, k, h);
     __syncthreads();
-    cube_inv<T, B / 2, KIND, G2<T, B>::NT>(X);
-    from_cube<T, B>(v, X, a, y);
-    __syncthreads();
+    cube_inv<T, B / 2, KIND, G2<T, B>::NT>(cube);
+    from_cube<T, B>(v, cube, a, k, h);
   }
-  inv_level0<T, B, KIND>(v, X, AD, a, y, seg);
+  z_inv<T, B, KIND>(v, hx, k, a, h);
+  y_inv<T, B, KIND>(v, pl, a, k, h);
+  x_inv<T, B, KIND>(v, a, seg);
 }
 
 // ============================================================ stream helpers
@@ -1090,12 +1226,13 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
   constexpr int NT = G::NT, ES = G::ES, Q = G::Q;
   constexpr int HEAD = 64 * ES + G::MASKB;  // coarse values + mask
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char *R2 = smem;
-  T *X = reinterpret_cast<T *>(R2);
-  T *AD = reinterpret_cast<T *>(R2 + G::XBI);
-  unsigned *ROWOFF = reinterpret_cast<unsigned *>(R2);
+  constexpr int ZH = G::ZH;
+  T *CB = reinterpret_cast<T *>(smem);  // cube of the coarser levels
+  unsigned *ROWOFF = reinterpret_cast<unsigned *>(smem);  // row offsets (before the cube)
   unsigned char *BUF0 = smem + G::R2D;  // two payload buffers of G::PBCAP bytes
   unsigned char *OT = BUF0 + 2 * G::PBCAP;  // output tile [z][y][x]
+  T2 *PL = reinterpret_cast<T2 *>(OT);  // level-0 plane and halo, inside the tile area
+  T2 *HX = reinterpret_cast<T2 *>(OT + G::PLANE);
   __shared__ __align__(8) unsigned long long s_bar[2];
   __shared__ unsigned s_u[40];
   __shared__ unsigned s_nnz[2], s_bad[2];
@@ -1103,11 +1240,11 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
 
   WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
   const int tid = threadIdx.x, lane = tid & 31;
-  const int ap = tid % G::HP, r = tid / G::HP;
-  const int y = r < B / 2 ? 2 * r : 2 * (r - B / 2) + 1;
+  const int ap = tid % G::HP, k = (tid / G::HP) % G::NK, h = tid / (NT / 2);
   const int seg = lane - ap;
   const int x0 = 2 * ap;
-  const bool cE = (x0 % Q == 0) && (y % Q == 0);
+  const int zr = h * ZH + ap;  // z of this thread's two mask rows
+  const bool cE = (x0 % Q == 0) && ((2 * k) % Q == 0);  // column (x0, 2k) holds coarse values
   const bool pre = a.stage2 != 0;  // decoded payloads sit in 16-byte aligned slots
 
   // metadata of block b into buffer slot j, and (with stage 2) the start
@@ -1193,20 +1330,20 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
     const unsigned char *MASK = P + 64 * ES;
     if (tid == 0) s_badx = 0;
     __syncthreads();
-    // this thread's mask rows (z = 2ap, 2ap + 1 at row y) and, transposed
-    // over the row's lanes, its own z-columns (x0 and x0 + 1)
-    const unsigned w0 = bad0 ? 0u : get_row<B>(MASK, 2 * ap, y), w1 = bad0 ? 0u : get_row<B>(MASK, 2 * ap + 1, y);
-    unsigned me = w0, mo = w1;
-    bit_transpose<B>(me, mo, ap);
+    // this thread's mask rows (z = zr at rows 2k, 2k + 1) and, transposed
+    // over the segment's lanes, its own column bits (bit 2 zl + p: column
+    // x0 + p at z = h B/2 + zl)
+    const unsigned R0 = bad0 ? 0u : get_row<B>(MASK, zr, 2 * k), R1 = bad0 ? 0u : get_row<B>(MASK, zr, 2 * k + 1);
+    const unsigned W[2] = {seg_transpose<B>(R0, ap), seg_transpose<B>(R1, ap)};
     if (!bad0) {
       // row populations -> row offsets; coarse positions carry no mask bit
-      ROWOFF[(2 * ap) * B + y] = __popc(w0);
-      ROWOFF[(2 * ap + 1) * B + y] = __popc(w1);
-      if ((y % Q) == 0) {
+      ROWOFF[zr * B + 2 * k] = __popc(R0);
+      ROWOFF[zr * B + 2 * k + 1] = __popc(R1);
+      if ((zr % Q) == 0 && ((2 * k) % Q) == 0) {
         unsigned cm = 0;
 #pragma unroll
         for (int x = 0; x < B; x += Q) cm |= 1u << x;
-        if (((2 * ap) % Q == 0 && (w0 & cm)) || ((2 * ap + 1) % Q == 0 && (w1 & cm))) atomicOr(&s_badx, 1u);
+        if (R0 & cm) atomicOr(&s_badx, 1u);
       }
       __syncthreads();
       constexpr int IPT = (B * B + NT - 1) / NT;
@@ -1217,7 +1354,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
         sum += loc[q];
       }
       unsigned tot;
-      unsigned ex = block_exsum<NT>(sum, s_u, tot);
+      unsigned ex = block_exsum_nb<NT>(sum, s_u, tot);
 #pragma unroll
       for (int q = 0; q < IPT; ++q) {
         ROWOFF[tid * IPT + q] = ex;
@@ -1229,42 +1366,54 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
     const bool bad = bad0 || s_badx != 0;
     if (bad && tid == 0) atomicCAS(&ws->status, 0u, ST_CORRUPT);
 
-    T2 v[B];
+    T2 v[2][ZH];
 #pragma unroll
-    for (int z = 0; z < B; ++z) {
-      v[z].x = T(0);
-      v[z].y = T(0);
-    }
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int zl = 0; zl < ZH; ++zl) {
+        v[r][zl].x = T(0);
+        v[r][zl].y = T(0);
+      }
     if (!bad) {
-      // kept values of this column pair (z unrolled: v[z] stays a register;
-      // threads whose columns keep nothing skip the rows entirely)
+      // kept values of this thread's columns (z unrolled: v stays in
+      // registers; threads whose columns keep nothing skip the rows)
       const unsigned lowE = (1u << x0) - 1u, lowO = (2u << x0) - 1u;
-      if (me | mo) {
+      if (W[0] | W[1]) {
 #pragma unroll
-        for (int z = 0; z < B; ++z) {
-          if (((me | mo) >> z) & 1u) {
-            const unsigned wd = get_row<B>(MASK, z, y);
-            const unsigned base = ROWOFF[z * B + y];
-            if ((me >> z) & 1u) v[z].x = VALS[base + __popc(wd & lowE)];
-            if ((mo >> z) & 1u) v[z].y = VALS[base + __popc(wd & lowO)];
+        for (int zl = 0; zl < ZH; ++zl) {
+          const int z = h * ZH + zl;
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const unsigned b2 = (W[r] >> (2 * zl)) & 3u;
+            if (b2) {
+              const unsigned wd = get_row<B>(MASK, z, 2 * k + r);
+              const unsigned base = ROWOFF[z * B + 2 * k + r];
+              if (b2 & 1u) v[r][zl].x = VALS[base + __popc(wd & lowE)];
+              if (b2 & 2u) v[r][zl].y = VALS[base + __popc(wd & lowO)];
+            }
           }
         }
       }
       if (cE) {
         const T *COARSE = reinterpret_cast<const T *>(P);
 #pragma unroll
-        for (int z = 0; z < B; z += Q) v[z].x = COARSE[((z / Q) * 4 + y / Q) * 4 + x0 / Q];
+        for (int zl = 0; zl < ZH; zl += Q) v[0][zl].x = COARSE[(((h * ZH + zl) / Q) * 4 + (2 * k) / Q) * 4 + x0 / Q];
       }
     }
+    // the previous block's tile store has read the tile area, which the
+    // level-0 exchange uses next
+    if (tid == 0) bulk_wait_read();
     __syncthreads();  // buffer j and the row offsets are free
     if (tid == 0 && nbid < a.nblocks) s_off = fetch(nbid, j ^ 1, nt0, nt1);
-    if (!bad) inv_all<T, B, KIND>(v, X, AD, ap, y, seg);
+    if (!bad) inv_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg);
     // block -> output tile -> TMA store, which drains while the next block
-    // is decoded; the tile is reused once the previous store has read it
-    if (tid == 0) bulk_wait_read();
-    __syncthreads();
+    // is decoded
+    __syncthreads();  // the plane and the halo have been read
 #pragma unroll
-    for (int z = 0; z < B; ++z) *reinterpret_cast<T2 *>(OT + ((z * B + y) * B + x0) * ES) = v[z];
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int zl = 0; zl < ZH; ++zl)
+        *reinterpret_cast<T2 *>(OT + (((h * ZH + zl) * B + 2 * k + r) * B + x0) * ES) = v[r][zl];
     fence_async_smem();
     __syncthreads();
     if (tid == 0) tma_store_tile(&omap, OT, bx * B, by * B, bz * B);
@@ -1278,28 +1427,33 @@ __global__ void __launch_bounds__(B * B / 2) k_dense2(const DenseArgs a)
 {
   using G = G2<T, B>;
   using T2 = typename V2T<T>::type;
+  constexpr int ZH = G::ZH;
   extern __shared__ __align__(128) unsigned char smem[];
-  T *X = reinterpret_cast<T *>(smem);
-  T *AD = reinterpret_cast<T *>(smem + (FWD ? G::XBF : G::XBI));
+  T *CB = reinterpret_cast<T *>(smem);
+  T2 *PL = reinterpret_cast<T2 *>(smem + G::CUBE_AL);
+  T2 *HX = reinterpret_cast<T2 *>(smem + G::CUBE_AL + G::PLANE);
   const int tid = threadIdx.x, lane = tid & 31;
-  const int ap = tid % G::HP, r = tid / G::HP;
-  const int y = r < B / 2 ? 2 * r : 2 * (r - B / 2) + 1;
+  const int ap = tid % G::HP, k = (tid / G::HP) % G::NK, h = tid / (G::NT / 2);
   const int seg = lane - ap;
   const int bid = blockIdx.x;
   const int bx = bid % a.nbx, by = (bid / a.nbx) % a.nby, bz = bid / (a.nbx * a.nby);
   const size_t zs = (size_t)a.ny * a.nx;
-  const size_t off = (size_t)(bz * B) * zs + (size_t)(by * B + y) * a.nx + (size_t)(bx * B + 2 * ap);
-  const T2 *src = reinterpret_cast<const T2 *>(reinterpret_cast<const T *>(a.src) + off);
-  T2 *dst = reinterpret_cast<T2 *>(reinterpret_cast<T *>(a.dst) + off);
-  T2 v[B];
+  const size_t base = (size_t)(bz * B + h * ZH) * zs + (size_t)(by * B + 2 * k) * a.nx + (size_t)(bx * B + 2 * ap);
+  const T *src = reinterpret_cast<const T *>(a.src) + base;
+  T *dst = reinterpret_cast<T *>(a.dst) + base;
+  T2 v[2][ZH];
 #pragma unroll
-  for (int z = 0; z < B; ++z) v[z] = src[z * zs / 2];
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int zl = 0; zl < ZH; ++zl) v[r][zl] = *reinterpret_cast<const T2 *>(src + zl * zs + r * a.nx);
   if constexpr (FWD)
-    fwd_all<T, B, KIND>(v, X, AD, ap, y, seg);
+    fwd_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg, [] {});
   else
-    inv_all<T, B, KIND>(v, X, AD, ap, y, seg);
+    inv_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg);
 #pragma unroll
-  for (int z = 0; z < B; ++z) dst[z * zs / 2] = v[z];
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int zl = 0; zl < ZH; ++zl) *reinterpret_cast<T2 *>(dst + zl * zs + r * a.nx) = v[r][zl];
 }
 
 // ============================================================ a0: min / max
