@@ -79,12 +79,14 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
   unsigned char *PF = smem;                                   // tile [z][y][x], filled by TMA
   T2 *PL = reinterpret_cast<T2 *>(smem + G::TILE);            // level-0 plane
   T *CB = reinterpret_cast<T *>(smem + G::TILE);              // cube (start of the plane area)
-  unsigned *ROWOFF = reinterpret_cast<unsigned *>(smem + G::TILE + G::CUBE_AL);
-  unsigned char *MASKU = smem + G::TILE + G::CUBE_AL + G::ROWB;  // mask rows (for placing values)
   T2 *HX = reinterpret_cast<T2 *>(smem + G::TILE + G::PLC);   // level-0 halo
+  // after the transform the halo area holds the row offsets and the mask
+  // rows; the next block writes it only after its first barrier, so the
+  // payload phase needs no barrier at its end
+  unsigned *ROWOFF = reinterpret_cast<unsigned *>(smem + G::TILE + G::PLC);
+  unsigned char *MASKU = smem + G::TILE + G::PLC + G::ROWB;  // mask rows (for placing values)
   __shared__ __align__(8) unsigned long long s_bar;
   __shared__ unsigned s_u[40];
-  __shared__ unsigned long long s_aoff;  // bytes used in this CTA's staging arena
 
   WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
   const int tid = threadIdx.x, lane = tid & 31;
@@ -121,8 +123,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     const int bx = lb % nbx, by = (lb / nbx) % nby, bz = lb / (nbx * nby);
     tma_load_tile(&maps.tm[f], PF, &s_bar, bx * B, by * B, bz * B, G::TILE);
   };
+  unsigned long long aoff = 0;  // bytes used in this CTA's staging arena (the same in every thread)
   if (tid == 0) {
-    s_aoff = 0;
     mbar_init(&s_bar);
     if ((int)blockIdx.x < a.nblocks) tile_of(blockIdx.x);
   }
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     fwd_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg, [&] {
       if (tid == 0 && nb < a.nblocks) tile_of(nb);
     });
+    if constexpr (G::L == 1) __syncthreads();  // no cube: the halo's last reads were just now
 
     // ---- significance bits (bit 2 zl + p: column x0 + p at z = h B/2 + zl),
     // mask rows by bit transpose over the segment
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
 
     // ---- slot [nnz | 0 | raw payload] -> this CTA's staging arena
     const int pbytes = 64 * ES + G::MASKB + (int)nnz * ES;
-    const unsigned long long so = s_aoff;
+    const unsigned long long so = aoff;
     const unsigned long long slot = (unsigned long long)((pbytes + 12 + 15) & ~15);
     const bool ok = so + slot <= a.arena_bytes;
     if (ok) {
@@ -236,8 +239,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
       a.table[2 * bid] = (unsigned long long)(arena - a.staging) + so;
       a.table[2 * bid + 1] = ok ? 8ull + (unsigned long long)pbytes : TB_LOST;
     }
-    __syncthreads();
-    if (tid == 0 && ok) s_aoff = so + slot;
+    if (ok) aoff = so + slot;
   }
 }
 

@@ -204,6 +204,8 @@ struct AiRow {
 
 __host__ __device__ constexpr AiRow ai_row(int k, int m)
 {
+  // (interior rows have weights (1, -1): kernels with compile-time rows
+  // evaluate them as one subtraction, which rounds the same way)
   if (k == 0) return AiRow{1, 2, 3, -4, 1, true};
   if (k == m - 1) return AiRow{m - 2, m - 3, -3, 4, -1, true};
   return AiRow{k - 1, k + 1, 1, -1, 0, false};
@@ -406,7 +408,7 @@ __device__ __forceinline__ void fwd_reg(T (&v)[B])
         q = addx(mulx((T)r.w0, a[k]), mulx((T)r.w1, a[r.s1]));
         q = addx(q, mulx((T)r.w2, a[r.s2]));
       } else {
-        q = addx(mulx((T)r.w0, a[r.s1]), mulx((T)r.w1, a[r.s2]));
+        q = subx(a[r.s1], a[r.s2]);  // interior weights (1, -1): both products exact
       }
       d[k] = subx(v[2 * k * S], addx(a[k], mulx(q, (T)0.125)));
     }
@@ -455,7 +457,7 @@ __device__ __forceinline__ void inv_reg(T (&v)[B])
         q = addx(mulx((T)r.w0, ak), mulx((T)r.w1, v[2 * r.s1 * S]));
         q = addx(q, mulx((T)r.w2, v[2 * r.s2 * S]));
       } else {
-        q = addx(mulx((T)r.w0, v[2 * r.s1 * S]), mulx((T)r.w1, v[2 * r.s2 * S]));
+        q = subx(v[2 * r.s1 * S], v[2 * r.s2 * S]);  // interior weights (1, -1): both products exact
       }
       e[k] = addx(addx(ak, mulx(q, (T)0.125)), v[(2 * k + 1) * S]);
       o[k] = subx(mulx((T)2, ak), e[k]);

@@ -214,9 +214,9 @@ struct G2 {
   static constexpr int CUBE_AL = (CUBE + 127) / 128 * 128;
   static constexpr int ROWB = B * B * 4;
   static constexpr int PMAX_AL = (PMAX + 127) / 128 * 128;
-  // stage kernel: tile | plane area (the cube at its start, then the row
-  // offsets and the mask rows) | halo
-  static constexpr int PLC0 = PLANE > CUBE_AL + ROWB + MASKB ? PLANE : CUBE_AL + ROWB + MASKB;
+  // stage kernel: tile | plane area (the cube at its start) | halo area
+  // (after the transform: the row offsets and the mask rows)
+  static constexpr int PLC0 = PLANE > CUBE_AL ? PLANE : CUBE_AL;
   static constexpr int PLC = (PLC0 + 127) / 128 * 128;
   static constexpr int SMEM_C = TILE + PLC + HALO;
   // staging slot of one block: [nnz | 0 | raw payload]; the finished
@@ -247,6 +247,7 @@ struct G2 {
   static constexpr int OTB = (OTB0 + 127) / 128 * 128;
   static constexpr int SMEM_D = R2D + 2 * PBCAP + OTB;
   static_assert(HP == NK && NK == ZH && NT == HP * NK * 2, "thread grid");
+  static_assert(HALO >= ROWB + MASKB, "row offsets and mask rows fit the halo area");
   static_assert(SMEM_C <= 227 * 1024 - 1024, "stage kernel shared memory");
   static_assert(SMEM_D <= 227 * 1024 - 1024, "decompress shared memory");
   static_assert(SMEM_S2B <= 227 * 1024 - 1024, "stage-2 shared memory");
@@ -484,6 +485,15 @@ __device__ __forceinline__ T2 ai_predp(T2 a, T2 a1, T2 a2, T w0, T w1, T w2, boo
   T2 q = add2(mul2(mk2(w0), x0), mul2(mk2(w1), x1));
   if (bnd) q = add2(q, mul2(mk2(w2), a2));
   return add2(a, mul2(q, mk2((T)0.125)));
+}
+
+// the same with a compile-time row: interior rows (weights 1, -1) as one
+// subtraction, which rounds exactly like the two exact products and the sum
+template <typename T2, typename T>
+__device__ __forceinline__ T2 ai_predc(const AiRow &r, T2 a, T2 a1, T2 a2)
+{
+  if (!r.bnd) return add2(a, mul2(sub2(a1, a2), mk2((T)0.125)));
+  return ai_predp<T2>(a, a1, a2, (T)r.w0, (T)r.w1, (T)r.w2, true);
 }
 
 // ---- finest y-level: row pairs exchange one pair value per (z, k, a)
@@ -738,8 +748,7 @@ __device__ __forceinline__ void zf_b(T2 (&v)[2][B / 2], T2 *hx, int k, int a)
 #pragma unroll
       for (int jl = 0; jl < MH; ++jl) {
         const AiRow rw = ai_row(lo + jl, m);
-        d[jl] = sub2(v[r][2 * jl], ai_predp<T2>(v[r][2 * jl + 1], src(rw.s1), src(rw.s2), (T)rw.w0, (T)rw.w1,
-                                                 (T)rw.w2, rw.bnd));
+        d[jl] = sub2(v[r][2 * jl], ai_predc<T2, T>(rw, v[r][2 * jl + 1], src(rw.s1), src(rw.s2)));
       }
 #pragma unroll
       for (int jl = 0; jl < MH; ++jl) {
@@ -856,8 +865,7 @@ __device__ __forceinline__ void zi_b(T2 (&v)[2][B / 2], T2 *hx, int k, int a)
 #pragma unroll
       for (int jl = 0; jl < MH; ++jl) {
         const AiRow rw = ai_row(lo + jl, m);
-        e[jl] = add2(ai_predp<T2>(v[r][2 * jl], src(rw.s1), src(rw.s2), (T)rw.w0, (T)rw.w1, (T)rw.w2, rw.bnd),
-                     v[r][2 * jl + 1]);
+        e[jl] = add2(ai_predc<T2, T>(rw, v[r][2 * jl], src(rw.s1), src(rw.s2)), v[r][2 * jl + 1]);
         o[jl] = sub2(mul2(mk2((T)2), v[r][2 * jl]), e[jl]);
       }
 #pragma unroll
@@ -930,12 +938,17 @@ __device__ __forceinline__ void cube_line(int li, int &base, int &step)
 }
 
 // one axis of one level: a thread per line, the line in registers
-// (compile-time stencils), written back in place
-template <typename T, int N, int KIND, int NT, int S, int AXIS, bool FWD>
+// (compile-time stencils), written back in place.  Along x and along y,
+// thread li gets a line of z-slice li / n, so the two passes of a level
+// touch each slice from one warp (n divides 32 or is a multiple of 16):
+// between them a warp barrier orders the accesses (WARP_ONLY).
+template <typename T, int N, int KIND, int NT, int S, int AXIS, bool FWD, bool WARP_ONLY>
 __device__ __forceinline__ void cube_pass(T *C)
 {
   constexpr int n = N / S, LINES = n * n;
   static_assert(LINES <= NT, "one line per thread");
+  static_assert(!WARP_ONLY || AXIS < 2, "only x and y lines share slices by warp");
+  static_assert(32 % n == 0 || n % 16 == 0, "a z-slice's lines lie in one warp");
   const int tid = threadIdx.x;
   if (tid < LINES) {
     int base, step;
@@ -951,7 +964,10 @@ __device__ __forceinline__ void cube_pass(T *C)
     for (int i = 0; i < n; ++i)
       if (KIND != W4 || (i & 1)) C[base + i * step] = e[i];  // W4 changes only the odd points
   }
-  __syncthreads();
+  if constexpr (WARP_ONLY)
+    __syncwarp();
+  else
+    __syncthreads();
 }
 
 // all levels of the N^3 cube down to 4^3 (x, y, z per level)
@@ -959,9 +975,9 @@ template <typename T, int N, int KIND, int NT, int S = 1>
 __device__ __forceinline__ void cube_fwd(T *C)
 {
   if constexpr (N / S >= 8) {
-    cube_pass<T, N, KIND, NT, S, 0, true>(C);
-    cube_pass<T, N, KIND, NT, S, 1, true>(C);
-    cube_pass<T, N, KIND, NT, S, 2, true>(C);
+    cube_pass<T, N, KIND, NT, S, 0, true, true>(C);
+    cube_pass<T, N, KIND, NT, S, 1, true, false>(C);
+    cube_pass<T, N, KIND, NT, S, 2, true, false>(C);
     cube_fwd<T, N, KIND, NT, 2 * S>(C);
   }
 }
@@ -971,9 +987,9 @@ __device__ __forceinline__ void cube_inv(T *C)
 {
   if constexpr (N / S >= 8) {
     cube_inv<T, N, KIND, NT, 2 * S>(C);
-    cube_pass<T, N, KIND, NT, S, 2, false>(C);
-    cube_pass<T, N, KIND, NT, S, 1, false>(C);
-    cube_pass<T, N, KIND, NT, S, 0, false>(C);
+    cube_pass<T, N, KIND, NT, S, 2, false, false>(C);
+    cube_pass<T, N, KIND, NT, S, 1, false, true>(C);
+    cube_pass<T, N, KIND, NT, S, 0, false, false>(C);
   }
 }
 
@@ -1284,6 +1300,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
   if (tid == 0) {
     mbar_init(&s_bar[0]);
     mbar_init(&s_bar[1]);
+    s_badx = 0;  // reset again after each block's last read
   }
   __syncthreads();
   __shared__ unsigned long long s_off;
@@ -1328,8 +1345,6 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
                         : (pre ? reinterpret_cast<const T *>(a.staging + (size_t)bid * a.slot + HEAD)
                                : reinterpret_cast<const T *>(a.in + a.data0 + s_off + 8 + HEAD));
     const unsigned char *MASK = P + 64 * ES;
-    if (tid == 0) s_badx = 0;
-    __syncthreads();
     // this thread's mask rows (z = zr at rows 2k, 2k + 1) and, transposed
     // over the segment's lanes, its own column bits (bit 2 zl + p: column
     // x0 + p at z = h B/2 + zl)
@@ -1403,8 +1418,11 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
     // the previous block's tile store has read the tile area, which the
     // level-0 exchange uses next
     if (tid == 0) bulk_wait_read();
-    __syncthreads();  // buffer j and the row offsets are free
-    if (tid == 0 && nbid < a.nblocks) s_off = fetch(nbid, j ^ 1, nt0, nt1);
+    __syncthreads();  // buffer j and the row offsets are free; s_badx has been read
+    if (tid == 0) {
+      s_badx = 0;
+      if (nbid < a.nblocks) s_off = fetch(nbid, j ^ 1, nt0, nt1);
+    }
     if (!bad) inv_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg);
     // block -> output tile -> TMA store, which drains while the next block
     // is decoded
