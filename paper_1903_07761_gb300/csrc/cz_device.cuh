@@ -275,6 +275,27 @@ __device__ __forceinline__ T pred4(const T (&w)[4], T c0, T c1, T c2, T c3)
   return mulx(p, (T)0.0625);
 }
 
+// Interior W4 rows have weights (-1, 9, 9, -1).  The products by -1 are
+// exact negations, and adding a negation is subtracting, so
+// ((-c0 + 9 c1) + 9 c2) + (-c3) rounds exactly like ((9 c1 - c0) + 9 c2) - c3.
+template <typename T>
+__device__ __forceinline__ T pred4i(T c0, T c1, T c2, T c3)
+{
+  T p = subx(mulx((T)9, c1), c0);
+  p = addx(p, mulx((T)9, c2));
+  p = subx(p, c3);
+  return mulx(p, (T)0.0625);
+}
+
+// a compile-time row: interior rows through pred4i
+template <typename T>
+__device__ __forceinline__ T pred4r(const W4Row &r, T c0, T c1, T c2, T c3)
+{
+  if (r.w[0] == -1 && r.w[1] == 9 && r.w[2] == 9 && r.w[3] == -1) return pred4i(c0, c1, c2, c3);
+  const T w[4] = {(T)r.w[0], (T)r.w[1], (T)r.w[2], (T)r.w[3]};
+  return pred4(w, c0, c1, c2, c3);
+}
+
 template <typename T>
 __device__ __forceinline__ T li_acc(const Stencil<T> &s, T d0, T d1, T d2)
 {
@@ -376,10 +397,8 @@ __device__ __forceinline__ void fwd_reg(T (&v)[B])
 #pragma unroll
     for (int k = 0; k < m; ++k) {
       const W4Row r = w4_row(k, m);
-      const T w[4] = {(T)r.w[0], (T)r.w[1], (T)r.w[2], (T)r.w[3]};
       d[k] = subx(v[(2 * k + 1) * S],
-                  pred4(w, v[2 * r.j0 * S], v[2 * (r.j0 + 1) * S], v[2 * (r.j0 + 2) * S],
-                        v[2 * (r.j0 + 3) * S]));
+                  pred4r(r, v[2 * r.j0 * S], v[2 * (r.j0 + 1) * S], v[2 * (r.j0 + 2) * S], v[2 * (r.j0 + 3) * S]));
     }
     if constexpr (KIND == W4LI) {
       T s_[m];
@@ -441,10 +460,8 @@ __device__ __forceinline__ void inv_reg(T (&v)[B])
 #pragma unroll
     for (int k = 0; k < m; ++k) {
       const W4Row r = w4_row(k, m);
-      const T w[4] = {(T)r.w[0], (T)r.w[1], (T)r.w[2], (T)r.w[3]};
-      v[(2 * k + 1) * S] =
-          addx(v[(2 * k + 1) * S], pred4(w, v[2 * r.j0 * S], v[2 * (r.j0 + 1) * S],
-                                         v[2 * (r.j0 + 2) * S], v[2 * (r.j0 + 3) * S]));
+      v[(2 * k + 1) * S] = addx(v[(2 * k + 1) * S], pred4r(r, v[2 * r.j0 * S], v[2 * (r.j0 + 1) * S],
+                                                          v[2 * (r.j0 + 2) * S], v[2 * (r.j0 + 3) * S]));
     }
   } else {
     T e[m], o[m];

@@ -487,12 +487,38 @@ __device__ __forceinline__ T2 ai_predp(T2 a, T2 a1, T2 a2, T w0, T w1, T w2, boo
   return add2(a, mul2(q, mk2((T)0.125)));
 }
 
+// packed interior W4 row (weights -1, 9, 9, -1; see pred4i)
+template <typename T2, typename T>
+__device__ __forceinline__ T2 pred4ip(T2 c0, T2 c1, T2 c2, T2 c3)
+{
+  T2 p = sub2(mul2(mk2((T)9), c1), c0);
+  p = add2(p, mul2(mk2((T)9), c2));
+  p = sub2(p, c3);
+  return mul2(p, mk2((T)0.0625));
+}
+
+// packed compile-time W4 row
+template <typename T2, typename T>
+__device__ __forceinline__ T2 pred4rp(const W4Row &r, T2 c0, T2 c1, T2 c2, T2 c3)
+{
+  if (r.w[0] == -1 && r.w[1] == 9 && r.w[2] == 9 && r.w[3] == -1) return pred4ip<T2, T>(c0, c1, c2, c3);
+  const T w[4] = {(T)r.w[0], (T)r.w[1], (T)r.w[2], (T)r.w[3]};
+  return pred4p<T2>(w, c0, c1, c2, c3);
+}
+
+// packed interior W3ai row (weights 1, -1)
+template <typename T2, typename T>
+__device__ __forceinline__ T2 ai_predip(T2 a, T2 a1, T2 a2)
+{
+  return add2(a, mul2(sub2(a1, a2), mk2((T)0.125)));
+}
+
 // the same with a compile-time row: interior rows (weights 1, -1) as one
 // subtraction, which rounds exactly like the two exact products and the sum
 template <typename T2, typename T>
 __device__ __forceinline__ T2 ai_predc(const AiRow &r, T2 a, T2 a1, T2 a2)
 {
-  if (!r.bnd) return add2(a, mul2(sub2(a1, a2), mk2((T)0.125)));
+  if (!r.bnd) return ai_predip<T2, T>(a, a1, a2);
   return ai_predp<T2>(a, a1, a2, (T)r.w0, (T)r.w1, (T)r.w2, true);
 }
 
@@ -599,12 +625,21 @@ __device__ __forceinline__ void x_inv(T2 (&v)[2][B / 2], int a, int seg)
     for (int zl = 0; zl < B / 2; ++zl) x0_inv<T, KIND>(s, v[r][zl]);
 }
 
-// ---- y (first_sync runs right after the first barrier)
+// ---- y (first_sync runs right after the first barrier).  A warp whose
+// row pairs are all interior takes the interior forms of its rows (the same
+// roundings); barriers stay outside the warp-uniform branches.
+template <int KIND>
+__device__ __forceinline__ bool y_interior(int k, int m)
+{
+  return KIND == W3AI ? (k >= 1 && k <= m - 2) : (k >= 1 && k <= m - 3);
+}
+
 template <typename T, int B, int KIND, typename T2, typename F>
 __device__ __forceinline__ void y_fwd(T2 (&v)[2][B / 2], T2 *pl, int a, int k, int h, F &&first_sync)
 {
   constexpr int ZH = B / 2, m = B / 2;
   const YP<T> s = make_yp<T, KIND>(k, m);
+  const bool wint = __all_sync(FULL, y_interior<KIND>(k, m));
   const int z0 = h * ZH;
   if constexpr (KIND == W3AI) {
     // the odd row's slot takes the pair average
@@ -615,34 +650,63 @@ __device__ __forceinline__ void y_fwd(T2 (&v)[2][B / 2], T2 *pl, int a, int k, i
     }
     __syncthreads();
     first_sync();
+    if (wint) {
 #pragma unroll
-    for (int zl = 0; zl < ZH; ++zl) {
-      const T2 av = v[1][zl];
-      const T2 a1 = plane_at<B>(pl, z0 + zl, s.k1, a), a2 = plane_at<B>(pl, z0 + zl, s.k2, a);
-      v[1][zl] = sub2(v[0][zl], ai_predp<T2>(av, a1, a2, s.aw[0], s.aw[1], s.aw[2], s.bnd));
-      v[0][zl] = av;
+      for (int zl = 0; zl < ZH; ++zl) {
+        const T2 av = v[1][zl];
+        const T2 a1 = plane_at<B>(pl, z0 + zl, k - 1, a), a2 = plane_at<B>(pl, z0 + zl, k + 1, a);
+        v[1][zl] = sub2(v[0][zl], ai_predip<T2, T>(av, a1, a2));
+        v[0][zl] = av;
+      }
+    } else {
+#pragma unroll
+      for (int zl = 0; zl < ZH; ++zl) {
+        const T2 av = v[1][zl];
+        const T2 a1 = plane_at<B>(pl, z0 + zl, s.k1, a), a2 = plane_at<B>(pl, z0 + zl, s.k2, a);
+        v[1][zl] = sub2(v[0][zl], ai_predp<T2>(av, a1, a2, s.aw[0], s.aw[1], s.aw[2], s.bnd));
+        v[0][zl] = av;
+      }
     }
   } else {
 #pragma unroll
     for (int zl = 0; zl < ZH; ++zl) plane_at<B>(pl, z0 + zl, k, a) = v[0][zl];
     __syncthreads();
     first_sync();
+    if (wint) {
 #pragma unroll
-    for (int zl = 0; zl < ZH; ++zl) {
-      const int z = z0 + zl;
-      v[1][zl] = sub2(v[1][zl], pred4p<T2>(s.w, plane_at<B>(pl, z, s.e[0], a), plane_at<B>(pl, z, s.e[1], a),
-                                            plane_at<B>(pl, z, s.e[2], a), plane_at<B>(pl, z, s.e[3], a)));
+      for (int zl = 0; zl < ZH; ++zl) {
+        const int z = z0 + zl;
+        v[1][zl] = sub2(v[1][zl], pred4ip<T2, T>(plane_at<B>(pl, z, k - 1, a), plane_at<B>(pl, z, k, a),
+                                                  plane_at<B>(pl, z, k + 1, a), plane_at<B>(pl, z, k + 2, a)));
+      }
+    } else {
+#pragma unroll
+      for (int zl = 0; zl < ZH; ++zl) {
+        const int z = z0 + zl;
+        v[1][zl] = sub2(v[1][zl], pred4p<T2>(s.w, plane_at<B>(pl, z, s.e[0], a), plane_at<B>(pl, z, s.e[1], a),
+                                              plane_at<B>(pl, z, s.e[2], a), plane_at<B>(pl, z, s.e[3], a)));
+      }
     }
     if constexpr (KIND == W4LI) {
       __syncthreads();
 #pragma unroll
       for (int zl = 0; zl < ZH; ++zl) plane_at<B>(pl, z0 + zl, k, a) = v[1][zl];
       __syncthreads();
+      if (wint) {  // two update terms: details k - 1 and k
 #pragma unroll
-      for (int zl = 0; zl < ZH; ++zl) {
-        const int z = z0 + zl;
-        v[0][zl] = add2(v[0][zl], li_accp<T2>(s.uw, s.nt, plane_at<B>(pl, z, s.d[0], a),
-                                               plane_at<B>(pl, z, s.d[1], a), plane_at<B>(pl, z, s.d[2], a)));
+        for (int zl = 0; zl < ZH; ++zl) {
+          const int z = z0 + zl;
+          const T2 acc = add2(mul2(mk2(s.uw[0]), plane_at<B>(pl, z, k - 1, a)),
+                              mul2(mk2(s.uw[1]), plane_at<B>(pl, z, k, a)));
+          v[0][zl] = add2(v[0][zl], acc);
+        }
+      } else {
+#pragma unroll
+        for (int zl = 0; zl < ZH; ++zl) {
+          const int z = z0 + zl;
+          v[0][zl] = add2(v[0][zl], li_accp<T2>(s.uw, s.nt, plane_at<B>(pl, z, s.d[0], a),
+                                                 plane_at<B>(pl, z, s.d[1], a), plane_at<B>(pl, z, s.d[2], a)));
+        }
       }
     }
   }
@@ -653,39 +717,69 @@ __device__ __forceinline__ void y_inv(T2 (&v)[2][B / 2], T2 *pl, int a, int k, i
 {
   constexpr int ZH = B / 2, m = B / 2;
   const YP<T> s = make_yp<T, KIND>(k, m);
+  const bool wint = __all_sync(FULL, y_interior<KIND>(k, m));
   const int z0 = h * ZH;
   if constexpr (KIND == W3AI) {
 #pragma unroll
     for (int zl = 0; zl < ZH; ++zl) plane_at<B>(pl, z0 + zl, k, a) = v[0][zl];
     __syncthreads();
+    if (wint) {
 #pragma unroll
-    for (int zl = 0; zl < ZH; ++zl) {
-      const T2 a1 = plane_at<B>(pl, z0 + zl, s.k1, a), a2 = plane_at<B>(pl, z0 + zl, s.k2, a);
-      const T2 f0 = add2(ai_predp<T2>(v[0][zl], a1, a2, s.aw[0], s.aw[1], s.aw[2], s.bnd), v[1][zl]);
-      v[1][zl] = sub2(mul2(mk2((T)2), v[0][zl]), f0);
-      v[0][zl] = f0;
+      for (int zl = 0; zl < ZH; ++zl) {
+        const T2 a1 = plane_at<B>(pl, z0 + zl, k - 1, a), a2 = plane_at<B>(pl, z0 + zl, k + 1, a);
+        const T2 f0 = add2(ai_predip<T2, T>(v[0][zl], a1, a2), v[1][zl]);
+        v[1][zl] = sub2(mul2(mk2((T)2), v[0][zl]), f0);
+        v[0][zl] = f0;
+      }
+    } else {
+#pragma unroll
+      for (int zl = 0; zl < ZH; ++zl) {
+        const T2 a1 = plane_at<B>(pl, z0 + zl, s.k1, a), a2 = plane_at<B>(pl, z0 + zl, s.k2, a);
+        const T2 f0 = add2(ai_predp<T2>(v[0][zl], a1, a2, s.aw[0], s.aw[1], s.aw[2], s.bnd), v[1][zl]);
+        v[1][zl] = sub2(mul2(mk2((T)2), v[0][zl]), f0);
+        v[0][zl] = f0;
+      }
     }
   } else {
     if constexpr (KIND == W4LI) {
 #pragma unroll
       for (int zl = 0; zl < ZH; ++zl) plane_at<B>(pl, z0 + zl, k, a) = v[1][zl];
       __syncthreads();
+      if (wint) {
 #pragma unroll
-      for (int zl = 0; zl < ZH; ++zl) {
-        const int z = z0 + zl;
-        v[0][zl] = sub2(v[0][zl], li_accp<T2>(s.uw, s.nt, plane_at<B>(pl, z, s.d[0], a),
-                                               plane_at<B>(pl, z, s.d[1], a), plane_at<B>(pl, z, s.d[2], a)));
+        for (int zl = 0; zl < ZH; ++zl) {
+          const int z = z0 + zl;
+          const T2 acc = add2(mul2(mk2(s.uw[0]), plane_at<B>(pl, z, k - 1, a)),
+                              mul2(mk2(s.uw[1]), plane_at<B>(pl, z, k, a)));
+          v[0][zl] = sub2(v[0][zl], acc);
+        }
+      } else {
+#pragma unroll
+        for (int zl = 0; zl < ZH; ++zl) {
+          const int z = z0 + zl;
+          v[0][zl] = sub2(v[0][zl], li_accp<T2>(s.uw, s.nt, plane_at<B>(pl, z, s.d[0], a),
+                                                 plane_at<B>(pl, z, s.d[1], a), plane_at<B>(pl, z, s.d[2], a)));
+        }
       }
       __syncthreads();
     }
 #pragma unroll
     for (int zl = 0; zl < ZH; ++zl) plane_at<B>(pl, z0 + zl, k, a) = v[0][zl];
     __syncthreads();
+    if (wint) {
 #pragma unroll
-    for (int zl = 0; zl < ZH; ++zl) {
-      const int z = z0 + zl;
-      v[1][zl] = add2(v[1][zl], pred4p<T2>(s.w, plane_at<B>(pl, z, s.e[0], a), plane_at<B>(pl, z, s.e[1], a),
-                                            plane_at<B>(pl, z, s.e[2], a), plane_at<B>(pl, z, s.e[3], a)));
+      for (int zl = 0; zl < ZH; ++zl) {
+        const int z = z0 + zl;
+        v[1][zl] = add2(v[1][zl], pred4ip<T2, T>(plane_at<B>(pl, z, k - 1, a), plane_at<B>(pl, z, k, a),
+                                                  plane_at<B>(pl, z, k + 1, a), plane_at<B>(pl, z, k + 2, a)));
+      }
+    } else {
+#pragma unroll
+      for (int zl = 0; zl < ZH; ++zl) {
+        const int z = z0 + zl;
+        v[1][zl] = add2(v[1][zl], pred4p<T2>(s.w, plane_at<B>(pl, z, s.e[0], a), plane_at<B>(pl, z, s.e[1], a),
+                                              plane_at<B>(pl, z, s.e[2], a), plane_at<B>(pl, z, s.e[3], a)));
+      }
     }
   }
 }
@@ -760,8 +854,7 @@ __device__ __forceinline__ void zf_b(T2 (&v)[2][B / 2], T2 *hx, int k, int a)
 #pragma unroll
       for (int jl = 0; jl < MH; ++jl) {
         const W4Row rw = w4_row(lo + jl, m);
-        const T w[4] = {(T)rw.w[0], (T)rw.w[1], (T)rw.w[2], (T)rw.w[3]};
-        d[jl] = sub2(v[r][2 * jl + 1], pred4p<T2>(w, src(rw.j0), src(rw.j0 + 1), src(rw.j0 + 2), src(rw.j0 + 3)));
+        d[jl] = sub2(v[r][2 * jl + 1], pred4rp<T2, T>(rw, src(rw.j0), src(rw.j0 + 1), src(rw.j0 + 2), src(rw.j0 + 3)));
       }
 #pragma unroll
       for (int jl = 0; jl < MH; ++jl) v[r][2 * jl + 1] = d[jl];
@@ -877,9 +970,8 @@ __device__ __forceinline__ void zi_b(T2 (&v)[2][B / 2], T2 *hx, int k, int a)
 #pragma unroll
       for (int jl = 0; jl < MH; ++jl) {
         const W4Row rw = w4_row(lo + jl, m);
-        const T w[4] = {(T)rw.w[0], (T)rw.w[1], (T)rw.w[2], (T)rw.w[3]};
         v[r][2 * jl + 1] =
-            add2(v[r][2 * jl + 1], pred4p<T2>(w, src(rw.j0), src(rw.j0 + 1), src(rw.j0 + 2), src(rw.j0 + 3)));
+            add2(v[r][2 * jl + 1], pred4rp<T2, T>(rw, src(rw.j0), src(rw.j0 + 1), src(rw.j0 + 2), src(rw.j0 + 3)));
       }
     }
   }
