@@ -124,7 +124,9 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     tma_load_tile(&maps.tm[f], PF, &s_bar, bx * B, by * B, bz * B, G::TILE);
   };
   unsigned long long aoff = 0;  // bytes used in this CTA's staging arena (the same in every thread)
+  __shared__ BlockWalk s_wk;  // the next tile's block (one field)
   if (tid == 0) {
+    s_wk.init(blockIdx.x + gridDim.x, gridDim.x, a.nbx, a.nby);
     mbar_init(&s_bar);
     if ((int)blockIdx.x < a.nblocks) tile_of(blockIdx.x);
   }
@@ -152,21 +154,21 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
 
     // ---- forward transform
     fwd_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg, [&] {
-      if (tid == 0 && nb < a.nblocks) tile_of(nb);
+      if (tid == 0 && nb < a.nblocks) {
+        if constexpr (NF == 1) {
+          tma_load_tile(&maps.tm[0], PF, &s_bar, s_wk.bx * B, s_wk.by * B, s_wk.bz * B, G::TILE);
+          s_wk.next();
+        } else {
+          tile_of(nb);
+        }
+      }
     });
     if constexpr (G::L == 1) __syncthreads();  // no cube: the halo's last reads were just now
 
     // ---- significance bits (bit 2 zl + p: column x0 + p at z = h B/2 + zl),
     // mask rows by bit transpose over the segment
     if constexpr (NF > 1) t = s_t[field_of<NF>(maps, a.nf, bid)];
-    unsigned W[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      W[r] = 0;
-#pragma unroll
-      for (int zl = 0; zl < ZH; ++zl)
-        W[r] |= ((unsigned)keep(v[r][zl].x, t) << (2 * zl)) | ((unsigned)keep(v[r][zl].y, t) << (2 * zl + 1));
-    }
+    unsigned W[2] = {keep_bits<ZH>(v[0], t), keep_bits<ZH>(v[1], t)};
     if (cE) W[0] &= ~ccm;
     const unsigned R0 = seg_transpose<B>(W[0], ap), R1 = seg_transpose<B>(W[1], ap);  // rows (zr, 2k), (zr, 2k+1)
     ROWOFF[zr * B + 2 * k] = __popc(R0);

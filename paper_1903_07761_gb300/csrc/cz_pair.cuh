@@ -185,6 +185,33 @@ __device__ __forceinline__ double2 sub2(double2 a, double2 b)
 __device__ __forceinline__ bool keep(float d, float t) { return !(fabsf(d) < t); }
 __device__ __forceinline__ bool keep(double d, double t) { return !(fabs(d) < t); }
 
+// Significance bits of a thread's half columns: bit 2 zl + p for component
+// p of v[zl].  For FP32 the sign of |d| - t (explicitly rounded, subnormals
+// kept) is the rule: negative iff |d| < t; +0 on a tie; NaN (positive, the
+// canonical GPU NaN) for a NaN detail or threshold; one funnel shift per
+// value collects the "dropped" sign bits.
+template <int ZH>
+__device__ __forceinline__ unsigned keep_bits(const float2 (&v)[ZH], float t)
+{
+  unsigned nk = 0;
+#pragma unroll
+  for (int zl = ZH - 1; zl >= 0; --zl) {
+    nk = __funnelshift_l(__float_as_uint(__fsub_rn(fabsf(v[zl].y), t)), nk, 1);
+    nk = __funnelshift_l(__float_as_uint(__fsub_rn(fabsf(v[zl].x), t)), nk, 1);
+  }
+  return ZH == 16 ? ~nk : (~nk & ((1u << (2 * ZH)) - 1u));
+}
+
+template <int ZH>
+__device__ __forceinline__ unsigned keep_bits(const double2 (&v)[ZH], double t)
+{
+  unsigned w = 0;
+#pragma unroll
+  for (int zl = 0; zl < ZH; ++zl)
+    w |= ((unsigned)keep(v[zl].x, t) << (2 * zl)) | ((unsigned)keep(v[zl].y, t) << (2 * zl + 1));
+  return w;
+}
+
 // ------------------------------------------------------------ geometry
 template <typename T, int B>
 struct G2 {
@@ -327,6 +354,34 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
   }
   return false;
 }
+
+// ------------------------------------------------------------ block walk
+// Block coordinates of bid, bid + step, bid + 2 step, ... of an nbx x nby x
+// nbz block grid, advanced without divisions: step's digits are added with
+// one carry per axis.  Kept in shared memory and used by one thread.
+struct BlockWalk {
+  int bx, by, bz, sx, sy, sz, nbx, nby;
+  __device__ __forceinline__ void init(int bid, int step, int nbx_, int nby_)
+  {
+    nbx = nbx_;
+    nby = nby_;
+    bx = bid % nbx;
+    by = (bid / nbx) % nby;
+    bz = bid / (nbx * nby);
+    sx = step % nbx;
+    sy = (step / nbx) % nby;
+    sz = step / (nbx * nby);
+  }
+  __device__ __forceinline__ void next()
+  {
+    int x = bx + sx, c = x >= nbx;
+    bx = c ? x - nbx : x;
+    int y = by + sy + c;
+    c = y >= nby;
+    by = c ? y - nby : y;
+    bz += sz + c;
+  }
+};
 
 // ------------------------------------------------------------ bit transpose
 // Over the B/2 lanes of a segment: lane a holds w with bit 2i + p = entry
@@ -1389,10 +1444,12 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
     return o0;
   };
 
+  __shared__ BlockWalk s_wk;  // coordinates of this CTA's current block
   if (tid == 0) {
     mbar_init(&s_bar[0]);
     mbar_init(&s_bar[1]);
     s_badx = 0;  // reset again after each block's last read
+    s_wk.init(blockIdx.x, gridDim.x, a.nbx, a.nby);
   }
   __syncthreads();
   __shared__ unsigned long long s_off;
@@ -1403,7 +1460,6 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
   int j = 0;
 
   for (int bid = blockIdx.x; bid < a.nblocks; bid += gridDim.x, j ^= 1) {
-    const int bx = bid % a.nbx, by = (bid / a.nbx) % a.nby, bz = bid / (a.nbx * a.nby);
     unsigned char *P = BUF0 + j * G::PBCAP;
     // next block's table entry, loaded now and used after the scatter
     const int nbid = bid + (int)gridDim.x;
@@ -1526,7 +1582,10 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
         *reinterpret_cast<T2 *>(OT + (((h * ZH + zl) * B + 2 * k + r) * B + x0) * ES) = v[r][zl];
     fence_async_smem();
     __syncthreads();
-    if (tid == 0) tma_store_tile(&omap, OT, bx * B, by * B, bz * B);
+    if (tid == 0) {
+      tma_store_tile(&omap, OT, s_wk.bx * B, s_wk.by * B, s_wk.bz * B);
+      s_wk.next();
+    }
   }
   if (tid == 0) bulk_wait_all();
 }
