@@ -330,6 +330,14 @@ __device__ __forceinline__ void tma_store_tile(const CUtensorMap *tm, const void
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
+// 16-byte asynchronous copy global -> shared (no register waits on it)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n\tcp.async.commit_group;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // the CTA's bulk stores have finished reading shared memory
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
@@ -1180,15 +1188,20 @@ __device__ __forceinline__ void fwd_all(T2 (&v)[2][B / 2], T2 *pl, T2 *hx, T *cu
 
 // Whole inverse transform.  The cube must not overlap the plane or the
 // halo; the caller orders the plane's and the halo's previous uses by a
-// barrier before the call, and their last reads by one after it.
-template <typename T, int B, int KIND, typename T2>
-__device__ __forceinline__ void inv_all(T2 (&v)[2][B / 2], T2 *pl, T2 *hx, T *cube, int a, int k, int h, int seg)
+// barrier before the call, and their last reads by one after it.  side()
+// runs after the first barrier (at the start without coarser levels).
+template <typename T, int B, int KIND, typename T2, typename F>
+__device__ __forceinline__ void inv_all(T2 (&v)[2][B / 2], T2 *pl, T2 *hx, T *cube, int a, int k, int h, int seg,
+                                        F &&side)
 {
   if constexpr (G2<T, B>::L > 1) {
     to_cube<T, B>(v, cube, a, k, h);
     __syncthreads();
+    side();
     cube_inv<T, B / 2, KIND, G2<T, B>::NT>(cube);
     from_cube<T, B>(v, cube, a, k, h);
+  } else {
+    side();
   }
   z_inv<T, B, KIND>(v, hx, k, a, h);
   y_inv<T, B, KIND>(v, pl, a, k, h);
@@ -1409,6 +1422,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
   const int zr = h * ZH + ap;  // z of this thread's two mask rows
   const bool cE = (x0 % Q == 0) && ((2 * k) % Q == 0);  // column (x0, 2k) holds coarse values
   const bool pre = a.stage2 != 0;  // decoded payloads sit in 16-byte aligned slots
+  constexpr int FT = NT - 32;      // lane 0 of the last warp: fetches the next block
 
   // metadata of block b into buffer slot j, and (with stage 2) the start
   // of its payload copy; called by thread 0 with b's table entry (t0, t1)
@@ -1445,6 +1459,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
   };
 
   __shared__ BlockWalk s_wk;  // coordinates of this CTA's current block
+  __shared__ __align__(16) unsigned long long s_tab[2];  // the next block's table entry
   if (tid == 0) {
     mbar_init(&s_bar[0]);
     mbar_init(&s_bar[1]);
@@ -1456,30 +1471,28 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
   if (tid == 0 && (int)blockIdx.x < a.nblocks)
     s_off = fetch(blockIdx.x, 0, pre ? a.table[2 * blockIdx.x] : 0ull, pre ? a.table[2 * blockIdx.x + 1] : 0ull);
   __syncthreads();
-  unsigned phase[2] = {0u, 0u};
+  unsigned phase = 0;  // bit j: parity of buffer j's next completion (a register, not an indexed array)
   int j = 0;
 
   for (int bid = blockIdx.x; bid < a.nblocks; bid += gridDim.x, j ^= 1) {
     unsigned char *P = BUF0 + j * G::PBCAP;
-    // next block's table entry, loaded now and used after the scatter
+    // next block's table entry, fetched now (asynchronously, into shared
+    // memory) by the thread that later starts its payload copy
     const int nbid = bid + (int)gridDim.x;
-    unsigned long long nt0 = 0, nt1 = 0;
-    if (tid == 0 && pre && nbid < a.nblocks) {
-      nt0 = a.table[2 * nbid];
-      nt1 = a.table[2 * nbid + 1];
-    }
+    if (tid == FT && pre && nbid < a.nblocks) cp_async16(s_tab, a.table + 2 * nbid);
     const unsigned nnz = s_nnz[j];
     const int pbytes = HEAD + (int)nnz * ES;
     bool bad0 = s_bad[j] != 0;
     if (pre) {
       if (!bad0) {
-        if (!mbar_wait(&s_bar[j], phase[j])) {
+        const unsigned par = (phase >> j) & 1u;
+        if (!mbar_wait(&s_bar[j], par)) {
           // the copy never completed: record, wait once more for it, stop
           if (tid == 0) atomicCAS(&ws->status, 0u, ST_TIMEOUT);
-          mbar_wait(&s_bar[j], phase[j]);
+          mbar_wait(&s_bar[j], par);
           break;
         }
-        phase[j] ^= 1u;
+        phase ^= 1u << j;
       }
     } else if (!bad0) {
       const unsigned *c32 = reinterpret_cast<const unsigned *>(a.in + a.data0 + s_off);
@@ -1567,11 +1580,24 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
     // level-0 exchange uses next
     if (tid == 0) bulk_wait_read();
     __syncthreads();  // buffer j and the row offsets are free; s_badx has been read
-    if (tid == 0) {
-      s_badx = 0;
-      if (nbid < a.nblocks) s_off = fetch(nbid, j ^ 1, nt0, nt1);
-    }
-    if (!bad) inv_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg);
+    if (tid == 0) s_badx = 0;
+    // the next block's metadata and payload copy, issued by a thread of the
+    // last warp (idle in the first passes of the coarser levels)
+    auto fetch_next = [&] {
+      if (tid == FT && nbid < a.nblocks) {
+        unsigned long long t0 = 0, t1 = 0;
+        if (pre) {
+          cp_async_wait_all();
+          t0 = s_tab[0];
+          t1 = s_tab[1];
+        }
+        s_off = fetch(nbid, j ^ 1, t0, t1);
+      }
+    };
+    if (!bad)
+      inv_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg, fetch_next);
+    else
+      fetch_next();
     // block -> output tile -> TMA store, which drains while the next block
     // is decoded
     __syncthreads();  // the plane and the halo have been read
@@ -1618,7 +1644,7 @@ __global__ void __launch_bounds__(B * B / 2) k_dense2(const DenseArgs a)
   if constexpr (FWD)
     fwd_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg, [] {});
   else
-    inv_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg);
+    inv_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg, [] {});
 #pragma unroll
   for (int r = 0; r < 2; ++r)
 #pragma unroll
