@@ -171,10 +171,10 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     unsigned W[2] = {keep_bits<ZH>(v[0], t), keep_bits<ZH>(v[1], t)};
     if (cE) W[0] &= ~ccm;
     const unsigned R0 = seg_transpose<B>(W[0], ap), R1 = seg_transpose<B>(W[1], ap);  // rows (zr, 2k), (zr, 2k+1)
-    ROWOFF[zr * B + 2 * k] = __popc(R0);
-    ROWOFF[zr * B + 2 * k + 1] = __popc(R1);
-    put_row<B>(MASKU, zr, 2 * k, R0);
-    put_row<B>(MASKU, zr, 2 * k + 1, R1);
+    ROWOFF[rpad<B>(zr, 2 * k)] = __popc(R0);
+    ROWOFF[rpad<B>(zr, 2 * k + 1)] = __popc(R1);
+    put_rowi<B>(MASKU, rpad<B>(zr, 2 * k), R0);
+    put_rowi<B>(MASKU, rpad<B>(zr, 2 * k + 1), R1);
     __syncthreads();
     unsigned nnz;
     {
@@ -182,13 +182,13 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
       unsigned loc[IPT], sum = 0;
 #pragma unroll
       for (int q = 0; q < IPT; ++q) {
-        loc[q] = ROWOFF[tid * IPT + q];
+        loc[q] = ROWOFF[rpad_of<B>(tid * IPT + q)];
         sum += loc[q];
       }
       unsigned ex = block_exsum_nb<NT>(sum, s_u, nnz);
 #pragma unroll
       for (int q = 0; q < IPT; ++q) {
-        ROWOFF[tid * IPT + q] = ex;
+        ROWOFF[rpad_of<B>(tid * IPT + q)] = ex;
         ex += loc[q];
       }
     }
@@ -201,9 +201,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     const bool ok = so + slot <= a.arena_bytes;
     if (ok) {
       unsigned char *P = arena + so + 8;
-      // mask rows: a coalesced copy of the shared rows (8-byte aligned)
-      for (int i = tid; i < G::MASKB / 8; i += NT)
-        reinterpret_cast<uint2 *>(P + 64 * ES)[i] = reinterpret_cast<const uint2 *>(MASKU)[i];
+      // mask rows: a coalesced copy of the shared (padded) rows
+      for (int i = tid; i < B * B; i += NT) put_rowi<B>(P + 64 * ES, i, get_rowi<B>(MASKU, rpad_of<B>(i)));
       if (cE) {
 #pragma unroll
         for (int zl = 0; zl < ZH; zl += Q)
@@ -220,8 +219,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
           for (int r = 0; r < 2; ++r) {
             const unsigned b2 = (W[r] >> (2 * zl)) & 3u;
             if (b2) {
-              const unsigned wd = get_row<B>(MASKU, z, 2 * k + r);
-              const unsigned base = ROWOFF[z * B + 2 * k + r];
+              const unsigned wd = get_rowi<B>(MASKU, rpad<B>(z, 2 * k + r));
+              const unsigned base = ROWOFF[rpad<B>(z, 2 * k + r)];
               if (b2 & 1u) VALS[base + __popc(wd & lowE)] = v[r][zl].x;
               if (b2 & 2u) VALS[base + __popc(wd & lowO)] = v[r][zl].y;
             }

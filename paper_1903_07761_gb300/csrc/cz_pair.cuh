@@ -239,7 +239,10 @@ struct G2 {
   // cube of the coarser levels: (B/2)^2 rows of B/2 + 1 elements
   static constexpr int CUBE = L > 1 ? (B / 2) * (B / 2) * (B / 2 + 1) * ES : 0;
   static constexpr int CUBE_AL = (CUBE + 127) / 128 * 128;
-  static constexpr int ROWB = B * B * 4;
+  // row offsets and mask rows in shared memory: B + 1 rows per z, so that
+  // the rows of one y over consecutive z fall in distinct banks
+  static constexpr int ROWB = B * (B + 1) * 4;
+  static constexpr int MASKBP = B * (B + 1) * B / 8;
   static constexpr int PMAX_AL = (PMAX + 127) / 128 * 128;
   // stage kernel: tile | plane area (the cube at its start) | halo area
   // (after the transform: the row offsets and the mask rows)
@@ -274,7 +277,7 @@ struct G2 {
   static constexpr int OTB = (OTB0 + 127) / 128 * 128;
   static constexpr int SMEM_D = R2D + 2 * PBCAP + OTB;
   static_assert(HP == NK && NK == ZH && NT == HP * NK * 2, "thread grid");
-  static_assert(HALO >= ROWB + MASKB, "row offsets and mask rows fit the halo area");
+  static_assert(HALO >= ROWB + MASKBP, "row offsets and mask rows fit the halo area");
   static_assert(SMEM_C <= 227 * 1024 - 1024, "stage kernel shared memory");
   static_assert(SMEM_D <= 227 * 1024 - 1024, "decompress shared memory");
   static_assert(SMEM_S2B <= 227 * 1024 - 1024, "stage-2 shared memory");
@@ -1220,29 +1223,54 @@ __device__ __forceinline__ void st_le_f64(unsigned char *p, double v)
   st_le<unsigned long long>(p, (unsigned long long)__double_as_longlong(v));
 }
 
-// store a B-bit row word at bit offset (z*B + y)*B of the mask
+// B-bit row word number m of a mask (bit offset m*B)
+template <int B>
+__device__ __forceinline__ void put_rowi(unsigned char *mask, int m, unsigned w)
+{
+  if constexpr (B == 32)
+    reinterpret_cast<unsigned *>(mask)[m] = w;
+  else if constexpr (B == 16)
+    reinterpret_cast<unsigned short *>(mask)[m] = (unsigned short)w;
+  else
+    mask[m] = (unsigned char)w;
+}
+
+template <int B>
+__device__ __forceinline__ unsigned get_rowi(const unsigned char *mask, int m)
+{
+  if constexpr (B == 32)
+    return reinterpret_cast<const unsigned *>(mask)[m];
+  else if constexpr (B == 16)
+    return reinterpret_cast<const unsigned short *>(mask)[m];
+  else
+    return mask[m];
+}
+
+// row (z, y) of a stream mask (row z*B + y)
 template <int B>
 __device__ __forceinline__ void put_row(unsigned char *mask, int z, int y, unsigned w)
 {
-  const int bit = (z * B + y) * B;
-  if constexpr (B == 32)
-    *reinterpret_cast<unsigned *>(mask + bit / 8) = w;
-  else if constexpr (B == 16)
-    *reinterpret_cast<unsigned short *>(mask + bit / 8) = (unsigned short)w;
-  else
-    mask[bit / 8] = (unsigned char)w;
+  put_rowi<B>(mask, z * B + y, w);
 }
 
 template <int B>
 __device__ __forceinline__ unsigned get_row(const unsigned char *mask, int z, int y)
 {
-  const int bit = (z * B + y) * B;
-  if constexpr (B == 32)
-    return *reinterpret_cast<const unsigned *>(mask + bit / 8);
-  else if constexpr (B == 16)
-    return *reinterpret_cast<const unsigned short *>(mask + bit / 8);
-  else
-    return mask[bit / 8];
+  return get_rowi<B>(mask, z * B + y);
+}
+
+// index of row (z, y) in the padded shared-memory tables (B + 1 rows per z)
+template <int B>
+__device__ __forceinline__ int rpad(int z, int y)
+{
+  return z * (B + 1) + y;
+}
+
+// row offset table entry of scan position p (rows in stream order)
+template <int B>
+__device__ __forceinline__ int rpad_of(int p)
+{
+  return rpad<B>(p / B, p % B);
 }
 
 template <typename T>
@@ -1513,8 +1541,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
     const unsigned W[2] = {seg_transpose<B>(R0, ap), seg_transpose<B>(R1, ap)};
     if (!bad0) {
       // row populations -> row offsets; coarse positions carry no mask bit
-      ROWOFF[zr * B + 2 * k] = __popc(R0);
-      ROWOFF[zr * B + 2 * k + 1] = __popc(R1);
+      ROWOFF[rpad<B>(zr, 2 * k)] = __popc(R0);
+      ROWOFF[rpad<B>(zr, 2 * k + 1)] = __popc(R1);
       if ((zr % Q) == 0 && ((2 * k) % Q) == 0) {
         unsigned cm = 0;
 #pragma unroll
@@ -1526,14 +1554,14 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
       unsigned loc[IPT], sum = 0;
 #pragma unroll
       for (int q = 0; q < IPT; ++q) {
-        loc[q] = ROWOFF[tid * IPT + q];
+        loc[q] = ROWOFF[rpad_of<B>(tid * IPT + q)];
         sum += loc[q];
       }
       unsigned tot;
       unsigned ex = block_exsum_nb<NT>(sum, s_u, tot);
 #pragma unroll
       for (int q = 0; q < IPT; ++q) {
-        ROWOFF[tid * IPT + q] = ex;
+        ROWOFF[rpad_of<B>(tid * IPT + q)] = ex;
         ex += loc[q];
       }
       if (tid == 0 && tot != nnz) atomicOr(&s_badx, 1u);
@@ -1563,7 +1591,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
             const unsigned b2 = (W[r] >> (2 * zl)) & 3u;
             if (b2) {
               const unsigned wd = get_row<B>(MASK, z, 2 * k + r);
-              const unsigned base = ROWOFF[z * B + 2 * k + r];
+              const unsigned base = ROWOFF[rpad<B>(z, 2 * k + r)];
               if (b2 & 1u) v[r][zl].x = VALS[base + __popc(wd & lowE)];
               if (b2 & 2u) v[r][zl].y = VALS[base + __popc(wd & lowO)];
             }
