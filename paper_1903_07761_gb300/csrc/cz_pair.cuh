@@ -1259,6 +1259,26 @@ __device__ __forceinline__ unsigned get_row(const unsigned char *mask, int z, in
   return get_rowi<B>(mask, z * B + y);
 }
 
+// rows (z, y) and (z, y + 1), y even, in one load (they are adjacent)
+template <int B>
+__device__ __forceinline__ void get_row_pair(const unsigned char *mask, int z, int y, unsigned &r0, unsigned &r1)
+{
+  const int m = z * B + y;
+  if constexpr (B == 32) {
+    const uint2 w = reinterpret_cast<const uint2 *>(mask)[m >> 1];
+    r0 = w.x;
+    r1 = w.y;
+  } else if constexpr (B == 16) {
+    const unsigned w = reinterpret_cast<const unsigned *>(mask)[m >> 1];
+    r0 = w & 0xFFFFu;
+    r1 = w >> 16;
+  } else {
+    const unsigned w = reinterpret_cast<const unsigned short *>(mask)[m >> 1];
+    r0 = w & 0xFFu;
+    r1 = w >> 8;
+  }
+}
+
 // index of row (z, y) in the padded shared-memory tables (B + 1 rows per z)
 template <int B>
 __device__ __forceinline__ int rpad(int z, int y)
@@ -1537,7 +1557,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
     // this thread's mask rows (z = zr at rows 2k, 2k + 1) and, transposed
     // over the segment's lanes, its own column bits (bit 2 zl + p: column
     // x0 + p at z = h B/2 + zl)
-    const unsigned R0 = bad0 ? 0u : get_row<B>(MASK, zr, 2 * k), R1 = bad0 ? 0u : get_row<B>(MASK, zr, 2 * k + 1);
+    unsigned R0 = 0, R1 = 0;
+    if (!bad0) get_row_pair<B>(MASK, zr, 2 * k, R0, R1);
     const unsigned W[2] = {seg_transpose<B>(R0, ap), seg_transpose<B>(R1, ap)};
     if (!bad0) {
       // row populations -> row offsets; coarse positions carry no mask bit
