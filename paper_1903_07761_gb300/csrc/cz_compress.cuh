@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
 
   WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
   const int tid = threadIdx.x, lane = tid & 31;
-  const int ap = tid % G::HP, k = (tid / G::HP) % G::NK, h = tid / (NT / 2);
+  int ap, k, h;
+  quad_of<B>(tid, ap, k, h);
   const int seg = lane - ap;
   const int x0 = 2 * ap;
   const int zr = h * ZH + ap;  // z of this thread's two mask rows

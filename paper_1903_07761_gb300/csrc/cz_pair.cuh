@@ -366,6 +366,27 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
   return false;
 }
 
+// ------------------------------------------------------------ thread grid
+// Thread tid holds x-pair a of row pair k over z-half h.  With B >= 16 the
+// warps alternate between the halves, so the warps holding the boundary row
+// pairs (whose y-step takes the longer general form) land on four different
+// schedulers; the half stays the same across a warp.
+template <int B>
+__device__ __forceinline__ void quad_of(int tid, int &a, int &k, int &h)
+{
+  constexpr int HP = B / 2, NT = B * B / 2;
+  if constexpr (NT >= 64) {
+    const int w = tid >> 5, lane = tid & 31;
+    h = w & 1;
+    k = (w >> 1) * (32 / HP) + lane / HP;
+    a = lane % HP;
+  } else {
+    a = tid % HP;
+    k = (tid / HP) % (B / 2);
+    h = tid / (NT / 2);
+  }
+}
+
 // ------------------------------------------------------------ block walk
 // Block coordinates of bid, bid + step, bid + 2 step, ... of an nbx x nby x
 // nbz block grid, advanced without divisions: step's digits are added with
@@ -1464,7 +1485,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
 
   WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
   const int tid = threadIdx.x, lane = tid & 31;
-  const int ap = tid % G::HP, k = (tid / G::HP) % G::NK, h = tid / (NT / 2);
+  int ap, k, h;
+  quad_of<B>(tid, ap, k, h);
   const int seg = lane - ap;
   const int x0 = 2 * ap;
   const int zr = h * ZH + ap;  // z of this thread's two mask rows
@@ -1677,7 +1699,8 @@ __global__ void __launch_bounds__(B * B / 2) k_dense2(const DenseArgs a)
   T2 *PL = reinterpret_cast<T2 *>(smem + G::CUBE_AL);
   T2 *HX = reinterpret_cast<T2 *>(smem + G::CUBE_AL + G::PLANE);
   const int tid = threadIdx.x, lane = tid & 31;
-  const int ap = tid % G::HP, k = (tid / G::HP) % G::NK, h = tid / (G::NT / 2);
+  int ap, k, h;
+  quad_of<B>(tid, ap, k, h);
   const int seg = lane - ap;
   const int bid = blockIdx.x;
   const int bx = bid % a.nbx, by = (bid / a.nbx) % a.nby, bz = bid / (a.nbx * a.nby);
