@@ -273,9 +273,12 @@ struct G2 {
   // decompress payload buffer: whole payloads of up to PBCAP bytes (with
   // 32^3 blocks most payloads, the rest read their values from global memory)
   static constexpr int PBCAP = B == 32 ? (PMAX_AL < 16384 ? PMAX_AL : 16384) : PMAX_AL;
+  // payload buffers: with 32^3 blocks (one CTA per SM) a copy is issued two
+  // blocks ahead; smaller blocks keep two buffers and more CTAs per SM
+  static constexpr int NPB = B == 32 ? 3 : 2;
   static constexpr int OTB0 = TILE > PLANE + HALO ? TILE : PLANE + HALO;
   static constexpr int OTB = (OTB0 + 127) / 128 * 128;
-  static constexpr int SMEM_D = R2D + 2 * PBCAP + OTB;
+  static constexpr int SMEM_D = R2D + NPB * PBCAP + OTB;
   static_assert(HP == NK && NK == ZH && NT == HP * NK * 2, "thread grid");
   static_assert(HALO >= ROWB + MASKBP, "row offsets and mask rows fit the halo area");
   static_assert(SMEM_C <= 227 * 1024 - 1024, "stage kernel shared memory");
@@ -1474,13 +1477,14 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
   constexpr int ZH = G::ZH;
   T *CB = reinterpret_cast<T *>(smem);  // cube of the coarser levels
   unsigned *ROWOFF = reinterpret_cast<unsigned *>(smem);  // row offsets (before the cube)
-  unsigned char *BUF0 = smem + G::R2D;  // two payload buffers of G::PBCAP bytes
-  unsigned char *OT = BUF0 + 2 * G::PBCAP;  // output tile [z][y][x]
+  constexpr int NPB = G::NPB;
+  unsigned char *BUF0 = smem + G::R2D;  // NPB payload buffers of G::PBCAP bytes
+  unsigned char *OT = BUF0 + NPB * G::PBCAP;  // output tile [z][y][x]
   T2 *PL = reinterpret_cast<T2 *>(OT);  // level-0 plane and halo, inside the tile area
   T2 *HX = reinterpret_cast<T2 *>(OT + G::PLANE);
-  __shared__ __align__(8) unsigned long long s_bar[2];
+  __shared__ __align__(8) unsigned long long s_bar[NPB];
   __shared__ unsigned s_u[40];
-  __shared__ unsigned s_nnz[2], s_bad[2];
+  __shared__ unsigned s_nnz[NPB], s_bad[NPB];
   __shared__ unsigned s_badx;
 
   WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
@@ -1529,26 +1533,32 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
   };
 
   __shared__ BlockWalk s_wk;  // coordinates of this CTA's current block
-  __shared__ __align__(16) unsigned long long s_tab[2];  // the next block's table entry
+  __shared__ __align__(16) unsigned long long s_tab[2];  // a later block's table entry
+  __shared__ unsigned long long s_off[NPB];  // without stage 2: each buffer's chunk offset
   if (tid == 0) {
-    mbar_init(&s_bar[0]);
-    mbar_init(&s_bar[1]);
+    for (int q = 0; q < NPB; ++q) mbar_init(&s_bar[q]);
     s_badx = 0;  // reset again after each block's last read
     s_wk.init(blockIdx.x, gridDim.x, a.nbx, a.nby);
   }
   __syncthreads();
-  __shared__ unsigned long long s_off;
-  if (tid == 0 && (int)blockIdx.x < a.nblocks)
-    s_off = fetch(blockIdx.x, 0, pre ? a.table[2 * blockIdx.x] : 0ull, pre ? a.table[2 * blockIdx.x + 1] : 0ull);
+  if (tid == 0) {
+    // the first NPB - 1 blocks' copies
+    for (int q = 0; q < NPB - 1; ++q) {
+      const int b = blockIdx.x + q * gridDim.x;
+      if (b < a.nblocks) s_off[q] = fetch(b, q, pre ? a.table[2 * b] : 0ull, pre ? a.table[2 * b + 1] : 0ull);
+    }
+  }
   __syncthreads();
   unsigned phase = 0;  // bit j: parity of buffer j's next completion (a register, not an indexed array)
   int j = 0;
 
-  for (int bid = blockIdx.x; bid < a.nblocks; bid += gridDim.x, j ^= 1) {
+  for (int bid = blockIdx.x; bid < a.nblocks; bid += gridDim.x, j = j + 1 < NPB ? j + 1 : 0) {
     unsigned char *P = BUF0 + j * G::PBCAP;
-    // next block's table entry, fetched now (asynchronously, into shared
-    // memory) by the thread that later starts its payload copy
-    const int nbid = bid + (int)gridDim.x;
+    // the table entry of the block NPB - 1 ahead, fetched now
+    // (asynchronously, into shared memory) by the thread that later starts
+    // its payload copy into the buffer this block frees
+    const int nbid = bid + (NPB - 1) * (int)gridDim.x;
+    const int jn = j == 0 ? NPB - 1 : j - 1;  // (j + NPB - 1) mod NPB
     if (tid == FT && pre && nbid < a.nblocks) cp_async16(s_tab, a.table + 2 * nbid);
     const unsigned nnz = s_nnz[j];
     const int pbytes = HEAD + (int)nnz * ES;
@@ -1565,7 +1575,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
         phase ^= 1u << j;
       }
     } else if (!bad0) {
-      const unsigned *c32 = reinterpret_cast<const unsigned *>(a.in + a.data0 + s_off);
+      const unsigned *c32 = reinterpret_cast<const unsigned *>(a.in + a.data0 + s_off[j]);
       const int cp = pbytes <= G::PBCAP ? pbytes : HEAD;
       for (int w = tid; w < cp / 4; w += NT) reinterpret_cast<unsigned *>(P)[w] = __ldg(c32 + 2 + w);
       __syncthreads();
@@ -1574,7 +1584,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
     const T *VALS = pbytes <= G::PBCAP
                         ? reinterpret_cast<const T *>(P + HEAD)
                         : (pre ? reinterpret_cast<const T *>(a.staging + (size_t)bid * a.slot + HEAD)
-                               : reinterpret_cast<const T *>(a.in + a.data0 + s_off + 8 + HEAD));
+                               : reinterpret_cast<const T *>(a.in + a.data0 + s_off[j] + 8 + HEAD));
     const unsigned char *MASK = P + 64 * ES;
     // this thread's mask rows (z = zr at rows 2k, 2k + 1) and, transposed
     // over the segment's lanes, its own column bits (bit 2 zl + p: column
@@ -1662,7 +1672,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
           t0 = s_tab[0];
           t1 = s_tab[1];
         }
-        s_off = fetch(nbid, j ^ 1, t0, t1);
+        s_off[jn] = fetch(nbid, jn, t0, t1);
       }
     };
     if (!bad)
