@@ -254,18 +254,25 @@ def served(rates=(1000.0, 5000.0), n: int = 400, budget_gb: float = 40.0, stream
 # ------------------------------------------------------------------ FP64
 def _w3ai_fp64_ops_per_element(B: int) -> float:
     """FP64 instructions per element of the exact-build W3ai transform (one
-    direction) over all levels and axes, counted from the kernels' steps:
-    per pair the average (add, mul) and the detail (sub) plus the predicted
-    half-cell value, 5 operations in the interior (two weight multiplies,
-    add, multiply by 1/8, add) and 7 at the two boundary pairs of a line."""
-    total, frac = 0.0, 1.0
-    n = B
+    direction) over all levels and axes, counted from the kernels' steps.
+    Forward, per pair: the average (add, mul), the predicted half-cell value
+    and the detail (sub); inverse, per pair: the predicted value, its sum
+    with the detail (add) and the second sample (mul, sub).  The finest x-
+    and y-steps use run-time stencils: 8 operations per interior pair (two
+    weight multiplies, add, multiply by 1/8, add) and 10 at the two boundary
+    pairs of a line.  The finest z-step and the coarser levels use
+    compile-time rows, whose interior form is one subtraction: 6 per
+    interior pair, 10 at the boundary pairs."""
+    total, frac, n, level = 0.0, 1.0, B, 0
     while n >= 8:
         m = n // 2
-        per_line = (m - 2) * 8 + 2 * 10
-        total += 3 * frac * per_line / n
+        run_time = (m - 2) * 8 + 2 * 10
+        compile_time = (m - 2) * 6 + 2 * 10
+        lines = 2 * run_time + compile_time if level == 0 else 3 * compile_time
+        total += frac * lines / n
         n //= 2
         frac /= 8
+        level += 1
     return total
 
 
