@@ -62,6 +62,23 @@ def test_stream_and_decode_bit_identical(dtype, block, shape, kind, stage2):
         np.testing.assert_array_equal(rec.view(np.uint8), want.view(np.uint8))
 
 
+@pytest.mark.parametrize("stage2", [True, False])
+@pytest.mark.parametrize("dtype,block,shape", [
+    (np.float32, 32, (64, 160, 544)),  # 17 x 5 x 2 = 170 blocks: more than one per stage CTA
+    (np.float64, 16, (64, 96, 400)),   # 25 x 6 x 4 = 600 blocks
+])
+def test_non_cubic_grid_with_several_blocks_per_cta(dtype, block, shape, stage2):
+    """The persistent kernels walk their blocks in steps of the grid size
+    over a non-cubic block grid (carries in x and y); every block's tile and
+    output tile must land at its own coordinates."""
+    f = smooth_field(shape, dtype, seed=5)
+    ref = O.compress(f, block, O.W3AI, 1e-3, stage2=stage2)
+    got = gpu_compress(f, block, O.W3AI, 1e-3, stage2=stage2)
+    assert got == ref, describe_diff(got, ref)
+    rec = gpu_decompress(got)
+    np.testing.assert_array_equal(rec.view(np.uint8), O.decompress(ref).view(np.uint8))
+
+
 @pytest.mark.parametrize("dtype,block", [(np.float64, 16), (np.float32, 16)])
 def test_payload_exactly_at_the_stage2_shared_capacity(dtype, block):
     """One block whose payload is exactly 16 KiB (the stage-2 kernels'
