@@ -1090,8 +1090,8 @@ __device__ __forceinline__ void z_inv(T2 (&v)[2][B / 2], T2 *hx, int k, int a, i
 
 // ============================================================ coarser levels
 // After level 0 the coarse values (all coordinates even) form an N^3 cube,
-// N = B/2, held by the threads of even rows in v[2j].x.  Levels 1.. are the
-// same transform on that cube, run in shared memory by all NT threads:
+// N = B/2, held in v[0][2 jl].x of every thread (to_cube).  Levels 1.. are
+// the same transform on that cube, run in shared memory by up to NT threads:
 // C(x, y, z) = C[(z N + y)(N + 1) + x] (rows padded by one element, so that
 // lines along x, taken y-fastest across threads, hit distinct banks).
 template <int N>
