@@ -32,6 +32,7 @@ W4, W4LI, W3AI = 0, 1, 2
 F32, F64 = 0, 1
 EPS_REL, EPS_ABS = 0, 1
 BOUND_PAPER, BOUND_STRICT = 0, 1
+FLAG_ZERO4, FLAG_ZERO8 = 2, 4  # bit zeroing of the kept details (Sec. 3, Exp. 2)
 OK, ERR_ARG, ERR_CAPACITY, ERR_CORRUPT = 0, -1, -2, -3
 HEADER_BYTES = 128
 
@@ -79,6 +80,11 @@ def lib():
                 f.argtypes = [C.c_int, C.c_int,
                               C.c_float if sfx == "f32" else C.c_double,
                               C.c_int, P, P, C.c_size_t]
+                f.restype = C.c_int64
+                f = getattr(L, f"czo_encode_block_z_{sfx}")
+                f.argtypes = [C.c_int, C.c_int,
+                              C.c_float if sfx == "f32" else C.c_double,
+                              C.c_int, C.c_int, P, P, C.c_size_t]
                 f.restype = C.c_int64
                 f = getattr(L, f"czo_decode_block_{sfx}")
                 f.argtypes = [C.c_int, C.c_int, C.c_int, P, C.c_size_t, P]
@@ -167,14 +173,14 @@ def update_weight(m: int, k: int, j: int):
 
 
 # ---------------------------------------------------------------- block codec
-def encode_block(kind: int, t: float, blk: np.ndarray, stage2: bool) -> bytes:
+def encode_block(kind: int, t: float, blk: np.ndarray, stage2: bool, zbits: int = 0) -> bytes:
     blk = np.ascontiguousarray(blk)
     B = blk.shape[0]
     s = blk.dtype.itemsize
     cap = 64 * s + B ** 3 // 8 + B ** 3 * s + 4096
     out = np.zeros(cap, np.uint8)
-    n = getattr(lib(), f"czo_encode_block_{_sfx(blk)}")(
-        kind, B, t, int(stage2), _ptr(blk), _ptr(out), cap)
+    n = getattr(lib(), f"czo_encode_block_z_{_sfx(blk)}")(
+        kind, B, t, int(stage2), int(zbits), _ptr(blk), _ptr(out), cap)
     assert n >= 0, n
     return out[:n].tobytes()
 
@@ -190,18 +196,23 @@ def decode_block(kind: int, B: int, dtype, chunk: bytes, stage2: bool) -> np.nda
 
 
 # ---------------------------------------------------------------- whole field
+def zero_flag(zbits: int) -> int:
+    return {0: 0, 4: FLAG_ZERO4, 8: FLAG_ZERO8}[int(zbits)]
+
+
 def params(shape, block, dtype, kind, eps, eps_mode=EPS_REL, stage2=True, range_=-1.0,
-           bound_mode=0):
+           bound_mode=0, zbits=0):
     nz, ny, nx = shape
     return Params(nx, ny, nz, block, F64 if np.dtype(dtype) == np.float64 else F32,
-                  kind, eps_mode, int(stage2), int(bound_mode), 0, float(eps), float(range_))
+                  kind, eps_mode, int(stage2), int(bound_mode), zero_flag(zbits), float(eps), float(range_))
 
 
 def compress(field: np.ndarray, block: int, kind: int, eps: float,
              eps_mode: int = EPS_REL, stage2: bool = True, range_: float = -1.0,
-             bound_mode: int = 0) -> bytes:
+             bound_mode: int = 0, zbits: int = 0) -> bytes:
+    """zbits = 4 / 8: bit zeroing Z4 / Z8 of the kept details (Sec. 3, Exp. 2)."""
     field = np.ascontiguousarray(field)
-    p = params(field.shape, block, field.dtype, kind, eps, eps_mode, stage2, range_, bound_mode)
+    p = params(field.shape, block, field.dtype, kind, eps, eps_mode, stage2, range_, bound_mode, zbits)
     cap = C.c_size_t()
     r = lib().czo_compress_bound(C.byref(p), C.byref(cap))
     if r != OK:
@@ -233,7 +244,8 @@ def read_header(stream: bytes) -> dict:
     if r != OK:
         raise ValueError(f"bad header: {r}")
     return dict(nx=p.nx, ny=p.ny, nz=p.nz, block=p.block, dtype=p.dtype, kind=p.kind,
-                eps_mode=p.eps_mode, stage2=p.stage2, bound_mode=p.bound_mode, eps=p.eps, range=p.range,
+                eps_mode=p.eps_mode, stage2=p.stage2, bound_mode=p.bound_mode, flags=p.flags,
+                eps=p.eps, range=p.range,
                 t=t.value, min=mn.value, max=mx.value, total=tot.value)
 
 

@@ -277,7 +277,7 @@ int czo_rle_decode(const uint32_t *tokens, size_t ntok, const uint8_t *lits,
  *   0 u32 magic "CCZ1"   4 u16 version=1   6 u16 header bytes=128
  *   8 i32 nx  12 i32 ny  16 i32 nz
  *  20 u8 B  21 u8 dtype  22 u8 kind  23 u8 stage2  24 u8 eps_mode  25 u8 L
- *  26 u8 bound_mode  28 u32 nblocks
+ *  26 u8 bound_mode  27 u8 flags (bit zeroing)  28 u32 nblocks
  *  32 f64 eps  40 f64 t (threshold as used, widened)  48 f64 min  56 f64 max
  *  64 f64 range  72 u64 chunk-section bytes  80 u64 total stream bytes
  * Then (nblocks+1) u64 chunk offsets relative to the chunk section, which
@@ -306,6 +306,7 @@ static void czo_write_header(uint8_t *out, const czo_params *p, double t,
   out[24] = (uint8_t)p->eps_mode;
   out[25] = (uint8_t)L;
   out[26] = (uint8_t)p->bound_mode;
+  out[27] = (uint8_t)(p->flags & (CZO_FLAG_ZERO4 | CZO_FLAG_ZERO8));
   memcpy(out + 28, &nb, 4);
   memcpy(out + 32, &p->eps, 8);
   memcpy(out + 40, &t, 8);
@@ -336,6 +337,7 @@ int czo_read_header(const uint8_t *in, size_t n, czo_params *p, double *t,
   p->stage2 = in[23];
   p->eps_mode = in[24];
   p->bound_mode = in[26];
+  p->flags = in[27] & (CZO_FLAG_ZERO4 | CZO_FLAG_ZERO8);
   memcpy(&p->eps, in + 32, 8);
   memcpy(t, in + 40, 8);
   memcpy(mn, in + 48, 8);
@@ -367,6 +369,10 @@ static int check_params(const czo_params *p)
   if (p->kind < CZO_W4 || p->kind > CZO_W3AI) return CZO_ERR_ARG;
   if (!(p->eps >= 0)) return CZO_ERR_ARG;
   if (p->bound_mode != CZO_BOUND_PAPER && p->bound_mode != CZO_BOUND_STRICT) return CZO_ERR_ARG;
+  /* one zeroing width at most; the strict bound does not cover its error */
+  const int z = p->flags & (CZO_FLAG_ZERO4 | CZO_FLAG_ZERO8);
+  if (z == (CZO_FLAG_ZERO4 | CZO_FLAG_ZERO8)) return CZO_ERR_ARG;
+  if (z && p->bound_mode == CZO_BOUND_STRICT) return CZO_ERR_ARG;
   return CZO_OK;
 }
 

@@ -52,6 +52,9 @@ enum {
 };
 
 #define CZO_HEADER_BYTES 128
+/* bit zeroing (Sec. 3, Exp. 2): the 4 / 8 least significant bits of every
+ * kept detail coefficient are cleared before the lossless substage */
+enum { CZO_FLAG_ZERO4 = 2, CZO_FLAG_ZERO8 = 4 };
 #define CZO_MAGIC 0x315A4343u /* bytes "CCZ1" */
 #define CZO_ZMIN_WORDS 2      /* shortest zero run coded as a run (32-bit words) */
 
@@ -64,7 +67,9 @@ typedef struct czo_params {
   int32_t stage2;     /* 1: byte shuffle + zero-RLE per chunk                  */
   int32_t bound_mode; /* CZO_BOUND_PAPER: threshold t ; CZO_BOUND_STRICT:
                          threshold t / C (see czo_synthesis_norm)             */
-  int32_t flags;      /* unused by the oracle (library build options)          */
+  int32_t flags;      /* CZO_FLAG_ZERO4 / CZO_FLAG_ZERO8: bit zeroing of the
+                         kept details; other bits (library build options)
+                         are ignored                                          */
   double eps;
   double range;       /* >= 0: use this range ; < 0: compute max - min         */
 } czo_params;
@@ -87,6 +92,12 @@ int64_t czo_encode_block_f32(int kind, int B, float t, int stage2,
                              const float *blk, uint8_t *out, size_t cap);
 int64_t czo_encode_block_f64(int kind, int B, double t, int stage2,
                              const double *blk, uint8_t *out, size_t cap);
+/* the same with the zbits (0, 4 or 8) least significant bits of every kept
+ * detail cleared */
+int64_t czo_encode_block_z_f32(int kind, int B, float t, int stage2, int zbits,
+                               const float *blk, uint8_t *out, size_t cap);
+int64_t czo_encode_block_z_f64(int kind, int B, double t, int stage2, int zbits,
+                               const double *blk, uint8_t *out, size_t cap);
 /* chunk bytes -> reconstructed block values */
 int czo_decode_block_f32(int kind, int B, int stage2, const uint8_t *chunk,
                          size_t n, float *blk);

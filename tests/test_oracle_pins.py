@@ -19,6 +19,7 @@ re-typing the oracle's formulas:
     tokens match hand-derived fixtures; lossless round trips;
   * PSNR of a known perturbation (Sec. 3, Eq. (1), with the factor 2).
 """
+import ctypes as C
 import json
 import os
 from fractions import Fraction
@@ -523,3 +524,67 @@ def test_corrupt_chunks_are_rejected():
         O.decompress(bytes(bad))
     with pytest.raises(ValueError):
         O.decompress(bytes(s[:-8]))
+
+
+# ---------------------------------------------------------------- bit zeroing
+def _raw_payload(chunk: bytes, B: int, dtype):
+    """[nnz | 0 | coarse | mask | values] of a chunk without stage 2."""
+    s = np.dtype(dtype).itemsize
+    nnz = int(np.frombuffer(chunk[:4], np.uint32)[0])
+    p = chunk[8:]
+    coarse = np.frombuffer(p[:64 * s], dtype)
+    mask = np.frombuffer(p[64 * s:64 * s + B ** 3 // 8], np.uint8)
+    vals = np.frombuffer(p[64 * s + B ** 3 // 8:64 * s + B ** 3 // 8 + nnz * s], dtype)
+    return nnz, coarse, mask, vals
+
+
+@pytest.mark.parametrize("dtype,B", [(np.float32, 32), (np.float32, 8), (np.float64, 16)])
+@pytest.mark.parametrize("kind", [O.W4, O.W4LI, O.W3AI])
+def test_bit_zeroing_clears_the_low_bits_of_the_kept_details_only(dtype, B, kind):
+    """Sec. 3, Exp. 2 (Z4 / Z8): the zbits least significant bits of every
+    kept detail coefficient are zeroed; which details are kept, the mask and
+    the coarse values do not change.  Checked against numpy bit masks of the
+    unzeroed chunk's values."""
+    rng = np.random.default_rng(kind * 10 + B)
+    blk = (rng.standard_normal((B, B, B)) * rng.uniform(0.1, 10, (B, B, B))).astype(dtype)
+    base = O.encode_block(kind, 0.5, blk, stage2=False)
+    n0, c0, m0, v0 = _raw_payload(base, B, dtype)
+    assert n0 > 0
+    ut = np.uint32 if np.dtype(dtype).itemsize == 4 else np.uint64
+    for zbits in (4, 8):
+        ch = O.encode_block(kind, 0.5, blk, stage2=False, zbits=zbits)
+        n, c, m, v = _raw_payload(ch, B, dtype)
+        assert n == n0
+        np.testing.assert_array_equal(m, m0)
+        np.testing.assert_array_equal(c.view(ut), c0.view(ut))
+        want = v0.view(ut) & ~ut((1 << zbits) - 1)
+        np.testing.assert_array_equal(v.view(ut), want)
+        assert np.any(v.view(ut) != v0.view(ut))
+        # the same block through stage 2 decodes to the same values
+        ch2 = O.encode_block(kind, 0.5, blk, stage2=True, zbits=zbits)
+        np.testing.assert_array_equal(O.decode_block(kind, B, dtype, ch2, True).view(ut),
+                                      O.decode_block(kind, B, dtype, ch, False).view(ut))
+
+
+def test_bit_zeroing_flags_and_header():
+    f = np.random.default_rng(3).standard_normal((32, 32, 64)).astype(np.float32)
+    for zbits, flag in ((0, 0), (4, O.FLAG_ZERO4), (8, O.FLAG_ZERO8)):
+        s = O.compress(f, 16, O.W3AI, 1e-2, zbits=zbits)
+        assert s[27] == flag and O.read_header(s)["flags"] == flag
+    p = O.params(f.shape, 16, f.dtype, O.W3AI, 1e-2)
+    cap = C.c_size_t()
+    for flags, bound in ((O.FLAG_ZERO4 | O.FLAG_ZERO8, O.BOUND_PAPER), (O.FLAG_ZERO8, O.BOUND_STRICT)):
+        p.flags, p.bound_mode = flags, bound
+        assert O.lib().czo_compress_bound(C.byref(p), C.byref(cap)) == O.ERR_ARG
+
+
+def test_z8_shrinks_the_stage2_stream_of_a_smooth_field():
+    """Zeroing the low byte of every kept FP32 detail empties one shuffled
+    byte plane of the values, which the zero-run coder removes; the decoded
+    field moves by at most 2^8 ulp per kept coefficient."""
+    from paper_1903_07761_gb300 import inputs
+    f = inputs.config0(seed=0)
+    s0 = O.compress(f, 32, O.W3AI, 1e-3)
+    s8 = O.compress(f, 32, O.W3AI, 1e-3, zbits=8)
+    assert len(s8) < len(s0)
+    assert abs(O.psnr(f, O.decompress(s8)) - O.psnr(f, O.decompress(s0))) < 0.1
