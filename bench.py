@@ -364,47 +364,49 @@ def run_gpu(args, rank, world, local_rank):
                "fields_in_flight": depth, "steps": reps}
         del lanes
 
-    # other kinds (context: the headline is per kind)
-    per_kind = {}
-    if not args.headline_only:
-        for kname, kk in cz.KINDS.items():
-            pk = cz.params_for(tuple(field.shape), False, B, kk, args.eps, cz.EPS_REL, True, -1.0)
-            ln_ref = {}
+    # other kinds (context: the headline is per kind), and bit zeroing
+    # Z4 / Z8 of the kept details for the headline kind (Sec. 3, Exp. 2)
+    def measure(pk):
+        r = cz.cz_compress(pk, field.data_ptr(), out.data_ptr(), cap, nb.data_ptr(),
+                           ws.data_ptr(), ws.numel(), s)
+        assert r == cz.OK
+        ln = int(nb.item())
+        hb = cz.C.create_string_buffer(out[:cz.HEADER_BYTES].cpu().numpy().tobytes(), 128)
 
-            def kstep():
-                r = cz.cz_compress(pk, field.data_ptr(), out.data_ptr(), cap, nb.data_ptr(),
-                                   ws.data_ptr(), ws.numel(), s)
-                assert r == cz.OK
-                ln_ref["n"] = int(nb.item())
-
-            kstep()
-            hb = cz.C.create_string_buffer(out[:cz.HEADER_BYTES].cpu().numpy().tobytes(), 128)
-            ln = ln_ref["n"]
-
-            def kdec():
-                r = cz.lib().cz_decompress(out.data_ptr(), ln, hb, rec.data_ptr(), nbytes_field,
-                                           ws.data_ptr(), ws.numel(), s)
-                assert r == cz.OK
-            reps = 5
-            ce = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-                   torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-            for a_, b_, c_ in ce:
-                a_.record(stream)
-                cz.cz_compress(pk, field.data_ptr(), out.data_ptr(), cap, nb.data_ptr(),
-                               ws.data_ptr(), ws.numel(), s)
-                b_.record(stream)
-                kdec()
-                c_.record(stream)
-            torch.cuda.synchronize()
-            cm = statistics.median(a_.elapsed_time(b_) for a_, b_, _ in ce)
-            dm = statistics.median(b_.elapsed_time(c_) for _, b_, c_ in ce)
-            d = rec.double() - field.double()
-            mse_k = float((d * d).mean().item())
-            del d
-            per_kind[kname] = {
-                "compress_gbs": nbytes_field / cm / 1e6, "decompress_gbs": nbytes_field / dm / 1e6,
+        def kdec():
+            r = cz.lib().cz_decompress(out.data_ptr(), ln, hb, rec.data_ptr(), nbytes_field,
+                                       ws.data_ptr(), ws.numel(), s)
+            assert r == cz.OK
+        reps = 5
+        ce = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a_, b_, c_ in ce:
+            a_.record(stream)
+            cz.cz_compress(pk, field.data_ptr(), out.data_ptr(), cap, nb.data_ptr(),
+                           ws.data_ptr(), ws.numel(), s)
+            b_.record(stream)
+            kdec()
+            c_.record(stream)
+        torch.cuda.synchronize()
+        cm = statistics.median(a_.elapsed_time(b_) for a_, b_, _ in ce)
+        dm = statistics.median(b_.elapsed_time(c_) for _, b_, c_ in ce)
+        d = rec.double() - field.double()
+        mse_k = float((d * d).mean().item())
+        del d
+        return {"compress_gbs": nbytes_field / cm / 1e6, "decompress_gbs": nbytes_field / dm / 1e6,
                 "cr": nbytes_field / ln,
                 "psnr_db": 20 * math.log10((fmax - fmin) / (2 * math.sqrt(mse_k))) if mse_k > 0 else None}
+
+    per_kind = {}
+    bit_zeroing = None
+    if not args.headline_only:
+        for kname, kk in cz.KINDS.items():
+            per_kind[kname] = measure(cz.params_for(tuple(field.shape), False, B, kk, args.eps, cz.EPS_REL, True,
+                                                    -1.0))
+        bit_zeroing = {"kind": args.kind, "eps": args.eps}
+        for z in (0, 4, 8):
+            bit_zeroing[f"z{z}"] = measure(cz.params_for(tuple(field.shape), False, B, kind, args.eps, cz.EPS_REL,
+                                                         True, -1.0, zero_bits=z))
 
     # batched fields and the served request stream (rank 0, one GPU)
     batched_res = served_res = fp64_res = None
@@ -469,6 +471,7 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "per_kind": per_kind,
+        "bit_zeroing": bit_zeroing,
         "batched": batched_res,
         "served": served_res,
         "fp64": fp64_res,

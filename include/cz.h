@@ -65,6 +65,13 @@ enum { CZ_BOUND_PAPER = 0, CZ_BOUND_STRICT = 1 };
  * is recorded in the stream header; decompression uses the build the
  * stream was made with. */
 enum { CZ_FLAG_FAST = 1 };
+/* flags: CZ_FLAG_ZERO4 / CZ_FLAG_ZERO8 zero the 4 / 8 least significant
+ * bits of every kept detail coefficient before the lossless substage (bit
+ * zeroing "Z4" / "Z8", Sec. 3 Exp. 2): more zero bytes for stage 2 at a
+ * small loss of precision; the mask and the coarse values are untouched.
+ * At most one of the two; not with CZ_BOUND_STRICT (whose bound does not
+ * cover the zeroing error).  Recorded in the stream header. */
+enum { CZ_FLAG_ZERO4 = 2, CZ_FLAG_ZERO8 = 4 };
 
 enum {
   CZ_OK = 0,
@@ -86,7 +93,7 @@ typedef struct cz_params {
   int32_t eps_mode;   /* CZ_EPS_REL (default) or CZ_EPS_ABS                 */
   int32_t stage2;     /* 1: byte shuffle + zero-RLE each chunk; 0: raw      */
   int32_t bound_mode; /* CZ_BOUND_PAPER (default) or CZ_BOUND_STRICT        */
-  int32_t flags;      /* 0 or CZ_FLAG_FAST                                  */
+  int32_t flags;      /* CZ_FLAG_FAST, CZ_FLAG_ZERO4 / CZ_FLAG_ZERO8, or 0   */
   double eps;         /* tolerance, >= 0                                    */
   double range;       /* >= 0: max - min supplied by the caller (skips the
                          min/max pass); < 0: computed on the device        */

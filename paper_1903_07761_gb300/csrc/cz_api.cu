@@ -39,7 +39,10 @@ int check(const cz_params *p, Shape *sh)
   if (p->eps_mode != CZ_EPS_REL && p->eps_mode != CZ_EPS_ABS) return CZ_ERR_ARG;
   if (p->stage2 != 0 && p->stage2 != 1) return CZ_ERR_ARG;
   if (p->bound_mode != CZ_BOUND_PAPER && p->bound_mode != CZ_BOUND_STRICT) return CZ_ERR_ARG;
-  if (p->flags & ~CZ_FLAG_FAST) return CZ_ERR_ARG;
+  if (p->flags & ~(CZ_FLAG_FAST | CZ_FLAG_ZERO4 | CZ_FLAG_ZERO8)) return CZ_ERR_ARG;
+  const int zf = p->flags & (CZ_FLAG_ZERO4 | CZ_FLAG_ZERO8);
+  if (zf == (CZ_FLAG_ZERO4 | CZ_FLAG_ZERO8)) return CZ_ERR_ARG;  // one zeroing width at most
+  if (zf && p->bound_mode == CZ_BOUND_STRICT) return CZ_ERR_ARG;  // the strict bound excludes zeroing
   if (!(p->eps >= 0) || std::isinf(p->eps)) return CZ_ERR_ARG;
   if (std::isnan(p->range)) return CZ_ERR_ARG;
   if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0) return CZ_ERR_ARG;
@@ -231,6 +234,12 @@ struct WsLayout {
 };
 
 size_t big_bytes(long long nblocks) { return (4ull * nblocks + 255) / 256 * 256; }
+
+// bit zeroing width of the kept details (0, 4 or 8)
+int zero_bits(const cz_params &p)
+{
+  return (p.flags & CZ_FLAG_ZERO8) ? 8 : (p.flags & CZ_FLAG_ZERO4) ? 4 : 0;
+}
 
 WsLayout ws_layout(const cz_params *p, const Shape &sh)
 {
@@ -512,6 +521,7 @@ int compress_batch_impl(int n, const cz_params *p, const void *const *d_fields, 
     a.nf = nf;
     a.stage2 = p0.stage2;
     a.kind = p0.kind;
+    a.zbits = zero_bits(p0);
     a.dtype = p0.dtype;
     S2Args sa{};
     sa.staging = a.staging;
@@ -621,6 +631,7 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
   a.eps_mode = p->eps_mode;
   a.stage2 = p->stage2;
   a.kind = p->kind;
+  a.zbits = zero_bits(*p);
   a.dtype = p->dtype;
   S2Args sa{};
   sa.staging = a.staging;
@@ -863,7 +874,7 @@ int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used)
   q.stage2 = h[23];
   q.eps_mode = h[24];
   q.bound_mode = h[26];
-  q.flags = h[27] & CZ_FLAG_FAST;
+  q.flags = h[27] & (CZ_FLAG_FAST | CZ_FLAG_ZERO4 | CZ_FLAG_ZERO8);
   std::memcpy(&q.eps, h + 32, 8);
   std::memcpy(&q.range, h + 64, 8);
   if (std::isnan(q.range)) return CZ_ERR_CORRUPT;

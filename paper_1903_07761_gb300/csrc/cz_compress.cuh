@@ -222,8 +222,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
             if (b2) {
               const unsigned wd = get_rowi<B>(MASKU, rpad<B>(z, 2 * k + r));
               const unsigned base = ROWOFF[rpad<B>(z, 2 * k + r)];
-              if (b2 & 1u) VALS[base + __popc(wd & lowE)] = v[r][zl].x;
-              if (b2 & 2u) VALS[base + __popc(wd & lowO)] = v[r][zl].y;
+              if (b2 & 1u) VALS[base + __popc(wd & lowE)] = zero_low(v[r][zl].x, a.zbits);
+              if (b2 & 2u) VALS[base + __popc(wd & lowO)] = zero_low(v[r][zl].y, a.zbits);
             }
           }
         }

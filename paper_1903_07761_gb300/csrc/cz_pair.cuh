@@ -97,6 +97,7 @@ struct FwdArgs {
   double eps, range, cnorm;
   int nx, ny, nz, nbx, nby, nbz, nblocks, nf;
   int eps_mode, stage2, kind, dtype;
+  int zbits;  // bit zeroing: 0, 4 or 8 least significant bits of each kept detail cleared
 };
 
 struct InvArgs {
@@ -184,6 +185,16 @@ __device__ __forceinline__ double2 sub2(double2 a, double2 b)
 // threshold keeps the value)
 __device__ __forceinline__ bool keep(float d, float t) { return !(fabsf(d) < t); }
 __device__ __forceinline__ bool keep(double d, double t) { return !(fabs(d) < t); }
+
+// the value with the zbits least significant bits of its pattern cleared
+__device__ __forceinline__ float zero_low(float v, int zbits)
+{
+  return __uint_as_float(__float_as_uint(v) & ~((1u << zbits) - 1u));
+}
+__device__ __forceinline__ double zero_low(double v, int zbits)
+{
+  return __longlong_as_double(__double_as_longlong(v) & ~((1ll << zbits) - 1ll));
+}
 
 // Significance bits of a thread's half columns: bit 2 zl + p for component
 // p of v[zl].  For FP32 the sign of |d| - t (explicitly rounded, subnormals

@@ -127,11 +127,19 @@ def test_bound_mode_and_flags_are_checked(cz):
     with pytest.raises(cz.CzError):
         cz.cz_compress_bound(p)
     p = cz.params_for((32, 32, 32), False, 32, "w4", 1e-3, cz.EPS_REL, True, 1.0)
-    p.flags = 2  # unknown flag
+    p.flags = 8  # unknown flag
     with pytest.raises(cz.CzError):
         cz.cz_compress_bound(p)
-    p.flags = cz.FLAG_FAST
-    assert cz.cz_compress_bound(p) > 0
+    p.flags = cz.FLAG_ZERO4 | cz.FLAG_ZERO8  # one zeroing width at most
+    with pytest.raises(cz.CzError):
+        cz.cz_compress_bound(p)
+    for f in (cz.FLAG_FAST, cz.FLAG_ZERO4, cz.FLAG_ZERO8, cz.FLAG_FAST | cz.FLAG_ZERO8):
+        p.flags = f
+        assert cz.cz_compress_bound(p) > 0
+    p = cz.params_for((32, 32, 32), False, 32, "w4", 1e-3, cz.EPS_REL, True, 1.0,
+                      bound_mode=cz.BOUND_STRICT, zero_bits=8)  # the strict bound excludes zeroing
+    with pytest.raises(cz.CzError):
+        cz.cz_compress_bound(p)
 
 
 def test_struct_layouts_match_the_header(cz, tmp_path):

@@ -98,3 +98,27 @@ def test_batch_tuned_and_graph_replay_give_the_same_streams():
         torch.cuda.synchronize()
         got = [bytes(o[:int(n)].cpu().numpy()) for o, n in zip(outs, nbytes.cpu().tolist())]
         assert got == ref
+
+
+def test_batch_with_bit_zeroing_groups_and_matches_the_oracle():
+    """Fields with and without bit zeroing in one batch: each stream equals
+    the oracle's with the same zeroing width."""
+    import torch
+    from paper_1903_07761_gb300 import cz
+    items = _fields(11, n=4)
+    zb = [8, 0, 4, 8]
+    tens = [torch.from_numpy(f).cuda() for f, _, _ in items]
+    params, caps, outs = [], [], []
+    for (f, B, e), t, z in zip(items, tens, zb):
+        p = cz.params_for(tuple(t.shape), t.dtype == torch.float64, B, "w3ai", e, zero_bits=z)
+        params.append(p)
+        caps.append(cz.cz_compress_bound(p))
+        outs.append(torch.zeros(caps[-1], dtype=torch.uint8, device="cuda"))
+    nbytes = torch.zeros(len(items), dtype=torch.int64, device="cuda")
+    ws = torch.empty(cz.cz_batch_workspace_size(params), dtype=torch.uint8, device="cuda")
+    b = cz.BatchArgs(params, [t.data_ptr() for t in tens], [o.data_ptr() for o in outs], caps)
+    s = torch.cuda.current_stream().cuda_stream
+    assert cz.cz_compress_batch(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(), s) == cz.OK
+    torch.cuda.synchronize()
+    for (f, B, e), o, n, z in zip(items, outs, nbytes.cpu().tolist(), zb):
+        assert bytes(o[:int(n)].cpu().numpy()) == O.compress(f, B, O.W3AI, e, zbits=z)

@@ -62,6 +62,20 @@ def test_stream_and_decode_bit_identical(dtype, block, shape, kind, stage2):
         np.testing.assert_array_equal(rec.view(np.uint8), want.view(np.uint8))
 
 
+@pytest.mark.parametrize("zbits", [4, 8])
+@pytest.mark.parametrize("stage2", [True, False])
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("dtype,block,shape", [CASES[0], CASES[3]])
+def test_bit_zeroing_streams_bit_identical(dtype, block, shape, kind, stage2, zbits):
+    """Bit zeroing Z4 / Z8 (Sec. 3, Exp. 2): the kept details' low bits are
+    cleared on the GPU exactly as in the oracle."""
+    f = smooth_field(shape, dtype, seed=31 + kind)
+    ref = O.compress(f, block, kind, 1e-3, stage2=stage2, zbits=zbits)
+    got = gpu_compress(f, block, kind, 1e-3, stage2=stage2, zbits=zbits)
+    assert got == ref, describe_diff(got, ref)
+    np.testing.assert_array_equal(gpu_decompress(got).view(np.uint8), O.decompress(ref).view(np.uint8))
+
+
 @pytest.mark.parametrize("stage2", [True, False])
 @pytest.mark.parametrize("dtype,block,shape", [
     (np.float32, 32, (64, 160, 544)),  # 17 x 5 x 2 = 170 blocks: more than one per stage CTA
