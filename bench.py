@@ -366,16 +366,20 @@ def run_gpu(args, rank, world, local_rank):
 
     # other kinds (context: the headline is per kind), and bit zeroing
     # Z4 / Z8 of the kept details for the headline kind (Sec. 3, Exp. 2)
-    def measure(pk):
+    def measure(pk, ws_=None):
+        ws_ = ws if ws_ is None else ws_
         r = cz.cz_compress(pk, field.data_ptr(), out.data_ptr(), cap, nb.data_ptr(),
-                           ws.data_ptr(), ws.numel(), s)
+                           ws_.data_ptr(), ws_.numel(), s)
         assert r == cz.OK
+        st_ = cz.cz_status(ws_.data_ptr(), s)
+        if st_ != cz.OK:
+            raise cz.CzError(st_, "compress (device)")
         ln = int(nb.item())
         hb = cz.C.create_string_buffer(out[:cz.HEADER_BYTES].cpu().numpy().tobytes(), 128)
 
         def kdec():
             r = cz.lib().cz_decompress(out.data_ptr(), ln, hb, rec.data_ptr(), nbytes_field,
-                                       ws.data_ptr(), ws.numel(), s)
+                                       ws_.data_ptr(), ws_.numel(), s)
             assert r == cz.OK
         reps = 5
         ce = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
@@ -383,7 +387,7 @@ def run_gpu(args, rank, world, local_rank):
         for a_, b_, c_ in ce:
             a_.record(stream)
             cz.cz_compress(pk, field.data_ptr(), out.data_ptr(), cap, nb.data_ptr(),
-                           ws.data_ptr(), ws.numel(), s)
+                           ws_.data_ptr(), ws_.numel(), s)
             b_.record(stream)
             kdec()
             c_.record(stream)
@@ -398,7 +402,7 @@ def run_gpu(args, rank, world, local_rank):
                 "psnr_db": 20 * math.log10((fmax - fmin) / (2 * math.sqrt(mse_k))) if mse_k > 0 else None}
 
     per_kind = {}
-    bit_zeroing = None
+    bit_zeroing = block_sizes = None
     if not args.headline_only:
         for kname, kk in cz.KINDS.items():
             per_kind[kname] = measure(cz.params_for(tuple(field.shape), False, B, kk, args.eps, cz.EPS_REL, True,
@@ -407,6 +411,15 @@ def run_gpu(args, rank, world, local_rank):
         for z in (0, 4, 8):
             bit_zeroing[f"z{z}"] = measure(cz.params_for(tuple(field.shape), False, B, kind, args.eps, cz.EPS_REL,
                                                          True, -1.0, zero_bits=z))
+        # block-size study (Sec. 3): 8^3 / 16^3 / 32^3 blocks of the same field
+        block_sizes = {"kind": args.kind, "eps": args.eps}
+        for bb in (8, 16, 32):
+            pb = cz.params_for(tuple(field.shape), False, bb, kind, args.eps, cz.EPS_REL, True, -1.0)
+            need = max(cz.cz_workspace_size(pb), ws.numel())
+            ws_b = ws if need == ws.numel() else torch.empty(need, dtype=torch.uint8, device=dev)
+            block_sizes[f"b{bb}"] = measure(pb, ws_b)
+            del ws_b
+        torch.cuda.empty_cache()
 
     # batched fields and the served request stream (rank 0, one GPU)
     batched_res = served_res = fp64_res = None
@@ -472,6 +485,7 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clk,
         "per_kind": per_kind,
         "bit_zeroing": bit_zeroing,
+        "block_sizes": block_sizes,
         "batched": batched_res,
         "served": served_res,
         "fp64": fp64_res,

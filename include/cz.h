@@ -134,6 +134,23 @@ int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header,
                   void *d_field, size_t field_cap, void *d_ws, size_t ws_bytes,
                   void *stream);
 
+/* Random access (the paper's per-block decompression, Sec. 2.3: blocks are
+ * compressed independently): decode the blocks d_ids[0..n) of the stream
+ * d_in into n consecutive B^3 tiles at d_tiles (tile i holds block d_ids[i],
+ * x fastest, then y, then z; tiles_cap >= n * B^3 * element bytes).  d_ids
+ * is a device array of n int32 block indices in the stream's x-fastest
+ * block order; they may repeat.  The workspace needs room for n blocks
+ * (cz_decompress_blocks_workspace_size; cz_workspace_size of the stream's
+ * parameters suffices for n <= nblocks).  An index outside the stream sets the status word to
+ * CZ_ERR_ARG and a bad chunk CZ_ERR_CORRUPT; such tiles are zeros.  n = 0
+ * is a no-op.  Header handling as for cz_decompress. */
+int cz_decompress_blocks(const void *d_in, size_t in_bytes, const void *h_header, const int32_t *d_ids, int n,
+                         void *d_tiles, size_t tiles_cap, void *d_ws, size_t ws_bytes, void *stream);
+
+/* Workspace bytes cz_decompress_blocks needs to decode n blocks of a stream
+ * made with parameters p.  Returns CZ_OK or CZ_ERR_ARG. */
+int cz_decompress_blocks_workspace_size(const cz_params *p, int n, size_t *bytes);
+
 /* Size of the workspace that cz_compress_noalloc uses: 64 MiB. */
 #define CZ_NOALLOC_WS_BYTES (64u << 20)
 

@@ -887,11 +887,17 @@ int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used)
   return CZ_OK;
 }
 
-int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header, void *d_field,
-                  size_t field_cap, void *d_ws, size_t ws_bytes, void *stream)
+namespace {
+
+// Decompress the whole field (ids == nullptr) or the n blocks ids[0..n) into
+// n consecutive B^3 tiles.  The decoded blocks are numbered 0..n-1 in the
+// workspace; with tiles the block grid is 1 x 1 x n, so block i lands at
+// z = i B of the B x B x nB tile array.
+int decompress_impl(const void *d_in, size_t in_bytes, const void *h_header, const int32_t *ids, int n,
+                    void *d_out, size_t out_cap, void *d_ws, size_t ws_bytes, void *stream)
 {
-  if (!d_in || !d_field || !d_ws) return CZ_ERR_ARG;
-  if (((uintptr_t)d_in % 16) || ((uintptr_t)d_field % 16) || ((uintptr_t)d_ws % 16)) return CZ_ERR_ARG;
+  if (!d_in || !d_out || !d_ws) return CZ_ERR_ARG;
+  if (((uintptr_t)d_in % 16) || ((uintptr_t)d_out % 16) || ((uintptr_t)d_ws % 16)) return CZ_ERR_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   unsigned char hb[HEADER_BYTES];
   if (in_bytes < (size_t)HEADER_BYTES) return CZ_ERR_CORRUPT;
@@ -908,50 +914,95 @@ int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header, void 
   check(&p, &sh);
   const unsigned long long total = rd64(hb + 80), data_bytes = rd64(hb + 72);
   if (total > in_bytes || sh.data0 + data_bytes != total) return CZ_ERR_CORRUPT;
-  if ((size_t)p.nx * p.ny * p.nz * sh.es > field_cap) return CZ_ERR_CAPACITY;
+  const int nchunks = sh.nblocks;
+  // the decoded blocks: the whole grid, or n tiles stacked along z
+  cz_params q = p;
+  Shape dsh = sh;
+  if (ids) {
+    if (n < 0) return CZ_ERR_ARG;
+    if (n == 0) return CZ_OK;
+    if ((long long)n * p.block > INT32_MAX) return CZ_ERR_ARG;
+    q.nx = q.ny = p.block;
+    q.nz = n * p.block;
+    dsh.nbx = dsh.nby = 1;
+    dsh.nbz = n;
+    dsh.nblocks = n;
+  }
+  if ((size_t)q.nx * q.ny * q.nz * sh.es > out_cap) return CZ_ERR_CAPACITY;
   const Lanes L = lanes_for(p);
   // workspace: header | block table (nnz, bad flag) | list of the large
-  // chunks | one staging slot per block for the decoded stage-2 payloads
+  // chunks | one staging slot per decoded block for the stage-2 payloads
   // (within cz_workspace_size)
   const size_t slot = (size_t)L.slot_bytes();
-  const size_t need =
-      p.stage2 ? WS_HDR + table_bytes(sh) + big_bytes(sh.nblocks) + (size_t)sh.nblocks * slot : (size_t)WS_HDR;
+  const size_t need = p.stage2 ? WS_HDR + table_bytes(dsh) + big_bytes(dsh.nblocks) + (size_t)dsh.nblocks * slot
+                               : (size_t)WS_HDR;
   if (ws_bytes < need) return CZ_ERR_CAPACITY;
   if (cudaMemsetAsync(d_ws, 0, WS_HDR, s) != cudaSuccess) return CZ_ERR_CUDA;
   unsigned char *wsb = reinterpret_cast<unsigned char *>(d_ws);
   InvArgs a{};
   a.in = reinterpret_cast<const unsigned char *>(d_in);
-  a.field = d_field;
+  a.field = d_out;
   a.ws = d_ws;
   a.in_bytes = total;
   a.data0 = sh.data0;
-  a.nx = p.nx;
-  a.ny = p.ny;
-  a.nz = p.nz;
-  a.nbx = sh.nbx;
-  a.nby = sh.nby;
-  a.nbz = sh.nbz;
-  a.nblocks = sh.nblocks;
+  a.nx = q.nx;
+  a.ny = q.ny;
+  a.nz = q.nz;
+  a.nbx = dsh.nbx;
+  a.nby = dsh.nby;
+  a.nbz = dsh.nbz;
+  a.nblocks = dsh.nblocks;
   a.stage2 = p.stage2;
+  a.ids = ids;
+  a.nchunks = nchunks;
   a.table = reinterpret_cast<const unsigned long long *>(wsb + WS_HDR);
-  a.staging = wsb + WS_HDR + table_bytes(sh) + big_bytes(sh.nblocks);
+  a.staging = wsb + WS_HDR + table_bytes(dsh) + big_bytes(dsh.nblocks);
   a.slot = slot;
   UnArgs ua{};
   ua.in = a.in;
-  ua.staging = wsb + WS_HDR + table_bytes(sh) + big_bytes(sh.nblocks);
+  ua.staging = wsb + WS_HDR + table_bytes(dsh) + big_bytes(dsh.nblocks);
   ua.ws = d_ws;
-  ua.biglist = reinterpret_cast<int *>(wsb + WS_HDR + table_bytes(sh));
+  ua.biglist = reinterpret_cast<int *>(wsb + WS_HDR + table_bytes(dsh));
   ua.table = reinterpret_cast<unsigned long long *>(wsb + WS_HDR);
+  ua.ids = ids;
+  ua.nchunks = nchunks;
   ua.in_bytes = total;
   ua.data0 = sh.data0;
   ua.slot = slot;
-  ua.nblocks = sh.nblocks;
+  ua.nblocks = dsh.nblocks;
   CUtensorMap om;
-  if (!make_tile_map(&om, &p, d_field)) return CZ_ERR_CUDA;
-  return L.decompress(p.kind, &om, &a, &ua, grid_for(&p, sh, 1), grid_for(&p, sh, 4), grid_for(&p, sh, 5), s) ==
+  if (!make_tile_map(&om, &q, d_out)) return CZ_ERR_CUDA;
+  return L.decompress(p.kind, &om, &a, &ua, grid_for(&p, dsh, 1), grid_for(&p, dsh, 4), grid_for(&p, dsh, 5), s) ==
                  cudaSuccess
              ? CZ_OK
              : CZ_ERR_CUDA;
+}
+
+}  // namespace
+
+int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header, void *d_field,
+                  size_t field_cap, void *d_ws, size_t ws_bytes, void *stream)
+{
+  return decompress_impl(d_in, in_bytes, h_header, nullptr, 0, d_field, field_cap, d_ws, ws_bytes, stream);
+}
+
+int cz_decompress_blocks_workspace_size(const cz_params *p, int n, size_t *bytes)
+{
+  Shape sh;
+  const int r = check(p, &sh);
+  if (r != CZ_OK || !bytes || n < 0) return r ? r : CZ_ERR_ARG;
+  sh.nblocks = n;
+  *bytes = p->stage2 ? WS_HDR + table_bytes(sh) + big_bytes(n) + (size_t)n * (size_t)lanes_for(*p).slot_bytes()
+                     : (size_t)WS_HDR;
+  return CZ_OK;
+}
+
+int cz_decompress_blocks(const void *d_in, size_t in_bytes, const void *h_header, const int32_t *d_ids, int n,
+                         void *d_tiles, size_t tiles_cap, void *d_ws, size_t ws_bytes, void *stream)
+{
+  if (!d_ids && n > 0) return CZ_ERR_ARG;
+  if (!d_ids) return n == 0 ? CZ_OK : CZ_ERR_ARG;
+  return decompress_impl(d_in, in_bytes, h_header, d_ids, n, d_tiles, tiles_cap, d_ws, ws_bytes, stream);
 }
 
 int cz_status(const void *d_ws, void *stream)

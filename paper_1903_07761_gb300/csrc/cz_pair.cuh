@@ -34,6 +34,7 @@ namespace czp {
 using namespace czd;
 
 // numeric values of the public status codes
+constexpr unsigned ST_ARG = (unsigned)-1;
 constexpr unsigned ST_CAPACITY = (unsigned)-2;
 constexpr unsigned ST_CORRUPT = (unsigned)-3;
 constexpr unsigned ST_TIMEOUT = (unsigned)-4;
@@ -106,6 +107,8 @@ struct InvArgs {
   void *ws;
   const unsigned char *staging;       // stage 2: decoded payloads, one slot per block
   const unsigned long long *table;    // stage 2: per block nnz, bad flag
+  const int *ids;                     // random access: chunk of each decoded block (else the identity)
+  int nchunks;                        // blocks in the stream
   unsigned long long in_bytes, data0, slot;
   int nx, ny, nz, nbx, nby, nbz, nblocks;
   int stage2;
@@ -118,6 +121,8 @@ struct UnArgs {
   unsigned long long *table;  // per block: nnz, bad flag
   void *ws;                   // header: count of large chunks (nbig)
   int *biglist;               // ids of the chunks with large payloads
+  const int *ids;             // random access: chunk of each decoded block (else the identity)
+  int nchunks;                // blocks in the stream
   unsigned long long in_bytes, data0, slot;
   int nblocks;
 };
@@ -1385,14 +1390,20 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_unstage(const UnArgs a)
   // large launch then visits alone
   const int count = BIG ? (int)*(volatile const unsigned *)&wsh->nbig : a.nblocks;
   for (int it = blockIdx.x; it < count; it += gridDim.x) {
-    const int bid = BIG ? a.biglist[it] : it;
+    const int bid = BIG ? a.biglist[it] : it;  // the decoded block (its staging slot and table entry)
     if (tid == 0) {
       unsigned bad = 0;
       const unsigned long long *tab = reinterpret_cast<const unsigned long long *>(a.in + HEADER_BYTES);
-      const unsigned long long o0 = tab[bid], o1 = tab[bid + 1];
+      int c = a.ids ? a.ids[bid] : bid;  // its chunk in the stream
+      if (c < 0 || c >= a.nchunks) {
+        atomicCAS(&wsh->status, 0u, ST_ARG);
+        c = 0;
+        bad = 1;
+      }
+      const unsigned long long o0 = tab[c], o1 = tab[c + 1];
       const unsigned long long avail = a.in_bytes - a.data0;
       unsigned nnz = 0, ntok = 0;
-      if (o0 > o1 || o1 > avail || o1 - o0 < 8 || (o0 & 3) || ((o1 - o0) & 3)) {
+      if (bad || o0 > o1 || o1 > avail || o1 - o0 < 8 || (o0 & 3) || ((o1 - o0) & 3)) {
         bad = 1;
       } else {
         const unsigned *c32 = reinterpret_cast<const unsigned *>(a.in + a.data0 + o0);
@@ -1520,10 +1531,16 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
       nnz = bad ? 0u : (unsigned)t0;
     } else {
       const unsigned long long *tab = reinterpret_cast<const unsigned long long *>(a.in + HEADER_BYTES);
-      o0 = tab[b];
-      const unsigned long long o1 = tab[b + 1];
+      int c = a.ids ? a.ids[b] : b;  // the block's chunk in the stream
+      if (c < 0 || c >= a.nchunks) {
+        atomicCAS(&ws->status, 0u, ST_ARG);
+        c = 0;
+        bad = 1;
+      }
+      o0 = tab[c];
+      const unsigned long long o1 = tab[c + 1];
       const unsigned long long avail = a.in_bytes - a.data0;
-      if (o0 > o1 || o1 > avail || o1 - o0 < 8 || (o0 & 3) || ((o1 - o0) & 3)) {
+      if (bad || o0 > o1 || o1 > avail || o1 - o0 < 8 || (o0 & 3) || ((o1 - o0) & 3)) {
         bad = 1;
       } else {
         const unsigned *c32 = reinterpret_cast<const unsigned *>(a.in + a.data0 + o0);

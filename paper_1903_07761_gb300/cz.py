@@ -73,6 +73,8 @@ def lib():
             L.cz_workspace_size.argtypes = [PP, C.POINTER(C.c_size_t)]
             L.cz_compress.argtypes = [PP, P, P, C.c_size_t, P, P, C.c_size_t, P]
             L.cz_decompress.argtypes = [P, C.c_size_t, P, P, C.c_size_t, P, C.c_size_t, P]
+            L.cz_decompress_blocks.argtypes = [P, C.c_size_t, P, P, C.c_int, P, C.c_size_t, P, C.c_size_t, P]
+            L.cz_decompress_blocks_workspace_size.argtypes = [PP, C.c_int, C.POINTER(C.c_size_t)]
             L.cz_compress_noalloc.argtypes = [PP, P, P, C.c_size_t, P, P]
             L.cz_stream_concat.argtypes = [C.c_int, C.POINTER(P), C.POINTER(C.c_size_t), P, C.c_size_t,
                                            C.POINTER(C.c_size_t)]
@@ -93,7 +95,8 @@ def lib():
             L.cz_strerror.restype = C.c_char_p
             L.cz_forward_dense.argtypes = [PP, P, P, P]
             L.cz_inverse_dense.argtypes = [PP, P, P, P]
-            for f in (L.cz_compress_bound, L.cz_workspace_size, L.cz_compress, L.cz_decompress,
+            for f in (L.cz_compress_bound, L.cz_workspace_size, L.cz_compress, L.cz_decompress, L.cz_decompress_blocks,
+                      L.cz_decompress_blocks_workspace_size,
                       L.cz_compress_noalloc, L.cz_batch_workspace_size, L.cz_compress_batch,
                       L.cz_batch_tune, L.cz_stream_concat, L.cz_server_create, L.cz_server_submit, L.cz_server_poll,
                       L.cz_server_wait, L.cz_server_destroy, L.cz_read_header, L.cz_status, L.cz_forward_dense, L.cz_inverse_dense):
@@ -288,6 +291,42 @@ def decompress(stream_t, nbytes: int | None = None, header: bytes | None = None,
         st = cz_status(wsb.data_ptr(), s)
         if st != OK:
             raise CzError(st, "cz_decompress (device)")
+    return out
+
+
+def decompress_blocks(stream_t, ids, nbytes: int | None = None, header: bytes | None = None, out=None,
+                      ws: Workspace | None = None, stream=None, check: bool = True):
+    """Random access: decode the blocks ids (a CUDA int32 tensor of block
+    indices in x-fastest block order) into a new (or given) tensor of shape
+    [len(ids), B, B, B]."""
+    import torch
+    if header is None:
+        header = stream_t[:HEADER_BYTES].cpu().numpy().tobytes()
+    p, _ = cz_read_header(header)
+    assert ids.is_cuda and ids.dtype == torch.int32 and ids.is_contiguous()
+    k = ids.numel()
+    n = int(nbytes) if nbytes is not None else stream_t.numel()
+    dt = torch.float64 if p.dtype == F64 else torch.float32
+    B = p.block
+    if out is None:
+        out = torch.empty((k, B, B, B), dtype=dt, device=stream_t.device)
+    ws = ws or Workspace(stream_t.device)
+    need = C.c_size_t()
+    r = lib().cz_decompress_blocks_workspace_size(C.byref(p), k, C.byref(need))
+    if r != OK:
+        raise CzError(r, "cz_decompress_blocks_workspace_size")
+    wsb = ws.get(need.value)
+    s = _stream(stream)
+    hdr = C.create_string_buffer(bytes(header[:HEADER_BYTES]), HEADER_BYTES)
+    r = lib().cz_decompress_blocks(stream_t.data_ptr(), n, hdr, ids.data_ptr() if k else None, k,
+                                   out.data_ptr(), out.numel() * out.element_size(), wsb.data_ptr(), wsb.numel(),
+                                   s or None)
+    if r != OK:
+        raise CzError(r, "cz_decompress_blocks")
+    if check and k:
+        st = cz_status(wsb.data_ptr(), s)
+        if st != OK:
+            raise CzError(st, "cz_decompress_blocks (device)")
     return out
 
 
