@@ -147,10 +147,13 @@ struct V2T<double> {
 
 __device__ __forceinline__ float2 mk2(float s) { return make_float2(s, s); }
 __device__ __forceinline__ double2 mk2(double s) { return make_double2(s, s); }
-// Pair arithmetic lane by lane with explicitly rounded scalar ops.  (The
-// packed f32x2 multiply and add are each exact, but chained packed
-// multiply -> add sequences were measured to differ from separately rounded
-// scalar ops: they are not used on the exact path.)
+// Pair arithmetic.  FP32 sums and differences of pairs are one packed
+// add.rn.f32x2 / sub.rn.f32x2 each: both round each lane exactly like the
+// scalar operation (IEEE round to nearest, subnormals kept).  Products stay
+// two explicitly rounded scalar multiplies: chained packed multiply -> add
+// sequences were measured to differ from separately rounded scalar ops, so
+// no packed product feeds a packed sum on the exact path.  FP64 pairs are
+// scalar throughout.
 #ifdef CZ_FAST
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
@@ -159,9 +162,23 @@ __device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 sub2(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 #else
+__device__ __forceinline__ unsigned long long pk2(float2 a)
+{
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r)
+{
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
 __device__ __forceinline__ float2 add2(float2 a, float2 b)
 {
-  return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
 }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b)
 {
@@ -178,7 +195,9 @@ __device__ __forceinline__ double2 mul2(double2 a, double2 b)
 // subtraction lane by lane (exactly a - b, signed zeros included)
 __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 {
-  return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
 }
 __device__ __forceinline__ double2 sub2(double2 a, double2 b)
 {
@@ -834,7 +853,7 @@ __device__ __forceinline__ void y_inv(T2 (&v)[2][B / 2], T2 *pl, int a, int k, i
       for (int zl = 0; zl < ZH; ++zl) {
         const T2 a1 = plane_at<B>(pl, z0 + zl, k - 1, a), a2 = plane_at<B>(pl, z0 + zl, k + 1, a);
         const T2 f0 = add2(ai_predip<T2, T>(v[0][zl], a1, a2), v[1][zl]);
-        v[1][zl] = sub2(mul2(mk2((T)2), v[0][zl]), f0);
+        v[1][zl] = sub2(add2(v[0][zl], v[0][zl]), f0);
         v[0][zl] = f0;
       }
     } else {
@@ -842,7 +861,7 @@ __device__ __forceinline__ void y_inv(T2 (&v)[2][B / 2], T2 *pl, int a, int k, i
       for (int zl = 0; zl < ZH; ++zl) {
         const T2 a1 = plane_at<B>(pl, z0 + zl, s.k1, a), a2 = plane_at<B>(pl, z0 + zl, s.k2, a);
         const T2 f0 = add2(ai_predp<T2>(v[0][zl], a1, a2, s.aw[0], s.aw[1], s.aw[2], s.bnd), v[1][zl]);
-        v[1][zl] = sub2(mul2(mk2((T)2), v[0][zl]), f0);
+        v[1][zl] = sub2(add2(v[0][zl], v[0][zl]), f0);
         v[0][zl] = f0;
       }
     }
@@ -1065,7 +1084,7 @@ __device__ __forceinline__ void zi_b(T2 (&v)[2][B / 2], T2 *hx, int k, int a)
       for (int jl = 0; jl < MH; ++jl) {
         const AiRow rw = ai_row(lo + jl, m);
         e[jl] = add2(ai_predc<T2, T>(rw, v[r][2 * jl], src(rw.s1), src(rw.s2)), v[r][2 * jl + 1]);
-        o[jl] = sub2(mul2(mk2((T)2), v[r][2 * jl]), e[jl]);
+        o[jl] = sub2(add2(v[r][2 * jl], v[r][2 * jl]), e[jl]);
       }
 #pragma unroll
       for (int jl = 0; jl < MH; ++jl) {

@@ -181,6 +181,33 @@ def served(rates=(1000.0, 5000.0), n: int = 400, budget_gb: float = 40.0, stream
                          torch.zeros(1, dtype=torch.int64, device="cuda"))
         return outs[key]
 
+    # load every kernel the trace uses once before any clock starts (CUDA
+    # loads a kernel's module at its first launch): plain and batched
+    # compress and decompress, FP32 32^3 and FP64 16^3 blocks, and the same
+    # through a server
+    warm = []
+    for f64 in (False, True):
+        B = 16 if f64 else 32
+        f = pool.fields[(32, f64)]
+        st, nb = cz.compress(f, block=B, kind=kind, eps=1e-3)
+        cz.decompress(st, nbytes=int(nb.item()))
+        cz.compress_batch([f, f], block=B, kind=kind, eps=1e-3)
+        warm += [(0.0, cz.OP_COMPRESS, 32, f64, 1e-3), (0.0, cz.OP_DECOMPRESS, 32, f64, 1e-3)] * 2
+    with cz.Server(int(budget_gb * (1 << 30)), streams) as srv:
+        tks = []
+        for i, (_, op, e, f64, eps) in enumerate(warm):
+            o, nb = out_for(op, e, f64, i)
+            if op == cz.OP_COMPRESS:
+                p = cz.params_for((e, e, e), f64, 16 if f64 else 32, kind, eps)
+                tks.append(srv.submit_compress(p, pool.fields[(e, f64)].data_ptr(), o.data_ptr(), o.numel(),
+                                               nb.data_ptr()))
+            else:
+                sd, sn, hdr = pool.stream_of(e, f64, eps, kind)
+                tks.append(srv.submit_decompress(sd.data_ptr(), sn, hdr, o.data_ptr(), o.numel()))
+        for tk in tks:
+            assert srv.wait(tk)[0] == cz.OK
+    torch.cuda.synchronize()
+
     results = []
     for rate in rates:
         reqs = _trace(rate, n, seed + int(rate), max_edge)
