@@ -28,7 +28,7 @@ NVFLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler"
 
 # (type, block) instantiations of the kernels
 INST = [("float", "f32", 8), ("float", "f32", 16), ("float", "f32", 32),
-        ("double", "f64", 8), ("double", "f64", 16)]
+        ("double", "f64", 8), ("double", "f64", 16), ("double", "f64", 32)]
 
 
 def nvcc() -> str:

@@ -34,7 +34,6 @@ int check(const cz_params *p, Shape *sh)
   const int B = p->block;
   if (B != 8 && B != 16 && B != 32) return CZ_ERR_ARG;
   if (p->dtype != CZ_F32 && p->dtype != CZ_F64) return CZ_ERR_ARG;
-  if (p->dtype == CZ_F64 && B == 32) return CZ_ERR_ARG;  // 256 KiB tile: not provided
   if (p->kind < CZ_W4 || p->kind > CZ_W3AI) return CZ_ERR_ARG;
   if (p->eps_mode != CZ_EPS_REL && p->eps_mode != CZ_EPS_ABS) return CZ_ERR_ARG;
   if (p->stage2 != 0 && p->stage2 != 1) return CZ_ERR_ARG;
@@ -184,13 +183,14 @@ struct Lanes {
   cudaError_t (*dense)(int, int, const DenseArgs *, int, cudaStream_t);
   int (*occupancy)(int, int);
   int (*slot_bytes)();
+  int (*scratch_bytes)();  // global scratch per CTA (FP64 32^3 only)
 };
 
 #define CZ_LANES(sfx)                                                                                      \
   Lanes                                                                                                    \
   {                                                                                                        \
     czl_compress_##sfx, czl_compress_batch_##sfx, czl_decompress_##sfx, czl_dense_##sfx, czl_occupancy_##sfx, \
-        czl_slot_bytes_##sfx                                                                               \
+        czl_slot_bytes_##sfx, czl_scratch_bytes_##sfx                                                      \
   }
 
 Lanes lanes_for(const cz_params &p)
@@ -202,7 +202,8 @@ Lanes lanes_for(const cz_params &p)
     return fast ? CZ_LANES(f32_b32_fast) : CZ_LANES(f32_b32);
   }
   if (p.block == 8) return fast ? CZ_LANES(f64_b8_fast) : CZ_LANES(f64_b8);
-  return fast ? CZ_LANES(f64_b16_fast) : CZ_LANES(f64_b16);
+  if (p.block == 16) return fast ? CZ_LANES(f64_b16_fast) : CZ_LANES(f64_b16);
+  return fast ? CZ_LANES(f64_b32_fast) : CZ_LANES(f64_b32);
 }
 
 int sm_count()
@@ -229,11 +230,40 @@ size_t lb_bytes(const Shape &sh) { return (8ull * sh.nblocks + 255) / 256 * 256;
 size_t table_bytes(const Shape &sh) { return (16ull * sh.nblocks + 255) / 256 * 256; }
 
 struct WsLayout {
-  size_t lb, table, big, staging, total, arena;
+  size_t lb, table, big, staging, scratch, total, arena;
   int grid, grid2, grid3;
 };
 
 size_t big_bytes(long long nblocks) { return (4ull * nblocks + 255) / 256 * 256; }
+
+// global scratch of the FP64 32^3 kernels: one block per CTA of the stage
+// kernel, the large stage-2 kernel and the large stage-2 inverse kernel
+// (the largest of their grids; 0 bytes for every other lane)
+size_t scratch_need(const cz_params *p, const Shape &sh, int grid, int grid3)
+{
+  const size_t per = (size_t)lanes_for(*p).scratch_bytes();
+  if (!per) return 0;
+  int n = grid > grid3 ? grid : grid3;
+  const int gu = grid_for(p, sh, 5);
+  n = n > gu ? n : gu;
+  return per * (size_t)n;
+}
+
+// workspace of decompress_impl for the decoded blocks dsh: header | block
+// table | list of the large chunks | one staging slot per decoded block
+// (stage 2 only) | scratch of the large stage-2 inverse kernel (FP64 32^3)
+size_t dec_ws_need(const cz_params *p, const Shape &dsh, size_t *scratch_off)
+{
+  if (!p->stage2) {
+    if (scratch_off) *scratch_off = 0;
+    return WS_HDR;
+  }
+  const Lanes L = lanes_for(*p);
+  const size_t off = WS_HDR + table_bytes(dsh) + big_bytes(dsh.nblocks) + (size_t)dsh.nblocks * L.slot_bytes();
+  if (scratch_off) *scratch_off = off;
+  const size_t per = (size_t)L.scratch_bytes();
+  return off + (per ? per * (size_t)grid_for(p, dsh, 5) : 0);
+}
 
 // bit zeroing width of the kept details (0, 4 or 8)
 int zero_bits(const cz_params &p)
@@ -254,7 +284,8 @@ WsLayout ws_layout(const cz_params *p, const Shape &sh)
   w.staging = w.big + big_bytes(sh.nblocks);
   // blocks are dealt round robin to the stage CTAs
   w.arena = (((size_t)sh.nblocks + w.grid - 1) / w.grid) * (size_t)L.slot_bytes();
-  w.total = w.staging + w.arena * (size_t)w.grid;
+  w.scratch = w.staging + w.arena * (size_t)w.grid;
+  w.total = w.scratch + scratch_need(p, sh, w.grid, w.grid3);
   return w;
 }
 
@@ -282,7 +313,10 @@ bool make_tile_map(CUtensorMap *tm, const cz_params *p, const void *d_field)
   const cuuint64_t es = p->dtype == CZ_F64 ? 8 : 4;
   const cuuint64_t dims[3] = {(cuuint64_t)p->nx, (cuuint64_t)p->ny, (cuuint64_t)p->nz};
   const cuuint64_t strides[2] = {(cuuint64_t)p->nx * es, (cuuint64_t)p->nx * p->ny * es};
-  const cuuint32_t box[3] = {(cuuint32_t)p->block, (cuuint32_t)p->block, (cuuint32_t)p->block};
+  // (the FP64 32^3 kernels address the field directly and do not use the
+  // map: a box of 8 z-planes keeps it within the encoder's limits)
+  const cuuint32_t bz = (p->dtype == CZ_F64 && p->block == 32) ? 8u : (cuuint32_t)p->block;
+  const cuuint32_t box[3] = {(cuuint32_t)p->block, (cuuint32_t)p->block, bz};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r =
       enc(tm, p->dtype == CZ_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
@@ -354,7 +388,7 @@ struct BatchKnobs {
 };
 
 struct BatchLayout {
-  size_t keys, lb, table, big, staging, total, arena;
+  size_t keys, lb, table, big, staging, scratch, total, arena;
   int grid, grid2, grid3, tiles, nblocks;
 };
 
@@ -388,7 +422,8 @@ BatchLayout batch_layout(const Group &g, const cz_params *p, const BatchKnobs &k
   w.big = w.table + (16ull * w.nblocks + 255) / 256 * 256;
   w.staging = w.big + big_bytes(w.nblocks);
   w.arena = (((size_t)w.nblocks + w.grid - 1) / w.grid) * (size_t)L.slot_bytes();
-  w.total = w.staging + w.arena * (size_t)w.grid;
+  w.scratch = w.staging + w.arena * (size_t)w.grid;
+  w.total = w.scratch + scratch_need(&p0, all, w.grid, w.grid3);
   return w;
 }
 
@@ -483,7 +518,7 @@ int compress_batch_impl(int n, const cz_params *p, const void *const *d_fields, 
       mm.n[f] = need_range ? (unsigned long long)p[i].nx * p[i].ny * p[i].nz : 0ull;
       maxn = mm.n[f] > maxn ? mm.n[f] : maxn;
       if (!make_tile_map(&maps.tm[f], &p[i], d_fields[i])) return CZ_ERR_CUDA;
-      maps.g[f] = FieldGeo{sh.nbx, sh.nby, first, p[i].eps_mode, p[i].eps, p[i].range};
+      maps.g[f] = FieldGeo{d_fields[i], sh.nbx, sh.nby, first, p[i].eps_mode, p[i].eps, p[i].range};
       FieldOut &fo = bo.f[f];
       fo.out = reinterpret_cast<unsigned char *>(d_outs[i]);
       fo.out_bytes = d_out_bytes ? reinterpret_cast<unsigned long long *>(d_out_bytes + i) : nullptr;
@@ -515,6 +550,7 @@ int compress_batch_impl(int n, const cz_params *p, const void *const *d_fields, 
     a.biglist = reinterpret_cast<int *>(wsb + w.big);
     a.staging = wsb + w.staging;
     a.arena_bytes = w.arena;
+    a.scratch = wsb + w.scratch;
     a.table = reinterpret_cast<unsigned long long *>(wsb + w.table);
     a.cnorm = threshold_divisor(&p0);
     a.nblocks = w.nblocks;
@@ -528,6 +564,7 @@ int compress_batch_impl(int n, const cz_params *p, const void *const *d_fields, 
     sa.table = a.table;
     sa.ws = d_ws;
     sa.biglist = a.biglist;
+    sa.scratch = a.scratch;
     sa.nblocks = w.nblocks;
     PlaceArgs pa{};
     pa.staging = a.staging;
@@ -617,6 +654,7 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
   a.biglist = reinterpret_cast<int *>(wsb + wl.big);
   a.staging = wsb + wl.staging;
   a.arena_bytes = wl.arena;
+  a.scratch = wsb + wl.scratch;
   a.table = reinterpret_cast<unsigned long long *>(wsb + wl.table);
   a.eps = p->eps;
   a.range = p->range;
@@ -638,6 +676,7 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
   sa.table = a.table;
   sa.ws = d_ws;
   sa.biglist = a.biglist;
+  sa.scratch = a.scratch;
   sa.nblocks = sh.nblocks;
   PlaceArgs pa{};
   pa.staging = a.staging;
@@ -934,8 +973,8 @@ int decompress_impl(const void *d_in, size_t in_bytes, const void *h_header, con
   // chunks | one staging slot per decoded block for the stage-2 payloads
   // (within cz_workspace_size)
   const size_t slot = (size_t)L.slot_bytes();
-  const size_t need = p.stage2 ? WS_HDR + table_bytes(dsh) + big_bytes(dsh.nblocks) + (size_t)dsh.nblocks * slot
-                               : (size_t)WS_HDR;
+  size_t scr = 0;
+  const size_t need = dec_ws_need(&p, dsh, &scr);
   if (ws_bytes < need) return CZ_ERR_CAPACITY;
   if (cudaMemsetAsync(d_ws, 0, WS_HDR, s) != cudaSuccess) return CZ_ERR_CUDA;
   unsigned char *wsb = reinterpret_cast<unsigned char *>(d_ws);
@@ -963,6 +1002,7 @@ int decompress_impl(const void *d_in, size_t in_bytes, const void *h_header, con
   ua.staging = wsb + WS_HDR + table_bytes(dsh) + big_bytes(dsh.nblocks);
   ua.ws = d_ws;
   ua.biglist = reinterpret_cast<int *>(wsb + WS_HDR + table_bytes(dsh));
+  ua.scratch = wsb + scr;
   ua.table = reinterpret_cast<unsigned long long *>(wsb + WS_HDR);
   ua.ids = ids;
   ua.nchunks = nchunks;
@@ -991,9 +1031,10 @@ int cz_decompress_blocks_workspace_size(const cz_params *p, int n, size_t *bytes
   Shape sh;
   const int r = check(p, &sh);
   if (r != CZ_OK || !bytes || n < 0) return r ? r : CZ_ERR_ARG;
+  sh.nbx = sh.nby = 1;
+  sh.nbz = n;
   sh.nblocks = n;
-  *bytes = p->stage2 ? WS_HDR + table_bytes(sh) + big_bytes(n) + (size_t)n * (size_t)lanes_for(*p).slot_bytes()
-                     : (size_t)WS_HDR;
+  *bytes = dec_ws_need(p, sh, nullptr);
   return CZ_OK;
 }
 

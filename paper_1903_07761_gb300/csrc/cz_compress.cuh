@@ -31,6 +31,7 @@ struct S2Args {
   unsigned long long *table;  // per block: slot offset, chunk bytes (~0: lost)
   const void *ws;             // header: count of large payloads (nbig)
   const int *biglist;         // ids of the blocks with large payloads
+  unsigned char *scratch;     // FP64 32^3: shuffled payloads, one G2::SCRATCH block per large CTA
   int nblocks;
 };
 

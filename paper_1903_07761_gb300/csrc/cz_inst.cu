@@ -8,6 +8,7 @@
 #include "cz_compress.cuh"
 #include "cz_launch.h"
 #include "cz_pair.cuh"
+#include "cz_slab.cuh"
 
 #ifndef CZ_T
 #error "CZ_T must be defined"
@@ -21,6 +22,7 @@ using namespace czp;
 namespace {
 
 using G = G2<CZ_T, CZ_B>;
+using SGi = SG<CZ_T, 32>;  // slab geometry (used only when G::SLAB)
 
 // raise the dynamic shared-memory limit of kernel KERN once per device
 template <auto KERN>
@@ -37,7 +39,9 @@ cudaError_t prepare(int smem)
   return e;
 }
 
-// stage 2 on every slot (small and large payloads), when enabled
+// stage 2 on every slot (small and large payloads), when enabled (a
+// template, so that only the kernels of this lane are instantiated)
+template <int = 0>
 cudaError_t stage2_k(const S2Args &sa, int stage2, int grid2, int grid3, cudaStream_t s)
 {
   cudaError_t e = cudaSuccess;
@@ -47,7 +51,14 @@ cudaError_t stage2_k(const S2Args &sa, int stage2, int grid2, int grid3, cudaStr
     k_stage2<CZ_T, CZ_B, false><<<grid2, 128, G::SMEM_S2, s>>>(sa);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if constexpr (G::HAS_BIG) {
+    if constexpr (G::SLAB) {
+      constexpr int sm = 4 * G::NBWMAX * 4;
+      e = prepare<k_stage2_huge<CZ_T, CZ_B>>(sm);
+      if (e != cudaSuccess) return e;
+      k_stage2_huge<CZ_T, CZ_B><<<grid3, 512, sm, s>>>(sa);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    } else if constexpr (G::HAS_BIG) {
       e = prepare<k_stage2<CZ_T, CZ_B, true>>(G::SMEM_S2B);
       if (e != cudaSuccess) return e;
       k_stage2<CZ_T, CZ_B, true><<<grid3, 512, G::SMEM_S2B, s>>>(sa);
@@ -62,12 +73,20 @@ template <int KIND>
 cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const S2Args &sa, const PlaceArgs &pa, int grid,
                        int grid2, int grid3, const cudaEvent_t *marks, cudaStream_t s)
 {
-  cudaError_t e = prepare<k_stage1<CZ_T, CZ_B, KIND, 1>>(G::SMEM_C);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   StageMaps<1> maps{};
   maps.tm[0] = tm;
-  if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
-  k_stage1<CZ_T, CZ_B, KIND, 1><<<grid, G::NT, G::SMEM_C, s>>>(maps, a);
+  if constexpr (G::SLAB) {
+    e = prepare<k_stage1_slab<CZ_T, CZ_B, KIND, 1>>(SGi::SMEM);
+    if (e != cudaSuccess) return e;
+    if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
+    k_stage1_slab<CZ_T, CZ_B, KIND, 1><<<grid, SGi::NT, SGi::SMEM, s>>>(maps, a);
+  } else {
+    e = prepare<k_stage1<CZ_T, CZ_B, KIND, 1>>(G::SMEM_C);
+    if (e != cudaSuccess) return e;
+    if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
+    k_stage1<CZ_T, CZ_B, KIND, 1><<<grid, G::NT, G::SMEM_C, s>>>(maps, a);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (marks && (e = cudaEventRecord(marks[1], s)) != cudaSuccess) return e;
@@ -88,9 +107,16 @@ template <int KIND>
 cudaError_t compress_batch_k(const StageMaps<MAXF> &maps, const FwdArgs &a, const S2Args &sa, const BatchOut &bo,
                              const PlaceArgs &pa, int grid, int grid2, int grid3, int tiles, cudaStream_t s)
 {
-  cudaError_t e = prepare<k_stage1<CZ_T, CZ_B, KIND, MAXF>>(G::SMEM_C);
-  if (e != cudaSuccess) return e;
-  k_stage1<CZ_T, CZ_B, KIND, MAXF><<<grid, G::NT, G::SMEM_C, s>>>(maps, a);
+  cudaError_t e;
+  if constexpr (G::SLAB) {
+    e = prepare<k_stage1_slab<CZ_T, CZ_B, KIND, MAXF>>(SGi::SMEM);
+    if (e != cudaSuccess) return e;
+    k_stage1_slab<CZ_T, CZ_B, KIND, MAXF><<<grid, SGi::NT, SGi::SMEM, s>>>(maps, a);
+  } else {
+    e = prepare<k_stage1<CZ_T, CZ_B, KIND, MAXF>>(G::SMEM_C);
+    if (e != cudaSuccess) return e;
+    k_stage1<CZ_T, CZ_B, KIND, MAXF><<<grid, G::NT, G::SMEM_C, s>>>(maps, a);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if ((e = stage2_k(sa, pa.stage2, grid2, grid3, s)) != cudaSuccess) return e;
@@ -120,42 +146,71 @@ cudaError_t decompress_k(const CUtensorMap &om, const InvArgs &a, const UnArgs &
       if (e != cudaSuccess) return e;
     }
   }
-  e = prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D);
-  if (e != cudaSuccess) return e;
-  k_decompress2<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_D, s>>>(om, a);
+  if constexpr (G::SLAB) {
+    e = prepare<k_decompress_slab<CZ_T, CZ_B, KIND>>(SGi::SMEM);
+    if (e != cudaSuccess) return e;
+    k_decompress_slab<CZ_T, CZ_B, KIND><<<grid, SGi::NT, SGi::SMEM, s>>>(a);
+  } else {
+    e = prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D);
+    if (e != cudaSuccess) return e;
+    k_decompress2<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_D, s>>>(om, a);
+  }
   return cudaGetLastError();
 }
 
 template <int KIND, bool FWD>
 cudaError_t dense_k(const DenseArgs &a, int nblocks, cudaStream_t s)
 {
-  cudaError_t e = prepare<k_dense2<CZ_T, CZ_B, KIND, FWD>>(G::SMEM_DN0);
-  if (e != cudaSuccess) return e;
-  k_dense2<CZ_T, CZ_B, KIND, FWD><<<nblocks, G::NT, G::SMEM_DN0, s>>>(a);
+  cudaError_t e;
+  if constexpr (G::SLAB) {
+    e = prepare<k_dense_slab<CZ_T, CZ_B, KIND, FWD>>(SGi::SMEM);
+    if (e != cudaSuccess) return e;
+    k_dense_slab<CZ_T, CZ_B, KIND, FWD><<<nblocks, SGi::NT, SGi::SMEM, s>>>(a);
+  } else {
+    e = prepare<k_dense2<CZ_T, CZ_B, KIND, FWD>>(G::SMEM_DN0);
+    if (e != cudaSuccess) return e;
+    k_dense2<CZ_T, CZ_B, KIND, FWD><<<nblocks, G::NT, G::SMEM_DN0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
 template <int KIND>
 int occupancy_c()
 {
-  if (prepare<k_stage1<CZ_T, CZ_B, KIND, 1>>(G::SMEM_C) != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage1<CZ_T, CZ_B, KIND, 1>, G::NT, G::SMEM_C) !=
-      cudaSuccess)
-    return 0;
+  if constexpr (G::SLAB) {
+    if (prepare<k_stage1_slab<CZ_T, CZ_B, KIND, 1>>(SGi::SMEM) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage1_slab<CZ_T, CZ_B, KIND, 1>, SGi::NT,
+                                                      SGi::SMEM) != cudaSuccess)
+      return 0;
+  } else {
+    if (prepare<k_stage1<CZ_T, CZ_B, KIND, 1>>(G::SMEM_C) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage1<CZ_T, CZ_B, KIND, 1>, G::NT, G::SMEM_C) !=
+        cudaSuccess)
+      return 0;
+  }
   return n;
 }
 
 template <bool BIG>
 int occupancy_s2()
 {
-  constexpr int sm = BIG ? G::SMEM_S2B : G::SMEM_S2;
-  if (prepare<k_stage2<CZ_T, CZ_B, BIG>>(sm) != cudaSuccess) return 0;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage2<CZ_T, CZ_B, BIG>, BIG ? 512 : 128, sm) !=
-      cudaSuccess)
-    return 0;
-  return n;
+  if constexpr (BIG && G::SLAB) {
+    constexpr int sm = 4 * G::NBWMAX * 4;
+    if (prepare<k_stage2_huge<CZ_T, CZ_B>>(sm) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage2_huge<CZ_T, CZ_B>, 512, sm) != cudaSuccess)
+      return 0;
+    return n;
+  } else {
+    constexpr int sm = BIG ? G::SMEM_S2B : G::SMEM_S2;
+    if (prepare<k_stage2<CZ_T, CZ_B, BIG>>(sm) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage2<CZ_T, CZ_B, BIG>, BIG ? 512 : 128, sm) !=
+        cudaSuccess)
+      return 0;
+    return n;
+  }
 }
 
 template <bool BIG>
@@ -173,12 +228,20 @@ int occupancy_u()
 template <int KIND>
 int occupancy_d()
 {
-  if (prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D) != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decompress2<CZ_T, CZ_B, KIND>, G::NT, G::SMEM_D) !=
-      cudaSuccess)
-    return 0;
-  return n;
+  if constexpr (G::SLAB) {
+    if (prepare<k_decompress_slab<CZ_T, CZ_B, KIND>>(SGi::SMEM) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decompress_slab<CZ_T, CZ_B, KIND>, SGi::NT,
+                                                      SGi::SMEM) != cudaSuccess)
+      return 0;
+    return n;
+  } else {
+    if (prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decompress2<CZ_T, CZ_B, KIND>, G::NT, G::SMEM_D) !=
+        cudaSuccess)
+      return 0;
+    return n;
+  }
 }
 
 }  // namespace
@@ -286,3 +349,7 @@ static int occupancy_query(int kind, int which)
 
 // bytes of the staging slot of the largest payload
 extern "C" int CZ_CAT(czl_slot_bytes_, CZ_SUFFIX)() { return G::PSLOT; }
+
+// global scratch per CTA of the stage kernel, the large stage-2 kernel and
+// the large stage-2 inverse kernel (FP64 32^3 only; 0 otherwise)
+extern "C" int CZ_CAT(czl_scratch_bytes_, CZ_SUFFIX)() { return G::SCRATCH; }

@@ -30,15 +30,18 @@ struct StageMaps;
   extern "C" cudaError_t czl_dense_##sfx(int kind, int fwd, const czp::DenseArgs *a, int nblocks,   \
                                          cudaStream_t s);                                           \
   extern "C" int czl_occupancy_##sfx(int kind, int which);                                         \
-  extern "C" int czl_slot_bytes_##sfx();
+  extern "C" int czl_slot_bytes_##sfx();                                                           \
+  extern "C" int czl_scratch_bytes_##sfx();
 
 CZ_DECLARE_LAUNCHERS(f32_b8)
 CZ_DECLARE_LAUNCHERS(f32_b16)
 CZ_DECLARE_LAUNCHERS(f32_b32)
 CZ_DECLARE_LAUNCHERS(f64_b8)
 CZ_DECLARE_LAUNCHERS(f64_b16)
+CZ_DECLARE_LAUNCHERS(f64_b32)
 CZ_DECLARE_LAUNCHERS(f32_b8_fast)
 CZ_DECLARE_LAUNCHERS(f32_b16_fast)
 CZ_DECLARE_LAUNCHERS(f32_b32_fast)
 CZ_DECLARE_LAUNCHERS(f64_b8_fast)
 CZ_DECLARE_LAUNCHERS(f64_b16_fast)
+CZ_DECLARE_LAUNCHERS(f64_b32_fast)

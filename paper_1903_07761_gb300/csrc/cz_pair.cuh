@@ -60,6 +60,7 @@ constexpr int MAXF = 32;  // fields per batched launch
 
 // per-field geometry and threshold inputs of the stage kernel
 struct FieldGeo {
+  const void *field;    // the field (read directly by the slab kernels)
   int nbx, nby, first;  // block grid (x, y) and the field's first global block
   int eps_mode;
   double eps, range_in;  // range_in < 0: range from this field's min/max keys
@@ -95,6 +96,7 @@ struct FwdArgs {
   unsigned char *staging;     // raw payloads, one arena per CTA
   unsigned long long *table;  // per block: staging offset, nnz
   unsigned long long arena_bytes;
+  unsigned char *scratch;  // slab kernels: one G2::SCRATCH block per CTA
   double eps, range, cnorm;
   int nx, ny, nz, nbx, nby, nbz, nblocks, nf;
   int eps_mode, stage2, kind, dtype;
@@ -121,6 +123,7 @@ struct UnArgs {
   unsigned long long *table;  // per block: nnz, bad flag
   void *ws;                   // header: count of large chunks (nbig)
   int *biglist;               // ids of the chunks with large payloads
+  unsigned char *scratch;     // FP64 32^3: shuffled payloads, one G2::SCRATCH block per large CTA
   const int *ids;             // random access: chunk of each decoded block (else the identity)
   int nchunks;                // blocks in the stream
   unsigned long long in_bytes, data0, slot;
@@ -298,7 +301,7 @@ struct G2 {
   static constexpr int SMEM_S2B = PMAX_AL + 4 * NBWMAX * 4;
   // stage-2 inverse kernels: payload + three per-token arrays
   static constexpr int SMEM_U = SHCAP + 3 * 128 * 4;
-  static constexpr int SMEM_UB = PMAX_AL + 3 * 512 * 4;
+  static constexpr int SMEM_UB = (ES == 8 && B == 32 ? 0 : PMAX_AL) + 3 * 512 * 4;
   // dense kernels: cube | plane | halo
   static constexpr int SMEM_DN0 = CUBE_AL + PLANE + HALO;
   // decompress: row offsets, later the cube | two payload buffers | output
@@ -314,12 +317,18 @@ struct G2 {
   static constexpr int OTB0 = TILE > PLANE + HALO ? TILE : PLANE + HALO;
   static constexpr int OTB = (OTB0 + 127) / 128 * 128;
   static constexpr int SMEM_D = R2D + NPB * PBCAP + OTB;
+  // FP64 32^3 blocks (256 KiB) fit neither the registers nor the shared
+  // memory of one CTA: they take the slab kernels (cz_slab.cuh), whose
+  // block lives in global memory (a scratch block per CTA, L2-resident),
+  // and large stage-2 payloads are shuffled in global scratch too
+  static constexpr bool SLAB = ES == 8 && B == 32;
+  static constexpr int SCRATCH = SLAB ? (PMAX_AL > TILE ? PMAX_AL : TILE) : 0;  // per CTA
   static_assert(HP == NK && NK == ZH && NT == HP * NK * 2, "thread grid");
   static_assert(HALO >= ROWB + MASKBP, "row offsets and mask rows fit the halo area");
-  static_assert(SMEM_C <= 227 * 1024 - 1024, "stage kernel shared memory");
-  static_assert(SMEM_D <= 227 * 1024 - 1024, "decompress shared memory");
-  static_assert(SMEM_S2B <= 227 * 1024 - 1024, "stage-2 shared memory");
-  static_assert(WMAX < 65536, "zero-RLE tokens hold run lengths below 65536 words");
+  static_assert(SLAB || SMEM_C <= 227 * 1024 - 1024, "stage kernel shared memory");
+  static_assert(SLAB || SMEM_D <= 227 * 1024 - 1024, "decompress shared memory");
+  static_assert(SLAB || SMEM_S2B <= 227 * 1024 - 1024, "stage-2 shared memory");
+  static_assert(SLAB || WMAX < 65536, "zero-RLE tokens hold run lengths below 65536 words");
 };
 
 // ------------------------------------------------------------ TMA / mbarrier
@@ -1393,9 +1402,12 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_unstage(const UnArgs a)
 {
   using G = G2<T, B>;
   constexpr int NT = BIG ? 512 : 128, ES = G::ES;
-  constexpr int CAPB = BIG ? G::PMAX_AL : G::SHCAP;
+  // FP64 32^3: the large launch's shuffled payload lives in a global
+  // scratch block per CTA (it does not fit in shared memory)
+  constexpr bool GP = BIG && G::SLAB;
+  constexpr int CAPB = BIG ? (GP ? 0 : G::PMAX_AL) : G::SHCAP;
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char *P = smem;
+  unsigned char *P = GP ? a.scratch + (size_t)blockIdx.x * G::SCRATCH : smem;
   unsigned *TL = reinterpret_cast<unsigned *>(smem + CAPB);  // per token of a round: first literal,
   unsigned *TO = TL + NT;                                      // first output word,
   unsigned *TK = TO + NT;                                      // the token

@@ -122,3 +122,23 @@ def test_batch_with_bit_zeroing_groups_and_matches_the_oracle():
     torch.cuda.synchronize()
     for (f, B, e), o, n, z in zip(items, outs, nbytes.cpu().tolist(), zb):
         assert bytes(o[:int(n)].cpu().numpy()) == O.compress(f, B, O.W3AI, e, zbits=z)
+
+
+def test_batch_with_fp64_32_blocks_matches_the_oracle():
+    """FP64 fields with 32^3 blocks (the slab kernels) in one batched call,
+    next to FP32 fields: every stream equals the oracle's."""
+    import torch
+    from paper_1903_07761_gb300 import cz, inputs
+    rng = np.random.default_rng(41)
+    items = []
+    for i in range(5):
+        f64 = i % 2 == 0
+        dims = tuple(int(32 * rng.integers(1, 3)) for _ in range(3))
+        f = inputs.field(inputs.P, dims, np.float64 if f64 else np.float32, seed=3100 + i, nbubbles=4)
+        items.append((f, float(rng.choice([1e-2, 1e-3, 1e-4]))))
+    tens = [torch.from_numpy(f).cuda() for f, _ in items]
+    res = cz.compress_batch(tens, block=32, kind="w3ai", eps=[e for _, e in items])
+    torch.cuda.synchronize()
+    for (f, e), (out, nb) in zip(items, res):
+        got = out[:int(nb.item())].cpu().numpy().tobytes()
+        assert got == O.compress(f, 32, O.W3AI, e)

@@ -25,9 +25,6 @@ def test_bad_parameters_are_refused():
     with pytest.raises(cz.CzError) as e:
         cz.compress(f, block=32)
     assert e.value.code == cz.ERR_ARG
-    g = torch.zeros((32, 32, 32), device="cuda", dtype=torch.float64)
-    with pytest.raises(cz.CzError):
-        cz.compress(g, block=32)  # FP64 with 32^3 blocks is not provided
     with pytest.raises(cz.CzError):
         cz.compress(torch.zeros((16, 16, 16), device="cuda"), block=12)
     with pytest.raises(cz.CzError):

@@ -22,6 +22,7 @@ CASES = [
     (np.float32, 8, (8, 24, 40)),
     (np.float64, 16, (32, 16, 48)),
     (np.float64, 8, (24, 8, 16)),
+    (np.float64, 32, (32, 64, 96)),  # 256 KiB blocks: the slab kernels
 ]
 
 
@@ -65,7 +66,7 @@ def test_stream_and_decode_bit_identical(dtype, block, shape, kind, stage2):
 @pytest.mark.parametrize("zbits", [4, 8])
 @pytest.mark.parametrize("stage2", [True, False])
 @pytest.mark.parametrize("kind", KINDS)
-@pytest.mark.parametrize("dtype,block,shape", [CASES[0], CASES[3]])
+@pytest.mark.parametrize("dtype,block,shape", [CASES[0], CASES[3], CASES[5]])
 def test_bit_zeroing_streams_bit_identical(dtype, block, shape, kind, stage2, zbits):
     """Bit zeroing Z4 / Z8 (Sec. 3, Exp. 2): the kept details' low bits are
     cleared on the GPU exactly as in the oracle."""
@@ -80,6 +81,7 @@ def test_bit_zeroing_streams_bit_identical(dtype, block, shape, kind, stage2, zb
 @pytest.mark.parametrize("dtype,block,shape", [
     (np.float32, 32, (64, 160, 544)),  # 17 x 5 x 2 = 170 blocks: more than one per stage CTA
     (np.float64, 16, (64, 96, 400)),   # 25 x 6 x 4 = 600 blocks
+    (np.float64, 32, (64, 160, 1024)),  # 32 x 5 x 2 = 320 blocks of 32^3 (more than one per slab CTA)
 ])
 def test_non_cubic_grid_with_several_blocks_per_cta(dtype, block, shape, stage2):
     """The persistent kernels walk their blocks in steps of the grid size
@@ -93,7 +95,7 @@ def test_non_cubic_grid_with_several_blocks_per_cta(dtype, block, shape, stage2)
     np.testing.assert_array_equal(rec.view(np.uint8), O.decompress(ref).view(np.uint8))
 
 
-@pytest.mark.parametrize("dtype,block", [(np.float64, 16), (np.float32, 16)])
+@pytest.mark.parametrize("dtype,block", [(np.float64, 16), (np.float32, 16), (np.float64, 32)])
 def test_payload_exactly_at_the_stage2_shared_capacity(dtype, block):
     """One block whose payload is exactly 16 KiB (the stage-2 kernels'
     shared-memory capacity) and has no zero-word runs, so its finished chunk
@@ -191,7 +193,7 @@ def test_dense_coefficients_match_oracle_per_block(dtype, block, shape, kind):
 
 
 def test_single_block_and_all_constant_field():
-    for dtype, block in ((np.float32, 32), (np.float64, 16), (np.float32, 8)):
+    for dtype, block in ((np.float32, 32), (np.float64, 16), (np.float32, 8), (np.float64, 32)):
         f = np.full((block,) * 3, 3.25, dtype)
         for kind in KINDS:
             ref = O.compress(f, block, kind, 1e-3)
@@ -220,3 +222,26 @@ def test_nan_values_are_kept_like_the_oracle():
     np.testing.assert_array_equal(np.isnan(rec), np.isnan(want))
     ok = ~np.isnan(want)
     np.testing.assert_array_equal(rec[ok].view(np.uint32), want[ok].view(np.uint32))
+
+
+@pytest.mark.parametrize("stage2", [True, False])
+@pytest.mark.parametrize("kind", KINDS)
+def test_fp64_32_payloads_beyond_one_token_field(kind, stage2):
+    """FP64 32^3 blocks with every detail kept (eps = 0): a payload of
+    66,560 words.  Without zero words the literal run is longer than a
+    token's 16-bit field and splits into (65535, 0) and the rest; on a
+    constant field (every detail exactly 0, all kept) the zero-word runs of
+    the shuffled payload are long.  Both go through the global-scratch
+    stage-2 coder and decoder."""
+    rng = np.random.default_rng(17 + kind)
+    noisy = rng.standard_normal((32, 32, 64))
+    const = np.full((32, 32, 32), -1.5)
+    for f in (noisy, const):
+        ref = O.compress(f, 32, kind, 0.0, stage2=stage2)
+        got = gpu_compress(f, 32, kind, 0.0, stage2=stage2)
+        assert got == ref, describe_diff(got, ref)
+        np.testing.assert_array_equal(gpu_decompress(got).view(np.uint8), O.decompress(ref).view(np.uint8))
+    if stage2:
+        d0, offs = O.chunk_table(O.compress(noisy, 32, kind, 0.0))
+        toks = np.frombuffer(O.compress(noisy, 32, kind, 0.0)[d0 + 8:d0 + 16], np.uint32)
+        assert toks[0] == 65535  # the first token of a split literal run
