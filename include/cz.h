@@ -87,7 +87,7 @@ enum {
 
 typedef struct cz_params {
   int32_t nx, ny, nz; /* field dims in elements; each a multiple of block   */
-  int32_t block;      /* cubic block edge B: 8, 16 or 32 (32 only for F32)  */
+  int32_t block;      /* cubic block edge B: 8, 16 or 32                    */
   int32_t dtype;      /* CZ_F32 or CZ_F64                                   */
   int32_t kind;       /* CZ_W4, CZ_W4LI or CZ_W3AI                          */
   int32_t eps_mode;   /* CZ_EPS_REL (default) or CZ_EPS_ABS                 */
@@ -105,7 +105,9 @@ int cz_compress_bound(const cz_params *p, size_t *bytes);
 /* Device workspace needed by cz_compress / cz_decompress for p: a status
  * word, the min/max keys, one u64 look-back word per block, a block table
  * (16 bytes per block) and the staging slots the chunks are built in (room
- * for the largest chunk of every block, about the size of the field).
+ * for the largest chunk of every block, about the size of the field).  FP64
+ * with 32^3 blocks adds one 260 KiB scratch block per CTA of the kernels
+ * that hold a block or a large payload in global memory.
  * Needs the current device (it sizes the persistent grids by its SM count). */
 int cz_workspace_size(const cz_params *p, size_t *bytes);
 

@@ -144,7 +144,7 @@ class _Pool:
     def stream_of(self, e, f64, eps, kind):
         key = (e, f64, eps, kind)
         if key not in self.streams:
-            out, nb = cz.compress(self.fields[(e, f64)], block=16 if f64 else 32, kind=kind, eps=eps)
+            out, nb = cz.compress(self.fields[(e, f64)], block=32, kind=kind, eps=eps)
             n = int(nb.item())
             self.streams[key] = (out[:n].clone(), n, out[:cz.HEADER_BYTES].cpu().numpy().tobytes())
         return self.streams[key]
@@ -175,7 +175,7 @@ def served(rates=(1000.0, 5000.0), n: int = 400, budget_gb: float = 40.0, stream
     def out_for(op, e, f64, i):
         key = (op, e, f64, i % ring)
         if key not in outs:
-            p = cz.params_for((e, e, e), f64, 16 if f64 else 32, kind, 1e-3)
+            p = cz.params_for((e, e, e), f64, 32, kind, 1e-3)
             nbytes = cz.cz_compress_bound(p) if op == cz.OP_COMPRESS else e ** 3 * (8 if f64 else 4)
             outs[key] = (torch.empty(nbytes, dtype=torch.uint8, device="cuda"),
                          torch.zeros(1, dtype=torch.int64, device="cuda"))
@@ -183,11 +183,11 @@ def served(rates=(1000.0, 5000.0), n: int = 400, budget_gb: float = 40.0, stream
 
     # load every kernel the trace uses once before any clock starts (CUDA
     # loads a kernel's module at its first launch): plain and batched
-    # compress and decompress, FP32 32^3 and FP64 16^3 blocks, and the same
+    # compress and decompress, FP32 and FP64 32^3 blocks, and the same
     # through a server
     warm = []
     for f64 in (False, True):
-        B = 16 if f64 else 32
+        B = 32
         f = pool.fields[(32, f64)]
         st, nb = cz.compress(f, block=B, kind=kind, eps=1e-3)
         cz.decompress(st, nbytes=int(nb.item()))
@@ -198,7 +198,7 @@ def served(rates=(1000.0, 5000.0), n: int = 400, budget_gb: float = 40.0, stream
         for i, (_, op, e, f64, eps) in enumerate(warm):
             o, nb = out_for(op, e, f64, i)
             if op == cz.OP_COMPRESS:
-                p = cz.params_for((e, e, e), f64, 16 if f64 else 32, kind, eps)
+                p = cz.params_for((e, e, e), f64, 32, kind, eps)
                 tks.append(srv.submit_compress(p, pool.fields[(e, f64)].data_ptr(), o.data_ptr(), o.numel(),
                                                nb.data_ptr()))
             else:
@@ -227,7 +227,7 @@ def served(rates=(1000.0, 5000.0), n: int = 400, budget_gb: float = 40.0, stream
                     pass
                 o, nb = out_for(op, e, f64, i)
                 if op == cz.OP_COMPRESS:
-                    p = cz.params_for((e, e, e), f64, 16 if f64 else 32, kind, eps)
+                    p = cz.params_for((e, e, e), f64, 32, kind, eps)
                     tk = srv.submit_compress(p, pool.fields[(e, f64)].data_ptr(), o.data_ptr(), o.numel(),
                                              nb.data_ptr())
                 else:
@@ -243,7 +243,7 @@ def served(rates=(1000.0, 5000.0), n: int = 400, budget_gb: float = 40.0, stream
 
         # ---- one at a time, plain launches, same trace
         s = torch.cuda.current_stream().cuda_stream
-        ws = torch.empty(max(cz.cz_workspace_size(cz.params_for((e, e, e), f64, 16 if f64 else 32, kind, eps))
+        ws = torch.empty(max(cz.cz_workspace_size(cz.params_for((e, e, e), f64, 32, kind, eps))
                              for _, _, e, f64, eps in reqs), dtype=torch.uint8, device="cuda")
         plat = []
         t0 = time.perf_counter()
@@ -252,7 +252,7 @@ def served(rates=(1000.0, 5000.0), n: int = 400, budget_gb: float = 40.0, stream
                 pass
             o, nb = out_for(op, e, f64, i)
             if op == cz.OP_COMPRESS:
-                p = cz.params_for((e, e, e), f64, 16 if f64 else 32, kind, eps)
+                p = cz.params_for((e, e, e), f64, 32, kind, eps)
                 r = cz.cz_compress(p, pool.fields[(e, f64)].data_ptr(), o.data_ptr(), o.numel(), nb.data_ptr(),
                                    ws.data_ptr(), ws.numel(), s)
             else:
@@ -272,30 +272,34 @@ def served(rates=(1000.0, 5000.0), n: int = 400, budget_gb: float = 40.0, stream
         })
     return {
         "workload": f"Poisson compress/decompress 1:1, cubic edges log-uniform [32,{max_edge}] step 32, "
-                    f"70% FP32 (32^3 blocks) / 30% FP64 (16^3 blocks), eps in {{1e-3,1e-4}}, {kind}, "
+                    f"70% FP32 / 30% FP64, 32^3 blocks, eps in {{1e-3,1e-4}}, {kind}, "
                     f"budget {budget_gb:g} GB, {streams} streams",
         "runs": results,
     }
 
 
 # ------------------------------------------------------------------ FP64
-def _w3ai_fp64_ops_per_element(B: int) -> float:
+def _w3ai_fp64_ops_per_element(B: int, xy_run_time: bool = True) -> float:
     """FP64 instructions per element of the exact-build W3ai transform (one
     direction) over all levels and axes, counted from the kernels' steps.
     Forward, per pair: the average (add, mul), the predicted half-cell value
     and the detail (sub); inverse, per pair: the predicted value, its sum
-    with the detail (add) and the second sample (mul, sub).  The finest x-
-    and y-steps use run-time stencils: 8 operations per interior pair (two
-    weight multiplies, add, multiply by 1/8, add) and 10 at the two boundary
-    pairs of a line.  The finest z-step and the coarser levels use
-    compile-time rows, whose interior form is one subtraction: 6 per
-    interior pair, 10 at the boundary pairs."""
+    with the detail (add) and the second sample (mul, sub).  Compile-time
+    rows (interior form one subtraction) take 6 operations per interior
+    pair and 10 at the two boundary pairs of a line.  In the register-
+    resident kernels the finest x- and y-steps use run-time stencils
+    (xy_run_time): 8 operations per interior pair (two weight multiplies,
+    add, multiply by 1/8, add) and 10 at the boundary pairs; the slab
+    kernels of 32^3 FP64 blocks use compile-time rows on every line."""
     total, frac, n, level = 0.0, 1.0, B, 0
     while n >= 8:
         m = n // 2
         run_time = (m - 2) * 8 + 2 * 10
         compile_time = (m - 2) * 6 + 2 * 10
-        lines = 2 * run_time + compile_time if level == 0 else 3 * compile_time
+        if level == 0 and xy_run_time:
+            lines = 2 * run_time + compile_time
+        else:
+            lines = 3 * compile_time
         total += frac * lines / n
         n //= 2
         frac /= 8
@@ -303,15 +307,12 @@ def _w3ai_fp64_ops_per_element(B: int) -> float:
     return total
 
 
-def fp64(n: int = 768, kind: str = "w3ai", eps: float = 1e-3, reps: int = 10, seed: int = 2001):
-    """The FP64 case: 768^3 density field in 16^3 blocks.  GB300's FP64 rate
-    is low enough that this path is bound by the FP64 pipe, not by HBM; the
-    FP64 rate is measured here with a probe kernel (independent DFMA chains)."""
+def _fp64_case(f, B: int, kind: str, eps: float, reps: int):
+    """Compress / decompress times (ms) and stream bytes of field f."""
     import ctypes as C
     import torch
-    f = torch.from_numpy(inputs.cavitation("rho", n, np.float64, seed=seed)).cuda()
     nbytes = f.numel() * 8
-    p = cz.params_for(tuple(f.shape), True, 16, kind, eps)
+    p = cz.params_for(tuple(f.shape), True, B, kind, eps)
     cap = cz.cz_compress_bound(p)
     out = torch.empty(cap, dtype=torch.uint8, device="cuda")
     ws = torch.empty(cz.cz_workspace_size(p), dtype=torch.uint8, device="cuda")
@@ -329,19 +330,37 @@ def fp64(n: int = 768, kind: str = "w3ai", eps: float = 1e-3, reps: int = 10, se
     def dec():
         assert cz.lib().cz_decompress(out.data_ptr(), ln, hdr, rec.data_ptr(), nbytes, ws.data_ptr(), ws.numel(), s) == cz.OK
 
-    def timed(fn):
-        for _ in range(2):
-            fn()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+    c_ms, d_ms = _timed(comp, reps), _timed(dec, reps)
+    torch.cuda.synchronize()
+    err = float((rec - f).abs().max())
+    del out, ws, rec
+    return c_ms, d_ms, ln, err
 
-    c_ms, d_ms = timed(comp), timed(dec)
+
+def _timed(fn, reps):
+    import torch
+    for _ in range(2):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def fp64(n: int = 768, kind: str = "w3ai", eps: float = 1e-3, reps: int = 10, seed: int = 2001):
+    """The FP64 case: 768^3 density field in 16^3 blocks, and the same field
+    in 32^3 blocks (the slab kernels).  GB300's FP64 rate is low enough that
+    this path is bound by the FP64 pipe, not by HBM; the FP64 rate is
+    measured here with a probe kernel (independent DFMA chains)."""
+    import ctypes as C
+    import torch
+    f = torch.from_numpy(inputs.cavitation("rho", n, np.float64, seed=seed)).cuda()
+    nbytes = f.numel() * 8
+    s = torch.cuda.current_stream().cuda_stream
     # FP64 probe: DFMA instructions per second
     L = cz.lib()
     L.czi_fp64_probe.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
@@ -353,28 +372,37 @@ def fp64(n: int = 768, kind: str = "w3ai", eps: float = 1e-3, reps: int = 10, se
     def probe():
         assert L.czi_fp64_probe(grid, thr, iters, sink.data_ptr(), s) == cz.OK
 
-    p_ms = timed(probe)
+    p_ms = _timed(probe, reps)
     dfma_per_s = grid * thr * iters * 8 / (p_ms * 1e-3)
-    ops = _w3ai_fp64_ops_per_element(16) + 1.0  # + the significance compare
-    comp_ops_per_s = ops * f.numel() / (c_ms * 1e-3)
-    dec_ops_per_s = _w3ai_fp64_ops_per_element(16) * f.numel() / (d_ms * 1e-3)
-    peaks = None
     try:
         import json, os
         with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")) as fh:
             peaks = float(json.load(fh)["hbm_gbs"])
     except Exception:
         peaks = 6800.0
-    return {
+
+    def case(B):
+        c_ms, d_ms, ln, err = _fp64_case(f, B, kind, eps, reps)
+        dops = _w3ai_fp64_ops_per_element(B, xy_run_time=(B != 32))
+        ops = dops + 1.0  # + the significance compare
+        return {
+            "compress_ms": c_ms, "decompress_ms": d_ms,
+            "compress_gbs": nbytes / c_ms / 1e6, "decompress_gbs": nbytes / d_ms / 1e6,
+            "cr": nbytes / ln, "linf": err,
+            "hbm_frac_compress": (2 * nbytes + ln) / (c_ms * 1e-3) / 1e9 / peaks,
+            "hbm_frac_decompress": (ln + nbytes) / (d_ms * 1e-3) / 1e9 / peaks,
+            "fp64_ops_per_element": {"compress": ops, "decompress": dops},
+            "fp64_pipe_frac_compress": ops * f.numel() / (c_ms * 1e-3) / dfma_per_s,
+            "fp64_pipe_frac_decompress": dops * f.numel() / (d_ms * 1e-3) / dfma_per_s,
+        }
+
+    r = case(16)
+    r32 = case(32)
+    r.update({
         "workload": f"rho-field {n}^3 FP64, 16^3 blocks, {kind}, eps=1e-3*range, stage 2 on, range computed",
-        "compress_ms": c_ms, "decompress_ms": d_ms,
-        "compress_gbs": nbytes / c_ms / 1e6, "decompress_gbs": nbytes / d_ms / 1e6,
-        "cr": nbytes / ln,
-        "hbm_frac_compress": (2 * nbytes + ln) / (c_ms * 1e-3) / 1e9 / peaks,
-        "hbm_frac_decompress": (ln + nbytes) / (d_ms * 1e-3) / 1e9 / peaks,
         "fp64_probe_dfma_per_s": dfma_per_s,
-        "fp64_ops_per_element": {"compress": ops, "decompress": _w3ai_fp64_ops_per_element(16)},
-        "fp64_pipe_frac_compress": comp_ops_per_s / dfma_per_s,
-        "fp64_pipe_frac_decompress": dec_ops_per_s / dfma_per_s,
         "bound": "fp64 alu",
-    }
+        "blocks_32": dict(r32, workload=f"the same field in 32^3 blocks (slab kernels: the block in global "
+                                         f"memory, L2-resident)"),
+    })
+    return r

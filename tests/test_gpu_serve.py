@@ -9,7 +9,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-def _mix(seed, n=24):
+def _mix(seed, n=24, f64_block=16):
     from paper_1903_07761_gb300 import inputs
     rng = np.random.default_rng(seed)
     out = []
@@ -18,7 +18,7 @@ def _mix(seed, n=24):
         e = int(32 * rng.integers(1, 5))
         dims = (e, e, e)
         f = inputs.field(inputs.P, dims, np.float64 if f64 else np.float32, seed=4000 + i, nbubbles=4)
-        out.append((f, 16 if f64 else 32, float(rng.choice([1e-3, 1e-4])), "w3ai" if i % 2 else "w4"))
+        out.append((f, f64_block if f64 else 32, float(rng.choice([1e-3, 1e-4])), "w3ai" if i % 2 else "w4"))
     return out
 
 
@@ -28,11 +28,12 @@ def _alone(cz, torch, t, B, e, kind):
     return out[:int(nb.item())].cpu().numpy().tobytes()
 
 
-@pytest.mark.parametrize("budget_mib,streams", [(2048, 4), (96, 2)])
-def test_mixed_requests_equal_alone(budget_mib, streams):
+@pytest.mark.parametrize("budget_mib,streams,f64_block", [(2048, 4, 16), (96, 2, 16), (2048, 4, 32)])
+def test_mixed_requests_equal_alone(budget_mib, streams, f64_block):
+    """f64_block = 32: the FP64 requests take 32^3 blocks (the slab kernels)."""
     import torch
     from paper_1903_07761_gb300 import cz
-    items = _mix(1)
+    items = _mix(1, f64_block=f64_block)
     tens = [torch.from_numpy(f).cuda() for f, _, _, _ in items]
     alone = [_alone(cz, torch, t, B, e, k) for t, (_, B, e, k) in zip(tens, items)]
     # decompress requests of the first few streams, mixed in
