@@ -362,7 +362,8 @@ int czo_read_header(const uint8_t *in, size_t n, czo_params *p, double *t,
 static int check_params(const czo_params *p)
 {
   int B = p->block;
-  if (B != 8 && B != 16 && B != 32) return CZO_ERR_ARG;
+  /* block edges of the paper's block-size study (Sec. 3, Exp. 3) */
+  if (B != 8 && B != 16 && B != 32 && B != 64) return CZO_ERR_ARG;
   if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0) return CZO_ERR_ARG;
   if (p->nx % B || p->ny % B || p->nz % B) return CZO_ERR_ARG;
   if (p->dtype != CZO_F32 && p->dtype != CZO_F64) return CZO_ERR_ARG;

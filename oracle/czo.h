@@ -60,7 +60,7 @@ enum { CZO_FLAG_ZERO4 = 2, CZO_FLAG_ZERO8 = 4 };
 
 typedef struct czo_params {
   int32_t nx, ny, nz; /* field dims in elements, C order [nz][ny][nx]        */
-  int32_t block;      /* cubic block edge B: 8, 16 or 32                       */
+  int32_t block;      /* cubic block edge B: 8, 16, 32 or 64                   */
   int32_t dtype;      /* CZO_F32 / CZO_F64                                     */
   int32_t kind;       /* CZO_W4 / CZO_W4LI / CZO_W3AI                          */
   int32_t eps_mode;   /* CZO_EPS_REL: t = eps*range ; CZO_EPS_ABS: t = eps     */

@@ -164,11 +164,16 @@ def test_w4li_keeps_w4_details():
 
 
 # ------------------------------------------------------------- polynomials
-def poly_field(B, deg, rng):
+def poly_field(B, deg, rng, total=False):
+    """Integer-coefficient polynomial of degree <= deg in each coordinate
+    (total: of total degree <= deg, so that at B = 64 every sample and every
+    product the transform forms stays below 2^53 and is exact in fp64)."""
     z, y, x = np.meshgrid(*(np.arange(B, dtype=float),) * 3, indexing="ij")
     f = np.zeros((B, B, B))
     for _ in range(6):
         a, b, c = rng.integers(0, deg + 1, 3)
+        while total and a + b + c > deg:
+            a, b, c = rng.integers(0, deg + 1, 3)
         f += rng.integers(-3, 4) * x ** a * y ** b * z ** c
     return f + rng.integers(-50, 50)
 
@@ -180,12 +185,12 @@ def detail_mask(B):
     return m
 
 
-@pytest.mark.parametrize("B", [8, 16, 32])
+@pytest.mark.parametrize("B", [8, 16, 32, 64])
 @pytest.mark.parametrize("kind", KINDS)
 def test_polynomial_reproduction_gives_zero_details(B, kind):
     rng = np.random.default_rng(B * 10 + kind)
     deg = 2 if kind == O.W3AI else 3
-    f = poly_field(B, deg, rng)
+    f = poly_field(B, deg, rng, total=B == 64)
     c = O.fwd3d(kind, f)
     assert np.all(c[detail_mask(B)] == 0.0)
     # one degree more is not reproduced: the pin is tight
@@ -268,6 +273,26 @@ def test_huge_eps_keeps_only_coarse_and_decodes_pure_prediction(kind):
 def test_huge_eps_on_cubic_field_is_exact():
     f = poly_field(16, 3, np.random.default_rng(14))
     s = O.compress(f, 16, O.W4, 1e300, eps_mode=O.EPS_ABS)
+    np.testing.assert_array_equal(O.decompress(s), f)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_64_cubed_blocks_keep_no_details_of_a_reproduced_polynomial(kind):
+    """64^3 blocks (Sec. 3, Exp. 3): four levels down to the 4^3 coarse
+    cube.  A polynomial the wavelet reproduces (cubic for W4 / W4li,
+    quadratic for W3ai, on dyadic integer samples) has zero details, so at
+    any threshold every block's chunk holds nnz = 0 and the 64 coarse values
+    alone decode the field exactly."""
+    rng = np.random.default_rng(640 + kind)
+    f = poly_field(64, 2 if kind == O.W3AI else 3, rng, total=True)
+    f = np.concatenate([f, f[::-1].copy()], axis=0)  # two blocks along z
+    s = O.compress(f, 64, kind, 1e-9, eps_mode=O.EPS_ABS, stage2=False)
+    assert O.read_header(s)["block"] == 64
+    data0, offs = O.chunk_table(s)
+    assert len(offs) == 3
+    for b in range(2):
+        assert np.frombuffer(s, np.uint32, count=1, offset=data0 + int(offs[b]))[0] == 0
+        assert offs[b + 1] - offs[b] == 8 + 64 * 8 + 64 ** 3 // 8  # header, coarse values, empty mask
     np.testing.assert_array_equal(O.decompress(s), f)
 
 
@@ -379,7 +404,7 @@ def test_strict_norm_closed_form_w3ai_b8():
 
 
 @pytest.mark.parametrize("kind", KINDS)
-@pytest.mark.parametrize("B", [8, 16, 32])
+@pytest.mark.parametrize("B", [8, 16, 32, 64])
 def test_strict_mode_keeps_error_below_nominal_threshold(kind, B):
     rng = np.random.default_rng(100 * B + kind)
     f = np.cumsum(np.cumsum(rng.standard_normal((B, 2 * B, B)), axis=2), axis=1)
