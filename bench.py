@@ -411,9 +411,9 @@ def run_gpu(args, rank, world, local_rank):
         for z in (0, 4, 8):
             bit_zeroing[f"z{z}"] = measure(cz.params_for(tuple(field.shape), False, B, kind, args.eps, cz.EPS_REL,
                                                          True, -1.0, zero_bits=z))
-        # block-size study (Sec. 3): 8^3 / 16^3 / 32^3 blocks of the same field
+        # block-size study (Sec. 3, Exp. 3): 8^3 / 16^3 / 32^3 / 64^3 blocks of the same field
         block_sizes = {"kind": args.kind, "eps": args.eps}
-        for bb in (8, 16, 32):
+        for bb in (8, 16, 32, 64):
             pb = cz.params_for(tuple(field.shape), False, bb, kind, args.eps, cz.EPS_REL, True, -1.0)
             need = max(cz.cz_workspace_size(pb), ws.numel())
             ws_b = ws if need == ws.numel() else torch.empty(need, dtype=torch.uint8, device=dev)

@@ -87,7 +87,7 @@ enum {
 
 typedef struct cz_params {
   int32_t nx, ny, nz; /* field dims in elements; each a multiple of block   */
-  int32_t block;      /* cubic block edge B: 8, 16 or 32                    */
+  int32_t block;      /* cubic block edge B: 8, 16, 32 or 64 (64: F32 only) */
   int32_t dtype;      /* CZ_F32 or CZ_F64                                   */
   int32_t kind;       /* CZ_W4, CZ_W4LI or CZ_W3AI                          */
   int32_t eps_mode;   /* CZ_EPS_REL (default) or CZ_EPS_ABS                 */

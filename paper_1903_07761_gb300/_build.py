@@ -27,7 +27,7 @@ NVFLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler"
            "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 # (type, block) instantiations of the kernels
-INST = [("float", "f32", 8), ("float", "f32", 16), ("float", "f32", 32),
+INST = [("float", "f32", 8), ("float", "f32", 16), ("float", "f32", 32), ("float", "f32", 64),
         ("double", "f64", 8), ("double", "f64", 16), ("double", "f64", 32)]
 
 

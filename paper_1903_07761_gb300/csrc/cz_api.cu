@@ -32,8 +32,9 @@ int check(const cz_params *p, Shape *sh)
 {
   if (!p) return CZ_ERR_ARG;
   const int B = p->block;
-  if (B != 8 && B != 16 && B != 32) return CZ_ERR_ARG;
+  if (B != 8 && B != 16 && B != 32 && B != 64) return CZ_ERR_ARG;
   if (p->dtype != CZ_F32 && p->dtype != CZ_F64) return CZ_ERR_ARG;
+  if (B == 64 && p->dtype != CZ_F32) return CZ_ERR_ARG;  // 64^3 blocks: FP32 only
   if (p->kind < CZ_W4 || p->kind > CZ_W3AI) return CZ_ERR_ARG;
   if (p->eps_mode != CZ_EPS_REL && p->eps_mode != CZ_EPS_ABS) return CZ_ERR_ARG;
   if (p->stage2 != 0 && p->stage2 != 1) return CZ_ERR_ARG;
@@ -53,7 +54,7 @@ int check(const cz_params *p, Shape *sh)
     sh->nby = p->ny / B;
     sh->nbz = p->nz / B;
     sh->nblocks = (int)nb;
-    sh->L = B == 8 ? 1 : (B == 16 ? 2 : 3);
+    sh->L = B == 8 ? 1 : (B == 16 ? 2 : (B == 32 ? 3 : 4));
     sh->es = p->dtype == CZ_F64 ? 8 : 4;
     sh->data0 = (HEADER_BYTES + 8ull * (nb + 1) + 15) / 16 * 16;
   }
@@ -126,18 +127,18 @@ double synthesis_norm_uncached(int kind, int B)
 {
   int L = 0;
   while ((B >> L) > 4) ++L;
-  double R[3][32], E[3][32];
+  double R[4][64], E[4][64];
   for (int l = 0; l < L; ++l) {
     const int nl = B >> l;
     for (int x = 0; x < B; ++x) R[l][x] = E[l][x] = 0.0;
     for (int j = 0; j < nl; ++j) {
-      double w[32] = {0};
+      double w[64] = {0};
       w[j] = 1.0;
       for (int k = l; k >= 0; --k) {
         const int nk = B >> k;
         inv1d_host(kind, w, nk);
         if (k > 0) {
-          double u[32] = {0};
+          double u[64] = {0};
           for (int i = 0; i < nk; ++i) u[2 * i] = w[i];
           for (int i = 0; i < 2 * nk; ++i) w[i] = u[i];
         }
@@ -166,8 +167,8 @@ double threshold_divisor(const cz_params *p)
 {
   if (p->bound_mode != CZ_BOUND_STRICT) return 1.0;
   static std::mutex mu;
-  static double cache[3][3] = {{0}};
-  const int bi = p->block == 8 ? 0 : (p->block == 16 ? 1 : 2);
+  static double cache[3][4] = {{0}};
+  const int bi = p->block == 8 ? 0 : (p->block == 16 ? 1 : (p->block == 32 ? 2 : 3));
   std::lock_guard<std::mutex> lock(mu);
   double &c = cache[p->kind][bi];
   if (c == 0.0) c = synthesis_norm_uncached(p->kind, p->block);
@@ -199,7 +200,8 @@ Lanes lanes_for(const cz_params &p)
   if (p.dtype == CZ_F32) {
     if (p.block == 8) return fast ? CZ_LANES(f32_b8_fast) : CZ_LANES(f32_b8);
     if (p.block == 16) return fast ? CZ_LANES(f32_b16_fast) : CZ_LANES(f32_b16);
-    return fast ? CZ_LANES(f32_b32_fast) : CZ_LANES(f32_b32);
+    if (p.block == 32) return fast ? CZ_LANES(f32_b32_fast) : CZ_LANES(f32_b32);
+    return fast ? CZ_LANES(f32_b64_fast) : CZ_LANES(f32_b64);
   }
   if (p.block == 8) return fast ? CZ_LANES(f64_b8_fast) : CZ_LANES(f64_b8);
   if (p.block == 16) return fast ? CZ_LANES(f64_b16_fast) : CZ_LANES(f64_b16);
@@ -218,7 +220,11 @@ int sm_count()
 int grid_for(const cz_params *p, const Shape &sh, int which)
 {
   const Lanes L = lanes_for(*p);
-  const int occ = L.occupancy(p->kind, which);
+  int occ = L.occupancy(p->kind, which);
+  // kernels that hold a block or a large payload in global scratch (one
+  // scratch block per CTA): at most two CTAs per SM, which bounds the
+  // scratch of the large stage-2 kernels
+  if (L.scratch_bytes() && (which == 3 || which == 5) && occ > 2) occ = 2;
   const long long g = (long long)sm_count() * (occ > 0 ? occ : 1);
   return (int)(g < sh.nblocks ? g : sh.nblocks);
 }
@@ -313,9 +319,10 @@ bool make_tile_map(CUtensorMap *tm, const cz_params *p, const void *d_field)
   const cuuint64_t es = p->dtype == CZ_F64 ? 8 : 4;
   const cuuint64_t dims[3] = {(cuuint64_t)p->nx, (cuuint64_t)p->ny, (cuuint64_t)p->nz};
   const cuuint64_t strides[2] = {(cuuint64_t)p->nx * es, (cuuint64_t)p->nx * p->ny * es};
-  // (the FP64 32^3 kernels address the field directly and do not use the
-  // map: a box of 8 z-planes keeps it within the encoder's limits)
-  const cuuint32_t bz = (p->dtype == CZ_F64 && p->block == 32) ? 8u : (cuuint32_t)p->block;
+  // (the kernels of FP64 32^3 and of 64^3 blocks address the field directly
+  // and do not use the map: a box of 8 z-planes keeps it within the
+  // encoder's limits)
+  const cuuint32_t bz = ((p->dtype == CZ_F64 && p->block == 32) || p->block == 64) ? 8u : (cuuint32_t)p->block;
   const cuuint32_t box[3] = {(cuuint32_t)p->block, (cuuint32_t)p->block, bz};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r =
@@ -575,7 +582,7 @@ int compress_batch_impl(int n, const cz_params *p, const void *const *d_fields, 
     pa.cnorm = a.cnorm;
     pa.nblocks = w.nblocks;
     pa.block = p0.block;
-    pa.levels = p0.block == 8 ? 1 : (p0.block == 16 ? 2 : 3);
+    pa.levels = p0.block == 8 ? 1 : (p0.block == 16 ? 2 : (p0.block == 32 ? 3 : 4));
     pa.stage2 = p0.stage2;
     pa.kind = p0.kind;
     pa.dtype = p0.dtype;

@@ -155,17 +155,18 @@ __host__ __device__ constexpr T li_weight(int m, int j, int t)
   return (T)f.n / (T)f.d;  // one correctly rounded quotient in T
 }
 
-// table for runtime lookups: levels with m = 4, 8, 16 coarse values
+// table for runtime lookups: levels with m = 4, 8, 16, 32 coarse values
+// (lines of up to 64 points)
 template <typename T>
 struct LiTable {
-  T u[3][16][3];
+  T u[4][32][3];
 };
 
 template <typename T>
 __host__ __device__ constexpr LiTable<T> make_li_table()
 {
   LiTable<T> tb{};
-  for (int mi = 0; mi < 3; ++mi) {
+  for (int mi = 0; mi < 4; ++mi) {
     const int m = 4 << mi;
     for (int j = 0; j < m; ++j)
       for (int t = 0; t < 3; ++t) tb.u[mi][j][t] = li_weight<T>(m, j, t);
@@ -181,12 +182,12 @@ __device__ __forceinline__ T li_lookup(int m, int j, int t);
 template <>
 __device__ __forceinline__ float li_lookup<float>(int m, int j, int t)
 {
-  return c_li_f.u[m == 4 ? 0 : (m == 8 ? 1 : 2)][j][t];
+  return c_li_f.u[m == 4 ? 0 : (m == 8 ? 1 : (m == 16 ? 2 : 3))][j][t];
 }
 template <>
 __device__ __forceinline__ double li_lookup<double>(int m, int j, int t)
 {
-  return c_li_d.u[m == 4 ? 0 : (m == 8 ? 1 : 2)][j][t];
+  return c_li_d.u[m == 4 ? 0 : (m == 8 ? 1 : (m == 16 ? 2 : 3))][j][t];
 }
 
 // ------------------------------------------------------------ W3ai rows

@@ -22,7 +22,7 @@ using namespace czp;
 namespace {
 
 using G = G2<CZ_T, CZ_B>;
-using SGi = SG<CZ_T, 32>;  // slab geometry (used only when G::SLAB)
+using SGi = SG<CZ_T, CZ_B>;  // slab geometry (used only when G::SLAB)
 
 // raise the dynamic shared-memory limit of kernel KERN once per device
 template <auto KERN>

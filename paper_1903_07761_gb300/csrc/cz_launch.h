@@ -36,12 +36,14 @@ struct StageMaps;
 CZ_DECLARE_LAUNCHERS(f32_b8)
 CZ_DECLARE_LAUNCHERS(f32_b16)
 CZ_DECLARE_LAUNCHERS(f32_b32)
+CZ_DECLARE_LAUNCHERS(f32_b64)
 CZ_DECLARE_LAUNCHERS(f64_b8)
 CZ_DECLARE_LAUNCHERS(f64_b16)
 CZ_DECLARE_LAUNCHERS(f64_b32)
 CZ_DECLARE_LAUNCHERS(f32_b8_fast)
 CZ_DECLARE_LAUNCHERS(f32_b16_fast)
 CZ_DECLARE_LAUNCHERS(f32_b32_fast)
+CZ_DECLARE_LAUNCHERS(f32_b64_fast)
 CZ_DECLARE_LAUNCHERS(f64_b8_fast)
 CZ_DECLARE_LAUNCHERS(f64_b16_fast)
 CZ_DECLARE_LAUNCHERS(f64_b32_fast)

@@ -259,7 +259,13 @@ struct G2 {
   static constexpr int NK = B / 2;  // row pairs (y = 2k, 2k + 1)
   static constexpr int ZH = B / 2;  // z-values of one half column
   static constexpr int MH = B / 4;  // z-pairs of one half column
-  static constexpr int L = (B == 8) ? 1 : (B == 16) ? 2 : 3;
+  static constexpr int L = (B == 8) ? 1 : (B == 16) ? 2 : (B == 32) ? 3 : 4;
+  // FP64 32^3 blocks (256 KiB) and 64^3 blocks (1 MiB FP32) fit neither
+  // the registers nor the shared memory of one CTA: they take the slab
+  // kernels (cz_slab.cuh), whose block lives in global memory (a scratch
+  // block per CTA, L2-resident), and large stage-2 payloads are shuffled in
+  // global scratch too
+  static constexpr bool SLAB = (sizeof(T) == 8 && B == 32) || B == 64;
   static constexpr int Q = B / 4;
   static constexpr int ES = (int)sizeof(T);
   static constexpr int LGES = ES == 8 ? 3 : 2;
@@ -290,8 +296,10 @@ struct G2 {
   // staging slot of one block: [nnz | 0 | raw payload]; the finished
   // stage-2 chunk replaces it in place and is at most 12 bytes longer than
   // the payload (every coded run of >= 2 zero words saves at least one
-  // word; one trailing token), so a slot holds payload + 12 bytes
-  static constexpr int PSLOT = (PMAX + 12 + 15) / 16 * 16;
+  // word; one trailing token), plus one token per 65535 literal words that
+  // a payload of more than 65535 words may split off (slab lanes only), so
+  // a slot holds payload + 12 + 4 * (words / 65535) bytes
+  static constexpr int PSLOT = (PMAX + 12 + 4 * (WMAX / 65535) + 15) / 16 * 16;
   // stage-2 kernels: the shuffled payload lives in shared memory; payloads
   // of up to SHCAP bytes go to small CTAs, larger ones to large CTAs
   static constexpr int SHCAP = PMAX_AL < 16384 ? PMAX_AL : 16384;
@@ -301,7 +309,7 @@ struct G2 {
   static constexpr int SMEM_S2B = PMAX_AL + 4 * NBWMAX * 4;
   // stage-2 inverse kernels: payload + three per-token arrays
   static constexpr int SMEM_U = SHCAP + 3 * 128 * 4;
-  static constexpr int SMEM_UB = (ES == 8 && B == 32 ? 0 : PMAX_AL) + 3 * 512 * 4;
+  static constexpr int SMEM_UB = (SLAB ? 0 : PMAX_AL) + 3 * 512 * 4;
   // dense kernels: cube | plane | halo
   static constexpr int SMEM_DN0 = CUBE_AL + PLANE + HALO;
   // decompress: row offsets, later the cube | two payload buffers | output
@@ -317,11 +325,6 @@ struct G2 {
   static constexpr int OTB0 = TILE > PLANE + HALO ? TILE : PLANE + HALO;
   static constexpr int OTB = (OTB0 + 127) / 128 * 128;
   static constexpr int SMEM_D = R2D + NPB * PBCAP + OTB;
-  // FP64 32^3 blocks (256 KiB) fit neither the registers nor the shared
-  // memory of one CTA: they take the slab kernels (cz_slab.cuh), whose
-  // block lives in global memory (a scratch block per CTA, L2-resident),
-  // and large stage-2 payloads are shuffled in global scratch too
-  static constexpr bool SLAB = ES == 8 && B == 32;
   static constexpr int SCRATCH = SLAB ? (PMAX_AL > TILE ? PMAX_AL : TILE) : 0;  // per CTA
   static_assert(HP == NK && NK == ZH && NT == HP * NK * 2, "thread grid");
   static_assert(HALO >= ROWB + MASKBP, "row offsets and mask rows fit the halo area");

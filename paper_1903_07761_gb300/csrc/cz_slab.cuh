@@ -1,9 +1,9 @@
-// cz_slab.cuh -- FP64 blocks of 32^3 (256 KiB): kernels whose block lives in
-// global memory.
+// cz_slab.cuh -- blocks of 32^3 FP64 (256 KiB) and 64^3 FP32 (1 MiB):
+// kernels whose block lives in global memory.
 //
-// A 32^3 FP64 block holds more bytes than a CTA's shared memory and than
-// the register file of an SM, so the register-resident kernels of
-// cz_pair.cuh cannot take it.  Here a CTA works on a block held in global
+// Such a block holds more bytes than a CTA's shared memory and than the
+// register file of an SM, so the register-resident kernels of cz_pair.cuh
+// cannot take it.  Here a CTA works on a block held in global
 // memory: its own scratch block when compressing (written by the first
 // pass, which reads the field; L2-resident, one per CTA), the output block
 // of the field itself when decompressing.  The transform is the same as
@@ -11,14 +11,15 @@
 // z-lines of the current coarse cube): every pass gives one thread a whole
 // line, which it transforms in registers with the line functions of
 // cz_device.cuh (fwd_reg / inv_reg, the same rounded operations in the same
-// order as the oracle), and writes back in place.  The 16^3 cube of the
-// coarser levels moves to shared memory and takes the cube passes of
-// cz_pair.cuh.  Significance, mask rows and compaction go one warp per
+// order as the oracle), and writes back in place.  The last two levels
+// (edges 16 and 8) move to a 16^3 cube in shared memory and take the cube
+// passes of cz_pair.cuh.  Significance, mask rows and compaction go one warp per
 // x-row (lane = x): a ballot is the row's mask word.
 //
 // GB300's FP64 pipe is far slower than its FP32 pipe, so FP64 blocks are
 // bound by FP64 instructions, not by memory: the extra L2 traffic of the
-// global block costs little.  Stage 2 of payloads too large for shared
+// global block costs little.  64^3 blocks serve the block-size study
+// (Sec. 3, Exp. 3).  Stage 2 of payloads too large for shared
 // memory (k_stage2_huge, and k_unstage's large launch) shuffles in a
 // global scratch block per CTA as well.
 #pragma once
@@ -32,18 +33,23 @@ template <typename T, int B>
 struct SG {
   static constexpr int NT = 256;       // threads per CTA
   static constexpr int NW = NT / 32;   // warps
-  static constexpr int N = B / 2;      // edge of the coarser levels' cube
   static constexpr int ROWS = B * B;   // x-rows of a block
   static constexpr int RPT = ROWS / NT;  // rows per thread in the row scans
+  static constexpr int MWPR = B / 32;  // 32-bit mask words per x-row
   static constexpr int Q = B / 4;      // spacing of the coarse values
   static constexpr int ES = (int)sizeof(T);
   static constexpr int HEAD = 64 * ES + B * B * B / 8;  // coarse values + mask
-  static constexpr int CUBE = N * N * (N + 1) * ES;
+  // the last levels (edge 16 and 8) run on a 16^3 cube in shared memory,
+  // the positions that are multiples of S0 = B / 16
+  static constexpr int NC = 16, S0 = B / NC;
+  static constexpr int CUBE = NC * NC * (NC + 1) * ES;
   static constexpr int CUBE_AL = (CUBE + 127) / 128 * 128;
   // shared memory: cube | mask words | row offsets
-  static constexpr int SMEM = CUBE_AL + 2 * ROWS * 4;
-  static_assert(B == 32, "32-bit mask rows, one warp lane per x");
-  static_assert(ROWS % NT == 0, "whole rows per thread");
+  static constexpr int SMEM = CUBE_AL + ROWS * MWPR * 4 + ROWS * 4;
+  static constexpr int MINB = B == 64 ? 1 : 2;  // CTAs per SM (registers: a line of B values)
+  // (checked where a slab kernel is instantiated: whole 32-bit mask words
+  // per row with the lanes on x, whole rows per thread)
+  static constexpr bool OK = (B == 32 || B == 64) && ROWS % NT == 0;
 };
 
 // element (x, y, z) of a B^3 block inside a dense array
@@ -54,9 +60,9 @@ struct BView {
   __device__ __forceinline__ T &at(int x, int y, int z) const { return p[z * sz + y * sy + x]; }
 };
 
-// ---- level-0 passes: one line per thread, lines dealt round robin
-// x-lines (rows): read from src (the field, or the block itself), written
-// to dst; rows are contiguous, so they move as 16-byte vectors
+// ---- the finest x-lines (rows): read from src (the field, or the block
+// itself), written to dst; rows are contiguous, so they move as 16-byte
+// vectors
 template <typename T, int B, int KIND, bool FWD, int NT>
 __device__ __forceinline__ void slab_x(const T *src, long long ssy, long long ssz, const BView<T> &dst)
 {
@@ -87,38 +93,41 @@ __device__ __forceinline__ void slab_x(const T *src, long long ssy, long long ss
   }
 }
 
-// y-lines (AXIS 1, thread per (x, z)) or z-lines (AXIS 2, thread per (x, y)),
-// consecutive threads on consecutive x; W4 changes only the odd points
-template <typename T, int B, int KIND, bool FWD, int NT, int AXIS>
-__device__ __forceinline__ void slab_yz(const BView<T> &v)
+// ---- one axis of the level of stride S (n = B / S points per line): one
+// line per thread, lines dealt round robin; for y- and z-lines consecutive
+// threads take consecutive x.  W4 changes only the odd points.
+template <typename T, int B, int KIND, bool FWD, int NT, int AXIS, int S>
+__device__ __forceinline__ void slab_pass(const BView<T> &v)
 {
-  const long long st = AXIS == 1 ? v.sy : v.sz;
+  constexpr int n = B / S;
+  const long long st = AXIS == 0 ? S : (AXIS == 1 ? S * v.sy : S * v.sz);
 #pragma unroll 1
-  for (int r = threadIdx.x; r < B * B; r += NT) {
-    const int x = r % B, o = r / B;  // o: z for y-lines, y for z-lines
-    T *base = AXIS == 1 ? &v.at(x, 0, o) : &v.at(x, o, 0);
-    T e[B];
+  for (int r = threadIdx.x; r < n * n; r += NT) {
+    const int f = (r % n) * S, g = (r / n) * S;  // the line's two other coordinates
+    T *base = AXIS == 0 ? &v.at(0, f, g) : (AXIS == 1 ? &v.at(f, 0, g) : &v.at(f, g, 0));
+    T e[n];
 #pragma unroll
-    for (int i = 0; i < B; ++i) e[i] = base[i * st];
+    for (int i = 0; i < n; ++i) e[i] = base[i * st];
     if constexpr (FWD)
-      fwd_reg<T, KIND, B, 1>(e);
+      fwd_reg<T, KIND, n, 1>(e);
     else
-      inv_reg<T, KIND, B, 1>(e);
+      inv_reg<T, KIND, n, 1>(e);
 #pragma unroll
-    for (int i = 0; i < B; ++i)
+    for (int i = 0; i < n; ++i)
       if (KIND != W4 || (i & 1)) base[i * st] = e[i];
   }
 }
 
-// the coarser levels: the (B/2)^3 values at even positions -> shared-memory
-// cube -> levels 1.. (cube passes) -> back
-template <typename T, int B, int KIND, bool FWD, int NT>
+// the last levels: the 16^3 values at multiples of S -> shared-memory cube
+// -> cube passes (edges 16 and 8) -> back
+template <typename T, int B, int KIND, bool FWD, int NT, int S>
 __device__ __forceinline__ void slab_cube(const BView<T> &v, T *C)
 {
-  constexpr int N = B / 2;
+  constexpr int N = B / S;
+  static_assert(N == 16, "the shared-memory cube holds the edge-16 level");
   for (int i = threadIdx.x; i < N * N * N; i += NT) {
     const int x = i % N, y = (i / N) % N, z = i / (N * N);
-    C[cidx<N>(x, y, z)] = v.at(2 * x, 2 * y, 2 * z);
+    C[cidx<N>(x, y, z)] = v.at(S * x, S * y, S * z);
   }
   __syncthreads();
   if constexpr (FWD)
@@ -127,51 +136,81 @@ __device__ __forceinline__ void slab_cube(const BView<T> &v, T *C)
     cube_inv<T, N, KIND, NT>(C);
   for (int i = threadIdx.x; i < N * N * N; i += NT) {
     const int x = i % N, y = (i / N) % N, z = i / (N * N);
-    v.at(2 * x, 2 * y, 2 * z) = C[cidx<N>(x, y, z)];
+    v.at(S * x, S * y, S * z) = C[cidx<N>(x, y, z)];
   }
   __syncthreads();
 }
 
-// whole forward transform: field block (src) -> v (every value rewritten)
+// levels of stride S and coarser (the finest x-lines already done when S = 1)
+template <typename T, int B, int KIND, int NT, int S>
+__device__ __forceinline__ void slab_fwd_from(const BView<T> &v, T *C)
+{
+  if constexpr (B / S > 16) {
+    if constexpr (S > 1) {
+      slab_pass<T, B, KIND, true, NT, 0, S>(v);
+      __syncthreads();
+    }
+    slab_pass<T, B, KIND, true, NT, 1, S>(v);
+    __syncthreads();
+    slab_pass<T, B, KIND, true, NT, 2, S>(v);
+    __syncthreads();
+    slab_fwd_from<T, B, KIND, NT, 2 * S>(v, C);
+  } else {
+    slab_cube<T, B, KIND, true, NT, S>(v, C);
+  }
+}
+
+template <typename T, int B, int KIND, int NT, int S>
+__device__ __forceinline__ void slab_inv_from(const BView<T> &v, T *C)
+{
+  if constexpr (B / S > 16) {
+    slab_inv_from<T, B, KIND, NT, 2 * S>(v, C);
+    slab_pass<T, B, KIND, false, NT, 2, S>(v);
+    __syncthreads();
+    slab_pass<T, B, KIND, false, NT, 1, S>(v);
+    __syncthreads();
+    if constexpr (S == 1)
+      slab_x<T, B, KIND, false, NT>(v.p, v.sy, v.sz, v);
+    else
+      slab_pass<T, B, KIND, false, NT, 0, S>(v);
+    __syncthreads();
+  } else {
+    slab_cube<T, B, KIND, false, NT, S>(v, C);
+  }
+}
+
+// whole forward transform: field block (src) -> v (every value rewritten);
+// per level the x-, y- and z-lines (Sec. 2.2)
 template <typename T, int B, int KIND, int NT>
 __device__ __forceinline__ void slab_fwd(const T *src, long long ssy, long long ssz, const BView<T> &v, T *C)
 {
   slab_x<T, B, KIND, true, NT>(src, ssy, ssz, v);
   __syncthreads();
-  slab_yz<T, B, KIND, true, NT, 1>(v);
-  __syncthreads();
-  slab_yz<T, B, KIND, true, NT, 2>(v);
-  __syncthreads();
-  slab_cube<T, B, KIND, true, NT>(v, C);
+  slab_fwd_from<T, B, KIND, NT, 1>(v, C);
 }
 
 // whole inverse transform in place (levels from the coarsest, axes z, y, x)
 template <typename T, int B, int KIND, int NT>
 __device__ __forceinline__ void slab_inv(const BView<T> &v, T *C)
 {
-  slab_cube<T, B, KIND, false, NT>(v, C);
-  slab_yz<T, B, KIND, false, NT, 2>(v);
-  __syncthreads();
-  slab_yz<T, B, KIND, false, NT, 1>(v);
-  __syncthreads();
-  slab_x<T, B, KIND, false, NT>(v.p, v.sy, v.sz, v);
-  __syncthreads();
+  slab_inv_from<T, B, KIND, NT, 1>(v, C);
 }
 
 // ---- compression: the same slot as k_stage1 writes
 //   [nnz | 0 | 64 coarse values | mask row words | kept details in position order]
 // NF = 1: one field described by a; NF > 1: fields of one batched group
 template <typename T, int B, int KIND, int NF>
-__global__ void __launch_bounds__(SG<T, B>::NT, 2) k_stage1_slab(const __grid_constant__ StageMaps<NF> maps,
-                                                                 const FwdArgs a)
+__global__ void __launch_bounds__(SG<T, B>::NT, SG<T, B>::MINB) k_stage1_slab(
+    const __grid_constant__ StageMaps<NF> maps, const FwdArgs a)
 {
+  static_assert(SG<T, B>::OK, "slab geometry: B = 32 or 64");
   using S = SG<T, B>;
   using G = G2<T, B>;
-  constexpr int NT = S::NT, NW = S::NW, Q = S::Q, ES = S::ES, ROWS = S::ROWS, RPT = S::RPT;
+  constexpr int NT = S::NT, NW = S::NW, Q = S::Q, ES = S::ES, ROWS = S::ROWS, RPT = S::RPT, MWPR = S::MWPR;
   extern __shared__ __align__(128) unsigned char smem[];
   T *C = reinterpret_cast<T *>(smem);
-  unsigned *MW = reinterpret_cast<unsigned *>(smem + S::CUBE_AL);  // mask words
-  unsigned *RO = MW + ROWS;                                          // row offsets
+  unsigned *MW = reinterpret_cast<unsigned *>(smem + S::CUBE_AL);  // mask words (MWPR per row)
+  unsigned *RO = MW + ROWS * MWPR;                                   // row offsets
   __shared__ unsigned s_u[40];
   __shared__ T s_t[NF];
 
@@ -210,13 +249,18 @@ __global__ void __launch_bounds__(SG<T, B>::NT, 2) k_stage1_slab(const __grid_co
 
     slab_fwd<T, B, KIND, NT>(src, nx, nx * ny, v, C);
 
-    // ---- mask rows (coarse positions carry no bit), row offsets
+    // ---- mask rows (coarse positions carry no bit; word h of a row holds
+    // x = 32 h + lane), row offsets
     for (int r = wid; r < ROWS; r += NW) {
       const int z = r / B, y = r % B;
-      const T d = v.at(lane, y, z);
-      const bool coarse = (lane % Q == 0) && (y % Q == 0) && (z % Q == 0);
-      const unsigned w = __ballot_sync(FULL, !coarse && keep(d, t));
-      if (lane == 0) MW[r] = w;
+#pragma unroll
+      for (int h = 0; h < MWPR; ++h) {
+        const int x = 32 * h + lane;
+        const T d = v.at(x, y, z);
+        const bool coarse = (x % Q == 0) && (y % Q == 0) && (z % Q == 0);
+        const unsigned w = __ballot_sync(FULL, !coarse && keep(d, t));
+        if (lane == 0) MW[r * MWPR + h] = w;
+      }
     }
     __syncthreads();
     unsigned nnz;
@@ -224,7 +268,9 @@ __global__ void __launch_bounds__(SG<T, B>::NT, 2) k_stage1_slab(const __grid_co
       unsigned loc[RPT], sum = 0;
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
-        loc[q] = __popc(MW[tid * RPT + q]);
+        loc[q] = 0;
+#pragma unroll
+        for (int h = 0; h < MWPR; ++h) loc[q] += __popc(MW[(tid * RPT + q) * MWPR + h]);
         sum += loc[q];
       }
       unsigned ex = block_exsum<NT>(sum, s_u, nnz);
@@ -237,24 +283,33 @@ __global__ void __launch_bounds__(SG<T, B>::NT, 2) k_stage1_slab(const __grid_co
     __syncthreads();
 
     // ---- slot [nnz | 0 | raw payload] -> this CTA's staging arena
+    // (room for the finished stage-2 chunk: payload + 12 bytes + one split
+    // token per 65535 words)
     const int pbytes = S::HEAD + (int)nnz * ES;
     const unsigned long long so = aoff;
-    const unsigned long long slot = (unsigned long long)((pbytes + 12 + 15) & ~15);
+    const unsigned long long slot = (unsigned long long)((pbytes + 12 + 4 * ((pbytes / 4) / 65535) + 15) & ~15);
     const bool ok = so + slot <= a.arena_bytes;
     if (ok) {
       unsigned char *P = arena + so + 8;
       unsigned *MASK = reinterpret_cast<unsigned *>(P + 64 * ES);
-      for (int i = tid; i < ROWS; i += NT) MASK[i] = MW[i];
+      for (int i = tid; i < ROWS * MWPR; i += NT) MASK[i] = MW[i];
       T *COARSE = reinterpret_cast<T *>(P);
       T *VALS = reinterpret_cast<T *>(P + S::HEAD);
       for (int r = wid; r < ROWS; r += NW) {
         const int z = r / B, y = r % B;
-        const unsigned w = MW[r];
         const bool crow = (y % Q == 0) && (z % Q == 0);
-        if (w == 0 && !crow) continue;  // warp-uniform
-        const T d = v.at(lane, y, z);
-        if ((w >> lane) & 1u) VALS[RO[r] + __popc(w & ((1u << lane) - 1u))] = zero_low(d, a.zbits);
-        if (crow && lane % Q == 0) COARSE[((z / Q) * 4 + y / Q) * 4 + lane / Q] = d;
+        unsigned base = RO[r];
+#pragma unroll
+        for (int h = 0; h < MWPR; ++h) {
+          const unsigned w = MW[r * MWPR + h];
+          if (w != 0 || crow) {  // warp-uniform
+            const int x = 32 * h + lane;
+            const T d = v.at(x, y, z);
+            if ((w >> lane) & 1u) VALS[base + __popc(w & ((1u << lane) - 1u))] = zero_low(d, a.zbits);
+            if (crow && x % Q == 0) COARSE[((z / Q) * 4 + y / Q) * 4 + x / Q] = d;
+          }
+          base += __popc(w);
+        }
       }
     }
     if (tid == 0) {
@@ -277,11 +332,12 @@ __global__ void __launch_bounds__(SG<T, B>::NT, 2) k_stage1_slab(const __grid_co
 // ---- decompression, in place in the output block (the field, or a tile of
 // the random-access output)
 template <typename T, int B, int KIND>
-__global__ void __launch_bounds__(SG<T, B>::NT, 2) k_decompress_slab(const InvArgs a)
+__global__ void __launch_bounds__(SG<T, B>::NT, SG<T, B>::MINB) k_decompress_slab(const InvArgs a)
 {
+  static_assert(SG<T, B>::OK, "slab geometry: B = 32 or 64");
   using S = SG<T, B>;
   using G = G2<T, B>;
-  constexpr int NT = S::NT, NW = S::NW, Q = S::Q, ES = S::ES, ROWS = S::ROWS, RPT = S::RPT;
+  constexpr int NT = S::NT, NW = S::NW, Q = S::Q, ES = S::ES, ROWS = S::ROWS, RPT = S::RPT, MWPR = S::MWPR;
   extern __shared__ __align__(128) unsigned char smem[];
   T *C = reinterpret_cast<T *>(smem);
   unsigned *RO = reinterpret_cast<unsigned *>(smem + S::CUBE_AL);  // row offsets
@@ -313,7 +369,7 @@ __global__ void __launch_bounds__(SG<T, B>::NT, 2) k_decompress_slab(const InvAr
         }
         const unsigned long long o0 = tab[c], o1 = tab[c + 1];
         const unsigned long long avail = a.in_bytes - a.data0;
-        // chunks of FP64 payloads are whole numbers of 8-byte words
+        // chunks are whole numbers of elements (8-byte words for FP64)
         if (bad || o0 > o1 || o1 > avail || o1 - o0 < 8 || (o0 & (ES - 1)) || ((o1 - o0) & 3)) {
           bad = 1;
         } else {
@@ -337,16 +393,21 @@ __global__ void __launch_bounds__(SG<T, B>::NT, 2) k_decompress_slab(const InvAr
     const unsigned *MASK = reinterpret_cast<const unsigned *>(P + 64 * ES);
     if (!bad0) {
       // row populations -> row offsets; coarse positions carry no mask bit
+      // (cm: their bits within each of a row's words)
       unsigned loc[RPT], sum = 0;
       unsigned cm = 0;
 #pragma unroll
-      for (int x = 0; x < B; x += Q) cm |= 1u << x;
+      for (int x = 0; x < 32; x += Q) cm |= 1u << x;
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int r = tid * RPT + q, z = r / B, y = r % B;
-        const unsigned w = MASK[r];
-        if ((z % Q) == 0 && (y % Q) == 0 && (w & cm)) atomicOr(&s_badx, 1u);
-        loc[q] = __popc(w);
+        loc[q] = 0;
+#pragma unroll
+        for (int h = 0; h < MWPR; ++h) {
+          const unsigned w = MASK[r * MWPR + h];
+          if ((z % Q) == 0 && (y % Q) == 0 && (w & cm)) atomicOr(&s_badx, 1u);
+          loc[q] += __popc(w);
+        }
         sum += loc[q];
       }
       unsigned tot;
@@ -370,13 +431,19 @@ __global__ void __launch_bounds__(SG<T, B>::NT, 2) k_decompress_slab(const InvAr
     const T *VALS = reinterpret_cast<const T *>(P + S::HEAD);
     for (int r = wid; r < ROWS; r += NW) {
       const int z = r / B, y = r % B;
-      T d = T(0);
-      if (!bad) {
-        const unsigned w = MASK[r];
-        if ((w >> lane) & 1u) d = VALS[RO[r] + __popc(w & ((1u << lane) - 1u))];
-        if ((y % Q) == 0 && (z % Q) == 0 && (lane % Q) == 0) d = COARSE[((z / Q) * 4 + y / Q) * 4 + lane / Q];
+      unsigned base = bad ? 0u : RO[r];
+#pragma unroll
+      for (int h = 0; h < MWPR; ++h) {
+        const int x = 32 * h + lane;
+        T d = T(0);
+        if (!bad) {
+          const unsigned w = MASK[r * MWPR + h];
+          if ((w >> lane) & 1u) d = VALS[base + __popc(w & ((1u << lane) - 1u))];
+          if ((y % Q) == 0 && (z % Q) == 0 && (x % Q) == 0) d = COARSE[((z / Q) * 4 + y / Q) * 4 + x / Q];
+          base += __popc(w);
+        }
+        v.at(x, y, z) = d;
       }
-      v.at(lane, y, z) = d;
     }
     __syncthreads();
     if (!bad) slab_inv<T, B, KIND, NT>(v, C);
@@ -388,6 +455,7 @@ __global__ void __launch_bounds__(SG<T, B>::NT, 2) k_decompress_slab(const InvAr
 template <typename T, int B, int KIND, bool FWD>
 __global__ void __launch_bounds__(SG<T, B>::NT) k_dense_slab(const DenseArgs a)
 {
+  static_assert(SG<T, B>::OK, "slab geometry: B = 32 or 64");
   using S = SG<T, B>;
   constexpr int NT = S::NT, NW = S::NW, ROWS = S::ROWS;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -401,7 +469,8 @@ __global__ void __launch_bounds__(SG<T, B>::NT) k_dense_slab(const DenseArgs a)
   if constexpr (FWD) {
     slab_fwd<T, B, KIND, NT>(src, nx, nx * ny, v, C);
   } else {
-    for (int r = wid; r < ROWS; r += NW) v.at(lane, r % B, r / B) = src[(r / B) * nx * ny + (r % B) * nx + lane];
+    for (int r = wid; r < ROWS; r += NW)
+      for (int x = lane; x < B; x += 32) v.at(x, r % B, r / B) = src[(r / B) * nx * ny + (r % B) * nx + x];
     __syncthreads();
     slab_inv<T, B, KIND, NT>(v, C);
   }

@@ -56,7 +56,8 @@ def test_strerror_covers_every_code(cz):
 
 
 @pytest.mark.parametrize("dims,block,f64", [((32, 32, 32), 32, False), ((16, 48, 32), 16, True),
-                                            ((8, 8, 24), 8, False), ((32, 32, 64), 32, True)])
+                                            ((8, 8, 24), 8, False), ((32, 32, 64), 32, True),
+                                            ((64, 64, 64), 64, False)])
 def test_compress_bound_covers_the_worst_stream(cz, dims, block, f64):
     p = cz.params_for(dims, f64, block, "w4", 0.0, cz.EPS_REL, True, 1.0)
     bound = cz.cz_compress_bound(p)
@@ -71,7 +72,7 @@ def test_compress_bound_covers_the_worst_stream(cz, dims, block, f64):
 
 def test_invalid_parameters_are_refused_on_the_host(cz):
     bad = [((32, 32, 48), 32, False), ((16, 16, 16), 12, False), ((32, 32, 24), 32, True),
-           ((0, 32, 32), 32, False)]
+           ((0, 32, 32), 32, False), ((64, 64, 64), 64, True), ((64, 64, 64), 128, False)]
     for dims, block, f64 in bad:
         p = cz.params_for(dims, f64, block, "w4", 1e-3, cz.EPS_REL, True, 1.0)
         with pytest.raises(cz.CzError) as e:

@@ -23,6 +23,7 @@ CASES = [
     (np.float64, 16, (32, 16, 48)),
     (np.float64, 8, (24, 8, 16)),
     (np.float64, 32, (32, 64, 96)),  # 256 KiB blocks: the slab kernels
+    (np.float32, 64, (64, 64, 128)),  # 1 MiB blocks: the slab kernels, four levels
 ]
 
 
@@ -193,7 +194,7 @@ def test_dense_coefficients_match_oracle_per_block(dtype, block, shape, kind):
 
 
 def test_single_block_and_all_constant_field():
-    for dtype, block in ((np.float32, 32), (np.float64, 16), (np.float32, 8), (np.float64, 32)):
+    for dtype, block in ((np.float32, 32), (np.float64, 16), (np.float32, 8), (np.float64, 32), (np.float32, 64)):
         f = np.full((block,) * 3, 3.25, dtype)
         for kind in KINDS:
             ref = O.compress(f, block, kind, 1e-3)

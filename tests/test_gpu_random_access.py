@@ -28,6 +28,7 @@ def _blocks(field, B):
     (np.float64, 16, (32, 48, 64)),
     (np.float32, 8, (16, 24, 40)),
     (np.float64, 32, (32, 64, 96)),
+    (np.float32, 64, (64, 64, 128)),
 ])
 def test_decoded_blocks_equal_the_oracle_field_blocks(dtype, block, shape, kind, stage2):
     import torch
