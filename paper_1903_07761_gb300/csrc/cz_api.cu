@@ -180,7 +180,8 @@ struct Lanes {
                           int, const cudaEvent_t *, cudaStream_t);
   cudaError_t (*compress_batch)(int, const StageMaps<MAXF> *, const FwdArgs *, const S2Args *, const BatchOut *,
                                 const PlaceArgs *, int, int, int, int, cudaStream_t);
-  cudaError_t (*decompress)(int, const CUtensorMap *, const InvArgs *, const UnArgs *, int, int, int, cudaStream_t);
+  cudaError_t (*decompress)(int, const CUtensorMap *, const InvArgs *, const UnArgs *, int, int, int,
+                            const cudaEvent_t *, cudaStream_t);
   cudaError_t (*dense)(int, int, const DenseArgs *, int, cudaStream_t);
   int (*occupancy)(int, int);
   int (*slot_bytes)();
@@ -940,7 +941,8 @@ namespace {
 // workspace; with tiles the block grid is 1 x 1 x n, so block i lands at
 // z = i B of the B x B x nB tile array.
 int decompress_impl(const void *d_in, size_t in_bytes, const void *h_header, const int32_t *ids, int n,
-                    void *d_out, size_t out_cap, void *d_ws, size_t ws_bytes, void *stream)
+                    void *d_out, size_t out_cap, void *d_ws, size_t ws_bytes, void *stream,
+                    const cudaEvent_t *marks = nullptr)
 {
   if (!d_in || !d_out || !d_ws) return CZ_ERR_ARG;
   if (((uintptr_t)d_in % 16) || ((uintptr_t)d_out % 16) || ((uintptr_t)d_ws % 16)) return CZ_ERR_ARG;
@@ -1019,13 +1021,24 @@ int decompress_impl(const void *d_in, size_t in_bytes, const void *h_header, con
   ua.nblocks = dsh.nblocks;
   CUtensorMap om;
   if (!make_tile_map(&om, &q, d_out)) return CZ_ERR_CUDA;
-  return L.decompress(p.kind, &om, &a, &ua, grid_for(&p, dsh, 1), grid_for(&p, dsh, 4), grid_for(&p, dsh, 5), s) ==
-                 cudaSuccess
+  return L.decompress(p.kind, &om, &a, &ua, grid_for(&p, dsh, 1), grid_for(&p, dsh, 4), grid_for(&p, dsh, 5), marks,
+                      s) == cudaSuccess
              ? CZ_OK
              : CZ_ERR_CUDA;
 }
 
 }  // namespace
+
+// Not part of the ABI: cz_decompress with one CUDA event recorded right before the decode kernel
+// (after the stage-2 inverse launches), for timing the kernels one by one.
+int czi_decompress_marked(const void *d_in, size_t in_bytes, const void *h_header, void *d_field, size_t field_cap,
+                          void *d_ws, size_t ws_bytes, void *stream, void *const *events)
+{
+  if (!events || !events[0]) return CZ_ERR_ARG;
+  cudaEvent_t ev[1] = {reinterpret_cast<cudaEvent_t>(events[0])};
+  return decompress_impl(d_in, in_bytes, h_header, nullptr, 0, d_field, field_cap, d_ws, ws_bytes, stream, ev);
+}
+
 
 int cz_decompress(const void *d_in, size_t in_bytes, const void *h_header, void *d_field,
                   size_t field_cap, void *d_ws, size_t ws_bytes, void *stream)

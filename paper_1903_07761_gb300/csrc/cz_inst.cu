@@ -127,9 +127,10 @@ cudaError_t compress_batch_k(const StageMaps<MAXF> &maps, const FwdArgs &a, cons
   return cudaGetLastError();
 }
 
+// marks (optional): marks[0] is recorded right before the decode kernel
 template <int KIND>
 cudaError_t decompress_k(const CUtensorMap &om, const InvArgs &a, const UnArgs &ua, int grid, int gridu, int gridub,
-                         cudaStream_t s)
+                         const cudaEvent_t *marks, cudaStream_t s)
 {
   cudaError_t e;
   if (a.stage2) {
@@ -149,10 +150,12 @@ cudaError_t decompress_k(const CUtensorMap &om, const InvArgs &a, const UnArgs &
   if constexpr (G::SLAB) {
     e = prepare<k_decompress_slab<CZ_T, CZ_B, KIND>>(SGi::SMEM);
     if (e != cudaSuccess) return e;
+    if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
     k_decompress_slab<CZ_T, CZ_B, KIND><<<grid, SGi::NT, SGi::SMEM, s>>>(a);
   } else {
     e = prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D);
     if (e != cudaSuccess) return e;
+    if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
     k_decompress2<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_D, s>>>(om, a);
   }
   return cudaGetLastError();
@@ -280,12 +283,12 @@ extern "C" cudaError_t CZ_CAT(czl_compress_batch_, CZ_SUFFIX)(int kind, const St
 
 extern "C" cudaError_t CZ_CAT(czl_decompress_, CZ_SUFFIX)(int kind, const CUtensorMap *om, const InvArgs *a,
                                                            const UnArgs *ua, int grid, int gridu, int gridub,
-                                                           cudaStream_t s)
+                                                           const cudaEvent_t *marks, cudaStream_t s)
 {
   switch (kind) {
-    case W4: return decompress_k<W4>(*om, *a, *ua, grid, gridu, gridub, s);
-    case W4LI: return decompress_k<W4LI>(*om, *a, *ua, grid, gridu, gridub, s);
-    default: return decompress_k<W3AI>(*om, *a, *ua, grid, gridu, gridub, s);
+    case W4: return decompress_k<W4>(*om, *a, *ua, grid, gridu, gridub, marks, s);
+    case W4LI: return decompress_k<W4LI>(*om, *a, *ua, grid, gridu, gridub, marks, s);
+    default: return decompress_k<W3AI>(*om, *a, *ua, grid, gridu, gridub, marks, s);
   }
 }
 

@@ -25,8 +25,8 @@ struct StageMaps;
       const czp::BatchOut *bo, const czp::PlaceArgs *pa, int grid, int grid2, int grid3, int tiles,    \
       cudaStream_t s);                                                                                  \
   extern "C" cudaError_t czl_decompress_##sfx(int kind, const CUtensorMap *om, const czp::InvArgs *a,  \
-                                              const czp::UnArgs *ua,                                  \
-                                              int grid, int gridu, int gridub, cudaStream_t s);       \
+                                              const czp::UnArgs *ua, int grid, int gridu, int gridub, \
+                                              const cudaEvent_t *marks, cudaStream_t s);              \
   extern "C" cudaError_t czl_dense_##sfx(int kind, int fwd, const czp::DenseArgs *a, int nblocks,   \
                                          cudaStream_t s);                                           \
   extern "C" int czl_occupancy_##sfx(int kind, int which);                                         \
