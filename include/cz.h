@@ -153,6 +153,49 @@ int cz_decompress_blocks(const void *d_in, size_t in_bytes, const void *h_header
  * made with parameters p.  Returns CZ_OK or CZ_ERR_ARG. */
 int cz_decompress_blocks_workspace_size(const cz_params *p, int n, size_t *bytes);
 
+/* ---- decoded-block cache for random access (Sec. 2.3, "Data
+ * decompression": recently decompressed blocks are kept, and later requests
+ * for them are served without decompressing again) --------------------------
+ * A cache owns device memory for `capacity` decoded B^3 tiles of one
+ * element type and block edge (and as many tiles of staging for the blocks
+ * a call decodes), allocated by cz_cache_create on the current device.
+ * It serves one stream at a time: a call with another stream (other device
+ * address, length or header) empties it first.  Not thread-safe: one host
+ * thread uses a cache at a time, with one CUDA stream. */
+typedef struct cz_cache cz_cache;
+
+/* Create a cache of `capacity` (>= 1) tiles for blocks of edge `block` and
+ * element type `dtype` (CZ_F32 / CZ_F64).  CZ_ERR_ARG for bad arguments,
+ * CZ_ERR_CUDA if the memory cannot be allocated. */
+int cz_cache_create(int capacity, int block, int dtype, cz_cache **out);
+void cz_cache_destroy(cz_cache *c);
+
+/* Fetch blocks h_ids[0..n) (a HOST array; ids may repeat) of the stream
+ * d_in into n consecutive B^3 tiles at d_tiles, as cz_decompress_blocks
+ * does.  A block held by the cache is copied from it; the others (each
+ * once) are decoded with cz_decompress_blocks into the staging tiles, then
+ * take the cache slots of the least recently used blocks that this call
+ * does not request.  All copies are one kernel on `stream`; nothing is
+ * synchronised.  n <= capacity; every id must lie in the stream (checked on
+ * the host: CZ_ERR_ARG before anything is enqueued); the stream's block
+ * edge and type must match the cache's.  d_ws / ws_bytes as for
+ * cz_decompress_blocks with n blocks.  *h_hits (may be NULL) receives the
+ * number of requests served from the cache (blocks it held when the call
+ * began).  Header handling as for cz_decompress.  Device-side errors (a
+ * corrupt chunk) go to the status word of d_ws, as for
+ * cz_decompress_blocks; the block is then cached as the zeros it decoded
+ * to, so after a call that set the status word, empty the cache
+ * (cz_cache_clear). */
+int cz_cache_fetch(cz_cache *c, const void *d_in, size_t in_bytes, const void *h_header, const int32_t *h_ids,
+                   int n, void *d_tiles, size_t tiles_cap, void *d_ws, size_t ws_bytes, void *stream, int *h_hits);
+
+/* Forget every cached block (the memory stays allocated). */
+int cz_cache_clear(cz_cache *c);
+
+/* Blocks the cache holds now, and the cumulative counts of requests served
+ * from it (hits) and blocks it decoded (misses). */
+int cz_cache_stats(const cz_cache *c, int *held, long long *hits, long long *misses);
+
 /* Size of the workspace that cz_compress_noalloc uses: 64 MiB. */
 #define CZ_NOALLOC_WS_BYTES (64u << 20)
 

@@ -60,7 +60,7 @@ def _jobs(verbose_ptxas: bool):
                    f"-DCZ_B={b}", *(["-DCZ_FAST"] if fast else []), "-c", os.path.join(CSRC, "cz_inst.cu"),
                    "-o", obj]
             jobs.append((obj, cmd))
-    for name in ("cz_api", "cz_noalloc", "cz_serve"):
+    for name in ("cz_api", "cz_noalloc", "cz_serve", "cz_cache"):
         obj = os.path.join(BUILD_DIR, f"{name}.o")
         jobs.append((obj, [nvcc(), *ARCH, *NVFLAGS, *extra, "-c", os.path.join(CSRC, f"{name}.cu"),
                            "-o", obj]))

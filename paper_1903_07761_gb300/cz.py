@@ -95,8 +95,16 @@ def lib():
             L.cz_strerror.restype = C.c_char_p
             L.cz_forward_dense.argtypes = [PP, P, P, P]
             L.cz_inverse_dense.argtypes = [PP, P, P, P]
+            L.cz_cache_create.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(P)]
+            L.cz_cache_destroy.argtypes = [P]
+            L.cz_cache_destroy.restype = None
+            L.cz_cache_fetch.argtypes = [P, P, C.c_size_t, P, P, C.c_int, P, C.c_size_t, P, C.c_size_t, P,
+                                         C.POINTER(C.c_int)]
+            L.cz_cache_clear.argtypes = [P]
+            L.cz_cache_stats.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
             for f in (L.cz_compress_bound, L.cz_workspace_size, L.cz_compress, L.cz_decompress, L.cz_decompress_blocks,
-                      L.cz_decompress_blocks_workspace_size,
+                      L.cz_decompress_blocks_workspace_size, L.cz_cache_create, L.cz_cache_fetch, L.cz_cache_clear,
+                      L.cz_cache_stats,
                       L.cz_compress_noalloc, L.cz_batch_workspace_size, L.cz_compress_batch,
                       L.cz_batch_tune, L.cz_stream_concat, L.cz_server_create, L.cz_server_submit, L.cz_server_poll,
                       L.cz_server_wait, L.cz_server_destroy, L.cz_read_header, L.cz_status, L.cz_forward_dense, L.cz_inverse_dense):
@@ -328,6 +336,81 @@ def decompress_blocks(stream_t, ids, nbytes: int | None = None, header: bytes | 
         if st != OK:
             raise CzError(st, "cz_decompress_blocks (device)")
     return out
+
+
+class Cache:
+    """Decoded-block cache (cz_cache_*): fetch(stream_t, ids) returns the
+    tiles of blocks ids (a host sequence of block indices) as a new (or
+    given) CUDA tensor [len(ids), B, B, B], decoding only the blocks the
+    cache does not hold."""
+
+    def __init__(self, capacity: int, block: int, f64: bool = False):
+        self.capacity, self.block, self.f64 = capacity, block, f64
+        h = C.c_void_p()
+        r = lib().cz_cache_create(capacity, block, F64 if f64 else F32, C.byref(h))
+        if r != OK:
+            raise CzError(r, "cz_cache_create")
+        self._h = h
+        self._ws = None
+
+    def fetch(self, stream_t, ids, nbytes: int | None = None, header: bytes | None = None, out=None,
+              ws: Workspace | None = None, stream=None, check: bool = True):
+        import numpy as np
+        import torch
+        if header is None:
+            header = stream_t[:HEADER_BYTES].cpu().numpy().tobytes()
+        p, _ = cz_read_header(header)
+        ids = np.ascontiguousarray(np.asarray(ids, dtype=np.int32))
+        k = int(ids.size)
+        n = int(nbytes) if nbytes is not None else stream_t.numel()
+        B = self.block
+        dt = torch.float64 if self.f64 else torch.float32
+        if out is None:
+            out = torch.empty((k, B, B, B), dtype=dt, device=stream_t.device)
+        ws = ws or self._ws or Workspace(stream_t.device)
+        self._ws = ws
+        need = C.c_size_t()
+        r = lib().cz_decompress_blocks_workspace_size(C.byref(p), max(k, 1), C.byref(need))
+        if r != OK:
+            raise CzError(r, "cz_decompress_blocks_workspace_size")
+        wsb = ws.get(need.value)
+        s = _stream(stream)
+        hdr = C.create_string_buffer(bytes(header[:HEADER_BYTES]), HEADER_BYTES)
+        hits = C.c_int(0)
+        r = lib().cz_cache_fetch(self._h, stream_t.data_ptr(), n, hdr,
+                                 ids.ctypes.data_as(C.c_void_p) if k else None, k, out.data_ptr(),
+                                 out.numel() * out.element_size(), wsb.data_ptr(), wsb.numel(), s or None,
+                                 C.byref(hits))
+        if r != OK:
+            raise CzError(r, "cz_cache_fetch")
+        if check and k:
+            st = cz_status(wsb.data_ptr(), s)
+            if st != OK:
+                raise CzError(st, "cz_cache_fetch (device)")
+        return out, hits.value
+
+    def clear(self):
+        r = lib().cz_cache_clear(self._h)
+        if r != OK:
+            raise CzError(r, "cz_cache_clear")
+
+    def stats(self):
+        held, hits, misses = C.c_int(), C.c_longlong(), C.c_longlong()
+        r = lib().cz_cache_stats(self._h, C.byref(held), C.byref(hits), C.byref(misses))
+        if r != OK:
+            raise CzError(r, "cz_cache_stats")
+        return held.value, hits.value, misses.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cz_cache_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def compress_batch(fields, block=None, kind="w3ai", eps=1e-3, eps_mode: int = EPS_REL,

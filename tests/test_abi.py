@@ -160,3 +160,17 @@ def test_struct_layouts_match_the_header(cz, tmp_path):
     want = [C.sizeof(cz.Params), C.sizeof(cz.Request), cz.Params.eps.offset, cz.Request.h_header.offset,
             cz.Request.d_out.offset]
     assert got == want
+
+
+def test_cache_arguments_are_refused_before_any_cuda_call(cz):
+    """cz_cache_create / cz_cache_fetch check their arguments on the host
+    before touching the device (so this runs without a GPU)."""
+    h = C.c_void_p()
+    for cap, B, dt in ((0, 32, cz.F32), (4, 12, cz.F32), (4, 32, 7)):
+        assert cz.lib().cz_cache_create(cap, B, dt, C.byref(h)) == cz.ERR_ARG
+        assert not h.value
+    hits = C.c_int(5)
+    assert cz.lib().cz_cache_fetch(None, None, 0, None, None, 0, None, 0, None, 0, None, C.byref(hits)) == cz.ERR_ARG
+    assert hits.value == 0
+    assert cz.lib().cz_cache_clear(None) == cz.ERR_ARG
+    assert cz.lib().cz_cache_stats(None, None, None, None) == cz.ERR_ARG
