@@ -50,10 +50,15 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+# the sources of the register-resident kernels and their launches (the
+# kernels the traffic keys describe)
+KERNEL_SOURCES = ("cz_compress.cuh", "cz_device.cuh", "cz_inst.cu", "cz_pair.cuh")
+
+
 def csrc_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1903_07761_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
+    for name in KERNEL_SOURCES:
         with open(os.path.join(d, name), "rb") as fh:
             h.update(name.encode())
             h.update(fh.read())
@@ -437,6 +442,15 @@ def run_gpu(args, rank, world, local_rank):
             del ws_b
         torch.cuda.empty_cache()
 
+    # random access with and without the decoded-block cache, on the
+    # headline stream (compressed again: the studies above reused `out`)
+    random_access = None
+    if not args.headline_only and rank == 0:
+        from paper_1903_07761_gb300 import workloads
+        compress_call()
+        ra_len = int(nb.item())
+        random_access = workloads.random_access(out[:ra_len], ra_len, header)
+
     # batched fields and the served request stream (rank 0, one GPU)
     batched_res = served_res = fp64_res = None
     if rank == 0 and world == 1:
@@ -518,6 +532,7 @@ def run_gpu(args, rank, world, local_rank):
         "per_kind": per_kind,
         "bit_zeroing": bit_zeroing,
         "block_sizes": block_sizes,
+        "random_access": random_access,
         "batched": batched_res,
         "served": served_res,
         "fp64": fp64_res,

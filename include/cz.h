@@ -254,6 +254,24 @@ int cz_batch_tune(int n, const cz_params *p, const void *const *d_fields,
                   uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes,
                   void *stream, int reps);
 
+/* ---- quantities of a cell-struct array (the paper's solver stores all
+ * quantities of a cell together and compresses chosen quantities from that
+ * storage, Sec. 2.1 / 2.2) ---------------------------------------------------
+ * d_cells holds nz*ny*nx cells of ncomp elements of one type, C order
+ * [nz][ny][nx][ncomp].  Quantity i of the call is component comps[i]
+ * (a host array; 0 <= comps[i] < ncomp) and is compressed with parameters
+ * p[i] (all with the same nx, ny, nz and dtype; kind, block, eps, stage 2
+ * and flags may differ) into d_outs[i] (capacity out_caps[i], length to
+ * d_out_bytes[i], a device array of n u64, may be NULL).  One kernel reads
+ * every cell once and writes the n chosen components as dense fields into
+ * the workspace; a cz_compress_batch call then compresses them, so every
+ * stream is identical to cz_compress of that component alone.  Errors as
+ * for cz_compress_batch; d_ws must hold cz_aos_workspace_size() bytes. */
+int cz_aos_workspace_size(int n, const cz_params *p, size_t *bytes);
+int cz_compress_aos(int n, const cz_params *p, const void *d_cells, int ncomp, const int32_t *comps,
+                    void *const *d_outs, const size_t *out_caps, uint64_t *d_out_bytes, void *d_ws,
+                    size_t ws_bytes, void *stream);
+
 /* ---- request server (the paper compresses in situ, while the simulation
  * runs, Sec. 2.2; here requests of mixed sizes and precisions arrive at any
  * time and share the device) ----------------------------------------------

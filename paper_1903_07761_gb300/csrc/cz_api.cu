@@ -781,6 +781,101 @@ int cz_batch_tune(int n, const cz_params *p, const void *const *d_fields, void *
   return r;
 }
 
+// ---- quantities of a cell-struct array: de-interleave, then one batched
+// compression of the chosen components
+extern "C++" {
+namespace {
+
+struct AosPick {
+  int n;
+  int comp[MAXF];
+  void *out[MAXF];
+};
+
+// one cell per thread (grid-stride): its chosen components go to their
+// dense fields; consecutive threads read consecutive cells and write
+// consecutive elements of every field
+template <typename T>
+__global__ void __launch_bounds__(256) k_deinterleave(const T *cells, int ncomp, const AosPick pick,
+                                                      unsigned long long ncells)
+{
+  for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < ncells; i += (unsigned long long)gridDim.x * 256)
+    for (int q = 0; q < pick.n; ++q) reinterpret_cast<T *>(pick.out[q])[i] = cells[i * ncomp + pick.comp[q]];
+}
+
+size_t aos_field_bytes(const cz_params &p)
+{
+  return ((size_t)p.nx * p.ny * p.nz * (p.dtype == CZ_F64 ? 8 : 4) + 255) / 256 * 256;
+}
+
+int aos_check(int n, const cz_params *p)
+{
+  if (n < 1 || n > MAXF || !p) return CZ_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (check(&p[i], nullptr) != CZ_OK) return CZ_ERR_ARG;
+    if (p[i].nx != p[0].nx || p[i].ny != p[0].ny || p[i].nz != p[0].nz || p[i].dtype != p[0].dtype)
+      return CZ_ERR_ARG;
+  }
+  return CZ_OK;
+}
+
+}  // namespace
+}  // extern "C++"
+
+int cz_aos_workspace_size(int n, const cz_params *p, size_t *bytes)
+{
+  if (!bytes) return CZ_ERR_ARG;
+  const int r = aos_check(n, p);
+  if (r != CZ_OK) return r;
+  size_t b = 0;
+  const int rb = cz_batch_workspace_size(n, p, &b);
+  if (rb != CZ_OK) return rb;
+  *bytes = (b + 255) / 256 * 256 + (size_t)n * aos_field_bytes(p[0]);
+  return CZ_OK;
+}
+
+int cz_compress_aos(int n, const cz_params *p, const void *d_cells, int ncomp, const int32_t *comps,
+                    void *const *d_outs, const size_t *out_caps, uint64_t *d_out_bytes, void *d_ws,
+                    size_t ws_bytes, void *stream)
+{
+  int r = aos_check(n, p);
+  if (r != CZ_OK) return r;
+  if (!d_cells || !comps || !d_outs || !out_caps || !d_ws || ncomp < 1 || ncomp > 4096) return CZ_ERR_ARG;
+  const size_t es = p[0].dtype == CZ_F64 ? 8 : 4;
+  if ((uintptr_t)d_cells % es || (uintptr_t)d_ws % 16) return CZ_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (comps[i] < 0 || comps[i] >= ncomp) return CZ_ERR_ARG;
+  size_t need = 0;
+  if ((r = cz_aos_workspace_size(n, p, &need)) != CZ_OK) return r;
+  if (ws_bytes < need) return CZ_ERR_CAPACITY;
+  // workspace: the batched compression's (its status word first) | the n
+  // dense fields
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned char *wsb = reinterpret_cast<unsigned char *>(d_ws);
+  const size_t fb = aos_field_bytes(p[0]);
+  const size_t f0 = need - (size_t)n * fb;
+  AosPick pick{};
+  pick.n = n;
+  std::vector<const void *> fields(n);
+  for (int i = 0; i < n; ++i) {
+    pick.comp[i] = comps[i];
+    pick.out[i] = wsb + f0 + (size_t)i * fb;
+    fields[i] = pick.out[i];
+  }
+  const unsigned long long ncells = (unsigned long long)p[0].nx * p[0].ny * p[0].nz;
+  unsigned long long blocks = (ncells + 255) / 256;
+  const unsigned long long cap = (unsigned long long)sm_count() * 8;
+  if (blocks > cap) blocks = cap;
+  if (es == 8)
+    k_deinterleave<double><<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const double *>(d_cells), ncomp, pick,
+                                                            ncells);
+  else
+    k_deinterleave<float><<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const float *>(d_cells), ncomp, pick,
+                                                           ncells);
+  if (cudaGetLastError() != cudaSuccess) return CZ_ERR_CUDA;
+  return compress_batch_impl(n, p, fields.data(), d_outs, out_caps, d_out_bytes, wsb, f0, s, knobs_for(n, p));
+}
+
 int cz_stream_concat(int n, const void *const *h_streams, const size_t *sizes, void *h_out, size_t out_cap,
                      size_t *out_bytes)
 {

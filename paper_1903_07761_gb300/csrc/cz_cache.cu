@@ -46,8 +46,17 @@ struct cz_cache {
   int cap = 0, block = 0, dtype = 0;
   size_t tile = 0;
   unsigned char *slots = nullptr, *stage = nullptr;
-  TileCopy *d_plan = nullptr;  // room for 2 * cap copies
-  int32_t *d_ids = nullptr;    // room for cap block ids
+  // device copies of the plan (room for 2 * cap copies) and the ids (cap),
+  // and pinned host buffers they are uploaded from: a ring of NUP, so that
+  // the host may run up to NUP calls ahead of the device (a ring entry is
+  // free again once its event, recorded after its uploads, has completed)
+  static constexpr int NUP = 4;
+  TileCopy *d_plan[NUP] = {};
+  int32_t *d_ids[NUP] = {};
+  TileCopy *h_plan[NUP] = {};
+  int32_t *h_ids[NUP] = {};
+  cudaEvent_t uploaded[NUP] = {};
+  int next = 0;
   // the stream the cached blocks come from
   const void *src = nullptr;
   size_t src_bytes = 0;
@@ -94,9 +103,13 @@ int cz_cache_create(int capacity, int block, int dtype, cz_cache **out)
   c->owner.assign(capacity, -1);
   c->pos.resize(capacity);
   bool ok = cudaMalloc(&c->slots, c->tile * capacity) == cudaSuccess &&
-            cudaMalloc(&c->stage, c->tile * capacity) == cudaSuccess &&
-            cudaMalloc(&c->d_plan, sizeof(TileCopy) * 2 * (size_t)capacity) == cudaSuccess &&
-            cudaMalloc(&c->d_ids, sizeof(int32_t) * (size_t)capacity) == cudaSuccess;
+            cudaMalloc(&c->stage, c->tile * capacity) == cudaSuccess;
+  for (int u = 0; u < cz_cache::NUP && ok; ++u)
+    ok = cudaMalloc(&c->d_plan[u], sizeof(TileCopy) * 2 * (size_t)capacity) == cudaSuccess &&
+         cudaMalloc(&c->d_ids[u], sizeof(int32_t) * (size_t)capacity) == cudaSuccess &&
+         cudaMallocHost(&c->h_plan[u], sizeof(TileCopy) * 2 * (size_t)capacity) == cudaSuccess &&
+         cudaMallocHost(&c->h_ids[u], sizeof(int32_t) * (size_t)capacity) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->uploaded[u], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cz_cache_destroy(c);
     return CZ_ERR_CUDA;
@@ -111,8 +124,13 @@ void cz_cache_destroy(cz_cache *c)
   if (!c) return;
   cudaFree(c->slots);
   cudaFree(c->stage);
-  cudaFree(c->d_plan);
-  cudaFree(c->d_ids);
+  for (int u = 0; u < cz_cache::NUP; ++u) {
+    cudaFree(c->d_plan[u]);
+    cudaFree(c->d_ids[u]);
+    cudaFreeHost(c->h_plan[u]);
+    cudaFreeHost(c->h_ids[u]);
+    if (c->uploaded[u]) cudaEventDestroy(c->uploaded[u]);
+  }
   delete c;
 }
 
@@ -183,30 +201,36 @@ int cz_cache_fetch(cz_cache *c, const void *d_in, size_t in_bytes, const void *h
     if (!pinned[*it]) victim.push_back(*it);
   if ((int)victim.size() < nm) return CZ_ERR_ARG;  // cannot happen: distinct blocks <= n <= capacity
 
-  std::vector<TileCopy> plan;
-  plan.reserve(nm + n);
-  for (int m = 0; m < nm; ++m) plan.push_back({c->stage + (size_t)m * c->tile, c->slots + (size_t)victim[m] * c->tile});
+  // this call's ring entry: free once the uploads of the call NUP calls ago
+  // have completed
+  const int u = c->next;
+  if (cudaEventSynchronize(c->uploaded[u]) != cudaSuccess) return CZ_ERR_CUDA;
+  TileCopy *hp = c->h_plan[u];
+  int np = 0;
+  for (int m = 0; m < nm; ++m) hp[np++] = {c->stage + (size_t)m * c->tile, c->slots + (size_t)victim[m] * c->tile};
   unsigned char *out = reinterpret_cast<unsigned char *>(d_tiles);
   for (int i = 0; i < n; ++i) {
     const auto it = c->where.find(h_ids[i]);
     const unsigned char *src = it != c->where.end() ? c->slots + (size_t)it->second * c->tile
                                                     : c->stage + (size_t)miss_at[h_ids[i]] * c->tile;
-    plan.push_back({src, out + (size_t)i * c->tile});
+    hp[np++] = {src, out + (size_t)i * c->tile};
   }
 
   // enqueue: decode the missing blocks into the staging tiles, then the
-  // copies (host arrays are pageable: each copy has taken them by return)
+  // copies
   if (nm > 0) {
-    if (cudaMemcpyAsync(c->d_ids, miss.data(), sizeof(int32_t) * nm, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    std::memcpy(c->h_ids[u], miss.data(), sizeof(int32_t) * nm);
+    if (cudaMemcpyAsync(c->d_ids[u], c->h_ids[u], sizeof(int32_t) * nm, cudaMemcpyHostToDevice, s) != cudaSuccess)
       return CZ_ERR_CUDA;
-    r = cz_decompress_blocks(d_in, in_bytes, hb, c->d_ids, nm, c->stage, (size_t)nm * c->tile, d_ws, ws_bytes,
+    r = cz_decompress_blocks(d_in, in_bytes, hb, c->d_ids[u], nm, c->stage, (size_t)nm * c->tile, d_ws, ws_bytes,
                              stream);
     if (r != CZ_OK) return r;
   }
-  if (cudaMemcpyAsync(c->d_plan, plan.data(), sizeof(TileCopy) * plan.size(), cudaMemcpyHostToDevice, s) !=
-      cudaSuccess)
+  if (cudaMemcpyAsync(c->d_plan[u], hp, sizeof(TileCopy) * np, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return CZ_ERR_CUDA;
-  k_tile_copy<<<(unsigned)plan.size(), 256, 0, s>>>(c->d_plan, (int)plan.size(), (unsigned long long)c->tile);
+  if (cudaEventRecord(c->uploaded[u], s) != cudaSuccess) return CZ_ERR_CUDA;
+  c->next = (u + 1) % cz_cache::NUP;
+  k_tile_copy<<<(unsigned)np, 256, 0, s>>>(c->d_plan[u], np, (unsigned long long)c->tile);
   if (cudaGetLastError() != cudaSuccess) return CZ_ERR_CUDA;
 
   // commit: the decoded blocks take their slots; this call's blocks become

@@ -95,6 +95,9 @@ def lib():
             L.cz_strerror.restype = C.c_char_p
             L.cz_forward_dense.argtypes = [PP, P, P, P]
             L.cz_inverse_dense.argtypes = [PP, P, P, P]
+            L.cz_aos_workspace_size.argtypes = [C.c_int, PP, C.POINTER(C.c_size_t)]
+            L.cz_compress_aos.argtypes = [C.c_int, PP, P, C.c_int, P, C.POINTER(P), C.POINTER(C.c_size_t), P, P,
+                                          C.c_size_t, P]
             L.cz_cache_create.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(P)]
             L.cz_cache_destroy.argtypes = [P]
             L.cz_cache_destroy.restype = None
@@ -104,7 +107,7 @@ def lib():
             L.cz_cache_stats.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
             for f in (L.cz_compress_bound, L.cz_workspace_size, L.cz_compress, L.cz_decompress, L.cz_decompress_blocks,
                       L.cz_decompress_blocks_workspace_size, L.cz_cache_create, L.cz_cache_fetch, L.cz_cache_clear,
-                      L.cz_cache_stats,
+                      L.cz_cache_stats, L.cz_aos_workspace_size, L.cz_compress_aos,
                       L.cz_compress_noalloc, L.cz_batch_workspace_size, L.cz_compress_batch,
                       L.cz_batch_tune, L.cz_stream_concat, L.cz_server_create, L.cz_server_submit, L.cz_server_poll,
                       L.cz_server_wait, L.cz_server_destroy, L.cz_read_header, L.cz_status, L.cz_forward_dense, L.cz_inverse_dense):
@@ -338,6 +341,45 @@ def decompress_blocks(stream_t, ids, nbytes: int | None = None, header: bytes | 
     return out
 
 
+def compress_aos(cells, comps, block=None, kind="w3ai", eps=1e-3, eps_mode: int = EPS_REL, stage2: bool = True,
+                 bound_mode: int = BOUND_PAPER, stream=None, check: bool = True):
+    """Compress components comps of a contiguous CUDA cell array
+    [nz, ny, nx, ncomp] (float32/float64) in one call (cz_compress_aos).
+    block, kind and eps may be scalars or per-quantity lists.  Returns a
+    list of (stream_tensor, nbytes) pairs, one per component."""
+    import numpy as np
+    import torch
+    assert cells.is_cuda and cells.is_contiguous() and cells.dim() == 4
+    nz, ny, nx, ncomp = cells.shape
+    n = len(comps)
+    f64 = cells.dtype == torch.float64
+    per = lambda v: list(v) if isinstance(v, (list, tuple)) else [v] * n
+    blocks = per(block) if block is not None else [16 if f64 else 32] * n
+    params = [params_for((nz, ny, nx), f64, b, k, e, eps_mode, stage2, -1.0, bound_mode)
+              for b, k, e in zip(blocks, per(kind), per(eps))]
+    arr = (Params * n)(*params)
+    caps = [cz_compress_bound(q) for q in params]
+    outs = [torch.empty(c, dtype=torch.uint8, device=cells.device) for c in caps]
+    nbytes = torch.zeros(n, dtype=torch.int64, device=cells.device)
+    need = C.c_size_t()
+    r = lib().cz_aos_workspace_size(n, arr, C.byref(need))
+    if r != OK:
+        raise CzError(r, "cz_aos_workspace_size")
+    ws = torch.empty(need.value, dtype=torch.uint8, device=cells.device)
+    comps_a = np.ascontiguousarray(np.asarray(comps, dtype=np.int32))
+    s = _stream(stream)
+    r = lib().cz_compress_aos(n, arr, cells.data_ptr(), ncomp, comps_a.ctypes.data_as(C.c_void_p),
+                              (C.c_void_p * n)(*[o.data_ptr() for o in outs]), (C.c_size_t * n)(*caps),
+                              nbytes.data_ptr(), ws.data_ptr(), ws.numel(), s or None)
+    if r != OK:
+        raise CzError(r, "cz_compress_aos")
+    if check:
+        st = cz_status(ws.data_ptr(), s)
+        if st != OK:
+            raise CzError(st, "cz_compress_aos (device)")
+    return [(outs[i], nbytes[i]) for i in range(n)]
+
+
 class Cache:
     """Decoded-block cache (cz_cache_*): fetch(stream_t, ids) returns the
     tiles of blocks ids (a host sequence of block indices) as a new (or
@@ -359,7 +401,7 @@ class Cache:
         import torch
         if header is None:
             header = stream_t[:HEADER_BYTES].cpu().numpy().tobytes()
-        p, _ = cz_read_header(header)
+        header = bytes(header[:HEADER_BYTES])
         ids = np.ascontiguousarray(np.asarray(ids, dtype=np.int32))
         k = int(ids.size)
         n = int(nbytes) if nbytes is not None else stream_t.numel()
@@ -369,13 +411,22 @@ class Cache:
             out = torch.empty((k, B, B, B), dtype=dt, device=stream_t.device)
         ws = ws or self._ws or Workspace(stream_t.device)
         self._ws = ws
-        need = C.c_size_t()
-        r = lib().cz_decompress_blocks_workspace_size(C.byref(p), max(k, 1), C.byref(need))
-        if r != OK:
-            raise CzError(r, "cz_decompress_blocks_workspace_size")
-        wsb = ws.get(need.value)
+        # the parsed header, its C copy and the workspace size per request
+        # size, kept for the stream last seen
+        if getattr(self, "_hdr_key", None) != header:
+            self._hdr_key = header
+            self._hdr_p, _ = cz_read_header(header)
+            self._hdr_c = C.create_string_buffer(header, HEADER_BYTES)
+            self._need = {}
+        if k not in self._need:
+            need = C.c_size_t()
+            r = lib().cz_decompress_blocks_workspace_size(C.byref(self._hdr_p), max(k, 1), C.byref(need))
+            if r != OK:
+                raise CzError(r, "cz_decompress_blocks_workspace_size")
+            self._need[k] = need.value
+        wsb = ws.get(self._need[k])
         s = _stream(stream)
-        hdr = C.create_string_buffer(bytes(header[:HEADER_BYTES]), HEADER_BYTES)
+        hdr = self._hdr_c
         hits = C.c_int(0)
         r = lib().cz_cache_fetch(self._h, stream_t.data_ptr(), n, hdr,
                                  ids.ctypes.data_as(C.c_void_p) if k else None, k, out.data_ptr(),

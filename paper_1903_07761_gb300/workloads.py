@@ -278,6 +278,74 @@ def served(rates=(1000.0, 5000.0), n: int = 400, budget_gb: float = 40.0, stream
     }
 
 
+# ------------------------------------------------------------------ random access
+def random_access(stream_t, nbytes: int, header: bytes, steps: int = 200, capacity: int = 64, seed: int = 5000,
+                  radius: int = 1):
+    """Analysis-style random access (Sec. 2.3, Data decompression): a probe
+    point walks through the block grid, one block per step along a random
+    axis, and each step fetches the (2 radius + 1)^3 blocks around it
+    (clamped at the faces).  Consecutive neighbourhoods share most blocks,
+    which the decoded-block cache serves without decoding; the comparison
+    decodes every requested block with cz_decompress_blocks."""
+    import torch
+    p, _ = cz.cz_read_header(header)
+    B = p.block
+    nbx, nby, nbz = p.nx // B, p.ny // B, p.nz // B
+    rng = np.random.default_rng(seed)
+    pos = np.array([nbx // 2, nby // 2, nbz // 2])
+    reqs = []
+    for _ in range(steps):
+        ax = int(rng.integers(0, 3))
+        pos[ax] = min(max(pos[ax] + int(rng.choice([-1, 1])), 0), (nbx, nby, nbz)[ax] - 1)
+        ids = []
+        rr = range(-radius, radius + 1)
+        for dz in rr:
+            for dy in rr:
+                for dx in rr:
+                    x = min(max(pos[0] + dx, 0), nbx - 1)
+                    y = min(max(pos[1] + dy, 0), nby - 1)
+                    z = min(max(pos[2] + dz, 0), nbz - 1)
+                    ids.append(int((z * nby + y) * nbx + x))
+        reqs.append(ids)
+    dev_ids = [torch.tensor(r, dtype=torch.int32, device=stream_t.device) for r in reqs]
+    nreq1 = (2 * radius + 1) ** 3
+    out = torch.empty((nreq1, B, B, B), dtype=torch.float64 if p.dtype == cz.F64 else torch.float32,
+                      device=stream_t.device)
+    ws = cz.Workspace(stream_t.device)
+    # warm-up of both paths (kernel loading), then the timed walks
+    cz.decompress_blocks(stream_t, dev_ids[0], nbytes, header, out=out, ws=ws)
+    cache = cz.Cache(capacity, B, f64=p.dtype == cz.F64)
+    cache.fetch(stream_t, reqs[0], nbytes, header, out=out, ws=ws)
+    cache.clear()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    for d in dev_ids:
+        cz.decompress_blocks(stream_t, d, nbytes, header, out=out, ws=ws, check=False)
+    e[1].record()
+    hits = 0
+    e[2].record()
+    for r in reqs:
+        hits += cache.fetch(stream_t, r, nbytes, header, out=out, ws=ws, check=False)[1]
+    e[3].record()
+    torch.cuda.synchronize()
+    plain_ms, cache_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    st = cz.cz_status(ws.buf.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    if st != cz.OK:
+        raise cz.CzError(st, "random access (device)")
+    held, _, decoded = cache.stats()
+    cache.close()
+    nreq = steps * nreq1
+    return {
+        "workload": f"probe walk of {steps} steps through the {nbx}x{nby}x{nbz} grid of {B}^3 "
+                    f"{'FP64' if p.dtype == cz.F64 else 'FP32'} blocks, {nreq1} neighbouring blocks per step, "
+                    f"cache of {capacity} tiles",
+        "blocks_requested": nreq, "blocks_decoded_with_cache": decoded, "hit_rate": hits / nreq,
+        "plain_ms_per_step": plain_ms / steps, "cache_ms_per_step": cache_ms / steps,
+        "speedup": plain_ms / cache_ms,
+    }
+
+
 # ------------------------------------------------------------------ FP64
 def _w3ai_fp64_ops_per_element(B: int, xy_run_time: bool = True) -> float:
     """FP64 instructions per element of the exact-build W3ai transform (one
@@ -398,11 +466,20 @@ def fp64(n: int = 768, kind: str = "w3ai", eps: float = 1e-3, reps: int = 10, se
 
     r = case(16)
     r32 = case(32)
+    # random access on the 32^3 stream: decoding is FP64-bound here, so the
+    # decoded-block cache saves time, not only work
+    st32, nb32 = cz.compress(f, block=32, kind=kind, eps=eps)
+    ln32 = int(nb32.item())
+    ra = random_access(st32[:ln32], ln32, st32[:cz.HEADER_BYTES].cpu().numpy().tobytes(), steps=60,
+                       capacity=512, radius=3)
+    del st32
+    torch.cuda.empty_cache()
     r.update({
         "workload": f"rho-field {n}^3 FP64, 16^3 blocks, {kind}, eps=1e-3*range, stage 2 on, range computed",
         "fp64_probe_dfma_per_s": dfma_per_s,
         "bound": "fp64 alu",
         "blocks_32": dict(r32, workload=f"the same field in 32^3 blocks (slab kernels: the block in global "
                                          f"memory, L2-resident)"),
+        "random_access_32": ra,
     })
     return r

@@ -174,3 +174,16 @@ def test_cache_arguments_are_refused_before_any_cuda_call(cz):
     assert hits.value == 0
     assert cz.lib().cz_cache_clear(None) == cz.ERR_ARG
     assert cz.lib().cz_cache_stats(None, None, None, None) == cz.ERR_ARG
+
+
+def test_aos_arguments_are_refused_before_any_cuda_call(cz):
+    """cz_aos_workspace_size / cz_compress_aos refuse an empty call and
+    quantities of different field shapes on the host."""
+    need = C.c_size_t()
+    assert cz.lib().cz_aos_workspace_size(0, None, C.byref(need)) == cz.ERR_ARG
+    a = cz.params_for((32, 32, 32), False, 32, "w4", 1e-3)
+    b = cz.params_for((32, 32, 64), False, 32, "w4", 1e-3)
+    arr = (cz.Params * 2)(a, b)
+    assert cz.lib().cz_aos_workspace_size(2, arr, C.byref(need)) == cz.ERR_ARG
+    comps = (C.c_int32 * 2)(0, 1)
+    assert cz.lib().cz_compress_aos(2, arr, None, 4, comps, None, None, None, None, 0, None) == cz.ERR_ARG
