@@ -47,6 +47,9 @@ struct SG {
   // shared memory: cube | mask words | row offsets
   static constexpr int SMEM = CUBE_AL + ROWS * MWPR * 4 + ROWS * 4;
   static constexpr int MINB = B == 64 ? 1 : 2;  // CTAs per SM (registers: a line of B values)
+  // the warp-per-row loops take RB rows per round: their loads are all
+  // issued before the first one is used (one memory round trip per RB rows)
+  static constexpr int RB = 8;
   // (checked where a slab kernel is instantiated: whole 32-bit mask words
   // per row with the lanes on x, whole rows per thread)
   static constexpr bool OK = (B == 32 || B == 64) && ROWS % NT == 0;
@@ -206,7 +209,9 @@ __global__ void __launch_bounds__(SG<T, B>::NT, SG<T, B>::MINB) k_stage1_slab(
   static_assert(SG<T, B>::OK, "slab geometry: B = 32 or 64");
   using S = SG<T, B>;
   using G = G2<T, B>;
-  constexpr int NT = S::NT, NW = S::NW, Q = S::Q, ES = S::ES, ROWS = S::ROWS, RPT = S::RPT, MWPR = S::MWPR;
+  constexpr int NT = S::NT, NW = S::NW, Q = S::Q, ES = S::ES, ROWS = S::ROWS, RPT = S::RPT, MWPR = S::MWPR,
+                RB = S::RB;
+  static_assert(ROWS % (NW * RB) == 0, "whole rounds of RB rows per warp");
   extern __shared__ __align__(128) unsigned char smem[];
   T *C = reinterpret_cast<T *>(smem);
   unsigned *MW = reinterpret_cast<unsigned *>(smem + S::CUBE_AL);  // mask words (MWPR per row)
@@ -250,16 +255,23 @@ __global__ void __launch_bounds__(SG<T, B>::NT, SG<T, B>::MINB) k_stage1_slab(
     slab_fwd<T, B, KIND, NT>(src, nx, nx * ny, v, C);
 
     // ---- mask rows (coarse positions carry no bit; word h of a row holds
-    // x = 32 h + lane), row offsets
-    for (int r = wid; r < ROWS; r += NW) {
-      const int z = r / B, y = r % B;
+    // x = 32 h + lane), row offsets; a warp takes RB consecutive rows a round
+    for (int r0 = wid * RB; r0 < ROWS; r0 += NW * RB) {
+      T d[RB][MWPR];
 #pragma unroll
-      for (int h = 0; h < MWPR; ++h) {
-        const int x = 32 * h + lane;
-        const T d = v.at(x, y, z);
-        const bool coarse = (x % Q == 0) && (y % Q == 0) && (z % Q == 0);
-        const unsigned w = __ballot_sync(FULL, !coarse && keep(d, t));
-        if (lane == 0) MW[r * MWPR + h] = w;
+      for (int j = 0; j < RB; ++j)
+#pragma unroll
+        for (int h = 0; h < MWPR; ++h) d[j][h] = v.at(32 * h + lane, (r0 + j) % B, (r0 + j) / B);
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        const int r = r0 + j, z = r / B, y = r % B;
+#pragma unroll
+        for (int h = 0; h < MWPR; ++h) {
+          const int x = 32 * h + lane;
+          const bool coarse = (x % Q == 0) && (y % Q == 0) && (z % Q == 0);
+          const unsigned w = __ballot_sync(FULL, !coarse && keep(d[j][h], t));
+          if (lane == 0) MW[r * MWPR + h] = w;
+        }
       }
     }
     __syncthreads();
@@ -295,20 +307,31 @@ __global__ void __launch_bounds__(SG<T, B>::NT, SG<T, B>::MINB) k_stage1_slab(
       for (int i = tid; i < ROWS * MWPR; i += NT) MASK[i] = MW[i];
       T *COARSE = reinterpret_cast<T *>(P);
       T *VALS = reinterpret_cast<T *>(P + S::HEAD);
-      for (int r = wid; r < ROWS; r += NW) {
-        const int z = r / B, y = r % B;
-        const bool crow = (y % Q == 0) && (z % Q == 0);
-        unsigned base = RO[r];
+      for (int r0 = wid * RB; r0 < ROWS; r0 += NW * RB) {
+        // (rows without kept values or coarse values are not read:
+        // warp-uniform)
+        T d[RB][MWPR];
 #pragma unroll
-        for (int h = 0; h < MWPR; ++h) {
-          const unsigned w = MW[r * MWPR + h];
-          if (w != 0 || crow) {  // warp-uniform
+        for (int j = 0; j < RB; ++j) {
+          const int r = r0 + j, z = r / B, y = r % B;
+          const bool crow = (y % Q == 0) && (z % Q == 0);
+#pragma unroll
+          for (int h = 0; h < MWPR; ++h)
+            d[j][h] = (MW[r * MWPR + h] != 0 || crow) ? v.at(32 * h + lane, y, z) : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+          const int r = r0 + j, z = r / B, y = r % B;
+          const bool crow = (y % Q == 0) && (z % Q == 0);
+          unsigned base = RO[r];
+#pragma unroll
+          for (int h = 0; h < MWPR; ++h) {
+            const unsigned w = MW[r * MWPR + h];
             const int x = 32 * h + lane;
-            const T d = v.at(x, y, z);
-            if ((w >> lane) & 1u) VALS[base + __popc(w & ((1u << lane) - 1u))] = zero_low(d, a.zbits);
-            if (crow && x % Q == 0) COARSE[((z / Q) * 4 + y / Q) * 4 + x / Q] = d;
+            if ((w >> lane) & 1u) VALS[base + __popc(w & ((1u << lane) - 1u))] = zero_low(d[j][h], a.zbits);
+            if (crow && x % Q == 0) COARSE[((z / Q) * 4 + y / Q) * 4 + x / Q] = d[j][h];
+            base += __popc(w);
           }
-          base += __popc(w);
         }
       }
     }
@@ -337,7 +360,9 @@ __global__ void __launch_bounds__(SG<T, B>::NT, SG<T, B>::MINB) k_decompress_sla
   static_assert(SG<T, B>::OK, "slab geometry: B = 32 or 64");
   using S = SG<T, B>;
   using G = G2<T, B>;
-  constexpr int NT = S::NT, NW = S::NW, Q = S::Q, ES = S::ES, ROWS = S::ROWS, RPT = S::RPT, MWPR = S::MWPR;
+  constexpr int NT = S::NT, NW = S::NW, Q = S::Q, ES = S::ES, ROWS = S::ROWS, RPT = S::RPT, MWPR = S::MWPR,
+                RB = S::RB;
+  static_assert(ROWS % (NW * RB) == 0, "whole rounds of RB rows per warp");
   extern __shared__ __align__(128) unsigned char smem[];
   T *C = reinterpret_cast<T *>(smem);
   unsigned *RO = reinterpret_cast<unsigned *>(smem + S::CUBE_AL);  // row offsets
@@ -429,21 +454,34 @@ __global__ void __launch_bounds__(SG<T, B>::NT, SG<T, B>::MINB) k_decompress_sla
     // decodes to zeros
     const T *COARSE = reinterpret_cast<const T *>(P);
     const T *VALS = reinterpret_cast<const T *>(P + S::HEAD);
-    for (int r = wid; r < ROWS; r += NW) {
-      const int z = r / B, y = r % B;
-      unsigned base = bad ? 0u : RO[r];
+    // a warp takes RB consecutive rows a round: their mask words, then all
+    // their values, are loaded before any is used
+    for (int r0 = wid * RB; r0 < ROWS; r0 += NW * RB) {
+      unsigned w[RB][MWPR];
+      T d[RB][MWPR];
 #pragma unroll
-      for (int h = 0; h < MWPR; ++h) {
-        const int x = 32 * h + lane;
-        T d = T(0);
-        if (!bad) {
-          const unsigned w = MASK[r * MWPR + h];
-          if ((w >> lane) & 1u) d = VALS[base + __popc(w & ((1u << lane) - 1u))];
-          if ((y % Q) == 0 && (z % Q) == 0 && (x % Q) == 0) d = COARSE[((z / Q) * 4 + y / Q) * 4 + x / Q];
-          base += __popc(w);
+      for (int j = 0; j < RB; ++j)
+#pragma unroll
+        for (int h = 0; h < MWPR; ++h) w[j][h] = bad ? 0u : MASK[(r0 + j) * MWPR + h];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        const int r = r0 + j, z = r / B, y = r % B;
+        unsigned base = bad ? 0u : RO[r];
+#pragma unroll
+        for (int h = 0; h < MWPR; ++h) {
+          const int x = 32 * h + lane;
+          d[j][h] = T(0);
+          if (!bad) {
+            if ((w[j][h] >> lane) & 1u) d[j][h] = VALS[base + __popc(w[j][h] & ((1u << lane) - 1u))];
+            if ((y % Q) == 0 && (z % Q) == 0 && (x % Q) == 0) d[j][h] = COARSE[((z / Q) * 4 + y / Q) * 4 + x / Q];
+            base += __popc(w[j][h]);
+          }
         }
-        v.at(x, y, z) = d;
       }
+#pragma unroll
+      for (int j = 0; j < RB; ++j)
+#pragma unroll
+        for (int h = 0; h < MWPR; ++h) v.at(32 * h + lane, (r0 + j) % B, (r0 + j) / B) = d[j][h];
     }
     __syncthreads();
     if (!bad) slab_inv<T, B, KIND, NT>(v, C);
