@@ -16,6 +16,9 @@ pytestmark = pytest.mark.gpu
 
 KINDS = (O.W4, O.W4LI, O.W3AI)
 CASES = [(np.float32, 32, (64, 64, 96)), (np.float32, 16, (32, 48, 64)), (np.float64, 16, (32, 32, 48))]
+# the slab lanes (FP64 32^3, FP32 64^3) have a fast build too; a field of a
+# few of their blocks is enough for the per-coefficient gate
+COEF_CASES = CASES + [(np.float64, 32, (32, 32, 64)), (np.float32, 64, (64, 64, 64))]
 
 
 def _field(shape, dtype, seed=5):
@@ -41,7 +44,7 @@ def _blocks(shape, block):
 
 
 @pytest.mark.parametrize("kind", KINDS)
-@pytest.mark.parametrize("dtype,block,shape", CASES)
+@pytest.mark.parametrize("dtype,block,shape", COEF_CASES)
 def test_fast_coefficients_close_to_the_oracle(dtype, block, shape, kind):
     """W3ai (weights of at most 1/2 in magnitude): every coefficient within
     2^-20 of the field range of the oracle's.  W4 and W4li extrapolate at the
