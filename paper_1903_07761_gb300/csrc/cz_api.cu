@@ -985,7 +985,7 @@ int czi_fp64_probe(int grid, int threads, int iters, double *d_sink, void *strea
 // Not part of the ABI: the strict-bound divisor C of (kind, B), for tests.
 double czi_synthesis_norm(int kind, int block)
 {
-  if (kind < CZ_W4 || kind > CZ_W3AI || (block != 8 && block != 16 && block != 32)) return -1.0;
+  if (kind < CZ_W4 || kind > CZ_W3AI || (block != 8 && block != 16 && block != 32 && block != 64)) return -1.0;
   cz_params p{};
   p.kind = kind;
   p.block = block;

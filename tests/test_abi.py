@@ -119,7 +119,7 @@ def test_strict_divisor_equals_the_oracles(cz):
     L.czi_synthesis_norm.argtypes = [C.c_int, C.c_int]
     L.czi_synthesis_norm.restype = C.c_double
     for kind in (O.W4, O.W4LI, O.W3AI):
-        for B in (8, 16, 32):
+        for B in (8, 16, 32, 64):
             assert L.czi_synthesis_norm(kind, B) == O.synthesis_norm(kind, B)
 
 
