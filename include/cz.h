@@ -181,8 +181,9 @@ void cz_cache_destroy(cz_cache *c);
  * edge and type must match the cache's.  d_ws / ws_bytes as for
  * cz_decompress_blocks with n blocks.  *h_hits (may be NULL) receives the
  * number of requests served from the cache (blocks it held when the call
- * began).  Header handling as for cz_decompress.  Device-side errors (a
- * corrupt chunk) go to the status word of d_ws, as for
+ * began).  Header handling as for cz_decompress.  The call resets the
+ * status word of d_ws (also when every request is served from the cache);
+ * device-side errors (a corrupt chunk) go to it, as for
  * cz_decompress_blocks; the block is then cached as the zeros it decoded
  * to, so after a call that set the status word, empty the cache
  * (cz_cache_clear). */

@@ -218,6 +218,10 @@ int cz_cache_fetch(cz_cache *c, const void *d_in, size_t in_bytes, const void *h
 
   // enqueue: decode the missing blocks into the staging tiles, then the
   // copies
+  // the status word of d_ws reports this call: cz_decompress_blocks resets
+  // it when there are blocks to decode, a call served wholly from the cache
+  // resets it here
+  if (nm == 0 && d_ws && cudaMemsetAsync(d_ws, 0, sizeof(unsigned), s) != cudaSuccess) return CZ_ERR_CUDA;
   if (nm > 0) {
     std::memcpy(c->h_ids[u], miss.data(), sizeof(int32_t) * nm);
     if (cudaMemcpyAsync(c->d_ids[u], c->h_ids[u], sizeof(int32_t) * nm, cudaMemcpyHostToDevice, s) != cudaSuccess)

@@ -117,3 +117,21 @@ def test_bad_requests_are_refused_on_the_host():
         cz.Cache(0, 32)
     with pytest.raises(cz.CzError):
         cz.Cache(4, 12)
+
+
+def test_a_call_served_wholly_from_the_cache_resets_the_status_word():
+    """A fetch whose blocks are all held decodes nothing; it still resets
+    the status word of its workspace, so a workspace that held anything
+    before (here: every byte 0xAB) reports success."""
+    import torch
+    from paper_1903_07761_gb300 import cz
+    st, want = _stream(np.float32, 16, (16, 32, 32), seed=21)
+    c = cz.Cache(4, 16)
+    c.fetch(st, [0, 3])
+    ws = cz.Workspace()
+    ws.get(1 << 20).fill_(0xAB)
+    t, h = c.fetch(st, [3, 0, 3], ws=ws)  # raises on a bad status word
+    torch.cuda.synchronize()
+    assert h == 3
+    assert cz.cz_status(ws.buf.data_ptr(), torch.cuda.current_stream().cuda_stream) == cz.OK
+    np.testing.assert_array_equal(t.cpu().numpy().view(np.uint8), want[[3, 0, 3]].view(np.uint8))
