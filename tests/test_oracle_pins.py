@@ -613,3 +613,28 @@ def test_z8_shrinks_the_stage2_stream_of_a_smooth_field():
     s8 = O.compress(f, 32, O.W3AI, 1e-3, zbits=8)
     assert len(s8) < len(s0)
     assert abs(O.psnr(f, O.decompress(s8)) - O.psnr(f, O.decompress(s0))) < 0.1
+
+
+@pytest.mark.parametrize("dtype,B", [(np.float64, 32), (np.float32, 64)])
+def test_payloads_longer_than_a_token_field_split_as_defined(dtype, B):
+    """FP64 32^3 and FP32 64^3 payloads can exceed 65535 words (every
+    detail kept, eps = 0, on noise: no zero words).  A chunk then starts with
+    (65535, 0) tokens, one per full token field of literals, and the rest;
+    the literal words are the whole shuffled payload, and the stream decodes
+    to the exact transform's inverse."""
+    rng = np.random.default_rng(B)
+    f = rng.standard_normal((B, B, B)).astype(dtype)
+    s = O.compress(f, B, O.W4, 0.0)
+    d0, offs = O.chunk_table(s)
+    ch = s[d0 + int(offs[0]):d0 + int(offs[1])]
+    nnz, ntok = np.frombuffer(ch, np.uint32, count=2)
+    es = np.dtype(dtype).itemsize
+    W = (64 * es + B ** 3 // 8 + int(nnz) * es) // 4
+    assert nnz == B ** 3 - 64 and W > 65535
+    toks = np.frombuffer(ch, np.uint32, count=int(ntok), offset=8)
+    lit, zr = toks & 0xFFFF, toks >> 16
+    full = W // 65535 if W % 65535 else W // 65535 - 1
+    assert list(toks[:full]) == [65535] * full  # (65535, 0) while more than 65535 literals remain
+    assert int(lit.sum()) + int(zr.sum()) == W
+    assert len(ch) == 8 + 4 * int(ntok) + 4 * int(lit.sum())
+    np.testing.assert_array_equal(O.decompress(s), O.inv3d(O.W4, O.fwd3d(O.W4, f)).astype(dtype))
