@@ -255,6 +255,19 @@ int cz_batch_tune(int n, const cz_params *p, const void *const *d_fields,
                   uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes,
                   void *stream, int reps);
 
+/* The tuner's choices as JSON text, so that they outlive the process:
+ *   {"format": "cz-batch-knobs", "version": 1, "entries": [
+ *     {"signature": "<16 hex digits>", "s1_balanced": 0|1, "s2_div": 1..64}, ...]}
+ * A signature identifies a batch by the parameters of its fields (not by
+ * its buffers).  The choices are those of the device they were tuned on.
+ * Export: *len receives the text length + 1; with buf NULL only the size is
+ * returned, otherwise buf (cap bytes) receives the NUL-terminated text or
+ * CZ_ERR_CAPACITY.  Import: merges the entries of such a text (an entry
+ * replaces the one with its signature); CZ_ERR_ARG, and nothing changes,
+ * if the text is not of this form.  Host only: no CUDA call. */
+int cz_batch_knobs_export(char *buf, size_t cap, size_t *len);
+int cz_batch_knobs_import(const char *json);
+
 /* ---- quantities of a cell-struct array (the paper's solver stores all
  * quantities of a cell together and compresses chosen quantities from that
  * storage, Sec. 2.1 / 2.2) ---------------------------------------------------

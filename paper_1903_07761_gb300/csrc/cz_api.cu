@@ -10,7 +10,11 @@
 
 #include <cmath>
 #include <cstring>
+#include <cctype>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
+#include <string>
 #include <utility>
 #include <vector>
 
@@ -887,6 +891,97 @@ int cz_compress_aos(int n, const cz_params *p, const void *d_cells, int ncomp, c
                                                            ncells);
   if (cudaGetLastError() != cudaSuccess) return CZ_ERR_CUDA;
   return compress_batch_impl(n, p, fields.data(), d_outs, out_caps, d_out_bytes, wsb, f0, s, knobs_for(n, p));
+}
+
+// ---- the tuner's choices as JSON text
+int cz_batch_knobs_export(char *buf, size_t cap, size_t *len)
+{
+  if (!len) return CZ_ERR_ARG;
+  std::string out = "{\"format\": \"cz-batch-knobs\", \"version\": 1, \"entries\": [";
+  {
+    std::lock_guard<std::mutex> lock(g_knob_mu);
+    for (size_t i = 0; i < g_knobs.size(); ++i) {
+      char e[160];
+      std::snprintf(e, sizeof e, "%s{\"signature\": \"%016llx\", \"s1_balanced\": %d, \"s2_div\": %d}",
+                    i ? ", " : "", g_knobs[i].first, g_knobs[i].second.s1_balanced, g_knobs[i].second.s2_div);
+      out += e;
+    }
+  }
+  out += "]}";
+  *len = out.size() + 1;
+  if (!buf) return CZ_OK;
+  if (cap < out.size() + 1) return CZ_ERR_CAPACITY;
+  std::memcpy(buf, out.c_str(), out.size() + 1);
+  return CZ_OK;
+}
+
+int cz_batch_knobs_import(const char *json)
+{
+  if (!json) return CZ_ERR_ARG;
+  const std::string t(json);
+  auto ws = [&](size_t i) {
+    while (i < t.size() && (t[i] == ' ' || t[i] == '\n' || t[i] == '\r' || t[i] == '\t')) ++i;
+    return i;
+  };
+  // the value after "key": in t[b, e): a string's contents or a number's text
+  auto value = [&](size_t b, size_t e, const char *key, std::string &v) {
+    const std::string k = std::string("\"") + key + "\"";
+    const size_t at = t.find(k, b);
+    if (at == std::string::npos || at >= e) return false;
+    size_t i = ws(at + k.size());
+    if (i >= e || t[i] != ':') return false;
+    i = ws(i + 1);
+    if (i >= e) return false;
+    if (t[i] == '"') {
+      const size_t q = t.find('"', i + 1);
+      if (q == std::string::npos || q >= e) return false;
+      v = t.substr(i + 1, q - i - 1);
+    } else {
+      size_t j = i;
+      while (j < e && (std::isdigit((unsigned char)t[j]) || t[j] == '-')) ++j;
+      if (j == i) return false;
+      v = t.substr(i, j - i);
+    }
+    return true;
+  };
+  std::string v;
+  if (!value(0, t.size(), "format", v) || v != "cz-batch-knobs") return CZ_ERR_ARG;
+  if (!value(0, t.size(), "version", v) || v != "1") return CZ_ERR_ARG;
+  size_t i = t.find("\"entries\"");
+  if (i == std::string::npos) return CZ_ERR_ARG;
+  i = ws(i + 9);
+  if (i >= t.size() || t[i] != ':') return CZ_ERR_ARG;
+  i = ws(i + 1);
+  if (i >= t.size() || t[i] != '[') return CZ_ERR_ARG;
+  std::vector<std::pair<unsigned long long, BatchKnobs>> got;
+  i = ws(i + 1);
+  while (i < t.size() && t[i] != ']') {
+    if (t[i] != '{') return CZ_ERR_ARG;
+    const size_t e = t.find('}', i);
+    if (e == std::string::npos) return CZ_ERR_ARG;
+    std::string sig, s1, s2;
+    if (!value(i, e, "signature", sig) || !value(i, e, "s1_balanced", s1) || !value(i, e, "s2_div", s2))
+      return CZ_ERR_ARG;
+    if (sig.empty() || sig.size() > 16 || sig.find_first_not_of("0123456789abcdefABCDEF") != std::string::npos)
+      return CZ_ERR_ARG;
+    const int b1 = std::atoi(s1.c_str()), d2 = std::atoi(s2.c_str());
+    if ((s1 != "0" && s1 != "1") || d2 < 1 || d2 > 64 || s2 != std::to_string(d2)) return CZ_ERR_ARG;
+    got.push_back({std::stoull(sig, nullptr, 16), BatchKnobs{b1, d2}});
+    i = ws(e + 1);
+    if (i < t.size() && t[i] == ',') i = ws(i + 1);
+  }
+  if (i >= t.size()) return CZ_ERR_ARG;  // no closing bracket
+  std::lock_guard<std::mutex> lock(g_knob_mu);
+  for (const auto &g : got) {
+    bool found = false;
+    for (auto &k : g_knobs)
+      if (k.first == g.first) {
+        k.second = g.second;
+        found = true;
+      }
+    if (!found) g_knobs.push_back(g);
+  }
+  return CZ_OK;
 }
 
 int cz_stream_concat(int n, const void *const *h_streams, const size_t *sizes, void *h_out, size_t out_cap,

@@ -95,6 +95,8 @@ def lib():
             L.cz_strerror.restype = C.c_char_p
             L.cz_forward_dense.argtypes = [PP, P, P, P]
             L.cz_inverse_dense.argtypes = [PP, P, P, P]
+            L.cz_batch_knobs_export.argtypes = [P, C.c_size_t, C.POINTER(C.c_size_t)]
+            L.cz_batch_knobs_import.argtypes = [C.c_char_p]
             L.cz_aos_workspace_size.argtypes = [C.c_int, PP, C.POINTER(C.c_size_t)]
             L.cz_compress_aos.argtypes = [C.c_int, PP, P, C.c_int, P, C.POINTER(P), C.POINTER(C.c_size_t), P, P,
                                           C.c_size_t, P]
@@ -107,7 +109,8 @@ def lib():
             L.cz_cache_stats.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
             for f in (L.cz_compress_bound, L.cz_workspace_size, L.cz_compress, L.cz_decompress, L.cz_decompress_blocks,
                       L.cz_decompress_blocks_workspace_size, L.cz_cache_create, L.cz_cache_fetch, L.cz_cache_clear,
-                      L.cz_cache_stats, L.cz_aos_workspace_size, L.cz_compress_aos,
+                      L.cz_cache_stats, L.cz_aos_workspace_size, L.cz_compress_aos, L.cz_batch_knobs_export,
+                      L.cz_batch_knobs_import,
                       L.cz_compress_noalloc, L.cz_batch_workspace_size, L.cz_compress_batch,
                       L.cz_batch_tune, L.cz_stream_concat, L.cz_server_create, L.cz_server_submit, L.cz_server_poll,
                       L.cz_server_wait, L.cz_server_destroy, L.cz_read_header, L.cz_status, L.cz_forward_dense, L.cz_inverse_dense):
@@ -339,6 +342,28 @@ def decompress_blocks(stream_t, ids, nbytes: int | None = None, header: bytes | 
         if st != OK:
             raise CzError(st, "cz_decompress_blocks (device)")
     return out
+
+
+def save_tuning(path: str):
+    """Write the batch tuner's choices (cz_batch_knobs_export) to a JSON file."""
+    n = C.c_size_t()
+    r = lib().cz_batch_knobs_export(None, 0, C.byref(n))
+    if r != OK:
+        raise CzError(r, "cz_batch_knobs_export")
+    buf = C.create_string_buffer(n.value)
+    r = lib().cz_batch_knobs_export(C.cast(buf, C.c_void_p), n.value, C.byref(n))
+    if r != OK:
+        raise CzError(r, "cz_batch_knobs_export")
+    with open(path, "w") as fh:
+        fh.write(buf.value.decode())
+
+
+def load_tuning(path: str):
+    """Merge the batch tuner's choices from a JSON file (cz_batch_knobs_import)."""
+    with open(path) as fh:
+        r = lib().cz_batch_knobs_import(fh.read().encode())
+    if r != OK:
+        raise CzError(r, "cz_batch_knobs_import")
 
 
 def compress_aos(cells, comps, block=None, kind="w3ai", eps=1e-3, eps_mode: int = EPS_REL, stage2: bool = True,
