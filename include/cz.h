@@ -160,7 +160,8 @@ int cz_decompress_blocks_workspace_size(const cz_params *p, int n, size_t *bytes
  * element type and block edge (and as many tiles of staging for the blocks
  * a call decodes), allocated by cz_cache_create on the current device.
  * It serves one stream at a time: a call with another stream (other device
- * address, length or header) empties it first.  Not thread-safe: one host
+ * address, length or header) empties it first; a stream rewritten in place
+ * with the same length and header is not noticed, so clear the cache then.  Not thread-safe: one host
  * thread uses a cache at a time, with one CUDA stream. */
 typedef struct cz_cache cz_cache;
 
@@ -327,7 +328,10 @@ int cz_server_submit(void *server, const cz_request *req, uint64_t *ticket);
  * is reported once, then forgotten. */
 int cz_server_poll(void *server, uint64_t ticket, int *state, int *result,
                    double *latency_ms);
-/* Block until the ticket is done; then as cz_server_poll. */
+/* Block until the ticket is done; then as cz_server_poll.  CZ_ERR_ARG for
+ * an unknown ticket, or one that another thread's poll or wait reported (and
+ * so forgot) while this call waited.  submit, poll and wait may be called
+ * from several host threads at once. */
 int cz_server_wait(void *server, uint64_t ticket, int *result, double *latency_ms);
 /* Finish all queued and running work, then free the server. */
 int cz_server_destroy(void *server);

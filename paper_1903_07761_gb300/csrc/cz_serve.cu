@@ -184,8 +184,14 @@ class Server {
     std::unique_lock<std::mutex> lock(mu_);
     auto it = reqs_.find(ticket);
     if (it == reqs_.end()) return CZ_ERR_ARG;
-    done_cv_.wait(lock, [&] { return reqs_[ticket].state == CZ_REQ_DONE; });
+    // find, never operator[]: a ticket that another thread reported (and so
+    // removed) meanwhile must not come back as a fresh, never-done entry
+    done_cv_.wait(lock, [&] {
+      const auto j = reqs_.find(ticket);
+      return j == reqs_.end() || j->second.state == CZ_REQ_DONE;
+    });
     it = reqs_.find(ticket);
+    if (it == reqs_.end()) return CZ_ERR_ARG;  // reported to another caller
     int st;
     report(it->second, &st, result, latency_ms);
     reqs_.erase(it);
