@@ -222,3 +222,47 @@ def test_batch_tuner_choices_round_trip_through_json(cz, tmp_path):
         assert L.cz_batch_knobs_import(bad) == cz.ERR_ARG, bad
     cz.save_tuning(str(dst))
     assert dst.read_text() == before
+
+
+def test_read_header_refuses_or_parses_every_mutated_header(cz):
+    """Thousands of headers with one to three bytes changed: the parser
+    either refuses with CZ_ERR_CORRUPT or returns parameters that pass the
+    parameter checks (block edge, dims a multiple of it, codes in range, the
+    block count equal to the dims').  A change confined to bytes it does not
+    read (the level count, min/max, sizes, padding) leaves the parameters
+    as they were."""
+    f = np.random.default_rng(5).standard_normal((32, 64, 96)).astype(np.float32)
+    s = O.compress(f, 32, O.W4LI, 1e-3, O.EPS_REL, True)[:cz.HEADER_BYTES]
+    p0, t0 = cz.cz_read_header(s)
+    fields = lambda p: (p.nx, p.ny, p.nz, p.block, p.dtype, p.kind, p.stage2, p.eps_mode, p.bound_mode,
+                        p.flags, p.eps, p.range)
+    ignored = {25} | set(range(40, 64)) | set(range(72, 128))
+    rng = np.random.default_rng(11)
+    accepted = refused = 0
+    for _ in range(3000):
+        h = bytearray(s)
+        pos = rng.choice(cz.HEADER_BYTES, size=int(rng.integers(1, 4)), replace=False)
+        for q in pos:
+            h[q] ^= int(rng.integers(1, 256))
+        try:
+            p, _ = cz.cz_read_header(bytes(h))
+        except cz.CzError as e:
+            assert e.code == cz.ERR_CORRUPT, (pos, e.code)
+            assert not set(pos.tolist()) <= ignored, pos
+            refused += 1
+            continue
+        accepted += 1
+        if set(pos.tolist()) <= ignored:
+            assert fields(p) == fields(p0), pos
+            continue
+        assert p.block in (8, 16, 32, 64) and (p.block != 64 or p.dtype == cz.F32)
+        assert all(n > 0 and n % p.block == 0 for n in (p.nx, p.ny, p.nz))
+        assert p.dtype in (cz.F32, cz.F64) and p.kind in (cz.W4, cz.W4LI, cz.W3AI)
+        assert p.stage2 in (0, 1) and p.eps_mode in (cz.EPS_REL, cz.EPS_ABS)
+        assert p.bound_mode in (cz.BOUND_PAPER, cz.BOUND_STRICT) and p.eps >= 0
+        nb = int.from_bytes(bytes(h[28:32]), "little")
+        assert nb == (p.nx // p.block) * (p.ny // p.block) * (p.nz // p.block)
+    assert accepted > 0 and refused > 0
+    # shorter than a header: refused as an argument error
+    buf = C.create_string_buffer(s, cz.HEADER_BYTES)
+    assert cz.lib().cz_read_header(buf, cz.HEADER_BYTES - 1, C.byref(cz.Params()), None) == cz.ERR_ARG
