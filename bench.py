@@ -540,7 +540,7 @@ def run_gpu(args, rank, world, local_rank):
         slabs = max(1, args.cpu_slabs)
         byts, secs = cpu_oracle_run(field_np, B, kind, args.eps, slabs, fmax - fmin)
         cpu = {"value": byts / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"compress+decompress of the first {slabs} z-slab(s) of 32 cells "
+               "sample": f"compress+decompress of the first {min(slabs, n // B)} of the {n // B} z-slabs of {B} cells "
                          f"({byts / 2**20:.0f} MiB, {slabs * (n // B) ** 2} blocks) of the same "
                          f"field, threshold from the full range, single thread, {secs:.1f} s"}
         # context: the same oracle on every host core (independent tasks)
@@ -631,7 +631,7 @@ def run_reference(args, rank, world):
         times.append(secs)
     ms = 1e3 * sum(times) / len(times)
     value = byts / (ms * 1e-3) / 1e9
-    sample = (f"compress+decompress of one z-slab of 32 cells ({byts / 2**20:.0f} MiB, "
+    sample = (f"compress+decompress of one z-slab of {B} cells ({byts / 2**20:.0f} MiB, "
               f"{(n // B) ** 2} blocks) of the {n}^3 field per step, single thread")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
