@@ -106,8 +106,9 @@ int cz_compress_bound(const cz_params *p, size_t *bytes);
  * word, the min/max keys, one u64 look-back word per block, a block table
  * (16 bytes per block) and the staging slots the chunks are built in (room
  * for the largest chunk of every block, about the size of the field).  FP64
- * with 32^3 blocks adds one 260 KiB scratch block per CTA of the kernels
- * that hold a block or a large payload in global memory.
+ * with 32^3 blocks and FP32 with 64^3 blocks add one scratch block per CTA
+ * (260 KiB / 1.03 MiB) of the kernels that hold a block or a large payload
+ * in global memory.
  * Needs the current device (it sizes the persistent grids by its SM count). */
 int cz_workspace_size(const cz_params *p, size_t *bytes);
 
