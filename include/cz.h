@@ -228,8 +228,8 @@ int cz_compress_noalloc(const cz_params *p, const void *d_field, void *d_out,
 
 /* ---- many fields in one call (the paper compresses many blocks of many
  * quantities per node, Sec. 2.2; here whole fields are batched) ----------
- * Fields with the same dtype, block, kind, stage2 and bound_mode (at most
- * 32 at a time, in the order given) share one persistent launch of each
+ * Fields with the same dtype, block, kind, stage2, bound_mode and flags (at
+ * most 32 at a time, in the order given) share one persistent launch of each
  * kernel: their blocks form one index space, each block finds its field,
  * and every field still gets its own stream, identical byte for byte to the
  * one cz_compress would write.  Field i is d_fields[i] (parameters p[i]),
@@ -295,8 +295,8 @@ int cz_compress_aos(int n, const cz_params *p, const void *d_cells, int ncomp, c
  * (the HBM budget; every admitted request takes its workspace from it) and
  * `streams` CUDA streams, and runs a worker thread that admits waiting
  * requests in arrival order as streams and pool memory free up.  Compress
- * requests that wait together and share dtype, block, kind, stage2 and
- * bound_mode are launched as one cz_compress_batch call.  Requests keep
+ * requests that wait together and share dtype, block, kind, stage2,
+ * bound_mode and flags are launched as one cz_compress_batch call.  Requests keep
  * their buffers (caller-owned, on the device) until they are done; results
  * are identical to cz_compress / cz_decompress on the same inputs.  Latency
  * is measured from submission to the worker seeing the request's work
