@@ -644,7 +644,7 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def main():
+def build_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -661,7 +661,11 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-fields comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-requests comparison")
     ap.add_argument("--no-fp64", action="store_true", help="skip the 768^3 FP64 case")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = build_parser().parse_args()
     if args.warmup < 3:
         args.warmup = 3
 

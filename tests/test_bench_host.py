@@ -41,3 +41,32 @@ def test_all_cores_oracle_run_covers_its_sample():
     f = inputs.cavitation("p", 64, np.float32, seed=3)
     byts, secs, cores = bench.cpu_oracle_all_cores(f, 32, O.W3AI, 1e-3, 2, float(f.max() - f.min()))
     assert byts == f.nbytes and secs > 0 and cores >= 1
+
+
+def test_profile_commands_run_committed_files_with_valid_flags():
+    """Every profile summary gives the command that made it; each
+    `python bench.py ...` there must still parse with the benchmark's
+    options, and every file a command names must be in the repository."""
+    import glob
+    import importlib.util
+    import shlex
+    spec = importlib.util.spec_from_file_location("bench_for_profiles", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    parser = bench.build_parser()
+    tracked = set(subprocess.run(["git", "ls-files"], cwd=ROOT, capture_output=True, text=True,
+                                 check=True).stdout.split())
+    found = 0
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        text = open(path).read().replace("\\\n", " ")
+        for line in text.splitlines():
+            line = line.split("#")[0]
+            if "python bench.py" not in line:
+                continue
+            args = shlex.split(line.split("python bench.py", 1)[1])
+            parser.parse_args(args)  # exits on an unknown option
+            found += 1
+        for name in ("bench.py", "__graft_entry__.py"):
+            if name in text:
+                assert name in tracked
+    assert found >= 3
