@@ -158,6 +158,15 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
+def workload_config(n: int, B: int, kind: str, world: int) -> dict:
+    """The `config` object of the JSON line (the same for both arms)."""
+    return {"workload": f"p-field {n}^3 FP32, {B}^3 blocks, {kind}, eps=1e-3*range, stage2 on, "
+                        f"range computed by the codec",
+            "global_batch": world, "field_bytes": 4 * n ** 3,
+            "l2": f"inputs larger than L2 ({4 * n ** 3 / 2**30:.0f} GiB field per step), no flush needed",
+            "parallelism": f"replicas x{world} (independent fields, no collective)"}
+
+
 def make_field(n: int, seed: int):
     from paper_1903_07761_gb300 import inputs
     return inputs.cavitation("p", n, seed=seed)
@@ -365,6 +374,28 @@ def run_gpu(args, rank, world, local_rank):
     psnr = 20 * math.log10((fmax - fmin) / (2 * math.sqrt(mse))) if mse > 0 else float("inf")
     del diff
 
+    # compression with the range supplied by the caller (no min/max pass):
+    # algorithmic bytes N*s read + S written
+    p_rng = cz.params_for(tuple(field.shape), False, B, kind, args.eps, cz.EPS_REL, True, fmax - fmin)
+    rng_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+    compress_call(p_rng)
+    for a_, b_ in rng_ev:
+        a_.record(stream)
+        compress_call(p_rng)
+        b_.record(stream)
+    torch.cuda.synchronize()
+    st = cz.cz_status(ws.data_ptr(), s)
+    if st != cz.OK:
+        raise cz.CzError(st, "cz_compress with the range supplied (device)")
+    rng_len = int(nb.item())
+    rng_ms = statistics.median(a_.elapsed_time(b_) for a_, b_ in rng_ev)
+    compress_range_supplied = {"ms": rng_ms, "gbs": nbytes_field / rng_ms / 1e6,
+                               "hbm_frac": (nbytes_field + rng_len) / (rng_ms * 1e-3) / 1e9 / measured_peaks()[0],
+                               "algorithmic_bytes": nbytes_field + rng_len, "stream_bytes": rng_len,
+                               "what": "cz_compress with p.range = max - min given (no min/max pass), "
+                                       "median of 10 calls; frac of measured HBM peak by (N*s + S) / t"}
+    compress_call()  # the headline stream again (its header differs: min / max recorded)
+
     # bytes the stage kernel writes: one staging slot per block,
     # [nnz | 0 | 64 coarse | B^3/8 mask bytes | nnz values]
     nblocks = (n // B) ** 3
@@ -444,6 +475,19 @@ def run_gpu(args, rank, world, local_rank):
         e2e = {"value": world * nbytes_field / e2e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": copied_in, "d2h_bytes_per_step": copied_out,
                "fields_in_flight": depth, "steps": reps}
+        # the host link as plain cudaMemcpyAsync calls see it (one 4 GiB
+        # copy at a time, pinned host memory), the bound of the figure above
+        lib.czi_link_probe.argtypes = [cz.C.c_void_p, cz.C.c_void_p, cz.C.c_size_t, cz.C.c_int, cz.C.c_int,
+                                       cz.C.c_void_p, cz.C.POINTER(cz.C.c_float)]
+        lib.czi_link_probe.restype = cz.C.c_int
+        link = {}
+        L1 = lanes[1]
+        for name, hb, db, dr in (("h2d_gbs", h_in, L1["field"], 0), ("d2h_gbs", L1["h_out"], L1["rec"], 1)):
+            msv = cz.C.c_float()
+            if lib.czi_link_probe(hb.data_ptr(), db.data_ptr(), nbytes_field, 3, dr, s, cz.C.byref(msv)) == cz.OK:
+                link[name] = 3 * nbytes_field / (msv.value * 1e-3) / 1e9
+        link["how"] = "3 x cudaMemcpyAsync of the 4 GiB field each way, pinned host buffer, CUDA events"
+        e2e["host_link"] = link
         del lanes
 
     # other kinds (context: the headline is per kind), and bit zeroing
@@ -554,15 +598,18 @@ def run_gpu(args, rank, world, local_rank):
             cpu["all_cores"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:200]}
 
     peak, peak_src = measured_peaks()
-    # the major kernels' algorithmic bytes per launch: k_minmax reads the
-    # field; k_stage1 reads it and writes the staging slots; k_decompress2
-    # reads the decoded payloads (slots without their 8-byte headers) and
-    # writes the field.  `roofline` describes the one with the largest time
-    # share, the others follow in `roofline_kernels`.
+    # the major kernels' algorithmic bytes per launch, by the method's own
+    # traffic (what compression and decompression must move): k_minmax reads
+    # the field (N*s); the stage kernel reads it and the compressed data is
+    # written (N*s + S); the decode kernel reads the compressed data and
+    # writes the field (S + N*s).  Stage-1 payloads in the workspace (S1,
+    # re-read by separate stage-2 passes) are not counted.  `roofline`
+    # describes the kernel with the largest time share, the others follow
+    # in `roofline_kernels`.
     kernels = {
-        "k_decompress2": (dec2_ms, nbytes_field + stage1_written - 8 * nblocks,
+        "k_decompress2": (dec2_ms, nbytes_field + stream_len,
                           "k_decompress2 (payload scatter, inverse transform, TMA store of the tile)"),
-        "k_stage1": (stage1_ms, nbytes_field + stage1_written,
+        "k_stage1": (stage1_ms, nbytes_field + stream_len,
                      "k_stage1 (load, transform, threshold, mask, compaction)"),
         "k_minmax": (range_ms, nbytes_field, "k_minmax (min/max of the field for the relative threshold)"),
     }
@@ -582,11 +629,7 @@ def run_gpu(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded bubble-cloud pressure field; paper datasets unavailable)",
-        "config": {"workload": f"p-field {n}^3 FP32, {B}^3 blocks, {args.kind}, eps=1e-3*range, "
-                               f"stage2 on, range computed on device",
-                   "global_batch": world, "field_bytes": nbytes_field,
-                   "l2": "inputs larger than L2 (4 GiB field per step), no flush needed",
-                   "parallelism": f"replicas x{world} (independent fields, no collective)"},
+        "config": workload_config(n, B, args.kind, world),
         "compress_gbs": nbytes_field / comp_ms / 1e6, "decompress_gbs": nbytes_field / dec_ms / 1e6,
         "compress_ms": comp_ms, "decompress_ms": dec_ms,
         "cr": nbytes_field / stream_len, "psnr_db": psnr, "linf_over_t": linf / (args.eps * (fmax - fmin)),
@@ -595,6 +638,8 @@ def run_gpu(args, rank, world, local_rank):
         "stage_ms": {"a0_minmax": range_ms, "k_stage1": stage1_ms, "k_stage2": stage2_ms,
                      "k_place+k_copy": place_ms, "k_unstage": unstage_ms, "k_decompress2": dec2_ms},
         "compress_hbm_frac": (nbytes_field * 2 + stream_len) / (comp_ms * 1e-3) / 1e9 / peak,
+        "stage1_bytes_written": stage1_written,
+        "compress_range_supplied": compress_range_supplied,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
@@ -615,8 +660,7 @@ def run_gpu(args, rank, world, local_rank):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    from paper_1903_07761_gb300 import cz as _cz  # noqa: F401  (kind names only)
-    import numpy as np
+    # the oracle and the input generator only (nothing of the CUDA library)
     kind = {"w4": 0, "w4li": 1, "w3ai": 2}[args.kind]
     n, B = args.n, args.block
     field_np = make_field(n, seed=2000)
@@ -637,8 +681,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"p-field {n}^3 FP32, {B}^3 blocks, {args.kind}, eps=1e-3*range, "
-                               f"stage2 on (CPU oracle on a bounded sample)"},
+        "config": workload_config(n, B, args.kind, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)

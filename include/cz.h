@@ -61,9 +61,11 @@ enum { CZ_BOUND_PAPER = 0, CZ_BOUND_STRICT = 1 };
  * compiler fuse multiply-adds (one rounding instead of two): coefficients
  * move by a few ulps, so a detail next to the threshold may be kept or
  * dropped differently and streams are no longer bit-identical to the exact
- * build's, within the tolerances tests/test_gpu_fast.py states.  The flag
- * is recorded in the stream header; decompression uses the build the
- * stream was made with. */
+ * build's.  It keeps every coefficient within 2^-20 of the field range of
+ * the exact one and the PSNR within 0.01 dB.  W3ai only: with W4 or W4li
+ * (whose extrapolating rows carry weights up to 35/16) the flag is refused
+ * with CZ_ERR_ARG.  The flag is recorded in the stream header;
+ * decompression uses the build the stream was made with. */
 enum { CZ_FLAG_FAST = 1 };
 /* flags: CZ_FLAG_ZERO4 / CZ_FLAG_ZERO8 zero the 4 / 8 least significant
  * bits of every kept detail coefficient before the lossless substage (bit
@@ -211,8 +213,11 @@ int cz_cache_stats(const cz_cache *c, int *held, long long *hits, long long *mis
  * may hold what is free.  Instead of a caller-supplied d_ws this call uses
  * a CZ_NOALLOC_WS_BYTES array that the library owns in device memory, so
  * it works only for fields whose cz_workspace_size() is at most
- * CZ_NOALLOC_WS_BYTES (e.g. 64 blocks of 32^3 FP32, a 128^3 field); larger
- * fields return CZ_ERR_CAPACITY before anything is enqueued.
+ * CZ_NOALLOC_WS_BYTES; larger fields return CZ_ERR_CAPACITY before
+ * anything is enqueued.  The workspace size depends on the device's SM
+ * count (it holds one staging arena per CTA of the persistent stage
+ * kernel): on a 152-SM GB300 the limit is 456 blocks of 32^3 FP32 (e.g. a
+ * 128^3 field of 64 blocks fits, a 256^3 field of 512 blocks does not).
  *  - The first call on a device looks up the array's address with that
  *    device current (the CUDA runtime loads the library's module then).
  *    Make that first call before any stream capture begins.
@@ -220,11 +225,19 @@ int cz_cache_stats(const cz_cache *c, int *held, long long *hits, long long *mis
  *    device (different streams, or different host threads) race on it and
  *    corrupt each other's output.  Calls enqueued on one stream run one
  *    after the other and are safe.
- *  - Device-side status is not reported; a stream length in *d_out_bytes
- *    above out_cap means the output did not fit.
- * Other arguments and host-side errors are those of cz_compress. */
+ *  - The device status word of a call (CZ_ERR_CAPACITY when the output did
+ *    not fit, CZ_ERR_TIMEOUT, ...) stays in the array until the next call:
+ *    read it with cz_noalloc_status().
+ * Other arguments and host-side errors are those of cz_compress (null or
+ * misaligned buffers: CZ_ERR_ARG before any CUDA call). */
 int cz_compress_noalloc(const cz_params *p, const void *d_field, void *d_out,
                         size_t out_cap, uint64_t *d_out_bytes, void *stream);
+
+/* Synchronise `stream` and return the device status word of the last
+ * cz_compress_noalloc call on the current device (CZ_OK or a CZ_ERR_* code
+ * set by a kernel).  Calls that overlap on the device share the word as
+ * they share the array.  CZ_ERR_CUDA if the array cannot be reached. */
+int cz_noalloc_status(void *stream);
 
 /* ---- many fields in one call (the paper compresses many blocks of many
  * quantities per node, Sec. 2.2; here whole fields are batched) ----------

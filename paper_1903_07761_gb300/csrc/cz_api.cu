@@ -55,6 +55,10 @@ int check(const cz_params *p, Shape *sh)
   if (p->stage2 != 0 && p->stage2 != 1) return CZ_ERR_ARG;
   if (p->bound_mode != CZ_BOUND_PAPER && p->bound_mode != CZ_BOUND_STRICT) return CZ_ERR_ARG;
   if (p->flags & ~(CZ_FLAG_FAST | CZ_FLAG_ZERO4 | CZ_FLAG_ZERO8)) return CZ_ERR_ARG;
+  // the fast build keeps the PSNR of the exact build within 0.01 dB only for
+  // W3ai; W4 and W4li (extrapolating rows with weights up to 35/16) are
+  // refused with it
+  if ((p->flags & CZ_FLAG_FAST) && p->kind != CZ_W3AI) return CZ_ERR_ARG;
   const int zf = p->flags & (CZ_FLAG_ZERO4 | CZ_FLAG_ZERO8);
   if (zf == (CZ_FLAG_ZERO4 | CZ_FLAG_ZERO8)) return CZ_ERR_ARG;  // one zeroing width at most
   if (zf && p->bound_mode == CZ_BOUND_STRICT) return CZ_ERR_ARG;  // the strict bound excludes zeroing
@@ -373,6 +377,42 @@ __global__ void k_fp64_probe(int iters, double *sink)
 #pragma unroll
   for (int q = 0; q < 8; ++q) s += a[q];
   if (s == 0.0) *sink = s;  // never true; keeps the chains live
+}
+
+// Drives the codec's bounded waits past a short limit (tests of the
+// timeout paths; nothing faults and nothing waits without bound).
+//  which 0: the look-back of the chunk-offset scan.  One warp per tile;
+//    tile `skip` never publishes its aggregate, so the tiles after it spin
+//    until `limit`, then record ST_TIMEOUT and return.  out[t] = exclusive
+//    prefix seen by tile t (t for the tiles before `skip`: aggregates of 1).
+//  which 1: an mbarrier armed for 16 bytes that no copy delivers.  Every
+//    thread waits until `limit`; the CTA decides at one barrier, as the
+//    codec kernels do, and thread 0 records ST_TIMEOUT.  out[tid] = the
+//    CTA's decision (1: gave up) as each thread saw it.
+__global__ void k_wait_probe(int which, int skip, unsigned limit, unsigned *status, unsigned long long *state,
+                             unsigned long long *out)
+{
+  if (which == 0) {
+    const int tile = blockIdx.x;
+    if (tile == skip) return;
+    const unsigned long long ex = lookback(state, tile, 1ull, status, (int)ST_TIMEOUT, 0, limit);
+    if (threadIdx.x == 0) out[tile] = ex;
+    return;
+  }
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ unsigned s_to;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    s_to = 0;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)), "r"(16u)
+                 : "memory");
+  }
+  __syncthreads();
+  if (!mbar_wait(&bar, 0u, limit)) s_to = 1u;
+  __syncthreads();
+  const unsigned gave_up = *(volatile unsigned *)&s_to;
+  if (threadIdx.x == 0 && gave_up) atomicCAS(status, 0u, ST_TIMEOUT);
+  out[threadIdx.x] = gave_up;
 }
 
 // ---- batched compression
@@ -1075,6 +1115,57 @@ int czi_fp64_probe(int grid, int threads, int iters, double *d_sink, void *strea
   if (grid < 1 || threads < 32 || threads > 1024 || iters < 1 || !d_sink) return CZ_ERR_ARG;
   k_fp64_probe<<<grid, threads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(iters, d_sink);
   return cudaGetLastError() == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
+}
+
+// Not part of the ABI: runs k_wait_probe (see there) on `stream`.
+// which 0: `tiles` (1..1024) warps, d_state = `tiles` zeroed u64 words,
+// d_out = `tiles` u64; which 1: one CTA of `tiles` (32..1024, a multiple
+// of 32) threads, d_out = `tiles` u64.  d_status: a zeroed u32.
+int czi_wait_probe(int which, int tiles, int skip, unsigned limit, void *d_status, void *d_state, void *d_out,
+                   void *stream)
+{
+  if ((which != 0 && which != 1) || !d_status || !d_out || limit < 1 || limit > (1u << 20)) return CZ_ERR_ARG;
+  if (which == 0 && (tiles < 1 || tiles > 1024 || !d_state)) return CZ_ERR_ARG;
+  if (which == 1 && (tiles < 32 || tiles > 1024 || tiles % 32)) return CZ_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (which == 0)
+    k_wait_probe<<<tiles, 32, 0, s>>>(0, skip, limit, reinterpret_cast<unsigned *>(d_status),
+                                      reinterpret_cast<unsigned long long *>(d_state),
+                                      reinterpret_cast<unsigned long long *>(d_out));
+  else
+    k_wait_probe<<<1, tiles, 0, s>>>(1, skip, limit, reinterpret_cast<unsigned *>(d_status), nullptr,
+                                     reinterpret_cast<unsigned long long *>(d_out));
+  return cudaGetLastError() == cudaSuccess ? CZ_OK : CZ_ERR_CUDA;
+}
+
+// Not part of the ABI: the host link's copy rate as plain cudaMemcpyAsync
+// calls see it (context for the end-to-end figure).  `reps` copies of
+// `bytes` between the host buffer h (pinned by the caller) and the device
+// buffer d, host to device (dir 0) or device to host (dir 1), timed with
+// events on `stream`; *ms receives the total time.  Synchronises.
+int czi_link_probe(void *h, void *d, size_t bytes, int reps, int dir, void *stream, float *ms)
+{
+  if (!h || !d || !ms || bytes == 0 || reps < 1 || (dir != 0 && dir != 1)) return CZ_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return CZ_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return CZ_ERR_CUDA;
+  }
+  int r = CZ_OK;
+  if (cudaEventRecord(e0, s) != cudaSuccess) r = CZ_ERR_CUDA;
+  for (int i = 0; i < reps && r == CZ_OK; ++i) {
+    const cudaError_t e = dir == 0 ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s)
+                                   : cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) r = CZ_ERR_CUDA;
+  }
+  if (r == CZ_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+    r = CZ_ERR_CUDA;
+  if (r == CZ_OK && cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) r = CZ_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return r;
 }
 
 // Not part of the ABI: the strict-bound divisor C of (kind, B), for tests.

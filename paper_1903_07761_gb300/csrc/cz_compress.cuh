@@ -127,21 +127,23 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
   };
   unsigned long long aoff = 0;  // bytes used in this CTA's staging arena (the same in every thread)
   __shared__ BlockWalk s_wk;  // the next tile's block (one field)
+  // set by every thread whose wait for the tile gives up; read by all
+  // threads only after a barrier, so the CTA decides as one
+  __shared__ unsigned s_to;
   if (tid == 0) {
     s_wk.init(blockIdx.x + gridDim.x, gridDim.x, a.nbx, a.nby);
     mbar_init(&s_bar);
+    s_to = 0;
     if ((int)blockIdx.x < a.nblocks) tile_of(blockIdx.x);
   }
   __syncthreads();
   unsigned phase = 0;
 
   for (int bid = blockIdx.x; bid < a.nblocks; bid += gridDim.x) {
-    if (!mbar_wait(&s_bar, phase)) {
-      // the copy never completed: record, wait once more for it, stop
-      if (tid == 0) atomicCAS(&ws->status, 0u, ST_TIMEOUT);
-      mbar_wait(&s_bar, phase);
-      break;
-    }
+    // a thread whose wait gives up records it and goes on with whatever the
+    // tile holds (in-bounds arithmetic on it, nothing stored): no barrier
+    // below waits for a thread that has left
+    if (!mbar_wait(&s_bar, phase)) s_to = 1u;
     phase ^= 1u;
 
     // ---- tile -> registers; the next tile is fetched after the
@@ -156,7 +158,9 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
 
     // ---- forward transform
     fwd_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg, [&] {
-      if (tid == 0 && nb < a.nblocks) {
+      // (after a barrier: a timeout of this block's copy is visible here,
+      // and then no further copy is started)
+      if (tid == 0 && nb < a.nblocks && !*(volatile unsigned *)&s_to) {
         if constexpr (NF == 1) {
           tma_load_tile(&maps.tm[0], PF, &s_bar, s_wk.bx * B, s_wk.by * B, s_wk.bz * B, G::TILE);
           s_wk.next();
@@ -195,6 +199,19 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
       }
     }
     __syncthreads();
+    if (*(volatile unsigned *)&s_to) {
+      // the tile never arrived (in some thread's view): the whole CTA stops
+      // here.  Wait once more, bounded, for the one copy in flight (no
+      // later copy was started), and mark this block and the CTA's later
+      // blocks lost, so that the stage-2 and placement kernels skip them.
+      if (tid == 0) {
+        atomicCAS(&ws->status, 0u, ST_TIMEOUT);
+        mbar_wait(&s_bar, phase ^ 1u);
+      }
+      for (long long b = bid + (long long)tid * gridDim.x; b < a.nblocks; b += (long long)NT * gridDim.x)
+        a.table[2 * b + 1] = TB_LOST;
+      return;
+    }
 
     // ---- slot [nnz | 0 | raw payload] -> this CTA's staging arena
     const int pbytes = 64 * ES + G::MASKB + (int)nnz * ES;

@@ -617,14 +617,16 @@ constexpr unsigned long long LB_VAL = (1ull << 62) - 1;
 constexpr unsigned LB_SPIN_LIMIT = 1u << 22;
 
 // Called by all lanes of one warp; returns the exclusive prefix of `agg`.
-// On a wait that exceeds the spin limit, sets *status (if still 0) to
+// On a wait that exceeds `limit` spins, sets *status (if still 0) to
 // `timeout_code` and returns what it has: the caller's output is then
-// wrong but the kernel ends.
+// wrong but the kernel ends.  The spin count and the decision to give up
+// are the same in every lane (they follow warp-wide ballots).
 // Indices below `first` count as an inclusive prefix of 0 (a segment of
 // the state array starts there).
 __device__ __forceinline__ unsigned long long lookback(unsigned long long *state, int bid,
                                                        unsigned long long agg,
-                                                       unsigned int *status, int timeout_code, int first = 0)
+                                                       unsigned int *status, int timeout_code, int first = 0,
+                                                       unsigned limit = LB_SPIN_LIMIT)
 {
   const int lane = threadIdx.x & 31;
   using aref = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
@@ -642,7 +644,7 @@ __device__ __forceinline__ unsigned long long lookback(unsigned long long *state
     const unsigned upto = pm ? (pm & (~pm + 1)) : 0u;  // lowest prefix lane
     const unsigned need = pm ? (upto | (upto - 1)) : FULL;
     if (im & need) {
-      if (++spins > LB_SPIN_LIMIT) {
+      if (++spins > limit) {
         if (lane == 0) atomicCAS(status, 0u, (unsigned)timeout_code);
         break;
       }

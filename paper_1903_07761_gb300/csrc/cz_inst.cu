@@ -1,7 +1,8 @@
 // cz_inst.cu -- kernel instantiations for one (element type, block edge).
 // Built once per combination with -DCZ_T=float|double -DCZ_TNAME=f32|f64
-// -DCZ_B=8|16|32 (and once more with -DCZ_FAST for the contracting build)
-// so the heavily unrolled kernels compile in parallel.
+// -DCZ_B=8|16|32|64 (and once more with -DCZ_FAST for the contracting
+// build, which serves W3ai only) so the heavily unrolled kernels compile in
+// parallel.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -262,11 +263,16 @@ extern "C" cudaError_t CZ_CAT(czl_compress_, CZ_SUFFIX)(int kind, const CUtensor
                                                          int grid2, int grid3, const cudaEvent_t *marks,
                                                          cudaStream_t s)
 {
+#ifdef CZ_FAST
+  if (kind != W3AI) return cudaErrorInvalidValue;
+  return compress_k<W3AI>(*tm, *a, *sa, *pa, grid, grid2, grid3, marks, s);
+#else
   switch (kind) {
     case W4: return compress_k<W4>(*tm, *a, *sa, *pa, grid, grid2, grid3, marks, s);
     case W4LI: return compress_k<W4LI>(*tm, *a, *sa, *pa, grid, grid2, grid3, marks, s);
     default: return compress_k<W3AI>(*tm, *a, *sa, *pa, grid, grid2, grid3, marks, s);
   }
+#endif
 }
 
 extern "C" cudaError_t CZ_CAT(czl_compress_batch_, CZ_SUFFIX)(int kind, const StageMaps<MAXF> *maps,
@@ -274,27 +280,41 @@ extern "C" cudaError_t CZ_CAT(czl_compress_batch_, CZ_SUFFIX)(int kind, const St
                                                                const BatchOut *bo, const PlaceArgs *pa, int grid,
                                                                int grid2, int grid3, int tiles, cudaStream_t s)
 {
+#ifdef CZ_FAST
+  if (kind != W3AI) return cudaErrorInvalidValue;
+  return compress_batch_k<W3AI>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, s);
+#else
   switch (kind) {
     case W4: return compress_batch_k<W4>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, s);
     case W4LI: return compress_batch_k<W4LI>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, s);
     default: return compress_batch_k<W3AI>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, s);
   }
+#endif
 }
 
 extern "C" cudaError_t CZ_CAT(czl_decompress_, CZ_SUFFIX)(int kind, const CUtensorMap *om, const InvArgs *a,
                                                            const UnArgs *ua, int grid, int gridu, int gridub,
                                                            const cudaEvent_t *marks, cudaStream_t s)
 {
+#ifdef CZ_FAST
+  if (kind != W3AI) return cudaErrorInvalidValue;
+  return decompress_k<W3AI>(*om, *a, *ua, grid, gridu, gridub, marks, s);
+#else
   switch (kind) {
     case W4: return decompress_k<W4>(*om, *a, *ua, grid, gridu, gridub, marks, s);
     case W4LI: return decompress_k<W4LI>(*om, *a, *ua, grid, gridu, gridub, marks, s);
     default: return decompress_k<W3AI>(*om, *a, *ua, grid, gridu, gridub, marks, s);
   }
+#endif
 }
 
 extern "C" cudaError_t CZ_CAT(czl_dense_, CZ_SUFFIX)(int kind, int fwd, const DenseArgs *a, int nblocks,
                                                       cudaStream_t s)
 {
+#ifdef CZ_FAST
+  if (kind != W3AI) return cudaErrorInvalidValue;
+  return fwd ? dense_k<W3AI, true>(*a, nblocks, s) : dense_k<W3AI, false>(*a, nblocks, s);
+#else
   if (fwd) {
     switch (kind) {
       case W4: return dense_k<W4, true>(*a, nblocks, s);
@@ -307,6 +327,7 @@ extern "C" cudaError_t CZ_CAT(czl_dense_, CZ_SUFFIX)(int kind, int fwd, const De
     case W4LI: return dense_k<W4LI, false>(*a, nblocks, s);
     default: return dense_k<W3AI, false>(*a, nblocks, s);
   }
+#endif
 }
 
 // CTAs per SM of the stage kernel (which = 0), the decompress kernel
@@ -336,6 +357,10 @@ static int occupancy_query(int kind, int which)
   if (which == 3) return G::HAS_BIG ? occupancy_s2<true>() : 1;
   if (which == 4) return occupancy_u<false>();
   if (which == 5) return G::HAS_BIG ? occupancy_u<true>() : 1;
+#ifdef CZ_FAST
+  if (kind != W3AI) return 0;
+  return which == 0 ? occupancy_c<W3AI>() : occupancy_d<W3AI>();
+#else
   if (which == 0) {
     switch (kind) {
       case W4: return occupancy_c<W4>();
@@ -348,6 +373,7 @@ static int occupancy_query(int kind, int which)
     case W4LI: return occupancy_d<W4LI>();
     default: return occupancy_d<W3AI>();
   }
+#endif
 }
 
 // bytes of the staging slot of the largest payload

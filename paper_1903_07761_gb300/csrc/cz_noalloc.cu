@@ -7,6 +7,7 @@
 // loaded by the CUDA runtime the first time its symbol is looked up.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "../../include/cz.h"
@@ -40,6 +41,9 @@ void *workspace_of_current_device()
 int cz_compress_noalloc(const cz_params *p, const void *d_field, void *d_out, size_t out_cap,
                         uint64_t *d_out_bytes, void *stream)
 {
+  // the caller's buffers are checked as cz_compress checks them, before
+  // any CUDA call (the workspace lookup below is one)
+  if (!d_field || !d_out || ((uintptr_t)d_field % 16) || ((uintptr_t)d_out % 16)) return CZ_ERR_ARG;
   size_t need = 0;
   const int r = cz_workspace_size(p, &need);
   if (r != CZ_OK) return r;
@@ -50,4 +54,12 @@ int cz_compress_noalloc(const cz_params *p, const void *d_field, void *d_out, si
   // (status word, ticket, min/max keys, look-back words) on `stream` before
   // its kernels run; the rest is written before it is read.
   return cz_compress(p, d_field, d_out, out_cap, d_out_bytes, ws, (size_t)CZ_NOALLOC_WS_BYTES, stream);
+}
+
+int cz_noalloc_status(void *stream)
+{
+  // the status word is the first word of the workspace
+  void *ws = workspace_of_current_device();
+  if (!ws) return CZ_ERR_CUDA;
+  return cz_status(ws, stream);
 }

@@ -400,11 +400,15 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // generic-proxy writes to shared memory, made visible to the async proxy
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// bounded wait for the mbarrier phase with the given parity; false on timeout
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+// bounded wait for the mbarrier phase with the given parity; false on
+// timeout.  A timeout is one thread's view: the kernels record it in a
+// shared flag and decide at their next barrier, all threads together,
+// whether the CTA gives up (so no thread is left waiting at a barrier for
+// threads that have gone).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned limit = WAIT_LIMIT)
 {
   const unsigned addr = smem_u32(bar);
-  for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
+  for (unsigned it = 0; it < limit; ++it) {
     unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -1542,6 +1546,10 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
   __shared__ unsigned s_u[40];
   __shared__ unsigned s_nnz[NPB], s_bad[NPB];
   __shared__ unsigned s_badx;
+  // s_pend[j]: a payload copy into buffer j was started and not yet seen
+  // complete; s_to: some thread's wait for a copy gave up (read by all
+  // threads only after a barrier, so the CTA decides as one)
+  __shared__ unsigned s_pend[NPB], s_to;
 
   WsHdr *ws = reinterpret_cast<WsHdr *>(a.ws);
   const int tid = threadIdx.x, lane = tid & 31;
@@ -1589,6 +1597,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
     if (pre && !bad) {
       const int pbytes = HEAD + (int)nnz * ES;
       const int cp = pbytes <= G::PBCAP ? pbytes : HEAD;
+      s_pend[j] = 1u;
       bulk_load(BUF0 + j * G::PBCAP, a.staging + (size_t)b * a.slot, (unsigned)((cp + 15) & ~15), &s_bar[j]);
     }
     return o0;
@@ -1598,7 +1607,11 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
   __shared__ __align__(16) unsigned long long s_tab[2];  // a later block's table entry
   __shared__ unsigned long long s_off[NPB];  // without stage 2: each buffer's chunk offset
   if (tid == 0) {
-    for (int q = 0; q < NPB; ++q) mbar_init(&s_bar[q]);
+    for (int q = 0; q < NPB; ++q) {
+      mbar_init(&s_bar[q]);
+      s_pend[q] = 0;
+    }
+    s_to = 0;
     s_badx = 0;  // reset again after each block's last read
     s_wk.init(blockIdx.x, gridDim.x, a.nbx, a.nby);
   }
@@ -1627,13 +1640,12 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
     bool bad0 = s_bad[j] != 0;
     if (pre) {
       if (!bad0) {
-        const unsigned par = (phase >> j) & 1u;
-        if (!mbar_wait(&s_bar[j], par)) {
-          // the copy never completed: record, wait once more for it, stop
-          if (tid == 0) atomicCAS(&ws->status, 0u, ST_TIMEOUT);
-          mbar_wait(&s_bar[j], par);
-          break;
-        }
+        // a thread whose wait gives up records it and goes on with whatever
+        // the buffer holds (in-bounds work, nothing stored before the vote)
+        if (!mbar_wait(&s_bar[j], (phase >> j) & 1u))
+          s_to = 1u;
+        else if (tid == 0)
+          s_pend[j] = 0u;
         phase ^= 1u << j;
       }
     } else if (!bad0) {
@@ -1682,6 +1694,19 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
       if (tid == 0 && tot != nnz) atomicOr(&s_badx, 1u);
     }
     __syncthreads();
+    if (*(volatile unsigned *)&s_to) {
+      // a payload copy never arrived (in some thread's view): the whole CTA
+      // stops here.  Before leaving, wait once more, bounded, for every
+      // copy it started that has not been seen complete (this block's and
+      // the one issued ahead), and for its tile stores.
+      if (tid == 0) {
+        atomicCAS(&ws->status, 0u, ST_TIMEOUT);
+        for (int q = 0; q < NPB; ++q)
+          if (s_pend[q]) mbar_wait(&s_bar[q], ((phase >> q) & 1u) ^ (q == j ? 1u : 0u));
+        bulk_wait_all();
+      }
+      return;
+    }
     const bool bad = bad0 || s_badx != 0;
     if (bad && tid == 0) atomicCAS(&ws->status, 0u, ST_CORRUPT);
 

@@ -76,6 +76,7 @@ def lib():
             L.cz_decompress_blocks.argtypes = [P, C.c_size_t, P, P, C.c_int, P, C.c_size_t, P, C.c_size_t, P]
             L.cz_decompress_blocks_workspace_size.argtypes = [PP, C.c_int, C.POINTER(C.c_size_t)]
             L.cz_compress_noalloc.argtypes = [PP, P, P, C.c_size_t, P, P]
+            L.cz_noalloc_status.argtypes = [P]
             L.cz_stream_concat.argtypes = [C.c_int, C.POINTER(P), C.POINTER(C.c_size_t), P, C.c_size_t,
                                            C.POINTER(C.c_size_t)]
             L.cz_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(P)]
@@ -111,7 +112,7 @@ def lib():
                       L.cz_decompress_blocks_workspace_size, L.cz_cache_create, L.cz_cache_fetch, L.cz_cache_clear,
                       L.cz_cache_stats, L.cz_aos_workspace_size, L.cz_compress_aos, L.cz_batch_knobs_export,
                       L.cz_batch_knobs_import,
-                      L.cz_compress_noalloc, L.cz_batch_workspace_size, L.cz_compress_batch,
+                      L.cz_compress_noalloc, L.cz_noalloc_status, L.cz_batch_workspace_size, L.cz_compress_batch,
                       L.cz_batch_tune, L.cz_stream_concat, L.cz_server_create, L.cz_server_submit, L.cz_server_poll,
                       L.cz_server_wait, L.cz_server_destroy, L.cz_read_header, L.cz_status, L.cz_forward_dense, L.cz_inverse_dense):
                 f.restype = C.c_int
@@ -147,6 +148,11 @@ def cz_compress_noalloc(p: Params, d_field: int, d_out: int, out_cap: int, d_out
     """cz_compress with the library's own fixed workspace (no allocation)."""
     return lib().cz_compress_noalloc(C.byref(p), d_field, d_out, out_cap, d_out_bytes or None,
                                      stream or None)
+
+
+def cz_noalloc_status(stream: int) -> int:
+    """Device status word of the last cz_compress_noalloc call (synchronises)."""
+    return lib().cz_noalloc_status(stream or None)
 
 
 class BatchArgs:

@@ -33,7 +33,7 @@ def test_header_declares_the_boundary():
     names = _declared()
     for n in ("cz_compress", "cz_decompress", "cz_compress_bound", "cz_workspace_size",
               "cz_read_header", "cz_status", "cz_strerror", "cz_forward_dense",
-              "cz_inverse_dense", "cz_compress_noalloc"):
+              "cz_inverse_dense", "cz_compress_noalloc", "cz_noalloc_status"):
         assert n in names
 
 
@@ -89,6 +89,12 @@ def test_invalid_parameters_are_refused_on_the_host(cz):
     assert cz.cz_compress(p, 0, 0, 1 << 20, 0, 0, 1 << 20, 0) == cz.ERR_ARG
     assert cz.lib().cz_compress_noalloc(C.byref(cz.params_for((32, 32, 48), False, 32, "w4", 1e-3)),
                                         None, None, 0, None, None) == cz.ERR_ARG
+    # a valid shape with null or misaligned buffers: refused before the
+    # no-alloc entry point looks up its workspace (a CUDA call)
+    ok = C.byref(cz.params_for((128, 128, 128), False, 32, "w4", 1e-3))
+    assert cz.lib().cz_compress_noalloc(ok, None, None, 1 << 20, None, None) == cz.ERR_ARG
+    assert cz.lib().cz_compress_noalloc(ok, 0x1000, None, 1 << 20, None, None) == cz.ERR_ARG
+    assert cz.lib().cz_compress_noalloc(ok, 0x1008, 0x2000, 1 << 20, None, None) == cz.ERR_ARG
 
 
 def test_read_header_of_an_oracle_stream(cz):
@@ -134,9 +140,20 @@ def test_bound_mode_and_flags_are_checked(cz):
     p.flags = cz.FLAG_ZERO4 | cz.FLAG_ZERO8  # one zeroing width at most
     with pytest.raises(cz.CzError):
         cz.cz_compress_bound(p)
-    for f in (cz.FLAG_FAST, cz.FLAG_ZERO4, cz.FLAG_ZERO8, cz.FLAG_FAST | cz.FLAG_ZERO8):
+    for f in (cz.FLAG_ZERO4, cz.FLAG_ZERO8):
         p.flags = f
         assert cz.cz_compress_bound(p) > 0
+    # the fast build: W3ai only (W4 / W4li miss its 0.01 dB PSNR gate)
+    for kind in ("w4", "w4li", "w3ai"):
+        for f in (cz.FLAG_FAST, cz.FLAG_FAST | cz.FLAG_ZERO8):
+            p = cz.params_for((32, 32, 32), False, 32, kind, 1e-3, cz.EPS_REL, True, 1.0)
+            p.flags = f
+            if kind == "w3ai":
+                assert cz.cz_compress_bound(p) > 0
+            else:
+                with pytest.raises(cz.CzError) as e:
+                    cz.cz_compress_bound(p)
+                assert e.value.code == cz.ERR_ARG
     p = cz.params_for((32, 32, 32), False, 32, "w4", 1e-3, cz.EPS_REL, True, 1.0,
                       bound_mode=cz.BOUND_STRICT, zero_bits=8)  # the strict bound excludes zeroing
     with pytest.raises(cz.CzError):

@@ -1,6 +1,8 @@
 """The fast build (CZ_FLAG_FAST): the compiler may fuse multiply-adds, so
 coefficients move by a few ulps and the streams are no longer those of the
-exact build.  The gates, against the CPU oracle:
+exact build.  It serves W3ai only (W4 and W4li are refused on the host:
+their extrapolating rows flip enough keep/drop decisions to miss the PSNR
+gate).  The gates, against the CPU oracle:
   * every coefficient within 2^-20 of the field range of the oracle's;
   * PSNR within 0.01 dB of the oracle's, compression factor within 1 %;
   * in strict bound mode, a decoded error of at most eps * range (plus the
@@ -14,7 +16,7 @@ import oracle as O
 
 pytestmark = pytest.mark.gpu
 
-KINDS = (O.W4, O.W4LI, O.W3AI)
+KINDS = (O.W3AI,)  # the kinds the fast build serves
 CASES = [(np.float32, 32, (64, 64, 96)), (np.float32, 16, (32, 48, 64)), (np.float64, 16, (32, 32, 48))]
 # the slab lanes (FP64 32^3, FP32 64^3) have a fast build too; a field of a
 # few of their blocks is enough for the per-coefficient gate
@@ -46,41 +48,25 @@ def _blocks(shape, block):
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("dtype,block,shape", COEF_CASES)
 def test_fast_coefficients_close_to_the_oracle(dtype, block, shape, kind):
-    """W3ai (weights of at most 1/2 in magnitude): every coefficient within
-    2^-20 of the field range of the oracle's.  W4 and W4li extrapolate at the
-    right end of every line with weights up to 35/16, so one rounding of such
-    a product is already about 2^-19 of the values' magnitude and the oracle
-    (in T) carries errors of that size itself: there the fast coefficients
-    must be no farther from the FP64 evaluation of the same input than twice
-    the exact build's distance, plus 2^-20 of the range."""
+    """Every coefficient within 2^-20 of the field range of the oracle's."""
     import torch
     from paper_1903_07761_gb300 import cz
     f = _field(shape, dtype)
     fast = _dense(cz, torch, f, block, kind, True)
     exact = _dense(cz, torch, f, block, kind, False)
     rng = float(f.max()) - float(f.min())
-    d_oracle = d_fast = d_exact = 0.0
+    d_oracle = 0.0
     for sl in _blocks(shape, block):
         want = O.fwd3d(kind, f[sl]).astype(np.float64)
-        truth = O.fwd3d(kind, f[sl].astype(np.float64))
         d_oracle = max(d_oracle, float(np.abs(fast[sl] - want).max()))
-        d_fast = max(d_fast, float(np.abs(fast[sl] - truth).max()))
-        d_exact = max(d_exact, float(np.abs(exact[sl] - truth).max()))
         np.testing.assert_array_equal(exact[sl], want)  # the exact build is the oracle
-    if kind == O.W3AI:
-        assert d_oracle <= 2.0 ** -20 * rng, d_oracle / rng
-    else:
-        assert d_fast <= 2 * d_exact + 2.0 ** -20 * rng, (d_fast / rng, d_exact / rng)
+    assert d_oracle <= 2.0 ** -20 * rng, d_oracle / rng
 
 
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("dtype,block,shape", CASES)
 def test_fast_psnr_within_0p01_db_and_cr_within_1pct(dtype, block, shape, kind):
-    """On fields of 54 to 192 blocks (PSNR is a whole-field figure).  W3ai
-    meets the 0.01 dB target; for W4 and W4li, fused rounding at the
-    extrapolating and lifted rows flips enough keep/drop decisions at the
-    threshold to move PSNR by up to 0.015 dB (either way) on these fields:
-    the target is not met there, and the test holds them to 0.02 dB."""
+    """On fields of 54 to 192 blocks (PSNR is a whole-field figure)."""
     import torch
     from paper_1903_07761_gb300 import cz
     shape = tuple(int(1.5 * n) if n % (2 * block) == 0 and block == 32 else 2 * n for n in shape)
@@ -96,7 +82,7 @@ def test_fast_psnr_within_0p01_db_and_cr_within_1pct(dtype, block, shape, kind):
         ref = O.compress(f, block, kind, eps)
         want = O.decompress(ref)
         pg, po = O.psnr(f, rec), O.psnr(f, want)
-        assert abs(pg - po) <= (0.01 if kind == O.W3AI else 0.02), (pg, po)
+        assert abs(pg - po) <= 0.01, (pg, po)
         assert abs(len(s) - len(ref)) <= 0.01 * len(ref)
 
 
@@ -114,3 +100,13 @@ def test_fast_strict_bound_holds(dtype, block, shape, kind):
     ulp = np.finfo(dtype).eps * float(np.abs(f).max()) * 8
     err = float(np.abs(rec.astype(np.float64) - f.astype(np.float64)).max())
     assert err <= eps * rng + 1e-6 + ulp, (err, eps * rng)
+
+
+@pytest.mark.parametrize("kind", (O.W4, O.W4LI))
+def test_fast_build_refuses_w4_and_w4li(kind):
+    import torch
+    from paper_1903_07761_gb300 import cz
+    f = torch.from_numpy(_field((32, 32, 32), np.float32)).cuda()
+    with pytest.raises(cz.CzError) as e:
+        cz.compress(f, block=32, kind=kind, eps=1e-3, fast=True)
+    assert e.value.code == cz.ERR_ARG

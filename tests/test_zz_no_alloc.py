@@ -38,6 +38,7 @@ def test_noalloc_matches_workspace_entry_point(kind, stage2, range_):
         nb = torch.zeros(1, dtype=torch.int64, device="cuda")
         r = cz.cz_compress_noalloc(p, f.data_ptr(), out.data_ptr(), cap, nb.data_ptr(), s)
         assert r == cz.OK
+        assert cz.cz_noalloc_status(s) == cz.OK
         torch.cuda.synchronize()
         n = int(nb.item())
         got = out[:n].cpu().numpy().tobytes()
@@ -60,7 +61,7 @@ def test_noalloc_refuses_fields_beyond_its_workspace():
     assert int(out.sum().item()) == 0
 
 
-def test_noalloc_output_too_small_reports_length():
+def test_noalloc_output_too_small_reports_length_and_status():
     import torch
     from paper_1903_07761_gb300 import cz, inputs
     f = torch.from_numpy(inputs.config0(seed=1)).cuda()
@@ -72,7 +73,14 @@ def test_noalloc_output_too_small_reports_length():
     out = torch.zeros(small, dtype=torch.uint8, device="cuda")
     nb = torch.zeros(1, dtype=torch.int64, device="cuda")
     assert cz.cz_compress_noalloc(p, f.data_ptr(), out.data_ptr(), small, nb.data_ptr(), s) == cz.OK
+    # the device status word of that call, kept in the library's array
+    assert cz.cz_noalloc_status(s) == cz.ERR_CAPACITY
     torch.cuda.synchronize()
     assert int(nb.item()) == len(full) > small
     np.testing.assert_array_equal(out[:cz.HEADER_BYTES].cpu().numpy(),
                                   np.frombuffer(full[:cz.HEADER_BYTES], np.uint8))
+    # the next call that fits clears it
+    out2 = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+    assert cz.cz_compress_noalloc(p, f.data_ptr(), out2.data_ptr(), cap, nb.data_ptr(), s) == cz.OK
+    assert cz.cz_noalloc_status(s) == cz.OK
+    assert out2[:int(nb.item())].cpu().numpy().tobytes() == full
