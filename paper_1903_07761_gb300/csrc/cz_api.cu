@@ -236,10 +236,31 @@ int sm_count()
   return sms > 0 ? sms : 1;
 }
 
-// persistent grids: one CTA per resident slot, at most one per block
+// decoder choice (a test and measurement hook): 0 = one CTA per block (the
+// default; measured the faster of the two), 1 = the half-block decoder
+// where the lane has one
+int g_decoder_mode = 0;
+
+// the half-block decoder (two CTAs per block, one per z-half) decodes p's
+// blocks
+bool use_half(const cz_params &p)
+{
+  if (__atomic_load_n(&g_decoder_mode, __ATOMIC_RELAXED) != 1) return false;
+  return lanes_for(p).occupancy(p.kind, 6) > 0;
+}
+
+// persistent grids: one CTA per resident slot, at most one per block (per
+// half block for the half-block decoder, whose grid is even so that a CTA
+// keeps its half)
 int grid_for(const cz_params *p, const Shape &sh, int which)
 {
   const Lanes L = lanes_for(*p);
+  if (which == 1 && use_half(*p)) {
+    const long long g = (long long)sm_count() * L.occupancy(p->kind, 6);
+    long long c = g < 2ll * sh.nblocks ? g : 2ll * sh.nblocks;
+    c &= ~1ll;
+    return (int)(c < 2 ? 2 : c);
+  }
   int occ = L.occupancy(p->kind, which);
   // kernels that hold a block or a large payload in global scratch (one
   // scratch block per CTA): at most two CTAs per SM, which bounds the
@@ -331,8 +352,9 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
   return fn;
 }
 
-// 3D tiled tensor map over the field, one B^3 box per block (no swizzle)
-bool make_tile_map(CUtensorMap *tm, const cz_params *p, const void *d_field)
+// 3D tiled tensor map over the field, one B^3 box per block (no swizzle);
+// half = true: a B x B x B/2 box (the half-block decoder's stores)
+bool make_tile_map(CUtensorMap *tm, const cz_params *p, const void *d_field, bool half = false)
 {
   auto enc = tensor_map_encoder();
   if (!enc) return false;
@@ -342,7 +364,9 @@ bool make_tile_map(CUtensorMap *tm, const cz_params *p, const void *d_field)
   // (the kernels of FP64 32^3 and of 64^3 blocks address the field directly
   // and do not use the map: a box of 8 z-planes keeps it within the
   // encoder's limits)
-  const cuuint32_t bz = ((p->dtype == CZ_F64 && p->block == 32) || p->block == 64) ? 8u : (cuuint32_t)p->block;
+  const cuuint32_t bz = ((p->dtype == CZ_F64 && p->block == 32) || p->block == 64) ? 8u
+                        : half                                                   ? (cuuint32_t)p->block / 2
+                                                                                 : (cuuint32_t)p->block;
   const cuuint32_t box[3] = {(cuuint32_t)p->block, (cuuint32_t)p->block, bz};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r =
@@ -1168,6 +1192,16 @@ int czi_link_probe(void *h, void *d, size_t bytes, int reps, int dir, void *stre
   return r;
 }
 
+// Not part of the ABI: which decoder later calls use (tests and timing
+// compare the two): 0 = one CTA per block everywhere (the default), 1 = the
+// half-block decoder where the lane has one (FP32, blocks of edge 16 and 32).
+int czi_set_decoder(int mode)
+{
+  if (mode != 0 && mode != 1) return CZ_ERR_ARG;
+  __atomic_store_n(&g_decoder_mode, mode, __ATOMIC_RELAXED);
+  return CZ_OK;
+}
+
 // Not part of the ABI: the strict-bound divisor C of (kind, B), for tests.
 double czi_synthesis_norm(int kind, int block)
 {
@@ -1314,8 +1348,9 @@ int decompress_impl(const void *d_in, size_t in_bytes, const void *h_header, con
   ua.data0 = sh.data0;
   ua.slot = slot;
   ua.nblocks = dsh.nblocks;
+  a.half = use_half(p) ? 1 : 0;
   CUtensorMap om;
-  if (!make_tile_map(&om, &q, d_out)) return CZ_ERR_CUDA;
+  if (!make_tile_map(&om, &q, d_out, a.half != 0)) return CZ_ERR_CUDA;
   return L.decompress(p.kind, &om, &a, &ua, grid_for(&p, dsh, 1), grid_for(&p, dsh, 4), grid_for(&p, dsh, 5), marks,
                       s) == cudaSuccess
              ? CZ_OK

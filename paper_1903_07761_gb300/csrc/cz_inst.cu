@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "cz_compress.cuh"
+#include "cz_half.cuh"
 #include "cz_launch.h"
 #include "cz_pair.cuh"
 #include "cz_slab.cuh"
@@ -24,6 +25,8 @@ namespace {
 
 using G = G2<CZ_T, CZ_B>;
 using SGi = SG<CZ_T, CZ_B>;  // slab geometry (used only when G::SLAB)
+// lanes with the half-block decoder (FP32 blocks of edge 16 and 32)
+constexpr bool HAS_HALF = sizeof(CZ_T) == 4 && (CZ_B == 16 || CZ_B == 32);
 
 // raise the dynamic shared-memory limit of kernel KERN once per device
 template <auto KERN>
@@ -153,6 +156,20 @@ cudaError_t decompress_k(const CUtensorMap &om, const InvArgs &a, const UnArgs &
     if (e != cudaSuccess) return e;
     if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
     k_decompress_slab<CZ_T, CZ_B, KIND><<<grid, SGi::NT, SGi::SMEM, s>>>(a);
+  } else if constexpr (HAS_HALF) {
+    if (a.half) {
+      using GHi = GH<CZ_T, CZ_B>;
+      if (grid < 2 || (grid & 1)) return cudaErrorInvalidValue;  // a CTA keeps its half: an even grid
+      e = prepare<k_decompress_h<CZ_T, CZ_B, KIND>>(GHi::SMEM);
+      if (e != cudaSuccess) return e;
+      if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
+      k_decompress_h<CZ_T, CZ_B, KIND><<<grid, GHi::NT, GHi::SMEM, s>>>(om, a);
+    } else {
+      e = prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D);
+      if (e != cudaSuccess) return e;
+      if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
+      k_decompress2<CZ_T, CZ_B, KIND><<<grid, G::NT, G::SMEM_D, s>>>(om, a);
+    }
   } else {
     e = prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D);
     if (e != cudaSuccess) return e;
@@ -227,6 +244,22 @@ int occupancy_u()
       cudaSuccess)
     return 0;
   return n;
+}
+
+template <int KIND>
+int occupancy_h()
+{
+  if constexpr (HAS_HALF) {
+    using GHi = GH<CZ_T, CZ_B>;
+    int n = 0;
+    if (prepare<k_decompress_h<CZ_T, CZ_B, KIND>>(GHi::SMEM) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decompress_h<CZ_T, CZ_B, KIND>, GHi::NT, GHi::SMEM) !=
+        cudaSuccess)
+      return 0;
+    return n;
+  } else {
+    return 0;
+  }
 }
 
 template <int KIND>
@@ -332,17 +365,18 @@ extern "C" cudaError_t CZ_CAT(czl_dense_, CZ_SUFFIX)(int kind, int fwd, const De
 
 // CTAs per SM of the stage kernel (which = 0), the decompress kernel
 // (which = 1), the small (2) or large (3) stage-2 kernel, the small (4) or
-// large (5) stage-2 inverse kernel
+// large (5) stage-2 inverse kernel, the half-block decoder (6; 0 where the
+// lane has none)
 static int occupancy_query(int kind, int which);
 
 // cached per device: later calls (e.g. inside a stream capture) make no
 // CUDA call but cudaGetDevice
 extern "C" int CZ_CAT(czl_occupancy_, CZ_SUFFIX)(int kind, int which)
 {
-  static int cache[64][3][6];  // device, kind, which; 0 = not yet known
+  static int cache[64][3][7];  // device, kind, which; 0 = not yet known
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || kind < 0 || kind > 2 || which < 0 ||
-      which > 5)
+      which > 6)
     return occupancy_query(kind, which);
   int v = __atomic_load_n(&cache[dev][kind][which], __ATOMIC_ACQUIRE);
   if (v > 0) return v;
@@ -359,8 +393,16 @@ static int occupancy_query(int kind, int which)
   if (which == 5) return G::HAS_BIG ? occupancy_u<true>() : 1;
 #ifdef CZ_FAST
   if (kind != W3AI) return 0;
+  if (which == 6) return occupancy_h<W3AI>();
   return which == 0 ? occupancy_c<W3AI>() : occupancy_d<W3AI>();
 #else
+  if (which == 6) {
+    switch (kind) {
+      case W4: return occupancy_h<W4>();
+      case W4LI: return occupancy_h<W4LI>();
+      default: return occupancy_h<W3AI>();
+    }
+  }
   if (which == 0) {
     switch (kind) {
       case W4: return occupancy_c<W4>();

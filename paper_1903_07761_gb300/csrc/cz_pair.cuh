@@ -114,6 +114,7 @@ struct InvArgs {
   unsigned long long in_bytes, data0, slot;
   int nx, ny, nz, nbx, nby, nbz, nblocks;
   int stage2;
+  int half;  // host side: 1 = the half-block decoder (two CTAs per block), 0 = one CTA per block
 };
 
 // stage-2 decoding: chunk -> raw payload in a staging slot
@@ -312,10 +313,9 @@ struct G2 {
   static constexpr int SMEM_UB = (SLAB ? 0 : PMAX_AL) + 3 * 512 * 4;
   // dense kernels: cube | plane | halo
   static constexpr int SMEM_DN0 = CUBE_AL + PLANE + HALO;
-  // decompress: row offsets, later the cube | two payload buffers | output
-  // tile, which holds the plane and the halo while level 0 runs
-  static constexpr int R2D0 = CUBE_AL > ROWB ? CUBE_AL : ROWB;
-  static constexpr int R2D = (R2D0 + 127) / 128 * 128;
+  // decompress: cube | row offsets | payload buffers | output tile, which
+  // holds the plane and the halo while level 0 runs
+  static constexpr int R2D = CUBE_AL + (ROWB + 127) / 128 * 128;
   // decompress payload buffer: whole payloads of up to PBCAP bytes (with
   // 32^3 blocks most payloads, the rest read their values from global memory)
   static constexpr int PBCAP = B == 32 ? (PMAX_AL < 16384 ? PMAX_AL : 16384) : PMAX_AL;
@@ -1535,8 +1535,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
   constexpr int HEAD = 64 * ES + G::MASKB;  // coarse values + mask
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int ZH = G::ZH;
-  T *CB = reinterpret_cast<T *>(smem);  // cube of the coarser levels
-  unsigned *ROWOFF = reinterpret_cast<unsigned *>(smem);  // row offsets (before the cube)
+  T *CB = reinterpret_cast<T *>(smem);                               // cube of the coarser levels
+  unsigned *ROWOFF = reinterpret_cast<unsigned *>(smem + G::CUBE_AL);  // row offsets
   constexpr int NPB = G::NPB;
   unsigned char *BUF0 = smem + G::R2D;  // NPB payload buffers of G::PBCAP bytes
   unsigned char *OT = BUF0 + NPB * G::PBCAP;  // output tile [z][y][x]
@@ -1667,22 +1667,22 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
     if (!bad0) get_row_pair<B>(MASK, zr, 2 * k, R0, R1);
     const unsigned W[2] = {seg_transpose<B>(R0, ap), seg_transpose<B>(R1, ap)};
     if (!bad0) {
-      // row populations -> row offsets; coarse positions carry no mask bit
-      ROWOFF[rpad<B>(zr, 2 * k)] = __popc(R0);
-      ROWOFF[rpad<B>(zr, 2 * k + 1)] = __popc(R1);
-      if ((zr % Q) == 0 && ((2 * k) % Q) == 0) {
-        unsigned cm = 0;
-#pragma unroll
-        for (int x = 0; x < B; x += Q) cm |= 1u << x;
-        if (R0 & cm) atomicOr(&s_badx, 1u);
-      }
-      __syncthreads();
-      constexpr int IPT = (B * B + NT - 1) / NT;
+      // row populations (rows in stream order, IPT per thread, straight
+      // from the mask) -> row offsets; coarse positions carry no mask bit
+      constexpr int IPT = B * B / NT;
       unsigned loc[IPT], sum = 0;
 #pragma unroll
       for (int q = 0; q < IPT; ++q) {
-        loc[q] = ROWOFF[rpad_of<B>(tid * IPT + q)];
+        const int row = tid * IPT + q;
+        const unsigned wd = get_rowi<B>(MASK, row);
+        loc[q] = __popc(wd);
         sum += loc[q];
+        if (((row / B) % Q) == 0 && ((row % B) % Q) == 0) {
+          unsigned cm = 0;
+#pragma unroll
+          for (int x = 0; x < B; x += Q) cm |= 1u << x;
+          if (wd & cm) atomicOr(&s_badx, 1u);
+        }
       }
       unsigned tot;
       unsigned ex = block_exsum_nb<NT>(sum, s_u, tot);
@@ -1744,14 +1744,17 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
         for (int zl = 0; zl < ZH; zl += Q) v[0][zl].x = COARSE[(((h * ZH + zl) / Q) * 4 + (2 * k) / Q) * 4 + x0 / Q];
       }
     }
-    // the previous block's tile store has read the tile area, which the
-    // level-0 exchange uses next
-    if (tid == 0) bulk_wait_read();
-    __syncthreads();  // buffer j and the row offsets are free; s_badx has been read
-    if (tid == 0) s_badx = 0;
     // the next block's metadata and payload copy, issued by a thread of the
-    // last warp (idle in the first passes of the coarser levels)
+    // last warp (idle in the first passes of the coarser levels), after a
+    // barrier that follows every thread's read of s_badx; thread 0 waits
+    // until the previous block's tile store has read the tile area, which
+    // the level-0 exchange uses next (other threads write it only after a
+    // later barrier)
     auto fetch_next = [&] {
+      if (tid == 0) {
+        s_badx = 0;
+        bulk_wait_read();
+      }
       if (tid == FT && nbid < a.nblocks) {
         unsigned long long t0 = 0, t1 = 0;
         if (pre) {
@@ -1762,10 +1765,16 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
         s_off[jn] = fetch(nbid, jn, t0, t1);
       }
     };
-    if (!bad)
+    if (!bad && G::L > 1) {
+      // fetch_next runs after the cube's first barrier; the cube passes'
+      // barriers follow it
       inv_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg, fetch_next);
-    else
+    } else {
+      if (tid == 0) bulk_wait_read();
+      __syncthreads();
       fetch_next();
+      if (!bad) inv_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg, [] {});
+    }
     // block -> output tile -> TMA store, which drains while the next block
     // is decoded
     __syncthreads();  // the plane and the halo have been read
