@@ -204,37 +204,45 @@ def _oracle_worker_ready(_):
 def _oracle_worker_task(a):
     import numpy as np
     import oracle as O
-    z0, z1, y0, y1, block, kind, eps, rng = a
-    sub = np.ascontiguousarray(_ORACLE_SHARED[z0:z1, y0:y1])
+    fidx, z0, z1, y0, y1, block, kind, eps, rng = a
+    sub = np.ascontiguousarray(_ORACLE_SHARED[fidx, z0:z1, y0:y1])
     s = O.compress(sub, block, kind, eps, range_=rng)
     O.decompress(s)
     return sub.nbytes
 
 
-def cpu_oracle_all_cores(field_np, block, kind, eps, slabs, rng):
-    """Oracle compress + decompress of the first `slabs` block-rows of z on
-    every host core.  Returns (bytes, seconds, cores)."""
+def _slab_tasks(shape, block, kind, eps, rng, fidx=0):
+    """Independent oracle tasks over a field: z-slabs of one block row, each
+    cut into (about) four y-ranges of whole blocks."""
+    ny = shape[1]
+    q = max(block, (ny // 4) // block * block)
+    return [(fidx, z, z + block, y, min(y + q, ny), block, kind, eps, rng)
+            for z in range(0, shape[0], block) for y in range(0, ny, q)]
+
+
+def cpu_oracle_pool(fields, tasks):
+    """Run oracle compress + decompress tasks (see _slab_tasks) over the
+    given fields (equal shapes and type) on every host core.  Returns
+    (bytes, seconds, cores)."""
     import multiprocessing as mp
     import shutil
     import numpy as np
-    sample = field_np[: slabs * block]
-    d = "/dev/shm" if os.path.isdir("/dev/shm") and shutil.disk_usage("/dev/shm").free > 2 * sample.nbytes \
+    shape, dt = fields[0].shape, fields[0].dtype
+    total = sum(f.nbytes for f in fields)
+    d = "/dev/shm" if os.path.isdir("/dev/shm") and shutil.disk_usage("/dev/shm").free > 2 * total \
         else tempfile.gettempdir()
     fd, path = tempfile.mkstemp(dir=d, suffix=".oracle_sample")
     os.close(fd)
     try:
-        mm = np.memmap(path, dtype=sample.dtype, mode="w+", shape=sample.shape)
-        mm[:] = sample
+        mm = np.memmap(path, dtype=dt, mode="w+", shape=(len(fields),) + tuple(shape))
+        for i, f in enumerate(fields):
+            mm[i] = f
         mm.flush()
         del mm
         cores = os.cpu_count() or 1
-        ny = sample.shape[1]
-        q = max(block, (ny // 4) // block * block)
-        tasks = [(z, z + block, y, min(y + q, ny), block, kind, eps, rng)
-                 for z in range(0, sample.shape[0], block) for y in range(0, ny, q)]
         ctx = mp.get_context("spawn")
         with ctx.Pool(cores, initializer=_oracle_worker_init,
-                      initargs=(path, sample.shape, sample.dtype.str)) as pool:
+                      initargs=(path, (len(fields),) + tuple(shape), dt.str)) as pool:
             pool.map(_oracle_worker_ready, range(cores))
             t0 = time.perf_counter()
             done = sum(pool.map(_oracle_worker_task, tasks, chunksize=1))
@@ -242,6 +250,63 @@ def cpu_oracle_all_cores(field_np, block, kind, eps, slabs, rng):
         return done, secs, cores
     finally:
         os.unlink(path)
+
+
+def cpu_oracle_all_cores(field_np, block, kind, eps, slabs, rng):
+    """Oracle compress + decompress of the first `slabs` block-rows of z on
+    every host core.  Returns (bytes, seconds, cores)."""
+    sample = field_np[: slabs * block]
+    return cpu_oracle_pool([sample], _slab_tasks(sample.shape, block, kind, eps, rng))
+
+
+def oracle_sweep_timing(n1: int = 512, seed1: int = 1000, slabs: int = 1, slabs_all: int = 2):
+    """The oracle as it stands on the small Gaussian-bubble field (128^3, W4,
+    eps 1e-3) and on the 512^3 bubble-cloud sweep, single-threaded and on all
+    host cores.  The cloud runs take bounded samples: the first `slabs`
+    z-slabs of blocks of the pressure field per kind at eps 1e-3 (one
+    thread), and the first `slabs_all` z-slabs of every field for all 36
+    runs of the sweep (all cores), each with the threshold of its full
+    field.  (The oracle forms the W4li update weights from their exact
+    fractions at every use, so W4li runs far slower than the other kinds.)"""
+    import oracle as O
+    from paper_1903_07761_gb300 import inputs
+    out = {"cores_all": os.cpu_count() or 1}
+    f0 = inputs.config0(seed=0)
+    r0 = float(f0.max()) - float(f0.min())
+    t0 = time.perf_counter()
+    O.decompress(O.compress(f0, 32, O.W4, 1e-3, range_=r0))
+    secs = time.perf_counter() - t0
+    out["small_single"] = {"gbs": f0.nbytes / secs / 1e9, "seconds": secs, "cores": 1,
+                           "what": "128^3 FP32 Gaussian bubbles, 32^3 blocks, W4, eps 1e-3, compress + decompress"}
+    tasks0 = [(0, z, z + 32, y, y + 32, 32, O.W4, 1e-3, r0) for z in range(0, 128, 32) for y in range(0, 128, 32)]
+    b, secs, cores = cpu_oracle_pool([f0], tasks0)
+    out["small_all"] = {"gbs": b / secs / 1e9, "seconds": secs, "cores": cores}
+    names = ("alpha", "rho", "p")
+    fields = [inputs.cavitation(w, n1, seed=seed1) for w in names]
+    rngs = [float(f.max()) - float(f.min()) for f in fields]
+    single = {}
+    smp = fields[2][: slabs * 32]
+    for kname, kk in (("w4", O.W4), ("w4li", O.W4LI), ("w3ai", O.W3AI)):
+        t0 = time.perf_counter()
+        O.decompress(O.compress(smp, 32, kk, 1e-3, range_=rngs[2]))
+        secs = time.perf_counter() - t0
+        single[kname] = {"gbs": smp.nbytes / secs / 1e9, "seconds": secs}
+    out["cloud_single_p_eps1e-3"] = {
+        "per_kind": single, "cores": 1,
+        "what": f"the first {slabs} z-slab(s) of 32^3 blocks ({smp.nbytes / 2**20:.0f} MiB) of the {n1}^3 "
+                f"FP32 p-field, compress + decompress, one thread"}
+    samples = [f[: slabs_all * 32] for f in fields]
+    tasks = []
+    for fi in range(3):
+        for kk in (O.W4, O.W4LI, O.W3AI):
+            for eps in (1e-2, 1e-3, 1e-4, 1e-5):
+                tasks += _slab_tasks(samples[fi].shape, 32, kk, eps, rngs[fi], fidx=fi)
+    b, secs, cores = cpu_oracle_pool(samples, tasks)
+    out["cloud_all"] = {"gbs": b / secs / 1e9, "seconds": secs, "cores": cores,
+                        "what": f"all 36 runs of the {n1}^3 sweep (3 fields x 3 kinds x 4 eps) on the first "
+                                f"{slabs_all} z-slab(s) of each field ({samples[0].nbytes / 2**20:.0f} MiB), "
+                                f"compress + decompress, {len(tasks)} tasks"}
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -557,7 +622,7 @@ def run_gpu(args, rank, world, local_rank):
         random_access = workloads.random_access(out[:ra_len], ra_len, header)
 
     # batched fields and the served request stream (rank 0, one GPU)
-    batched_res = served_res = fp64_res = None
+    batched_res = served_res = fp64_res = config1_res = None
     if rank == 0 and world == 1:
         from paper_1903_07761_gb300 import workloads
         del rec
@@ -570,6 +635,9 @@ def run_gpu(args, rank, world, local_rank):
             torch.cuda.empty_cache()
         if not args.no_fp64:
             fp64_res = workloads.fp64()
+            torch.cuda.empty_cache()
+        if not args.no_config1:
+            config1_res = {"gpu": workloads.config1()}
             torch.cuda.empty_cache()
 
     # reductions over ranks (max time)
@@ -596,6 +664,12 @@ def run_gpu(args, rank, world, local_rank):
                                           f"independent tasks on {acores} worker processes, {asecs:.2f} s"}
         except Exception as exc:  # context only: report, do not fail the run
             cpu["all_cores"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:200]}
+        # the oracle on the small field and on the bubble-cloud sweep (context)
+        if config1_res is not None:
+            try:
+                config1_res["oracle"] = oracle_sweep_timing()
+            except Exception as exc:
+                config1_res["oracle"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:200]}
 
     peak, peak_src = measured_peaks()
     # the major kernels' algorithmic bytes per launch, by the method's own
@@ -651,6 +725,7 @@ def run_gpu(args, rank, world, local_rank):
         "batched": batched_res,
         "served": served_res,
         "fp64": fp64_res,
+        "config1": config1_res,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -704,6 +779,7 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-fields comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-requests comparison")
     ap.add_argument("--no-fp64", action="store_true", help="skip the 768^3 FP64 case")
+    ap.add_argument("--no-config1", action="store_true", help="skip the 512^3 bubble-cloud sweep")
     return ap
 
 

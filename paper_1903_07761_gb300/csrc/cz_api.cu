@@ -236,9 +236,10 @@ int sm_count()
   return sms > 0 ? sms : 1;
 }
 
-// decoder choice (a test and measurement hook): 0 = one CTA per block (the
-// default; measured the faster of the two), 1 = the half-block decoder
-// where the lane has one
+// decoder choice (a test and measurement hook): 0 = each lane's default
+// (FP32 32^3 blocks: the decoder that computes the next block's row offsets
+// during the coarser levels; other lanes: one CTA per block), 1 = the
+// half-block decoder where the lane has one, 2 = k_decompress2 everywhere
 int g_decoder_mode = 0;
 
 // the half-block decoder (two CTAs per block, one per z-half) decodes p's
@@ -247,6 +248,14 @@ bool use_half(const cz_params &p)
 {
   if (__atomic_load_n(&g_decoder_mode, __ATOMIC_RELAXED) != 1) return false;
   return lanes_for(p).occupancy(p.kind, 6) > 0;
+}
+
+// the decoder InvArgs::decoder names for p
+int decoder_of(const cz_params &p)
+{
+  const int m = __atomic_load_n(&g_decoder_mode, __ATOMIC_RELAXED);
+  if (m == 1) return use_half(p) ? 1 : 2;
+  return m;
 }
 
 // persistent grids: one CTA per resident slot, at most one per block (per
@@ -1193,11 +1202,13 @@ int czi_link_probe(void *h, void *d, size_t bytes, int reps, int dir, void *stre
 }
 
 // Not part of the ABI: which decoder later calls use (tests and timing
-// compare the two): 0 = one CTA per block everywhere (the default), 1 = the
-// half-block decoder where the lane has one (FP32, blocks of edge 16 and 32).
+// compare them): 0 = each lane's default, 1 = the half-block decoder where
+// the lane has one (FP32, blocks of edge 16 and 32), 2 = k_decompress2
+// (one CTA per block, row offsets scanned at the start of each block)
+// everywhere.
 int czi_set_decoder(int mode)
 {
-  if (mode != 0 && mode != 1) return CZ_ERR_ARG;
+  if (mode < 0 || mode > 2) return CZ_ERR_ARG;
   __atomic_store_n(&g_decoder_mode, mode, __ATOMIC_RELAXED);
   return CZ_OK;
 }
@@ -1348,9 +1359,9 @@ int decompress_impl(const void *d_in, size_t in_bytes, const void *h_header, con
   ua.data0 = sh.data0;
   ua.slot = slot;
   ua.nblocks = dsh.nblocks;
-  a.half = use_half(p) ? 1 : 0;
+  a.decoder = decoder_of(p);
   CUtensorMap om;
-  if (!make_tile_map(&om, &q, d_out, a.half != 0)) return CZ_ERR_CUDA;
+  if (!make_tile_map(&om, &q, d_out, a.decoder == 1)) return CZ_ERR_CUDA;
   return L.decompress(p.kind, &om, &a, &ua, grid_for(&p, dsh, 1), grid_for(&p, dsh, 4), grid_for(&p, dsh, 5), marks,
                       s) == cudaSuccess
              ? CZ_OK

@@ -114,7 +114,7 @@ struct InvArgs {
   unsigned long long in_bytes, data0, slot;
   int nx, ny, nz, nbx, nby, nbz, nblocks;
   int stage2;
-  int half;  // host side: 1 = the half-block decoder (two CTAs per block), 0 = one CTA per block
+  int decoder;  // host side: 0 = the lane's default decoder, 1 = two CTAs per block (half blocks), 2 = k_decompress2
 };
 
 // stage-2 decoding: chunk -> raw payload in a staging slot
@@ -1175,7 +1175,17 @@ __device__ __forceinline__ void cube_line(int li, int &base, int &step)
 // thread li gets a line of z-slice li / n, so the two passes of a level
 // touch each slice from one warp (n divides 32 or is a multiple of 16):
 // between them a warp barrier orders the accesses (WARP_ONLY).
-template <typename T, int N, int KIND, int NT, int S, int AXIS, bool FWD, bool WARP_ONLY>
+// barrier of the NTH threads that use barrier ID (a multiple of 32 threads,
+// whole warps; ID 0 is __syncthreads')
+template <int ID, int NTH>
+__device__ __forceinline__ void named_sync()
+{
+  asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(NTH) : "memory");
+}
+
+// NB > 0: the passes' barriers span only threads 0..NB-1 (named barrier 1),
+// so that other warps of the CTA can do other work meanwhile
+template <typename T, int N, int KIND, int NT, int S, int AXIS, bool FWD, bool WARP_ONLY, int NB = 0>
 __device__ __forceinline__ void cube_pass(T *C)
 {
   constexpr int n = N / S, LINES = n * n;
@@ -1199,6 +1209,8 @@ __device__ __forceinline__ void cube_pass(T *C)
   }
   if constexpr (WARP_ONLY)
     __syncwarp();
+  else if constexpr (NB > 0)
+    named_sync<1, NB>();
   else
     __syncthreads();
 }
@@ -1215,14 +1227,14 @@ __device__ __forceinline__ void cube_fwd(T *C)
   }
 }
 
-template <typename T, int N, int KIND, int NT, int S = 1>
+template <typename T, int N, int KIND, int NT, int S = 1, int NB = 0>
 __device__ __forceinline__ void cube_inv(T *C)
 {
   if constexpr (N / S >= 8) {
-    cube_inv<T, N, KIND, NT, 2 * S>(C);
-    cube_pass<T, N, KIND, NT, S, 2, false, false>(C);
-    cube_pass<T, N, KIND, NT, S, 1, false, true>(C);
-    cube_pass<T, N, KIND, NT, S, 0, false, false>(C);
+    cube_inv<T, N, KIND, NT, 2 * S, NB>(C);
+    cube_pass<T, N, KIND, NT, S, 2, false, false, NB>(C);
+    cube_pass<T, N, KIND, NT, S, 1, false, true, NB>(C);
+    cube_pass<T, N, KIND, NT, S, 0, false, false, NB>(C);
   }
 }
 

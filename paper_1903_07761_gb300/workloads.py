@@ -12,7 +12,13 @@
   and 30 % FP64, eps in {1e-3, 1e-4}, through the request server under an
   HBM budget, against one-at-a-time plain launches on the same trace.
 
-Both return plain dicts for the benchmark line.  Inputs are synthetic
+* config1(): the bubble-cloud sweep -- gas fraction, density and pressure
+  of one 200-bubble cloud on a 512^3 domain (FP32, 32^3 blocks), every
+  kind at eps in {1e-2, 1e-3, 1e-4, 1e-5}: compression factor, PSNR, the
+  largest error over the threshold, and compress / decompress GB/s (the
+  paper's wavelet-type experiment, Sec. 3 Exp. 1, on synthetic fields).
+
+All return plain dicts for the benchmark line.  Inputs are synthetic
 (seeded); see inputs/czgen.c.
 """
 from __future__ import annotations
@@ -483,3 +489,75 @@ def fp64(n: int = 768, kind: str = "w3ai", eps: float = 1e-3, reps: int = 10, se
         "random_access_32": ra,
     })
     return r
+
+
+# ------------------------------------------------------------------ bubble-cloud sweep
+def config1(n: int = 512, fields=("alpha", "rho", "p"), kinds=("w4", "w4li", "w3ai"),
+            eps_list=(1e-2, 1e-3, 1e-4, 1e-5), reps: int = 3, seed: int = 1000, nbubbles: int = 200):
+    """Every (field, kind, eps) of the sweep: the stream is made once, then
+    compress and decompress are each timed `reps` times (median, CUDA
+    events, range computed on the device as in the headline)."""
+    import statistics
+
+    import torch
+    s = torch.cuda.current_stream().cuda_stream
+    rows = []
+    for fname in fields:
+        f = torch.from_numpy(inputs.cavitation(fname, n, np.float32, seed=seed, nbubbles=nbubbles)).cuda()
+        nbytes_field = f.numel() * 4
+        fmin, fmax = float(f.min().item()), float(f.max().item())
+        rng = fmax - fmin
+        rec = torch.empty_like(f)
+        for kind in kinds:
+            for eps in eps_list:
+                p = cz.params_for(tuple(f.shape), False, 32, kind, eps)
+                cap = cz.cz_compress_bound(p)
+                out = torch.empty(cap, dtype=torch.uint8, device="cuda")
+                ws = torch.empty(cz.cz_workspace_size(p), dtype=torch.uint8, device="cuda")
+                nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+                def comp():
+                    r = cz.cz_compress(p, f.data_ptr(), out.data_ptr(), cap, nb.data_ptr(), ws.data_ptr(),
+                                       ws.numel(), s)
+                    assert r == cz.OK
+
+                comp()
+                assert cz.cz_status(ws.data_ptr(), s) == cz.OK
+                ln = int(nb.item())
+                hdr = out[:cz.HEADER_BYTES].cpu().numpy().tobytes()
+
+                def dec():
+                    r = cz.cz_decompress(out.data_ptr(), ln, hdr, rec.data_ptr(), nbytes_field, ws.data_ptr(),
+                                         ws.numel(), s)
+                    assert r == cz.OK
+
+                tc, td = [], []
+                for _ in range(reps):
+                    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                    e0.record()
+                    comp()
+                    e1.record()
+                    dec()
+                    e2.record()
+                    torch.cuda.synchronize()
+                    tc.append(e0.elapsed_time(e1))
+                    td.append(e1.elapsed_time(e2))
+                assert cz.cz_status(ws.data_ptr(), s) == cz.OK
+                d = rec.double() - f.double()
+                mse = float((d * d).mean().item())
+                linf = float(d.abs().max().item())
+                del d
+                cm, dm = statistics.median(tc), statistics.median(td)
+                rows.append({
+                    "field": fname, "kind": kind, "eps": eps, "cr": nbytes_field / ln,
+                    "psnr_db": 20 * math.log10(rng / (2 * math.sqrt(mse))) if mse > 0 else None,
+                    "linf_over_t": linf / (eps * rng) if rng > 0 else None,
+                    "compress_gbs": nbytes_field / cm / 1e6, "decompress_gbs": nbytes_field / dm / 1e6,
+                })
+                del out, ws
+        del f, rec
+        torch.cuda.empty_cache()
+    return {"workload": f"bubble cloud ({nbubbles} tanh-interface bubbles, seed {seed}) on {n}^3, FP32, "
+                        f"32^3 blocks, fields {'/'.join(fields)}, stage 2 on, range computed; "
+                        f"{reps} timed calls each (median)",
+            "rows": rows}

@@ -70,3 +70,20 @@ def test_profile_commands_run_committed_files_with_valid_flags():
             if name in text:
                 assert name in tracked
     assert found >= 3
+
+
+def test_oracle_sweep_timing_reports_every_part():
+    """The oracle timings beside the bubble-cloud sweep (single thread and
+    all host cores), on a 64^3 cloud so that the test stays short."""
+    sys.path.insert(0, ROOT)
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    sys.modules["bench"] = bench
+    spec.loader.exec_module(bench)
+    out = bench.oracle_sweep_timing(n1=64)
+    assert out["cores_all"] >= 1
+    for k in ("small_single", "small_all", "cloud_all"):
+        assert out[k]["gbs"] > 0 and out[k]["cores"] >= 1
+    assert set(out["cloud_single_p_eps1e-3"]["per_kind"]) == {"w4", "w4li", "w3ai"}
+    assert "36 runs" in out["cloud_all"]["what"]
