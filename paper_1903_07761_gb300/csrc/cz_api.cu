@@ -236,10 +236,9 @@ int sm_count()
   return sms > 0 ? sms : 1;
 }
 
-// decoder choice (a test and measurement hook): 0 = each lane's default
-// (FP32 32^3 blocks: the decoder that computes the next block's row offsets
-// during the coarser levels; other lanes: one CTA per block), 1 = the
-// half-block decoder where the lane has one, 2 = k_decompress2 everywhere
+// decoder choice (a test and measurement hook): 0 = one CTA per block (the
+// default; measured the faster), 1 = the half-block decoder where the lane
+// has one
 int g_decoder_mode = 0;
 
 // the half-block decoder (two CTAs per block, one per z-half) decodes p's
@@ -251,12 +250,7 @@ bool use_half(const cz_params &p)
 }
 
 // the decoder InvArgs::decoder names for p
-int decoder_of(const cz_params &p)
-{
-  const int m = __atomic_load_n(&g_decoder_mode, __ATOMIC_RELAXED);
-  if (m == 1) return use_half(p) ? 1 : 2;
-  return m;
-}
+int decoder_of(const cz_params &p) { return use_half(p) ? 1 : 0; }
 
 // persistent grids: one CTA per resident slot, at most one per block (per
 // half block for the half-block decoder, whose grid is even so that a CTA
@@ -1202,13 +1196,11 @@ int czi_link_probe(void *h, void *d, size_t bytes, int reps, int dir, void *stre
 }
 
 // Not part of the ABI: which decoder later calls use (tests and timing
-// compare them): 0 = each lane's default, 1 = the half-block decoder where
-// the lane has one (FP32, blocks of edge 16 and 32), 2 = k_decompress2
-// (one CTA per block, row offsets scanned at the start of each block)
-// everywhere.
+// compare the two): 0 = one CTA per block everywhere (the default), 1 = the
+// half-block decoder where the lane has one (FP32, blocks of edge 16 and 32).
 int czi_set_decoder(int mode)
 {
-  if (mode < 0 || mode > 2) return CZ_ERR_ARG;
+  if (mode != 0 && mode != 1) return CZ_ERR_ARG;
   __atomic_store_n(&g_decoder_mode, mode, __ATOMIC_RELAXED);
   return CZ_OK;
 }

@@ -7,7 +7,6 @@
 #include <cuda_runtime.h>
 
 #include "cz_compress.cuh"
-#include "cz_decode.cuh"
 #include "cz_half.cuh"
 #include "cz_launch.h"
 #include "cz_pair.cuh"
@@ -26,10 +25,8 @@ namespace {
 
 using G = G2<CZ_T, CZ_B>;
 using SGi = SG<CZ_T, CZ_B>;  // slab geometry (used only when G::SLAB)
-// lanes with the half-block decoder (FP32 blocks of edge 16 and 32) and
-// with the overlapped decoder (FP32 blocks of edge 32, its default)
+// lanes with the half-block decoder (FP32 blocks of edge 16 and 32)
 constexpr bool HAS_HALF = sizeof(CZ_T) == 4 && (CZ_B == 16 || CZ_B == 32);
-constexpr bool HAS_OVL = sizeof(CZ_T) == 4 && CZ_B == 32;
 
 // raise the dynamic shared-memory limit of kernel KERN once per device
 template <auto KERN>
@@ -167,14 +164,6 @@ cudaError_t decompress_k(const CUtensorMap &om, const InvArgs &a, const UnArgs &
       if (e != cudaSuccess) return e;
       if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
       k_decompress_h<CZ_T, CZ_B, KIND><<<grid, GHi::NT, GHi::SMEM, s>>>(om, a);
-    } else if (HAS_OVL && a.decoder == 0) {
-      if constexpr (HAS_OVL) {
-        using GDi = GD<CZ_T, CZ_B>;
-        e = prepare<k_decompress3<CZ_T, CZ_B, KIND>>(GDi::SMEM);
-        if (e != cudaSuccess) return e;
-        if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
-        k_decompress3<CZ_T, CZ_B, KIND><<<grid, G::NT, GDi::SMEM, s>>>(om, a);
-      }
     } else {
       e = prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D);
       if (e != cudaSuccess) return e;
@@ -284,22 +273,10 @@ int occupancy_d()
       return 0;
     return n;
   } else {
-    // one CTA per SM for both one-CTA-per-block decoders (their registers)
-    int n2 = 0;
     if (prepare<k_decompress2<CZ_T, CZ_B, KIND>>(G::SMEM_D) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_decompress2<CZ_T, CZ_B, KIND>, G::NT, G::SMEM_D) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decompress2<CZ_T, CZ_B, KIND>, G::NT, G::SMEM_D) !=
         cudaSuccess)
       return 0;
-    n = n2;
-    if constexpr (HAS_OVL) {
-      using GDi = GD<CZ_T, CZ_B>;
-      int n3 = 0;
-      if (prepare<k_decompress3<CZ_T, CZ_B, KIND>>(GDi::SMEM) != cudaSuccess) return 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, k_decompress3<CZ_T, CZ_B, KIND>, G::NT, GDi::SMEM) !=
-          cudaSuccess)
-        return 0;
-      n = n3 < n2 ? n3 : n2;
-    }
     return n;
   }
 }

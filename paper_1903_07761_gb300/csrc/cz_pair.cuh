@@ -114,7 +114,7 @@ struct InvArgs {
   unsigned long long in_bytes, data0, slot;
   int nx, ny, nz, nbx, nby, nbz, nblocks;
   int stage2;
-  int decoder;  // host side: 0 = the lane's default decoder, 1 = two CTAs per block (half blocks), 2 = k_decompress2
+  int decoder;  // host side: 0 = one CTA per block, 1 = two CTAs per block (half blocks)
 };
 
 // stage-2 decoding: chunk -> raw payload in a staging slot

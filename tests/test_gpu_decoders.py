@@ -1,12 +1,9 @@
-"""Every block decoder against the CPU oracle.
+"""Both block decoders against the CPU oracle.
 
-Three decoders, chosen with a test hook (czi_set_decoder): the default
-(mode 0; for FP32 32^3 blocks the decoder that computes the next block's
-row offsets while the coarser levels run, one CTA per block elsewhere), two
-CTAs per block for FP32 blocks of edge 16 and 32 (mode 1; one per z-half,
-each rebuilding the coarse cube and its z-step halo from the payload), and
-one CTA per block with the row offsets scanned at the start of each block
-(mode 2).  All must give fields bit-identical to
+Two decoders, chosen with a test hook (czi_set_decoder): one CTA per block
+(mode 0, the default) and, for FP32 blocks of edge 16 and 32, two CTAs per
+block (mode 1; one per z-half, each rebuilding the coarse cube and its
+z-step halo from the payload).  Both must give fields bit-identical to
 the oracle's: every kind, stage 2 on and off, ragged block grids with
 several blocks per CTA, eps = 0 (payloads above the decoders' shared-memory
 buffers, whose values are read from global memory), random access and
@@ -25,7 +22,7 @@ pytestmark = pytest.mark.gpu
 KINDS = (O.W4, O.W4LI, O.W3AI)
 
 
-@pytest.fixture(params=[0, 1, 2], ids=["default", "half", "whole"])
+@pytest.fixture(params=[0, 1], ids=["whole", "half"])
 def decoder(request):
     from paper_1903_07761_gb300 import cz
     L = cz.lib()
