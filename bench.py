@@ -631,7 +631,9 @@ def run_gpu(args, rank, world, local_rank):
             batched_res = workloads.batched()
             torch.cuda.empty_cache()
         if not args.no_serve:
-            served_res = workloads.served()
+            # the full request-rate sweep of the served workload: 2000
+            # requests at each of 100 ... 5000 per second
+            served_res = workloads.served(rates=(100.0, 200.0, 500.0, 1000.0, 2000.0, 5000.0), n=2000)
             torch.cuda.empty_cache()
         if not args.no_fp64:
             fp64_res = workloads.fp64()

@@ -252,29 +252,42 @@ int cz_noalloc_status(void *stream);
  * captured in a CUDA graph once a call outside the capture has set up the
  * kernels.  Errors as for cz_compress; the status word is shared.
  * Host-side: d_ws must hold cz_batch_workspace_size() bytes (the largest
- * group's workspace; groups run one after another and reuse it). */
+ * group's workspace under any tuner setting; groups run one after another
+ * and reuse it).  Each group uses the tuner's choices for its fields'
+ * parameters (cz_batch_tune), else the defaults. */
 int cz_batch_workspace_size(int n, const cz_params *p, size_t *bytes);
 int cz_compress_batch(int n, const cz_params *p, const void *const *d_fields,
                       void *const *d_outs, const size_t *out_caps,
                       uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes,
                       void *stream);
 
-/* Autotuner of the batched launch: times cz_compress_batch on these very
- * arguments under each candidate block-to-CTA mapping (a stage grid of one
- * CTA per SM, or the fewest CTAs that keep the same number of rounds) and
- * stage-2 grid size (all resident CTAs, or half), `reps` timed calls each
- * after one warm-up, and keeps the fastest for later calls with the same
- * field parameters.  Synchronises `stream`.  The outputs are overwritten. */
+/* Autotuner of the batched launch: for every group of the batch (the
+ * fields that share one launch) it times the group's launches on these very
+ * arguments under each candidate setting of four knobs, `reps` timed calls
+ * each after one warm-up, and keeps the fastest for later calls with the
+ * same field parameters:
+ *  - the lifting tile shape of the stage kernel: the block in registers
+ *    (pair quads, one CTA of B^2/2 threads per block) or, where a lane has
+ *    both (FP32 32^3), the slab kernel (the block in a global scratch block,
+ *    one 256-thread CTA per block, two per SM);
+ *  - the block-to-CTA mapping: one CTA per resident slot, or the fewest CTAs
+ *    that keep the same number of rounds (blocks per CTA);
+ *  - the stage-2 grid: all resident CTAs, or half;
+ *  - the scan granularity: 64, 128 or 256 chunks per look-back tile.
+ * Streams are identical under every setting.  Synchronises `stream`.  The
+ * outputs are overwritten.  d_ws must hold cz_batch_workspace_size() bytes. */
 int cz_batch_tune(int n, const cz_params *p, const void *const *d_fields,
                   void *const *d_outs, const size_t *out_caps,
                   uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes,
                   void *stream, int reps);
 
 /* The tuner's choices as JSON text, so that they outlive the process:
- *   {"format": "cz-batch-knobs", "version": 1, "entries": [
- *     {"signature": "<16 hex digits>", "s1_balanced": 0|1, "s2_div": 1..64}, ...]}
- * A signature identifies a batch by the parameters of its fields (not by
- * its buffers).  The choices are those of the device they were tuned on.
+ *   {"format": "cz-batch-knobs", "version": 2, "entries": [
+ *     {"signature": "<16 hex digits>", "s1_balanced": 0|1, "s2_div": 1..64,
+ *      "place_tile": 64|128|256, "slab": 0|1}, ...]}
+ * A signature identifies a group of fields by their parameters (not by their
+ * buffers).  The choices are those of the device they were tuned on.
+ * Version 1 texts (without place_tile and slab) are read with 128 and 0.
  * Export: *len receives the text length + 1; with buf NULL only the size is
  * returned, otherwise buf (cap bytes) receives the NUL-terminated text or
  * CZ_ERR_CAPACITY.  Import: merges the entries of such a text (an entry

@@ -198,20 +198,21 @@ struct Lanes {
   cudaError_t (*compress)(int, const CUtensorMap *, const FwdArgs *, const S2Args *, const PlaceArgs *, int, int,
                           int, const cudaEvent_t *, cudaStream_t);
   cudaError_t (*compress_batch)(int, const StageMaps<MAXF> *, const FwdArgs *, const S2Args *, const BatchOut *,
-                                const PlaceArgs *, int, int, int, int, cudaStream_t);
+                                const PlaceArgs *, int, int, int, int, int, int, cudaStream_t);
   cudaError_t (*decompress)(int, const CUtensorMap *, const InvArgs *, const UnArgs *, int, int, int,
                             const cudaEvent_t *, cudaStream_t);
   cudaError_t (*dense)(int, int, const DenseArgs *, int, cudaStream_t);
   int (*occupancy)(int, int);
   int (*slot_bytes)();
   int (*scratch_bytes)();  // global scratch per CTA (FP64 32^3 only)
+  int (*alt_scratch_bytes)();  // per CTA of the batched slab stage kernel where the tuner may pick it
 };
 
 #define CZ_LANES(sfx)                                                                                      \
   Lanes                                                                                                    \
   {                                                                                                        \
     czl_compress_##sfx, czl_compress_batch_##sfx, czl_decompress_##sfx, czl_dense_##sfx, czl_occupancy_##sfx, \
-        czl_slot_bytes_##sfx, czl_scratch_bytes_##sfx                                                      \
+        czl_slot_bytes_##sfx, czl_scratch_bytes_##sfx, czl_alt_scratch_bytes_##sfx                         \
   }
 
 Lanes lanes_for(const cz_params &p)
@@ -355,8 +356,10 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
   return fn;
 }
 
-// 3D tiled tensor map over the field, one B^3 box per block (no swizzle);
-// half = true: a B x B x B/2 box (the half-block decoder's stores)
+// 3D tiled tensor map over the field, one B^3 box per block; FP32 32^3
+// W4li boxes (128-byte rows) take the 128-byte swizzle (the stage kernel and
+// the one-CTA-per-block decoder address their W4li tiles that way); half =
+// true: a B x B x B/2 box without swizzle (the half-block decoder's stores)
 bool make_tile_map(CUtensorMap *tm, const cz_params *p, const void *d_field, bool half = false)
 {
   auto enc = tensor_map_encoder();
@@ -375,7 +378,9 @@ bool make_tile_map(CUtensorMap *tm, const cz_params *p, const void *d_field, boo
   const CUresult r =
       enc(tm, p->dtype == CZ_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
           const_cast<void *>(d_field), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+          (p->dtype == CZ_F32 && p->block == 32 && p->kind == CZ_W4LI && !half) ? CU_TENSOR_MAP_SWIZZLE_128B
+                                                                                : CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
@@ -471,11 +476,27 @@ std::vector<Group> plan_batch(int n, const cz_params *p)
   return out;
 }
 
-// knobs chosen by cz_batch_tune for a batch signature
+// knobs chosen by cz_batch_tune for a group of fields (one launch)
 struct BatchKnobs {
   int s1_balanced;  // stage grid: fewest CTAs with the same number of rounds
   int s2_div;       // stage-2 CTAs: resident slots / s2_div
+  int place_tile;   // scan granularity: chunks per look-back tile (64, 128, 256)
+  int slab;         // stage kernel: 0 = register-resident pair quads, 1 = slab kernel (block in global scratch)
 };
+
+constexpr BatchKnobs DEFAULT_KNOBS{0, 1, 128, 0};
+
+// the knob settings the tuner tries for a group whose first field is p0
+std::vector<BatchKnobs> knob_candidates(const cz_params &p0)
+{
+  std::vector<BatchKnobs> c;
+  const bool alt = lanes_for(p0).alt_scratch_bytes() > 0;
+  for (int slab = 0; slab <= (alt ? 1 : 0); ++slab)
+    for (int b = 0; b <= 1; ++b)
+      for (int d = 1; d <= 2; ++d)
+        for (int pt : {64, 128, 256}) c.push_back(BatchKnobs{b, d, pt, slab});
+  return c;
+}
 
 struct BatchLayout {
   size_t keys, lb, table, big, staging, scratch, total, arena;
@@ -485,6 +506,7 @@ struct BatchLayout {
 BatchLayout batch_layout(const Group &g, const cz_params *p, const BatchKnobs &kn)
 {
   const cz_params &p0 = p[g.idx[0]];
+  const int PT = kn.place_tile;
   BatchLayout w{};
   w.nblocks = 0;
   w.tiles = 0;
@@ -492,11 +514,18 @@ BatchLayout batch_layout(const Group &g, const cz_params *p, const BatchKnobs &k
     Shape sh;
     check(&p[i], &sh);
     w.nblocks += sh.nblocks;
-    w.tiles += (sh.nblocks + PLACE_TILE - 1) / PLACE_TILE;
+    w.tiles += (sh.nblocks + PT - 1) / PT;
   }
   Shape all{};
   all.nblocks = w.nblocks;
-  w.grid = grid_for(&p0, all, 0);
+  const Lanes L = lanes_for(p0);
+  const bool slab = kn.slab && L.alt_scratch_bytes() > 0;
+  if (slab) {
+    const long long gs = (long long)sm_count() * (L.occupancy(p0.kind, 7) > 0 ? L.occupancy(p0.kind, 7) : 1);
+    w.grid = (int)(gs < w.nblocks ? gs : w.nblocks);
+  } else {
+    w.grid = grid_for(&p0, all, 0);
+  }
   if (kn.s1_balanced) {
     const int rounds = (w.nblocks + w.grid - 1) / w.grid;
     w.grid = (w.nblocks + rounds - 1) / rounds;
@@ -505,7 +534,6 @@ BatchLayout batch_layout(const Group &g, const cz_params *p, const BatchKnobs &k
   w.grid3 = grid_for(&p0, all, 3) / (kn.s2_div > 0 ? kn.s2_div : 1);
   if (w.grid2 < 1) w.grid2 = 1;
   if (w.grid3 < 1) w.grid3 = 1;
-  const Lanes L = lanes_for(p0);
   w.keys = WS_HDR;
   w.lb = w.keys + 16 * MAXF;
   w.table = w.lb + (8ull * w.tiles + 255) / 256 * 256;
@@ -513,20 +541,26 @@ BatchLayout batch_layout(const Group &g, const cz_params *p, const BatchKnobs &k
   w.staging = w.big + big_bytes(w.nblocks);
   w.arena = (((size_t)w.nblocks + w.grid - 1) / w.grid) * (size_t)L.slot_bytes();
   w.scratch = w.staging + w.arena * (size_t)w.grid;
-  w.total = w.scratch + scratch_need(&p0, all, w.grid, w.grid3);
+  size_t scr = scratch_need(&p0, all, w.grid, w.grid3);
+  if (slab) {
+    const size_t alt = (size_t)L.alt_scratch_bytes() * (size_t)w.grid;
+    scr = alt > scr ? alt : scr;
+  }
+  w.total = w.scratch + scr;
   return w;
 }
 
 std::mutex g_knob_mu;
 std::vector<std::pair<unsigned long long, BatchKnobs>> g_knobs;
 
-// signature of a batch: the parameters of every field (not the pointers)
-unsigned long long batch_signature(int n, const cz_params *p)
+// signature of a group of fields: the parameters of every field of the
+// group (not the pointers)
+unsigned long long group_signature(const Group &g, const cz_params *p)
 {
   unsigned long long h = 1469598103934665603ull;
   auto mix = [&](unsigned long long v) { h = (h ^ v) * 1099511628211ull; };
-  mix((unsigned long long)n);
-  for (int i = 0; i < n; ++i) {
+  mix((unsigned long long)g.idx.size());
+  for (int i : g.idx) {
     mix((unsigned long long)p[i].nx);
     mix((unsigned long long)p[i].ny);
     mix((unsigned long long)p[i].nz);
@@ -536,18 +570,22 @@ unsigned long long batch_signature(int n, const cz_params *p)
   return h;
 }
 
-BatchKnobs knobs_for(int n, const cz_params *p)
+BatchKnobs knobs_for(const Group &g, const cz_params *p)
 {
-  const unsigned long long sig = batch_signature(n, p);
+  const unsigned long long sig = group_signature(g, p);
   std::lock_guard<std::mutex> lock(g_knob_mu);
   for (auto &e : g_knobs)
-    if (e.first == sig) return e.second;
-  return BatchKnobs{0, 1};
+    if (e.first == sig) {
+      BatchKnobs k = e.second;
+      if (k.slab && lanes_for(p[g.idx[0]]).alt_scratch_bytes() == 0) k.slab = 0;  // not this lane's choice
+      return k;
+    }
+  return DEFAULT_KNOBS;
 }
 
-void set_knobs(int n, const cz_params *p, const BatchKnobs &k)
+void set_knobs(const Group &g, const cz_params *p, const BatchKnobs &k)
 {
-  const unsigned long long sig = batch_signature(n, p);
+  const unsigned long long sig = group_signature(g, p);
   std::lock_guard<std::mutex> lock(g_knob_mu);
   for (auto &e : g_knobs)
     if (e.first == sig) {
@@ -557,21 +595,132 @@ void set_knobs(int n, const cz_params *p, const BatchKnobs &k)
   g_knobs.push_back({sig, k});
 }
 
-size_t batch_ws_need(int n, const cz_params *p, const BatchKnobs &kn)
+// workspace for every group under its stored knobs, or under every
+// candidate setting (all = true: room for whatever the tuner picks).  The
+// largest layouts are those with the most look-back tiles (64 chunks) and
+// the full stage-2 grid, so only those candidates are laid out.
+size_t batch_ws_need(int n, const cz_params *p, bool all)
 {
   size_t need = WS_HDR;
   for (const Group &g : plan_batch(n, p)) {
-    const BatchLayout w = batch_layout(g, p, kn);
-    need = w.total > need ? w.total : need;
+    std::vector<BatchKnobs> ks;
+    if (all) {
+      for (const BatchKnobs &k : knob_candidates(p[g.idx[0]]))
+        if (k.place_tile == 64 && k.s2_div == 1) ks.push_back(k);
+    } else {
+      ks.push_back(knobs_for(g, p));
+    }
+    for (const BatchKnobs &kn : ks) {
+      const BatchLayout w = batch_layout(g, p, kn);
+      need = w.total > need ? w.total : need;
+    }
   }
   return need;
 }
 
-int compress_batch_impl(int n, const cz_params *p, const void *const *d_fields, void *const *d_outs,
-                        const size_t *out_caps, uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes,
-                        cudaStream_t s, const BatchKnobs &kn)
+// one group's launches (its fields share dtype, block, kind, stage 2, bound
+// mode and flags) with knobs kn; the workspace is the group's alone
+int compress_group(const Group &g, const cz_params *p, const void *const *d_fields, void *const *d_outs,
+                   const size_t *out_caps, uint64_t *d_out_bytes, unsigned char *wsb, cudaStream_t s,
+                   const BatchKnobs &kn)
 {
-  const NvtxRange nvtx("cz_compress_batch");
+  const cz_params &p0 = p[g.idx[0]];
+  const BatchLayout w = batch_layout(g, p, kn);
+  const int nf = (int)g.idx.size();
+  // ticket, min/max keys (min keys all ones) and look-back words
+  if (cudaMemsetAsync(wsb + 4, 0, w.table - 4, s) != cudaSuccess) return CZ_ERR_CUDA;
+  if (cudaMemset2DAsync(wsb + w.keys, 16, 0xFF, 8, nf, s) != cudaSuccess) return CZ_ERR_CUDA;
+  unsigned long long *keys = reinterpret_cast<unsigned long long *>(wsb + w.keys);
+  MinmaxArgs mm{};
+  mm.keys = keys;
+  unsigned long long maxn = 0;
+  StageMaps<MAXF> maps{};
+  BatchOut bo{};
+  bo.nf = nf;
+  int first = 0, tfirst = 0;
+  for (int f = 0; f < nf; ++f) {
+    const int i = g.idx[f];
+    Shape sh;
+    check(&p[i], &sh);
+    const bool need_range = p[i].range < 0 && p[i].eps_mode == CZ_EPS_REL;
+    mm.field[f] = d_fields[i];
+    mm.n[f] = need_range ? (unsigned long long)p[i].nx * p[i].ny * p[i].nz : 0ull;
+    maxn = mm.n[f] > maxn ? mm.n[f] : maxn;
+    if (!make_tile_map(&maps.tm[f], &p[i], d_fields[i])) return CZ_ERR_CUDA;
+    maps.g[f] = FieldGeo{d_fields[i], sh.nbx, sh.nby, first, p[i].eps_mode, p[i].eps, p[i].range};
+    FieldOut &fo = bo.f[f];
+    fo.out = reinterpret_cast<unsigned char *>(d_outs[i]);
+    fo.out_bytes = d_out_bytes ? reinterpret_cast<unsigned long long *>(d_out_bytes + i) : nullptr;
+    fo.out_cap = out_caps[i];
+    fo.data0 = sh.data0;
+    fo.eps = p[i].eps;
+    fo.range_in = p[i].range;
+    fo.nx = p[i].nx;
+    fo.ny = p[i].ny;
+    fo.nz = p[i].nz;
+    fo.nblocks = sh.nblocks;
+    fo.first = first;
+    fo.tfirst = tfirst;
+    fo.eps_mode = p[i].eps_mode;
+    first += sh.nblocks;
+    tfirst += (sh.nblocks + kn.place_tile - 1) / kn.place_tile;
+  }
+  if (maxn > 0) {
+    const dim3 grid((unsigned)((maxn + MM_CHUNK - 1) / MM_CHUNK), (unsigned)nf);
+    if (p0.dtype == CZ_F32)
+      k_minmax_multi<float><<<grid, 512, 0, s>>>(mm);
+    else
+      k_minmax_multi<double><<<grid, 512, 0, s>>>(mm);
+    if (cudaGetLastError() != cudaSuccess) return CZ_ERR_CUDA;
+  }
+  FwdArgs a{};
+  a.ws = wsb;
+  a.keys = keys;
+  a.biglist = reinterpret_cast<int *>(wsb + w.big);
+  a.staging = wsb + w.staging;
+  a.arena_bytes = w.arena;
+  a.scratch = wsb + w.scratch;
+  a.table = reinterpret_cast<unsigned long long *>(wsb + w.table);
+  a.cnorm = threshold_divisor(&p0);
+  a.nblocks = w.nblocks;
+  a.nf = nf;
+  a.stage2 = p0.stage2;
+  a.kind = p0.kind;
+  a.zbits = zero_bits(p0);
+  a.dtype = p0.dtype;
+  S2Args sa{};
+  sa.staging = a.staging;
+  sa.table = a.table;
+  sa.ws = wsb;
+  sa.biglist = a.biglist;
+  sa.scratch = a.scratch;
+  sa.nblocks = w.nblocks;
+  PlaceArgs pa{};
+  pa.staging = a.staging;
+  pa.table = a.table;
+  pa.keys = keys;
+  pa.lbst = reinterpret_cast<unsigned long long *>(wsb + w.lb);
+  pa.ws = wsb;
+  pa.cnorm = a.cnorm;
+  pa.nblocks = w.nblocks;
+  pa.block = p0.block;
+  pa.levels = p0.block == 8 ? 1 : (p0.block == 16 ? 2 : (p0.block == 32 ? 3 : 4));
+  pa.stage2 = p0.stage2;
+  pa.kind = p0.kind;
+  pa.dtype = p0.dtype;
+  pa.bound_mode = p0.bound_mode;
+  pa.flags = p0.flags;
+  const Lanes L = lanes_for(p0);
+  const int slab = kn.slab && L.alt_scratch_bytes() > 0 ? 1 : 0;
+  if (L.compress_batch(p0.kind, &maps, &a, &sa, &bo, &pa, w.grid, w.grid2, w.grid3, w.tiles, kn.place_tile, slab,
+                       s) != cudaSuccess)
+    return CZ_ERR_CUDA;
+  return CZ_OK;
+}
+
+int batch_check(int n, const cz_params *p, const void *const *d_fields, void *const *d_outs, const size_t *out_caps,
+                const void *d_ws)
+{
   if (n < 0 || (n > 0 && (!p || !d_fields || !d_outs || !out_caps)) || !d_ws) return CZ_ERR_ARG;
   if ((uintptr_t)d_ws % 16) return CZ_ERR_ARG;
   for (int i = 0; i < n; ++i) {
@@ -582,99 +731,26 @@ int compress_batch_impl(int n, const cz_params *p, const void *const *d_fields, 
       return CZ_ERR_ARG;
     if (out_caps[i] < sh.data0) return CZ_ERR_CAPACITY;
   }
-  if (ws_bytes < batch_ws_need(n, p, kn)) return CZ_ERR_CAPACITY;
+  return CZ_OK;
+}
+
+// every group with its stored knobs (the tuner's choices, else the
+// defaults), or with `force` for every group
+int compress_batch_impl(int n, const cz_params *p, const void *const *d_fields, void *const *d_outs,
+                        const size_t *out_caps, uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes,
+                        cudaStream_t s, const BatchKnobs *force = nullptr)
+{
+  const NvtxRange nvtx("cz_compress_batch");
+  const int r = batch_check(n, p, d_fields, d_outs, out_caps, d_ws);
+  if (r != CZ_OK) return r;
+  if (ws_bytes < batch_ws_need(n, p, force != nullptr)) return CZ_ERR_CAPACITY;
   unsigned char *wsb = reinterpret_cast<unsigned char *>(d_ws);
   if (cudaMemsetAsync(d_ws, 0, 4, s) != cudaSuccess) return CZ_ERR_CUDA;  // status, once for the batch
   for (const Group &g : plan_batch(n, p)) {
-    const cz_params &p0 = p[g.idx[0]];
-    const BatchLayout w = batch_layout(g, p, kn);
-    const int nf = (int)g.idx.size();
-    // ticket, min/max keys (min keys all ones) and look-back words
-    if (cudaMemsetAsync(wsb + 4, 0, w.table - 4, s) != cudaSuccess) return CZ_ERR_CUDA;
-    if (cudaMemset2DAsync(wsb + w.keys, 16, 0xFF, 8, nf, s) != cudaSuccess) return CZ_ERR_CUDA;
-    unsigned long long *keys = reinterpret_cast<unsigned long long *>(wsb + w.keys);
-    MinmaxArgs mm{};
-    mm.keys = keys;
-    unsigned long long maxn = 0;
-    StageMaps<MAXF> maps{};
-    BatchOut bo{};
-    bo.nf = nf;
-    int first = 0, tfirst = 0;
-    for (int f = 0; f < nf; ++f) {
-      const int i = g.idx[f];
-      Shape sh;
-      check(&p[i], &sh);
-      const bool need_range = p[i].range < 0 && p[i].eps_mode == CZ_EPS_REL;
-      mm.field[f] = d_fields[i];
-      mm.n[f] = need_range ? (unsigned long long)p[i].nx * p[i].ny * p[i].nz : 0ull;
-      maxn = mm.n[f] > maxn ? mm.n[f] : maxn;
-      if (!make_tile_map(&maps.tm[f], &p[i], d_fields[i])) return CZ_ERR_CUDA;
-      maps.g[f] = FieldGeo{d_fields[i], sh.nbx, sh.nby, first, p[i].eps_mode, p[i].eps, p[i].range};
-      FieldOut &fo = bo.f[f];
-      fo.out = reinterpret_cast<unsigned char *>(d_outs[i]);
-      fo.out_bytes = d_out_bytes ? reinterpret_cast<unsigned long long *>(d_out_bytes + i) : nullptr;
-      fo.out_cap = out_caps[i];
-      fo.data0 = sh.data0;
-      fo.eps = p[i].eps;
-      fo.range_in = p[i].range;
-      fo.nx = p[i].nx;
-      fo.ny = p[i].ny;
-      fo.nz = p[i].nz;
-      fo.nblocks = sh.nblocks;
-      fo.first = first;
-      fo.tfirst = tfirst;
-      fo.eps_mode = p[i].eps_mode;
-      first += sh.nblocks;
-      tfirst += (sh.nblocks + PLACE_TILE - 1) / PLACE_TILE;
-    }
-    if (maxn > 0) {
-      const dim3 grid((unsigned)((maxn + MM_CHUNK - 1) / MM_CHUNK), (unsigned)nf);
-      if (p0.dtype == CZ_F32)
-        k_minmax_multi<float><<<grid, 512, 0, s>>>(mm);
-      else
-        k_minmax_multi<double><<<grid, 512, 0, s>>>(mm);
-      if (cudaGetLastError() != cudaSuccess) return CZ_ERR_CUDA;
-    }
-    FwdArgs a{};
-    a.ws = d_ws;
-    a.keys = keys;
-    a.biglist = reinterpret_cast<int *>(wsb + w.big);
-    a.staging = wsb + w.staging;
-    a.arena_bytes = w.arena;
-    a.scratch = wsb + w.scratch;
-    a.table = reinterpret_cast<unsigned long long *>(wsb + w.table);
-    a.cnorm = threshold_divisor(&p0);
-    a.nblocks = w.nblocks;
-    a.nf = nf;
-    a.stage2 = p0.stage2;
-    a.kind = p0.kind;
-    a.zbits = zero_bits(p0);
-    a.dtype = p0.dtype;
-    S2Args sa{};
-    sa.staging = a.staging;
-    sa.table = a.table;
-    sa.ws = d_ws;
-    sa.biglist = a.biglist;
-    sa.scratch = a.scratch;
-    sa.nblocks = w.nblocks;
-    PlaceArgs pa{};
-    pa.staging = a.staging;
-    pa.table = a.table;
-    pa.keys = keys;
-    pa.lbst = reinterpret_cast<unsigned long long *>(wsb + w.lb);
-    pa.ws = d_ws;
-    pa.cnorm = a.cnorm;
-    pa.nblocks = w.nblocks;
-    pa.block = p0.block;
-    pa.levels = p0.block == 8 ? 1 : (p0.block == 16 ? 2 : (p0.block == 32 ? 3 : 4));
-    pa.stage2 = p0.stage2;
-    pa.kind = p0.kind;
-    pa.dtype = p0.dtype;
-    pa.bound_mode = p0.bound_mode;
-    pa.flags = p0.flags;
-    const Lanes L = lanes_for(p0);
-    if (L.compress_batch(p0.kind, &maps, &a, &sa, &bo, &pa, w.grid, w.grid2, w.grid3, w.tiles, s) != cudaSuccess)
-      return CZ_ERR_CUDA;
+    BatchKnobs kn = force ? *force : knobs_for(g, p);
+    if (kn.slab && lanes_for(p[g.idx[0]]).alt_scratch_bytes() == 0) kn.slab = 0;  // not this lane's choice
+    const int rg = compress_group(g, p, d_fields, d_outs, out_caps, d_out_bytes, wsb, s, kn);
+    if (rg != CZ_OK) return rg;
   }
   return CZ_OK;
 }
@@ -813,9 +889,7 @@ int cz_batch_workspace_size(int n, const cz_params *p, size_t *bytes)
   if (n < 0 || !bytes || (n > 0 && !p)) return CZ_ERR_ARG;
   for (int i = 0; i < n; ++i)
     if (check(&p[i], nullptr) != CZ_OK) return CZ_ERR_ARG;
-  // room for every knob setting the tuner may pick
-  const size_t a = batch_ws_need(n, p, BatchKnobs{0, 1}), b = batch_ws_need(n, p, BatchKnobs{1, 1});
-  *bytes = a > b ? a : b;
+  *bytes = batch_ws_need(n, p, true);  // room for every knob setting the tuner may pick
   return CZ_OK;
 }
 
@@ -823,7 +897,7 @@ int cz_compress_batch(int n, const cz_params *p, const void *const *d_fields, vo
                       const size_t *out_caps, uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes, void *stream)
 {
   return compress_batch_impl(n, p, d_fields, d_outs, out_caps, d_out_bytes, d_ws, ws_bytes,
-                             reinterpret_cast<cudaStream_t>(stream), knobs_for(n, p));
+                             reinterpret_cast<cudaStream_t>(stream));
 }
 
 int cz_batch_tune(int n, const cz_params *p, const void *const *d_fields, void *const *d_outs,
@@ -831,37 +905,46 @@ int cz_batch_tune(int n, const cz_params *p, const void *const *d_fields, void *
                   int reps)
 {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const BatchKnobs cand[4] = {{0, 1}, {1, 1}, {0, 2}, {1, 2}};
+  int r = batch_check(n, p, d_fields, d_outs, out_caps, d_ws);
+  if (r != CZ_OK) return r;
+  if (ws_bytes < batch_ws_need(n, p, true)) return CZ_ERR_CAPACITY;
+  unsigned char *wsb = reinterpret_cast<unsigned char *>(d_ws);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return CZ_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
     cudaEventDestroy(e0);
     return CZ_ERR_CUDA;
   }
-  int best = -1;
-  float best_ms = 0;
-  int r = CZ_OK;
-  for (int c = 0; c < 4 && r == CZ_OK; ++c) {
-    r = compress_batch_impl(n, p, d_fields, d_outs, out_caps, d_out_bytes, d_ws, ws_bytes, s, cand[c]);  // warm
-    if (r != CZ_OK) break;
-    if (cudaEventRecord(e0, s) != cudaSuccess) r = CZ_ERR_CUDA;
-    for (int q = 0; q < (reps > 0 ? reps : 3) && r == CZ_OK; ++q)
-      r = compress_batch_impl(n, p, d_fields, d_outs, out_caps, d_out_bytes, d_ws, ws_bytes, s, cand[c]);
-    if (r != CZ_OK) break;
-    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-      r = CZ_ERR_CUDA;
-      break;
+  // every group on its own: each candidate once to warm up, then `reps`
+  // timed launches; the fastest is kept for the group's signature
+  for (const Group &g : plan_batch(n, p)) {
+    const std::vector<BatchKnobs> cand = knob_candidates(p[g.idx[0]]);
+    int best = -1;
+    float best_ms = 0;
+    for (size_t c = 0; c < cand.size() && r == CZ_OK; ++c) {
+      if (cudaMemsetAsync(wsb, 0, 4, s) != cudaSuccess) r = CZ_ERR_CUDA;
+      if (r == CZ_OK) r = compress_group(g, p, d_fields, d_outs, out_caps, d_out_bytes, wsb, s, cand[c]);
+      if (r != CZ_OK) break;
+      if (cudaEventRecord(e0, s) != cudaSuccess) r = CZ_ERR_CUDA;
+      for (int q = 0; q < (reps > 0 ? reps : 3) && r == CZ_OK; ++q)
+        r = compress_group(g, p, d_fields, d_outs, out_caps, d_out_bytes, wsb, s, cand[c]);
+      if (r != CZ_OK) break;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        r = CZ_ERR_CUDA;
+        break;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (best < 0 || ms < best_ms) {
+        best = (int)c;
+        best_ms = ms;
+      }
     }
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (best < 0 || ms < best_ms) {
-      best = c;
-      best_ms = ms;
-    }
+    if (r != CZ_OK) break;
+    if (best >= 0) set_knobs(g, p, cand[best]);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (r == CZ_OK && best >= 0) set_knobs(n, p, cand[best]);
   return r;
 }
 
@@ -957,20 +1040,23 @@ int cz_compress_aos(int n, const cz_params *p, const void *d_cells, int ncomp, c
     k_deinterleave<float><<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const float *>(d_cells), ncomp, pick,
                                                            ncells);
   if (cudaGetLastError() != cudaSuccess) return CZ_ERR_CUDA;
-  return compress_batch_impl(n, p, fields.data(), d_outs, out_caps, d_out_bytes, wsb, f0, s, knobs_for(n, p));
+  return compress_batch_impl(n, p, fields.data(), d_outs, out_caps, d_out_bytes, wsb, f0, s);
 }
 
 // ---- the tuner's choices as JSON text
 int cz_batch_knobs_export(char *buf, size_t cap, size_t *len)
 {
   if (!len) return CZ_ERR_ARG;
-  std::string out = "{\"format\": \"cz-batch-knobs\", \"version\": 1, \"entries\": [";
+  std::string out = "{\"format\": \"cz-batch-knobs\", \"version\": 2, \"entries\": [";
   {
     std::lock_guard<std::mutex> lock(g_knob_mu);
     for (size_t i = 0; i < g_knobs.size(); ++i) {
-      char e[160];
-      std::snprintf(e, sizeof e, "%s{\"signature\": \"%016llx\", \"s1_balanced\": %d, \"s2_div\": %d}",
-                    i ? ", " : "", g_knobs[i].first, g_knobs[i].second.s1_balanced, g_knobs[i].second.s2_div);
+      char e[224];
+      const BatchKnobs &k = g_knobs[i].second;
+      std::snprintf(e, sizeof e,
+                    "%s{\"signature\": \"%016llx\", \"s1_balanced\": %d, \"s2_div\": %d, \"place_tile\": %d, "
+                    "\"slab\": %d}",
+                    i ? ", " : "", g_knobs[i].first, k.s1_balanced, k.s2_div, k.place_tile, k.slab);
       out += e;
     }
   }
@@ -1013,7 +1099,8 @@ int cz_batch_knobs_import(const char *json)
   };
   std::string v;
   if (!value(0, t.size(), "format", v) || v != "cz-batch-knobs") return CZ_ERR_ARG;
-  if (!value(0, t.size(), "version", v) || v != "1") return CZ_ERR_ARG;
+  if (!value(0, t.size(), "version", v) || (v != "1" && v != "2")) return CZ_ERR_ARG;
+  const bool v2 = v == "2";  // version 1 entries: look-back tiles of 128 chunks, register-resident kernels
   size_t i = t.find("\"entries\"");
   if (i == std::string::npos) return CZ_ERR_ARG;
   i = ws(i + 9);
@@ -1026,14 +1113,16 @@ int cz_batch_knobs_import(const char *json)
     if (t[i] != '{') return CZ_ERR_ARG;
     const size_t e = t.find('}', i);
     if (e == std::string::npos) return CZ_ERR_ARG;
-    std::string sig, s1, s2;
+    std::string sig, s1, s2, spt = "128", ssl = "0";
     if (!value(i, e, "signature", sig) || !value(i, e, "s1_balanced", s1) || !value(i, e, "s2_div", s2))
       return CZ_ERR_ARG;
+    if (v2 && (!value(i, e, "place_tile", spt) || !value(i, e, "slab", ssl))) return CZ_ERR_ARG;
     if (sig.empty() || sig.size() > 16 || sig.find_first_not_of("0123456789abcdefABCDEF") != std::string::npos)
       return CZ_ERR_ARG;
-    const int b1 = std::atoi(s1.c_str()), d2 = std::atoi(s2.c_str());
+    const int b1 = std::atoi(s1.c_str()), d2 = std::atoi(s2.c_str()), pt = std::atoi(spt.c_str());
     if ((s1 != "0" && s1 != "1") || d2 < 1 || d2 > 64 || s2 != std::to_string(d2)) return CZ_ERR_ARG;
-    got.push_back({std::stoull(sig, nullptr, 16), BatchKnobs{b1, d2}});
+    if ((spt != "64" && spt != "128" && spt != "256") || (ssl != "0" && ssl != "1")) return CZ_ERR_ARG;
+    got.push_back({std::stoull(sig, nullptr, 16), BatchKnobs{b1, d2, pt, ssl == "1" ? 1 : 0}});
     i = ws(e + 1);
     if (i < t.size() && t[i] == ',') i = ws(i + 1);
   }
@@ -1203,6 +1292,22 @@ int czi_set_decoder(int mode)
   if (mode != 0 && mode != 1) return CZ_ERR_ARG;
   __atomic_store_n(&g_decoder_mode, mode, __ATOMIC_RELAXED);
   return CZ_OK;
+}
+
+// Not part of the ABI: cz_compress_batch with one knob setting forced on
+// every group (tests: streams must not depend on it): s1_balanced (0, 1),
+// s2_div (1, 2), place_tile (64, 128, 256), slab (0, 1; ignored where the
+// lane has no slab alternative).  d_ws as for cz_compress_batch.
+int czi_compress_batch_knobs(int n, const cz_params *p, const void *const *d_fields, void *const *d_outs,
+                             const size_t *out_caps, uint64_t *d_out_bytes, void *d_ws, size_t ws_bytes,
+                             void *stream, int s1_balanced, int s2_div, int place_tile, int slab)
+{
+  if ((s1_balanced != 0 && s1_balanced != 1) || (s2_div != 1 && s2_div != 2) ||
+      (place_tile != 64 && place_tile != 128 && place_tile != 256) || (slab != 0 && slab != 1))
+    return CZ_ERR_ARG;
+  const BatchKnobs kn{s1_balanced, s2_div, place_tile, slab};
+  return compress_batch_impl(n, p, d_fields, d_outs, out_caps, d_out_bytes, d_ws, ws_bytes,
+                             reinterpret_cast<cudaStream_t>(stream), &kn);
 }
 
 // Not part of the ABI: the strict-bound divisor C of (kind, B), for tests.

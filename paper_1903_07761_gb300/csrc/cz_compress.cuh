@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
   using G = G2<T, B>;
   using T2 = typename V2T<T>::type;
   constexpr int NT = G::NT, ES = G::ES, Q = G::Q, ZH = G::ZH;
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *smem = align1024(smem_raw);
   unsigned char *PF = smem;                                   // tile [z][y][x], filled by TMA
   T2 *PL = reinterpret_cast<T2 *>(smem + G::TILE);            // level-0 plane
   T *CB = reinterpret_cast<T *>(smem + G::TILE);              // cube (start of the plane area)
@@ -147,17 +148,28 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     phase ^= 1u;
 
     // ---- tile -> registers; the next tile is fetched after the
-    // transform's first barrier, when every thread has read this one
+    // transform's first barrier, when every thread has read this one.
+    // W4li (swizzled 128-byte rows): the finest x-level first, row by row in
+    // the tile, then the pairs (two values of one 16-byte chunk) at their
+    // swizzled places.
+    constexpr bool RX = G::template rowx<KIND>();
+    if constexpr (RX) {
+      x_rows<T, B, KIND, true, NT>(PF);
+      fence_async_smem();  // the next tile's copy overwrites these writes
+      __syncthreads();
+    }
     T2 v[2][ZH];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
-      for (int zl = 0; zl < ZH; ++zl)
-        v[r][zl] = *reinterpret_cast<const T2 *>(PF + (((h * ZH + zl) * B + 2 * k + r) * B + x0) * ES);
+      for (int zl = 0; zl < ZH; ++zl) {
+        const unsigned o = (unsigned)((((h * ZH + zl) * B + 2 * k + r) * B + x0) * ES);
+        v[r][zl] = *reinterpret_cast<const T2 *>(PF + (RX ? swz128(o) : o));
+      }
     const int nb = bid + (int)gridDim.x;
 
     // ---- forward transform
-    fwd_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg, [&] {
+    fwd_all<T, B, KIND, !RX>(v, PL, HX, CB, ap, k, h, seg, [&] {
       // (after a barrier: a timeout of this block's copy is visible here,
       // and then no further copy is started)
       if (tid == 0 && nb < a.nblocks && !*(volatile unsigned *)&s_to) {
@@ -523,10 +535,12 @@ __device__ __forceinline__ int field_of_tile(const BatchOut &bo, int tile)
   return f;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(PLACE_TILE) k_place_multi(const __grid_constant__ BatchOut bo, const PlaceArgs a)
+// PT chunks (and threads) per CTA: the scan granularity, a knob of the
+// batch tuner (64, 128 or 256)
+template <typename T, int PT>
+__global__ void __launch_bounds__(PT) k_place_multi(const __grid_constant__ BatchOut bo, const PlaceArgs a)
 {
-  constexpr int PT = PLACE_TILE, NT = PLACE_TILE;
+  constexpr int NT = PT;
   __shared__ unsigned s_u[40];
   __shared__ int s_tile;
   __shared__ unsigned long long s_excl;

@@ -27,6 +27,10 @@ using G = G2<CZ_T, CZ_B>;
 using SGi = SG<CZ_T, CZ_B>;  // slab geometry (used only when G::SLAB)
 // lanes with the half-block decoder (FP32 blocks of edge 16 and 32)
 constexpr bool HAS_HALF = sizeof(CZ_T) == 4 && (CZ_B == 16 || CZ_B == 32);
+// lanes where the batched stage kernel can also be the slab kernel (the
+// block in global scratch) instead of the register-resident one: the tuner
+// picks (FP32 32^3)
+constexpr bool HAS_SLAB_ALT = !G::SLAB && SGi::OK;
 
 // raise the dynamic shared-memory limit of kernel KERN once per device
 template <auto KERN>
@@ -107,24 +111,39 @@ cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const S2Args &sa
   return cudaGetLastError();
 }
 
+// place_tile: chunks per look-back tile (64, 128 or 256); slab: the slab
+// stage kernel where the lane also has the register-resident one
 template <int KIND>
 cudaError_t compress_batch_k(const StageMaps<MAXF> &maps, const FwdArgs &a, const S2Args &sa, const BatchOut &bo,
-                             const PlaceArgs &pa, int grid, int grid2, int grid3, int tiles, cudaStream_t s)
+                             const PlaceArgs &pa, int grid, int grid2, int grid3, int tiles, int place_tile, int slab,
+                             cudaStream_t s)
 {
   cudaError_t e;
-  if constexpr (G::SLAB) {
-    e = prepare<k_stage1_slab<CZ_T, CZ_B, KIND, MAXF>>(SGi::SMEM);
-    if (e != cudaSuccess) return e;
-    k_stage1_slab<CZ_T, CZ_B, KIND, MAXF><<<grid, SGi::NT, SGi::SMEM, s>>>(maps, a);
-  } else {
-    e = prepare<k_stage1<CZ_T, CZ_B, KIND, MAXF>>(G::SMEM_C);
-    if (e != cudaSuccess) return e;
-    k_stage1<CZ_T, CZ_B, KIND, MAXF><<<grid, G::NT, G::SMEM_C, s>>>(maps, a);
+  if (place_tile != 64 && place_tile != 128 && place_tile != 256) return cudaErrorInvalidValue;
+  if (slab && !G::SLAB && !HAS_SLAB_ALT) return cudaErrorInvalidValue;
+  if constexpr (G::SLAB || HAS_SLAB_ALT) {
+    if (G::SLAB || slab) {
+      e = prepare<k_stage1_slab<CZ_T, CZ_B, KIND, MAXF>>(SGi::SMEM);
+      if (e != cudaSuccess) return e;
+      k_stage1_slab<CZ_T, CZ_B, KIND, MAXF><<<grid, SGi::NT, SGi::SMEM, s>>>(maps, a);
+    }
+  }
+  if constexpr (!G::SLAB) {
+    if (!slab) {
+      e = prepare<k_stage1<CZ_T, CZ_B, KIND, MAXF>>(G::SMEM_C);
+      if (e != cudaSuccess) return e;
+      k_stage1<CZ_T, CZ_B, KIND, MAXF><<<grid, G::NT, G::SMEM_C, s>>>(maps, a);
+    }
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if ((e = stage2_k(sa, pa.stage2, grid2, grid3, s)) != cudaSuccess) return e;
-  k_place_multi<CZ_T><<<tiles, PLACE_TILE, 0, s>>>(bo, pa);
+  if (place_tile == 64)
+    k_place_multi<CZ_T, 64><<<tiles, 64, 0, s>>>(bo, pa);
+  else if (place_tile == 128)
+    k_place_multi<CZ_T, 128><<<tiles, 128, 0, s>>>(bo, pa);
+  else
+    k_place_multi<CZ_T, 256><<<tiles, 256, 0, s>>>(bo, pa);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_copy_multi<CZ_T><<<(pa.nblocks + 7) / 8, 256, 0, s>>>(bo, pa);
@@ -247,6 +266,21 @@ int occupancy_u()
 }
 
 template <int KIND>
+int occupancy_slab_alt()
+{
+  if constexpr (HAS_SLAB_ALT) {
+    int n = 0;
+    if (prepare<k_stage1_slab<CZ_T, CZ_B, KIND, MAXF>>(SGi::SMEM) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage1_slab<CZ_T, CZ_B, KIND, MAXF>, SGi::NT,
+                                                      SGi::SMEM) != cudaSuccess)
+      return 0;
+    return n;
+  } else {
+    return 0;
+  }
+}
+
+template <int KIND>
 int occupancy_h()
 {
   if constexpr (HAS_HALF) {
@@ -311,16 +345,17 @@ extern "C" cudaError_t CZ_CAT(czl_compress_, CZ_SUFFIX)(int kind, const CUtensor
 extern "C" cudaError_t CZ_CAT(czl_compress_batch_, CZ_SUFFIX)(int kind, const StageMaps<MAXF> *maps,
                                                                const FwdArgs *a, const S2Args *sa,
                                                                const BatchOut *bo, const PlaceArgs *pa, int grid,
-                                                               int grid2, int grid3, int tiles, cudaStream_t s)
+                                                               int grid2, int grid3, int tiles, int place_tile,
+                                                               int slab, cudaStream_t s)
 {
 #ifdef CZ_FAST
   if (kind != W3AI) return cudaErrorInvalidValue;
-  return compress_batch_k<W3AI>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, s);
+  return compress_batch_k<W3AI>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, place_tile, slab, s);
 #else
   switch (kind) {
-    case W4: return compress_batch_k<W4>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, s);
-    case W4LI: return compress_batch_k<W4LI>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, s);
-    default: return compress_batch_k<W3AI>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, s);
+    case W4: return compress_batch_k<W4>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, place_tile, slab, s);
+    case W4LI: return compress_batch_k<W4LI>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, place_tile, slab, s);
+    default: return compress_batch_k<W3AI>(*maps, *a, *sa, *bo, *pa, grid, grid2, grid3, tiles, place_tile, slab, s);
   }
 #endif
 }
@@ -366,17 +401,18 @@ extern "C" cudaError_t CZ_CAT(czl_dense_, CZ_SUFFIX)(int kind, int fwd, const De
 // CTAs per SM of the stage kernel (which = 0), the decompress kernel
 // (which = 1), the small (2) or large (3) stage-2 kernel, the small (4) or
 // large (5) stage-2 inverse kernel, the half-block decoder (6; 0 where the
-// lane has none)
+// lane has none), the batched slab stage kernel where the lane's own is the
+// register-resident one (7; 0 where it has none)
 static int occupancy_query(int kind, int which);
 
 // cached per device: later calls (e.g. inside a stream capture) make no
 // CUDA call but cudaGetDevice
 extern "C" int CZ_CAT(czl_occupancy_, CZ_SUFFIX)(int kind, int which)
 {
-  static int cache[64][3][7];  // device, kind, which; 0 = not yet known
+  static int cache[64][3][8];  // device, kind, which; 0 = not yet known
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || kind < 0 || kind > 2 || which < 0 ||
-      which > 6)
+      which > 7)
     return occupancy_query(kind, which);
   int v = __atomic_load_n(&cache[dev][kind][which], __ATOMIC_ACQUIRE);
   if (v > 0) return v;
@@ -394,6 +430,7 @@ static int occupancy_query(int kind, int which)
 #ifdef CZ_FAST
   if (kind != W3AI) return 0;
   if (which == 6) return occupancy_h<W3AI>();
+  if (which == 7) return occupancy_slab_alt<W3AI>();
   return which == 0 ? occupancy_c<W3AI>() : occupancy_d<W3AI>();
 #else
   if (which == 6) {
@@ -401,6 +438,13 @@ static int occupancy_query(int kind, int which)
       case W4: return occupancy_h<W4>();
       case W4LI: return occupancy_h<W4LI>();
       default: return occupancy_h<W3AI>();
+    }
+  }
+  if (which == 7) {
+    switch (kind) {
+      case W4: return occupancy_slab_alt<W4>();
+      case W4LI: return occupancy_slab_alt<W4LI>();
+      default: return occupancy_slab_alt<W3AI>();
     }
   }
   if (which == 0) {
@@ -424,3 +468,8 @@ extern "C" int CZ_CAT(czl_slot_bytes_, CZ_SUFFIX)() { return G::PSLOT; }
 // global scratch per CTA of the stage kernel, the large stage-2 kernel and
 // the large stage-2 inverse kernel (FP64 32^3 only; 0 otherwise)
 extern "C" int CZ_CAT(czl_scratch_bytes_, CZ_SUFFIX)() { return G::SCRATCH; }
+
+// global scratch per CTA of the batched slab stage kernel where the tuner
+// may pick it instead of the register-resident one (one block; 0 where the
+// lane has no such choice)
+extern "C" int CZ_CAT(czl_alt_scratch_bytes_, CZ_SUFFIX)() { return HAS_SLAB_ALT ? (int)SGi::SCR : 0; }

@@ -23,7 +23,7 @@ struct StageMaps;
   extern "C" cudaError_t czl_compress_batch_##sfx(                                                   \
       int kind, const czp::StageMaps<32> *maps, const czp::FwdArgs *a, const czp::S2Args *sa,          \
       const czp::BatchOut *bo, const czp::PlaceArgs *pa, int grid, int grid2, int grid3, int tiles,    \
-      cudaStream_t s);                                                                                  \
+      int place_tile, int slab, cudaStream_t s);                                                        \
   extern "C" cudaError_t czl_decompress_##sfx(int kind, const CUtensorMap *om, const czp::InvArgs *a,  \
                                               const czp::UnArgs *ua, int grid, int gridu, int gridub, \
                                               const cudaEvent_t *marks, cudaStream_t s);              \
@@ -31,7 +31,8 @@ struct StageMaps;
                                          cudaStream_t s);                                           \
   extern "C" int czl_occupancy_##sfx(int kind, int which);                                         \
   extern "C" int czl_slot_bytes_##sfx();                                                           \
-  extern "C" int czl_scratch_bytes_##sfx();
+  extern "C" int czl_scratch_bytes_##sfx();                                                        \
+  extern "C" int czl_alt_scratch_bytes_##sfx();
 
 CZ_DECLARE_LAUNCHERS(f32_b8)
 CZ_DECLARE_LAUNCHERS(f32_b16)

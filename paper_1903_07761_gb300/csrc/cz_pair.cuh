@@ -267,6 +267,13 @@ struct G2 {
   // block per CTA, L2-resident), and large stage-2 payloads are shuffled in
   // global scratch too
   static constexpr bool SLAB = (sizeof(T) == 8 && B == 32) || B == 64;
+  // W4li with FP32 32^3 blocks runs the finest x-level row by row in shared
+  // memory (rowx), on tiles the TMA copies with the 128-byte swizzle (their
+  // rows are 128 bytes): its x-step with shuffles costs more than the extra
+  // shared-memory traffic (measured: compression -12 %, decompression
+  // -16 %), while W4 and W3ai are faster with the shuffles on plain tiles.
+  template <int KIND>
+  static constexpr bool rowx() { return sizeof(T) == 4 && B == 32 && KIND == W4LI; }
   static constexpr int Q = B / 4;
   static constexpr int ES = (int)sizeof(T);
   static constexpr int LGES = ES == 8 ? 3 : 2;
@@ -293,7 +300,9 @@ struct G2 {
   // (after the transform: the row offsets and the mask rows)
   static constexpr int PLC0 = PLANE > CUBE_AL ? PLANE : CUBE_AL;
   static constexpr int PLC = (PLC0 + 127) / 128 * 128;
-  static constexpr int SMEM_C = TILE + PLC + HALO;
+  // (+ 1 KiB: the kernels align their shared memory to 1024 bytes, the
+  // period of the 128-byte swizzle)
+  static constexpr int SMEM_C = TILE + PLC + HALO + 1024;
   // staging slot of one block: [nnz | 0 | raw payload]; the finished
   // stage-2 chunk replaces it in place and is at most 12 bytes longer than
   // the payload (every coded run of >= 2 zero words saves at least one
@@ -324,12 +333,12 @@ struct G2 {
   static constexpr int NPB = B == 32 ? 3 : 2;
   static constexpr int OTB0 = TILE > PLANE + HALO ? TILE : PLANE + HALO;
   static constexpr int OTB = (OTB0 + 127) / 128 * 128;
-  static constexpr int SMEM_D = R2D + NPB * PBCAP + OTB;
+  static constexpr int SMEM_D = OTB + R2D + NPB * PBCAP + 1024;
   static constexpr int SCRATCH = SLAB ? (PMAX_AL > TILE ? PMAX_AL : TILE) : 0;  // per CTA
   static_assert(HP == NK && NK == ZH && NT == HP * NK * 2, "thread grid");
   static_assert(HALO >= ROWB + MASKBP, "row offsets and mask rows fit the halo area");
-  static_assert(SLAB || SMEM_C <= 227 * 1024 - 1024, "stage kernel shared memory");
-  static_assert(SLAB || SMEM_D <= 227 * 1024 - 1024, "decompress shared memory");
+  static_assert(SLAB || SMEM_C <= 227 * 1024 - 512, "stage kernel shared memory");
+  static_assert(SLAB || SMEM_D <= 227 * 1024 - 512, "decompress shared memory");
   static_assert(SLAB || SMEM_S2B <= 227 * 1024 - 1024, "stage-2 shared memory");
   static_assert(SLAB || WMAX < 65536, "zero-RLE tokens hold run lengths below 65536 words");
 };
@@ -419,6 +428,17 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
   }
   return false;
 }
+
+// the dynamic shared memory rounded up to 1024 bytes (the period of the
+// 128-byte TMA swizzle); the kernels allocate 1 KiB more
+__device__ __forceinline__ unsigned char *align1024(unsigned char *p)
+{
+  return p + ((1024u - (smem_u32(p) & 1023u)) & 1023u);
+}
+
+// byte offset o of a tile of 128-byte rows as the 128-byte TMA swizzle
+// places it: 16-byte chunk c of row r lands at chunk c ^ (r mod 8)
+__device__ __forceinline__ unsigned swz128(unsigned o) { return o ^ ((o >> 3) & 0x70u); }
 
 // ------------------------------------------------------------ thread grid
 // Thread tid holds x-pair a of row pair k over z-half h.  With B >= 16 the
@@ -1256,16 +1276,61 @@ __device__ __forceinline__ void from_cube(T2 (&v)[2][B / 2], const T *C, int a, 
   for (int jl = 0; jl < MH; ++jl) v[0][2 * jl].x = C[cidx<N>(a, k, h * MH + jl)];
 }
 
+// ---- the finest x-level row by row in a swizzled tile of 128-byte rows
+// (FP32 32^3 blocks): thread t takes rows t, t + NT, ... (consecutive lanes
+// take consecutive rows, so the eight 16-byte chunks of a quarter warp fall
+// in distinct bank groups), holds a row in registers and transforms it with
+// compile-time stencils (fwd_reg / inv_reg: the same rounded operations in
+// the same order as the pair kernels' x-step), and writes it back in place.
+template <typename T, int B, int KIND, bool FWD, int NT>
+__device__ __forceinline__ void x_rows(unsigned char *tile)
+{
+  static_assert(sizeof(T) == 4 && B == 32 && (B * B) % (2 * NT) == 0, "128-byte FP32 rows, two per round");
+#pragma unroll 1
+  for (int r0 = threadIdx.x; r0 < B * B; r0 += 2 * NT) {
+    T e[2][B];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int row = r0 + q * NT;
+      const unsigned char *rp = tile + row * 128;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float4 w = *reinterpret_cast<const float4 *>(rp + ((c ^ (row & 7)) << 4));
+        e[q][4 * c] = w.x;
+        e[q][4 * c + 1] = w.y;
+        e[q][4 * c + 2] = w.z;
+        e[q][4 * c + 3] = w.w;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if constexpr (FWD)
+        fwd_reg<T, KIND, B, 1>(e[q]);
+      else
+        inv_reg<T, KIND, B, 1>(e[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int row = r0 + q * NT;
+      unsigned char *rp = tile + row * 128;
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        *reinterpret_cast<float4 *>(rp + ((c ^ (row & 7)) << 4)) =
+            make_float4(e[q][4 * c], e[q][4 * c + 1], e[q][4 * c + 2], e[q][4 * c + 3]);
+    }
+  }
+}
+
 // Whole forward transform.  The plane area and the cube may overlap (the
 // cube is written after the plane's last read); the halo is separate.
 // first_sync runs right after the first barrier (every thread has read its
 // input by then).  Ends without a barrier: from_cube's reads of the cube
 // are ordered by the caller's next barrier.
-template <typename T, int B, int KIND, typename T2, typename F>
+template <typename T, int B, int KIND, bool XSTEP = true, typename T2, typename F>
 __device__ __forceinline__ void fwd_all(T2 (&v)[2][B / 2], T2 *pl, T2 *hx, T *cube, int a, int k, int h, int seg,
                                         F &&first_sync)
 {
-  x_fwd<T, B, KIND>(v, a, seg);
+  if constexpr (XSTEP) x_fwd<T, B, KIND>(v, a, seg);
   y_fwd<T, B, KIND>(v, pl, a, k, h, first_sync);
   z_fwd<T, B, KIND>(v, hx, k, a, h);
   if constexpr (G2<T, B>::L > 1) {
@@ -1280,7 +1345,7 @@ __device__ __forceinline__ void fwd_all(T2 (&v)[2][B / 2], T2 *pl, T2 *hx, T *cu
 // halo; the caller orders the plane's and the halo's previous uses by a
 // barrier before the call, and their last reads by one after it.  side()
 // runs after the first barrier (at the start without coarser levels).
-template <typename T, int B, int KIND, typename T2, typename F>
+template <typename T, int B, int KIND, bool XSTEP = true, typename T2, typename F>
 __device__ __forceinline__ void inv_all(T2 (&v)[2][B / 2], T2 *pl, T2 *hx, T *cube, int a, int k, int h, int seg,
                                         F &&side)
 {
@@ -1295,7 +1360,7 @@ __device__ __forceinline__ void inv_all(T2 (&v)[2][B / 2], T2 *pl, T2 *hx, T *cu
   }
   z_inv<T, B, KIND>(v, hx, k, a, h);
   y_inv<T, B, KIND>(v, pl, a, k, h);
-  x_inv<T, B, KIND>(v, a, seg);
+  if constexpr (XSTEP) x_inv<T, B, KIND>(v, a, seg);
 }
 
 // ============================================================ stream helpers
@@ -1545,13 +1610,15 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
   using T2 = typename V2T<T>::type;
   constexpr int NT = G::NT, ES = G::ES, Q = G::Q;
   constexpr int HEAD = 64 * ES + G::MASKB;  // coarse values + mask
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *smem = align1024(smem_raw);
   constexpr int ZH = G::ZH;
-  T *CB = reinterpret_cast<T *>(smem);                               // cube of the coarser levels
-  unsigned *ROWOFF = reinterpret_cast<unsigned *>(smem + G::CUBE_AL);  // row offsets
+  unsigned char *OT = smem;  // output tile [z][y][x] (swizzled 128-byte rows for FP32 32^3 W4li)
+  constexpr bool RX = G::template rowx<KIND>();  // the finest x-level row by row in the tile
+  T *CB = reinterpret_cast<T *>(smem + G::OTB);                                 // cube of the coarser levels
+  unsigned *ROWOFF = reinterpret_cast<unsigned *>(smem + G::OTB + G::CUBE_AL);  // row offsets
   constexpr int NPB = G::NPB;
-  unsigned char *BUF0 = smem + G::R2D;  // NPB payload buffers of G::PBCAP bytes
-  unsigned char *OT = BUF0 + NPB * G::PBCAP;  // output tile [z][y][x]
+  unsigned char *BUF0 = smem + G::OTB + G::R2D;  // NPB payload buffers of G::PBCAP bytes
   T2 *PL = reinterpret_cast<T2 *>(OT);  // level-0 plane and halo, inside the tile area
   T2 *HX = reinterpret_cast<T2 *>(OT + G::PLANE);
   __shared__ __align__(8) unsigned long long s_bar[NPB];
@@ -1780,21 +1847,29 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_decompress2(const __grid_const
     if (!bad && G::L > 1) {
       // fetch_next runs after the cube's first barrier; the cube passes'
       // barriers follow it
-      inv_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg, fetch_next);
+      inv_all<T, B, KIND, !RX>(v, PL, HX, CB, ap, k, h, seg, fetch_next);
     } else {
       if (tid == 0) bulk_wait_read();
       __syncthreads();
       fetch_next();
-      if (!bad) inv_all<T, B, KIND>(v, PL, HX, CB, ap, k, h, seg, [] {});
+      if (!bad) inv_all<T, B, KIND, !RX>(v, PL, HX, CB, ap, k, h, seg, [] {});
     }
     // block -> output tile -> TMA store, which drains while the next block
-    // is decoded
+    // is decoded.  W4li (swizzled 128-byte rows): the pairs go to their
+    // swizzled places, then the finest x-level runs row by row in the tile
+    // (a bad block's zeros stay zeros).
     __syncthreads();  // the plane and the halo have been read
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
-      for (int zl = 0; zl < ZH; ++zl)
-        *reinterpret_cast<T2 *>(OT + (((h * ZH + zl) * B + 2 * k + r) * B + x0) * ES) = v[r][zl];
+      for (int zl = 0; zl < ZH; ++zl) {
+        const unsigned o = (unsigned)((((h * ZH + zl) * B + 2 * k + r) * B + x0) * ES);
+        *reinterpret_cast<T2 *>(OT + (RX ? swz128(o) : o)) = v[r][zl];
+      }
+    if constexpr (RX) {
+      __syncthreads();
+      if (!bad) x_rows<T, B, KIND, false, NT>(OT);
+    }
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {

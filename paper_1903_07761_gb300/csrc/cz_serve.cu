@@ -13,8 +13,15 @@
 // one by one).  A request that waits behind one that does not fit may be
 // admitted before it, unless the waiting one has waited longer than the
 // starvation limit, after which admission waits for it.
+//
+// The worker owns a host core while the server is active: with work in
+// flight, or within IDLE_SPIN of the last request, it polls the streams'
+// events and an arrival flag without sleeping (a sleep and a wake-up cost
+// tens of microseconds each, more than a small request takes on the GPU);
+// it blocks on the condition variable only after that.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -32,6 +39,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int MAX_GROUP = 32;                             // requests per batched launch
 constexpr auto STARVE_LIMIT = std::chrono::milliseconds(50);
+constexpr auto IDLE_SPIN = std::chrono::milliseconds(50);   // polling without sleep after the last activity
 
 struct Req {
   uint64_t ticket = 0;
@@ -165,6 +173,7 @@ class Server {
     *ticket = q.ticket;
     reqs_[q.ticket] = q;
     queue_.push_back(q.ticket);
+    arrived_.store(true, std::memory_order_release);
     cv_.notify_all();
     return CZ_OK;
   }
@@ -359,18 +368,27 @@ class Server {
   {
     cudaSetDevice(dev_);
     std::unique_lock<std::mutex> lock(mu_);
+    Clock::time_point active = Clock::now();  // the last admission, retirement or arrival
     for (;;) {
+      arrived_.store(false, std::memory_order_relaxed);
       const bool r = retire();
       const bool a = admit();
       bool busy = false;
       for (Slot &s : slots_) busy |= s.busy;
       if (stop_ && !busy && queue_.empty()) break;
-      if (!r && !a) {
-        // work in flight: poll the events again shortly; idle: sleep until a submit
-        if (busy)
-          cv_.wait_for(lock, std::chrono::microseconds(20));
-        else
-          cv_.wait_for(lock, std::chrono::milliseconds(5));
+      const Clock::time_point now = Clock::now();
+      if (r || a) active = now;
+      if (r || a) continue;
+      if (busy || now - active < IDLE_SPIN) {
+        // poll: let submitters and pollers take the lock, then look again
+        // (events, arrivals) without sleeping
+        lock.unlock();
+        for (int i = 0; i < 64 && !arrived_.load(std::memory_order_acquire); ++i) std::this_thread::yield();
+        lock.lock();
+        if (arrived_.load(std::memory_order_relaxed)) active = Clock::now();
+      } else {
+        cv_.wait_for(lock, std::chrono::milliseconds(5));  // idle: sleep until a submit
+        active = Clock::now();
       }
     }
   }
@@ -384,6 +402,7 @@ class Server {
   std::mutex mu_;
   std::condition_variable cv_, done_cv_;
   bool stop_ = false;
+  std::atomic<bool> arrived_{false};  // a submit since the worker last looked
   uint64_t next_ = 0;
   std::unordered_map<uint64_t, Req> reqs_;
   std::list<uint64_t> queue_;  // arrival order; erasing one entry keeps the others' iterators

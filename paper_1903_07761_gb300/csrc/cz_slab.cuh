@@ -53,6 +53,11 @@ struct SG {
   // (checked where a slab kernel is instantiated: whole 32-bit mask words
   // per row with the lanes on x, whole rows per thread)
   static constexpr bool OK = (B == 32 || B == 64) && ROWS % NT == 0;
+  // global scratch per CTA of the stage kernel: the lane's scratch block
+  // (room for the largest payload too) where the slab kernels are the
+  // lane's own, one block otherwise (FP32 32^3, where the batch tuner may
+  // pick them instead of the register-resident kernels)
+  static constexpr size_t SCR = G2<T, B>::SLAB ? (size_t)G2<T, B>::SCRATCH : (size_t)B * B * B * ES;
 };
 
 // element (x, y, z) of a B^3 block inside a dense array
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(SG<T, B>::NT, SG<T, B>::MINB) k_stage1_slab(
     s_t[tid] = tf;
   }
   __syncthreads();
-  const BView<T> v{reinterpret_cast<T *>(a.scratch + (size_t)blockIdx.x * G::SCRATCH), B, (long long)B * B};
+  const BView<T> v{reinterpret_cast<T *>(a.scratch + (size_t)blockIdx.x * S::SCR), B, (long long)B * B};
   unsigned char *arena = a.staging + (size_t)blockIdx.x * a.arena_bytes;
   unsigned long long aoff = 0;  // bytes used in this CTA's staging arena (the same in every thread)
 

@@ -23,6 +23,8 @@ All return plain dicts for the benchmark line.  Inputs are synthetic
 """
 from __future__ import annotations
 
+import ctypes as C
+import json
 import math
 import time
 
@@ -87,27 +89,40 @@ def batched(nfields: int = 64, reps: int = 10, seed: int = 3000, nbubbles: int =
         plain_streams.append(bytes(o[:int(one.item())].cpu().numpy()))
     del ws_plain
 
-    # batched: tune once, capture one call in a CUDA graph, replay
+    # batched: one call captured in a CUDA graph and replayed, first with the
+    # default knobs, then after the tuner has chosen them for each group
     ws = torch.empty(cz.cz_batch_workspace_size(params), dtype=torch.uint8, device="cuda")
     b = cz.BatchArgs(params, [t.data_ptr() for t in fields], [o.data_ptr() for o in outs], caps)
-    assert cz.cz_batch_tune(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(), s, 3) == cz.OK
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        assert cz.cz_compress_batch(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(), side.cuda_stream) == cz.OK
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=side):
-        assert cz.cz_compress_batch(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(),
-                                    torch.cuda.current_stream().cuda_stream) == cz.OK
-    g.replay()
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(reps):
+
+    def graph_ms():
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            assert cz.cz_compress_batch(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(), side.cuda_stream) == cz.OK
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            assert cz.cz_compress_batch(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(),
+                                        torch.cuda.current_stream().cuda_stream) == cz.OK
         g.replay()
-    e1.record()
-    torch.cuda.synchronize()
-    batch_ms = e0.elapsed_time(e1) / reps
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    untuned_ms = graph_ms()
+    t0 = time.perf_counter()
+    assert cz.cz_batch_tune(b, nbytes.data_ptr(), ws.data_ptr(), ws.numel(), s, 3) == cz.OK
+    tune_s = time.perf_counter() - t0
+    batch_ms = graph_ms()
+    n = C.c_size_t()
+    assert cz.lib().cz_batch_knobs_export(None, 0, C.byref(n)) == cz.OK
+    buf = C.create_string_buffer(n.value)
+    assert cz.lib().cz_batch_knobs_export(C.cast(buf, C.c_void_p), n.value, C.byref(n)) == cz.OK
+    knobs = json.loads(buf.value.decode())["entries"]
     lens = nbytes.cpu().tolist()
     same = all(bytes(o[:n].cpu().numpy()) == ps for o, n, ps in zip(outs, lens, plain_streams))
     stream_bytes = sum(lens)
@@ -126,6 +141,11 @@ def batched(nfields: int = 64, reps: int = 10, seed: int = 3000, nbubbles: int =
         "plain_ms": plain_ms, "plain_gbs": bytes_total / plain_ms / 1e6,
         "batched_ms": batch_ms, "batched_gbs": bytes_total / batch_ms / 1e6,
         "speedup": plain_ms / batch_ms, "streams_identical": same,
+        "untuned_batched_ms": untuned_ms, "tuned_over_untuned": untuned_ms / batch_ms, "tune_s": tune_s,
+        "tuned_knobs": knobs,
+        "knobs": "per group: slab = stage kernel with the block in global scratch (FP32 32^3 only) instead of "
+                 "in registers; s1_balanced = fewest stage CTAs with the same rounds; s2_div = stage-2 CTAs "
+                 "/ resident slots; place_tile = chunks per look-back tile",
         "psnr_db_sample": ps, "graph": True,
     }
 

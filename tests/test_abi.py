@@ -209,32 +209,43 @@ def test_aos_arguments_are_refused_before_any_cuda_call(cz):
 def test_batch_tuner_choices_round_trip_through_json(cz, tmp_path):
     """cz_batch_knobs_export / _import (host only): choices written by one
     process are read back by another; an entry replaces the one with its
-    signature; malformed texts are refused and change nothing."""
+    signature; version 1 texts (before the scan-granularity and kernel-family
+    knobs) still load, with tiles of 128 chunks and the register-resident
+    kernels; malformed texts are refused and change nothing."""
     import json
-    text = json.dumps({"format": "cz-batch-knobs", "version": 1, "entries": [
-        {"signature": "00000000000000ab", "s1_balanced": 1, "s2_div": 2},
-        {"signature": "fedcba9876543210", "s1_balanced": 0, "s2_div": 1}]}, indent=2)
+    text = json.dumps({"format": "cz-batch-knobs", "version": 2, "entries": [
+        {"signature": "00000000000000ab", "s1_balanced": 1, "s2_div": 2, "place_tile": 64, "slab": 1},
+        {"signature": "fedcba9876543210", "s1_balanced": 0, "s2_div": 1, "place_tile": 256, "slab": 0}]}, indent=2)
     src = tmp_path / "in.json"
     src.write_text(text)
     cz.load_tuning(str(src))
     dst = tmp_path / "out.json"
     cz.save_tuning(str(dst))
     d = json.loads(dst.read_text())
-    assert d["format"] == "cz-batch-knobs" and d["version"] == 1
-    got = {e["signature"]: (e["s1_balanced"], e["s2_div"]) for e in d["entries"]}
-    assert got["00000000000000ab"] == (1, 2) and got["fedcba9876543210"] == (0, 1)
+    assert d["format"] == "cz-batch-knobs" and d["version"] == 2
+
+    def entries():
+        return {e["signature"]: (e["s1_balanced"], e["s2_div"], e["place_tile"], e["slab"])
+                for e in json.loads(dst.read_text())["entries"]}
+    got = entries()
+    assert got["00000000000000ab"] == (1, 2, 64, 1) and got["fedcba9876543210"] == (0, 1, 256, 0)
     L = cz.lib()
     assert L.cz_batch_knobs_import(b'{"format":"cz-batch-knobs","version":1,"entries":'
                                    b'[{"signature":"ab","s1_balanced":0,"s2_div":4}]}') == cz.OK
     cz.save_tuning(str(dst))
-    got = {e["signature"]: (e["s1_balanced"], e["s2_div"]) for e in json.loads(dst.read_text())["entries"]}
-    assert got["00000000000000ab"] == (0, 4) and got["fedcba9876543210"] == (0, 1)
+    got = entries()
+    assert got["00000000000000ab"] == (0, 4, 128, 0) and got["fedcba9876543210"] == (0, 1, 256, 0)
     before = dst.read_text()
     for bad in (b"{}", b'{"format": "other", "version": 1, "entries": []}',
-                b'{"format": "cz-batch-knobs", "version": 2, "entries": []}',
+                b'{"format": "cz-batch-knobs", "version": 3, "entries": []}',
                 b'{"format": "cz-batch-knobs", "version": 1, "entries": [{"signature": "xyz", "s1_balanced": 0, "s2_div": 1}]}',
                 b'{"format": "cz-batch-knobs", "version": 1, "entries": [{"signature": "ab", "s1_balanced": 0, "s2_div": 0}]}',
                 b'{"format": "cz-batch-knobs", "version": 1, "entries": [{"signature": "ab", "s1_balanced": 2, "s2_div": 1}]}',
+                b'{"format": "cz-batch-knobs", "version": 2, "entries": [{"signature": "ab", "s1_balanced": 0, "s2_div": 1}]}',
+                b'{"format": "cz-batch-knobs", "version": 2, "entries": [{"signature": "ab", "s1_balanced": 0, "s2_div": 1, '
+                b'"place_tile": 100, "slab": 0}]}',
+                b'{"format": "cz-batch-knobs", "version": 2, "entries": [{"signature": "ab", "s1_balanced": 0, "s2_div": 1, '
+                b'"place_tile": 64, "slab": 2}]}',
                 b'{"format": "cz-batch-knobs", "version": 1, "entries": [{"signature": "cd", "s1_balanced": 0, "s2_div": 1}'):
         assert L.cz_batch_knobs_import(bad) == cz.ERR_ARG, bad
     cz.save_tuning(str(dst))

@@ -142,3 +142,43 @@ def test_batch_with_fp64_32_blocks_matches_the_oracle():
     for (f, e), (out, nb) in zip(items, res):
         got = out[:int(nb.item())].cpu().numpy().tobytes()
         assert got == O.compress(f, 32, O.W3AI, e)
+
+
+@pytest.mark.parametrize("kind", ["w3ai", "w4li"])
+def test_every_tuner_setting_gives_the_same_streams(kind):
+    """Every knob setting the tuner may pick -- stage kernel family (FP32
+    32^3: the block in registers or in global scratch), stage grid, stage-2
+    grid, look-back tile of 64 / 128 / 256 chunks -- writes the streams that
+    cz_compress writes for each field alone (and hence the oracle's)."""
+    import ctypes as C
+    import itertools
+    import torch
+    from paper_1903_07761_gb300 import cz
+    items = _fields(5, n=9)
+    tens = [torch.from_numpy(f).cuda() for f, _, _ in items]
+    params, caps, outs, ref = [], [], [], []
+    for (f, B, e), t in zip(items, tens):
+        p = cz.params_for(tuple(t.shape), t.dtype == torch.float64, B, kind, e)
+        params.append(p)
+        caps.append(cz.cz_compress_bound(p))
+        outs.append(torch.zeros(caps[-1], dtype=torch.uint8, device="cuda"))
+        single, snb = cz.compress(t, block=B, kind=kind, eps=e)
+        ref.append(single[:int(snb.item())].cpu().numpy().tobytes())
+    nbytes = torch.zeros(len(items), dtype=torch.int64, device="cuda")
+    ws = torch.empty(cz.cz_batch_workspace_size(params), dtype=torch.uint8, device="cuda")
+    b = cz.BatchArgs(params, [t.data_ptr() for t in tens], [o.data_ptr() for o in outs], caps)
+    L = cz.lib()
+    L.czi_compress_batch_knobs.argtypes = [C.c_int, C.POINTER(cz.Params), C.POINTER(C.c_void_p),
+                                           C.POINTER(C.c_void_p), C.POINTER(C.c_size_t), C.c_void_p, C.c_void_p,
+                                           C.c_size_t, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]
+    L.czi_compress_batch_knobs.restype = C.c_int
+    s = torch.cuda.current_stream().cuda_stream
+    for slab, s1, s2, pt in itertools.product((0, 1), (0, 1), (1, 2), (64, 128, 256)):
+        for o in outs:
+            o.fill_(0xA5)
+        r = L.czi_compress_batch_knobs(b.n, b.params, b.fields, b.outs, b.caps, nbytes.data_ptr(), ws.data_ptr(),
+                                       ws.numel(), s, s1, s2, pt, slab)
+        assert r == cz.OK
+        assert cz.cz_status(ws.data_ptr(), s) == cz.OK
+        got = [bytes(o[:int(n)].cpu().numpy()) for o, n in zip(outs, nbytes.cpu().tolist())]
+        assert got == ref, (slab, s1, s2, pt)
