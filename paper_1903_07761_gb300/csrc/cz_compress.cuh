@@ -58,6 +58,144 @@ constexpr unsigned long long TB_LOST = 0xFFFFFFFFFFFFFFFFull;
 constexpr unsigned long long TB_FIN = 1ull << 62;
 __device__ __forceinline__ unsigned long long tb_size(unsigned long long cb) { return cb & ~TB_FIN; }
 
+// ---- stage 2 of one slot, in place: [nnz | 0 | raw payload of pbytes]
+// becomes [nnz | ntok | tokens | literal words].  The payload is scattered
+// into byte-shuffled order (byte b of element e at b * E + e; element sizes
+// are powers of two, so no division) in SH, the zero-word runs are found
+// from a ballot bitmap with one scan, and the tokens and literals replace
+// the slot's contents.  Run by the NT threads OFF .. OFF + NT - 1 of a group
+// that synchronises with barrier BAR (0: the whole CTA); AUX holds four
+// bitmap arrays of `cap` words; s_u (>= 40 words) and s_i (>= 40) are the
+// group's scan scratch.  Returns the chunk bytes (the same in every thread).
+template <typename T, int NT, int BAR = 0, int OFF = 0>
+__device__ __forceinline__ unsigned stage2_chunk(unsigned *ch, int pbytes, unsigned char *SH, unsigned *AUX, int cap,
+                                                 unsigned *s_u, int *s_i)
+{
+  constexpr int NWP = NT / 32, ES = (int)sizeof(T), LGES = ES == 8 ? 3 : 2;
+  const int tid = (int)threadIdx.x - OFF, lane = threadIdx.x & 31, wid = tid >> 5;
+  const unsigned *SH32 = reinterpret_cast<const unsigned *>(SH);
+  const int E = pbytes >> LGES, W = pbytes >> 2, NB = (W + 31) >> 5;
+  unsigned *ZBM = AUX, *CM = AUX + cap, *EB = AUX + 2 * cap, *PRE = AUX + 3 * cap;
+  // payload word k holds bytes 0..3 of element 4k / ES at byte offset 4k % ES
+  const unsigned *raw = ch + 2;
+  for (int k0 = tid; k0 < W; k0 += 4 * NT) {
+    unsigned wv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) wv[j] = k0 + j * NT < W ? raw[k0 + j * NT] : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = k0 + j * NT;
+      if (k < W) {
+        const int e = (4 * k) >> LGES, b0 = (4 * k) & (ES - 1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) SH[(b0 + q) * E + e] = (unsigned char)(wv[j] >> (8 * q));
+      }
+    }
+  }
+  group_sync<BAR, NT>();  // the slot's payload is no longer needed
+  for (int g = wid; g < NB; g += NWP) {
+    const int w = g * 32 + lane;
+    const unsigned bal = __ballot_sync(FULL, w < W && SH32[w] == 0u);
+    if (lane == 0) ZBM[g] = bal;
+  }
+  group_sync<BAR, NT>();
+  // coded words C: zero words with a zero neighbour; a run starts at an
+  // S bit and ends before an Eb bit (or at W)
+  const int KB = (NB + NT - 1) / NT;  // bitmap words per thread (contiguous)
+  unsigned mine = 0;
+  for (int q = 0; q < KB; ++q) {
+    const int g = tid * KB + q;
+    if (g < NB) {
+      const unsigned Z = ZBM[g];
+      const unsigned Zp = g > 0 ? ZBM[g - 1] : 0u, Zn = g + 1 < NB ? ZBM[g + 1] : 0u;
+      const unsigned valid = (g == NB - 1 && (W & 31)) ? ((1u << (W & 31)) - 1u) : FULL;
+      const unsigned C = Z & ((Z << 1) | (Zp >> 31) | (Z >> 1) | ((Zn & 1u) << 31)) & valid;
+      // coded bit of the word before: zero with a zero neighbour
+      const unsigned cin = g > 0 ? ((Zp >> 31) & (((Zp >> 30) & 1u) | (Z & 1u))) : 0u;
+      CM[g] = C;
+      EB[g] = ~C & ((C << 1) | cin) & valid;
+      mine += (unsigned)__popc(C & ~((C << 1) | cin)) | ((unsigned)__popc(C) << 16);
+    }
+  }
+  unsigned tot;
+  unsigned run = block_exsum<NT, BAR, OFF>(mine, s_u, tot);  // packed: runs | coded words << 16
+  for (int q = 0; q < KB; ++q) {
+    const int g = tid * KB + q;
+    if (g < NB) {
+      PRE[g] = run;
+      const unsigned C = CM[g];
+      const unsigned cin = g > 0 ? (CM[g - 1] >> 31) : 0u;
+      run += (unsigned)__popc(C & ~((C << 1) | cin)) | ((unsigned)__popc(C) << 16);
+    }
+  }
+  const unsigned ns_tot = tot & 0xFFFFu, nc_tot = tot >> 16;
+  // the last word is coded iff it and the word before it are zero
+  const int l = W - 1;
+  const unsigned lastc =
+      (((ZBM[l >> 5] >> (l & 31)) & 1u) && l > 0 && ((ZBM[(l - 1) >> 5] >> ((l - 1) & 31)) & 1u)) ? 1u : 0u;
+  group_sync<BAR, NT>();
+  const unsigned ntok = ns_tot + (lastc ? 0u : 1u);
+  const unsigned nlit = (unsigned)W - nc_tot;
+  unsigned *tok = ch + 2;
+  unsigned *lit = tok + ntok;
+  // Run ends (Eb bits) around this thread's words: the last one before
+  // them (group max-scan, 0 if none -- no run ends at position 0) and the
+  // first one after them (group min-scan, W if none).
+  int my_last = 0, my_first = W;
+  for (int q = 0; q < KB; ++q) {
+    const int g = tid * KB + q;
+    if (g < NB && EB[g]) {
+      my_last = max(my_last, g * 32 + 31 - (int)__clz(EB[g]));
+      my_first = min(my_first, g * 32 + __ffs(EB[g]) - 1);
+    }
+  }
+  int pe_words = block_exmax<NT, BAR, OFF>(my_last, 0, s_i);
+  const int ne_after = block_rexmin<NT, BAR, OFF>(my_first, W, s_i);
+  // one token per run: (literal words since the previous run, run length);
+  // a final (literals, 0) token when the payload does not end in a run
+  for (int q = 0; q < KB; ++q) {
+    const int g = tid * KB + q;
+    if (g >= NB) break;
+    const unsigned C = CM[g], Eb = EB[g];
+    const unsigned cin = g > 0 ? (CM[g - 1] >> 31) : 0u;
+    unsigned S = C & ~((C << 1) | cin);
+    unsigned k = PRE[g] & 0xFFFFu;
+    while (S) {
+      const int b = __ffs(S) - 1;
+      S &= S - 1u;
+      const int p = g * 32 + b;
+      // previous run's end (or 0), this run's end (or W)
+      const unsigned below = Eb & ((1u << b) - 1u), above = Eb & ~((2u << b) - 1u);
+      const int pe = below ? g * 32 + 31 - (int)__clz(below) : pe_words;
+      int ne = ne_after;
+      if (above) {
+        ne = g * 32 + __ffs(above) - 1;
+      } else {
+        for (int h = q + 1; h < KB && tid * KB + h < NB; ++h)  // this thread's later words
+          if (EB[tid * KB + h]) {
+            ne = (tid * KB + h) * 32 + __ffs(EB[tid * KB + h]) - 1;
+            break;
+          }
+      }
+      tok[k] = (unsigned)(p - pe) | ((unsigned)(ne - p) << 16);
+      if (k + 1 == ns_tot && !lastc) tok[k + 1] = (unsigned)(W - ne);
+      ++k;
+    }
+    if (Eb) pe_words = g * 32 + 31 - (int)__clz(Eb);
+  }
+  if (tid == 0) {
+    if (ns_tot == 0) tok[0] = (unsigned)W;  // no run at all
+    ch[1] = ntok;
+  }
+  for (int w = tid; w < W; w += NT) {
+    const int g = w >> 5, b = w & 31;
+    const unsigned C = CM[g];
+    if (!((C >> b) & 1u)) lit[(unsigned)w - ((PRE[g] >> 16) + __popc(C & ((1u << b) - 1u)))] = SH32[w];
+  }
+  group_sync<BAR, NT>();
+  return 8u + 4u * ntok + 4u * nlit;
+}
+
 // field of global block bid among the nf fields of a batched launch
 template <int NF>
 __device__ __forceinline__ int field_of(const StageMaps<NF> &maps, int nf, int bid)
@@ -169,7 +307,7 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     const int nb = bid + (int)gridDim.x;
 
     // ---- forward transform
-    fwd_all<T, B, KIND, !RX>(v, PL, HX, CB, ap, k, h, seg, [&] {
+    auto prefetch = [&] {
       // (after a barrier: a timeout of this block's copy is visible here,
       // and then no further copy is started)
       if (tid == 0 && nb < a.nblocks && !*(volatile unsigned *)&s_to) {
@@ -180,7 +318,8 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
           tile_of(nb);
         }
       }
-    });
+    };
+    fwd_all<T, B, KIND, !RX>(v, PL, HX, CB, ap, k, h, seg, prefetch);
     if constexpr (G::L == 1) __syncthreads();  // no cube: the halo's last reads were just now
 
     // ---- significance bits (bit 2 zl + p: column x0 + p at z = h B/2 + zl),
@@ -275,152 +414,32 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
   }
 }
 
-// ---- stage 2, in place
+// ---- stage 2, in place, over the slots of all blocks
 template <typename T, int B, bool BIG>
 __global__ void __launch_bounds__(BIG ? 512 : 128) k_stage2(const S2Args a)
 {
   using G = G2<T, B>;
-  constexpr int NT = BIG ? 512 : 128, NWP = NT / 32, ES = G::ES, LGES = G::LGES;
+  constexpr int NT = BIG ? 512 : 128;
   constexpr int CAPB = BIG ? G::PMAX_AL : G::SHCAP;  // payload bytes in shared memory
   constexpr int cap = BIG ? G::NBWMAX : G::NBS;     // bitmap words
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ unsigned s_u[40];
   __shared__ int s_i[40];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  unsigned char *SH = smem;
-  const unsigned *SH32 = reinterpret_cast<const unsigned *>(smem);
   unsigned *AUX = reinterpret_cast<unsigned *>(smem + CAPB);
 
-  // the small launch visits every block (and skips the large payloads); the
-  // large launch visits only the blocks the stage kernel listed
+  // the small launch visits every block (and skips the large payloads and
+  // those the stage kernel has coded already); the large launch visits
+  // only the blocks the stage kernel listed
   const int count = BIG ? (int)reinterpret_cast<const WsHdr *>(a.ws)->nbig : a.nblocks;
   for (int it = blockIdx.x; it < count; it += gridDim.x) {
     const int bid = BIG ? a.biglist[it] : it;
     const unsigned long long so = a.table[2 * bid], cb = a.table[2 * bid + 1];
-    if (cb == TB_LOST || (cb & TB_FIN)) continue;  // staging overflow, or finished by the other launch
+    if (cb == TB_LOST || (cb & TB_FIN)) continue;  // staging overflow, or finished already
     const int pbytes = (int)cb - 8;
     if ((pbytes > G::SHCAP) != BIG) continue;  // the other launch's payload
     unsigned *ch = reinterpret_cast<unsigned *>(a.staging + so);
-    const int E = pbytes >> LGES, W = pbytes >> 2, NB = (W + 31) >> 5;
-    unsigned *ZBM = AUX, *CM = AUX + cap, *EB = AUX + 2 * cap, *PRE = AUX + 3 * cap;
-    // payload word k holds bytes 0..3 of element 4k / ES at byte offset 4k % ES
-    const unsigned *raw = ch + 2;
-    for (int k0 = tid; k0 < W; k0 += 4 * NT) {
-      unsigned wv[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) wv[j] = k0 + j * NT < W ? raw[k0 + j * NT] : 0u;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int k = k0 + j * NT;
-        if (k < W) {
-          const int e = (4 * k) >> LGES, b0 = (4 * k) & (ES - 1);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) SH[(b0 + q) * E + e] = (unsigned char)(wv[j] >> (8 * q));
-        }
-      }
-    }
-    __syncthreads();  // the slot's payload is no longer needed
-    for (int g = wid; g < NB; g += NWP) {
-      const int w = g * 32 + lane;
-      const unsigned bal = __ballot_sync(FULL, w < W && SH32[w] == 0u);
-      if (lane == 0) ZBM[g] = bal;
-    }
-    __syncthreads();
-    // coded words C: zero words with a zero neighbour; a run starts at an
-    // S bit and ends before an Eb bit (or at W)
-    const int KB = (NB + NT - 1) / NT;  // bitmap words per thread (contiguous)
-    unsigned mine = 0;
-    for (int q = 0; q < KB; ++q) {
-      const int g = tid * KB + q;
-      if (g < NB) {
-        const unsigned Z = ZBM[g];
-        const unsigned Zp = g > 0 ? ZBM[g - 1] : 0u, Zn = g + 1 < NB ? ZBM[g + 1] : 0u;
-        const unsigned valid = (g == NB - 1 && (W & 31)) ? ((1u << (W & 31)) - 1u) : FULL;
-        const unsigned C = Z & ((Z << 1) | (Zp >> 31) | (Z >> 1) | ((Zn & 1u) << 31)) & valid;
-        // coded bit of the word before: zero with a zero neighbour
-        const unsigned cin = g > 0 ? ((Zp >> 31) & (((Zp >> 30) & 1u) | (Z & 1u))) : 0u;
-        CM[g] = C;
-        EB[g] = ~C & ((C << 1) | cin) & valid;
-        mine += (unsigned)__popc(C & ~((C << 1) | cin)) | ((unsigned)__popc(C) << 16);
-      }
-    }
-    unsigned tot;
-    unsigned run = block_exsum<NT>(mine, s_u, tot);  // packed: runs | coded words << 16
-    for (int q = 0; q < KB; ++q) {
-      const int g = tid * KB + q;
-      if (g < NB) {
-        PRE[g] = run;
-        const unsigned C = CM[g];
-        const unsigned cin = g > 0 ? (CM[g - 1] >> 31) : 0u;
-        run += (unsigned)__popc(C & ~((C << 1) | cin)) | ((unsigned)__popc(C) << 16);
-      }
-    }
-    const unsigned ns_tot = tot & 0xFFFFu, nc_tot = tot >> 16;
-    // the last word is coded iff it and the word before it are zero
-    const int l = W - 1;
-    const unsigned lastc =
-        (((ZBM[l >> 5] >> (l & 31)) & 1u) && l > 0 && ((ZBM[(l - 1) >> 5] >> ((l - 1) & 31)) & 1u)) ? 1u : 0u;
-    __syncthreads();
-    const unsigned ntok = ns_tot + (lastc ? 0u : 1u);
-    const unsigned nlit = (unsigned)W - nc_tot;
-    unsigned *tok = ch + 2;
-    unsigned *lit = tok + ntok;
-    // Run ends (Eb bits) around this thread's words: the last one before
-    // them (block max-scan, 0 if none -- no run ends at position 0) and the
-    // first one after them (block min-scan, W if none).
-    int my_last = 0, my_first = W;
-    for (int q = 0; q < KB; ++q) {
-      const int g = tid * KB + q;
-      if (g < NB && EB[g]) {
-        my_last = max(my_last, g * 32 + 31 - (int)__clz(EB[g]));
-        my_first = min(my_first, g * 32 + __ffs(EB[g]) - 1);
-      }
-    }
-    int pe_words = block_exmax<NT>(my_last, 0, s_i);
-    const int ne_after = block_rexmin<NT>(my_first, W, s_i);
-    // one token per run: (literal words since the previous run, run length);
-    // a final (literals, 0) token when the payload does not end in a run
-    for (int q = 0; q < KB; ++q) {
-      const int g = tid * KB + q;
-      if (g >= NB) break;
-      const unsigned C = CM[g], Eb = EB[g];
-      const unsigned cin = g > 0 ? (CM[g - 1] >> 31) : 0u;
-      unsigned S = C & ~((C << 1) | cin);
-      unsigned k = PRE[g] & 0xFFFFu;
-      while (S) {
-        const int b = __ffs(S) - 1;
-        S &= S - 1u;
-        const int p = g * 32 + b;
-        // previous run's end (or 0), this run's end (or W)
-        const unsigned below = Eb & ((1u << b) - 1u), above = Eb & ~((2u << b) - 1u);
-        const int pe = below ? g * 32 + 31 - (int)__clz(below) : pe_words;
-        int ne = ne_after;
-        if (above) {
-          ne = g * 32 + __ffs(above) - 1;
-        } else {
-          for (int h = q + 1; h < KB && tid * KB + h < NB; ++h)  // this thread's later words
-            if (EB[tid * KB + h]) {
-              ne = (tid * KB + h) * 32 + __ffs(EB[tid * KB + h]) - 1;
-              break;
-            }
-        }
-        tok[k] = (unsigned)(p - pe) | ((unsigned)(ne - p) << 16);
-        if (k + 1 == ns_tot && !lastc) tok[k + 1] = (unsigned)(W - ne);
-        ++k;
-      }
-      if (Eb) pe_words = g * 32 + 31 - (int)__clz(Eb);
-    }
-    if (tid == 0) {
-      if (ns_tot == 0) tok[0] = (unsigned)W;  // no run at all
-      ch[1] = ntok;
-      a.table[2 * bid + 1] = TB_FIN | (8ull + 4ull * ntok + 4ull * nlit);
-    }
-    for (int w = tid; w < W; w += NT) {
-      const int g = w >> 5, b = w & 31;
-      const unsigned C = CM[g];
-      if (!((C >> b) & 1u)) lit[(unsigned)w - ((PRE[g] >> 16) + __popc(C & ((1u << b) - 1u)))] = SH32[w];
-    }
-    __syncthreads();
+    const unsigned cbytes = stage2_chunk<T, NT>(ch, pbytes, smem, AUX, cap, s_u, s_i);
+    if (threadIdx.x == 0) a.table[2 * bid + 1] = TB_FIN | (unsigned long long)cbytes;
   }
 }
 

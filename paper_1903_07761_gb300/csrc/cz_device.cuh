@@ -501,31 +501,44 @@ __device__ __forceinline__ U warp_incl_sum(U v)
   return v;
 }
 
-// Exclusive block-wide prefix of v over threads 0..NT-1; tmp >= 33 words.
-template <int NT, typename U>
+// Barrier of the NTH threads that use barrier BAR (whole warps): 0 is
+// __syncthreads (the whole CTA), others are named barriers of a thread
+// group.  The scans below run over the NT threads OFF .. OFF + NT - 1 of
+// such a group (OFF a multiple of 32; the defaults: the whole CTA).
+template <int BAR, int NTH>
+__device__ __forceinline__ void group_sync()
+{
+  if constexpr (BAR == 0)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NTH) : "memory");
+}
+
+// Exclusive prefix of v over the group's threads; tmp >= 33 words.
+template <int NT, int BAR = 0, int OFF = 0, typename U>
 __device__ __forceinline__ U block_exsum(U v, U *tmp, U &total)
 {
   constexpr int NWP = NT / 32;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = ((int)threadIdx.x - OFF) >> 5;
   const U inc = warp_incl_sum(v);
   if (lane == 31) tmp[wid] = inc;
-  __syncthreads();
+  group_sync<BAR, NT>();
   if (wid == 0) {
     const U t = lane < NWP ? tmp[lane] : U(0);
     const U ti = warp_incl_sum(t);
     if (lane < NWP) tmp[lane] = ti - t;
     if (lane == NWP - 1) tmp[32] = ti;
   }
-  __syncthreads();
+  group_sync<BAR, NT>();
   const U r = tmp[wid] + inc - v;
   total = tmp[32];
-  __syncthreads();
+  group_sync<BAR, NT>();
   return r;
 }
 
-// Exclusive block-wide prefix with one barrier: every warp adds up the
-// totals of the warps before it itself.  tmp (>= NT/32 words) must not be
-// written again before the caller's next barrier.
+// Exclusive prefix with one barrier: every warp adds up the totals of the
+// warps before it itself.  tmp (>= NT/32 words) must not be written again
+// before the caller's next barrier.
 template <int NT, typename U>
 __device__ __forceinline__ U block_exsum_nb(U v, U *tmp, U &total)
 {
@@ -541,12 +554,12 @@ __device__ __forceinline__ U block_exsum_nb(U v, U *tmp, U &total)
   return before + inc - v;
 }
 
-// Exclusive block-wide max over earlier threads (init if none).
-template <int NT>
+// Exclusive max over the group's earlier threads (init if none).
+template <int NT, int BAR = 0, int OFF = 0>
 __device__ __forceinline__ int block_exmax(int v, int init, int *tmp)
 {
   constexpr int NWP = NT / 32;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = ((int)threadIdx.x - OFF) >> 5;
   int inc = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -556,7 +569,7 @@ __device__ __forceinline__ int block_exmax(int v, int init, int *tmp)
   int ex = __shfl_up_sync(FULL, inc, 1);
   if (lane == 0) ex = init;
   if (lane == 31) tmp[wid] = inc;
-  __syncthreads();
+  group_sync<BAR, NT>();
   if (wid == 0) {
     int t = lane < NWP ? tmp[lane] : init;
 #pragma unroll
@@ -568,18 +581,18 @@ __device__ __forceinline__ int block_exmax(int v, int init, int *tmp)
     if (lane == 0) e = init;
     if (lane < NWP) tmp[lane] = e;
   }
-  __syncthreads();
+  group_sync<BAR, NT>();
   const int r = max(tmp[wid], ex);
-  __syncthreads();
+  group_sync<BAR, NT>();
   return r;
 }
 
-// Exclusive block-wide min over later threads (init if none).
-template <int NT>
+// Exclusive min over the group's later threads (init if none).
+template <int NT, int BAR = 0, int OFF = 0>
 __device__ __forceinline__ int block_rexmin(int v, int init, int *tmp)
 {
   constexpr int NWP = NT / 32;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = ((int)threadIdx.x - OFF) >> 5;
   int inc = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -589,7 +602,7 @@ __device__ __forceinline__ int block_rexmin(int v, int init, int *tmp)
   int ex = __shfl_down_sync(FULL, inc, 1);
   if (lane == 31) ex = init;
   if (lane == 0) tmp[wid] = inc;
-  __syncthreads();
+  group_sync<BAR, NT>();
   if (wid == 0) {
     int t = lane < NWP ? tmp[lane] : init;
 #pragma unroll
@@ -601,9 +614,9 @@ __device__ __forceinline__ int block_rexmin(int v, int init, int *tmp)
     if (lane == 31 || lane == NWP - 1) e = init;
     if (lane < NWP) tmp[lane] = e;
   }
-  __syncthreads();
+  group_sync<BAR, NT>();
   const int r = min(tmp[wid], ex);
-  __syncthreads();
+  group_sync<BAR, NT>();
   return r;
 }
 

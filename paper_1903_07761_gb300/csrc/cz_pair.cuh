@@ -1236,14 +1236,14 @@ __device__ __forceinline__ void cube_pass(T *C)
 }
 
 // all levels of the N^3 cube down to 4^3 (x, y, z per level)
-template <typename T, int N, int KIND, int NT, int S = 1>
+template <typename T, int N, int KIND, int NT, int S = 1, int NB = 0>
 __device__ __forceinline__ void cube_fwd(T *C)
 {
   if constexpr (N / S >= 8) {
-    cube_pass<T, N, KIND, NT, S, 0, true, true>(C);
-    cube_pass<T, N, KIND, NT, S, 1, true, false>(C);
-    cube_pass<T, N, KIND, NT, S, 2, true, false>(C);
-    cube_fwd<T, N, KIND, NT, 2 * S>(C);
+    cube_pass<T, N, KIND, NT, S, 0, true, true, NB>(C);
+    cube_pass<T, N, KIND, NT, S, 1, true, false, NB>(C);
+    cube_pass<T, N, KIND, NT, S, 2, true, false, NB>(C);
+    cube_fwd<T, N, KIND, NT, 2 * S, NB>(C);
   }
 }
 
