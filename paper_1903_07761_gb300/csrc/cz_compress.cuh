@@ -66,7 +66,8 @@ __device__ __forceinline__ unsigned long long tb_size(unsigned long long cb) { r
 // the slot's contents.  Run by the NT threads OFF .. OFF + NT - 1 of a group
 // that synchronises with barrier BAR (0: the whole CTA); AUX holds four
 // bitmap arrays of `cap` words; s_u (>= 40 words) and s_i (>= 40) are the
-// group's scan scratch.  Returns the chunk bytes (the same in every thread).
+// group's scan scratch.  Five barriers per payload.  Returns the chunk
+// bytes (the same in every thread).
 template <typename T, int NT, int BAR = 0, int OFF = 0>
 __device__ __forceinline__ unsigned stage2_chunk(unsigned *ch, int pbytes, unsigned char *SH, unsigned *AUX, int cap,
                                                  unsigned *s_u, int *s_i)
@@ -118,7 +119,7 @@ __device__ __forceinline__ unsigned stage2_chunk(unsigned *ch, int pbytes, unsig
     }
   }
   unsigned tot;
-  unsigned run = block_exsum<NT, BAR, OFF>(mine, s_u, tot);  // packed: runs | coded words << 16
+  unsigned run = block_exsum_nb<NT, BAR, OFF>(mine, s_u, tot);  // packed: runs | coded words << 16
   for (int q = 0; q < KB; ++q) {
     const int g = tid * KB + q;
     if (g < NB) {
@@ -133,7 +134,6 @@ __device__ __forceinline__ unsigned stage2_chunk(unsigned *ch, int pbytes, unsig
   const int l = W - 1;
   const unsigned lastc =
       (((ZBM[l >> 5] >> (l & 31)) & 1u) && l > 0 && ((ZBM[(l - 1) >> 5] >> ((l - 1) & 31)) & 1u)) ? 1u : 0u;
-  group_sync<BAR, NT>();
   const unsigned ntok = ns_tot + (lastc ? 0u : 1u);
   const unsigned nlit = (unsigned)W - nc_tot;
   unsigned *tok = ch + 2;
@@ -149,8 +149,10 @@ __device__ __forceinline__ unsigned stage2_chunk(unsigned *ch, int pbytes, unsig
       my_first = min(my_first, g * 32 + __ffs(EB[g]) - 1);
     }
   }
-  int pe_words = block_exmax<NT, BAR, OFF>(my_last, 0, s_i);
-  const int ne_after = block_rexmin<NT, BAR, OFF>(my_first, W, s_i);
+  // (its barrier also orders every thread's PRE words before the literal
+  // loop reads them)
+  int pe_words, ne_after;
+  block_exmax_rexmin_nb<NT, BAR, OFF>(my_last, 0, my_first, W, s_i, pe_words, ne_after);
   // one token per run: (literal words since the previous run, run length);
   // a final (literals, 0) token when the payload does not end in a run
   for (int q = 0; q < KB; ++q) {

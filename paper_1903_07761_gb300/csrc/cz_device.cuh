@@ -539,19 +539,54 @@ __device__ __forceinline__ U block_exsum(U v, U *tmp, U &total)
 // Exclusive prefix with one barrier: every warp adds up the totals of the
 // warps before it itself.  tmp (>= NT/32 words) must not be written again
 // before the caller's next barrier.
-template <int NT, typename U>
+template <int NT, int BAR = 0, int OFF = 0, typename U>
 __device__ __forceinline__ U block_exsum_nb(U v, U *tmp, U &total)
 {
   constexpr int NWP = NT / 32;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = ((int)threadIdx.x - OFF) >> 5;
   const U inc = warp_incl_sum(v);
   if (lane == 31) tmp[wid] = inc;
-  __syncthreads();
+  group_sync<BAR, NT>();
   const U t = lane < NWP ? tmp[lane] : U(0);
   const U ti = warp_incl_sum(t);
   const U before = __shfl_sync(FULL, ti - t, wid);  // exclusive prefix of this warp's total
   total = __shfl_sync(FULL, ti, NWP - 1);
   return before + inc - v;
+}
+
+// Both of the scans below with one barrier: the exclusive max of vmax over
+// the group's earlier threads (imax if none) and the exclusive min of vmin
+// over its later threads (imin if none).  tmp >= 2 * NT/32 words, not
+// written again before the caller's next barrier.
+template <int NT, int BAR = 0, int OFF = 0>
+__device__ __forceinline__ void block_exmax_rexmin_nb(int vmax, int imax, int vmin, int imin, int *tmp, int &exmax,
+                                                      int &rexmin)
+{
+  constexpr int NWP = NT / 32;
+  const int lane = threadIdx.x & 31, wid = ((int)threadIdx.x - OFF) >> 5;
+  int fwd = vmax, bwd = vmin;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(FULL, fwd, o);
+    if (lane >= o) fwd = max(fwd, n);
+    const int m = __shfl_down_sync(FULL, bwd, o);
+    if (lane + o < 32) bwd = min(bwd, m);
+  }
+  int ex = __shfl_up_sync(FULL, fwd, 1);
+  if (lane == 0) ex = imax;
+  int rx = __shfl_down_sync(FULL, bwd, 1);
+  if (lane == 31) rx = imin;
+  if (lane == 31) tmp[wid] = fwd;       // the warp's max
+  if (lane == 0) tmp[NWP + wid] = bwd;  // the warp's min
+  group_sync<BAR, NT>();
+  int pm = imax, pn = imin;
+#pragma unroll
+  for (int q = 0; q < NWP; ++q) {
+    if (q < wid) pm = max(pm, tmp[q]);
+    if (q > wid) pn = min(pn, tmp[NWP + q]);
+  }
+  exmax = max(pm, ex);
+  rexmin = min(pn, rx);
 }
 
 // Exclusive max over the group's earlier threads (init if none).

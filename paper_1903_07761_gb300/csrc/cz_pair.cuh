@@ -1495,7 +1495,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_unstage(const UnArgs a)
   unsigned *TL = reinterpret_cast<unsigned *>(smem + CAPB);  // per token of a round: first literal,
   unsigned *TO = TL + NT;                                      // first output word,
   unsigned *TK = TO + NT;                                      // the token
-  __shared__ unsigned s_u[40];
+  __shared__ unsigned long long s_u64[NT / 32];
   __shared__ unsigned s_nnz, s_ntok, s_bad;
   __shared__ unsigned long long s_off, s_len;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1555,9 +1555,13 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_unstage(const UnArgs a)
         const unsigned k = r0 + tid;
         const unsigned tk = k < ntok ? __ldg(tok + k) : 0u;
         const unsigned nl = tk & 0xFFFFu, run = nl + (tk >> 16);
-        unsigned tl, to_;
-        const unsigned lp = block_exsum<NT>(nl, s_u, tl);
-        const unsigned op = block_exsum<NT>(run, s_u, to_);
+        // both prefixes in one scan (one barrier): literal words in the low
+        // half, output words in the high half (each sum stays below 2^32)
+        unsigned long long tot2;
+        const unsigned long long ex2 =
+            block_exsum_nb<NT>((unsigned long long)nl | ((unsigned long long)run << 32), s_u64, tot2);
+        const unsigned lp = (unsigned)ex2, op = (unsigned)(ex2 >> 32);
+        const unsigned tl = (unsigned)tot2, to_ = (unsigned)(tot2 >> 32);
         TL[tid] = lit_carry + lp;
         TO[tid] = out_carry + op;
         TK[tid] = tk;
