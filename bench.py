@@ -593,7 +593,7 @@ def run_gpu(args, rank, world, local_rank):
                 "psnr_db": 20 * math.log10((fmax - fmin) / (2 * math.sqrt(mse_k))) if mse_k > 0 else None}
 
     per_kind = {}
-    bit_zeroing = block_sizes = None
+    bit_zeroing = block_sizes = aggregate = None
     if not args.headline_only:
         for kname, kk in cz.KINDS.items():
             per_kind[kname] = measure(cz.params_for(tuple(field.shape), False, B, kk, args.eps, cz.EPS_REL, True,
@@ -610,6 +610,19 @@ def run_gpu(args, rank, world, local_rank):
             ws_b = ws if need == ws.numel() else torch.empty(need, dtype=torch.uint8, device=dev)
             block_sizes[f"b{bb}"] = measure(pb, ws_b)
             del ws_b
+        torch.cuda.empty_cache()
+        # aggregate chunks (Sec. 3, Exp. 2 and 3): G consecutive blocks per
+        # stage-2 chunk, against one chunk per block of the same edge
+        aggregate = {"kind": args.kind, "eps": args.eps}
+        for bb, gs in ((B, (4, 8)), (16, (16,)), (8, (16,))):
+            for g in gs:
+                pg = cz.params_for(tuple(field.shape), False, bb, kind, args.eps, cz.EPS_REL, True, -1.0, group=g)
+                need = max(cz.cz_workspace_size(pg), ws.numel())
+                ws_g = ws if need == ws.numel() else torch.empty(need, dtype=torch.uint8, device=dev)
+                res = measure(pg, ws_g)
+                res["cr_gain"] = res["cr"] / block_sizes[f"b{bb}"]["cr"] - 1
+                aggregate[f"b{bb}_g{g}"] = res
+                del ws_g
         torch.cuda.empty_cache()
 
     # random access with and without the decoded-block cache, on the
@@ -722,6 +735,7 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clk,
         "per_kind": per_kind,
         "bit_zeroing": bit_zeroing,
+        "aggregate_chunks": aggregate,
         "block_sizes": block_sizes,
         "random_access": random_access,
         "batched": batched_res,

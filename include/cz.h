@@ -74,6 +74,23 @@ enum { CZ_FLAG_FAST = 1 };
  * At most one of the two; not with CZ_BOUND_STRICT (whose bound does not
  * cover the zeroing error).  Recorded in the stream header. */
 enum { CZ_FLAG_ZERO4 = 2, CZ_FLAG_ZERO8 = 4 };
+/* flags: aggregate chunks (Sec. 3, Exp. 2 and 3: the stage-1 output of
+ * several blocks is concatenated and the lossless substage codes the
+ * concatenation as one buffer).  CZ_FLAG_GROUP4 / 8 / 16 put G = 4 / 8 / 16
+ * consecutive blocks (x-fastest block order; the last group may hold fewer)
+ * in one chunk with one offset-table entry: the chunk is [u32 nnz of each
+ * block | u32 ntok | tokens | literal words], the zero-run code of the byte
+ * shuffle of the blocks' concatenated payloads.  The stream then carries
+ * ceil(nblocks / G) + 1 offsets.  Stage 2 only, and only where G times the
+ * largest block payload is at most CZ_GROUP_MAX_BYTES (FP32 32^3 blocks:
+ * G <= 8; FP64 32^3: G = 4; FP32 64^3: none); otherwise CZ_ERR_ARG.
+ * cz_compress, cz_compress_noalloc, cz_decompress, cz_decompress_blocks
+ * (which decodes the whole group of each requested block) and
+ * cz_stream_concat (slabs whose block counts are multiples of G, but the
+ * last) take such streams; cz_compress_batch, cz_compress_aos and the server
+ * refuse the flag.  Recorded in the stream header. */
+enum { CZ_FLAG_GROUP4 = 8, CZ_FLAG_GROUP8 = 16, CZ_FLAG_GROUP16 = 24 };
+#define CZ_GROUP_MAX_BYTES (1792u * 1024u)
 
 enum {
   CZ_OK = 0,
@@ -95,7 +112,8 @@ typedef struct cz_params {
   int32_t eps_mode;   /* CZ_EPS_REL (default) or CZ_EPS_ABS                 */
   int32_t stage2;     /* 1: byte shuffle + zero-RLE each chunk; 0: raw      */
   int32_t bound_mode; /* CZ_BOUND_PAPER (default) or CZ_BOUND_STRICT        */
-  int32_t flags;      /* CZ_FLAG_FAST, CZ_FLAG_ZERO4 / CZ_FLAG_ZERO8, or 0   */
+  int32_t flags;      /* CZ_FLAG_FAST, CZ_FLAG_ZERO4 / CZ_FLAG_ZERO8,
+                         CZ_FLAG_GROUP4 / 8 / 16 (or'ed), or 0            */
   double eps;         /* tolerance, >= 0                                    */
   double range;       /* >= 0: max - min supplied by the caller (skips the
                          min/max pass); < 0: computed on the device        */

@@ -33,6 +33,9 @@ F32, F64 = 0, 1
 EPS_REL, EPS_ABS = 0, 1
 BOUND_PAPER, BOUND_STRICT = 0, 1
 FLAG_ZERO4, FLAG_ZERO8 = 2, 4  # bit zeroing of the kept details (Sec. 3, Exp. 2)
+# aggregate chunks of 4 / 8 / 16 consecutive blocks (Sec. 3, Exp. 2 and 3)
+FLAG_GROUP4, FLAG_GROUP8, FLAG_GROUP16 = 8, 16, 24
+GROUP_MASK = 24
 OK, ERR_ARG, ERR_CAPACITY, ERR_CORRUPT = 0, -1, -2, -3
 HEADER_BYTES = 128
 
@@ -200,19 +203,32 @@ def zero_flag(zbits: int) -> int:
     return {0: 0, 4: FLAG_ZERO4, 8: FLAG_ZERO8}[int(zbits)]
 
 
+def group_flag(group: int) -> int:
+    return {1: 0, 4: FLAG_GROUP4, 8: FLAG_GROUP8, 16: FLAG_GROUP16}[int(group)]
+
+
+def group_blocks(flags: int) -> int:
+    """Blocks per chunk of a flags word: 1, 4, 8 or 16."""
+    code = (int(flags) & GROUP_MASK) >> 3
+    return 2 << code if code else 1
+
+
 def params(shape, block, dtype, kind, eps, eps_mode=EPS_REL, stage2=True, range_=-1.0,
-           bound_mode=0, zbits=0):
+           bound_mode=0, zbits=0, group=1):
     nz, ny, nx = shape
     return Params(nx, ny, nz, block, F64 if np.dtype(dtype) == np.float64 else F32,
-                  kind, eps_mode, int(stage2), int(bound_mode), zero_flag(zbits), float(eps), float(range_))
+                  kind, eps_mode, int(stage2), int(bound_mode), zero_flag(zbits) | group_flag(group),
+                  float(eps), float(range_))
 
 
 def compress(field: np.ndarray, block: int, kind: int, eps: float,
              eps_mode: int = EPS_REL, stage2: bool = True, range_: float = -1.0,
-             bound_mode: int = 0, zbits: int = 0) -> bytes:
-    """zbits = 4 / 8: bit zeroing Z4 / Z8 of the kept details (Sec. 3, Exp. 2)."""
+             bound_mode: int = 0, zbits: int = 0, group: int = 1) -> bytes:
+    """zbits = 4 / 8: bit zeroing Z4 / Z8 of the kept details (Sec. 3, Exp. 2).
+    group = 4 / 8 / 16: aggregate chunks, each over that many consecutive
+    blocks (Sec. 3, Exp. 2 and 3; stage 2 only)."""
     field = np.ascontiguousarray(field)
-    p = params(field.shape, block, field.dtype, kind, eps, eps_mode, stage2, range_, bound_mode, zbits)
+    p = params(field.shape, block, field.dtype, kind, eps, eps_mode, stage2, range_, bound_mode, zbits, group)
     cap = C.c_size_t()
     r = lib().czo_compress_bound(C.byref(p), C.byref(cap))
     if r != OK:
@@ -261,12 +277,15 @@ def decompress(stream: bytes) -> np.ndarray:
 
 
 def chunk_table(stream: bytes):
-    """(data_start, offsets[nblocks+1]) parsed from a stream."""
+    """(data_start, offsets[nchunks+1]) parsed from a stream (one chunk per
+    block, or per group of blocks with a group flag)."""
     h = read_header(stream)
     B = h["block"]
     nb = (h["nx"] // B) * (h["ny"] // B) * (h["nz"] // B)
-    offs = np.frombuffer(stream, np.uint64, count=nb + 1, offset=HEADER_BYTES).astype(np.int64)
-    data0 = (HEADER_BYTES + 8 * (nb + 1) + 15) // 16 * 16
+    G = group_blocks(h["flags"])
+    nc = (nb + G - 1) // G
+    offs = np.frombuffer(stream, np.uint64, count=nc + 1, offset=HEADER_BYTES).astype(np.int64)
+    data0 = (HEADER_BYTES + 8 * (nc + 1) + 15) // 16 * 16
     return data0, offs
 
 

@@ -273,15 +273,75 @@ int czo_rle_decode(const uint32_t *tokens, size_t ntok, const uint8_t *lits,
 }
 
 /* --------------------------------------------------------------------------
+ * Stage 2 of one payload: byte shuffle with element size s, then the zero
+ * run-length code.  The tokens and then the literal words go to out (cap
+ * bytes); *ntok gets the token count.  Returns the bytes written or < 0.
+ * -------------------------------------------------------------------------- */
+static int64_t stage2_encode(const uint8_t *pay, size_t pbytes, int s, uint8_t *out,
+                             size_t cap, uint32_t *ntok)
+{
+  uint8_t *sh = (uint8_t *)malloc(pbytes + 4);
+  size_t tok_cap = pbytes / 4 + 16;
+  uint32_t *tok = (uint32_t *)malloc(tok_cap * 4);
+  uint8_t *lit = (uint8_t *)malloc(pbytes + 4);
+  size_t nt = 0, nl = 0;
+  int64_t r = CZO_ERR_ARG;
+  if (sh && tok && lit) {
+    czo_shuffle(pay, pbytes, s, sh);
+    r = czo_rle_encode(sh, pbytes, tok, tok_cap, &nt, lit, pbytes, &nl);
+    if (r >= 0) {
+      if (4 * nt + nl > cap) {
+        r = CZO_ERR_CAPACITY;
+      } else {
+        memcpy(out, tok, 4 * nt);
+        memcpy(out + 4 * nt, lit, nl);
+        *ntok = (uint32_t)nt;
+        r = (int64_t)(4 * nt + nl);
+      }
+    }
+  }
+  free(sh);
+  free(tok);
+  free(lit);
+  return r;
+}
+
+/* the inverse: ntok tokens then literal words in the n bytes at in -> the
+ * pbytes of the payload */
+static int stage2_decode(const uint8_t *in, size_t n, uint32_t ntok, int s, uint8_t *pay,
+                         size_t pbytes)
+{
+  if ((size_t)ntok > n / 4 || n % 4 != 0) return CZO_ERR_CORRUPT;
+  uint32_t *tok = (uint32_t *)malloc((size_t)ntok * 4 + 4);
+  uint8_t *sh = (uint8_t *)malloc(pbytes + 4);
+  int r = CZO_ERR_ARG;
+  if (tok && sh) {
+    memcpy(tok, in, (size_t)ntok * 4);
+    r = czo_rle_decode(tok, ntok, in + (size_t)ntok * 4, n - (size_t)ntok * 4, sh, pbytes);
+    if (r == CZO_OK) czo_unshuffle(sh, pbytes, s, pay);
+  }
+  free(tok);
+  free(sh);
+  return r;
+}
+
+int czo_group_blocks(int32_t flags)
+{
+  const int code = (flags & CZO_GROUP_MASK) >> 3;
+  return code ? 2 << code : 1;
+}
+
+/* --------------------------------------------------------------------------
  * Stream header (little-endian, 128 bytes):
  *   0 u32 magic "CCZ1"   4 u16 version=1   6 u16 header bytes=128
  *   8 i32 nx  12 i32 ny  16 i32 nz
  *  20 u8 B  21 u8 dtype  22 u8 kind  23 u8 stage2  24 u8 eps_mode  25 u8 L
- *  26 u8 bound_mode  27 u8 flags (bit zeroing)  28 u32 nblocks
+ *  26 u8 bound_mode  27 u8 flags (bit zeroing, group code)  28 u32 nblocks
  *  32 f64 eps  40 f64 t (threshold as used, widened)  48 f64 min  56 f64 max
  *  64 f64 range  72 u64 chunk-section bytes  80 u64 total stream bytes
- * Then (nblocks+1) u64 chunk offsets relative to the chunk section, which
- * starts at the next multiple of 16 bytes.
+ * Then (nchunks+1) u64 chunk offsets relative to the chunk section, which
+ * starts at the next multiple of 16 bytes; nchunks = ceil(nblocks / G) with
+ * G blocks per chunk (1 unless a group flag is set).
  * -------------------------------------------------------------------------- */
 static void czo_write_header(uint8_t *out, const czo_params *p, double t,
                              double mn, double mx, double range,
@@ -306,7 +366,7 @@ static void czo_write_header(uint8_t *out, const czo_params *p, double t,
   out[24] = (uint8_t)p->eps_mode;
   out[25] = (uint8_t)L;
   out[26] = (uint8_t)p->bound_mode;
-  out[27] = (uint8_t)(p->flags & (CZO_FLAG_ZERO4 | CZO_FLAG_ZERO8));
+  out[27] = (uint8_t)(p->flags & (CZO_FLAG_ZERO4 | CZO_FLAG_ZERO8 | CZO_GROUP_MASK));
   memcpy(out + 28, &nb, 4);
   memcpy(out + 32, &p->eps, 8);
   memcpy(out + 40, &t, 8);
@@ -337,7 +397,7 @@ int czo_read_header(const uint8_t *in, size_t n, czo_params *p, double *t,
   p->stage2 = in[23];
   p->eps_mode = in[24];
   p->bound_mode = in[26];
-  p->flags = in[27] & (CZO_FLAG_ZERO4 | CZO_FLAG_ZERO8);
+  p->flags = in[27] & (CZO_FLAG_ZERO4 | CZO_FLAG_ZERO8 | CZO_GROUP_MASK);
   memcpy(&p->eps, in + 32, 8);
   memcpy(t, in + 40, 8);
   memcpy(mn, in + 48, 8);
@@ -374,6 +434,8 @@ static int check_params(const czo_params *p)
   const int z = p->flags & (CZO_FLAG_ZERO4 | CZO_FLAG_ZERO8);
   if (z == (CZO_FLAG_ZERO4 | CZO_FLAG_ZERO8)) return CZO_ERR_ARG;
   if (z && p->bound_mode == CZO_BOUND_STRICT) return CZO_ERR_ARG;
+  /* aggregate chunks group the lossless substage's input */
+  if ((p->flags & CZO_GROUP_MASK) && !p->stage2) return CZO_ERR_ARG;
   return CZO_OK;
 }
 

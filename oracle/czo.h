@@ -27,6 +27,12 @@
  *   - keep a detail iff !(|d| < t), t = eps * (max - min) of the whole field.
  *   - stream: header, (nblocks+1) u64 chunk offsets, one chunk per block;
  *     optional stage 2 = byte shuffle + zero run-length coding per chunk.
+ *   - aggregate chunks (Sec. 3, Exp. 2 and 3: the stage-1 output of several
+ *     blocks is concatenated and the buffer coded by the lossless substage
+ *     as one stream): with a group flag, G consecutive blocks (x-fastest
+ *     block order; the last group may hold fewer) share one chunk and one
+ *     table entry.  The chunk is [nnz of each block | ntok | tokens |
+ *     literals] over the byte shuffle of the concatenated payloads.
  */
 #ifndef CZO_H
 #define CZO_H
@@ -55,6 +61,9 @@ enum {
 /* bit zeroing (Sec. 3, Exp. 2): the 4 / 8 least significant bits of every
  * kept detail coefficient are cleared before the lossless substage */
 enum { CZO_FLAG_ZERO4 = 2, CZO_FLAG_ZERO8 = 4 };
+/* aggregate chunks (Sec. 3, Exp. 2): a two-bit field, G = 2 << code
+ * consecutive blocks per chunk (code 0: one chunk per block); stage 2 only */
+enum { CZO_FLAG_GROUP4 = 8, CZO_FLAG_GROUP8 = 16, CZO_FLAG_GROUP16 = 24, CZO_GROUP_MASK = 24 };
 #define CZO_MAGIC 0x315A4343u /* bytes "CCZ1" */
 #define CZO_ZMIN_WORDS 2      /* shortest zero run coded as a run (32-bit words) */
 
@@ -68,8 +77,8 @@ typedef struct czo_params {
   int32_t bound_mode; /* CZO_BOUND_PAPER: threshold t ; CZO_BOUND_STRICT:
                          threshold t / C (see czo_synthesis_norm)             */
   int32_t flags;      /* CZO_FLAG_ZERO4 / CZO_FLAG_ZERO8: bit zeroing of the
-                         kept details; other bits (library build options)
-                         are ignored                                          */
+                         kept details; CZO_FLAG_GROUP*: aggregate chunks;
+                         other bits (library build options) are ignored      */
   double eps;
   double range;       /* >= 0: use this range ; < 0: compute max - min         */
 } czo_params;
@@ -131,6 +140,9 @@ double czo_threshold(double eps, int eps_mode, double range);
  *   C = max_i sum_l ( R_l(ix) R_l(iy) R_l(iz) - E_l(ix) E_l(iy) E_l(iz) ).
  * Returns a negative value for an unsupported (kind, B). */
 double czo_synthesis_norm(int kind, int B);
+
+/* blocks per chunk of a flags word: 1, 4, 8 or 16 */
+int czo_group_blocks(int32_t flags);
 
 /* ---- stage 2 primitives ---------------------------------------------------- */
 void czo_shuffle(const uint8_t *in, size_t nbytes, int s, uint8_t *out);

@@ -40,8 +40,25 @@ struct NvtxRange {
 
 struct Shape {
   int nbx, nby, nbz, nblocks, L, es;
+  int G, nchunks;  // blocks per chunk (1, or 4 / 8 / 16 with aggregate chunks) and chunks
   unsigned long long data0;
 };
+
+constexpr int GROUP_FLAGS = CZ_FLAG_GROUP16;  // the two-bit group field
+
+// blocks per chunk of a flags word: 1, 4, 8 or 16
+int group_of(int flags)
+{
+  const int code = (flags & GROUP_FLAGS) >> 3;
+  return code ? 2 << code : 1;
+}
+
+// bytes of the largest stage-1 payload of one block
+size_t pmax_bytes(int block, int es)
+{
+  const size_t v = (size_t)block * block * block;
+  return 64 * (size_t)es + v / 8 + (v - 64) * (size_t)es;
+}
 
 int check(const cz_params *p, Shape *sh)
 {
@@ -54,7 +71,7 @@ int check(const cz_params *p, Shape *sh)
   if (p->eps_mode != CZ_EPS_REL && p->eps_mode != CZ_EPS_ABS) return CZ_ERR_ARG;
   if (p->stage2 != 0 && p->stage2 != 1) return CZ_ERR_ARG;
   if (p->bound_mode != CZ_BOUND_PAPER && p->bound_mode != CZ_BOUND_STRICT) return CZ_ERR_ARG;
-  if (p->flags & ~(CZ_FLAG_FAST | CZ_FLAG_ZERO4 | CZ_FLAG_ZERO8)) return CZ_ERR_ARG;
+  if (p->flags & ~(CZ_FLAG_FAST | CZ_FLAG_ZERO4 | CZ_FLAG_ZERO8 | GROUP_FLAGS)) return CZ_ERR_ARG;
   // the fast build keeps the PSNR of the exact build within 0.01 dB only for
   // W3ai; W4 and W4li (extrapolating rows with weights up to 35/16) are
   // refused with it
@@ -62,6 +79,11 @@ int check(const cz_params *p, Shape *sh)
   const int zf = p->flags & (CZ_FLAG_ZERO4 | CZ_FLAG_ZERO8);
   if (zf == (CZ_FLAG_ZERO4 | CZ_FLAG_ZERO8)) return CZ_ERR_ARG;  // one zeroing width at most
   if (zf && p->bound_mode == CZ_BOUND_STRICT) return CZ_ERR_ARG;  // the strict bound excludes zeroing
+  // aggregate chunks group the input of stage 2, and a group's payload
+  // must fit the large group coder's buffer
+  const int G = group_of(p->flags);
+  if (G > 1 && (!p->stage2 || (size_t)G * pmax_bytes(B, p->dtype == CZ_F64 ? 8 : 4) > CZ_GROUP_MAX_BYTES))
+    return CZ_ERR_ARG;
   if (!(p->eps >= 0) || std::isinf(p->eps)) return CZ_ERR_ARG;
   if (std::isnan(p->range)) return CZ_ERR_ARG;
   if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0) return CZ_ERR_ARG;
@@ -75,7 +97,9 @@ int check(const cz_params *p, Shape *sh)
     sh->nblocks = (int)nb;
     sh->L = B == 8 ? 1 : (B == 16 ? 2 : (B == 32 ? 3 : 4));
     sh->es = p->dtype == CZ_F64 ? 8 : 4;
-    sh->data0 = (HEADER_BYTES + 8ull * (nb + 1) + 15) / 16 * 16;
+    sh->G = G;
+    sh->nchunks = (int)((nb + G - 1) / G);
+    sh->data0 = (HEADER_BYTES + 8ull * (sh->nchunks + 1) + 15) / 16 * 16;
   }
   return CZ_OK;
 }
@@ -196,14 +220,15 @@ double threshold_divisor(const cz_params *p)
 
 struct Lanes {
   cudaError_t (*compress)(int, const CUtensorMap *, const FwdArgs *, const S2Args *, const PlaceArgs *, int, int,
-                          int, const cudaEvent_t *, cudaStream_t);
+                          int, const GroupArgs *, const int *, const cudaEvent_t *, cudaStream_t);
   cudaError_t (*compress_batch)(int, const StageMaps<MAXF> *, const FwdArgs *, const S2Args *, const BatchOut *,
                                 const PlaceArgs *, int, int, int, int, int, int, cudaStream_t);
-  cudaError_t (*decompress)(int, const CUtensorMap *, const InvArgs *, const UnArgs *, int, int, int,
+  cudaError_t (*decompress)(int, const CUtensorMap *, const InvArgs *, const UnArgs *, int, const int *,
                             const cudaEvent_t *, cudaStream_t);
   cudaError_t (*dense)(int, int, const DenseArgs *, int, cudaStream_t);
   int (*occupancy)(int, int);
   int (*slot_bytes)();
+  int (*group_occupancy)(int, int);  // the group kernels (coder tiers 0-2, decoder tiers 0-2)
   int (*scratch_bytes)();  // global scratch per CTA (FP64 32^3 only)
   int (*alt_scratch_bytes)();  // per CTA of the batched slab stage kernel where the tuner may pick it
 };
@@ -212,7 +237,7 @@ struct Lanes {
   Lanes                                                                                                    \
   {                                                                                                        \
     czl_compress_##sfx, czl_compress_batch_##sfx, czl_decompress_##sfx, czl_dense_##sfx, czl_occupancy_##sfx, \
-        czl_slot_bytes_##sfx, czl_scratch_bytes_##sfx, czl_alt_scratch_bytes_##sfx                         \
+        czl_slot_bytes_##sfx, czl_group_occupancy_##sfx, czl_scratch_bytes_##sfx, czl_alt_scratch_bytes_##sfx \
   }
 
 Lanes lanes_for(const cz_params &p)
@@ -283,7 +308,41 @@ size_t table_bytes(const Shape &sh) { return (16ull * sh.nblocks + 255) / 256 * 
 struct WsLayout {
   size_t lb, table, big, staging, scratch, total, arena;
   int grid, grid2, grid3;
+  // aggregate chunks: group table, group slots and the large group coder's
+  // scratch (one buffer of hcap bytes per CTA); zero sizes without groups
+  size_t gtable, gstage, gscratch;
+  unsigned long long gslot;
+  int hcap;
+  int ggrid[3];  // grids of the three coder tiers
 };
+
+// aggregate chunks: bytes of the largest group payload (a multiple of 128)
+// and of a group slot, which holds the finished chunk: the nnz words, ntok,
+// and at most the payload plus one trailing token plus one token per 65535
+// literal words split off
+int group_hcap(const cz_params *p, const Shape &sh)
+{
+  const size_t h = (size_t)sh.G * pmax_bytes(p->block, sh.es);
+  return (int)((h + 127) / 128 * 128);
+}
+
+unsigned long long group_slot(const Shape &sh, int hcap)
+{
+  return (4ull * sh.G + 16ull + (unsigned long long)hcap + 4ull * ((unsigned long long)hcap / 262140ull + 1ull) +
+          15ull) / 16ull * 16ull;
+}
+
+// grid of a group kernel over `items` (which: coder tiers 0, 1, 2, decoder
+// tiers 3, 4, 5); the last tiers hold an hcap buffer in global scratch per
+// CTA, so they run one CTA per SM
+int group_grid(const cz_params *p, int which, int hcap, long long items)
+{
+  int occ = 1;
+  if (which != 2 && which != 5) occ = lanes_for(*p).group_occupancy(which, hcap);
+  const long long g = (long long)sm_count() * (occ > 0 ? occ : 1);
+  const long long n = items > 0 ? items : 1;
+  return (int)(g < n ? g : n);
+}
 
 size_t big_bytes(long long nblocks) { return (4ull * nblocks + 255) / 256 * 256; }
 
@@ -300,6 +359,14 @@ size_t scratch_need(const cz_params *p, const Shape &sh, int grid, int grid3)
   return per * (size_t)n;
 }
 
+// offset of the decoded blocks' slots in the decompress workspace, after
+// the header, the block table and the list of the large chunks (aggregate
+// chunks: two lists of groups, for the decoder tiers)
+size_t dec_slots_off(const Shape &dsh)
+{
+  return WS_HDR + table_bytes(dsh) + big_bytes((dsh.G > 1 ? 2ll : 1ll) * dsh.nblocks);
+}
+
 // workspace of decompress_impl for the decoded blocks dsh: header | block
 // table | list of the large chunks | one staging slot per decoded block
 // (stage 2 only) | scratch of the large stage-2 inverse kernel (FP64 32^3)
@@ -310,8 +377,12 @@ size_t dec_ws_need(const cz_params *p, const Shape &dsh, size_t *scratch_off)
     return WS_HDR;
   }
   const Lanes L = lanes_for(*p);
-  const size_t off = WS_HDR + table_bytes(dsh) + big_bytes(dsh.nblocks) + (size_t)dsh.nblocks * L.slot_bytes();
+  const size_t off = dec_slots_off(dsh) + (size_t)dsh.nblocks * L.slot_bytes();
   if (scratch_off) *scratch_off = off;
+  if (dsh.G > 1) {  // the last decoder tier's buffers
+    const int hcap = group_hcap(p, dsh);
+    return off + (size_t)hcap * (size_t)group_grid(p, 5, hcap, dsh.nblocks);
+  }
   const size_t per = (size_t)L.scratch_bytes();
   return off + (per ? per * (size_t)grid_for(p, dsh, 5) : 0);
 }
@@ -337,6 +408,23 @@ WsLayout ws_layout(const cz_params *p, const Shape &sh)
   w.arena = (((size_t)sh.nblocks + w.grid - 1) / w.grid) * (size_t)L.slot_bytes();
   w.scratch = w.staging + w.arena * (size_t)w.grid;
   w.total = w.scratch + scratch_need(p, sh, w.grid, w.grid3);
+  w.gtable = w.gstage = w.gscratch = 0;
+  w.gslot = 0;
+  w.hcap = 0;
+  w.ggrid[0] = w.ggrid[1] = w.ggrid[2] = 0;
+  if (sh.G > 1) {
+    w.hcap = group_hcap(p, sh);
+    w.gslot = group_slot(sh, w.hcap);
+    for (int t = 0; t < 3; ++t) w.ggrid[t] = group_grid(p, t, w.hcap, sh.nchunks);
+    w.gtable = (w.total + 255) / 256 * 256;
+    w.gstage = w.gtable + (16ull * sh.nchunks + 255) / 256 * 256;
+    w.gscratch = (w.gstage + (size_t)sh.nchunks * w.gslot + 255) / 256 * 256;
+    w.total = w.gscratch + (size_t)w.hcap * (size_t)w.ggrid[2];
+    // cz_workspace_size covers decompression too, whose large-group decoder
+    // may run more CTAs (one per block, up to one per SM)
+    const size_t dec = dec_ws_need(p, sh, nullptr);
+    w.total = w.total > dec ? w.total : dec;
+  }
   return w;
 }
 
@@ -727,6 +815,7 @@ int batch_check(int n, const cz_params *p, const void *const *d_fields, void *co
     Shape sh;
     const int r = check(&p[i], &sh);
     if (r != CZ_OK) return r;
+    if (sh.G > 1) return CZ_ERR_ARG;  // batched launches take no aggregate chunks
     if (!d_fields[i] || !d_outs[i] || ((uintptr_t)d_fields[i] % 16) || ((uintptr_t)d_outs[i] % 16))
       return CZ_ERR_ARG;
     if (out_caps[i] < sh.data0) return CZ_ERR_CAPACITY;
@@ -835,7 +924,7 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
   a.nbz = sh.nbz;
   a.nblocks = sh.nblocks;
   a.eps_mode = p->eps_mode;
-  a.stage2 = p->stage2;
+  a.stage2 = sh.G > 1 ? 0 : p->stage2;  // aggregate chunks: raw slots, the group coders do stage 2
   a.kind = p->kind;
   a.zbits = zero_bits(*p);
   a.dtype = p->dtype;
@@ -863,15 +952,37 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
   pa.ny = p->ny;
   pa.nz = p->nz;
   pa.nblocks = sh.nblocks;
+  pa.hdr_nblocks = sh.nblocks;
   pa.block = p->block;
   pa.levels = sh.L;
   pa.eps_mode = p->eps_mode;
   pa.stage2 = p->stage2;
   pa.kind = p->kind;
   pa.dtype = p->dtype;
+  GroupArgs ga{};
+  if (sh.G > 1) {
+    // the group coders read the block slots and table and fill the group
+    // slots and table, over which placement and copy then run
+    ga.staging = a.staging;
+    ga.table = a.table;
+    ga.gstage = wsb + wl.gstage;
+    ga.gtable = reinterpret_cast<unsigned long long *>(wsb + wl.gtable);
+    ga.ws = d_ws;
+    ga.biglist = a.biglist;
+    ga.scratch = wsb + wl.gscratch;
+    ga.gslot = wl.gslot;
+    ga.hcap = wl.hcap;
+    ga.nblocks = sh.nblocks;
+    ga.ngroups = sh.nchunks;
+    ga.G = sh.G;
+    pa.staging = ga.gstage;
+    pa.table = ga.gtable;
+    pa.nblocks = sh.nchunks;
+  }
   CUtensorMap tm;
   if (!make_tile_map(&tm, p, d_field)) return CZ_ERR_CUDA;
-  return L.compress(p->kind, &tm, &a, &sa, &pa, wl.grid, wl.grid2, wl.grid3, marks, s) == cudaSuccess
+  return L.compress(p->kind, &tm, &a, &sa, &pa, wl.grid, wl.grid2, wl.grid3, sh.G > 1 ? &ga : nullptr, wl.ggrid,
+                    marks, s) == cudaSuccess
              ? CZ_OK
              : CZ_ERR_CUDA;
 }
@@ -888,7 +999,7 @@ int cz_batch_workspace_size(int n, const cz_params *p, size_t *bytes)
 {
   if (n < 0 || !bytes || (n > 0 && !p)) return CZ_ERR_ARG;
   for (int i = 0; i < n; ++i)
-    if (check(&p[i], nullptr) != CZ_OK) return CZ_ERR_ARG;
+    if (check(&p[i], nullptr) != CZ_OK || group_of(p[i].flags) > 1) return CZ_ERR_ARG;
   *bytes = batch_ws_need(n, p, true);  // room for every knob setting the tuner may pick
   return CZ_OK;
 }
@@ -979,7 +1090,7 @@ int aos_check(int n, const cz_params *p)
 {
   if (n < 1 || n > MAXF || !p) return CZ_ERR_ARG;
   for (int i = 0; i < n; ++i) {
-    if (check(&p[i], nullptr) != CZ_OK) return CZ_ERR_ARG;
+    if (check(&p[i], nullptr) != CZ_OK || group_of(p[i].flags) > 1) return CZ_ERR_ARG;
     if (p[i].nx != p[0].nx || p[i].ny != p[0].ny || p[i].nz != p[0].nz || p[i].dtype != p[0].dtype)
       return CZ_ERR_ARG;
   }
@@ -1146,7 +1257,7 @@ int cz_stream_concat(int n, const void *const *h_streams, const size_t *sizes, v
   if (n < 1 || !h_streams || !sizes || !out_bytes) return CZ_ERR_ARG;
   cz_params p0{}, pr{};
   double t0 = 0, tr = 0;
-  unsigned long long nz = 0, nblocks = 0, data = 0;
+  unsigned long long nz = 0, nblocks = 0, nchunks = 0, data = 0;
   double mn = 0, mx = 0;
   for (int r = 0; r < n; ++r) {
     if (!h_streams[r]) return CZ_ERR_ARG;
@@ -1179,12 +1290,16 @@ int cz_stream_concat(int n, const void *const *h_streams, const size_t *sizes, v
       if (std::isnan(mn) || (!std::isnan(a) && a < mn)) mn = a;
       if (std::isnan(mx) || (!std::isnan(b) && b > mx)) mx = b;
     }
+    // aggregate chunks: a slab's last group must be full unless it is the
+    // last slab (the joined stream's groups are the slabs' groups)
+    if (sh.G > 1 && r + 1 < n && sh.nblocks % sh.G) return CZ_ERR_ARG;
     nz += (unsigned long long)q.nz;
     nblocks += (unsigned long long)sh.nblocks;
+    nchunks += (unsigned long long)sh.nchunks;
     data += db;
   }
   if (nz > 0x7FFFFFFFull || nblocks > (1ull << 30)) return CZ_ERR_ARG;
-  const unsigned long long data0 = (HEADER_BYTES + 8ull * (nblocks + 1) + 15) / 16 * 16, total = data0 + data;
+  const unsigned long long data0 = (HEADER_BYTES + 8ull * (nchunks + 1) + 15) / 16 * 16, total = data0 + data;
   *out_bytes = (size_t)total;
   if (!h_out) return CZ_OK;  // size query
   if (out_cap < total) return CZ_ERR_CAPACITY;
@@ -1201,7 +1316,7 @@ int cz_stream_concat(int n, const void *const *h_streams, const size_t *sizes, v
   std::memcpy(o + 80, &total, 8);
   // offsets rebased by the data bytes of the slabs before (the exclusive
   // scan of per-rank sizes), chunks appended in rank order
-  unsigned long long base = 0, blk = 0;
+  unsigned long long base = 0, chk = 0;
   for (int r = 0; r < n; ++r) {
     const unsigned char *h = reinterpret_cast<const unsigned char *>(h_streams[r]);
     cz_params q;
@@ -1210,15 +1325,15 @@ int cz_stream_concat(int n, const void *const *h_streams, const size_t *sizes, v
     Shape sh;
     check(&q, &sh);
     const unsigned long long db = rd64(h + 72);
-    for (int b = 0; b < sh.nblocks; ++b) {
+    for (int b = 0; b < sh.nchunks; ++b) {
       const unsigned long long off = rd64(h + HEADER_BYTES + 8ull * b) + base;
-      std::memcpy(o + HEADER_BYTES + 8ull * (blk + b), &off, 8);
+      std::memcpy(o + HEADER_BYTES + 8ull * (chk + b), &off, 8);
     }
     std::memcpy(o + data0 + base, h + sh.data0, (size_t)db);
     base += db;
-    blk += (unsigned long long)sh.nblocks;
+    chk += (unsigned long long)sh.nchunks;
   }
-  std::memcpy(o + HEADER_BYTES + 8ull * nblocks, &base, 8);
+  std::memcpy(o + HEADER_BYTES + 8ull * nchunks, &base, 8);
   return CZ_OK;
 }
 
@@ -1357,7 +1472,7 @@ int cz_read_header(const void *h_in, size_t n, cz_params *p, double *t_used)
   q.stage2 = h[23];
   q.eps_mode = h[24];
   q.bound_mode = h[26];
-  q.flags = h[27] & (CZ_FLAG_FAST | CZ_FLAG_ZERO4 | CZ_FLAG_ZERO8);
+  q.flags = h[27] & (CZ_FLAG_FAST | CZ_FLAG_ZERO4 | CZ_FLAG_ZERO8 | GROUP_FLAGS);
   std::memcpy(&q.eps, h + 32, 8);
   std::memcpy(&q.range, h + 64, 8);
   if (std::isnan(q.range)) return CZ_ERR_CORRUPT;
@@ -1441,11 +1556,11 @@ int decompress_impl(const void *d_in, size_t in_bytes, const void *h_header, con
   a.ids = ids;
   a.nchunks = nchunks;
   a.table = reinterpret_cast<const unsigned long long *>(wsb + WS_HDR);
-  a.staging = wsb + WS_HDR + table_bytes(dsh) + big_bytes(dsh.nblocks);
+  a.staging = wsb + dec_slots_off(dsh);
   a.slot = slot;
   UnArgs ua{};
   ua.in = a.in;
-  ua.staging = wsb + WS_HDR + table_bytes(dsh) + big_bytes(dsh.nblocks);
+  ua.staging = wsb + dec_slots_off(dsh);
   ua.ws = d_ws;
   ua.biglist = reinterpret_cast<int *>(wsb + WS_HDR + table_bytes(dsh));
   ua.scratch = wsb + scr;
@@ -1456,11 +1571,25 @@ int decompress_impl(const void *d_in, size_t in_bytes, const void *h_header, con
   ua.data0 = sh.data0;
   ua.slot = slot;
   ua.nblocks = dsh.nblocks;
+  ua.group = sh.G;
+  int ugrid[3];
+  if (sh.G > 1) {
+    // the group decoder tiers: one item per group (whole field) or per
+    // requested block
+    ua.hcap = group_hcap(&p, sh);
+    const long long items = ids ? n : sh.nchunks;
+    ugrid[0] = group_grid(&p, 3, ua.hcap, items);
+    ugrid[1] = group_grid(&p, 4, ua.hcap, items);
+    ugrid[2] = group_grid(&p, 5, ua.hcap, dsh.nblocks);  // as dec_ws_need sized the scratch
+  } else {
+    ugrid[0] = grid_for(&p, dsh, 4);
+    ugrid[1] = grid_for(&p, dsh, 5);
+    ugrid[2] = 0;
+  }
   a.decoder = decoder_of(p);
   CUtensorMap om;
   if (!make_tile_map(&om, &q, d_out, a.decoder == 1)) return CZ_ERR_CUDA;
-  return L.decompress(p.kind, &om, &a, &ua, grid_for(&p, dsh, 1), grid_for(&p, dsh, 4), grid_for(&p, dsh, 5), marks,
-                      s) == cudaSuccess
+  return L.decompress(p.kind, &om, &a, &ua, grid_for(&p, dsh, 1), ugrid, marks, s) == cudaSuccess
              ? CZ_OK
              : CZ_ERR_CUDA;
 }

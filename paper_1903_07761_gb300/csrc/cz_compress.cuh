@@ -45,8 +45,23 @@ struct PlaceArgs {
   void *ws;
   unsigned long long out_cap, data0;
   double eps, range, cnorm;
-  int nx, ny, nz, nblocks;
+  int nx, ny, nz, nblocks;  // nblocks: chunks (table entries)
+  int hdr_nblocks;          // blocks of the field, for the header
   int block, levels, eps_mode, stage2, kind, dtype, bound_mode, flags;
+};
+
+// aggregate chunks (cz_group.cuh): the group coders' arguments
+struct GroupArgs {
+  const unsigned char *staging;       // block slots of the stage kernel: [nnz | 0 | payload]
+  const unsigned long long *table;    // per block: slot offset, 8 + payload bytes (TB_LOST: lost)
+  unsigned char *gstage;              // group slots, gslot bytes apart
+  unsigned long long *gtable;         // per group: slot offset, chunk bytes | TB_FIN (TB_LOST: lost)
+  void *ws;                           // header: status, count of the large groups (nbig)
+  int *biglist;                       // ids of the large groups
+  unsigned char *scratch;             // large groups: one shuffled buffer of hcap bytes per CTA
+  unsigned long long gslot;
+  int hcap;                           // bytes of the largest group payload (a multiple of 128)
+  int nblocks, ngroups, G;
 };
 
 constexpr int PLACE_TILE = 128;  // chunks (and threads) per k_place CTA
@@ -58,27 +73,16 @@ constexpr unsigned long long TB_LOST = 0xFFFFFFFFFFFFFFFFull;
 constexpr unsigned long long TB_FIN = 1ull << 62;
 __device__ __forceinline__ unsigned long long tb_size(unsigned long long cb) { return cb & ~TB_FIN; }
 
-// ---- stage 2 of one slot, in place: [nnz | 0 | raw payload of pbytes]
-// becomes [nnz | ntok | tokens | literal words].  The payload is scattered
-// into byte-shuffled order (byte b of element e at b * E + e; element sizes
-// are powers of two, so no division) in SH, the zero-word runs are found
-// from a ballot bitmap with one scan, and the tokens and literals replace
-// the slot's contents.  Run by the NT threads OFF .. OFF + NT - 1 of a group
-// that synchronises with barrier BAR (0: the whole CTA); AUX holds four
-// bitmap arrays of `cap` words; s_u (>= 40 words) and s_i (>= 40) are the
-// group's scan scratch.  Five barriers per payload.  Returns the chunk
-// bytes (the same in every thread).
-template <typename T, int NT, int BAR = 0, int OFF = 0>
-__device__ __forceinline__ unsigned stage2_chunk(unsigned *ch, int pbytes, unsigned char *SH, unsigned *AUX, int cap,
-                                                 unsigned *s_u, int *s_i)
+// ---- byte shuffle of payload words into SH: word k of raw (W words) holds
+// bytes 0..3 of element e0 + 4k / ES at byte offset 4k % ES, and byte b of
+// element e goes to b * E + e (element sizes are powers of two, so no
+// division).  A payload that is one piece of a longer buffer (an aggregate
+// chunk) passes its first element e0 and the buffer's element count E.
+template <typename T, int NT, int OFF = 0>
+__device__ __forceinline__ void shuffle_words(const unsigned *raw, int W, int e0, int E, unsigned char *SH)
 {
-  constexpr int NWP = NT / 32, ES = (int)sizeof(T), LGES = ES == 8 ? 3 : 2;
-  const int tid = (int)threadIdx.x - OFF, lane = threadIdx.x & 31, wid = tid >> 5;
-  const unsigned *SH32 = reinterpret_cast<const unsigned *>(SH);
-  const int E = pbytes >> LGES, W = pbytes >> 2, NB = (W + 31) >> 5;
-  unsigned *ZBM = AUX, *CM = AUX + cap, *EB = AUX + 2 * cap, *PRE = AUX + 3 * cap;
-  // payload word k holds bytes 0..3 of element 4k / ES at byte offset 4k % ES
-  const unsigned *raw = ch + 2;
+  constexpr int ES = (int)sizeof(T), LGES = ES == 8 ? 3 : 2;
+  const int tid = (int)threadIdx.x - OFF;
   for (int k0 = tid; k0 < W; k0 += 4 * NT) {
     unsigned wv[4];
 #pragma unroll
@@ -87,13 +91,32 @@ __device__ __forceinline__ unsigned stage2_chunk(unsigned *ch, int pbytes, unsig
     for (int j = 0; j < 4; ++j) {
       const int k = k0 + j * NT;
       if (k < W) {
-        const int e = (4 * k) >> LGES, b0 = (4 * k) & (ES - 1);
+        const int e = e0 + ((4 * k) >> LGES), b0 = (4 * k) & (ES - 1);
 #pragma unroll
         for (int q = 0; q < 4; ++q) SH[(b0 + q) * E + e] = (unsigned char)(wv[j] >> (8 * q));
       }
     }
   }
-  group_sync<BAR, NT>();  // the slot's payload is no longer needed
+}
+
+// ---- zero-run code of a shuffled payload of pbytes (< 256 KiB: the run
+// and word counts are packed in 16-bit halves) in SH: the zero-word runs
+// are found from a ballot bitmap with one scan, and [ntok | tokens |
+// literal words] are written from ch + 1 on (ch[0] is left alone).  Run by
+// the NT threads OFF .. OFF + NT - 1 of a group that synchronises with
+// barrier BAR (0: the whole CTA); AUX holds four bitmap arrays of `cap`
+// words; s_u (>= 40 words) and s_i (>= 40) are the group's scan scratch.
+// Four barriers.  Returns 8 + the bytes of tokens and literals (the same
+// in every thread).
+template <typename T, int NT, int BAR = 0, int OFF = 0>
+__device__ __forceinline__ unsigned stage2_code(unsigned *ch, int pbytes, const unsigned char *SH, unsigned *AUX,
+                                                int cap, unsigned *s_u, int *s_i)
+{
+  constexpr int NWP = NT / 32;
+  const int tid = (int)threadIdx.x - OFF, lane = threadIdx.x & 31, wid = tid >> 5;
+  const unsigned *SH32 = reinterpret_cast<const unsigned *>(SH);
+  const int W = pbytes >> 2, NB = (W + 31) >> 5;
+  unsigned *ZBM = AUX, *CM = AUX + cap, *EB = AUX + 2 * cap, *PRE = AUX + 3 * cap;
   for (int g = wid; g < NB; g += NWP) {
     const int w = g * 32 + lane;
     const unsigned bal = __ballot_sync(FULL, w < W && SH32[w] == 0u);
@@ -196,6 +219,19 @@ __device__ __forceinline__ unsigned stage2_chunk(unsigned *ch, int pbytes, unsig
   }
   group_sync<BAR, NT>();
   return 8u + 4u * ntok + 4u * nlit;
+}
+
+// ---- stage 2 of one slot, in place: [nnz | 0 | raw payload of pbytes]
+// becomes [nnz | ntok | tokens | literal words] (shuffle into SH, then the
+// zero-run code; five barriers).  Returns the chunk bytes.
+template <typename T, int NT, int BAR = 0, int OFF = 0>
+__device__ __forceinline__ unsigned stage2_chunk(unsigned *ch, int pbytes, unsigned char *SH, unsigned *AUX, int cap,
+                                                 unsigned *s_u, int *s_i)
+{
+  constexpr int LGES = sizeof(T) == 8 ? 3 : 2;
+  shuffle_words<T, NT, OFF>(ch + 2, pbytes >> 2, 0, pbytes >> LGES, SH);
+  group_sync<BAR, NT>();  // the slot's payload is no longer needed
+  return stage2_code<T, NT, BAR, OFF>(ch, pbytes, SH, AUX, cap, s_u, s_i);
 }
 
 // field of global block bid among the nf fields of a batched launch
@@ -506,7 +542,7 @@ __global__ void __launch_bounds__(PLACE_TILE) k_place(const PlaceArgs a)
     h[25] = (unsigned char)a.levels;
     h[26] = (unsigned char)a.bound_mode;
     h[27] = (unsigned char)a.flags;
-    st_le<unsigned>(h + 28, (unsigned)a.nblocks);
+    st_le<unsigned>(h + 28, (unsigned)a.hdr_nblocks);
     st_le_f64(h + 32, a.eps);
     st_le_f64(h + 40, (double)t);
     st_le_f64(h + 48, mn);

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "cz_compress.cuh"
+#include "cz_group.cuh"
 #include "cz_half.cuh"
 #include "cz_launch.h"
 #include "cz_pair.cuh"
@@ -77,9 +78,30 @@ cudaError_t stage2_k(const S2Args &sa, int stage2, int grid2, int grid3, cudaStr
   return e;
 }
 
+// aggregate chunks: the three tiers of the group coder over the raw slots
+// (ggrid: their grids)
+template <int = 0>
+cudaError_t group_k(const GroupArgs &ga, const int *ggrid, cudaStream_t s)
+{
+  if (ga.hcap <= 0 || ga.hcap > GROUP_MAX_BYTES || ga.hcap % 128) return cudaErrorInvalidValue;
+  cudaError_t e = prepare<k_group2<CZ_T, CZ_B, 0>>(GT<0>::SMEM);
+  if (e != cudaSuccess) return e;
+  k_group2<CZ_T, CZ_B, 0><<<ggrid[0], GT<0>::NT, GT<0>::SMEM, s>>>(ga);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = prepare<k_group2<CZ_T, CZ_B, 1>>(GT<1>::SMEM)) != cudaSuccess) return e;
+  k_group2<CZ_T, CZ_B, 1><<<ggrid[1], GT<1>::NT, GT<1>::SMEM, s>>>(ga);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = prepare<k_group_huge<CZ_T, CZ_B>>(GROUP_HSMEM)) != cudaSuccess) return e;
+  k_group_huge<CZ_T, CZ_B><<<ggrid[2], 512, ga.hcap / 8, s>>>(ga);  // four bitmap arrays of hcap / 128 words
+  return cudaGetLastError();
+}
+
+// ga: aggregate chunks (the stage kernel then writes raw slots, the group
+// coders replace stage 2, and pa describes the group table); else null
 template <int KIND>
 cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const S2Args &sa, const PlaceArgs &pa, int grid,
-                       int grid2, int grid3, const cudaEvent_t *marks, cudaStream_t s)
+                       int grid2, int grid3, const GroupArgs *ga, const int *ggrid, const cudaEvent_t *marks,
+                       cudaStream_t s)
 {
   cudaError_t e;
   StageMaps<1> maps{};
@@ -98,7 +120,11 @@ cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const S2Args &sa
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (marks && (e = cudaEventRecord(marks[1], s)) != cudaSuccess) return e;
-  if ((e = stage2_k(sa, pa.stage2, grid2, grid3, s)) != cudaSuccess) return e;
+  if (ga)
+    e = group_k(*ga, ggrid, s);
+  else
+    e = stage2_k(sa, pa.stage2, grid2, grid3, s);
+  if (e != cudaSuccess) return e;
   if (marks && (e = cudaEventRecord(marks[2], s)) != cudaSuccess) return e;
   const int tiles = (pa.nblocks + PLACE_TILE - 1) / PLACE_TILE;
   k_place<CZ_T><<<tiles, PLACE_TILE, 0, s>>>(pa);
@@ -152,11 +178,23 @@ cudaError_t compress_batch_k(const StageMaps<MAXF> &maps, const FwdArgs &a, cons
 
 // marks (optional): marks[0] is recorded right before the decode kernel
 template <int KIND>
-cudaError_t decompress_k(const CUtensorMap &om, const InvArgs &a, const UnArgs &ua, int grid, int gridu, int gridub,
+cudaError_t decompress_k(const CUtensorMap &om, const InvArgs &a, const UnArgs &ua, int grid, const int *ugrid,
                          const cudaEvent_t *marks, cudaStream_t s)
 {
+  const int gridu = ugrid[0], gridub = ugrid[1];
   cudaError_t e;
-  if (a.stage2) {
+  if (a.stage2 && ua.group > 1) {
+    // aggregate chunks: the three tiers of the group decoder
+    e = prepare<k_gunstage<CZ_T, CZ_B, 0>>(GT<0>::USMEM);
+    if (e != cudaSuccess) return e;
+    k_gunstage<CZ_T, CZ_B, 0><<<ugrid[0], GT<0>::NT, GT<0>::USMEM, s>>>(ua);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = prepare<k_gunstage<CZ_T, CZ_B, 1>>(GT<1>::USMEM)) != cudaSuccess) return e;
+    k_gunstage<CZ_T, CZ_B, 1><<<ugrid[1], GT<1>::NT, GT<1>::USMEM, s>>>(ua);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_gunstage<CZ_T, CZ_B, 2><<<ugrid[2], GT<2>::NT, GT<2>::USMEM, s>>>(ua);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if (a.stage2) {
     e = prepare<k_unstage<CZ_T, CZ_B, false>>(G::SMEM_U);
     if (e != cudaSuccess) return e;
     k_unstage<CZ_T, CZ_B, false><<<gridu, 128, G::SMEM_U, s>>>(ua);
@@ -265,6 +303,30 @@ int occupancy_u()
   return n;
 }
 
+// group kernels (which): coder tiers 0, 1, 2 (0, 1, 2), decoder tiers 0,
+// 1, 2 (3, 4, 5); hcap bytes of the largest group payload
+template <auto KERN>
+int occ_of(int nt, int smem, bool raise)
+{
+  int n = 0;
+  if (raise && prepare<KERN>(smem) != cudaSuccess) return 0;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, KERN, nt, smem) == cudaSuccess ? n : 0;
+}
+
+int occupancy_g(int which, int hcap)
+{
+  switch (which) {
+    case 0: return occ_of<k_group2<CZ_T, CZ_B, 0>>(GT<0>::NT, GT<0>::SMEM, true);
+    case 1: return occ_of<k_group2<CZ_T, CZ_B, 1>>(GT<1>::NT, GT<1>::SMEM, true);
+    case 2:
+      if (prepare<k_group_huge<CZ_T, CZ_B>>(GROUP_HSMEM) != cudaSuccess) return 0;
+      return occ_of<k_group_huge<CZ_T, CZ_B>>(512, hcap / 8, false);
+    case 3: return occ_of<k_gunstage<CZ_T, CZ_B, 0>>(GT<0>::NT, GT<0>::USMEM, true);
+    case 4: return occ_of<k_gunstage<CZ_T, CZ_B, 1>>(GT<1>::NT, GT<1>::USMEM, true);
+    default: return occ_of<k_gunstage<CZ_T, CZ_B, 2>>(GT<2>::NT, GT<2>::USMEM, false);
+  }
+}
+
 template <int KIND>
 int occupancy_slab_alt()
 {
@@ -327,17 +389,17 @@ int occupancy_d()
 
 extern "C" cudaError_t CZ_CAT(czl_compress_, CZ_SUFFIX)(int kind, const CUtensorMap *tm, const FwdArgs *a,
                                                          const S2Args *sa, const PlaceArgs *pa, int grid,
-                                                         int grid2, int grid3, const cudaEvent_t *marks,
-                                                         cudaStream_t s)
+                                                         int grid2, int grid3, const GroupArgs *ga,
+                                                         const int *ggrid, const cudaEvent_t *marks, cudaStream_t s)
 {
 #ifdef CZ_FAST
   if (kind != W3AI) return cudaErrorInvalidValue;
-  return compress_k<W3AI>(*tm, *a, *sa, *pa, grid, grid2, grid3, marks, s);
+  return compress_k<W3AI>(*tm, *a, *sa, *pa, grid, grid2, grid3, ga, ggrid, marks, s);
 #else
   switch (kind) {
-    case W4: return compress_k<W4>(*tm, *a, *sa, *pa, grid, grid2, grid3, marks, s);
-    case W4LI: return compress_k<W4LI>(*tm, *a, *sa, *pa, grid, grid2, grid3, marks, s);
-    default: return compress_k<W3AI>(*tm, *a, *sa, *pa, grid, grid2, grid3, marks, s);
+    case W4: return compress_k<W4>(*tm, *a, *sa, *pa, grid, grid2, grid3, ga, ggrid, marks, s);
+    case W4LI: return compress_k<W4LI>(*tm, *a, *sa, *pa, grid, grid2, grid3, ga, ggrid, marks, s);
+    default: return compress_k<W3AI>(*tm, *a, *sa, *pa, grid, grid2, grid3, ga, ggrid, marks, s);
   }
 #endif
 }
@@ -361,17 +423,17 @@ extern "C" cudaError_t CZ_CAT(czl_compress_batch_, CZ_SUFFIX)(int kind, const St
 }
 
 extern "C" cudaError_t CZ_CAT(czl_decompress_, CZ_SUFFIX)(int kind, const CUtensorMap *om, const InvArgs *a,
-                                                           const UnArgs *ua, int grid, int gridu, int gridub,
+                                                           const UnArgs *ua, int grid, const int *ugrid,
                                                            const cudaEvent_t *marks, cudaStream_t s)
 {
 #ifdef CZ_FAST
   if (kind != W3AI) return cudaErrorInvalidValue;
-  return decompress_k<W3AI>(*om, *a, *ua, grid, gridu, gridub, marks, s);
+  return decompress_k<W3AI>(*om, *a, *ua, grid, ugrid, marks, s);
 #else
   switch (kind) {
-    case W4: return decompress_k<W4>(*om, *a, *ua, grid, gridu, gridub, marks, s);
-    case W4LI: return decompress_k<W4LI>(*om, *a, *ua, grid, gridu, gridub, marks, s);
-    default: return decompress_k<W3AI>(*om, *a, *ua, grid, gridu, gridub, marks, s);
+    case W4: return decompress_k<W4>(*om, *a, *ua, grid, ugrid, marks, s);
+    case W4LI: return decompress_k<W4LI>(*om, *a, *ua, grid, ugrid, marks, s);
+    default: return decompress_k<W3AI>(*om, *a, *ua, grid, ugrid, marks, s);
   }
 #endif
 }
@@ -464,6 +526,13 @@ static int occupancy_query(int kind, int which)
 
 // bytes of the staging slot of the largest payload
 extern "C" int CZ_CAT(czl_slot_bytes_, CZ_SUFFIX)() { return G::PSLOT; }
+
+// CTAs per SM of a group kernel (see occupancy_g; 0 on error)
+extern "C" int CZ_CAT(czl_group_occupancy_, CZ_SUFFIX)(int which, int hcap)
+{
+  if (which < 0 || which > 5 || hcap <= 0 || hcap > GROUP_MAX_BYTES || hcap % 128) return 0;
+  return occupancy_g(which, hcap);
+}
 
 // global scratch per CTA of the stage kernel, the large stage-2 kernel and
 // the large stage-2 inverse kernel (FP64 32^3 only; 0 otherwise)

@@ -49,7 +49,7 @@ struct WsHdr {
   unsigned status;
   unsigned ticket;
   unsigned nbig;  // blocks whose payload exceeds the small stage-2 CTAs' capacity
-  unsigned pad1;
+  unsigned nbig2;  // aggregate chunks: groups beyond the second coder (or decoder) tier
   unsigned long long minkey, maxkey;
   unsigned long long out_bytes;
   unsigned long long bump;  // staging bytes handed out so far
@@ -129,6 +129,8 @@ struct UnArgs {
   int nchunks;                // blocks in the stream
   unsigned long long in_bytes, data0, slot;
   int nblocks;
+  int group;                  // blocks per aggregate chunk (1: one chunk per block)
+  int hcap;                   // aggregate chunks: scratch bytes per CTA of the large launch
 };
 
 struct DenseArgs {
@@ -1475,6 +1477,54 @@ __device__ __forceinline__ void threshold_of(double eps, int eps_mode, double cn
 }
 
 // ============================================================ decompress
+// ---- stage-2 inverse of one chunk's tokens, by all NT threads of the CTA:
+// block scans of (literal words, output words) per round of NT tokens place
+// every token; a warp per token copies its literals and writes its zero run
+// into the W words of the shuffled payload at SH32.  TL, TO, TK are NT
+// words each of shared memory, s_u64 NT / 32 words.  Returns false (in
+// some thread) when a token would read past the nlit_avail literal words or
+// write past the payload, or the tokens do not fill it exactly; such
+// tokens write nothing.
+template <int NT>
+__device__ __forceinline__ bool untoken(const unsigned *tok, unsigned ntok, const unsigned *lit,
+                                        unsigned long long nlit_avail, unsigned *SH32, unsigned W, unsigned *TL,
+                                        unsigned *TO, unsigned *TK, unsigned long long *s_u64)
+{
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  unsigned lit_carry = 0, out_carry = 0;
+  bool bad = false;
+  for (unsigned r0 = 0; r0 < ntok; r0 += NT) {
+    const unsigned k = r0 + tid;
+    const unsigned tk = k < ntok ? __ldg(tok + k) : 0u;
+    const unsigned nl = tk & 0xFFFFu, run = nl + (tk >> 16);
+    // both prefixes in one scan (one barrier): literal words in the low
+    // half, output words in the high half (each sum stays below 2^32)
+    unsigned long long tot2;
+    const unsigned long long ex2 =
+        block_exsum_nb<NT>((unsigned long long)nl | ((unsigned long long)run << 32), s_u64, tot2);
+    const unsigned lp = (unsigned)ex2, op = (unsigned)(ex2 >> 32);
+    const unsigned tl = (unsigned)tot2, to_ = (unsigned)(tot2 >> 32);
+    TL[tid] = lit_carry + lp;
+    TO[tid] = out_carry + op;
+    TK[tid] = tk;
+    __syncthreads();
+    const unsigned cnt = (ntok - r0) < (unsigned)NT ? (ntok - r0) : (unsigned)NT;
+    for (unsigned i = wid; i < cnt; i += NT / 32) {
+      const unsigned t = TK[i], l0 = TL[i], o0 = TO[i], n = t & 0xFFFFu, z = t >> 16;
+      if ((unsigned long long)l0 + n > nlit_avail || (unsigned long long)o0 + n + z > (unsigned long long)W) {
+        bad = true;
+        continue;
+      }
+      for (unsigned q = lane; q < n; q += 32) SH32[o0 + q] = __ldg(lit + l0 + q);
+      for (unsigned q = lane; q < z; q += 32) SH32[o0 + n + q] = 0u;
+    }
+    lit_carry += tl;
+    out_carry += to_;
+    __syncthreads();
+  }
+  return !(bad || out_carry != W || (unsigned long long)lit_carry > nlit_avail);
+}
+
 // ---- stage-2 inverse, one chunk at a time: block scans of (literal
 // words, output words) per token place every token; a warp per token copies
 // its literals and writes its zero run into the shuffled payload in shared
@@ -1498,7 +1548,7 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_unstage(const UnArgs a)
   __shared__ unsigned long long s_u64[NT / 32];
   __shared__ unsigned s_nnz, s_ntok, s_bad;
   __shared__ unsigned long long s_off, s_len;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x;
 
   WsHdr *wsh = reinterpret_cast<WsHdr *>(a.ws);
   // the small launch visits every chunk and lists the large ones, which the
@@ -1548,42 +1598,8 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_unstage(const UnArgs a)
       const unsigned *c32 = reinterpret_cast<const unsigned *>(a.in + a.data0 + s_off);
       const unsigned *tok = c32 + 2;
       const unsigned *lit = tok + ntok;
-      unsigned *SH32 = reinterpret_cast<unsigned *>(P);  // the shuffled payload
-      unsigned lit_carry = 0, out_carry = 0;
-      bool bad = false;
-      for (unsigned r0 = 0; r0 < ntok; r0 += NT) {
-        const unsigned k = r0 + tid;
-        const unsigned tk = k < ntok ? __ldg(tok + k) : 0u;
-        const unsigned nl = tk & 0xFFFFu, run = nl + (tk >> 16);
-        // both prefixes in one scan (one barrier): literal words in the low
-        // half, output words in the high half (each sum stays below 2^32)
-        unsigned long long tot2;
-        const unsigned long long ex2 =
-            block_exsum_nb<NT>((unsigned long long)nl | ((unsigned long long)run << 32), s_u64, tot2);
-        const unsigned lp = (unsigned)ex2, op = (unsigned)(ex2 >> 32);
-        const unsigned tl = (unsigned)tot2, to_ = (unsigned)(tot2 >> 32);
-        TL[tid] = lit_carry + lp;
-        TO[tid] = out_carry + op;
-        TK[tid] = tk;
-        __syncthreads();
-        // one warp per token: its literal words (coalesced), then its zero
-        // run; tokens that would read past the literals or write past the
-        // payload mark the chunk bad and write nothing
-        const unsigned cnt = (ntok - r0) < (unsigned)NT ? (ntok - r0) : (unsigned)NT;
-        for (unsigned i = wid; i < cnt; i += NT / 32) {
-          const unsigned t = TK[i], l0 = TL[i], o0 = TO[i], n = t & 0xFFFFu, z = t >> 16;
-          if ((unsigned long long)l0 + n > nlit_avail || (unsigned long long)o0 + n + z > (unsigned long long)W) {
-            bad = true;
-            continue;
-          }
-          for (unsigned q = lane; q < n; q += 32) SH32[o0 + q] = __ldg(lit + l0 + q);
-          for (unsigned q = lane; q < z; q += 32) SH32[o0 + n + q] = 0u;
-        }
-        lit_carry += tl;
-        out_carry += to_;
-        __syncthreads();
-      }
-      if (bad || out_carry != (unsigned)W || (unsigned long long)lit_carry > nlit_avail) atomicOr(&s_bad, 1u);
+      if (!untoken<NT>(tok, ntok, lit, nlit_avail, reinterpret_cast<unsigned *>(P), (unsigned)W, TL, TO, TK, s_u64))
+        atomicOr(&s_bad, 1u);
       __syncthreads();
       if (!s_bad) {
         // unshuffle straight into the slot: byte q of raw word k is byte

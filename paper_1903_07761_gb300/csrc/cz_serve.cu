@@ -148,6 +148,8 @@ class Server {
     q.r = *r;
     if (r->op == CZ_OP_COMPRESS) {
       q.p = r->params;
+      // compressions run as batched launches, which take no aggregate chunks
+      if (q.p.flags & (CZ_FLAG_GROUP4 | CZ_FLAG_GROUP8 | CZ_FLAG_GROUP16)) return CZ_ERR_ARG;
     } else if (r->op == CZ_OP_DECOMPRESS) {
       double t;
       const int e = cz_read_header(r->h_header, CZ_HEADER_BYTES, &q.p, &t);

@@ -546,21 +546,145 @@ __device__ __forceinline__ void put_pair(unsigned *tok, unsigned k, unsigned lit
   tok[k] = lit | (zr << 16);
 }
 
+// ---- zero-run code of a shuffled payload of pbytes (any size) in global
+// memory SH, by all NT = 512 threads of the CTA: [ntok | tokens | literal
+// words] are written from ch + 1 on (ch[0] is left alone).  The four bitmap
+// arrays of `cap` words (ZBM, CM, EB, PRC) live in shared memory at BM;
+// s_u / s_i (>= 40 words) are scan scratch and *s_lastend an int that is 0
+// on entry (and again on return).  Returns 8 + the bytes of tokens and
+// literals (the same in every thread).
+template <int NT>
+__device__ __forceinline__ unsigned long long huge_code(unsigned *ch, int pbytes, const unsigned char *SH,
+                                                        unsigned *BM, int cap, unsigned *s_u, int *s_i,
+                                                        int *s_lastend)
+{
+  constexpr int NWP = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const unsigned *SH32 = reinterpret_cast<const unsigned *>(SH);
+  unsigned *ZBM = BM, *CM = ZBM + cap, *EB = ZBM + 2 * cap, *PRC = ZBM + 3 * cap;  // PRC: coded words before
+  const int W = pbytes >> 2, NB = (W + 31) >> 5;
+  for (int g = wid; g < NB; g += NWP) {
+    const int w = g * 32 + lane;
+    const unsigned bal = __ballot_sync(FULL, w < W && SH32[w] == 0u);
+    if (lane == 0) ZBM[g] = bal;
+  }
+  __syncthreads();
+  // coded words C: zero words with a zero neighbour; a run starts at an S
+  // bit and ends before an Eb bit (or at W)
+  const int KB = (NB + NT - 1) / NT;  // bitmap words per thread (contiguous)
+  unsigned mine_s = 0, mine_c = 0;
+  for (int q = 0; q < KB; ++q) {
+    const int g = tid * KB + q;
+    if (g < NB) {
+      const unsigned Z = ZBM[g];
+      const unsigned Zp = g > 0 ? ZBM[g - 1] : 0u, Zn = g + 1 < NB ? ZBM[g + 1] : 0u;
+      const unsigned valid = (g == NB - 1 && (W & 31)) ? ((1u << (W & 31)) - 1u) : FULL;
+      const unsigned Cw = Z & ((Z << 1) | (Zp >> 31) | (Z >> 1) | ((Zn & 1u) << 31)) & valid;
+      const unsigned cin = g > 0 ? ((Zp >> 31) & (((Zp >> 30) & 1u) | (Z & 1u))) : 0u;
+      CM[g] = Cw;
+      EB[g] = ~Cw & ((Cw << 1) | cin) & valid;
+      mine_s += (unsigned)__popc(Cw & ~((Cw << 1) | cin));
+      mine_c += (unsigned)__popc(Cw);
+    }
+  }
+  unsigned ns_tot, nc_tot;
+  block_exsum<NT>(mine_s, s_u, ns_tot);
+  unsigned crun = block_exsum<NT>(mine_c, s_u, nc_tot);
+  for (int q = 0; q < KB; ++q) {
+    const int g = tid * KB + q;
+    if (g < NB) {
+      PRC[g] = crun;
+      crun += (unsigned)__popc(CM[g]);
+    }
+  }
+  // run ends around this thread's words: the last one before them (0 if
+  // none) and the first one after them (W if none)
+  int my_last = 0, my_first = W;
+  for (int q = 0; q < KB; ++q) {
+    const int g = tid * KB + q;
+    if (g < NB && EB[g]) {
+      my_last = max(my_last, g * 32 + 31 - (int)__clz(EB[g]));
+      my_first = min(my_first, g * 32 + __ffs(EB[g]) - 1);
+    }
+  }
+  const int pe0 = block_exmax<NT>(my_last, 0, s_i);
+  const int ne_after = block_rexmin<NT>(my_first, W, s_i);
+  const int l = W - 1;
+  const bool lastc =
+      (((ZBM[l >> 5] >> (l & 31)) & 1u) && l > 0 && ((ZBM[(l - 1) >> 5] >> ((l - 1) & 31)) & 1u));
+  // visit this thread's runs in order: f(start, previous run's end, end)
+  auto runs = [&](auto &&f) {
+    int pe_words = pe0;
+    for (int q = 0; q < KB; ++q) {
+      const int g = tid * KB + q;
+      if (g >= NB) break;
+      const unsigned Cw = CM[g], Eb = EB[g];
+      const unsigned cin = g > 0 ? (CM[g - 1] >> 31) : 0u;
+      unsigned Sb = Cw & ~((Cw << 1) | cin);
+      while (Sb) {
+        const int b = __ffs(Sb) - 1;
+        Sb &= Sb - 1u;
+        const int p = g * 32 + b;
+        const unsigned below = Eb & ((1u << b) - 1u), above = Eb & ~((2u << b) - 1u);
+        const int pe = below ? g * 32 + 31 - (int)__clz(below) : pe_words;
+        int ne = ne_after;
+        if (above) {
+          ne = g * 32 + __ffs(above) - 1;
+        } else {
+          for (int h = q + 1; h < KB && tid * KB + h < NB; ++h)
+            if (EB[tid * KB + h]) {
+              ne = (tid * KB + h) * 32 + __ffs(EB[tid * KB + h]) - 1;
+              break;
+            }
+        }
+        f(p, pe, ne);
+      }
+      if (Eb) pe_words = g * 32 + 31 - (int)__clz(Eb);
+    }
+  };
+  unsigned mine_t = 0;
+  runs([&](int p, int pe, int ne) { mine_t += pair_tokens((unsigned)(p - pe), (unsigned)(ne - p)); });
+  unsigned run_tok;
+  unsigned k = block_exsum<NT>(mine_t, s_u, run_tok);
+  // the last run end in the payload (0 if none): the trailing pair holds
+  // the literals after it, unless the payload ends in a run
+  if (my_last > 0) atomicMax(s_lastend, my_last);
+  __syncthreads();
+  const unsigned tail = (unsigned)(W - *s_lastend);
+  const unsigned ntok = run_tok + (lastc ? 0u : pair_tokens(tail, 0u));
+  const unsigned nlit = (unsigned)W - nc_tot;
+  unsigned *tok = ch + 2;
+  unsigned *lit = tok + ntok;
+  runs([&](int p, int pe, int ne) {
+    put_pair(tok, k, (unsigned)(p - pe), (unsigned)(ne - p));
+    k += pair_tokens((unsigned)(p - pe), (unsigned)(ne - p));
+  });
+  if (tid == 0) {
+    if (!lastc) put_pair(tok, run_tok, tail, 0u);
+    ch[1] = ntok;
+  }
+  for (int w = tid; w < W; w += NT) {
+    const int g = w >> 5, b = w & 31;
+    const unsigned Cw = CM[g];
+    if (!((Cw >> b) & 1u)) lit[(unsigned)w - (PRC[g] + __popc(Cw & ((1u << b) - 1u)))] = SH32[w];
+  }
+  __syncthreads();  // the scratch block and the bitmaps are free again
+  if (tid == 0) *s_lastend = 0;
+  return 8ull + 4ull * ntok + 4ull * nlit;
+}
+
 template <typename T, int B>
 __global__ void __launch_bounds__(512) k_stage2_huge(const S2Args a)
 {
   using G = G2<T, B>;
-  constexpr int NT = 512, NWP = NT / 32, LGES = G::LGES, ES = G::ES, cap = G::NBWMAX;
+  constexpr int NT = 512, LGES = G::LGES, cap = G::NBWMAX;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ unsigned s_u[40];
   __shared__ int s_i[40];
   __shared__ int s_lastend;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x;
   if (tid == 0) s_lastend = 0;  // ordered before its first use by the loop's barriers
   unsigned char *SH = a.scratch + (size_t)blockIdx.x * G::SCRATCH;
-  const unsigned *SH32 = reinterpret_cast<const unsigned *>(SH);
-  unsigned *ZBM = reinterpret_cast<unsigned *>(smem), *CM = ZBM + cap, *EB = ZBM + 2 * cap,
-           *PRC = ZBM + 3 * cap;  // coded words before each bitmap word
 
   const int count = (int)reinterpret_cast<const WsHdr *>(a.ws)->nbig;
   for (int it = blockIdx.x; it < count; it += gridDim.x) {
@@ -570,125 +694,20 @@ __global__ void __launch_bounds__(512) k_stage2_huge(const S2Args a)
     const int pbytes = (int)cb - 8;
     if (pbytes <= G::SHCAP) continue;  // the small launch's payload
     unsigned *ch = reinterpret_cast<unsigned *>(a.staging + so);
-    const int E = pbytes >> LGES, W = pbytes >> 2, NB = (W + 31) >> 5;
     // shuffle: payload word k holds bytes 0..3 of element 4k / ES at byte
     // offset 4k % ES
+    const int W = pbytes >> 2;
     const unsigned *raw = ch + 2;
     for (int k = tid; k < W; k += NT) {
       const unsigned wv = raw[k];
-      const int e = (4 * k) >> LGES, b0 = (4 * k) & (ES - 1);
+      const int e = (4 * k) >> LGES, b0 = (4 * k) & (G::ES - 1);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) SH[(b0 + q) * E + e] = (unsigned char)(wv >> (8 * q));
+      for (int q = 0; q < 4; ++q) SH[(b0 + q) * (pbytes >> LGES) + e] = (unsigned char)(wv >> (8 * q));
     }
     __syncthreads();  // the slot's payload is no longer needed
-    for (int g = wid; g < NB; g += NWP) {
-      const int w = g * 32 + lane;
-      const unsigned bal = __ballot_sync(FULL, w < W && SH32[w] == 0u);
-      if (lane == 0) ZBM[g] = bal;
-    }
-    __syncthreads();
-    // coded words C: zero words with a zero neighbour; a run starts at an S
-    // bit and ends before an Eb bit (or at W)
-    const int KB = (NB + NT - 1) / NT;  // bitmap words per thread (contiguous)
-    unsigned mine_s = 0, mine_c = 0;
-    for (int q = 0; q < KB; ++q) {
-      const int g = tid * KB + q;
-      if (g < NB) {
-        const unsigned Z = ZBM[g];
-        const unsigned Zp = g > 0 ? ZBM[g - 1] : 0u, Zn = g + 1 < NB ? ZBM[g + 1] : 0u;
-        const unsigned valid = (g == NB - 1 && (W & 31)) ? ((1u << (W & 31)) - 1u) : FULL;
-        const unsigned Cw = Z & ((Z << 1) | (Zp >> 31) | (Z >> 1) | ((Zn & 1u) << 31)) & valid;
-        const unsigned cin = g > 0 ? ((Zp >> 31) & (((Zp >> 30) & 1u) | (Z & 1u))) : 0u;
-        CM[g] = Cw;
-        EB[g] = ~Cw & ((Cw << 1) | cin) & valid;
-        mine_s += (unsigned)__popc(Cw & ~((Cw << 1) | cin));
-        mine_c += (unsigned)__popc(Cw);
-      }
-    }
-    unsigned ns_tot, nc_tot;
-    block_exsum<NT>(mine_s, s_u, ns_tot);
-    unsigned crun = block_exsum<NT>(mine_c, s_u, nc_tot);
-    for (int q = 0; q < KB; ++q) {
-      const int g = tid * KB + q;
-      if (g < NB) {
-        PRC[g] = crun;
-        crun += (unsigned)__popc(CM[g]);
-      }
-    }
-    // run ends around this thread's words: the last one before them (0 if
-    // none) and the first one after them (W if none)
-    int my_last = 0, my_first = W;
-    for (int q = 0; q < KB; ++q) {
-      const int g = tid * KB + q;
-      if (g < NB && EB[g]) {
-        my_last = max(my_last, g * 32 + 31 - (int)__clz(EB[g]));
-        my_first = min(my_first, g * 32 + __ffs(EB[g]) - 1);
-      }
-    }
-    const int pe0 = block_exmax<NT>(my_last, 0, s_i);
-    const int ne_after = block_rexmin<NT>(my_first, W, s_i);
-    const int l = W - 1;
-    const bool lastc =
-        (((ZBM[l >> 5] >> (l & 31)) & 1u) && l > 0 && ((ZBM[(l - 1) >> 5] >> ((l - 1) & 31)) & 1u));
-    // visit this thread's runs in order: f(start, previous run's end, end)
-    auto runs = [&](auto &&f) {
-      int pe_words = pe0;
-      for (int q = 0; q < KB; ++q) {
-        const int g = tid * KB + q;
-        if (g >= NB) break;
-        const unsigned Cw = CM[g], Eb = EB[g];
-        const unsigned cin = g > 0 ? (CM[g - 1] >> 31) : 0u;
-        unsigned Sb = Cw & ~((Cw << 1) | cin);
-        while (Sb) {
-          const int b = __ffs(Sb) - 1;
-          Sb &= Sb - 1u;
-          const int p = g * 32 + b;
-          const unsigned below = Eb & ((1u << b) - 1u), above = Eb & ~((2u << b) - 1u);
-          const int pe = below ? g * 32 + 31 - (int)__clz(below) : pe_words;
-          int ne = ne_after;
-          if (above) {
-            ne = g * 32 + __ffs(above) - 1;
-          } else {
-            for (int h = q + 1; h < KB && tid * KB + h < NB; ++h)
-              if (EB[tid * KB + h]) {
-                ne = (tid * KB + h) * 32 + __ffs(EB[tid * KB + h]) - 1;
-                break;
-              }
-          }
-          f(p, pe, ne);
-        }
-        if (Eb) pe_words = g * 32 + 31 - (int)__clz(Eb);
-      }
-    };
-    unsigned mine_t = 0;
-    runs([&](int p, int pe, int ne) { mine_t += pair_tokens((unsigned)(p - pe), (unsigned)(ne - p)); });
-    unsigned run_tok;
-    unsigned k = block_exsum<NT>(mine_t, s_u, run_tok);
-    // the last run end in the payload (0 if none): the trailing pair holds
-    // the literals after it, unless the payload ends in a run
-    if (my_last > 0) atomicMax(&s_lastend, my_last);
-    __syncthreads();
-    const unsigned tail = (unsigned)(W - s_lastend);
-    const unsigned ntok = run_tok + (lastc ? 0u : pair_tokens(tail, 0u));
-    const unsigned nlit = (unsigned)W - nc_tot;
-    unsigned *tok = ch + 2;
-    unsigned *lit = tok + ntok;
-    runs([&](int p, int pe, int ne) {
-      put_pair(tok, k, (unsigned)(p - pe), (unsigned)(ne - p));
-      k += pair_tokens((unsigned)(p - pe), (unsigned)(ne - p));
-    });
-    if (tid == 0) {
-      if (!lastc) put_pair(tok, run_tok, tail, 0u);
-      ch[1] = ntok;
-      a.table[2 * bid + 1] = TB_FIN | (8ull + 4ull * ntok + 4ull * nlit);
-    }
-    for (int w = tid; w < W; w += NT) {
-      const int g = w >> 5, b = w & 31;
-      const unsigned Cw = CM[g];
-      if (!((Cw >> b) & 1u)) lit[(unsigned)w - (PRC[g] + __popc(Cw & ((1u << b) - 1u)))] = SH32[w];
-    }
-    __syncthreads();  // the scratch block and the bitmaps are free again
-    if (tid == 0) s_lastend = 0;
+    const unsigned long long cbytes =
+        huge_code<NT>(ch, pbytes, SH, reinterpret_cast<unsigned *>(smem), cap, s_u, s_i, &s_lastend);
+    if (tid == 0) a.table[2 * bid + 1] = TB_FIN | cbytes;
   }
 }
 

@@ -22,6 +22,8 @@ EPS_REL, EPS_ABS = 0, 1
 BOUND_PAPER, BOUND_STRICT = 0, 1
 FLAG_FAST = 1
 FLAG_ZERO4, FLAG_ZERO8 = 2, 4  # bit zeroing Z4 / Z8 of the kept details
+FLAG_GROUP4, FLAG_GROUP8, FLAG_GROUP16 = 8, 16, 24  # aggregate chunks of 4 / 8 / 16 blocks
+GROUP_FLAGS = {1: 0, 4: FLAG_GROUP4, 8: FLAG_GROUP8, 16: FLAG_GROUP16}
 OK, ERR_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_TIMEOUT, ERR_CUDA, ERR_BUDGET = 0, -1, -2, -3, -4, -5, -6
 HEADER_BYTES = 128
 NOALLOC_WS_BYTES = 64 << 20  # CZ_NOALLOC_WS_BYTES
@@ -226,11 +228,12 @@ def cz_inverse_dense(p: Params, d_coef: int, d_field: int, stream: int) -> int:
 # ------------------------------------------------------------------ torch conveniences
 def params_for(shape, dtype_is_f64: bool, block: int, kind, eps: float, eps_mode: int = EPS_REL,
                stage2: bool = True, range_: float = -1.0, bound_mode: int = BOUND_PAPER,
-               fast: bool = False, zero_bits: int = 0) -> Params:
+               fast: bool = False, zero_bits: int = 0, group: int = 1) -> Params:
     nz, ny, nx = shape
     if isinstance(kind, str):
         kind = KINDS[kind]
-    flags = (FLAG_FAST if fast else 0) | {0: 0, 4: FLAG_ZERO4, 8: FLAG_ZERO8}[int(zero_bits)]
+    flags = ((FLAG_FAST if fast else 0) | {0: 0, 4: FLAG_ZERO4, 8: FLAG_ZERO8}[int(zero_bits)]
+             | GROUP_FLAGS[int(group)])
     return Params(nx, ny, nz, block, F64 if dtype_is_f64 else F32, kind, eps_mode,
                   int(stage2), int(bound_mode), flags, float(eps), float(range_))
 
@@ -259,18 +262,19 @@ class Workspace:
 def compress(field, block: int = 32, kind="w4", eps: float = 1e-3, eps_mode: int = EPS_REL,
              stage2: bool = True, range_: float = -1.0, out=None, ws: Workspace | None = None,
              stream=None, check: bool = True, bound_mode: int = BOUND_PAPER, fast: bool = False,
-             zero_bits: int = 0):
+             zero_bits: int = 0, group: int = 1):
     """Compress a contiguous CUDA tensor [nz, ny, nx] (float32/float64).
 
     zero_bits = 4 / 8 zeroes that many least significant bits of every kept
-    detail (bit zeroing Z4 / Z8).  Returns (stream_tensor, nbytes_tensor); the
+    detail (bit zeroing Z4 / Z8).  group = 4 / 8 / 16 codes that many
+    consecutive blocks as one aggregate chunk.  Returns (stream_tensor, nbytes_tensor); the
     stream is stream_tensor[:nbytes].  With check=True the call synchronises
     and raises on a device-side error.
     """
     import torch
     assert field.is_cuda and field.is_contiguous() and field.dim() == 3
     p = params_for(tuple(field.shape), field.dtype == torch.float64, block, kind, eps, eps_mode,
-                   stage2, range_, bound_mode, fast, zero_bits)
+                   stage2, range_, bound_mode, fast, zero_bits, group)
     cap = cz_compress_bound(p)
     if out is None or out.numel() < cap:
         out = torch.empty(cap, dtype=torch.uint8, device=field.device)

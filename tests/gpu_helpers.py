@@ -34,12 +34,12 @@ def describe_diff(gpu: bytes, ref: bytes) -> str:
 
 
 def gpu_compress(field_np, block, kind, eps, eps_mode=O.EPS_REL, stage2=True, range_=-1.0,
-                 bound_mode=0, zbits=0):
+                 bound_mode=0, zbits=0, group=1):
     import torch
     from paper_1903_07761_gb300 import cz
     f = torch.from_numpy(np.ascontiguousarray(field_np)).cuda()
     out, nb = cz.compress(f, block=block, kind=kind, eps=eps, eps_mode=eps_mode,
-                          stage2=stage2, range_=range_, bound_mode=bound_mode, zero_bits=zbits)
+                          stage2=stage2, range_=range_, bound_mode=bound_mode, zero_bits=zbits, group=group)
     torch.cuda.synchronize()
     n = int(nb.item())
     return out[:n].cpu().numpy().tobytes()

@@ -118,6 +118,47 @@ def test_read_header_of_an_oracle_stream(cz):
         cz.cz_read_header(bytes(bad))
 
 
+def test_group_flags_are_checked(cz):
+    """Aggregate chunks: stage 2 only, and G times the largest block
+    payload at most CZ_GROUP_MAX_BYTES (1792 KiB)."""
+    def bound(shape, f64, block, group, stage2=True):
+        p = cz.params_for(shape, f64, block, "w3ai", 1e-3, cz.EPS_REL, stage2, 1.0, group=group)
+        return cz.cz_compress_bound(p)
+
+    s = (64, 64, 64)
+    for block, f64, ok in ((32, False, (4, 8)), (32, True, (4,)), (16, False, (4, 8, 16)),
+                           (16, True, (4, 8, 16)), (8, True, (4, 8, 16)), (64, False, ())):
+        for g in (4, 8, 16):
+            if g in ok:
+                assert bound(s, f64, block, g) > 0
+            else:
+                with pytest.raises(cz.CzError) as e:
+                    bound(s, f64, block, g)
+                assert e.value.code == cz.ERR_ARG
+    with pytest.raises(cz.CzError) as e:
+        bound(s, False, 16, 4, stage2=False)
+    assert e.value.code == cz.ERR_ARG
+
+
+def test_batched_calls_refuse_group_flags_on_the_host(cz):
+    """Batched launches take no aggregate chunks: refused before any CUDA
+    call (the device pointers below are never touched)."""
+    p = cz.params_for((32, 32, 64), False, 16, "w3ai", 1e-3, group=4)
+    with pytest.raises(cz.CzError) as e:
+        cz.cz_batch_workspace_size([p])
+    assert e.value.code == cz.ERR_ARG
+    b = cz.BatchArgs([p], [1 << 20], [2 << 20], [1 << 20])
+    assert cz.cz_compress_batch(b, 0, 3 << 20, 1 << 20, 0) == cz.ERR_ARG
+
+
+def test_read_header_of_an_oracle_group_stream(cz):
+    f = np.random.default_rng(5).standard_normal((32, 32, 48)).astype(np.float32)
+    for g, flag in ((4, cz.FLAG_GROUP4), (8, cz.FLAG_GROUP8), (16, cz.FLAG_GROUP16)):
+        s = O.compress(f, 8, O.W4, 1e-2, group=g, zbits=4)
+        p, _ = cz.cz_read_header(s[:cz.HEADER_BYTES])
+        assert p.flags == flag | cz.FLAG_ZERO4
+
+
 def test_strict_divisor_equals_the_oracles(cz):
     """The library computes the strict-bound divisor C on the host in the
     same operation order as the oracle; equal C gives equal thresholds."""
@@ -134,7 +175,7 @@ def test_bound_mode_and_flags_are_checked(cz):
     with pytest.raises(cz.CzError):
         cz.cz_compress_bound(p)
     p = cz.params_for((32, 32, 32), False, 32, "w4", 1e-3, cz.EPS_REL, True, 1.0)
-    p.flags = 8  # unknown flag
+    p.flags = 32  # unknown flag
     with pytest.raises(cz.CzError):
         cz.cz_compress_bound(p)
     p.flags = cz.FLAG_ZERO4 | cz.FLAG_ZERO8  # one zeroing width at most
