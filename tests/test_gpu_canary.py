@@ -130,3 +130,52 @@ def test_batch_and_cell_struct_outputs_stay_inside_their_buffers():
     for i, ((o, _), c, B) in enumerate(zip(outs, comps, (32, 16))):
         got = o[:int(lens[i])].cpu().numpy().tobytes()
         assert got == O.compress(np.ascontiguousarray(cells[..., c]), B, O.W3AI, 0.0)
+
+
+GROUP_LANES = [(np.float32, 8, 16, (16, 32, 48)), (np.float32, 16, 16, (32, 32, 64)),
+               (np.float32, 32, 8, (32, 64, 96)), (np.float64, 16, 8, (16, 32, 64)),
+               (np.float64, 32, 4, (32, 32, 96))]
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-3])
+@pytest.mark.parametrize("dtype,B,G,shape", GROUP_LANES)
+def test_group_streams_stay_inside_their_buffers(dtype, B, G, shape, eps):
+    """Aggregate chunks: eps = 0 sends the groups through the large-group
+    tiers (global scratch), 1e-3 through the shared-memory ones; the decode
+    and a random-access call use exact-size workspaces too."""
+    import ctypes as C
+    import torch
+    from paper_1903_07761_gb300 import cz
+    f = _noise(shape, dtype, seed=B + G)
+    ft = torch.from_numpy(f).cuda()
+    p = cz.params_for(shape, dtype == np.float64, B, "w3ai", eps, cz.EPS_REL, True, -1.0, group=G)
+    cap = cz.cz_compress_bound(p)
+    out, out_w = _guarded(cap)
+    ws, ws_w = _guarded(cz.cz_workspace_size(p))
+    nb, nb_w = _guarded(8)
+    s = torch.cuda.current_stream().cuda_stream
+    assert cz.cz_compress(p, ft.data_ptr(), out.data_ptr(), cap, nb.data_ptr(), ws.data_ptr(), ws.numel(), s) == cz.OK
+    assert cz.cz_status(ws.data_ptr(), s) == cz.OK
+    assert _intact(out_w) and _intact(ws_w) and _intact(nb_w)
+    n = int(nb.view(torch.int64).item())
+    stream = out[:n].cpu().numpy().tobytes()
+    assert stream == O.compress(f, B, O.W3AI, eps, group=G)
+    want = O.decompress(stream)
+    hdr = cz.C.create_string_buffer(stream[:cz.HEADER_BYTES], cz.HEADER_BYTES)
+    need = C.c_size_t()
+    assert cz.lib().cz_decompress_blocks_workspace_size(C.byref(p), f.size // B ** 3, C.byref(need)) == cz.OK
+    fo, fo_w = _guarded(f.nbytes)
+    ws2, ws2_w = _guarded(need.value)
+    assert cz.lib().cz_decompress(out.data_ptr(), n, hdr, fo.data_ptr(), f.nbytes, ws2.data_ptr(), ws2.numel(),
+                                  s) == cz.OK
+    assert cz.cz_status(ws2.data_ptr(), s) == cz.OK
+    assert _intact(fo_w) and _intact(ws2_w)
+    np.testing.assert_array_equal(fo.cpu().numpy().view(dtype).reshape(shape).view(np.uint8), want.view(np.uint8))
+    ids = torch.tensor([f.size // B ** 3 - 1, 0, 1], dtype=torch.int32, device="cuda")
+    assert cz.lib().cz_decompress_blocks_workspace_size(C.byref(p), 3, C.byref(need)) == cz.OK
+    tl, tl_w = _guarded(3 * B ** 3 * f.itemsize)
+    ws3, ws3_w = _guarded(need.value)
+    assert cz.lib().cz_decompress_blocks(out.data_ptr(), n, hdr, ids.data_ptr(), 3, tl.data_ptr(), tl.numel(),
+                                         ws3.data_ptr(), ws3.numel(), s) == cz.OK
+    assert cz.cz_status(ws3.data_ptr(), s) == cz.OK
+    assert _intact(tl_w) and _intact(ws3_w)

@@ -59,3 +59,45 @@ def test_random_configurations_agree_with_the_oracle():
             t2, _ = cache.fetch(st, ids2)
             assert np.array_equal(t2.cpu().numpy().view(np.uint8), want[ids2].view(np.uint8)), what
         cache.close()
+
+
+# aggregate chunks: the group sizes each lane takes (FP32 64^3: none)
+GROUPS = {(np.float32, 8): (4, 8, 16), (np.float32, 16): (4, 8, 16), (np.float32, 32): (4, 8),
+          (np.float64, 8): (4, 8, 16), (np.float64, 16): (4, 8, 16), (np.float64, 32): (4,)}
+
+
+def test_random_group_configurations_agree_with_the_oracle():
+    """The same generator with aggregate chunks (stage 2 on, a group size
+    the lane takes): stream, decoded field, random-access tiles and cache
+    tiles."""
+    import torch
+    from paper_1903_07761_gb300 import cz
+    rng = np.random.default_rng(20261205)
+    done = 0
+    while done < 60:
+        c = _case(rng)
+        f, B, nb = c["f"], c["B"], c["nb"]
+        gs = GROUPS.get((f.dtype.type, B))
+        if not gs:
+            continue
+        g = int(rng.choice(gs))
+        what = {k: v for k, v in c.items() if k != "f"} | {"shape": f.shape, "dtype": str(f.dtype), "group": g,
+                                                            "case": done}
+        ref = O.compress(f, B, c["kind"], c["eps"], eps_mode=c["mode"], zbits=c["zbits"], group=g)
+        out, n = cz.compress(torch.from_numpy(f).cuda(), block=B, kind=c["kind"], eps=c["eps"],
+                             eps_mode=c["mode"], zero_bits=c["zbits"], group=g)
+        assert out[:int(n.item())].cpu().numpy().tobytes() == ref, what
+        want_field = O.decompress(ref)
+        rec = cz.decompress(out, nbytes=int(n.item())).cpu().numpy()
+        assert np.array_equal(rec.view(np.uint8), want_field.view(np.uint8)), what
+        want = want_field.reshape(nb[0], B, nb[1], B, nb[2], B).transpose(0, 2, 4, 1, 3, 5).reshape(-1, B, B, B)
+        st = torch.from_numpy(np.frombuffer(ref, np.uint8).copy()).cuda()
+        ids = rng.integers(0, want.shape[0], int(rng.integers(1, 6))).astype(np.int32)
+        tiles = cz.decompress_blocks(st, torch.from_numpy(ids).cuda()).cpu().numpy()
+        assert np.array_equal(tiles.view(np.uint8), want[ids].view(np.uint8)), what
+        cache = cz.Cache(8, B, f64=f.dtype == np.float64)
+        ids2 = rng.integers(0, want.shape[0], int(rng.integers(1, 8))).astype(np.int32)
+        t2, _ = cache.fetch(st, ids2)
+        assert np.array_equal(t2.cpu().numpy().view(np.uint8), want[ids2].view(np.uint8)), what
+        cache.close()
+        done += 1
