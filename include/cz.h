@@ -124,8 +124,10 @@ int cz_compress_bound(const cz_params *p, size_t *bytes);
 
 /* Device workspace needed by cz_compress / cz_decompress for p: a status
  * word, the min/max keys, one u64 look-back word per block, a block table
- * (16 bytes per block) and the staging slots the chunks are built in (room
- * for the largest chunk of every block, about the size of the field).  FP64
+ * (16 bytes per block), a mark byte and a list entry per block (the
+ * single-read compression of cz_compress), and the staging slots the
+ * chunks are built in (room for the largest chunk of every block, about
+ * the size of the field; aggregate chunks add as much again).  FP64
  * with 32^3 blocks and FP32 with 64^3 blocks add one scratch block per CTA
  * (260 KiB / 1.03 MiB) of the kernels that hold a block or a large payload
  * in global memory.
@@ -133,11 +135,18 @@ int cz_compress_bound(const cz_params *p, size_t *bytes);
 int cz_workspace_size(const cz_params *p, size_t *bytes);
 
 /* Compress d_field into d_out (capacity out_cap bytes).
- * Steps: optional min/max pass (range < 0 and eps_mode REL); a persistent
- * kernel that loads each block with TMA, transforms it, thresholds it and
- * writes mask + compacted values to a staging slot; optional stage 2 on
- * every slot; chunk offsets by a decoupled look-back over tiles of chunks;
- * a copy of the chunks into the stream.
+ * Steps: the field's min / max when range < 0; a persistent kernel that
+ * loads each block with TMA, transforms it, thresholds it and writes
+ * mask + compacted values to a staging slot; optional stage 2 on every
+ * slot; chunk offsets by a decoupled look-back over tiles of chunks; a copy
+ * of the chunks into the stream.  With range < 0, stage 2 on, the paper
+ * bound, no bit zeroing and no aggregate chunks (FP32 blocks of edge 8 to
+ * 32, FP64 of edge 8 and 16), the field is read once: a min / max pass over
+ * every 4th row of every 4th z-plane gives a threshold t_lo <= t, the stage
+ * kernel thresholds at t_lo and merges every block's min / max into the
+ * header's, and stage 2 drops the details below the exact t from the
+ * (few) slots that kept one.  The stream is the same byte for byte as with
+ * t known first.  Otherwise a min / max pass reads the whole field first.
  * *d_out_bytes (device u64, may be NULL) receives the stream length; if it
  * exceeds out_cap the status word is CZ_ERR_CAPACITY and the stream is
  * incomplete.  d_ws must hold cz_workspace_size() bytes; it is overwritten.

@@ -306,7 +306,7 @@ size_t lb_bytes(const Shape &sh) { return (8ull * sh.nblocks + 255) / 256 * 256;
 size_t table_bytes(const Shape &sh) { return (16ull * sh.nblocks + 255) / 256 * 256; }
 
 struct WsLayout {
-  size_t lb, table, big, staging, scratch, total, arena;
+  size_t lb, table, big, near, rlist, staging, scratch, total, arena;
   int grid, grid2, grid3;
   // aggregate chunks: group table, group slots and the large group coder's
   // scratch (one buffer of hcap bytes per CTA); zero sizes without groups
@@ -403,7 +403,11 @@ WsLayout ws_layout(const cz_params *p, const Shape &sh)
   w.lb = WS_HDR;
   w.table = w.lb + lb_bytes(sh);
   w.big = w.table + table_bytes(sh);
-  w.staging = w.big + big_bytes(sh.nblocks);
+  // speculative thresholds: one byte per block, and the list of the slots
+  // to refine
+  w.near = w.big + big_bytes(sh.nblocks);
+  w.rlist = w.near + ((size_t)sh.nblocks + 255) / 256 * 256;
+  w.staging = w.rlist + big_bytes(sh.nblocks);
   // blocks are dealt round robin to the stage CTAs
   w.arena = (((size_t)sh.nblocks + w.grid - 1) / w.grid) * (size_t)L.slot_bytes();
   w.scratch = w.staging + w.arena * (size_t)w.grid;
@@ -470,6 +474,31 @@ bool make_tile_map(CUtensorMap *tm, const cz_params *p, const void *d_field, boo
                                                                                 : CU_TENSOR_MAP_SWIZZLE_NONE,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+// the subsample of speculative thresholds (every 4th row of every 4th
+// z-plane): one warp per row, at most four 512-thread CTAs per SM
+template <typename T>
+cudaError_t run_minmax_sample(const cz_params *p, const void *field, WsHdr *ws, cudaStream_t s)
+{
+  const long long rows = (long long)((p->ny + 3) / 4) * ((p->nz + 3) / 4);
+  long long blocks = (rows + 15) / 16;
+  const long long cap = (long long)sm_count() * 4;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k_minmax_sample<T><<<(unsigned)blocks, 512, 0, s>>>(reinterpret_cast<const T *>(field), p->nx, p->ny, p->nz, ws);
+  return cudaGetLastError();
+}
+
+// speculative thresholds for p: the range is computed (one field, stage 2
+// on, the paper bound, no bit zeroing, no aggregate chunks, a
+// register-resident stage kernel); the stage kernel then merges the
+// blocks' min / max itself and stage 2 drops the details below the exact
+// threshold
+bool speculative(const cz_params *p, const Shape &sh)
+{
+  return p->range < 0 && p->stage2 && p->bound_mode == CZ_BOUND_PAPER && zero_bits(*p) == 0 && sh.G == 1 &&
+         lanes_for(*p).scratch_bytes() == 0;
 }
 
 template <typename T>
@@ -897,11 +926,18 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
   WsHdr *ws = reinterpret_cast<WsHdr *>(d_ws);
   unsigned char *wsb = reinterpret_cast<unsigned char *>(d_ws);
   if (cudaMemsetAsync(d_ws, 0, wl.table, s) != cudaSuccess) return CZ_ERR_CUDA;
+  const bool spec = speculative(p, sh);
   if (p->range < 0) {
     if (cudaMemsetAsync(&ws->minkey, 0xFF, 8, s) != cudaSuccess) return CZ_ERR_CUDA;
-    const size_t n = (size_t)p->nx * p->ny * p->nz;
-    const cudaError_t e = p->dtype == CZ_F32 ? run_minmax<float>(d_field, n, ws, s)
-                                             : run_minmax<double>(d_field, n, ws, s);
+    cudaError_t e;
+    if (spec) {  // the subsample only; the stage kernel merges the blocks' min / max
+      if (cudaMemsetAsync(&ws->skmin, 0xFF, 8, s) != cudaSuccess) return CZ_ERR_CUDA;
+      e = p->dtype == CZ_F32 ? run_minmax_sample<float>(p, d_field, ws, s)
+                             : run_minmax_sample<double>(p, d_field, ws, s);
+    } else {
+      const size_t n = (size_t)p->nx * p->ny * p->nz;
+      e = p->dtype == CZ_F32 ? run_minmax<float>(d_field, n, ws, s) : run_minmax<double>(d_field, n, ws, s);
+    }
     if (e != cudaSuccess) return CZ_ERR_CUDA;
   }
   const Lanes L = lanes_for(*p);
@@ -928,6 +964,8 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
   a.kind = p->kind;
   a.zbits = zero_bits(*p);
   a.dtype = p->dtype;
+  a.spec = spec ? 1 : 0;
+  a.near = spec ? wsb + wl.near : nullptr;
   S2Args sa{};
   sa.staging = a.staging;
   sa.table = a.table;
@@ -935,6 +973,11 @@ int compress_impl(const cz_params *p, const void *d_field, void *d_out, size_t o
   sa.biglist = a.biglist;
   sa.scratch = a.scratch;
   sa.nblocks = sh.nblocks;
+  sa.spec = a.spec;
+  sa.near = a.near;
+  sa.rlist = spec ? reinterpret_cast<int *>(wsb + wl.rlist) : nullptr;
+  sa.eps = p->eps;
+  sa.eps_mode = p->eps_mode;
   PlaceArgs pa{};
   pa.staging = a.staging;
   pa.table = a.table;

@@ -29,10 +29,21 @@ namespace czp {
 struct S2Args {
   unsigned char *staging;
   unsigned long long *table;  // per block: slot offset, chunk bytes (~0: lost)
-  const void *ws;             // header: count of large payloads (nbig)
+  const void *ws;             // header: count of large payloads (nbig), min / max keys
   const int *biglist;         // ids of the blocks with large payloads
   unsigned char *scratch;     // FP64 32^3: shuffled payloads, one G2::SCRATCH block per large CTA
   int nblocks;
+  // speculative thresholds (spec): the stage kernel kept the details with
+  // |d| >= t_lo, the threshold of the subsample's range (the header's
+  // skmin / skmax), and marked in near[] the blocks that kept one below
+  // near_threshold(t_lo); t comes from the final keys.  The slots that hold
+  // a value below t are listed in rlist (count in the header's nref) and
+  // coded by k_stage2_refine.
+  int spec;
+  const unsigned char *near;
+  int *rlist;
+  double eps;
+  int eps_mode;
 };
 
 struct PlaceArgs {
@@ -97,6 +108,35 @@ __device__ __forceinline__ void shuffle_words(const unsigned *raw, int W, int e0
       }
     }
   }
+}
+
+// shuffle_words of a whole payload of W words (E elements) that, for
+// FP32, also tests the value words from word vw0 on (one value each)
+// against t: returns whether this thread met a value with |v| < t (a
+// speculative slot to refine).  vw0 >= W tests nothing (FP64 always).
+template <typename T, int NT>
+__device__ __forceinline__ bool shuffle_check(const unsigned *raw, int W, int E, unsigned char *SH, int vw0, T t)
+{
+  constexpr int ES = (int)sizeof(T), LGES = ES == 8 ? 3 : 2;
+  bool drop = false;
+  for (int k0 = threadIdx.x; k0 < W; k0 += 4 * NT) {
+    unsigned wv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) wv[j] = k0 + j * NT < W ? raw[k0 + j * NT] : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = k0 + j * NT;
+      if (k < W) {
+        if constexpr (ES == 4) {
+          if (k >= vw0) drop |= fabsf(__uint_as_float(wv[j])) < (float)t;
+        }
+        const int e = (4 * k) >> LGES, b0 = (4 * k) & (ES - 1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) SH[(b0 + q) * E + e] = (unsigned char)(wv[j] >> (8 * q));
+      }
+    }
+  }
+  return drop;
 }
 
 // ---- zero-run code of a shuffled payload of pbytes (< 256 KiB: the run
@@ -221,6 +261,93 @@ __device__ __forceinline__ unsigned stage2_code(unsigned *ch, int pbytes, const 
   return 8u + 4u * ntok + 4u * nlit;
 }
 
+// ---- speculative thresholds: a slot that kept the details with |d| >=
+// t_lo, a lower bound of the threshold t, drops those below t: the value
+// list is checked (one barrier); only when some value is dropped are the
+// values copied to SH (>= pbytes bytes), the mask bits of the dropped ones
+// cleared and the rest moved down in place, and nnz rewritten (six more
+// barriers).  The kept set is then exactly {|d| >= t}, the set a pass with
+// t known from the start keeps.  AUX holds >= 2 ceil(nnz / 32) words; s_u
+// is scan scratch.  All NT threads of the CTA; returns the payload bytes.
+// (CHECKED: the caller has found a value to drop already)
+template <typename T, int B, int NT, bool CHECKED = false>
+__device__ __forceinline__ int refine_slot(unsigned *ch, int pbytes, T t, unsigned char *SH, unsigned *AUX,
+                                           unsigned *s_u)
+{
+  using G = G2<T, B>;
+  constexpr int ES = G::ES, NWP = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nnz = (int)ch[0];
+  unsigned char *P = reinterpret_cast<unsigned char *>(ch + 2);
+  T *vals = reinterpret_cast<T *>(P + 64 * ES + G::MASKB);
+  if constexpr (!CHECKED) {
+    int drop = 0;
+    for (int j = tid; j < nnz; j += NT) drop |= (fabs(vals[j]) < t) ? 1 : 0;
+    if (!__syncthreads_or(drop)) return pbytes;
+  }
+  // keep bits (bit j % 32 of word j / 32), the values to SH
+  const int NKW = (nnz + 31) >> 5;
+  unsigned *KF = AUX, *KP = AUX + NKW;
+  T *SV = reinterpret_cast<T *>(SH);
+  for (int j0 = wid * 32; j0 < nnz; j0 += NT) {
+    const int j = j0 + lane;
+    T v = T(0);
+    if (j < nnz) v = vals[j];
+    const unsigned keep = __ballot_sync(FULL, j < nnz && !(fabs(v) < t));
+    if (lane == 0) KF[j0 >> 5] = keep;
+    if (j < nnz) SV[j] = v;
+  }
+  __syncthreads();
+  // new index of each kept value: exclusive prefix of the keep counts
+  {
+    const int per = (NKW + NT - 1) / NT, w0 = tid * per;
+    unsigned sum = 0;
+    for (int q = 0; q < per; ++q)
+      if (w0 + q < NKW) sum += __popc(KF[w0 + q]);
+    unsigned tot;
+    unsigned ex = block_exsum<NT>(sum, s_u, tot);
+    for (int q = 0; q < per; ++q)
+      if (w0 + q < NKW) {
+        KP[w0 + q] = ex;
+        ex += __popc(KF[w0 + q]);
+      }
+    if (tid == 0) ch[0] = tot;
+  }
+  __syncthreads();
+  // mask rows: the j-th set bit (positions in stream order) is value j
+  {
+    unsigned *M = reinterpret_cast<unsigned *>(P + 64 * ES);
+    constexpr int NMW = G::NMW, per = (NMW + NT - 1) / NT;
+    const int m0 = tid * per;
+    unsigned words[per], sum = 0;
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+      words[q] = m0 + q < NMW ? M[m0 + q] : 0u;
+      sum += __popc(words[q]);
+    }
+    unsigned tot;
+    unsigned j = block_exsum<NT>(sum, s_u, tot);
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+      unsigned wd = words[q], out = 0u;
+      while (wd) {
+        const int b = __ffs(wd) - 1;
+        wd &= wd - 1u;
+        if ((KF[j >> 5] >> (j & 31)) & 1u) out |= 1u << b;
+        ++j;
+      }
+      if (m0 + q < NMW) M[m0 + q] = out;
+    }
+  }
+  // the kept values, moved down (from the copy in SH)
+  for (int j = tid; j < nnz; j += NT) {
+    const unsigned kw = KF[j >> 5];
+    if ((kw >> (j & 31)) & 1u) vals[KP[j >> 5] + __popc(kw & ((1u << (j & 31)) - 1u))] = SV[j];
+  }
+  __syncthreads();
+  return 64 * ES + G::MASKB + (int)ch[0] * ES;
+}
+
 // ---- stage 2 of one slot, in place: [nnz | 0 | raw payload of pbytes]
 // becomes [nnz | ntok | tokens | literal words] (shuffle into SH, then the
 // zero-run code; five barriers).  Returns the chunk bytes.
@@ -246,8 +373,59 @@ __device__ __forceinline__ int field_of(const StageMaps<NF> &maps, int nf, int b
 
 // NF = 1: one field described by a; NF > 1: up to NF fields of one group,
 // their blocks numbered consecutively (field by field) in one index space
-template <typename T, int B, int KIND, int NF>
-__global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__ StageMaps<NF> maps, const FwdArgs a)
+// ---- speculative thresholds: a warp's min / max (lo, hi; NaN never
+// enters) into the header's keys where it extends the extremes this CTA
+// has sent (s_kc; each is lowered / raised before the global atomic that
+// carries it, so a warp that reads it and skips is covered by that atomic;
+// the results are not waited for).
+template <typename T>
+__device__ __forceinline__ void send_extremes(T lo, T hi, unsigned long long *s_kc, WsHdr *ws)
+{
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min_nn(lo, __shfl_xor_sync(FULL, lo, o));
+    hi = max_nn(hi, __shfl_xor_sync(FULL, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    const unsigned long long kl = order_key(lo), kh = order_key(hi);
+    if (kl < *(volatile unsigned long long *)&s_kc[0]) {
+      atomicMin(&s_kc[0], kl);
+      atomicMin(&ws->minkey, kl);
+    }
+    if (kh > *(volatile unsigned long long *)&s_kc[1]) {
+      atomicMax(&s_kc[1], kh);
+      atomicMax(&ws->maxkey, kh);
+    }
+  }
+}
+
+// the same for a block tile of `bytes` bytes in shared memory, read by NT
+// threads in 16-byte pieces (out of line: the FP32 32^3 W3ai stage kernel,
+// which takes this path, keeps its registers for the transform)
+template <typename T, int NT>
+__device__ __noinline__ void tile_extremes(const unsigned char *tile, int bytes, unsigned long long *s_kc, WsHdr *ws)
+{
+  T lo = (T)INFINITY, hi = (T)-INFINITY;
+  for (int q = threadIdx.x; q < bytes / 16; q += NT) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 w = reinterpret_cast<const float4 *>(tile)[q];
+      lo = min3_nn(min3_nn(lo, w.x, w.y), w.z, w.w);
+      hi = max3_nn(max3_nn(hi, w.x, w.y), w.z, w.w);
+    } else {
+      const double2 w = reinterpret_cast<const double2 *>(tile)[q];
+      lo = min3_nn(lo, w.x, w.y);
+      hi = max3_nn(hi, w.x, w.y);
+    }
+  }
+  send_extremes<T>(lo, hi, s_kc, ws);
+}
+
+// SPEC (NF = 1): speculative thresholds (FwdArgs::spec).  At most 128
+// registers a thread, whatever the block edge (enough CTAs per SM for the
+// smaller edges: the speculative variant would otherwise take more)
+template <typename T, int B, int KIND, int NF, bool SPEC = false>
+__global__ void __launch_bounds__(B * B / 2, 65536 / (B * B / 2 * 128))
+    k_stage1(const __grid_constant__ StageMaps<NF> maps, const FwdArgs a)
 {
   using G = G2<T, B>;
   using T2 = typename V2T<T>::type;
@@ -277,8 +455,24 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
   double mn, mx, range;
   T t;
   __shared__ T s_t[NF];
+  static_assert(!SPEC || NF == 1, "speculative thresholds: one field");
+  // speculative thresholds: the extremes this CTA's warps have sent to the
+  // header's keys (send_extremes)
+  __shared__ unsigned long long s_kc[2];
+  if constexpr (SPEC) {
+    if (tid == 0) {
+      s_kc[0] = ~0ull;
+      s_kc[1] = 0ull;
+    }
+  }
+  __shared__ T s_thi;  // speculative thresholds: near_threshold(t_lo)
   if constexpr (NF == 1) {
-    threshold_of<T>(a.eps, a.eps_mode, a.cnorm, a.range, ws, mn, mx, range, t);
+    if constexpr (SPEC) {  // t_lo of the subsample's range, no larger than the field's threshold
+      t = threshold_between<T>(a.eps, a.eps_mode, *(volatile const unsigned long long *)&ws->skmin,
+                               *(volatile const unsigned long long *)&ws->skmax);
+      if (tid == 0) s_thi = near_threshold(t);
+    } else
+      threshold_of<T>(a.eps, a.eps_mode, a.cnorm, a.range, ws, mn, mx, range, t);
   } else if (tid < a.nf) {
     T tf;
     threshold_keys<T>(maps.g[tid].eps, maps.g[tid].eps_mode, a.cnorm, maps.g[tid].range_in, a.keys + 2 * tid, mn,
@@ -322,6 +516,9 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     // below waits for a thread that has left
     if (!mbar_wait(&s_bar, phase)) s_to = 1u;
     phase ^= 1u;
+    if constexpr (SPEC) {
+      if (tid == 0) a.near[bid] = 0;  // (set by the payload writes after the barriers below)
+    }
 
     // ---- tile -> registers; the next tile is fetched after the
     // transform's first barrier, when every thread has read this one.
@@ -329,8 +526,20 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
     // the tile, then the pairs (two values of one 16-byte chunk) at their
     // swizzled places.
     constexpr bool RX = G::template rowx<KIND>();
+    // speculative thresholds: the block's min / max into the header's keys,
+    // from the pairs as they are loaded, or where that leaves the kernel
+    // short of registers (FP32 32^3 W3ai) from the tile before the pairs
+    // are loaded; the W4li row pass takes it from the rows it reads
+    constexpr bool MM_TILE = SPEC && !RX && sizeof(T) == 4 && B == 32 && KIND == W3AI;
+    if constexpr (MM_TILE) tile_extremes<T, NT>(PF, G::TILE, s_kc, ws);
     if constexpr (RX) {
-      x_rows<T, B, KIND, true, NT>(PF);
+      if constexpr (SPEC) {
+        T lo = (T)INFINITY, hi = (T)-INFINITY;
+        x_rows<T, B, KIND, true, NT, true>(PF, lo, hi);
+        send_extremes<T>(lo, hi, s_kc, ws);
+      } else {
+        x_rows<T, B, KIND, true, NT>(PF);
+      }
       fence_async_smem();  // the next tile's copy overwrites these writes
       __syncthreads();
     }
@@ -342,6 +551,17 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
         const unsigned o = (unsigned)((((h * ZH + zl) * B + 2 * k + r) * B + x0) * ES);
         v[r][zl] = *reinterpret_cast<const T2 *>(PF + (RX ? swz128(o) : o));
       }
+    if constexpr (SPEC && !RX && !MM_TILE) {
+      T lo = (T)INFINITY, hi = (T)-INFINITY;
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int zl = 0; zl < ZH; ++zl) {
+          lo = min3_nn(lo, v[r][zl].x, v[r][zl].y);
+          hi = max3_nn(hi, v[r][zl].x, v[r][zl].y);
+        }
+      send_extremes<T>(lo, hi, s_kc, ws);
+    }
     const int nb = bid + (int)gridDim.x;
 
     // ---- forward transform
@@ -420,6 +640,10 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
       T *VALS = reinterpret_cast<T *>(P + 64 * ES + G::MASKB);
       const unsigned lowE = (1u << x0) - 1u, lowO = (2u << x0) - 1u;
       if (W[0] | W[1]) {
+        // speculative thresholds: whether a kept value lies below t_hi, a
+        // little above t_lo (the block is then tested by stage 2)
+        bool near = false;
+        const T thi = SPEC ? s_thi : T(0);
 #pragma unroll
         for (int zl = 0; zl < ZH; ++zl) {
           const int z = h * ZH + zl;
@@ -429,10 +653,19 @@ __global__ void __launch_bounds__(B * B / 2, 1) k_stage1(const __grid_constant__
             if (b2) {
               const unsigned wd = get_rowi<B>(MASKU, rpad<B>(z, 2 * k + r));
               const unsigned base = ROWOFF[rpad<B>(z, 2 * k + r)];
-              if (b2 & 1u) VALS[base + __popc(wd & lowE)] = zero_low(v[r][zl].x, a.zbits);
-              if (b2 & 2u) VALS[base + __popc(wd & lowO)] = zero_low(v[r][zl].y, a.zbits);
+              if (b2 & 1u) {
+                VALS[base + __popc(wd & lowE)] = zero_low(v[r][zl].x, a.zbits);
+                if constexpr (SPEC) near |= fabs(v[r][zl].x) < thi;
+              }
+              if (b2 & 2u) {
+                VALS[base + __popc(wd & lowO)] = zero_low(v[r][zl].y, a.zbits);
+                if constexpr (SPEC) near |= fabs(v[r][zl].y) < thi;
+              }
             }
           }
+        }
+        if constexpr (SPEC) {
+          if (near) a.near[bid] = 1;
         }
       }
     }
@@ -469,13 +702,80 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_stage2(const S2Args a)
   // those the stage kernel has coded already); the large launch visits
   // only the blocks the stage kernel listed
   const int count = BIG ? (int)reinterpret_cast<const WsHdr *>(a.ws)->nbig : a.nblocks;
+  // speculative thresholds: whether t_lo fell short of the exact
+  // threshold (then every slot is checked)
+  // (only the blocks marked near, where t is at most t_lo's near bound)
+  T t = T(0);
+  bool check = false, all = false;
+  if (a.spec) {
+    const WsHdr *h = reinterpret_cast<const WsHdr *>(a.ws);
+    t = threshold_between<T>(a.eps, a.eps_mode, h->minkey, h->maxkey);
+    const T tl = threshold_between<T>(a.eps, a.eps_mode, h->skmin, h->skmax);
+    check = t_bits(tl) != t_bits(t);
+    all = !(t <= near_threshold(tl));
+  }
   for (int it = blockIdx.x; it < count; it += gridDim.x) {
     const int bid = BIG ? a.biglist[it] : it;
     const unsigned long long so = a.table[2 * bid], cb = a.table[2 * bid + 1];
+    // (the mark is loaded with the table entry, so their latencies overlap)
+    const bool test = check && (all || a.near[bid] != 0);
     if (cb == TB_LOST || (cb & TB_FIN)) continue;  // staging overflow, or finished already
-    const int pbytes = (int)cb - 8;
+    int pbytes = (int)cb - 8;
     if ((pbytes > G::SHCAP) != BIG) continue;  // the other launch's payload
     unsigned *ch = reinterpret_cast<unsigned *>(a.staging + so);
+    unsigned cbytes;
+    if (!test) {
+      cbytes = stage2_chunk<T, NT>(ch, pbytes, smem, AUX, cap, s_u, s_i);
+    } else {
+      // speculative thresholds: the values are tested (FP32: while the
+      // payload is shuffled); a slot with one to drop is listed for
+      // k_stage2_refine, which spreads those over its CTAs
+      bool drop;
+      if constexpr (sizeof(T) == 4) {
+        constexpr int VW0 = (64 * 4 + G::MASKB) / 4;
+        drop = __syncthreads_or(shuffle_check<T, NT>(ch + 2, pbytes >> 2, pbytes >> 2, smem, VW0, t));
+      } else {
+        const T *vals = reinterpret_cast<const T *>(reinterpret_cast<const unsigned char *>(ch + 2) +
+                                                    64 * G::ES + G::MASKB);
+        bool d = false;
+        for (int j = threadIdx.x; j < (int)ch[0]; j += NT) d |= fabs(vals[j]) < t;
+        drop = __syncthreads_or(d);
+        if (!drop) shuffle_words<T, NT>(ch + 2, pbytes >> 2, 0, pbytes >> 3, smem);
+        __syncthreads();
+      }
+      if (drop) {
+        if (threadIdx.x == 0) a.rlist[atomicAdd(&reinterpret_cast<WsHdr *>(const_cast<void *>(a.ws))->nref, 1u)] = bid;
+        continue;
+      }
+      cbytes = stage2_code<T, NT>(ch, pbytes, smem, AUX, cap, s_u, s_i);
+    }
+    if (threadIdx.x == 0) a.table[2 * bid + 1] = TB_FIN | (unsigned long long)cbytes;
+  }
+}
+
+// ---- speculative thresholds: the slots the stage-2 launches listed (they
+// hold a value below the exact threshold t), one per CTA at a time: drop
+// those values, then stage 2 as above.  512 threads, the payload buffer and
+// the bitmaps of the large launch.
+template <typename T, int B>
+__global__ void __launch_bounds__(512) k_stage2_refine(const S2Args a)
+{
+  using G = G2<T, B>;
+  constexpr int NT = 512, CAPB = G::PMAX_AL, cap = G::NBWMAX;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ unsigned s_u[40];
+  __shared__ int s_i[40];
+  unsigned *AUX = reinterpret_cast<unsigned *>(smem + CAPB);
+  const WsHdr *h = reinterpret_cast<const WsHdr *>(a.ws);
+  const int count = (int)*(volatile const unsigned *)&h->nref;
+  if ((int)blockIdx.x >= count) return;
+  const T t = threshold_between<T>(a.eps, a.eps_mode, h->minkey, h->maxkey);
+  for (int it = blockIdx.x; it < count; it += gridDim.x) {
+    const int bid = a.rlist[it];
+    const unsigned long long so = a.table[2 * bid], cb = a.table[2 * bid + 1];
+    unsigned *ch = reinterpret_cast<unsigned *>(a.staging + so);
+    int pbytes = (int)cb - 8;
+    pbytes = refine_slot<T, B, NT, true>(ch, pbytes, t, smem, AUX, s_u);
     const unsigned cbytes = stage2_chunk<T, NT>(ch, pbytes, smem, AUX, cap, s_u, s_i);
     if (threadIdx.x == 0) a.table[2 * bid + 1] = TB_FIN | (unsigned long long)cbytes;
   }

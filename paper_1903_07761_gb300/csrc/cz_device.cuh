@@ -711,6 +711,27 @@ __device__ __forceinline__ unsigned long long lookback(unsigned long long *state
   return excl;
 }
 
+// min / max that ignore a NaN operand (IEEE minNum / maxNum)
+__device__ __forceinline__ float min_nn(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float max_nn(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double min_nn(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ double max_nn(double a, double b) { return fmax(a, b); }
+// three operands (FP32: one instruction; NaN operands are ignored as above)
+__device__ __forceinline__ float min3_nn(float a, float b, float c)
+{
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float max3_nn(float a, float b, float c)
+{
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ double min3_nn(double a, double b, double c) { return fmin(fmin(a, b), c); }
+__device__ __forceinline__ double max3_nn(double a, double b, double c) { return fmax(fmax(a, b), c); }
+
 // ------------------------------------------------------------ order keys
 __device__ __forceinline__ unsigned long long order_key(float f)
 {

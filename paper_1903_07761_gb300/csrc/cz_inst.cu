@@ -74,6 +74,15 @@ cudaError_t stage2_k(const S2Args &sa, int stage2, int grid2, int grid3, cudaStr
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
+    if constexpr (!G::SLAB) {
+      if (sa.spec) {  // speculative thresholds: the listed slots, one per CTA
+        e = prepare<k_stage2_refine<CZ_T, CZ_B>>(G::SMEM_S2B);
+        if (e != cudaSuccess) return e;
+        k_stage2_refine<CZ_T, CZ_B><<<grid3, 512, G::SMEM_S2B, s>>>(sa);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
+    }
   }
   return e;
 }
@@ -111,6 +120,11 @@ cudaError_t compress_k(const CUtensorMap &tm, const FwdArgs &a, const S2Args &sa
     if (e != cudaSuccess) return e;
     if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
     k_stage1_slab<CZ_T, CZ_B, KIND, 1><<<grid, SGi::NT, SGi::SMEM, s>>>(maps, a);
+  } else if (a.spec) {  // speculative thresholds
+    e = prepare<k_stage1<CZ_T, CZ_B, KIND, 1, true>>(G::SMEM_C);
+    if (e != cudaSuccess) return e;
+    if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
+    k_stage1<CZ_T, CZ_B, KIND, 1, true><<<grid, G::NT, G::SMEM_C, s>>>(maps, a);
   } else {
     e = prepare<k_stage1<CZ_T, CZ_B, KIND, 1>>(G::SMEM_C);
     if (e != cudaSuccess) return e;

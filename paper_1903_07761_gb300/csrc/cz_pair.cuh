@@ -28,6 +28,8 @@
 
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "cz_device.cuh"
 
 namespace czp {
@@ -53,6 +55,11 @@ struct WsHdr {
   unsigned long long minkey, maxkey;
   unsigned long long out_bytes;
   unsigned long long bump;  // staging bytes handed out so far
+  // speculative thresholds: min / max keys of a subsample of the field
+  // (every 4th row of every 4th z-plane), a lower bound of the range, and
+  // the count of the slots listed for refinement
+  unsigned long long skmin, skmax;
+  unsigned nref, pad2;
 };
 
 // ---- several fields in one launch (one group: same type, block, kind)
@@ -101,6 +108,13 @@ struct FwdArgs {
   int nx, ny, nz, nbx, nby, nbz, nblocks, nf;
   int eps_mode, stage2, kind, dtype;
   int zbits;  // bit zeroing: 0, 4 or 8 least significant bits of each kept detail cleared
+  // speculative thresholds (one field, range computed): the stage kernel
+  // merges each warp's min / max into the header's keys and thresholds at
+  // t_lo <= t, the threshold of a subsample's range (the header's skmin /
+  // skmax); near[bid] = 1 where the block kept a value below
+  // near_threshold(t_lo); stage 2 drops the details below the exact t
+  int spec;
+  unsigned char *near;
 };
 
 struct InvArgs {
@@ -1284,8 +1298,10 @@ __device__ __forceinline__ void from_cube(T2 (&v)[2][B / 2], const T *C, int a, 
 // in distinct bank groups), holds a row in registers and transforms it with
 // compile-time stencils (fwd_reg / inv_reg: the same rounded operations in
 // the same order as the pair kernels' x-step), and writes it back in place.
-template <typename T, int B, int KIND, bool FWD, int NT>
-__device__ __forceinline__ void x_rows(unsigned char *tile)
+// With MM, lo / hi also take the min / max of the rows' values as read
+// (NaN never enters).
+template <typename T, int B, int KIND, bool FWD, int NT, bool MM = false>
+__device__ __forceinline__ void x_rows(unsigned char *tile, T &lo, T &hi)
 {
   static_assert(sizeof(T) == 4 && B == 32 && (B * B) % (2 * NT) == 0, "128-byte FP32 rows, two per round");
 #pragma unroll 1
@@ -1302,6 +1318,10 @@ __device__ __forceinline__ void x_rows(unsigned char *tile)
         e[q][4 * c + 1] = w.y;
         e[q][4 * c + 2] = w.z;
         e[q][4 * c + 3] = w.w;
+        if constexpr (MM) {
+          lo = min3_nn(min3_nn(lo, w.x, w.y), w.z, w.w);
+          hi = max3_nn(max3_nn(hi, w.x, w.y), w.z, w.w);
+        }
       }
     }
 #pragma unroll
@@ -1323,14 +1343,24 @@ __device__ __forceinline__ void x_rows(unsigned char *tile)
   }
 }
 
+template <typename T, int B, int KIND, bool FWD, int NT>
+__device__ __forceinline__ void x_rows(unsigned char *tile)
+{
+  T lo = T(0), hi = T(0);
+  x_rows<T, B, KIND, FWD, NT, false>(tile, lo, hi);
+}
+
 // Whole forward transform.  The plane area and the cube may overlap (the
 // cube is written after the plane's last read); the halo is separate.
 // first_sync runs right after the first barrier (every thread has read its
 // input by then).  Ends without a barrier: from_cube's reads of the cube
 // are ordered by the caller's next barrier.
-template <typename T, int B, int KIND, bool XSTEP = true, typename T2, typename F>
+// side() runs after the barrier that follows the level-0 steps (at the end
+// without coarser levels), while the coarser levels' first pass keeps
+// half of the threads or fewer busy.
+template <typename T, int B, int KIND, bool XSTEP = true, typename T2, typename F, typename F2>
 __device__ __forceinline__ void fwd_all(T2 (&v)[2][B / 2], T2 *pl, T2 *hx, T *cube, int a, int k, int h, int seg,
-                                        F &&first_sync)
+                                        F &&first_sync, F2 &&side)
 {
   if constexpr (XSTEP) x_fwd<T, B, KIND>(v, a, seg);
   y_fwd<T, B, KIND>(v, pl, a, k, h, first_sync);
@@ -1338,9 +1368,19 @@ __device__ __forceinline__ void fwd_all(T2 (&v)[2][B / 2], T2 *pl, T2 *hx, T *cu
   if constexpr (G2<T, B>::L > 1) {
     to_cube<T, B>(v, cube, a, k, h);
     __syncthreads();
+    side();
     cube_fwd<T, B / 2, KIND, G2<T, B>::NT>(cube);
     from_cube<T, B>(v, cube, a, k, h);
+  } else {
+    side();
   }
+}
+
+template <typename T, int B, int KIND, bool XSTEP = true, typename T2, typename F>
+__device__ __forceinline__ void fwd_all(T2 (&v)[2][B / 2], T2 *pl, T2 *hx, T *cube, int a, int k, int h, int seg,
+                                        F &&first_sync)
+{
+  fwd_all<T, B, KIND, XSTEP>(v, pl, hx, cube, a, k, h, seg, first_sync, [] {});
 }
 
 // Whole inverse transform.  The cube must not overlap the plane or the
@@ -1475,6 +1515,34 @@ __device__ __forceinline__ void threshold_of(double eps, int eps_mode, double cn
 {
   threshold_keys<T>(eps, eps_mode, cnorm, range_in, &ws->minkey, mn, mx, range, t);
 }
+
+// the threshold of the range between two order keys, formed exactly as
+// threshold_keys does with the paper bound (divisor 1); monotonic in the
+// range, so the keys of any subset of the field give a threshold no larger
+// than the whole field's
+template <typename T>
+__device__ __forceinline__ T threshold_between(double eps, int eps_mode, unsigned long long kmin,
+                                               unsigned long long kmax)
+{
+  double mn = key_value(kmin, T(0)), mx = key_value(kmax, T(0));
+  mn = (double)(T)((T)mn + (T)0);
+  mx = (double)(T)((T)mx + (T)0);
+  const double range = (mn <= mx) ? mx - mn : 0.0;
+  return (T)(eps_mode == 1 ? eps : eps * range);
+}
+
+// speculative thresholds: a bound a little above t_lo (by 2^-10 of it).
+// Where the exact threshold t is at most this bound, only the blocks that
+// kept a value below it can hold one below t.
+template <typename T>
+__device__ __forceinline__ T near_threshold(T tlo)
+{
+  return tlo * (T)(1.0 + 1.0 / 1024.0);
+}
+
+// bits of a threshold, for comparing two of them exactly
+__device__ __forceinline__ unsigned long long t_bits(float t) { return __float_as_uint(t); }
+__device__ __forceinline__ unsigned long long t_bits(double t) { return (unsigned long long)__double_as_longlong(t); }
 
 // ============================================================ decompress
 // ---- stage-2 inverse of one chunk's tokens, by all NT threads of the CTA:
@@ -2010,6 +2078,48 @@ __global__ void __launch_bounds__(512) k_minmax_multi(const __grid_constant__ Mi
   const size_t len = a.n[f] - b0 < MM_CHUNK ? a.n[f] - b0 : MM_CHUNK;
   minmax_part<T>(reinterpret_cast<const T *>(a.field[f]) + b0, len, threadIdx.x, blockDim.x, &a.keys[2 * f],
                  &a.keys[2 * f + 1]);
+}
+
+// min / max of the subsample of speculative thresholds: every 4th row (y)
+// of every 4th z-plane, whole rows (16-byte vectors; a row is a multiple of
+// 8 elements), one warp per row; the keys go to the header's skmin / skmax
+template <typename T>
+__global__ void __launch_bounds__(512) k_minmax_sample(const T *__restrict__ xs, int nx, int ny, int nz, WsHdr *ws)
+{
+  constexpr int V = sizeof(T) == 4 ? 4 : 2;  // elements per 16-byte vector
+  using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const int lane = threadIdx.x & 31;
+  const long long rows_y = (ny + 3) / 4, rows = rows_y * ((nz + 3) / 4);
+  const long long w0 = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const long long ws_ = (long long)gridDim.x * (blockDim.x / 32);
+  T lo = (T)INFINITY, hi = (T)-INFINITY;
+  const int nv = nx / V;
+  for (long long r = w0; r < rows; r += ws_) {
+    const long long z = 4 * (r / rows_y), y = 4 * (r % rows_y);
+    const VT *row = reinterpret_cast<const VT *>(xs + (z * ny + y) * (long long)nx);
+    for (int q = lane; q < nv; q += 32) {
+      const VT v = __ldcs(row + q);
+      if constexpr (V == 4) {
+        lo = v.x < lo ? v.x : lo; hi = v.x > hi ? v.x : hi;
+        lo = v.y < lo ? v.y : lo; hi = v.y > hi ? v.y : hi;
+        lo = v.z < lo ? v.z : lo; hi = v.z > hi ? v.z : hi;
+        lo = v.w < lo ? v.w : lo; hi = v.w > hi ? v.w : hi;
+      } else {
+        lo = v.x < lo ? v.x : lo; hi = v.x > hi ? v.x : hi;
+        lo = v.y < lo ? v.y : lo; hi = v.y > hi ? v.y : hi;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T l2 = __shfl_xor_sync(FULL, lo, o), h2 = __shfl_xor_sync(FULL, hi, o);
+    lo = l2 < lo ? l2 : lo;
+    hi = h2 > hi ? h2 : hi;
+  }
+  if (lane == 0) {
+    atomicMin(&ws->skmin, order_key(lo));
+    atomicMax(&ws->skmax, order_key(hi));
+  }
 }
 
 }  // namespace czp
