@@ -741,7 +741,9 @@ def run_gpu(args, rank, world, local_rank):
                 "algorithmic_bytes": byts, "kernel_ms": ms}
 
     dominant = max(kernels, key=lambda k: kernels[k][0])
-    launches_per_step = 9  # k_minmax_sample, k_stage1, 2 x k_stage2, k_place, k_copy, 2 x k_unstage, k_decompress2
+    # k_minmax_sample, k_stage1, 2 x k_stage2 (small / large payloads),
+    # k_stage2_refine, k_place, k_copy, 2 x k_unstage, k_decompress2
+    launches_per_step = 10
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

@@ -36,9 +36,10 @@ struct S2Args {
   // speculative thresholds (spec): the stage kernel kept the details with
   // |d| >= t_lo, the threshold of the subsample's range (the header's
   // skmin / skmax), and marked in near[] the blocks that kept one below
-  // near_threshold(t_lo); t comes from the final keys.  The slots that hold
-  // a value below t are listed in rlist (count in the header's nref) and
-  // coded by k_stage2_refine.
+  // near_threshold(t_lo); t comes from the final keys.  Slots go to rlist
+  // (count in the header's nref): with block edges up to 16 those to test,
+  // for k_stage2_listed; with 32 those holding a value below t, for
+  // k_stage2_refine.
   int spec;
   const unsigned char *near;
   int *rlist;
@@ -82,6 +83,7 @@ constexpr int PLACE_TILE = 128;  // chunks (and threads) per k_place CTA
 // launch, which classifies by size, leaves it alone)
 constexpr unsigned long long TB_LOST = 0xFFFFFFFFFFFFFFFFull;
 constexpr unsigned long long TB_FIN = 1ull << 62;
+constexpr unsigned long long TB_SKIP = 1ull << 61;  // speculative thresholds: left to k_stage2_listed
 __device__ __forceinline__ unsigned long long tb_size(unsigned long long cb) { return cb & ~TB_FIN; }
 
 // ---- byte shuffle of payload words into SH: word k of raw (W words) holds
@@ -685,9 +687,46 @@ __global__ void __launch_bounds__(B * B / 2, 65536 / (B * B / 2 * 128))
   }
 }
 
-// ---- stage 2, in place, over the slots of all blocks
-template <typename T, int B, bool BIG>
-__global__ void __launch_bounds__(BIG ? 512 : 128) k_stage2(const S2Args a)
+// ---- speculative thresholds: the exact threshold t, and which slots are
+// tested against it (0: none, t_lo is t; 1: those marked near, t lies
+// within t_lo's near bound; 2: all)
+template <typename T>
+__device__ __forceinline__ int spec_mode(const S2Args &a, T &t)
+{
+  const WsHdr *h = reinterpret_cast<const WsHdr *>(a.ws);
+  t = threshold_between<T>(a.eps, a.eps_mode, h->minkey, h->maxkey);
+  const T tl = threshold_between<T>(a.eps, a.eps_mode, h->skmin, h->skmax);
+  return t_bits(tl) == t_bits(t) ? 0 : t <= near_threshold(tl) ? 1 : 2;
+}
+
+// ---- speculative thresholds, before stage 2 (block edges up to 16): flag
+// (TB_SKIP: the stage-2 launches pass over them) and list (rlist, count
+// nref) the slots to test against t, those marked near in mode 1 and all
+// in mode 2; k_stage2_listed takes them after the others
+template <typename T>
+__global__ void __launch_bounds__(256) k_spec_list(const S2Args a)
+{
+  T t;
+  const int mode = spec_mode<T>(a, t);
+  if (mode == 0) return;
+  WsHdr *hw = reinterpret_cast<WsHdr *>(const_cast<void *>(a.ws));
+  for (int b = blockIdx.x * 256 + threadIdx.x; b < a.nblocks; b += gridDim.x * 256) {
+    if (mode == 1 && a.near[b] == 0) continue;
+    const unsigned long long cb = a.table[2 * b + 1];
+    if (cb == TB_LOST || (cb & TB_FIN)) continue;
+    a.table[2 * b + 1] = cb | TB_SKIP;
+    a.rlist[atomicAdd(&hw->nref, 1u)] = b;
+  }
+}
+
+// ---- stage 2, in place, over the slots of all blocks.  SPEC (speculative
+// thresholds, S2Args::spec, block edge 32; a variant of its own, so that
+// the other keeps its registers): the slots to test (those marked near in
+// mode 1, all in mode 2) are tested against t, for FP32 while the payload
+// is shuffled, and one holding a value below t is listed (rlist, count
+// nref) for k_stage2_refine, which spreads those over its CTAs.
+template <typename T, int B, bool BIG, bool SPEC = false>
+__global__ void __launch_bounds__(BIG ? 512 : 128, BIG ? 4 : sizeof(T) == 4 ? 16 : 12) k_stage2(const S2Args a)
 {
   using G = G2<T, B>;
   constexpr int NT = BIG ? 512 : 128;
@@ -702,34 +741,23 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_stage2(const S2Args a)
   // those the stage kernel has coded already); the large launch visits
   // only the blocks the stage kernel listed
   const int count = BIG ? (int)reinterpret_cast<const WsHdr *>(a.ws)->nbig : a.nblocks;
-  // speculative thresholds: whether t_lo fell short of the exact
-  // threshold (then every slot is checked)
-  // (only the blocks marked near, where t is at most t_lo's near bound)
   T t = T(0);
-  bool check = false, all = false;
-  if (a.spec) {
-    const WsHdr *h = reinterpret_cast<const WsHdr *>(a.ws);
-    t = threshold_between<T>(a.eps, a.eps_mode, h->minkey, h->maxkey);
-    const T tl = threshold_between<T>(a.eps, a.eps_mode, h->skmin, h->skmax);
-    check = t_bits(tl) != t_bits(t);
-    all = !(t <= near_threshold(tl));
-  }
+  int mode = 0;
+  if constexpr (SPEC) mode = spec_mode<T>(a, t);
   for (int it = blockIdx.x; it < count; it += gridDim.x) {
     const int bid = BIG ? a.biglist[it] : it;
     const unsigned long long so = a.table[2 * bid], cb = a.table[2 * bid + 1];
     // (the mark is loaded with the table entry, so their latencies overlap)
-    const bool test = check && (all || a.near[bid] != 0);
-    if (cb == TB_LOST || (cb & TB_FIN)) continue;  // staging overflow, or finished already
-    int pbytes = (int)cb - 8;
+    const bool test = SPEC && (mode == 2 || (mode == 1 && a.near[bid] != 0));
+    // staging overflow, finished already, or left to k_stage2_listed
+    if (cb == TB_LOST || (cb & (TB_FIN | TB_SKIP))) continue;
+    const int pbytes = (int)cb - 8;
     if ((pbytes > G::SHCAP) != BIG) continue;  // the other launch's payload
     unsigned *ch = reinterpret_cast<unsigned *>(a.staging + so);
     unsigned cbytes;
     if (!test) {
       cbytes = stage2_chunk<T, NT>(ch, pbytes, smem, AUX, cap, s_u, s_i);
-    } else {
-      // speculative thresholds: the values are tested (FP32: while the
-      // payload is shuffled); a slot with one to drop is listed for
-      // k_stage2_refine, which spreads those over its CTAs
+    } else if constexpr (SPEC) {
       bool drop;
       if constexpr (sizeof(T) == 4) {
         constexpr int VW0 = (64 * 4 + G::MASKB) / 4;
@@ -743,8 +771,9 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_stage2(const S2Args a)
         if (!drop) shuffle_words<T, NT>(ch + 2, pbytes >> 2, 0, pbytes >> 3, smem);
         __syncthreads();
       }
-      if (drop) {
-        if (threadIdx.x == 0) a.rlist[atomicAdd(&reinterpret_cast<WsHdr *>(const_cast<void *>(a.ws))->nref, 1u)] = bid;
+      if (drop) {  // the slot is left as it is (only SH holds the shuffle)
+        if (threadIdx.x == 0)
+          a.rlist[atomicAdd(&reinterpret_cast<WsHdr *>(const_cast<void *>(a.ws))->nref, 1u)] = bid;
         continue;
       }
       cbytes = stage2_code<T, NT>(ch, pbytes, smem, AUX, cap, s_u, s_i);
@@ -753,8 +782,60 @@ __global__ void __launch_bounds__(BIG ? 512 : 128) k_stage2(const S2Args a)
   }
 }
 
-// ---- speculative thresholds: the slots the stage-2 launches listed (they
-// hold a value below the exact threshold t), one per CTA at a time: drop
+// ---- speculative thresholds, block edges up to 16: stage 2 of the slots
+// k_spec_list listed, CTAs and buffers as k_stage2's (BIG: the large
+// payloads).  The values are tested against t (FP32: while the payload is
+// shuffled); a slot holding one below t drops those first (refine_slot:
+// SH holds its values, AUX its keep bits), then is coded.  (Tested inside
+// k_stage2, the few slots to test made the common path of those small
+// blocks' launches about a quarter longer in instructions.)
+template <typename T, int B, bool BIG>
+__global__ void __launch_bounds__(BIG ? 512 : 128, BIG ? 4 : 12) k_stage2_listed(const S2Args a)
+{
+  using G = G2<T, B>;
+  constexpr int NT = BIG ? 512 : 128;
+  constexpr int CAPB = BIG ? G::PMAX_AL : G::SHCAP;
+  constexpr int cap = BIG ? G::NBWMAX : G::NBS;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ unsigned s_u[40];
+  __shared__ int s_i[40];
+  unsigned *AUX = reinterpret_cast<unsigned *>(smem + CAPB);
+  const WsHdr *h = reinterpret_cast<const WsHdr *>(a.ws);
+  const int count = (int)h->nref;
+  if ((int)blockIdx.x >= count) return;
+  const T t = threshold_between<T>(a.eps, a.eps_mode, h->minkey, h->maxkey);
+  for (int it = blockIdx.x; it < count; it += gridDim.x) {
+    const int bid = a.rlist[it];
+    const unsigned long long so = a.table[2 * bid], cb = a.table[2 * bid + 1];
+    int pbytes = (int)cb - 8;  // (the low half: TB_SKIP is a high bit)
+    if ((pbytes > G::SHCAP) != BIG) continue;  // the other launch's payload
+    unsigned *ch = reinterpret_cast<unsigned *>(a.staging + so);
+    bool drop;
+    if constexpr (sizeof(T) == 4) {
+      constexpr int VW0 = (64 * 4 + G::MASKB) / 4;
+      drop = __syncthreads_or(shuffle_check<T, NT>(ch + 2, pbytes >> 2, pbytes >> 2, smem, VW0, t));
+    } else {
+      const T *vals = reinterpret_cast<const T *>(reinterpret_cast<const unsigned char *>(ch + 2) + 64 * G::ES +
+                                                  G::MASKB);
+      bool d = false;
+      for (int j = threadIdx.x; j < (int)ch[0]; j += NT) d |= fabs(vals[j]) < t;
+      drop = __syncthreads_or(d);
+      if (!drop) shuffle_words<T, NT>(ch + 2, pbytes >> 2, 0, pbytes >> 3, smem);
+      __syncthreads();
+    }
+    unsigned cbytes;
+    if (drop) {  // the slot is as the stage kernel left it (SH holds the shuffle)
+      pbytes = refine_slot<T, B, NT, true>(ch, pbytes, t, smem, AUX, s_u);
+      cbytes = stage2_chunk<T, NT>(ch, pbytes, smem, AUX, cap, s_u, s_i);
+    } else {
+      cbytes = stage2_code<T, NT>(ch, pbytes, smem, AUX, cap, s_u, s_i);
+    }
+    if (threadIdx.x == 0) a.table[2 * bid + 1] = TB_FIN | (unsigned long long)cbytes;
+  }
+}
+
+// ---- speculative thresholds, block edge 32: the slots the stage-2 launches
+// listed (they hold a value below the exact threshold t), one per CTA at a time: drop
 // those values, then stage 2 as above.  512 threads, the payload buffer and
 // the bitmaps of the large launch.
 template <typename T, int B>

@@ -48,43 +48,78 @@ cudaError_t prepare(int smem)
   return e;
 }
 
-// stage 2 on every slot (small and large payloads), when enabled (a
-// template, so that only the kernels of this lane are instantiated)
-template <int = 0>
-cudaError_t stage2_k(const S2Args &sa, int stage2, int grid2, int grid3, cudaStream_t s)
+// one stage-2 launch (BIG: the large payloads, 512-thread CTAs); KIND 0:
+// k_stage2, 1: its speculative variant, 2: k_stage2_listed
+template <auto KERN, bool BIG>
+cudaError_t stage2_go(const S2Args &sa, int grid, cudaStream_t s)
 {
-  cudaError_t e = cudaSuccess;
-  if (stage2) {
-    e = prepare<k_stage2<CZ_T, CZ_B, false>>(G::SMEM_S2);
+  constexpr int sm = BIG ? G::SMEM_S2B : G::SMEM_S2;
+  cudaError_t e = prepare<KERN>(sm);
+  if (e != cudaSuccess) return e;
+  KERN<<<grid, BIG ? 512 : 128, sm, s>>>(sa);
+  return cudaGetLastError();
+}
+template <bool BIG, int KIND>
+cudaError_t stage2_one(const S2Args &sa, int grid, cudaStream_t s)
+{
+  if constexpr (KIND == 2)
+    return stage2_go<k_stage2_listed<CZ_T, CZ_B, BIG>, BIG>(sa, grid, s);
+  else
+    return stage2_go<k_stage2<CZ_T, CZ_B, BIG, KIND == 1>, BIG>(sa, grid, s);
+}
+
+// stage 2 on every slot (small and large payloads).  SPEC (speculative
+// thresholds): with block edges up to 16 the slots to test are listed
+// first and taken after the others by k_stage2_listed; with 32 they are
+// tested within k_stage2, and the listed slots that hold a value to drop
+// are refined after.  (Each measured the faster for its block edges.)
+template <bool SPEC>
+cudaError_t stage2_launch(const S2Args &sa, int grid2, int grid3, cudaStream_t s)
+{
+  constexpr bool LIST = SPEC && CZ_B <= 16;
+  constexpr int K = SPEC && !LIST ? 1 : 0;
+  if constexpr (LIST) {
+    const int gl = (sa.nblocks + 255) / 256 < grid2 ? (sa.nblocks + 255) / 256 : grid2;
+    k_spec_list<CZ_T><<<gl, 256, 0, s>>>(sa);
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_stage2<CZ_T, CZ_B, false><<<grid2, 128, G::SMEM_S2, s>>>(sa);
+  }
+  cudaError_t e = stage2_one<false, K>(sa, grid2, s);
+  if (e != cudaSuccess) return e;
+  if constexpr (G::SLAB) {
+    constexpr int sm = 4 * G::NBWMAX * 4;
+    e = prepare<k_stage2_huge<CZ_T, CZ_B>>(sm);
+    if (e != cudaSuccess) return e;
+    k_stage2_huge<CZ_T, CZ_B><<<grid3, 512, sm, s>>>(sa);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if constexpr (G::SLAB) {
-      constexpr int sm = 4 * G::NBWMAX * 4;
-      e = prepare<k_stage2_huge<CZ_T, CZ_B>>(sm);
-      if (e != cudaSuccess) return e;
-      k_stage2_huge<CZ_T, CZ_B><<<grid3, 512, sm, s>>>(sa);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-    } else if constexpr (G::HAS_BIG) {
-      e = prepare<k_stage2<CZ_T, CZ_B, true>>(G::SMEM_S2B);
-      if (e != cudaSuccess) return e;
-      k_stage2<CZ_T, CZ_B, true><<<grid3, 512, G::SMEM_S2B, s>>>(sa);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
+  } else {
+    if constexpr (G::HAS_BIG) {
+      if ((e = stage2_one<true, K>(sa, grid3, s)) != cudaSuccess) return e;
     }
-    if constexpr (!G::SLAB) {
-      if (sa.spec) {  // speculative thresholds: the listed slots, one per CTA
-        e = prepare<k_stage2_refine<CZ_T, CZ_B>>(G::SMEM_S2B);
-        if (e != cudaSuccess) return e;
-        k_stage2_refine<CZ_T, CZ_B><<<grid3, 512, G::SMEM_S2B, s>>>(sa);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-      }
+    if constexpr (LIST) {
+      if ((e = stage2_one<false, 2>(sa, grid2, s)) != cudaSuccess) return e;
+      if constexpr (G::HAS_BIG) e = stage2_one<true, 2>(sa, grid3, s);
+    } else if constexpr (SPEC) {
+      e = prepare<k_stage2_refine<CZ_T, CZ_B>>(G::SMEM_S2B);
+      if (e != cudaSuccess) return e;
+      k_stage2_refine<CZ_T, CZ_B><<<grid3, 512, G::SMEM_S2B, s>>>(sa);
+      e = cudaGetLastError();
     }
   }
   return e;
+}
+
+// stage 2, when enabled (a template, so that only the kernels of this lane
+// are instantiated); the speculative variant exists only for the lanes
+// whose stage kernel keeps the block in registers
+template <int = 0>
+cudaError_t stage2_k(const S2Args &sa, int stage2, int grid2, int grid3, cudaStream_t s)
+{
+  if (!stage2) return cudaSuccess;
+  if constexpr (!G::SLAB) {
+    if (sa.spec) return stage2_launch<true>(sa, grid2, grid3, s);
+  }
+  return stage2_launch<false>(sa, grid2, grid3, s);
 }
 
 // aggregate chunks: the three tiers of the group coder over the raw slots

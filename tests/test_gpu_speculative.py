@@ -43,6 +43,27 @@ def test_late_extreme_the_subsample_misses(kind, block, dtype, shape):
     np.testing.assert_array_equal(gpu_decompress(want).view(np.uint8), O.decompress(want).view(np.uint8))
 
 
+@pytest.mark.parametrize("excess", (5e-4, 2e-3))
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("block,dtype,shape", [(32, np.float32, (96, 64, 128)), (16, np.float32, (48, 64, 80)),
+                                                (8, np.float32, (32, 24, 40)), (16, np.float64, (48, 32, 64))])
+def test_range_just_beyond_the_subsample(kind, block, dtype, shape, excess):
+    """The field is clipped to its subsample's range (every 4th row of every
+    4th z-plane), then one voxel on no sampled row exceeds it by `excess` of
+    the range: t = (1 + excess) t_lo.  0.05 % lies within t_lo's near bound
+    (1 + 2^-10): only the slots marked near are tested; 0.2 % lies beyond
+    it: every slot is.  Small and large payloads (eps down to 1e-5)."""
+    f = _smooth(shape, dtype, seed=3 * block + kind)
+    s = f[::4, ::4, :]
+    lo, hi = float(s.min()), float(s.max())
+    f = np.clip(f, lo, hi).astype(dtype)
+    f[-3, -(block - 1), -2] = hi + excess * (hi - lo)
+    for eps in (1e-3, 1e-4, 1e-5):
+        want = O.compress(f, block, kind, eps)
+        got = gpu_compress(f, block, kind, eps)
+        assert got == want, describe_diff(got, want)
+
+
 @pytest.mark.parametrize("kind", KINDS)
 def test_negative_extreme_first_then_positive_late(kind):
     f = _smooth((64, 64, 96), np.float32, seed=9)
