@@ -401,27 +401,6 @@ __device__ __forceinline__ void send_extremes(T lo, T hi, unsigned long long *s_
   }
 }
 
-// the same for a block tile of `bytes` bytes in shared memory, read by NT
-// threads in 16-byte pieces (out of line: the FP32 32^3 W3ai stage kernel,
-// which takes this path, keeps its registers for the transform)
-template <typename T, int NT>
-__device__ __noinline__ void tile_extremes(const unsigned char *tile, int bytes, unsigned long long *s_kc, WsHdr *ws)
-{
-  T lo = (T)INFINITY, hi = (T)-INFINITY;
-  for (int q = threadIdx.x; q < bytes / 16; q += NT) {
-    if constexpr (sizeof(T) == 4) {
-      const float4 w = reinterpret_cast<const float4 *>(tile)[q];
-      lo = min3_nn(min3_nn(lo, w.x, w.y), w.z, w.w);
-      hi = max3_nn(max3_nn(hi, w.x, w.y), w.z, w.w);
-    } else {
-      const double2 w = reinterpret_cast<const double2 *>(tile)[q];
-      lo = min3_nn(lo, w.x, w.y);
-      hi = max3_nn(hi, w.x, w.y);
-    }
-  }
-  send_extremes<T>(lo, hi, s_kc, ws);
-}
-
 // SPEC (NF = 1): speculative thresholds (FwdArgs::spec).  At most 128
 // registers a thread, whatever the block edge (enough CTAs per SM for the
 // smaller edges: the speculative variant would otherwise take more)
@@ -529,11 +508,8 @@ __global__ void __launch_bounds__(B * B / 2, 65536 / (B * B / 2 * 128))
     // swizzled places.
     constexpr bool RX = G::template rowx<KIND>();
     // speculative thresholds: the block's min / max into the header's keys,
-    // from the pairs as they are loaded, or where that leaves the kernel
-    // short of registers (FP32 32^3 W3ai) from the tile before the pairs
-    // are loaded; the W4li row pass takes it from the rows it reads
-    constexpr bool MM_TILE = SPEC && !RX && sizeof(T) == 4 && B == 32 && KIND == W3AI;
-    if constexpr (MM_TILE) tile_extremes<T, NT>(PF, G::TILE, s_kc, ws);
+    // from the pairs as they are loaded; the W4li row pass takes it from the
+    // rows it reads
     if constexpr (RX) {
       if constexpr (SPEC) {
         T lo = (T)INFINITY, hi = (T)-INFINITY;
@@ -553,7 +529,7 @@ __global__ void __launch_bounds__(B * B / 2, 65536 / (B * B / 2 * 128))
         const unsigned o = (unsigned)((((h * ZH + zl) * B + 2 * k + r) * B + x0) * ES);
         v[r][zl] = *reinterpret_cast<const T2 *>(PF + (RX ? swz128(o) : o));
       }
-    if constexpr (SPEC && !RX && !MM_TILE) {
+    if constexpr (SPEC && !RX) {
       T lo = (T)INFINITY, hi = (T)-INFINITY;
 #pragma unroll
       for (int r = 0; r < 2; ++r)
