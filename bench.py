@@ -472,10 +472,13 @@ def run_gpu(args, rank, world, local_rank):
 
     # end to end through the ABI with host buffers (pinned), copies included:
     # every step uploads the field, compresses, downloads the stream, decodes
-    # and downloads the field.  Two fields are in flight on two streams, so
-    # one field's upload overlaps the previous field's download (the link
-    # carries both directions at once); each step's copies are inside the
-    # timed region.
+    # and downloads the field.  Uploads, compressions, decodes, stream and
+    # field downloads each run on a stream of their own, ordered by events;
+    # two sets of device buffers let one field's upload overlap the previous
+    # field's download (the link carries both directions at once).  The host
+    # reads a step's stream length (and enqueues its downloads and decode)
+    # once the next step's upload and compression are queued.  Every step's
+    # copies are inside the timed region.
     e2e = None
     if not args.no_e2e:
         h_in = torch.from_numpy(field_np).pin_memory()
@@ -483,58 +486,88 @@ def run_gpu(args, rank, world, local_rank):
         lanes = []
         for q in range(depth):
             lanes.append({
-                "st": torch.cuda.Stream(dev),
                 "field": field if q == 0 else torch.empty_like(field),
                 "out": out if q == 0 else torch.empty_like(out),
                 "ws": ws if q == 0 else torch.empty_like(ws),
+                "ws_d": torch.empty_like(ws),
                 "nb": nb if q == 0 else torch.empty_like(nb),
                 "rec": rec if q == 0 else torch.empty_like(rec),
                 "h_out": torch.empty_like(h_in).pin_memory(),
                 "h_stream": torch.empty(cap, dtype=torch.uint8).pin_memory(),
                 "h_nb": torch.empty(1, dtype=torch.int64).pin_memory(),
+                # the lane's buffers: field consumed, stream downloaded and
+                # decoded, decoded field downloaded
+                "ev_comp": torch.cuda.Event(), "ev_sdown": torch.cuda.Event(), "ev_dec": torch.cuda.Event(),
+                "ev_fdown": torch.cuda.Event(),
             })
+        s_up, s_c, s_d, s_sd, s_fd = (torch.cuda.Stream(dev) for _ in range(5))
+        for L in lanes:
+            for e_ in (L["ev_comp"], L["ev_sdown"], L["ev_dec"], L["ev_fdown"]):
+                e_.record(s_c)
         torch.cuda.synchronize()
         copied_in = copied_out = 0
 
-        def e2e_step(i):
-            nonlocal copied_in, copied_out
+        def e2e_front(i):
+            """Upload and compress field i (its lane's buffers once free)."""
             L = lanes[i % depth]
-            st = L["st"]
-            sp = st.cuda_stream
-            with torch.cuda.stream(st):
+            ev_up = torch.cuda.Event()
+            with torch.cuda.stream(s_up):
+                s_up.wait_event(L["ev_comp"])  # the lane's previous field is consumed
                 L["field"].copy_(h_in, non_blocking=True)
+                ev_up.record(s_up)
+            for e_ in (ev_up, L["ev_sdown"], L["ev_dec"]):  # the lane's previous stream is read
+                s_c.wait_event(e_)
             r = cz.cz_compress(p, L["field"].data_ptr(), L["out"].data_ptr(), cap, L["nb"].data_ptr(),
-                               L["ws"].data_ptr(), L["ws"].numel(), sp)
+                               L["ws"].data_ptr(), L["ws"].numel(), s_c.cuda_stream)
             if r != cz.OK:
                 raise cz.CzError(r, "cz_compress")
-            with torch.cuda.stream(st):
+            with torch.cuda.stream(s_c):
                 L["h_nb"].copy_(L["nb"], non_blocking=True)
-            st.synchronize()
+                L["ev_comp"].record(s_c)
+
+        def e2e_back(i):
+            """Download stream i, decode it and download the field."""
+            nonlocal copied_in, copied_out
+            L = lanes[i % depth]
+            L["ev_comp"].synchronize()
             ln = int(L["h_nb"].item())
-            with torch.cuda.stream(st):
+            with torch.cuda.stream(s_sd):
+                s_sd.wait_event(L["ev_comp"])
                 L["h_stream"][:ln].copy_(L["out"][:ln], non_blocking=True)
+                L["ev_sdown"].record(s_sd)
+            s_d.wait_event(L["ev_comp"])
+            s_d.wait_event(L["ev_fdown"])  # the lane's previous field is downloaded
             r = cz.lib().cz_decompress(L["out"].data_ptr(), ln, hdr_c, L["rec"].data_ptr(), nbytes_field,
-                                       L["ws"].data_ptr(), L["ws"].numel(), sp)
+                                       L["ws_d"].data_ptr(), L["ws_d"].numel(), s_d.cuda_stream)
             if r != cz.OK:
                 raise cz.CzError(r, "cz_decompress")
-            with torch.cuda.stream(st):
+            L["ev_dec"].record(s_d)
+            with torch.cuda.stream(s_fd):
+                s_fd.wait_event(L["ev_dec"])
                 L["h_out"].copy_(L["rec"], non_blocking=True)
+                L["ev_fdown"].record(s_fd)
             copied_in = nbytes_field
             copied_out = 8 + ln + nbytes_field
 
-        for i in range(depth):
-            e2e_step(i)
+        def e2e_run(steps):
+            for i in range(steps):
+                e2e_front(i)
+                if i > 0:
+                    e2e_back(i - 1)
+            e2e_back(steps - 1)
+
+        e2e_run(depth)
         torch.cuda.synchronize()
-        reps = max(4, min(args.steps, 8))
+        reps = max(4, min(args.steps, 16))
         t0 = time.perf_counter()
-        for i in range(reps):
-            e2e_step(i)
+        e2e_run(reps)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / reps
         for L in lanes:
-            st_ = cz.cz_status(L["ws"].data_ptr(), L["st"].cuda_stream)
-            if st_ != cz.OK:
-                raise cz.CzError(st_, "device status after the end-to-end steps")
+            for w_ in (L["ws"], L["ws_d"]):
+                st_ = cz.cz_status(w_.data_ptr(), s_c.cuda_stream)
+                if st_ != cz.OK:
+                    raise cz.CzError(st_, "device status after the end-to-end steps")
         if not torch.equal(lanes[0]["h_out"], lanes[1]["h_out"]):
             raise RuntimeError("end-to-end: the two lanes decoded different fields")
         e2e = {"value": world * nbytes_field / e2e_s / 1e9, "unit": UNIT,
@@ -556,7 +589,7 @@ def run_gpu(args, rank, world, local_rank):
         # streams, as in the end-to-end steps): the bound of a step that
         # uploads one field while it downloads another
         cur = torch.cuda.current_stream(dev)
-        sa, sb = lanes[0]["st"], lanes[1]["st"]
+        sa, sb = s_fd, s_up
         both = []
         for _ in range(3):
             e0, ea, eb, e1 = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
