@@ -14,7 +14,11 @@
 // zero-word runs are found from a ballot bitmap with one block scan, and
 // the chunk [nnz | ntok | tokens | literal words] replaces the slot's
 // contents.  Small CTAs take the payloads of up to G2::SHCAP bytes, a
-// second launch with large CTAs the rest.
+// second launch with large CTAs the rest.  With speculative thresholds the
+// slots that may hold a detail below the exact threshold are tested too:
+// inside a variant of k_stage2 for 32^3 blocks (k_stage2_refine then
+// refines those that do), after the others by k_stage2_listed for 8^3 and
+// 16^3 blocks (k_spec_list lists them first).
 //
 // k_place (one CTA per tile of 128 chunks, ticket order): chunk offsets by
 // a block scan plus one decoupled look-back per tile, offset-table entries;
